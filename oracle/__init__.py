@@ -1,0 +1,311 @@
+"""FP64 CPU oracle for radiance-texture synthesis -- TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the benchmark's
+CPU-baseline leg may import this package.  The product path (the CUDA library
+and its Python binding) never imports it, and this package imports nothing
+from the product path.
+
+The arithmetic lives in ``radtex_oracle.c`` (plain C11, FP64, OpenMP over
+fragments); this module only compiles it with gcc and marshals numpy arrays
+through ctypes.  Every function cites the passage of Fober, "Radiance Textures
+for Rasterizing Ray-Traced Data" (arXiv 2301.01719) it follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+F32, F16, BF16, E4M3, F64 = 0, 1, 2, 3, 4
+NEAREST, ANGULAR_BILINEAR, QUADRILINEAR = 0, 1, 2
+FLAG_BAD_OBJ, FLAG_NONFINITE = 1, 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "radtex_oracle.c")
+_LIB = os.path.join(_HERE, "libradtex_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_CODE_DTYPE = {F32: np.float32, F16: np.uint16, BF16: np.uint16, E4M3: np.uint8, F64: np.float64}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (C11, FP contraction off, OpenMP)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC",
+           "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            P, I32, I64, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+            sig = {
+                "oracle_equisolid": (None, [I64, P, P]),
+                "oracle_equisolid_normal": (None, [I64, P, P, P]),
+                "oracle_squarify": (None, [I64, P, P]),
+                "oracle_unsquarify": (None, [I64, P, P]),
+                "oracle_equisolid_inverse": (None, [I64, P, P]),
+                "oracle_equisolid_inverse_normal": (None, [I64, P, P, P]),
+                "oracle_reflection": (None, [I64, P, P]),
+                "oracle_texel_directions": (None, [I32, P]),
+                "oracle_encode": (None, [I32, I64, P, P]),
+                "oracle_decode": (None, [I32, I64, P, P]),
+                "oracle_encode_e4m3_buckets": (None, [I32, I32, I32, P, P, P]),
+                "oracle_locate": (U32, [P, P, I32, I64, P, P, P, I32, P, P]),
+                "oracle_shade": (U32, [P, P, P, I32, I64, P, P, P, I32, P]),
+                "oracle_shade64": (U32, [P, P, P, I32, I64, P, P, P, I32, P]),
+                "oracle_shade_backward": (U32, [P, P, P, I32, I64, P, P, P, I32, P, P, P, P]),
+                "oracle_shade_backward64": (U32, [P, P, P, I32, I64, P, P, P, I32, P, P, P, P]),
+                "oracle_eval_field": (None, [P, I32, I64, P, P, P]),
+                "oracle_fill_field": (None, [I32, I32, I32, P, I32, P]),
+                "oracle_fill_bucket_lobes": (None, [I32, I32, I32, P, P]),
+                "oracle_num_threads": (I32, []),
+                "oracle_set_num_threads": (None, [I32]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# --------------------------------------------------------------------------
+# Section 2.1 mapping functions (rows of vectors).
+# --------------------------------------------------------------------------
+
+def _map(name: str, x, width_in: int, width_out: int, extra=None) -> np.ndarray:
+    x = _c(x, np.float64).reshape(-1, width_in)
+    out = np.empty((x.shape[0], width_out))
+    if extra is None:
+        getattr(lib(), name)(x.shape[0], _p(x), _p(out))
+    else:
+        e = _c(extra, np.float64).reshape(-1, 3)
+        e = np.broadcast_to(e, (x.shape[0], 3)).copy()
+        getattr(lib(), name)(x.shape[0], _p(x), _p(e), _p(out))
+    return out
+
+
+def equisolid(I) -> np.ndarray:
+    """Eq. 1b: tangent-space incidence (k x 3) -> equisolid coordinate A (k x 2)."""
+    return _map("oracle_equisolid", I, 3, 2)
+
+
+def equisolid_normal(I, N) -> np.ndarray:
+    """Eq. 1a: sqrt(2) normalize(I + N), k x 3."""
+    return _map("oracle_equisolid_normal", I, 3, 3, N)
+
+
+def squarify(A) -> np.ndarray:
+    """Eq. 3: disc -> square, A (k x 2) -> B (k x 2)."""
+    return _map("oracle_squarify", A, 2, 2)
+
+
+def unsquarify(B) -> np.ndarray:
+    """Eq. 4a: square -> disc, B (k x 2) -> A (k x 2)."""
+    return _map("oracle_unsquarify", B, 2, 2)
+
+
+def equisolid_inverse(A) -> np.ndarray:
+    """Eq. 2c: A (k x 2) -> incidence I (k x 3), tangent space."""
+    return _map("oracle_equisolid_inverse", A, 2, 3)
+
+
+def equisolid_inverse_normal(A, N) -> np.ndarray:
+    """Eq. 2a-2b: A (k x 2) and a normal N -> incidence I (k x 3)."""
+    return _map("oracle_equisolid_inverse_normal", A, 2, 3, N)
+
+
+def reflection(A) -> np.ndarray:
+    """Eq. 4b: A (k x 2) -> equisolid reflection vector R (k x 3)."""
+    return _map("oracle_reflection", A, 2, 3)
+
+
+def texel_directions(n: int) -> np.ndarray:
+    """Directions of the n x n texel centres of a bucket (Eq. 4a then Eq. 2c), shape (n, n, 3) indexed [t, s]."""
+    out = np.empty((n, n, 3))
+    lib().oracle_texel_directions(n, _p(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Storage formats.
+# --------------------------------------------------------------------------
+
+def encode(fmt: int, x) -> np.ndarray:
+    """FP32 values -> codes of F32 / F16 / BF16 / E4M3 (no scale), round to nearest even."""
+    x = _c(x, np.float32)
+    out = np.empty(x.shape, dtype=_CODE_DTYPE[fmt])
+    lib().oracle_encode(fmt, x.size, _p(x), _p(out))
+    return out
+
+
+def decode(fmt: int, codes) -> np.ndarray:
+    codes = _c(codes, _CODE_DTYPE[fmt])
+    out = np.empty(codes.shape, dtype=np.float64)
+    lib().oracle_decode(fmt, codes.size, _p(codes), _p(out))
+    return out
+
+
+def encode_e4m3_buckets(atlas: np.ndarray, W: int, H: int, n: int):
+    """FP32 atlas ((h n) x (w n) x 4) -> (E4M3 codes, per-bucket FP32 scales (h x w))."""
+    atlas = _c(atlas, np.float32)
+    assert atlas.shape == (H * n, W * n, 4)
+    codes = np.empty(atlas.shape, dtype=np.uint8)
+    scales = np.empty((H, W), dtype=np.float32)
+    lib().oracle_encode_e4m3_buckets(W, H, n, _p(atlas), _p(codes), _p(scales))
+    return codes, scales
+
+
+class Texture:
+    """A texture as the oracle sees it: stored codes in the atlas layout plus E4M3 scales."""
+
+    def __init__(self, W: int, H: int, n: int, fmt: int, codes: np.ndarray, scales: np.ndarray | None = None):
+        self.W, self.H, self.n, self.fmt = int(W), int(H), int(n), int(fmt)
+        self.codes = _c(codes, _CODE_DTYPE[fmt])
+        assert self.codes.shape == (H * n, W * n, 4), self.codes.shape
+        self.scales = None if scales is None else _c(scales, np.float32)
+
+    @classmethod
+    def from_f32(cls, atlas: np.ndarray, W: int, H: int, n: int, fmt: int) -> "Texture":
+        """Quantise an FP32 atlas with the oracle's own encoders."""
+        if fmt == E4M3:
+            codes, scales = encode_e4m3_buckets(atlas, W, H, n)
+            return cls(W, H, n, fmt, codes, scales)
+        if fmt == F64:
+            return cls(W, H, n, fmt, np.asarray(atlas, dtype=np.float64))
+        return cls(W, H, n, fmt, encode(fmt, atlas))
+
+    def values(self) -> np.ndarray:
+        """The stored texels decoded exactly to FP64, atlas layout."""
+        v = decode(self.fmt, self.codes)
+        if self.fmt == E4M3:
+            v = v * np.repeat(np.repeat(self.scales.astype(np.float64), self.n, 0), self.n, 1)[..., None]
+        return v
+
+
+def _tables(textures):
+    dims = np.zeros((max(len(textures), 1), 4), dtype=np.int32)
+    codes = (ctypes.c_void_p * max(len(textures), 1))()
+    scales = (ctypes.c_void_p * max(len(textures), 1))()
+    for o, T in enumerate(textures):
+        if T is None:
+            continue
+        dims[o] = (T.W, T.H, T.n, T.fmt)
+        codes[o] = T.codes.ctypes.data
+        scales[o] = None if T.scales is None else T.scales.ctypes.data
+    return dims, codes, scales
+
+
+def _gbuf(uv, dirs, obj, dtype):
+    uv = _c(uv, dtype).reshape(-1, 2)
+    dirs = _c(dirs, dtype).reshape(-1, 3)
+    obj = _c(obj, np.int32).reshape(-1)
+    assert uv.shape[0] == dirs.shape[0] == obj.shape[0]
+    return uv, dirs, obj
+
+
+def shade(textures, uv, dirs, obj, filt: int, precise_inputs: bool = False):
+    """Forward synthesis (Section 2): F x 4 FP64 colours and the OR of the error flags.
+
+    textures: list indexed by object id (None for a missing object).
+    uv: F x 2, dirs: F x 3 (FP32 unless precise_inputs), obj: F int32 (< 0 = background).
+    """
+    dtype = np.float64 if precise_inputs else np.float32
+    uv, dirs, obj = _gbuf(uv, dirs, obj, dtype)
+    dims, codes, scales = _tables(textures)
+    out = np.empty((obj.shape[0], 4))
+    fn = lib().oracle_shade64 if precise_inputs else lib().oracle_shade
+    flags = fn(_p(dims), codes, scales, len(textures), obj.shape[0], _p(uv), _p(dirs), _p(obj), filt, _p(out))
+    return out, int(flags)
+
+
+def locate(textures, uv, dirs, obj, filt: int):
+    """Floors (F x 4 int32: u, v, s, t) and continuous coordinates (F x 4 FP64) of every fragment."""
+    uv, dirs, obj = _gbuf(uv, dirs, obj, np.float32)
+    dims, codes, _ = _tables(textures)
+    idx = np.empty((obj.shape[0], 4), dtype=np.int32)
+    coord = np.empty((obj.shape[0], 4))
+    flags = lib().oracle_locate(_p(dims), codes, len(textures), obj.shape[0], _p(uv), _p(dirs), _p(obj), filt,
+                                _p(idx), _p(coord))
+    return idx, coord, int(flags)
+
+
+def shade_backward(textures, uv, dirs, obj, filt: int, dL_dout, want_tex=True, want_uv=True, want_dir=True,
+                   precise_inputs: bool = False):
+    """Analytic FP64 gradients: (dL/dtex list of FP64 atlases or None, dL/duv F x 2, dL/ddir F x 3, flags)."""
+    dtype = np.float64 if precise_inputs else np.float32
+    uv, dirs, obj = _gbuf(uv, dirs, obj, dtype)
+    dims, codes, scales = _tables(textures)
+    g = _c(dL_dout, np.float64).reshape(-1, 4)
+    F = obj.shape[0]
+    gtex = [None] * len(textures)
+    gptr = (ctypes.c_void_p * max(len(textures), 1))()
+    if want_tex:
+        for o, T in enumerate(textures):
+            if T is not None:
+                gtex[o] = np.zeros((T.H * T.n, T.W * T.n, 4))
+                gptr[o] = gtex[o].ctypes.data
+    guv = np.empty((F, 2)) if want_uv else None
+    gdir = np.empty((F, 3)) if want_dir else None
+    fn = lib().oracle_shade_backward64 if precise_inputs else lib().oracle_shade_backward
+    flags = fn(_p(dims), codes, scales, len(textures), F, _p(uv), _p(dirs), _p(obj), filt, _p(g),
+               gptr if want_tex else None, _p(guv), _p(gdir))
+    return (gtex if want_tex else None), guv, gdir, int(flags)
+
+
+# --------------------------------------------------------------------------
+# Fills.
+# --------------------------------------------------------------------------
+
+def fill_field(W: int, H: int, n: int, lobes: np.ndarray) -> np.ndarray:
+    """FP32 atlas filled from the analytic multi-lobe field (rows of 11 parameters)."""
+    lobes = _c(lobes, np.float64).reshape(-1, 11)
+    atlas = np.empty((H * n, W * n, 4), dtype=np.float32)
+    lib().oracle_fill_field(W, H, n, _p(lobes), lobes.shape[0], _p(atlas))
+    return atlas
+
+
+def eval_field(lobes: np.ndarray, uv, dirs) -> np.ndarray:
+    lobes = _c(lobes, np.float64).reshape(-1, 11)
+    uv = _c(uv, np.float64).reshape(-1, 2)
+    dirs = _c(dirs, np.float64).reshape(-1, 3)
+    out = np.empty((uv.shape[0], 4))
+    lib().oracle_eval_field(_p(lobes), lobes.shape[0], uv.shape[0], _p(uv), _p(dirs), _p(out))
+    return out
+
+
+def fill_bucket_lobes(W: int, H: int, n: int, params: np.ndarray) -> np.ndarray:
+    """FP32 atlas from one cosine-power lobe per bucket (params: h x w x 8 FP32)."""
+    params = _c(params, np.float32).reshape(H * W, 8)
+    atlas = np.empty((H * n, W * n, 4), dtype=np.float32)
+    lib().oracle_fill_bucket_lobes(W, H, n, _p(params), _p(atlas))
+    return atlas
+
+
+def num_threads() -> int:
+    return int(lib().oracle_num_threads())
+
+
+def set_num_threads(k: int) -> None:
+    lib().oracle_set_num_threads(int(k))

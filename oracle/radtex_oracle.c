@@ -1,0 +1,782 @@
+/*
+ * radtex_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, double-precision CPU oracle for per-fragment radiance-texture
+ * synthesis, written from J. M. Fober, "Radiance Textures for Rasterizing
+ * Ray-Traced Data" (arXiv 2301.01719).  Only the test suite, the smoke check
+ * and the benchmark's CPU-baseline leg load this library.  It shares no code,
+ * header, table or helper with the CUDA library, and the CUDA library never
+ * calls it.
+ *
+ * What it computes, per fragment (Section 2, "Methodology"):
+ *   - the surface UV selects a bucket of the w x h bucket matrix;
+ *   - the tangent-space incidence I is projected with the equisolid mapping
+ *     (Eq. 1b), made square with the disc-to-square mapping (Eq. 3) and
+ *     clamped to the texel-centre range of the Note after Eq. 3;
+ *   - the selected texels are filtered: NEAREST, ANGULAR_BILINEAR (one bucket,
+ *     bilinear inside it: "single sample per bucket"), or QUADRILINEAR
+ *     (separable tent filter over u, v and the two in-bucket axes).
+ * The colour is the plain weighted sum over the taps, sum(w_u w_v w_s w_t T),
+ * evaluated in FP64 on texels decoded exactly from their stored codes.
+ *
+ * Readings of points the paper leaves open (each also listed in the design
+ * notes of the repository):
+ *   R1  I points from the surface to the eye, in the tangent frame (x along
+ *       dP/du, y along dP/dv, z = N).  Eq. 1b is applied literally, without
+ *       renormalising I; I = -N (zero denominator) maps to A = 0.
+ *   R2  Eq. 3 is singular only at A = 0, which maps to B = 0 (the limit); the
+ *       printed condition "A_x and A_y != 0" is read as "A != 0".
+ *   R3  Texel k of an n-texel bucket axis has its centre at B = (2k+1)/n - 1;
+ *       the clamp range [1/n - 1, 1 - 1/n] of the Note is then exactly the
+ *       first and last centre.  B_x selects the column s, B_y the row t;
+ *       u selects the bucket column i, v the bucket row j, no flip.
+ *   R4  Atlas layout: row-major (h n) x (w n) texels of 4 channels (RGBA),
+ *       texel (i, j, s, t) at row j n + t, column i n + s (Section 1.3
+ *       naming convention, Section 2 first paragraph).
+ *   R5  Spatial filtering: nearest bucket i = clamp(floor(u w), 0, w-1); the
+ *       bilinear coordinate is c = u w - 1/2 clamped to [-1, w], taps
+ *       clamp(floor(c)) and clamp(floor(c)+1) (clamp to edge).  Angular axes
+ *       use c = (B+1) n/2 (nearest) or (B+1) n/2 - 1/2 (bilinear) with the
+ *       same floor-and-clamp rule.  An exact boundary goes to the higher
+ *       index (floor).
+ *   R6  Gradients: at an integer coordinate the floor branch is taken; a
+ *       clamped coordinate has zero derivative; at |A_x| = |A_y| Eq. 3 uses
+ *       the x branch; at A = 0 the Jacobian of Eq. 3 is the identity.
+ *   R7  Storage formats: FP32, FP16 and BF16 round to nearest-even from FP32;
+ *       FP8 E4M3 (OCP 8-bit floating point, max finite 448, no infinities)
+ *       rounds to nearest-even with saturation, on v / s where s is one FP32
+ *       scale per bucket, s = amax / 448 (s = 1 if amax = 0).  The quantising
+ *       decision is taken in FP32, like the device encoder.
+ *
+ * Build: gcc -std=c11 -O2 -ffp-contract=off -fopenmp -shared -fPIC.
+ * FP contraction stays off so the results do not depend on the host ISA.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_F32 0
+#define OR_F16 1
+#define OR_BF16 2
+#define OR_E4M3 3
+#define OR_F64 4 /* oracle-only exact format, used by the pins */
+
+#define OR_NEAREST 0
+#define OR_ANGULAR_BILINEAR 1
+#define OR_QUADRILINEAR 2
+
+#define OR_FLAG_BAD_OBJ 1u
+#define OR_FLAG_NONFINITE 2u
+
+static const double SQRT2 = 1.41421356237309504880168872420969808;
+
+/* ------------------------------------------------------------------------ */
+/* Section 2.1: the incidence-to-bucket mapping and its inverses.           */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 1b: tangent-space equisolid projection (N_z = 1),
+ * A = sqrt(2) (I_x, I_y) / |(I_x, I_y, I_z + 1)|. */
+static void equisolid_ts(const double I[3], double A[2]) {
+    double zp = I[2] + 1.0;
+    double D = sqrt(I[0] * I[0] + I[1] * I[1] + zp * zp);
+    if (D == 0.0) {
+        A[0] = 0.0;
+        A[1] = 0.0;
+        return;
+    }
+    A[0] = SQRT2 * I[0] / D;
+    A[1] = SQRT2 * I[1] / D;
+}
+
+/* Eq. 1a: general normal.  The vector sqrt(2) * (I + N) / |I + N| whose first
+ * two entries are A (in a frame where N is the z axis) and whose last entry is
+ * sqrt(2) cos(theta/2).  The double bar of the equation is read as "normalise". */
+static void equisolid_normal(const double I[3], const double N[3], double A3[3]) {
+    double h[3] = {I[0] + N[0], I[1] + N[1], I[2] + N[2]};
+    double L = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+    if (L == 0.0) {
+        A3[0] = A3[1] = A3[2] = 0.0;
+        return;
+    }
+    for (int k = 0; k < 3; ++k) A3[k] = SQRT2 * h[k] / L;
+}
+
+/* Eq. 3: disc to square, B = A |A| / max(|A_x|, |A_y|); A = 0 gives B = 0. */
+static void squarify(const double A[2], double B[2]) {
+    double m = fmax(fabs(A[0]), fabs(A[1]));
+    if (m == 0.0) {
+        B[0] = 0.0;
+        B[1] = 0.0;
+        return;
+    }
+    double r = sqrt(A[0] * A[0] + A[1] * A[1]);
+    B[0] = A[0] * r / m;
+    B[1] = A[1] * r / m;
+}
+
+/* Eq. 4a: square to disc, A = B max(|B_x|, |B_y|) / |B|; B = 0 gives A = 0. */
+static void unsquarify(const double B[2], double A[2]) {
+    double r = sqrt(B[0] * B[0] + B[1] * B[1]);
+    if (r == 0.0) {
+        A[0] = 0.0;
+        A[1] = 0.0;
+        return;
+    }
+    double m = fmax(fabs(B[0]), fabs(B[1]));
+    A[0] = B[0] * m / r;
+    A[1] = B[1] * m / r;
+}
+
+/* Eq. 2c: tangent-space inverse equisolid mapping,
+ * I = (A_x sqrt(2 - |A|^2), A_y sqrt(2 - |A|^2), 1 - |A|^2). */
+static void equisolid_inverse_ts(const double A[2], double I[3]) {
+    double a2 = A[0] * A[0] + A[1] * A[1];
+    double s = sqrt(2.0 - a2);
+    I[0] = A[0] * s;
+    I[1] = A[1] * s;
+    I[2] = 1.0 - a2;
+}
+
+/* Eq. 2a then Eq. 2b: the half vector A' = (A_x / sqrt 2, A_y / sqrt 2,
+ * sqrt(1 - |A|^2 / 2)), then I = 2((A' . N) A' - N) + N. */
+static void equisolid_inverse_normal(const double A[2], const double N[3], double I[3]) {
+    double Ap[3];
+    Ap[0] = A[0] * sqrt(0.5);
+    Ap[1] = A[1] * sqrt(0.5);
+    Ap[2] = sqrt(1.0 - A[0] * A[0] / 2.0 - A[1] * A[1] / 2.0);
+    double d = Ap[0] * N[0] + Ap[1] * N[1] + Ap[2] * N[2];
+    for (int k = 0; k < 3; ++k) I[k] = 2.0 * (d * Ap[k] - N[k]) + N[k];
+}
+
+/* Eq. 4b: equisolid reflection vector,
+ * R = (-A_x sqrt(2 - |A|^2), -A_y sqrt(2 - |A|^2), 1 - |A|^2). */
+static void reflection(const double A[2], double R[3]) {
+    double a2 = A[0] * A[0] + A[1] * A[1];
+    double s = sqrt(2.0 - a2);
+    R[0] = -A[0] * s;
+    R[1] = -A[1] * s;
+    R[2] = 1.0 - a2;
+}
+
+/* Reading R3: centre of texel k on an n-texel bucket axis, in B units. */
+static double texel_centre(int64_t k, int64_t n) { return (2.0 * (double)k + 1.0) / (double)n - 1.0; }
+
+/* Direction of the texel centre (s, t): Eq. 4a then Eq. 2c. */
+static void texel_direction(int64_t s, int64_t t, int64_t n, double I[3]) {
+    double B[2] = {texel_centre(s, n), texel_centre(t, n)};
+    double A[2];
+    unsquarify(B, A);
+    equisolid_inverse_ts(A, I);
+}
+
+/* Batched entry points of the mapping functions (rows of 2 or 3 doubles). */
+void oracle_equisolid(int64_t count, const double* I, double* A) {
+    for (int64_t k = 0; k < count; ++k) equisolid_ts(I + 3 * k, A + 2 * k);
+}
+void oracle_equisolid_normal(int64_t count, const double* I, const double* N, double* A3) {
+    for (int64_t k = 0; k < count; ++k) equisolid_normal(I + 3 * k, N + 3 * k, A3 + 3 * k);
+}
+void oracle_squarify(int64_t count, const double* A, double* B) {
+    for (int64_t k = 0; k < count; ++k) squarify(A + 2 * k, B + 2 * k);
+}
+void oracle_unsquarify(int64_t count, const double* B, double* A) {
+    for (int64_t k = 0; k < count; ++k) unsquarify(B + 2 * k, A + 2 * k);
+}
+void oracle_equisolid_inverse(int64_t count, const double* A, double* I) {
+    for (int64_t k = 0; k < count; ++k) equisolid_inverse_ts(A + 2 * k, I + 3 * k);
+}
+void oracle_equisolid_inverse_normal(int64_t count, const double* A, const double* N, double* I) {
+    for (int64_t k = 0; k < count; ++k) equisolid_inverse_normal(A + 2 * k, N + 3 * k, I + 3 * k);
+}
+void oracle_reflection(int64_t count, const double* A, double* R) {
+    for (int64_t k = 0; k < count; ++k) reflection(A + 2 * k, R + 3 * k);
+}
+/* Directions of all n x n texel centres of a bucket, row t major: dirs[(t n + s) 3 + c]. */
+void oracle_texel_directions(int32_t n, double* dirs) {
+    for (int64_t t = 0; t < n; ++t)
+        for (int64_t s = 0; s < n; ++s) texel_direction(s, t, n, dirs + 3 * (t * n + s));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Storage formats (reading R7), written from the format definitions.       */
+/* ------------------------------------------------------------------------ */
+
+/* A binary floating-point format with `mbits` stored mantissa bits, minimum
+ * normal exponent `emin`, exponent bias `bias`, and largest finite value
+ * `maxf`.  Rounds |x| to nearest, ties to even; overflow gives +-infinity
+ * (FP16, BF16) or saturates to maxf (E4M3 "satfinite"). */
+typedef struct {
+    int mbits, emin, bias, ebits;
+    double maxf;
+    int saturate;
+} fmt_t;
+
+static const fmt_t FMT_F16 = {10, -14, 15, 5, 65504.0, 0};
+static const fmt_t FMT_BF16 = {7, -126, 127, 8, 3.38953138925153547590470800371487867e38, 0};
+static const fmt_t FMT_E4M3 = {3, -6, 7, 4, 448.0, 1};
+
+/* Round a finite non-negative double to the format's value set. */
+static double round_to_format(double a, const fmt_t* f) {
+    if (a == 0.0) return 0.0;
+    int e;
+    (void)frexp(a, &e); /* a = m 2^e, m in [0.5, 1): floor(log2 a) = e - 1 */
+    int ex = e - 1;
+    if (ex < f->emin) ex = f->emin; /* subnormal quantum */
+    double quantum = ldexp(1.0, ex - f->mbits);
+    double q = rint(a / quantum) * quantum; /* exact scaling; rint = ties to even */
+    if (q > f->maxf) {
+        if (f->saturate) return f->maxf;
+        /* IEEE overflow threshold: values that round above maxf become inf. */
+        return INFINITY;
+    }
+    return q;
+}
+
+/* Pack a value of the format's value set (or +-inf / NaN) into its code. */
+static uint32_t pack_format(double v, int negative, const fmt_t* f) {
+    uint32_t sign = negative ? (1u << (f->ebits + f->mbits)) : 0u;
+    uint32_t emask = (1u << f->ebits) - 1u;
+    if (isnan(v)) return sign | (emask << f->mbits) | ((1u << f->mbits) - 1u);
+    if (isinf(v)) return sign | (emask << f->mbits);
+    if (v == 0.0) return sign;
+    int e;
+    (void)frexp(v, &e);
+    int ex = e - 1;
+    if (ex < f->emin) { /* subnormal: exponent field 0, mantissa v / 2^(emin - mbits) */
+        uint32_t mant = (uint32_t)ldexp(v, f->mbits - f->emin);
+        return sign | mant;
+    }
+    uint32_t mant = (uint32_t)ldexp(ldexp(v, -ex) - 1.0, f->mbits);
+    uint32_t field = (uint32_t)(ex + f->bias);
+    return sign | (field << f->mbits) | mant;
+}
+
+static double unpack_format(uint32_t code, const fmt_t* f, int has_inf) {
+    uint32_t mmask = (1u << f->mbits) - 1u;
+    uint32_t emask = (1u << f->ebits) - 1u;
+    int negative = (code >> (f->ebits + f->mbits)) & 1u;
+    uint32_t field = (code >> f->mbits) & emask;
+    uint32_t mant = code & mmask;
+    double v;
+    if (field == emask && has_inf) {
+        v = mant ? NAN : INFINITY;
+    } else if (field == emask && !has_inf && mant == mmask) {
+        v = NAN; /* E4M3: S.1111.111 is the only NaN */
+    } else if (field == 0) {
+        v = ldexp((double)mant, f->emin - f->mbits);
+    } else {
+        v = ldexp(1.0 + ldexp((double)mant, -f->mbits), (int)field - f->bias);
+    }
+    return negative ? -v : v;
+}
+
+static uint32_t encode_float(float x, const fmt_t* f) {
+    double a = fabs((double)x);
+    int neg = signbit(x) ? 1 : 0;
+    if (isnan(x)) return pack_format(NAN, neg, f);
+    if (isinf(x)) return f->saturate ? pack_format(f->maxf, neg, f) : pack_format(INFINITY, neg, f);
+    return pack_format(round_to_format(a, f), neg, f);
+}
+
+static double decode_f16(uint16_t c) { return unpack_format(c, &FMT_F16, 1); }
+static double decode_bf16(uint16_t c) { return unpack_format(c, &FMT_BF16, 1); }
+static double decode_e4m3(uint8_t c) { return unpack_format(c, &FMT_E4M3, 0); }
+
+/* Encode `count` FP32 values to F32 (copy), F16 or BF16 codes. */
+void oracle_encode(int32_t fmt, int64_t count, const float* x, void* codes) {
+    for (int64_t k = 0; k < count; ++k) {
+        if (fmt == OR_F32)
+            ((float*)codes)[k] = x[k];
+        else if (fmt == OR_F16)
+            ((uint16_t*)codes)[k] = (uint16_t)encode_float(x[k], &FMT_F16);
+        else if (fmt == OR_BF16)
+            ((uint16_t*)codes)[k] = (uint16_t)encode_float(x[k], &FMT_BF16);
+        else if (fmt == OR_E4M3)
+            ((uint8_t*)codes)[k] = (uint8_t)encode_float(x[k], &FMT_E4M3);
+    }
+}
+
+/* Decode `count` codes of a format to FP64, exactly. */
+void oracle_decode(int32_t fmt, int64_t count, const void* codes, double* out) {
+    for (int64_t k = 0; k < count; ++k) {
+        if (fmt == OR_F32)
+            out[k] = (double)((const float*)codes)[k];
+        else if (fmt == OR_F16)
+            out[k] = decode_f16(((const uint16_t*)codes)[k]);
+        else if (fmt == OR_BF16)
+            out[k] = decode_bf16(((const uint16_t*)codes)[k]);
+        else if (fmt == OR_E4M3)
+            out[k] = decode_e4m3(((const uint8_t*)codes)[k]);
+        else
+            out[k] = ((const double*)codes)[k];
+    }
+}
+
+/* E4M3 with one FP32 scale per bucket (reading R7).  `atlas` is the FP32
+ * atlas of reading R4; codes have the same layout, scales are row-major w x h. */
+void oracle_encode_e4m3_buckets(int32_t W, int32_t H, int32_t n, const float* atlas, uint8_t* codes,
+                                float* scales) {
+    int64_t row = (int64_t)W * n * 4;
+#pragma omp parallel for schedule(static)
+    for (int64_t b = 0; b < (int64_t)W * H; ++b) {
+        int64_t i = b % W, j = b / W;
+        float amax = 0.0f;
+        for (int64_t t = 0; t < n; ++t)
+            for (int64_t s = 0; s < n; ++s)
+                for (int c = 0; c < 4; ++c) {
+                    float v = fabsf(atlas[(j * n + t) * row + (i * n + s) * 4 + c]);
+                    if (v > amax) amax = v;
+                }
+        float sc = (amax == 0.0f) ? 1.0f : amax / 448.0f;
+        scales[b] = sc;
+        for (int64_t t = 0; t < n; ++t)
+            for (int64_t s = 0; s < n; ++s)
+                for (int c = 0; c < 4; ++c) {
+                    int64_t e = (j * n + t) * row + (i * n + s) * 4 + c;
+                    float q = atlas[e] / sc; /* the decision is taken in FP32 */
+                    codes[e] = (uint8_t)encode_float(q, &FMT_E4M3);
+                }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Texture access (readings R4 and R7).                                     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t W, H, n;
+    int32_t fmt;
+    const void* codes;
+    const float* scale;
+} tex_t;
+
+static int64_t atlas_offset(const tex_t* T, int64_t i, int64_t j, int64_t s, int64_t t, int c) {
+    int64_t X = i * T->n + s, Y = j * T->n + t;
+    return (Y * T->W * T->n + X) * 4 + c;
+}
+
+/* The stored texel (i, j, s, t), channel c, decoded exactly to FP64. */
+static double texel(const tex_t* T, int64_t i, int64_t j, int64_t s, int64_t t, int c) {
+    int64_t e = atlas_offset(T, i, j, s, t, c);
+    switch (T->fmt) {
+        case OR_F32:
+            return (double)((const float*)T->codes)[e];
+        case OR_F16:
+            return decode_f16(((const uint16_t*)T->codes)[e]);
+        case OR_BF16:
+            return decode_bf16(((const uint16_t*)T->codes)[e]);
+        case OR_E4M3:
+            return decode_e4m3(((const uint8_t*)T->codes)[e]) * (double)T->scale[j * T->W + i];
+        default:
+            return ((const double*)T->codes)[e];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-fragment lookup: Eq. 1b, Eq. 3, the Note's clamp, the filter.        */
+/* ------------------------------------------------------------------------ */
+
+/* One filter axis: two taps (equal for a nearest axis), their weights, the
+ * continuous coordinate c, its floor, and dc/d(input) for the gradient. */
+typedef struct {
+    int64_t tap[2];
+    double w[2];
+    double c;
+    int64_t fl;
+    double dc; /* derivative of c with respect to the axis input (u, v, B_x or B_y) */
+} axis_t;
+
+static int64_t clampi(int64_t x, int64_t lo, int64_t hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+/* Spatial axis (reading R5); size = w or h, x = u or v. */
+static void spatial_axis(double x, int64_t size, int bilinear, axis_t* a) {
+    if (bilinear) {
+        double c = x * (double)size - 0.5;
+        a->dc = (c > -1.0 && c < (double)size) ? (double)size : 0.0;
+        if (c < -1.0) c = -1.0;
+        if (c > (double)size) c = (double)size;
+        double f = floor(c);
+        a->c = c;
+        a->fl = (int64_t)f;
+        a->tap[0] = clampi(a->fl, 0, size - 1);
+        a->tap[1] = clampi(a->fl + 1, 0, size - 1);
+        a->w[1] = c - f;
+        a->w[0] = 1.0 - a->w[1];
+    } else {
+        double c = x * (double)size;
+        if (c < 0.0) c = 0.0;
+        if (c > (double)size) c = (double)size;
+        a->c = c;
+        a->fl = (int64_t)floor(c);
+        a->tap[0] = a->tap[1] = clampi(a->fl, 0, size - 1);
+        a->w[0] = 1.0;
+        a->w[1] = 0.0;
+        a->dc = 0.0;
+    }
+}
+
+/* In-bucket axis (Note after Eq. 3, readings R3 and R5); B is one component of Eq. 3's output. */
+static void angular_axis(double B, int64_t n, int bilinear, axis_t* a) {
+    double lo = 1.0 / (double)n - 1.0, hi = 1.0 - 1.0 / (double)n;
+    double inside = (B > lo && B < hi) ? 1.0 : 0.0;
+    double Bc = B < lo ? lo : (B > hi ? hi : B);
+    if (bilinear) {
+        double c = (Bc + 1.0) * (double)n / 2.0 - 0.5;
+        double f = floor(c);
+        a->c = c;
+        a->fl = (int64_t)f;
+        a->tap[0] = clampi(a->fl, 0, n - 1);
+        a->tap[1] = clampi(a->fl + 1, 0, n - 1);
+        a->w[1] = c - f;
+        a->w[0] = 1.0 - a->w[1];
+        a->dc = inside * (double)n / 2.0;
+    } else {
+        double c = (Bc + 1.0) * (double)n / 2.0;
+        a->c = c;
+        a->fl = (int64_t)floor(c);
+        a->tap[0] = a->tap[1] = clampi(a->fl, 0, n - 1);
+        a->w[0] = 1.0;
+        a->w[1] = 0.0;
+        a->dc = 0.0;
+    }
+}
+
+typedef struct {
+    axis_t u, v, s, t;
+    double A[2], B[2];
+} lookup_t;
+
+static void locate_one(const tex_t* T, double u, double v, const double I[3], int filter, lookup_t* L) {
+    int spatial_bilinear = (filter == OR_QUADRILINEAR);
+    int angular_bilinear = (filter != OR_NEAREST);
+    spatial_axis(u, T->W, spatial_bilinear, &L->u);
+    spatial_axis(v, T->H, spatial_bilinear, &L->v);
+    equisolid_ts(I, L->A);  /* Eq. 1b */
+    squarify(L->A, L->B);   /* Eq. 3 */
+    angular_axis(L->B[0], T->n, angular_bilinear, &L->s);
+    angular_axis(L->B[1], T->n, angular_bilinear, &L->t);
+}
+
+/* Colour of one fragment: the plain sum over the 16 (u, v, s, t) taps. */
+static void colour_one(const tex_t* T, const lookup_t* L, double out[4]) {
+    for (int c = 0; c < 4; ++c) {
+        double acc = 0.0;
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int p = 0; p < 2; ++p)
+                    for (int q = 0; q < 2; ++q) {
+                        double w = L->u.w[a] * L->v.w[b] * L->s.w[p] * L->t.w[q];
+                        if (w == 0.0) continue; /* zero-weight tap: no texel read */
+                        acc += w * texel(T, L->u.tap[a], L->v.tap[b], L->s.tap[p], L->t.tap[q], c);
+                    }
+        out[c] = acc;
+    }
+}
+
+static void make_tex(const int32_t* dims, const void* const* codes, const float* const* scales, int32_t o,
+                     tex_t* T) {
+    T->W = dims[4 * o + 0];
+    T->H = dims[4 * o + 1];
+    T->n = dims[4 * o + 2];
+    T->fmt = dims[4 * o + 3];
+    T->codes = codes[o];
+    T->scale = scales ? scales[o] : NULL;
+}
+
+/* Validity of a fragment: 0 = background, 1 = shade, otherwise an error flag. */
+static uint32_t classify(int32_t o, int32_t n_obj, const void* const* codes, double u, double v,
+                         const double I[3], int* shade) {
+    *shade = 0;
+    if (o < 0) return 0;
+    if (o >= n_obj || codes[o] == NULL) return OR_FLAG_BAD_OBJ;
+    if (!isfinite(u) || !isfinite(v) || !isfinite(I[0]) || !isfinite(I[1]) || !isfinite(I[2]))
+        return OR_FLAG_NONFINITE;
+    *shade = 1;
+    return 0;
+}
+
+/* Continuous coordinates and floors of every fragment (for index parity).
+ * coord[4f..4f+3] = (c_u, c_v, c_s, c_t), idx likewise (floors); background
+ * and invalid fragments get zeros. */
+uint32_t oracle_locate(const int32_t* dims, const void* const* codes, int32_t n_obj, int64_t F, const float* uv,
+                       const float* dir, const int32_t* obj, int32_t filter, int32_t* idx, double* coord) {
+    uint32_t flags = 0;
+#pragma omp parallel for schedule(static) reduction(| : flags)
+    for (int64_t f = 0; f < F; ++f) {
+        double u = uv[2 * f], v = uv[2 * f + 1];
+        double I[3] = {dir[3 * f], dir[3 * f + 1], dir[3 * f + 2]};
+        int shade;
+        flags |= classify(obj[f], n_obj, codes, u, v, I, &shade);
+        for (int k = 0; k < 4; ++k) {
+            idx[4 * f + k] = 0;
+            coord[4 * f + k] = 0.0;
+        }
+        if (!shade) continue;
+        tex_t T;
+        make_tex(dims, codes, NULL, obj[f], &T);
+        lookup_t L;
+        locate_one(&T, u, v, I, filter, &L);
+        const axis_t* ax[4] = {&L.u, &L.v, &L.s, &L.t};
+        for (int k = 0; k < 4; ++k) {
+            idx[4 * f + k] = (int32_t)ax[k]->fl;
+            coord[4 * f + k] = ax[k]->c;
+        }
+    }
+    return flags;
+}
+
+static uint32_t shade_core(const int32_t* dims, const void* const* codes, const float* const* scales,
+                           int32_t n_obj, int64_t F, const float* uv32, const float* dir32, const double* uv64,
+                           const double* dir64, const int32_t* obj, int32_t filter, double* out) {
+    uint32_t flags = 0;
+#pragma omp parallel for schedule(static) reduction(| : flags)
+    for (int64_t f = 0; f < F; ++f) {
+        double u, v, I[3];
+        if (uv64) {
+            u = uv64[2 * f];
+            v = uv64[2 * f + 1];
+            for (int k = 0; k < 3; ++k) I[k] = dir64[3 * f + k];
+        } else {
+            u = uv32[2 * f];
+            v = uv32[2 * f + 1];
+            for (int k = 0; k < 3; ++k) I[k] = dir32[3 * f + k];
+        }
+        int shade;
+        flags |= classify(obj[f], n_obj, codes, u, v, I, &shade);
+        for (int c = 0; c < 4; ++c) out[4 * f + c] = 0.0;
+        if (!shade) continue;
+        tex_t T;
+        make_tex(dims, codes, scales, obj[f], &T);
+        lookup_t L;
+        locate_one(&T, u, v, I, filter, &L);
+        colour_one(&T, &L, out + 4 * f);
+    }
+    return flags;
+}
+
+/* Forward synthesis of F fragments with an FP32 G-buffer (uv: F x 2, dir: F x 3,
+ * obj: F; obj < 0 is background and gives 0).  dims: n_obj x (w, h, n, format);
+ * codes[o]: the stored atlas of object o (NULL: no such object); scales[o]: its
+ * per-bucket E4M3 scales.  out: F x 4 FP64.  Returns OR_FLAG_* bits. */
+uint32_t oracle_shade(const int32_t* dims, const void* const* codes, const float* const* scales, int32_t n_obj,
+                      int64_t F, const float* uv, const float* dir, const int32_t* obj, int32_t filter,
+                      double* out) {
+    return shade_core(dims, codes, scales, n_obj, F, uv, dir, NULL, NULL, obj, filter, out);
+}
+
+/* The same with an FP64 G-buffer (finite-difference pins). */
+uint32_t oracle_shade64(const int32_t* dims, const void* const* codes, const float* const* scales, int32_t n_obj,
+                        int64_t F, const double* uv, const double* dir, const int32_t* obj, int32_t filter,
+                        double* out) {
+    return shade_core(dims, codes, scales, n_obj, F, NULL, NULL, uv, dir, obj, filter, out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradients (reading R6).                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Jacobian of Eq. 3, J[r][c] = dB_r / dA_c. */
+static void squarify_jacobian(const double A[2], double J[2][2]) {
+    double ax = fabs(A[0]), ay = fabs(A[1]);
+    if (ax == 0.0 && ay == 0.0) {
+        J[0][0] = 1.0;
+        J[0][1] = 0.0;
+        J[1][0] = 0.0;
+        J[1][1] = 1.0;
+        return;
+    }
+    double r = sqrt(A[0] * A[0] + A[1] * A[1]);
+    if (ax >= ay) { /* B = A r / |A_x| */
+        double sx = A[0] > 0.0 ? 1.0 : -1.0;
+        J[0][0] = ax / r;
+        J[0][1] = sx * A[1] / r;
+        J[1][0] = sx * A[1] * (1.0 / r - r / (A[0] * A[0]));
+        J[1][1] = (r * r + A[1] * A[1]) / (r * ax);
+    } else { /* B = A r / |A_y| */
+        double sy = A[1] > 0.0 ? 1.0 : -1.0;
+        J[1][1] = ay / r;
+        J[1][0] = sy * A[0] / r;
+        J[0][1] = sy * A[0] * (1.0 / r - r / (A[1] * A[1]));
+        J[0][0] = (r * r + A[0] * A[0]) / (r * ay);
+    }
+}
+
+/* Jacobian of Eq. 1b, J[r][c] = dA_r / dI_c. */
+static void equisolid_jacobian(const double I[3], double J[2][3]) {
+    double zp = I[2] + 1.0;
+    double D = sqrt(I[0] * I[0] + I[1] * I[1] + zp * zp);
+    if (D == 0.0) {
+        memset(J, 0, sizeof(double) * 6);
+        return;
+    }
+    double D3 = D * D * D;
+    double g[3] = {I[0], I[1], zp}; /* dD/dI = g / D */
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 3; ++c) J[r][c] = SQRT2 * ((r == c ? 1.0 / D : 0.0) - I[r] * g[c] / D3);
+}
+
+static uint32_t backward_core(const int32_t* dims, const void* const* codes, const float* const* scales,
+                              int32_t n_obj, int64_t F, const float* uv32, const float* dir32, const double* uv64,
+                              const double* dir64, const int32_t* obj, int32_t filter, const double* dL_dout,
+                              double* const* dL_dtex, double* dL_duv, double* dL_ddir) {
+    uint32_t flags = 0;
+    /* Texel gradients are summed serially, in fragment order. */
+    for (int64_t f = 0; f < F; ++f) {
+        double u, v, I[3];
+        if (uv64) {
+            u = uv64[2 * f];
+            v = uv64[2 * f + 1];
+            for (int k = 0; k < 3; ++k) I[k] = dir64[3 * f + k];
+        } else {
+            u = uv32[2 * f];
+            v = uv32[2 * f + 1];
+            for (int k = 0; k < 3; ++k) I[k] = dir32[3 * f + k];
+        }
+        if (dL_duv) dL_duv[2 * f] = dL_duv[2 * f + 1] = 0.0;
+        if (dL_ddir) dL_ddir[3 * f] = dL_ddir[3 * f + 1] = dL_ddir[3 * f + 2] = 0.0;
+        int shade;
+        flags |= classify(obj[f], n_obj, codes, u, v, I, &shade);
+        if (!shade) continue;
+        tex_t T;
+        make_tex(dims, codes, scales, obj[f], &T);
+        lookup_t L;
+        locate_one(&T, u, v, I, filter, &L);
+        const double* g = dL_dout + 4 * f;
+        const double dw[2] = {-1.0, 1.0}; /* d(weight of tap k)/dc for a bilinear axis */
+        double gu = 0.0, gv = 0.0, gs = 0.0, gt = 0.0;
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int p = 0; p < 2; ++p)
+                    for (int q = 0; q < 2; ++q) {
+                        int64_t i = L.u.tap[a], j = L.v.tap[b], s = L.s.tap[p], t = L.t.tap[q];
+                        double w = L.u.w[a] * L.v.w[b] * L.s.w[p] * L.t.w[q];
+                        double gT = 0.0; /* sum over channels of g_c T_c */
+                        for (int c = 0; c < 4; ++c) gT += g[c] * texel(&T, i, j, s, t, c);
+                        gu += dw[a] * L.v.w[b] * L.s.w[p] * L.t.w[q] * gT;
+                        gv += L.u.w[a] * dw[b] * L.s.w[p] * L.t.w[q] * gT;
+                        gs += L.u.w[a] * L.v.w[b] * dw[p] * L.t.w[q] * gT;
+                        gt += L.u.w[a] * L.v.w[b] * L.s.w[p] * dw[q] * gT;
+                        if (dL_dtex && dL_dtex[obj[f]] && w != 0.0)
+                            for (int c = 0; c < 4; ++c) dL_dtex[obj[f]][atlas_offset(&T, i, j, s, t, c)] += w * g[c];
+                    }
+        if (dL_duv) {
+            dL_duv[2 * f] = gu * L.u.dc;
+            dL_duv[2 * f + 1] = gv * L.v.dc;
+        }
+        if (dL_ddir) {
+            double gB[2] = {gs * L.s.dc, gt * L.t.dc};
+            double J3[2][2], J1[2][3];
+            squarify_jacobian(L.A, J3);
+            equisolid_jacobian(I, J1);
+            double gA[2] = {gB[0] * J3[0][0] + gB[1] * J3[1][0], gB[0] * J3[0][1] + gB[1] * J3[1][1]};
+            for (int c = 0; c < 3; ++c) dL_ddir[3 * f + c] = gA[0] * J1[0][c] + gA[1] * J1[1][c];
+        }
+    }
+    return flags;
+}
+
+/* Gradients of L with respect to the texels (accumulated into the FP64 atlas
+ * dL_dtex[o], which the caller zeroes; NULL to skip), the UVs (F x 2) and the
+ * directions (F x 3), given dL/dout (F x 4).  NULL outputs are skipped. */
+uint32_t oracle_shade_backward(const int32_t* dims, const void* const* codes, const float* const* scales,
+                               int32_t n_obj, int64_t F, const float* uv, const float* dir, const int32_t* obj,
+                               int32_t filter, const double* dL_dout, double* const* dL_dtex, double* dL_duv,
+                               double* dL_ddir) {
+    return backward_core(dims, codes, scales, n_obj, F, uv, dir, NULL, NULL, obj, filter, dL_dout, dL_dtex, dL_duv,
+                         dL_ddir);
+}
+
+uint32_t oracle_shade_backward64(const int32_t* dims, const void* const* codes, const float* const* scales,
+                                 int32_t n_obj, int64_t F, const double* uv, const double* dir, const int32_t* obj,
+                                 int32_t filter, const double* dL_dout, double* const* dL_dtex, double* dL_duv,
+                                 double* dL_ddir) {
+    return backward_core(dims, codes, scales, n_obj, F, NULL, NULL, uv, dir, obj, filter, dL_dout, dL_dtex, dL_duv,
+                         dL_ddir);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Texture fills (the paper gives no field; these are the synthetic ones).  */
+/* Fill rule: T[i, j, s, t] = f((i + 1/2)/w, (j + 1/2)/h, Eq. 2c(Eq. 4a(B_s, B_t))). */
+/* ------------------------------------------------------------------------ */
+
+/* Analytic field with L lobes; lobe k has 11 parameters
+ * (a_0..a_3, alpha, beta, gamma, d_x, d_y, d_z, p):
+ * f_c(u, v, I) = sum_k a_kc (1/2 + 1/2 cos(2 pi (alpha u + beta v) + gamma)) max(0, I . d)^p. */
+static void field_eval(const double* lobes, int32_t L, double u, double v, const double I[3], double out[4]) {
+    static const double TWO_PI = 6.28318530717958647692528676655900577;
+    for (int c = 0; c < 4; ++c) out[c] = 0.0;
+    for (int k = 0; k < L; ++k) {
+        const double* P = lobes + 11 * k;
+        double spatial = 0.5 + 0.5 * cos(TWO_PI * (P[4] * u + P[5] * v) + P[6]);
+        double cosang = I[0] * P[7] + I[1] * P[8] + I[2] * P[9];
+        double lobe = cosang > 0.0 ? pow(cosang, P[10]) : 0.0;
+        for (int c = 0; c < 4; ++c) out[c] += P[c] * spatial * lobe;
+    }
+}
+
+/* Field values at arbitrary (uv, I) in FP64 (fitting targets): out count x 4. */
+void oracle_eval_field(const double* lobes, int32_t L, int64_t count, const double* uv, const double* dir,
+                       double* out) {
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < count; ++k) field_eval(lobes, L, uv[2 * k], uv[2 * k + 1], dir + 3 * k, out + 4 * k);
+}
+
+/* FP32 atlas (reading R4) filled from the analytic field by the fill rule. */
+void oracle_fill_field(int32_t W, int32_t H, int32_t n, const double* lobes, int32_t L, float* atlas) {
+#pragma omp parallel for schedule(static)
+    for (int64_t b = 0; b < (int64_t)W * H; ++b) {
+        int64_t i = b % W, j = b / W;
+        double u = ((double)i + 0.5) / W, v = ((double)j + 0.5) / H;
+        for (int64_t t = 0; t < n; ++t)
+            for (int64_t s = 0; s < n; ++s) {
+                double I[3], val[4];
+                texel_direction(s, t, n, I);
+                field_eval(lobes, L, u, v, I, val);
+                int64_t e = ((j * n + t) * (int64_t)W * n + (i * n + s)) * 4;
+                for (int c = 0; c < 4; ++c) atlas[e + c] = (float)val[c];
+            }
+    }
+}
+
+/* FP32 atlas filled from one cosine-power lobe per bucket.  params: w h x 8
+ * floats per bucket (rho_r, rho_g, rho_b, d_x, d_y, d_z, p, unused):
+ * T_c = rho_c max(0, I . d)^p for c < 3 and T_3 = max(0, I . d)^p. */
+void oracle_fill_bucket_lobes(int32_t W, int32_t H, int32_t n, const float* params, float* atlas) {
+#pragma omp parallel for schedule(static)
+    for (int64_t b = 0; b < (int64_t)W * H; ++b) {
+        int64_t i = b % W, j = b / W;
+        const float* P = params + 8 * b;
+        for (int64_t t = 0; t < n; ++t)
+            for (int64_t s = 0; s < n; ++s) {
+                double I[3];
+                texel_direction(s, t, n, I);
+                double cosang = I[0] * (double)P[3] + I[1] * (double)P[4] + I[2] * (double)P[5];
+                double lobe = cosang > 0.0 ? pow(cosang, (double)P[6]) : 0.0;
+                int64_t e = ((j * n + t) * (int64_t)W * n + (i * n + s)) * 4;
+                atlas[e + 0] = (float)((double)P[0] * lobe);
+                atlas[e + 1] = (float)((double)P[1] * lobe);
+                atlas[e + 2] = (float)((double)P[2] * lobe);
+                atlas[e + 3] = (float)lobe;
+            }
+    }
+}
+
+int32_t oracle_num_threads(void) {
+#ifdef _OPENMP
+    return (int32_t)omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void oracle_set_num_threads(int32_t k) {
+#ifdef _OPENMP
+    omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+}

@@ -1,0 +1,12 @@
+"""Seeded synthetic inputs for radiance-texture shading.
+
+This package is shared by the tests, the oracle checks and the benchmark.  It
+holds only scene generation (analytic ray casting of a G-buffer: UV,
+tangent-space view direction, object id) and seeded draws of field
+parameters.  It holds none of the method's arithmetic: no equisolid
+projection, no disc-to-square mapping, no filtering.  All draws use numpy's
+PCG64 generator with the seed given by the caller, and geometry is computed in
+FP64 then rounded to FP32, the G-buffer precision.
+"""
+from .scenes import GBuffer, quad_scene, sphere_plane_scene, sphere_plane_poses, voronoi_planes_scene  # noqa: F401
+from .fields import field_lobes, bucket_lobe_params  # noqa: F401
