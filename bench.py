@@ -1,0 +1,490 @@
+#!/usr/bin/env python
+"""Throughput of per-fragment radiance-texture synthesis on GB300.
+
+Workload (default): a unit sphere and a ground plane rendered from 60 orbit
+poses at 1920x1080 (124,416,000 fragments per step); each object carries a
+radiance texture of 1024 x 1024 buckets x 16 x 16 directions stored as FP16
+(2 GiB), filled from one seeded cosine-power lobe per bucket; quadrilinear
+filtering.  One step = the forward synthesis of every fragment plus the
+backward pass (texel, UV and direction gradients of L = 1/2 sum out^2, texel
+gradients zeroed first), all through the C ABI of libradtex.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "radiance lookups/s (Gfrag/s), forward + backward step"
+FALLBACK_HBM_GBS = 6800.0
+SCENE_SEED = 1002
+TEX_SEEDS = (2001, 2002)
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["radtex", "reference"], default="radtex")
+    p.add_argument("--views", type=int, default=60)
+    p.add_argument("--width", type=int, default=1920)
+    p.add_argument("--height", type=int, default=1080)
+    p.add_argument("--buckets", type=int, default=1024)
+    p.add_argument("--n", type=int, default=16)
+    p.add_argument("--storage", choices=["f32", "f16", "bf16", "e4m3"], default="f16")
+    p.add_argument("--filter", choices=["nearest", "angular_bilinear", "quadrilinear"], default="quadrilinear")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args(argv)
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_name(a) -> str:
+    return (f"sphere+plane {a.width}x{a.height} x {a.views} poses, 2 objects x {a.buckets}^2 buckets x {a.n}^2 "
+            f"directions {a.storage.upper()}, {a.filter}")
+
+
+def bytes_per_texel(storage: str) -> int:
+    return {"f32": 16, "f16": 8, "bf16": 8, "e4m3": 4}[storage]
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2301_01719_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    with open(path) as fh:
+        for line in fh:
+            parts = [x.strip() for x in line.strip().strip("|").split("|")]
+            if len(parts) >= 4 and parts[0] == kernel and parts[1] == workload and parts[3] == src:
+                try:
+                    return float(parts[2])
+                except ValueError:
+                    return None
+    return None
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region.
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.5)  # let the sampler start before the timed region
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        import datetime
+
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    ts = None
+                # keep the samples taken inside the timed region (with a 0.2 s margin)
+                if ts is not None and self.t0 is not None and not (self.t0 - 0.2 <= ts <= self.t1 + 0.2):
+                    continue
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline.
+# ---------------------------------------------------------------------------
+
+def oracle_textures(a):
+    import oracle
+    import synth
+
+    fmt = {"f32": oracle.F32, "f16": oracle.F16, "bf16": oracle.BF16, "e4m3": oracle.E4M3}[a.storage]
+    texs = []
+    for seed in TEX_SEEDS:
+        params = synth.bucket_lobe_params(seed, a.buckets, a.buckets)
+        atlas = oracle.fill_bucket_lobes(a.buckets, a.buckets, a.n, params)
+        texs.append(oracle.Texture.from_f32(atlas, a.buckets, a.buckets, a.n, fmt))
+        del atlas
+    return texs
+
+
+def cpu_baseline(a, g, seconds: float):
+    """The oracle as it stands, on a bounded sample of the workload's fragments."""
+    import oracle
+
+    filt = {"nearest": oracle.NEAREST, "angular_bilinear": oracle.ANGULAR_BILINEAR,
+            "quadrilinear": oracle.QUADRILINEAR}[a.filter]
+    texs = oracle_textures(a)
+    F = g.obj.shape[0]
+    # probe the rate on 1/500 of the fragments, then size the sample for `seconds`
+    stride = max(1, F // 200000)
+    t0 = time.perf_counter()
+    oracle.shade(texs, g.uv[::stride], g.dir[::stride], g.obj[::stride], filt)
+    rate = g.obj[::stride].shape[0] / max(time.perf_counter() - t0, 1e-6)
+    count = int(min(F, max(100000, rate * seconds)))
+    stride = max(1, F // count)
+    uv, d, o = g.uv[::stride], g.dir[::stride], g.obj[::stride]
+    t0 = time.perf_counter()
+    oracle.shade(texs, uv, d, o, filt)
+    dt = time.perf_counter() - t0
+    fwd = o.shape[0] / dt
+    # backward on a tenth of that sample (the texel-gradient sum is serial)
+    sub = max(1, 10)
+    gout = np.ones((o[::sub].shape[0], 4))
+    t0 = time.perf_counter()
+    oracle.shade_backward(texs, uv[::sub], d[::sub], o[::sub], filt, gout)
+    bwd = o[::sub].shape[0] / max(time.perf_counter() - t0, 1e-9)
+    step = 1.0 / (1.0 / fwd + 1.0 / bwd)
+    return {"value": step / 1e9, "unit": "Gfrag/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"every {stride}th fragment of the {F}-fragment step ({o.shape[0]} forward, "
+                       f"{o[::sub].shape[0]} backward), same textures"),
+            "fwd_gfrag_s": fwd / 1e9, "bwd_gfrag_s": bwd / 1e9}
+
+
+def run_reference(a):
+    """--impl reference: the FP64 CPU oracle on host cores, rank 0 only."""
+    import synth
+
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    g = synth.sphere_plane_scene(SCENE_SEED, views=min(a.views, 2), width=a.width, height=a.height)
+    import oracle
+
+    filt = {"nearest": oracle.NEAREST, "angular_bilinear": oracle.ANGULAR_BILINEAR,
+            "quadrilinear": oracle.QUADRILINEAR}[a.filter]
+    texs = oracle_textures(a)
+    # each step is a bounded sample: every k-th fragment of two poses, sized to ~2 s of oracle work
+    stride = max(1, g.F // 200000)
+    t0 = time.perf_counter()
+    oracle.shade(texs, g.uv[::stride], g.dir[::stride], g.obj[::stride], filt)
+    rate = g.obj[::stride].shape[0] / max(time.perf_counter() - t0, 1e-6)
+    count = int(min(g.F, max(50000, rate * 2.0)))
+    stride = max(1, g.F // count)
+    uv, d, o = g.uv[::stride], g.dir[::stride], g.obj[::stride]
+    gout = np.ones((o.shape[0], 4))
+    sub = 10
+    times = []
+    for k in range(a.warmup + a.steps):
+        t0 = time.perf_counter()
+        oracle.shade(texs, uv, d, o, filt)
+        t1 = time.perf_counter()
+        oracle.shade_backward(texs, uv[::sub], d[::sub], o[::sub], filt, gout[::sub])
+        t2 = time.perf_counter()
+        # normalise: forward over the sample + backward scaled to the same fragment count
+        times.append((t1 - t0) + (t2 - t1) * sub)
+    tt = times[a.warmup:]
+    mean = float(np.mean(tt))
+    value = o.shape[0] / mean / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gfrag/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "sample_fragments": int(o.shape[0])},
+            "cpu_baseline": {"value": value, "unit": "Gfrag/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"every {stride}th fragment of 2 poses per step; backward on a tenth, "
+                                       "scaled"},
+            "e2e": {"value": value, "unit": "Gfrag/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm.
+# ---------------------------------------------------------------------------
+
+def run_radtex(a):
+    import torch
+
+    import synth
+    from paper_2301_01719_gb300 import api, build
+
+    rank, world, local = dist_info()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device; libradtex has no CPU path")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    fmt = api.FORMAT_NAMES[a.storage]
+    filt = api.FILTER_NAMES[a.filter]
+
+    # Scene: every rank renders its own 60-pose orbit (weak scaling), in pinned host memory.
+    per = a.width * a.height
+    F = a.views * per
+    h_uv = torch.empty((F, 2), dtype=torch.float32, pin_memory=True)
+    h_dir = torch.empty((F, 3), dtype=torch.float32, pin_memory=True)
+    h_obj = torch.empty((F,), dtype=torch.int32, pin_memory=True)
+    t0 = time.perf_counter()
+    g = synth.sphere_plane_scene(SCENE_SEED + rank, views=a.views, width=a.width, height=a.height,
+                                 out=(h_uv.numpy(), h_dir.numpy(), h_obj.numpy()))
+    scene_s = time.perf_counter() - t0
+    uv = h_uv.to(dev)
+    dirs = h_dir.to(dev)
+    obj = h_obj.to(dev)
+
+    ctx = api.Context(local)
+    oids = []
+    for seed in TEX_SEEDS:
+        oid = api.rt_create_texture(ctx, a.buckets, a.buckets, a.n, fmt)
+        params = torch.from_numpy(synth.bucket_lobe_params(seed, a.buckets, a.buckets)).to(dev)
+        api.rt_fill_bucket_lobes(ctx, oid, params)
+        oids.append(oid)
+    torch.cuda.synchronize()
+    out = torch.empty((F, 4), dtype=torch.float32, device=dev)
+    duv = torch.empty((F, 2), dtype=torch.float32, device=dev)
+    ddir = torch.empty((F, 3), dtype=torch.float32, device=dev)
+    dtex = {o: torch.empty((a.n, a.n, a.buckets, a.buckets, 4), dtype=torch.float32, device=dev) for o in oids}
+
+    # Algorithmic bytes: distinct texels per frame (counted outside the timed region).
+    distinct = 0
+    for v in range(a.views):
+        sl = slice(v * per, (v + 1) * per)
+        counts = api.rt_footprint(ctx, uv[sl], dirs[sl], obj[sl], filt, len(oids))
+        distinct += sum(counts)
+    tb = bytes_per_texel(a.storage)
+    scale_bytes = 0  # E4M3 scales: 4 B per distinct bucket, counted as at most one per texel quad below
+    if a.storage == "e4m3":
+        scale_bytes = distinct // (a.n * a.n) * 4
+    fwd_bytes = 40 * F + distinct * tb + scale_bytes
+    bwd_bytes = (24 + 16 + 8 + 12) * F + distinct * (tb + 32) + scale_bytes
+
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        api.rt_shade(ctx, uv, dirs, obj, filt, out)
+        for t in dtex.values():
+            t.zero_()
+        api.rt_shade_backward(ctx, uv, dirs, obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = api.rt_get_error(ctx)
+    if st != api.RT_OK:
+        raise RuntimeError(f"device status after warm-up: {api.rt_status_string(st)}")
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(a.steps)]
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        clk.mark_start()
+        start.record(stream)
+        for k in range(a.steps):
+            e = ev[k]
+            e[0].record(stream)
+            api.rt_shade(ctx, uv, dirs, obj, filt, out)
+            e[1].record(stream)
+            for t in dtex.values():
+                t.zero_()
+            e[2].record(stream)
+            api.rt_shade_backward(ctx, uv, dirs, obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE)
+            e[3].record(stream)
+        end.record(stream)
+        torch.cuda.synchronize()
+        clk.mark_end()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = start.elapsed_time(end)
+    fwd_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    zero_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    bwd_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in ev]))
+    if world > 1:
+        import torch.distributed as dist
+
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / a.steps
+    value = world * F / (ms_per_step * 1e-3) / 1e9
+    st = api.rt_get_error(ctx)
+    if st != api.RT_OK:
+        raise RuntimeError(f"device status after timing: {api.rt_status_string(st)}")
+
+    # End to end through the public API with host buffers: H2D of the G-buffer,
+    # the step, D2H of the image, every step.
+    e2e = None
+    if not a.no_e2e:
+        h_out = torch.empty((F, 4), dtype=torch.float32, pin_memory=True)
+        d_uv = torch.empty_like(uv)
+        d_dir = torch.empty_like(dirs)
+        d_obj = torch.empty_like(obj)
+
+        def e2e_step():
+            d_uv.copy_(h_uv, non_blocking=True)
+            d_dir.copy_(h_dir, non_blocking=True)
+            d_obj.copy_(h_obj, non_blocking=True)
+            api.rt_shade(ctx, d_uv, d_dir, d_obj, filt, out)
+            for t in dtex.values():
+                t.zero_()
+            api.rt_shade_backward(ctx, d_uv, d_dir, d_obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE)
+            h_out.copy_(out, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(a.e2e_steps):
+            e2e_step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = s0.elapsed_time(s1) / a.e2e_steps
+        if world > 1:
+            import torch.distributed as dist
+
+            tt = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_ms = float(tt.item())
+        e2e = {"value": world * F / (e_ms * 1e-3) / 1e9, "unit": "Gfrag/s", "ms_per_step": e_ms,
+               "h2d_bytes_per_step": int(h_uv.nbytes + h_dir.nbytes + h_obj.nbytes),
+               "d2h_bytes_per_step": int(h_out.nbytes)}
+        del h_out
+
+    peak, peak_kind = measured_peak()
+    fwd_gbs = fwd_bytes / (fwd_ms * 1e-3) / 1e9
+    bwd_gbs = bwd_bytes / (bwd_ms * 1e-3) / 1e9
+    wl = workload_name(a)
+
+    def roof(achieved, kernel, nbytes):
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(kernel, wl), "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": int(nbytes), "kernel": kernel}
+
+    r_fwd = roof(fwd_gbs, "shade_kernel<QUADRILINEAR>" if filt == api.RT_QUADRILINEAR else "shade_kernel", fwd_bytes)
+    r_bwd = roof(bwd_gbs, "backward_kernel<QUADRILINEAR>" if filt == api.RT_QUADRILINEAR else "backward_kernel",
+                 bwd_bytes)
+    dominant = r_bwd if bwd_ms >= fwd_ms else r_fwd
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "Gfrag/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl, "fragments_per_step": F * world, "views": a.views, "width": a.width,
+                   "height": a.height, "buckets": a.buckets, "n": a.n, "storage": a.storage, "filter": a.filter,
+                   "objects": len(oids), "texture_bytes": int(sum(api.rt_texture_info(ctx, o)["bytes"] for o in oids)),
+                   "l2": "inputs larger than L2 (G-buffer %.1f GB, textures %.1f GB per rank)" % (
+                       24 * F / 1e9, sum(api.rt_texture_info(ctx, o)["bytes"] for o in oids) / 1e9),
+                   "step": "rt_shade + zero texel grads + rt_shade_backward(RT_ACCUMULATE, dL/dout = out)",
+                   "distinct_texels_per_step": int(distinct), "scene_gen_s": round(scene_s, 2)},
+        "fwd_gfrag_s": F / (fwd_ms * 1e-3) / 1e9, "bwd_gfrag_s": F / (bwd_ms * 1e-3) / 1e9,
+        "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "zero_grad_ms": zero_ms,
+        "roofline": dominant, "roofline_fwd": r_fwd, "roofline_bwd": r_bwd,
+        "gpu_launches": 2 * a.steps,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(a, g, a.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main(argv=None):
+    a = parse_args(argv)
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_radtex(a)
+
+
+if __name__ == "__main__":
+    main()

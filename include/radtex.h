@@ -1,0 +1,191 @@
+/*
+ * radtex.h -- C ABI of libradtex, GPU radiance-texture synthesis for GB300 (sm_103a).
+ *
+ * The method (J. M. Fober, "Radiance Textures for Rasterizing Ray-Traced Data",
+ * arXiv 2301.01719, Section 2): every texel of an ordinary w x h texture is
+ * replaced by a "bucket", an n x n discrete hemispherical radiance map.  A
+ * fragment's surface UV selects the bucket, and its incidence vector, mapped by
+ * the equisolid projection (Eq. 1b) and the disc-to-square mapping (Eq. 3) and
+ * clamped to the texel-centre range (Note after Eq. 3), selects the texels
+ * inside the bucket.  The texels are filtered in FP32 into the output colour.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named "device" are CUDA device pointers of the context's device;
+ *   the caller owns them.  "host" pointers are ordinary host memory.
+ * - All compute calls are asynchronous on the given stream (a cudaStream_t; NULL
+ *   is the legacy default stream), neither allocate nor synchronise, and may be
+ *   captured in a CUDA graph, unless their comment says otherwise.  Texture
+ *   creation and destruction are synchronous set-up calls.
+ * - Errors are returned as rt_status; nothing is thrown across the ABI.
+ *   Problems found on the device (an object id with no texture, a non-finite
+ *   UV or direction) make that fragment's outputs zero and set a sticky status
+ *   word that rt_get_error reads and clears.
+ * - G-buffer: F fragments, structure of arrays: uv (F x 2 float: u, v),
+ *   dir (F x 3 float: the tangent-space unit vector from the surface to the
+ *   eye, x along dP/du, y along dP/dv, z along the normal), obj (F int32:
+ *   object id, < 0 = background, whose outputs are zero and which reads no
+ *   texel).  uv, dir, obj and every F x k output must start on a 16-byte
+ *   boundary (RT_ERR_INVALID_ARG otherwise).
+ * - Texel (i, j, s, t) of an object is bucket column i (0..w-1, from u), bucket
+ *   row j (0..h-1, from v), in-bucket column s (0..n-1, from B_x) and row t
+ *   (from B_y); each texel holds 4 channels (RGBA).  Layouts:
+ *     RT_LAYOUT_ATLAS : the paper's texture, row-major (h n) x (w n) texels,
+ *                       texel (i, j, s, t) at row j n + t, column i n + s.
+ *     RT_LAYOUT_PLANES: n x n planes of w x h texels, texel (i, j, s, t) at
+ *                       index ((t n + s) h + j) w + i.  Textures the library
+ *                       owns are stored this way: fragments that are close on
+ *                       screen read texels that are close in memory.
+ */
+#ifndef RADTEX_H
+#define RADTEX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* rt_stream_t; /* identical to cudaStream_t */
+typedef struct rt_ctx rt_ctx;
+
+typedef enum {
+    RT_OK = 0,
+    RT_ERR_INVALID_ARG = 1,  /* a null, misaligned or out-of-range argument */
+    RT_ERR_OOM = 2,          /* device allocation failed (set-up calls only) */
+    RT_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    RT_ERR_BAD_OBJ_ID = 4,   /* device: an object id names no texture */
+    RT_ERR_NONFINITE = 5,    /* device: a UV or direction was NaN or infinite */
+    RT_ERR_TIMEOUT = 6,      /* device: a bounded wait gave up */
+    RT_ERR_UNSUPPORTED = 7   /* the combination of options is not implemented */
+} rt_status;
+
+typedef enum {
+    RT_F32 = 0,              /* 16 bytes per texel */
+    RT_F16 = 1,              /* 8 bytes per texel, round to nearest even */
+    RT_BF16 = 2,             /* 8 bytes per texel, round to nearest even */
+    RT_E4M3_BUCKET_SCALE = 3 /* 4 bytes per texel: OCP FP8 E4M3 codes of v / s, s = (bucket amax) / 448 */
+} rt_format;
+
+typedef enum {
+    RT_NEAREST = 0,          /* nearest bucket, nearest texel: 1 tap */
+    RT_ANGULAR_BILINEAR = 1, /* nearest bucket, bilinear inside it ("single sample per bucket", Section 2): 4 taps */
+    RT_QUADRILINEAR = 2      /* bilinear over u, v and over s, t: 16 taps */
+} rt_filter;
+
+typedef enum { RT_LAYOUT_ATLAS = 0, RT_LAYOUT_PLANES = 1 } rt_layout;
+
+/* rt_create_texture flags */
+#define RT_BORROW 1          /* use the caller's FP32 buffer in place; no copy */
+/* rt_shade_backward flags */
+#define RT_ACCUMULATE 1      /* add into dL_dtex / dL_duv / dL_ddir instead of overwriting */
+
+#define RT_MAX_OBJECTS 1024
+
+/* Creates a context on CUDA device `cuda_device`: a texture table and a sticky
+ * device status word.  *out receives the context; RT_ERR_INVALID_ARG for a bad
+ * device index, RT_ERR_OOM / RT_ERR_CUDA on failure. */
+rt_status rt_context_create(int cuda_device, rt_ctx** out);
+
+/* Destroys the context and frees every texture it owns (synchronises the device). */
+void rt_context_destroy(rt_ctx* ctx);
+
+/* Creates a radiance texture of w x h buckets of n x n texels (Section 2: the
+ * bucket matrix, stored as w n x h n texels).  1 <= w, h <= 65536, 1 <= n <= 64.
+ * src (device, FP32, 4 channels per texel, layout src_layout) gives the texel
+ * values; NULL leaves an owned texture zero (fill it with rt_fill_bucket_lobes).
+ * Without RT_BORROW the library allocates storage in RT_LAYOUT_PLANES and
+ * encodes src into `storage` (E4M3: one FP32 scale per bucket, s = amax / 448,
+ * s = 1 for an all-zero bucket; codes = round-to-nearest-even-satfinite(v / s)).
+ * With RT_BORROW, `storage` must be RT_F32 and src non-NULL: the library reads
+ * src in place, in src_layout, for as long as the texture lives; the caller
+ * keeps it alive and may update its values between calls (texture fitting).
+ * *obj_id_out receives the object id used in the G-buffer's obj array.
+ * Synchronous.  RT_ERR_INVALID_ARG for bad sizes/pointers, RT_ERR_OOM when the
+ * storage or the RT_MAX_OBJECTS ids are exhausted. */
+rt_status rt_create_texture(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, rt_format storage, rt_layout src_layout,
+                            const float* src, int32_t flags, int32_t* obj_id_out);
+
+/* Releases an object id and the storage the library owns for it (synchronises
+ * the device).  Fragments that still name the id read no texel and set
+ * RT_ERR_BAD_OBJ_ID. */
+rt_status rt_destroy_texture(rt_ctx* ctx, int32_t obj_id);
+
+/* Properties of an object (any output pointer may be NULL).  bytes = texel
+ * storage plus scales. */
+rt_status rt_texture_info(rt_ctx* ctx, int32_t obj_id, int32_t* w, int32_t* h, int32_t* n, int32_t* storage,
+                          int32_t* layout, int64_t* bytes);
+
+/* Copies the stored codes of an object into codes_dst (device; w n h n x 4
+ * elements of the storage type: float, uint16 (FP16/BF16 bits) or uint8
+ * (E4M3 codes)) in dst_layout, and for E4M3 the per-bucket scales into
+ * scales_dst (device, h x w floats, may be NULL).  Used to check the encoders. */
+rt_status rt_read_texture(rt_ctx* ctx, int32_t obj_id, rt_layout dst_layout, void* codes_dst, float* scales_dst,
+                          rt_stream_t stream);
+
+/* Fills an owned texture from one cosine-power lobe per bucket, evaluated at
+ * every texel centre's direction: B_k = (2k + 1)/n - 1, A = Eq. 4a(B),
+ * I = Eq. 2c(A); T_c = rho_c max(0, I . d)^p (c < 3), T_3 = max(0, I . d)^p;
+ * then encodes as rt_create_texture does.  params (device): h x w x 8 floats
+ * per bucket (rho_r, rho_g, rho_b, d_x, d_y, d_z, p, unused), row-major.
+ * RT_ERR_UNSUPPORTED for a borrowed texture. */
+rt_status rt_fill_bucket_lobes(rt_ctx* ctx, int32_t obj_id, const float* params, rt_stream_t stream);
+
+/* Forward synthesis of F >= 0 fragments (Section 2, Eq. 1b, Eq. 3, the Note's
+ * clamp), filtered with `filter` in FP32: out (device, F x 4 float, RGBA).
+ * Spatial addressing clamps to the edge; nearest indices take floor (an exact
+ * boundary goes to the higher index). */
+rt_status rt_shade(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F, rt_filter filter,
+                   float* out, rt_stream_t stream);
+
+/* The lookup coordinates of every fragment, for index checks: coord (device,
+ * F x 4 float) = the continuous coordinates (c_u, c_v, c_s, c_t) whose floors
+ * select the taps, idx (device, F x 4 int32) = those floors.  Spatial:
+ * c = u w (nearest) or u w - 1/2 clamped to [-1, w] (bilinear).  In-bucket:
+ * c = (B + 1) n / 2 (nearest) or (B + 1) n / 2 - 1/2 (bilinear), B clamped to
+ * [1/n - 1, 1 - 1/n].  Background and invalid fragments give zeros. */
+rt_status rt_locate(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F, rt_filter filter,
+                    int32_t* idx, float* coord, rt_stream_t stream);
+
+/* Gradients of a loss L given dL_dout (device, F x 4):
+ *   dL_dtex: host array of n_dtex device pointers indexed by object id (the
+ *            array itself may be NULL, and so may any entry): FP32 gradient of
+ *            the object's decoded texel values, 4 channels per texel, in the
+ *            object's storage layout (RT_LAYOUT_PLANES for owned textures, the
+ *            borrowed buffer's layout otherwise).  Summed with vector atomics.
+ *   dL_duv:  device F x 2 or NULL; dL_ddir: device F x 3 or NULL, through
+ *            the filter weights, the Note's clamp, Eq. 3 and Eq. 1b.
+ * Without RT_ACCUMULATE the per-fragment outputs are overwritten and each
+ * dL_dtex buffer is zeroed first (a full write of the buffer); with it, all
+ * outputs are added to.  Subgradients: the floor branch at integer
+ * coordinates, zero where a coordinate is clamped, the |A_x| >= |A_y| branch
+ * of Eq. 3 on its diagonal, the identity at A = 0. */
+rt_status rt_shade_backward(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,
+                            rt_filter filter, const float* dL_dout, float* const* dL_dtex, int32_t n_dtex,
+                            float* dL_duv, float* dL_ddir, int32_t flags, rt_stream_t stream);
+
+/* Counts the distinct texels read by the F fragments (any tap of non-zero or
+ * zero weight of the filter's footprint), per object: counts_host (host,
+ * n_counts entries indexed by object id).  A measurement utility: it allocates
+ * a bitmap of one bit per texel of every object and synchronises the stream. */
+rt_status rt_footprint(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,
+                       rt_filter filter, uint64_t* counts_host, int32_t n_counts, rt_stream_t stream);
+
+/* Converts an FP32 4-channel texture buffer of w x h buckets of n x n texels
+ * between layouts (device src and dst, which must not overlap). */
+rt_status rt_convert_layout(const float* src, rt_layout src_layout, float* dst, rt_layout dst_layout, int32_t w,
+                            int32_t h, int32_t n, rt_stream_t stream);
+
+/* Synchronises `stream`, then reads and clears the context's sticky status
+ * word: *device_status = RT_OK, or the first of RT_ERR_BAD_OBJ_ID,
+ * RT_ERR_NONFINITE, RT_ERR_TIMEOUT raised since the last call. */
+rt_status rt_get_error(rt_ctx* ctx, rt_stream_t stream, rt_status* device_status);
+
+/* A static English description of a status code. */
+const char* rt_status_string(rt_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RADTEX_H */

@@ -1,0 +1,93 @@
+"""ctypes binding of libradtex (include/radtex.h): the C entry points, same names.
+
+Argument marshalling only.  The library must have been built (``build.build()``
+or ``__graft_entry__.build()``); if it is missing, loading raises instead of
+falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libradtex.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "radtex.h")
+
+# rt_status
+RT_OK, RT_ERR_INVALID_ARG, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_BAD_OBJ_ID, RT_ERR_NONFINITE, RT_ERR_TIMEOUT, \
+    RT_ERR_UNSUPPORTED = range(8)
+# rt_format
+RT_F32, RT_F16, RT_BF16, RT_E4M3_BUCKET_SCALE = range(4)
+# rt_filter
+RT_NEAREST, RT_ANGULAR_BILINEAR, RT_QUADRILINEAR = range(3)
+# rt_layout
+RT_LAYOUT_ATLAS, RT_LAYOUT_PLANES = range(2)
+RT_BORROW = 1
+RT_ACCUMULATE = 1
+RT_MAX_OBJECTS = 1024
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+
+SIGNATURES = {
+    "rt_context_create": (_I32, [ctypes.c_int, ctypes.POINTER(_P)]),
+    "rt_context_destroy": (None, [_P]),
+    "rt_create_texture": (_I32, [_P, _I32, _I32, _I32, _I32, _I32, _P, _I32, ctypes.POINTER(_I32)]),
+    "rt_destroy_texture": (_I32, [_P, _I32]),
+    "rt_texture_info": (_I32, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                               ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
+    "rt_read_texture": (_I32, [_P, _I32, _I32, _P, _P, _P]),
+    "rt_fill_bucket_lobes": (_I32, [_P, _I32, _P, _P]),
+    "rt_shade": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, _P]),
+    "rt_locate": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, _P, _P]),
+    "rt_shade_backward": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, ctypes.POINTER(_P), _I32, _P, _P, _I32, _P]),
+    "rt_footprint": (_I32, [_P, _P, _P, _P, _I64, _I32, ctypes.POINTER(ctypes.c_uint64), _I32, _P]),
+    "rt_convert_layout": (_I32, [_P, _I32, _P, _I32, _I32, _I32, _I32, _P]),
+    "rt_get_error": (_I32, [_P, _P, ctypes.POINTER(_I32)]),
+    "rt_status_string": (ctypes.c_char_p, [_I32]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class RadtexError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        msg = lib().rt_status_string(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{fn} failed: {msg} (status {status})")
+
+
+def header_symbols() -> list[str]:
+    """Every function the public header declares."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^\s*(?:rt_status|void|const char\*)\s+(rt_\w+)\s*\(", text, flags=re.M)))
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is not built; run paper_2301_01719_gb300.build.build() "
+                                   "(or __graft_entry__.build()) first")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib
+
+
+def check(fn: str, status: int) -> None:
+    if status != RT_OK:
+        raise RadtexError(fn, status)
+
+
+def call(name: str, *args) -> None:
+    check(name, getattr(lib(), name)(*args))

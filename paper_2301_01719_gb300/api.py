@@ -1,0 +1,227 @@
+"""Python binding of libradtex for PyTorch tensors.
+
+Every function has the name of the C entry point it calls (include/radtex.h)
+and only marshals arguments: tensors become device pointers, sizes come from
+their shapes, and the stream defaults to PyTorch's current stream on the
+tensors' device.  All the work happens in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import (RT_ACCUMULATE, RT_ANGULAR_BILINEAR, RT_BF16, RT_BORROW, RT_E4M3_BUCKET_SCALE,  # noqa: F401
+                   RT_ERR_BAD_OBJ_ID, RT_ERR_CUDA, RT_ERR_INVALID_ARG, RT_ERR_NONFINITE, RT_ERR_OOM, RT_ERR_TIMEOUT,
+                   RT_ERR_UNSUPPORTED, RT_F16, RT_F32, RT_LAYOUT_ATLAS, RT_LAYOUT_PLANES, RT_MAX_OBJECTS, RT_NEAREST,
+                   RT_OK, RT_QUADRILINEAR, RadtexError)
+
+FORMAT_BYTES = {RT_F32: 16, RT_F16: 8, RT_BF16: 8, RT_E4M3_BUCKET_SCALE: 4}
+CODE_DTYPE = {RT_F32: torch.float32, RT_F16: torch.int16, RT_BF16: torch.int16, RT_E4M3_BUCKET_SCALE: torch.uint8}
+FORMAT_NAMES = {"f32": RT_F32, "f16": RT_F16, "bf16": RT_BF16, "e4m3": RT_E4M3_BUCKET_SCALE}
+FILTER_NAMES = {"nearest": RT_NEAREST, "angular_bilinear": RT_ANGULAR_BILINEAR, "quadrilinear": RT_QUADRILINEAR}
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream, device) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    return ctypes.c_void_p(handle)
+
+
+def _check(t: torch.Tensor, name: str, dtype, last_dim: int | None = None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if last_dim is not None and (t.dim() < 1 or t.shape[-1] != last_dim):
+        raise ValueError(f"{name} must have last dimension {last_dim}, got {tuple(t.shape)}")
+
+
+class Context:
+    """An rt_ctx on one CUDA device; destroyed with the object (or .close())."""
+
+    def __init__(self, device: int = 0):
+        h = ctypes.c_void_p()
+        _lib.call("rt_context_create", int(device), ctypes.byref(h))
+        self.handle = h
+        self.device = int(device)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.lib().rt_context_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rt_context_create(device: int = 0) -> Context:
+    return Context(device)
+
+
+def rt_context_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def rt_create_texture(ctx: Context, w: int, h: int, n: int, storage: int = RT_F32, src_layout: int = RT_LAYOUT_ATLAS,
+                      src: torch.Tensor | None = None, flags: int = 0) -> int:
+    """src: FP32 CUDA tensor with w*h*n*n*4 elements in src_layout (or None).  Returns the object id."""
+    if src is not None:
+        _check(src, "src", torch.float32)
+        if src.numel() != w * h * n * n * 4:
+            raise ValueError(f"src has {src.numel()} elements, expected {w * h * n * n * 4}")
+    out = ctypes.c_int32(-1)
+    _lib.call("rt_create_texture", ctx.handle, int(w), int(h), int(n), int(storage), int(src_layout), _ptr(src),
+              int(flags), ctypes.byref(out))
+    return out.value
+
+
+def rt_destroy_texture(ctx: Context, obj_id: int) -> None:
+    _lib.call("rt_destroy_texture", ctx.handle, int(obj_id))
+
+
+def rt_texture_info(ctx: Context, obj_id: int) -> dict:
+    vals = [ctypes.c_int32() for _ in range(5)]
+    nbytes = ctypes.c_int64()
+    _lib.call("rt_texture_info", ctx.handle, int(obj_id), *[ctypes.byref(v) for v in vals], ctypes.byref(nbytes))
+    w, h, n, storage, layout = (v.value for v in vals)
+    return {"w": w, "h": h, "n": n, "storage": storage, "layout": layout, "bytes": nbytes.value}
+
+
+def rt_read_texture(ctx: Context, obj_id: int, dst_layout: int = RT_LAYOUT_ATLAS, stream=None):
+    """Stored codes (and E4M3 scales) of an owned texture, as new CUDA tensors.
+
+    Atlas layout: codes shape (h n, w n, 4); planes: (n, n, h, w, 4).  Codes are
+    float32 (F32), int16 bit patterns (F16 / BF16) or uint8 (E4M3)."""
+    info = rt_texture_info(ctx, obj_id)
+    w, h, n, fmt = info["w"], info["h"], info["n"], info["storage"]
+    dev = torch.device("cuda", ctx.device)
+    shape = (h * n, w * n, 4) if dst_layout == RT_LAYOUT_ATLAS else (n, n, h, w, 4)
+    codes = torch.empty(shape, dtype=CODE_DTYPE[fmt], device=dev)
+    scales = torch.empty((h, w), dtype=torch.float32, device=dev) if fmt == RT_E4M3_BUCKET_SCALE else None
+    _lib.call("rt_read_texture", ctx.handle, int(obj_id), int(dst_layout), _ptr(codes), _ptr(scales),
+              _stream(stream, dev))
+    return codes, scales
+
+
+def rt_fill_bucket_lobes(ctx: Context, obj_id: int, params: torch.Tensor, stream=None) -> None:
+    """params: CUDA float32 (h, w, 8) per-bucket lobe parameters."""
+    _check(params, "params", torch.float32, 8)
+    info = rt_texture_info(ctx, obj_id)
+    if params.numel() != info["w"] * info["h"] * 8:
+        raise ValueError(f"params must hold h x w x 8 = {info['h']} x {info['w']} x 8 floats")
+    _lib.call("rt_fill_bucket_lobes", ctx.handle, int(obj_id), _ptr(params), _stream(stream, params.device))
+
+
+def _gbuffer(uv, dirs, obj):
+    _check(uv, "uv", torch.float32, 2)
+    _check(dirs, "dir", torch.float32, 3)
+    _check(obj, "obj", torch.int32)
+    F = obj.numel()
+    if uv.numel() != 2 * F or dirs.numel() != 3 * F:
+        raise ValueError("uv, dir and obj must describe the same number of fragments")
+    return F
+
+
+def rt_shade(ctx: Context, uv: torch.Tensor, dirs: torch.Tensor, obj: torch.Tensor, filter: int = RT_QUADRILINEAR,
+             out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Forward synthesis: (F, 4) float32 colours."""
+    F = _gbuffer(uv, dirs, obj)
+    if out is None:
+        out = torch.empty((F, 4), dtype=torch.float32, device=uv.device)
+    _check(out, "out", torch.float32, 4)
+    if out.numel() != 4 * F:
+        raise ValueError("out must hold F x 4 floats")
+    _lib.call("rt_shade", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(obj), F, int(filter), _ptr(out),
+              _stream(stream, uv.device))
+    return out
+
+
+def rt_locate(ctx: Context, uv, dirs, obj, filter: int = RT_QUADRILINEAR, stream=None):
+    """(idx (F, 4) int32 floors, coord (F, 4) float32 continuous coordinates)."""
+    F = _gbuffer(uv, dirs, obj)
+    idx = torch.empty((F, 4), dtype=torch.int32, device=uv.device)
+    coord = torch.empty((F, 4), dtype=torch.float32, device=uv.device)
+    _lib.call("rt_locate", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(obj), F, int(filter), _ptr(idx), _ptr(coord),
+              _stream(stream, uv.device))
+    return idx, coord
+
+
+def rt_shade_backward(ctx: Context, uv, dirs, obj, filter: int, dL_dout: torch.Tensor, dL_dtex=None,
+                      dL_duv: torch.Tensor | None = None, dL_ddir: torch.Tensor | None = None, flags: int = 0,
+                      stream=None) -> None:
+    """dL_dtex: dict {object id: FP32 CUDA tensor in the object's storage layout} or None."""
+    F = _gbuffer(uv, dirs, obj)
+    _check(dL_dout, "dL_dout", torch.float32, 4)
+    if dL_dout.numel() != 4 * F:
+        raise ValueError("dL_dout must hold F x 4 floats")
+    if dL_duv is not None:
+        _check(dL_duv, "dL_duv", torch.float32, 2)
+        if dL_duv.numel() != 2 * F:
+            raise ValueError("dL_duv must hold F x 2 floats")
+    if dL_ddir is not None:
+        _check(dL_ddir, "dL_ddir", torch.float32, 3)
+        if dL_ddir.numel() != 3 * F:
+            raise ValueError("dL_ddir must hold F x 3 floats")
+    n_dtex = 0
+    arr = None
+    if dL_dtex:
+        n_dtex = max(dL_dtex) + 1
+        arr = (ctypes.c_void_p * n_dtex)()
+        for o, t in dL_dtex.items():
+            _check(t, f"dL_dtex[{o}]", torch.float32)
+            info = rt_texture_info(ctx, o)
+            if t.numel() != info["w"] * info["h"] * info["n"] ** 2 * 4:
+                raise ValueError(f"dL_dtex[{o}] must hold w h n^2 x 4 floats")
+            arr[o] = t.data_ptr()
+    _lib.call("rt_shade_backward", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(obj), F, int(filter), _ptr(dL_dout),
+              arr, n_dtex, _ptr(dL_duv), _ptr(dL_ddir), int(flags), _stream(stream, uv.device))
+
+
+def rt_footprint(ctx: Context, uv, dirs, obj, filter: int = RT_QUADRILINEAR, n_counts: int = RT_MAX_OBJECTS,
+                 stream=None) -> list[int]:
+    """Distinct texels read, per object id (synchronises)."""
+    F = _gbuffer(uv, dirs, obj)
+    counts = (ctypes.c_uint64 * n_counts)()
+    _lib.call("rt_footprint", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(obj), F, int(filter), counts, n_counts,
+              _stream(stream, uv.device))
+    return [int(c) for c in counts]
+
+
+def rt_convert_layout(src: torch.Tensor, src_layout: int, dst_layout: int, w: int, h: int, n: int,
+                      dst: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    _check(src, "src", torch.float32)
+    if src.numel() != w * h * n * n * 4:
+        raise ValueError("src must hold w h n^2 x 4 floats")
+    if dst is None:
+        shape = (h * n, w * n, 4) if dst_layout == RT_LAYOUT_ATLAS else (n, n, h, w, 4)
+        dst = torch.empty(shape, dtype=torch.float32, device=src.device)
+    _check(dst, "dst", torch.float32)
+    if dst.numel() != src.numel():
+        raise ValueError("dst must hold as many floats as src")
+    _lib.call("rt_convert_layout", _ptr(src), int(src_layout), _ptr(dst), int(dst_layout), int(w), int(h), int(n),
+              _stream(stream, src.device))
+    return dst
+
+
+def rt_get_error(ctx: Context, stream=None) -> int:
+    """Synchronises the stream and returns (and clears) the sticky device status."""
+    st = ctypes.c_int32(0)
+    dev = torch.device("cuda", ctx.device)
+    _lib.call("rt_get_error", ctx.handle, _stream(stream, dev), ctypes.byref(st))
+    return st.value
+
+
+def rt_status_string(status: int) -> str:
+    return _lib.lib().rt_status_string(int(status)).decode()

@@ -1,0 +1,436 @@
+// api.cu -- the C ABI of libradtex (declared in include/radtex.h): context,
+// texture table, argument validation, kernel launches and the status model.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "radtex.h"
+#include "rt_device.cuh"
+#include "rt_internal.h"
+
+using rt::TexDesc;
+
+struct rt_ctx {
+    int device = 0;
+    TexDesc* d_table = nullptr;          // device copy of `table`
+    unsigned* d_status = nullptr;        // sticky device status word
+    unsigned* h_status = nullptr;        // pinned host mirror for rt_get_error
+    TexDesc table[RT_MAX_OBJECTS];       // host copy
+    void* owned[RT_MAX_OBJECTS];         // storage the library allocated (nullptr if borrowed)
+    float* scales[RT_MAX_OBJECTS];       // E4M3 scales the library allocated
+    int64_t bytes[RT_MAX_OBJECTS];
+    int n_obj = 0;                       // one past the highest id ever used
+};
+
+namespace {
+
+// Makes the context's device current for the duration of a call and restores
+// the caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+inline int texel_bytes(int fmt) {
+    switch (fmt) {
+        case RT_F32:
+            return 16;
+        case RT_F16:
+        case RT_BF16:
+            return 8;
+        case RT_E4M3_BUCKET_SCALE:
+            return 4;
+        default:
+            return 0;
+    }
+}
+
+inline rt_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return RT_OK;
+    if (e == cudaErrorMemoryAllocation) return RT_ERR_OOM;
+    return RT_ERR_CUDA;
+}
+
+inline bool valid_filter(int f) { return f == RT_NEAREST || f == RT_ANGULAR_BILINEAR || f == RT_QUADRILINEAR; }
+
+rt_status check_gbuffer(const float* uv, const float* dir, const int32_t* obj, int64_t F) {
+    if (F < 0) return RT_ERR_INVALID_ARG;
+    if (F == 0) return RT_OK;
+    if (!uv || !dir || !obj) return RT_ERR_INVALID_ARG;
+    if (!aligned16(uv) || !aligned16(dir) || !aligned16(obj)) return RT_ERR_INVALID_ARG;
+    return RT_OK;
+}
+
+rt_status upload_table(rt_ctx* ctx) {
+    cudaError_t e = cudaMemcpy(ctx->d_table, ctx->table, sizeof(TexDesc) * RT_MAX_OBJECTS, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rt_status_string(rt_status s) {
+    switch (s) {
+        case RT_OK:
+            return "ok";
+        case RT_ERR_INVALID_ARG:
+            return "invalid argument (null, misaligned or out-of-range)";
+        case RT_ERR_OOM:
+            return "device memory or object ids exhausted";
+        case RT_ERR_CUDA:
+            return "CUDA runtime error";
+        case RT_ERR_BAD_OBJ_ID:
+            return "a fragment named an object id with no texture";
+        case RT_ERR_NONFINITE:
+            return "a fragment had a non-finite UV or direction";
+        case RT_ERR_TIMEOUT:
+            return "a bounded device wait gave up";
+        case RT_ERR_UNSUPPORTED:
+            return "unsupported combination of options";
+    }
+    return "unknown status";
+}
+
+rt_status rt_context_create(int cuda_device, rt_ctx** out) {
+    if (!out) return RT_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) return RT_ERR_CUDA;
+    if (cuda_device < 0 || cuda_device >= count) return RT_ERR_INVALID_ARG;
+    rt_ctx* ctx = new (std::nothrow) rt_ctx();
+    if (!ctx) return RT_ERR_OOM;
+    std::memset(ctx->table, 0, sizeof(ctx->table));
+    std::memset(ctx->owned, 0, sizeof(ctx->owned));
+    std::memset(ctx->scales, 0, sizeof(ctx->scales));
+    std::memset(ctx->bytes, 0, sizeof(ctx->bytes));
+    ctx->device = cuda_device;
+    DeviceGuard g(cuda_device);
+    if (!g.ok) {
+        delete ctx;
+        return RT_ERR_CUDA;
+    }
+    cudaError_t e = cudaMalloc(&ctx->d_table, sizeof(TexDesc) * RT_MAX_OBJECTS);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(unsigned));
+    if (e == cudaSuccess) {
+        rt_status st = upload_table(ctx);
+        if (st != RT_OK) e = cudaErrorUnknown;
+    }
+    if (e != cudaSuccess) {
+        cudaFree(ctx->d_table);
+        cudaFree(ctx->d_status);
+        cudaFreeHost(ctx->h_status);
+        delete ctx;
+        return cuda_status(e);
+    }
+    *out = ctx;
+    return RT_OK;
+}
+
+void rt_context_destroy(rt_ctx* ctx) {
+    if (!ctx) return;
+    {
+        DeviceGuard g(ctx->device);
+        cudaDeviceSynchronize();
+        for (int o = 0; o < RT_MAX_OBJECTS; ++o) {
+            if (ctx->owned[o]) cudaFree(ctx->owned[o]);
+            if (ctx->scales[o]) cudaFree(ctx->scales[o]);
+        }
+        cudaFree(ctx->d_table);
+        cudaFree(ctx->d_status);
+        cudaFreeHost(ctx->h_status);
+    }
+    delete ctx;
+}
+
+rt_status rt_create_texture(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, rt_format storage, rt_layout src_layout,
+                            const float* src, int32_t flags, int32_t* obj_id_out) {
+    if (!ctx || !obj_id_out) return RT_ERR_INVALID_ARG;
+    if (w < 1 || h < 1 || n < 1 || w > 65536 || h > 65536 || n > 64) return RT_ERR_INVALID_ARG;
+    if (texel_bytes(storage) == 0) return RT_ERR_INVALID_ARG;
+    if (src_layout != RT_LAYOUT_ATLAS && src_layout != RT_LAYOUT_PLANES) return RT_ERR_INVALID_ARG;
+    if (src && !aligned16(src)) return RT_ERR_INVALID_ARG;
+    const bool borrow = (flags & RT_BORROW) != 0;
+    if (borrow && (storage != RT_F32 || !src)) return RT_ERR_INVALID_ARG;
+    int o = -1;
+    for (int k = 0; k < RT_MAX_OBJECTS; ++k)
+        if (!ctx->table[k].live) {
+            o = k;
+            break;
+        }
+    if (o < 0) return RT_ERR_OOM;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    // src may have been written on any stream of the device.
+    if (cudaDeviceSynchronize() != cudaSuccess) return RT_ERR_CUDA;
+
+    const int64_t texels = (int64_t)w * h * n * n;
+    TexDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.W = w;
+    d.H = h;
+    d.n = n;
+    d.fmt = storage;
+    d.plane = (int64_t)w * h;
+    d.fW = (float)w;
+    d.fH = (float)h;
+    d.half_n = 0.5f * (float)n;
+    d.lo = 1.0f / (float)n - 1.0f;
+    d.hi = 1.0f - 1.0f / (float)n;
+    d.live = 1;
+    void* storage_ptr = nullptr;
+    float* scale_ptr = nullptr;
+    if (borrow) {
+        d.base = src;
+        d.layout = src_layout;
+        ctx->bytes[o] = texels * 16;
+    } else {
+        d.layout = RT_LAYOUT_PLANES;
+        const int64_t bytes = texels * texel_bytes(storage);
+        cudaError_t e = cudaMalloc(&storage_ptr, (size_t)bytes);
+        if (e == cudaSuccess && storage == RT_E4M3_BUCKET_SCALE)
+            e = cudaMalloc(&scale_ptr, sizeof(float) * (size_t)d.plane);
+        if (e == cudaSuccess) {
+            if (src) {
+                e = rt::launch_encode(src, src_layout, storage_ptr, scale_ptr, w, h, n, storage, 0);
+            } else {
+                e = cudaMemset(storage_ptr, 0, (size_t)bytes);
+                if (e == cudaSuccess && scale_ptr) {
+                    std::vector<float> ones((size_t)d.plane, 1.0f);
+                    e = cudaMemcpy(scale_ptr, ones.data(), sizeof(float) * ones.size(), cudaMemcpyHostToDevice);
+                }
+            }
+        }
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            cudaFree(storage_ptr);
+            cudaFree(scale_ptr);
+            return cuda_status(e);
+        }
+        d.base = storage_ptr;
+        d.scale = scale_ptr;
+        ctx->owned[o] = storage_ptr;
+        ctx->scales[o] = scale_ptr;
+        ctx->bytes[o] = bytes + (scale_ptr ? (int64_t)sizeof(float) * d.plane : 0);
+    }
+    ctx->table[o] = d;
+    if (o + 1 > ctx->n_obj) ctx->n_obj = o + 1;
+    rt_status st = upload_table(ctx);
+    if (st != RT_OK) {
+        ctx->table[o].live = 0;
+        cudaFree(storage_ptr);
+        cudaFree(scale_ptr);
+        ctx->owned[o] = nullptr;
+        ctx->scales[o] = nullptr;
+        return st;
+    }
+    *obj_id_out = o;
+    return RT_OK;
+}
+
+rt_status rt_destroy_texture(rt_ctx* ctx, int32_t obj_id) {
+    if (!ctx || obj_id < 0 || obj_id >= RT_MAX_OBJECTS || !ctx->table[obj_id].live) return RT_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (ctx->owned[obj_id]) cudaFree(ctx->owned[obj_id]);
+    if (ctx->scales[obj_id]) cudaFree(ctx->scales[obj_id]);
+    ctx->owned[obj_id] = nullptr;
+    ctx->scales[obj_id] = nullptr;
+    ctx->bytes[obj_id] = 0;
+    std::memset(&ctx->table[obj_id], 0, sizeof(TexDesc));
+    rt_status st = upload_table(ctx);
+    return e != cudaSuccess ? cuda_status(e) : st;
+}
+
+rt_status rt_texture_info(rt_ctx* ctx, int32_t obj_id, int32_t* w, int32_t* h, int32_t* n, int32_t* storage,
+                          int32_t* layout, int64_t* bytes) {
+    if (!ctx || obj_id < 0 || obj_id >= RT_MAX_OBJECTS || !ctx->table[obj_id].live) return RT_ERR_INVALID_ARG;
+    const TexDesc& d = ctx->table[obj_id];
+    if (w) *w = d.W;
+    if (h) *h = d.H;
+    if (n) *n = d.n;
+    if (storage) *storage = d.fmt;
+    if (layout) *layout = d.layout;
+    if (bytes) *bytes = ctx->bytes[obj_id];
+    return RT_OK;
+}
+
+rt_status rt_read_texture(rt_ctx* ctx, int32_t obj_id, rt_layout dst_layout, void* codes_dst, float* scales_dst,
+                          rt_stream_t stream) {
+    if (!ctx || obj_id < 0 || obj_id >= RT_MAX_OBJECTS || !ctx->table[obj_id].live || !codes_dst)
+        return RT_ERR_INVALID_ARG;
+    if (dst_layout != RT_LAYOUT_ATLAS && dst_layout != RT_LAYOUT_PLANES) return RT_ERR_INVALID_ARG;
+    const TexDesc& d = ctx->table[obj_id];
+    if (d.layout != RT_LAYOUT_PLANES) return RT_ERR_UNSUPPORTED;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = rt::launch_read(d.base, d.fmt, d.W, d.H, d.n, dst_layout, codes_dst, s);
+    if (e == cudaSuccess && scales_dst && d.scale)
+        e = cudaMemcpyAsync(scales_dst, d.scale, sizeof(float) * (size_t)d.plane, cudaMemcpyDeviceToDevice, s);
+    return cuda_status(e);
+}
+
+rt_status rt_fill_bucket_lobes(rt_ctx* ctx, int32_t obj_id, const float* params, rt_stream_t stream) {
+    if (!ctx || obj_id < 0 || obj_id >= RT_MAX_OBJECTS || !ctx->table[obj_id].live || !params || !aligned16(params))
+        return RT_ERR_INVALID_ARG;
+    const TexDesc& d = ctx->table[obj_id];
+    if (!ctx->owned[obj_id]) return RT_ERR_UNSUPPORTED;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    return cuda_status(rt::launch_fill_lobes(params, ctx->owned[obj_id], ctx->scales[obj_id], d.W, d.H, d.n, d.fmt,
+                                             (cudaStream_t)stream));
+}
+
+rt_status rt_shade(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F, rt_filter filter,
+                   float* out, rt_stream_t stream) {
+    if (!ctx || !valid_filter(filter)) return RT_ERR_INVALID_ARG;
+    rt_status st = check_gbuffer(uv, dir, obj, F);
+    if (st != RT_OK) return st;
+    if (F == 0) return RT_OK;
+    if (!out || !aligned16(out)) return RT_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    return cuda_status(rt::launch_shade(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, out, ctx->d_status,
+                                        (cudaStream_t)stream));
+}
+
+rt_status rt_locate(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F, rt_filter filter,
+                    int32_t* idx, float* coord, rt_stream_t stream) {
+    if (!ctx || !valid_filter(filter)) return RT_ERR_INVALID_ARG;
+    rt_status st = check_gbuffer(uv, dir, obj, F);
+    if (st != RT_OK) return st;
+    if (F == 0) return RT_OK;
+    if (!idx || !coord || !aligned16(idx) || !aligned16(coord)) return RT_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    return cuda_status(rt::launch_locate(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, idx, coord,
+                                         ctx->d_status, (cudaStream_t)stream));
+}
+
+rt_status rt_shade_backward(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,
+                            rt_filter filter, const float* dL_dout, float* const* dL_dtex, int32_t n_dtex,
+                            float* dL_duv, float* dL_ddir, int32_t flags, rt_stream_t stream) {
+    if (!ctx || !valid_filter(filter)) return RT_ERR_INVALID_ARG;
+    rt_status st = check_gbuffer(uv, dir, obj, F);
+    if (st != RT_OK) return st;
+    if (n_dtex < 0 || n_dtex > RT_MAX_OBJECTS || (n_dtex > 0 && !dL_dtex)) return RT_ERR_INVALID_ARG;
+    if ((dL_duv && !aligned16(dL_duv)) || (dL_ddir && !aligned16(dL_ddir))) return RT_ERR_INVALID_ARG;
+    if (F > 0 && (!dL_dout || !aligned16(dL_dout))) return RT_ERR_INVALID_ARG;
+    const bool accumulate = (flags & RT_ACCUMULATE) != 0;
+    rt::GradTable grads;
+    std::memset(&grads, 0, sizeof(grads));
+    bool any = false;
+    for (int o = 0; o < n_dtex; ++o) {
+        if (!dL_dtex[o]) continue;
+        if (o >= RT_MAX_OBJECTS || !ctx->table[o].live || !aligned16(dL_dtex[o])) return RT_ERR_INVALID_ARG;
+        grads.p[o] = dL_dtex[o];
+        any = true;
+    }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!accumulate)
+        for (int o = 0; o < n_dtex && e == cudaSuccess; ++o)
+            if (grads.p[o]) {
+                const TexDesc& d = ctx->table[o];
+                e = cudaMemsetAsync(grads.p[o], 0, (size_t)16 * d.plane * d.n * d.n, s);
+            }
+    if (e == cudaSuccess && F > 0)
+        e = rt::launch_backward(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, dL_dout, grads, any, dL_duv,
+                                dL_ddir, accumulate, ctx->d_status, s);
+    return cuda_status(e);
+}
+
+rt_status rt_footprint(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,
+                       rt_filter filter, uint64_t* counts_host, int32_t n_counts, rt_stream_t stream) {
+    if (!ctx || !valid_filter(filter) || !counts_host || n_counts < 0) return RT_ERR_INVALID_ARG;
+    rt_status st = check_gbuffer(uv, dir, obj, F);
+    if (st != RT_OK) return st;
+    for (int o = 0; o < n_counts; ++o) counts_host[o] = 0;
+    if (F == 0) return RT_OK;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int64_t> offset(ctx->n_obj + 1, 0);
+    for (int o = 0; o < ctx->n_obj; ++o) {
+        const TexDesc& d = ctx->table[o];
+        int64_t texels = d.live ? d.plane * d.n * d.n : 0;
+        offset[o + 1] = offset[o] + (texels + 31) / 32;
+    }
+    const int64_t words = offset[ctx->n_obj];
+    uint32_t* bitmap = nullptr;
+    int64_t* d_offset = nullptr;
+    unsigned long long* d_count = nullptr;
+    cudaError_t e = cudaMalloc(&bitmap, sizeof(uint32_t) * (size_t)(words > 0 ? words : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d_offset, sizeof(int64_t) * offset.size());
+    if (e == cudaSuccess) e = cudaMalloc(&d_count, sizeof(unsigned long long) * (size_t)(ctx->n_obj + 1));
+    if (e == cudaSuccess) e = cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * (size_t)(words > 0 ? words : 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long) * (size_t)(ctx->n_obj + 1), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_offset, offset.data(), sizeof(int64_t) * offset.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = rt::launch_footprint_mark(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, bitmap, d_offset,
+                                      ctx->d_status, s);
+    for (int o = 0; o < ctx->n_obj && e == cudaSuccess; ++o)
+        e = rt::launch_popcount(bitmap + offset[o], offset[o + 1] - offset[o], d_count + o, s);
+    std::vector<unsigned long long> h((size_t)ctx->n_obj + 1, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), d_count, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(bitmap);
+    cudaFree(d_offset);
+    cudaFree(d_count);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int o = 0; o < n_counts && o < ctx->n_obj; ++o) counts_host[o] = h[o];
+    return RT_OK;
+}
+
+rt_status rt_convert_layout(const float* src, rt_layout src_layout, float* dst, rt_layout dst_layout, int32_t w,
+                            int32_t h, int32_t n, rt_stream_t stream) {
+    if (!src || !dst || !aligned16(src) || !aligned16(dst) || w < 1 || h < 1 || n < 1) return RT_ERR_INVALID_ARG;
+    if ((src_layout != RT_LAYOUT_ATLAS && src_layout != RT_LAYOUT_PLANES) ||
+        (dst_layout != RT_LAYOUT_ATLAS && dst_layout != RT_LAYOUT_PLANES))
+        return RT_ERR_INVALID_ARG;
+    return cuda_status(rt::launch_convert(src, src_layout, dst, dst_layout, w, h, n, (cudaStream_t)stream));
+}
+
+rt_status rt_get_error(rt_ctx* ctx, rt_stream_t stream, rt_status* device_status) {
+    if (!ctx || !device_status) return RT_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    unsigned bits = *ctx->h_status;
+    *device_status = (bits & rt::ST_BAD_OBJ)     ? RT_ERR_BAD_OBJ_ID
+                     : (bits & rt::ST_NONFINITE) ? RT_ERR_NONFINITE
+                     : (bits & rt::ST_TIMEOUT)   ? RT_ERR_TIMEOUT
+                                                 : RT_OK;
+    return RT_OK;
+}
+
+}  // extern "C"

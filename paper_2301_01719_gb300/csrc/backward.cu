@@ -1,0 +1,191 @@
+// backward.cu -- gradients of the lookup: texels, UV and direction.
+//
+// The filter weights are recomputed exactly as the forward pass computes them
+// (nothing is stored between the passes).  Texel gradients w_tap * dL/dout are
+// summed into FP32 buffers with 16-byte vector reductions (red.global.add.v4.f32),
+// one per tap of non-zero weight.  UV and direction gradients follow the chain
+// rule through the nested lerps, the Note's clamp (zero derivative where a
+// coordinate is clamped), Eq. 3 and Eq. 1b.
+#include "rt_device.cuh"
+#include "rt_filter.cuh"
+#include "rt_internal.h"
+
+namespace rt {
+
+constexpr int kBackThreads = 256;
+
+struct CoordGrad {
+    float gu, gv, gs, gt;  // dL/d(weight coordinate) of the u, v, s, t axes
+};
+
+template <int FILTER, int FMT, int LAYOUT>
+__device__ __forceinline__ CoordGrad backward_taps(const TexDesc& d, const Lookup<FILTER>& L, float4 g, float* grad,
+                                                   bool coord_grads) {
+    CoordGrad cg = {0.f, 0.f, 0.f, 0.f};
+    const float wu[2] = {1.f - L.u.w, L.u.w}, wv[2] = {1.f - L.v.w, L.v.w};
+    const float ws[2] = {1.f - L.s.w, L.s.w}, wt[2] = {1.f - L.t.w, L.t.w};
+    if (grad) {
+        const int nu = FILTER == RT_QUADRILINEAR ? 2 : 1;
+        const int ns = FILTER == RT_NEAREST ? 1 : 2;
+        for (int b = 0; b < nu; ++b)
+            for (int a = 0; a < nu; ++a)
+                for (int q = 0; q < ns; ++q)
+                    for (int p = 0; p < ns; ++p) {
+                        float w = (nu == 2 ? wu[a] * wv[b] : 1.f) * (ns == 2 ? ws[p] * wt[q] : 1.f);
+                        if (w == 0.f) continue;
+                        int64_t idx = texel_index<LAYOUT>(d, a ? L.u.k1 : L.u.k0, b ? L.v.k1 : L.v.k0,
+                                                          p ? L.s.k1 : L.s.k0, q ? L.t.k1 : L.t.k0);
+                        red_add_v4(grad + 4 * idx, make_float4(w * g.x, w * g.y, w * g.z, w * g.w));
+                    }
+    }
+    if (FILTER == RT_NEAREST || !coord_grads) return cg;
+    if (FILTER == RT_ANGULAR_BILINEAR) {
+        float4 t00, t10, t01, t11;
+        load_quad<FMT, LAYOUT>(d, L.u.k0, L.v.k0, L.s, L.t, t00, t10, t01, t11);
+        float4 x0 = lerp4(t00, t10, L.s.w), x1 = lerp4(t01, t11, L.s.w);
+        cg.gs = dot4(g, lerp4(sub4(t10, t00), sub4(t11, t01), L.t.w));
+        cg.gt = dot4(g, sub4(x1, x0));
+        return cg;
+    }
+    float4 c[2][2], ds[2][2], dt[2][2];
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            float4 t00, t10, t01, t11;
+            load_quad<FMT, LAYOUT>(d, a ? L.u.k1 : L.u.k0, b ? L.v.k1 : L.v.k0, L.s, L.t, t00, t10, t01, t11);
+            float4 x0 = lerp4(t00, t10, L.s.w), x1 = lerp4(t01, t11, L.s.w);
+            c[b][a] = lerp4(x0, x1, L.t.w);
+            ds[b][a] = lerp4(sub4(t10, t00), sub4(t11, t01), L.t.w);
+            dt[b][a] = sub4(x1, x0);
+        }
+    float4 y0 = lerp4(c[0][0], c[0][1], L.u.w), y1 = lerp4(c[1][0], c[1][1], L.u.w);
+    cg.gu = dot4(g, lerp4(sub4(c[0][1], c[0][0]), sub4(c[1][1], c[1][0]), L.v.w));
+    cg.gv = dot4(g, sub4(y1, y0));
+    cg.gs = dot4(g, lerp4(lerp4(ds[0][0], ds[0][1], L.u.w), lerp4(ds[1][0], ds[1][1], L.u.w), L.v.w));
+    cg.gt = dot4(g, lerp4(lerp4(dt[0][0], dt[0][1], L.u.w), lerp4(dt[1][0], dt[1][1], L.u.w), L.v.w));
+    return cg;
+}
+
+template <int FILTER>
+__device__ __forceinline__ CoordGrad backward_any(const TexDesc& d, const Lookup<FILTER>& L, float4 g, float* grad,
+                                                  bool coord_grads) {
+    switch (d.fmt) {
+        case RT_F16:
+            return backward_taps<FILTER, RT_F16, RT_LAYOUT_PLANES>(d, L, g, grad, coord_grads);
+        case RT_BF16:
+            return backward_taps<FILTER, RT_BF16, RT_LAYOUT_PLANES>(d, L, g, grad, coord_grads);
+        case RT_E4M3_BUCKET_SCALE:
+            return backward_taps<FILTER, RT_E4M3_BUCKET_SCALE, RT_LAYOUT_PLANES>(d, L, g, grad, coord_grads);
+        default:
+            if (d.layout == RT_LAYOUT_ATLAS)
+                return backward_taps<FILTER, RT_F32, RT_LAYOUT_ATLAS>(d, L, g, grad, coord_grads);
+            return backward_taps<FILTER, RT_F32, RT_LAYOUT_PLANES>(d, L, g, grad, coord_grads);
+    }
+}
+
+// dL/dI from dL/dB through Eq. 3 and Eq. 1b.
+//  Eq. 3 (x branch, |A_x| >= |A_y|, q = A_y / A_x = I_y / I_x):
+//    dB/dA = [[1, q], [-q^3, 1 + 2 q^2]] / sqrt(1 + q^2)   (rows B_x, B_y)
+//  and symmetrically on the y branch; the identity at A = 0.
+//  Eq. 1b: dA_r/dI_c = sqrt(2) (delta_rc / D - I_r g_c / D^3), g = (I_x, I_y, I_z + 1), D = |g|.
+__device__ __forceinline__ float3 direction_grad(float Ix, float Iy, float Iz, float gBx, float gBy) {
+    float ax = fabsf(Ix), ay = fabsf(Iy);
+    float gAx, gAy;
+    if (!(fmaxf(ax, ay) >= 1e-30f)) {
+        gAx = gBx;
+        gAy = gBy;
+    } else if (ax >= ay) {
+        float q = Iy / Ix;
+        float r = 1.0f / sqrtf(fmaf(q, q, 1.0f));
+        gAx = (gBx - gBy * q * q * q) * r;
+        gAy = (gBx * q + gBy * fmaf(2.0f * q, q, 1.0f)) * r;
+    } else {
+        float p = Ix / Iy;
+        float r = 1.0f / sqrtf(fmaf(p, p, 1.0f));
+        gAy = (gBy - gBx * p * p * p) * r;
+        gAx = (gBy * p + gBx * fmaf(2.0f * p, p, 1.0f)) * r;
+    }
+    float zp = Iz + 1.0f;
+    float D2 = Ix * Ix + Iy * Iy + zp * zp;
+    if (!(D2 > 1e-30f)) return make_float3(0.f, 0.f, 0.f);
+    float invD = 1.0f / sqrtf(D2);
+    float k = 1.41421356237f * invD;
+    float k3 = k * invD * invD;
+    float m = k3 * (gAx * Ix + gAy * Iy);
+    return make_float3(k * gAx - m * Ix, k * gAy - m * Iy, -m * zp);
+}
+
+template <int FILTER>
+__global__ void __launch_bounds__(kBackThreads) backward_kernel(
+    const TexDesc* __restrict__ table, int n_obj, const float* __restrict__ uv, const float* __restrict__ dir,
+    const int32_t* __restrict__ obj, int64_t F, const float* __restrict__ dL_dout, const __grid_constant__ GradTable grads,
+    bool any_grad, float* __restrict__ dL_duv, float* __restrict__ dL_ddir, bool accumulate, unsigned* status) {
+    __shared__ GStage<kBackThreads> S;
+    const Frag q = stage_gbuffer<kBackThreads>(uv, dir, obj, F, S);
+    const int64_t f = (int64_t)blockIdx.x * kBackThreads + threadIdx.x;
+    if (f >= F) return;
+    const bool coord_grads = (dL_duv != nullptr) || (dL_ddir != nullptr);
+    float2 guv = make_float2(0.f, 0.f);
+    float3 gdir = make_float3(0.f, 0.f, 0.f);
+    TexDesc d;
+    if (fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d)) {
+        const float4 go = __ldcs(reinterpret_cast<const float4*>(dL_dout) + f);
+        Lookup<FILTER> L = locate<FILTER>(d, q.u, q.v, q.x, q.y, q.z);
+        float* grad = any_grad ? grads.p[q.o] : nullptr;
+        CoordGrad cg = backward_any<FILTER>(d, L, go, grad, coord_grads);
+        if (FILTER == RT_QUADRILINEAR) {
+            float cu = fmaf(q.u, d.fW, -0.5f), cv = fmaf(q.v, d.fH, -0.5f);
+            guv.x = (cu > -1.0f && cu < d.fW) ? cg.gu * d.fW : 0.f;
+            guv.y = (cv > -1.0f && cv < d.fH) ? cg.gv * d.fH : 0.f;
+        }
+        if (FILTER != RT_NEAREST && dL_ddir) {
+            float gBx = (L.B.x > d.lo && L.B.x < d.hi) ? cg.gs * d.half_n : 0.f;
+            float gBy = (L.B.y > d.lo && L.B.y < d.hi) ? cg.gt * d.half_n : 0.f;
+            gdir = direction_grad(q.x, q.y, q.z, gBx, gBy);
+        }
+    }
+    if (dL_duv) {
+        float2* p = reinterpret_cast<float2*>(dL_duv) + f;
+        if (accumulate) {
+            float2 o = *p;
+            guv.x += o.x;
+            guv.y += o.y;
+        }
+        *p = guv;
+    }
+    if (dL_ddir) {
+        float* p = dL_ddir + 3 * f;
+        if (accumulate) {
+            gdir.x += p[0];
+            gdir.y += p[1];
+            gdir.z += p[2];
+        }
+        p[0] = gdir.x;
+        p[1] = gdir.y;
+        p[2] = gdir.z;
+    }
+}
+
+cudaError_t launch_backward(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
+                            int64_t F, int filter, const float* dL_dout, const GradTable& grads, bool any_grad,
+                            float* dL_duv, float* dL_ddir, bool accumulate, unsigned* status, cudaStream_t stream) {
+    dim3 grid((unsigned)((F + kBackThreads - 1) / kBackThreads)), block(kBackThreads);
+    switch (filter) {
+        case RT_NEAREST:
+            backward_kernel<RT_NEAREST><<<grid, block, 0, stream>>>(table, n_obj, uv, dir, obj, F, dL_dout, grads,
+                                                                    any_grad, dL_duv, dL_ddir, accumulate, status);
+            break;
+        case RT_ANGULAR_BILINEAR:
+            backward_kernel<RT_ANGULAR_BILINEAR><<<grid, block, 0, stream>>>(
+                table, n_obj, uv, dir, obj, F, dL_dout, grads, any_grad, dL_duv, dL_ddir, accumulate, status);
+            break;
+        default:
+            backward_kernel<RT_QUADRILINEAR><<<grid, block, 0, stream>>>(
+                table, n_obj, uv, dir, obj, F, dL_dout, grads, any_grad, dL_duv, dL_ddir, accumulate, status);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rt

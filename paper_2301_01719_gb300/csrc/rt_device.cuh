@@ -1,0 +1,225 @@
+// rt_device.cuh -- device-side pieces shared by the kernels of libradtex.
+//
+// The per-fragment lookup of Section 2 of Fober, "Radiance Textures for
+// Rasterizing Ray-Traced Data" (arXiv 2301.01719), in FP32:
+//   bucket  <- surface UV                     (Section 2, third paragraph)
+//   A       <- Eq. 1b (equisolid projection, tangent space)
+//   B       <- Eq. 3  (disc to square)
+//   B       <- clamp to [1/n - 1, 1 - 1/n]    (Note after Eq. 3)
+//   texels  <- floor / fractions of the continuous coordinates
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "radtex.h"
+
+namespace rt {
+
+enum : unsigned { ST_BAD_OBJ = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u };
+
+// One object of the texture table (64 bytes).  Built on the host when the
+// texture is created; read by every kernel through the read-only path.
+struct __align__(16) TexDesc {
+    const void* base;    // texel storage
+    const float* scale;  // per-bucket scale, row-major h x w (E4M3 only)
+    int64_t plane;       // texels per direction plane, w * h
+    int32_t W, H, n, fmt;
+    int16_t layout, live;
+    float fW, fH;        // w, h as float
+    float half_n;        // n / 2
+    float lo, hi;        // clamp range of B: 1/n - 1, 1 - 1/n
+};
+static_assert(sizeof(TexDesc) == 64, "TexDesc is 64 bytes");
+
+__device__ __forceinline__ TexDesc load_desc(const TexDesc* __restrict__ table, int o) {
+    const int4* p = reinterpret_cast<const int4*>(table + o);
+    int4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
+    TexDesc r;
+    int4* q = reinterpret_cast<int4*>(&r);
+    q[0] = a;
+    q[1] = b;
+    q[2] = c;
+    q[3] = d;
+    return r;
+}
+
+__device__ __forceinline__ bool finite3(float a, float b, float c) {
+    return isfinite(a) && isfinite(b) && isfinite(c);
+}
+
+// Eq. 1b followed by Eq. 3, B = A |A| / max(|A_x|, |A_y|) with
+// A = sqrt(2) I_xy / |(I_x, I_y, I_z + 1)|.  Since A is a positive multiple of
+// I_xy, B = sqrt(2) (I_xy / m) |I_xy| / |(I_x, I_y, I_z + 1)| with
+// m = max(|I_x|, |I_y|); dividing every component by m first keeps the sums
+// of squares away from underflow.  I_xy = 0 (also I = -N) gives B = 0, the
+// limit of Eq. 3; so does m < 1e-30, which moves B by less than 1e-30.
+__device__ __forceinline__ float2 incidence_to_square(float Ix, float Iy, float Iz) {
+    float m = fmaxf(fabsf(Ix), fabsf(Iy));
+    if (!(m >= 1e-30f)) return make_float2(0.f, 0.f);
+    float rm = 1.0f / m;
+    float x = Ix * rm, y = Iy * rm, z = (Iz + 1.0f) * rm;
+    float g2 = x * x + y * y;  // in [1, 2]
+    float D2 = g2 + z * z;
+    float k = 1.41421356237f * sqrtf(g2 / D2);
+    return make_float2(x * k, y * k);
+}
+
+// Continuous coordinate of a spatial axis and its two taps (clamp to edge).
+struct Axis {
+    int k0, k1;  // taps (equal on a nearest axis)
+    float w;     // weight of k1 (0 on a nearest axis)
+    float c;     // continuous coordinate
+    int fl;      // floor(c)
+};
+
+__device__ __forceinline__ Axis spatial_axis_bilinear(float x, float size, int isize) {
+    Axis a;
+    float c = fmaf(x, size, -0.5f);
+    c = fminf(fmaxf(c, -1.0f), size);
+    float f = floorf(c);
+    a.c = c;
+    a.fl = (int)f;
+    a.w = c - f;
+    a.k0 = min(max(a.fl, 0), isize - 1);
+    a.k1 = min(max(a.fl + 1, 0), isize - 1);
+    return a;
+}
+
+__device__ __forceinline__ Axis spatial_axis_nearest(float x, float size, int isize) {
+    Axis a;
+    float c = fminf(fmaxf(x * size, 0.0f), size);
+    a.c = c;
+    a.fl = (int)floorf(c);
+    a.k0 = a.k1 = min(a.fl, isize - 1);
+    a.w = 0.0f;
+    return a;
+}
+
+// In-bucket axis: B clamped to [lo, hi] (the Note after Eq. 3), texel k centred at
+// B = (2k + 1)/n - 1.
+__device__ __forceinline__ Axis angular_axis_bilinear(float B, float lo, float hi, float half_n, int n) {
+    Axis a;
+    float Bc = fminf(fmaxf(B, lo), hi);
+    float c = fmaf(Bc + 1.0f, half_n, -0.5f);
+    c = fminf(fmaxf(c, 0.0f), (float)(n - 1));
+    float f = floorf(c);
+    a.c = c;
+    a.fl = (int)f;
+    a.w = c - f;
+    a.k0 = a.fl;
+    a.k1 = min(a.fl + 1, n - 1);
+    return a;
+}
+
+__device__ __forceinline__ Axis angular_axis_nearest(float B, float lo, float hi, float half_n, int n) {
+    Axis a;
+    float Bc = fminf(fmaxf(B, lo), hi);
+    float c = (Bc + 1.0f) * half_n;
+    a.c = c;
+    a.fl = (int)floorf(c);
+    a.k0 = a.k1 = min(max(a.fl, 0), n - 1);
+    a.w = 0.0f;
+    return a;
+}
+
+template <int FILTER>
+struct Lookup {
+    Axis u, v, s, t;
+    float2 B;
+};
+
+template <int FILTER>
+__device__ __forceinline__ Lookup<FILTER> locate(const TexDesc& d, float u, float v, float Ix, float Iy, float Iz) {
+    Lookup<FILTER> L;
+    if (FILTER == RT_QUADRILINEAR) {
+        L.u = spatial_axis_bilinear(u, d.fW, d.W);
+        L.v = spatial_axis_bilinear(v, d.fH, d.H);
+    } else {
+        L.u = spatial_axis_nearest(u, d.fW, d.W);
+        L.v = spatial_axis_nearest(v, d.fH, d.H);
+    }
+    L.B = incidence_to_square(Ix, Iy, Iz);
+    if (FILTER == RT_NEAREST) {
+        L.s = angular_axis_nearest(L.B.x, d.lo, d.hi, d.half_n, d.n);
+        L.t = angular_axis_nearest(L.B.y, d.lo, d.hi, d.half_n, d.n);
+    } else {
+        L.s = angular_axis_bilinear(L.B.x, d.lo, d.hi, d.half_n, d.n);
+        L.t = angular_axis_bilinear(L.B.y, d.lo, d.hi, d.half_n, d.n);
+    }
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// Texel addressing and decoding.
+// ---------------------------------------------------------------------------
+
+template <int LAYOUT>
+__device__ __forceinline__ int64_t texel_index(const TexDesc& d, int i, int j, int s, int t) {
+    if (LAYOUT == RT_LAYOUT_PLANES)
+        return (int64_t)(t * d.n + s) * d.plane + (int64_t)j * d.W + i;
+    return ((int64_t)j * d.n + t) * ((int64_t)d.W * d.n) + (int64_t)i * d.n + s;
+}
+
+template <int FMT>
+__device__ __forceinline__ float4 load_texel(const void* base, int64_t idx, float scale);
+
+template <>
+__device__ __forceinline__ float4 load_texel<RT_F32>(const void* base, int64_t idx, float) {
+    return __ldg(reinterpret_cast<const float4*>(base) + idx);
+}
+
+template <>
+__device__ __forceinline__ float4 load_texel<RT_F16>(const void* base, int64_t idx, float) {
+    uint2 r = __ldg(reinterpret_cast<const uint2*>(base) + idx);
+    __half2 a = *reinterpret_cast<__half2*>(&r.x);
+    __half2 b = *reinterpret_cast<__half2*>(&r.y);
+    float2 fa = __half22float2(a), fb = __half22float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+template <>
+__device__ __forceinline__ float4 load_texel<RT_BF16>(const void* base, int64_t idx, float) {
+    uint2 r = __ldg(reinterpret_cast<const uint2*>(base) + idx);
+    __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162*>(&r.x);
+    __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162*>(&r.y);
+    float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+__device__ __forceinline__ float2 e4m3x2_to_float2(unsigned short v) {
+    __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)v, __NV_E4M3);
+    __half2 hh = *reinterpret_cast<__half2*>(&h);
+    return __half22float2(hh);
+}
+
+template <>
+__device__ __forceinline__ float4 load_texel<RT_E4M3_BUCKET_SCALE>(const void* base, int64_t idx, float scale) {
+    unsigned r = __ldg(reinterpret_cast<const unsigned*>(base) + idx);
+    float2 a = e4m3x2_to_float2((unsigned short)(r & 0xFFFFu));
+    float2 b = e4m3x2_to_float2((unsigned short)(r >> 16));
+    return make_float4(a.x * scale, a.y * scale, b.x * scale, b.y * scale);
+}
+
+__device__ __forceinline__ float4 lerp4(float4 a, float4 b, float w) {
+    return make_float4(fmaf(w, b.x - a.x, a.x), fmaf(w, b.y - a.y, a.y), fmaf(w, b.z - a.z, a.z),
+                       fmaf(w, b.w - a.w, a.w));
+}
+
+__device__ __forceinline__ float4 sub4(float4 a, float4 b) {
+    return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+
+// Vector reduction of four floats into global memory (one 16-byte atomic).
+__device__ __forceinline__ void red_add_v4(float* addr, float4 v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
+}
+
+}  // namespace rt

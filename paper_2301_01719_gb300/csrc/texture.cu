@@ -1,0 +1,271 @@
+// texture.cu -- texture set-up kernels: encoding, read-back, lobe fill, layout
+// conversion, and the footprint counter used to compute algorithmic bytes.
+#include "rt_device.cuh"
+#include "rt_filter.cuh"
+#include "rt_internal.h"
+
+namespace rt {
+
+constexpr int kThreads = 256;
+
+static inline unsigned blocks_for(int64_t items) { return (unsigned)((items + kThreads - 1) / kThreads); }
+
+// (i, j, s, t) of texel `idx` in the PLANES layout.
+__device__ __forceinline__ void planes_coords(int64_t idx, int W, int H, int n, int& i, int& j, int& s, int& t) {
+    int64_t plane = (int64_t)W * H;
+    int64_t p = idx / plane, r = idx - p * plane;
+    j = (int)(r / W);
+    i = (int)(r - (int64_t)j * W);
+    t = (int)(p / n);
+    s = (int)(p - (int64_t)t * n);
+}
+
+__device__ __forceinline__ int64_t index_in(int layout, int W, int H, int n, int i, int j, int s, int t) {
+    if (layout == RT_LAYOUT_PLANES) return ((int64_t)t * n + s) * ((int64_t)W * H) + (int64_t)j * W + i;
+    return ((int64_t)j * n + t) * ((int64_t)W * n) + (int64_t)i * n + s;
+}
+
+__device__ __forceinline__ uint2 pack_f16(float4 v) {
+    __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+    return make_uint2(*reinterpret_cast<unsigned*>(&a), *reinterpret_cast<unsigned*>(&b));
+}
+
+__device__ __forceinline__ uint2 pack_bf16(float4 v) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    return make_uint2(*reinterpret_cast<unsigned*>(&a), *reinterpret_cast<unsigned*>(&b));
+}
+
+// E4M3 codes of v / scale, round to nearest even with saturation; channel 0 in the low byte.
+__device__ __forceinline__ unsigned pack_e4m3(float4 v, float scale) {
+    float2 lo = make_float2(__fdiv_rn(v.x, scale), __fdiv_rn(v.y, scale));
+    float2 hi = make_float2(__fdiv_rn(v.z, scale), __fdiv_rn(v.w, scale));
+    unsigned a = __nv_cvt_float2_to_fp8x2(lo, __NV_SATFINITE, __NV_E4M3);
+    unsigned b = __nv_cvt_float2_to_fp8x2(hi, __NV_SATFINITE, __NV_E4M3);
+    return (a & 0xFFFFu) | (b << 16);
+}
+
+__device__ __forceinline__ float bucket_scale(float amax) { return amax == 0.0f ? 1.0f : __fdiv_rn(amax, 448.0f); }
+
+__device__ __forceinline__ float amax4(float4 v) {
+    return fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
+}
+
+// FP32 source (any layout) -> FP32 / FP16 / BF16 storage in PLANES, one thread per texel.
+__global__ void encode_elementwise(const float4* __restrict__ src, int src_layout, void* __restrict__ dst, int W,
+                                   int H, int n, int fmt, int64_t total) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    int i, j, s, t;
+    planes_coords(idx, W, H, n, i, j, s, t);
+    float4 v = src[index_in(src_layout, W, H, n, i, j, s, t)];
+    if (fmt == RT_F32)
+        reinterpret_cast<float4*>(dst)[idx] = v;
+    else if (fmt == RT_F16)
+        reinterpret_cast<uint2*>(dst)[idx] = pack_f16(v);
+    else
+        reinterpret_cast<uint2*>(dst)[idx] = pack_bf16(v);
+}
+
+// FP32 source -> E4M3 + per-bucket scale, one thread per bucket (amax pass, then encode pass).
+__global__ void encode_e4m3_buckets(const float4* __restrict__ src, int src_layout, unsigned* __restrict__ dst,
+                                    float* __restrict__ scale, int W, int H, int n) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)W * H) return;
+    int j = (int)(b / W), i = (int)(b - (int64_t)j * W);
+    float amax = 0.0f;
+    for (int t = 0; t < n; ++t)
+        for (int s = 0; s < n; ++s) amax = fmaxf(amax, amax4(src[index_in(src_layout, W, H, n, i, j, s, t)]));
+    float sc = bucket_scale(amax);
+    scale[b] = sc;
+    for (int t = 0; t < n; ++t)
+        for (int s = 0; s < n; ++s)
+            dst[index_in(RT_LAYOUT_PLANES, W, H, n, i, j, s, t)] =
+                pack_e4m3(src[index_in(src_layout, W, H, n, i, j, s, t)], sc);
+}
+
+cudaError_t launch_encode(const float* src, int src_layout, void* dst, float* scale, int W, int H, int n, int fmt,
+                          cudaStream_t stream) {
+    if (fmt == RT_E4M3_BUCKET_SCALE) {
+        int64_t buckets = (int64_t)W * H;
+        encode_e4m3_buckets<<<blocks_for(buckets), kThreads, 0, stream>>>(
+            reinterpret_cast<const float4*>(src), src_layout, reinterpret_cast<unsigned*>(dst), scale, W, H, n);
+    } else {
+        int64_t total = (int64_t)W * H * n * n;
+        encode_elementwise<<<blocks_for(total), kThreads, 0, stream>>>(reinterpret_cast<const float4*>(src),
+                                                                       src_layout, dst, W, H, n, fmt, total);
+    }
+    return cudaGetLastError();
+}
+
+// Stored codes (PLANES) -> codes in dst_layout; T is the per-texel code type.
+template <typename T>
+__global__ void read_codes(const T* __restrict__ src, T* __restrict__ dst, int W, int H, int n, int dst_layout,
+                           int64_t total) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    int i, j, s, t;
+    planes_coords(idx, W, H, n, i, j, s, t);
+    dst[index_in(dst_layout, W, H, n, i, j, s, t)] = src[idx];
+}
+
+cudaError_t launch_read(const void* src, int fmt, int W, int H, int n, int dst_layout, void* dst,
+                        cudaStream_t stream) {
+    int64_t total = (int64_t)W * H * n * n;
+    unsigned g = blocks_for(total);
+    if (fmt == RT_F32)
+        read_codes<float4><<<g, kThreads, 0, stream>>>(reinterpret_cast<const float4*>(src),
+                                                       reinterpret_cast<float4*>(dst), W, H, n, dst_layout, total);
+    else if (fmt == RT_E4M3_BUCKET_SCALE)
+        read_codes<unsigned><<<g, kThreads, 0, stream>>>(reinterpret_cast<const unsigned*>(src),
+                                                         reinterpret_cast<unsigned*>(dst), W, H, n, dst_layout, total);
+    else
+        read_codes<uint2><<<g, kThreads, 0, stream>>>(reinterpret_cast<const uint2*>(src),
+                                                      reinterpret_cast<uint2*>(dst), W, H, n, dst_layout, total);
+    return cudaGetLastError();
+}
+
+// Direction of the centre of texel (s, t): B = ((2s+1)/n - 1, (2t+1)/n - 1),
+// A = Eq. 4a(B) = B max(|B_x|, |B_y|) / |B|, I = Eq. 2c(A) =
+// (A_x sqrt(2 - |A|^2), A_y sqrt(2 - |A|^2), 1 - |A|^2).
+__device__ __forceinline__ float3 texel_centre_direction(int s, int t, int n) {
+    float Bx = (float)(2 * s + 1) / (float)n - 1.0f;
+    float By = (float)(2 * t + 1) / (float)n - 1.0f;
+    float r = sqrtf(Bx * Bx + By * By);
+    float Ax = 0.f, Ay = 0.f;
+    if (r > 0.f) {
+        float k = fmaxf(fabsf(Bx), fabsf(By)) / r;
+        Ax = Bx * k;
+        Ay = By * k;
+    }
+    float a2 = Ax * Ax + Ay * Ay;
+    float q = sqrtf(fmaxf(2.0f - a2, 0.0f));
+    return make_float3(Ax * q, Ay * q, 1.0f - a2);
+}
+
+__device__ __forceinline__ float4 lobe_value(const float* P, float3 I) {
+    float c = I.x * P[3] + I.y * P[4] + I.z * P[5];
+    float l = c > 0.f ? powf(c, P[6]) : 0.f;
+    return make_float4(P[0] * l, P[1] * l, P[2] * l, l);
+}
+
+__global__ void fill_lobes_kernel(const float* __restrict__ params, void* __restrict__ dst, float* __restrict__ scale,
+                                  int W, int H, int n, int fmt) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)W * H) return;
+    int j = (int)(b / W), i = (int)(b - (int64_t)j * W);
+    float P[8];
+    const float4* p4 = reinterpret_cast<const float4*>(params) + 2 * b;
+    float4 a = p4[0], c = p4[1];
+    P[0] = a.x; P[1] = a.y; P[2] = a.z; P[3] = a.w;
+    P[4] = c.x; P[5] = c.y; P[6] = c.z; P[7] = c.w;
+    float sc = 1.0f;
+    if (fmt == RT_E4M3_BUCKET_SCALE) {
+        float amax = 0.f;
+        for (int t = 0; t < n; ++t)
+            for (int s = 0; s < n; ++s) amax = fmaxf(amax, amax4(lobe_value(P, texel_centre_direction(s, t, n))));
+        sc = bucket_scale(amax);
+        scale[b] = sc;
+    }
+    for (int t = 0; t < n; ++t)
+        for (int s = 0; s < n; ++s) {
+            float4 v = lobe_value(P, texel_centre_direction(s, t, n));
+            int64_t idx = index_in(RT_LAYOUT_PLANES, W, H, n, i, j, s, t);
+            if (fmt == RT_F32)
+                reinterpret_cast<float4*>(dst)[idx] = v;
+            else if (fmt == RT_F16)
+                reinterpret_cast<uint2*>(dst)[idx] = pack_f16(v);
+            else if (fmt == RT_BF16)
+                reinterpret_cast<uint2*>(dst)[idx] = pack_bf16(v);
+            else
+                reinterpret_cast<unsigned*>(dst)[idx] = pack_e4m3(v, sc);
+        }
+}
+
+cudaError_t launch_fill_lobes(const float* params, void* dst, float* scale, int W, int H, int n, int fmt,
+                              cudaStream_t stream) {
+    int64_t buckets = (int64_t)W * H;
+    fill_lobes_kernel<<<blocks_for(buckets), kThreads, 0, stream>>>(params, dst, scale, W, H, n, fmt);
+    return cudaGetLastError();
+}
+
+__global__ void convert_kernel(const float4* __restrict__ src, int src_layout, float4* __restrict__ dst,
+                               int dst_layout, int W, int H, int n, int64_t total) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    int i, j, s, t;
+    planes_coords(idx, W, H, n, i, j, s, t);
+    dst[index_in(dst_layout, W, H, n, i, j, s, t)] = src[index_in(src_layout, W, H, n, i, j, s, t)];
+}
+
+cudaError_t launch_convert(const float* src, int src_layout, float* dst, int dst_layout, int W, int H, int n,
+                           cudaStream_t stream) {
+    int64_t total = (int64_t)W * H * n * n;
+    convert_kernel<<<blocks_for(total), kThreads, 0, stream>>>(reinterpret_cast<const float4*>(src), src_layout,
+                                                               reinterpret_cast<float4*>(dst), dst_layout, W, H, n,
+                                                               total);
+    return cudaGetLastError();
+}
+
+// Footprint: one bit per texel of every object (PLANES numbering), set for
+// every tap the forward kernel reads.
+template <int FILTER>
+__global__ void __launch_bounds__(kThreads) footprint_kernel(const TexDesc* __restrict__ table, int n_obj,
+                                                            const float* __restrict__ uv,
+                                                            const float* __restrict__ dir,
+                                                            const int32_t* __restrict__ obj, int64_t F,
+                                                            uint32_t* __restrict__ bitmap,
+                                                            const int64_t* __restrict__ word_offset,
+                                                            unsigned* status) {
+    __shared__ GStage<kThreads> S;
+    const Frag q = stage_gbuffer<kThreads>(uv, dir, obj, F, S);
+    const int64_t f = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (f >= F) return;
+    TexDesc d;
+    if (!fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d)) return;
+    Lookup<FILTER> L = locate<FILTER>(d, q.u, q.v, q.x, q.y, q.z);
+    const int64_t base = word_offset[q.o] * 32;
+    const int nu = FILTER == RT_QUADRILINEAR ? 2 : 1;
+    const int ns = FILTER == RT_NEAREST ? 1 : 2;
+    for (int b = 0; b < nu; ++b)
+        for (int a = 0; a < nu; ++a)
+            for (int t = 0; t < ns; ++t)
+                for (int p = 0; p < ns; ++p) {
+                    int64_t bit = base + texel_index<RT_LAYOUT_PLANES>(d, a ? L.u.k1 : L.u.k0, b ? L.v.k1 : L.v.k0,
+                                                                       p ? L.s.k1 : L.s.k0, t ? L.t.k1 : L.t.k0);
+                    atomicOr(bitmap + (bit >> 5), 1u << (bit & 31));
+                }
+}
+
+cudaError_t launch_footprint_mark(const TexDesc* table, int n_obj, const float* uv, const float* dir,
+                                  const int32_t* obj, int64_t F, int filter, uint32_t* bitmap,
+                                  const int64_t* word_offset, unsigned* status, cudaStream_t stream) {
+    unsigned grid = blocks_for(F);
+    if (filter == RT_NEAREST)
+        footprint_kernel<RT_NEAREST><<<grid, kThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, bitmap,
+                                                                    word_offset, status);
+    else if (filter == RT_ANGULAR_BILINEAR)
+        footprint_kernel<RT_ANGULAR_BILINEAR><<<grid, kThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, bitmap,
+                                                                             word_offset, status);
+    else
+        footprint_kernel<RT_QUADRILINEAR><<<grid, kThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, bitmap,
+                                                                         word_offset, status);
+    return cudaGetLastError();
+}
+
+__global__ void popcount_kernel(const uint32_t* __restrict__ bitmap, int64_t words, unsigned long long* count) {
+    unsigned long long local = 0;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x)
+        local += __popc(bitmap[w]);
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xFFFFFFFFu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
+}
+
+cudaError_t launch_popcount(const uint32_t* bitmap, int64_t words, unsigned long long* count, cudaStream_t stream) {
+    if (words <= 0) return cudaSuccess;
+    int64_t b = (words + kThreads - 1) / kThreads;
+    unsigned grid = (unsigned)(b < 4096 ? b : 4096);
+    popcount_kernel<<<grid, kThreads, 0, stream>>>(bitmap, words, count);
+    return cudaGetLastError();
+}
+
+}  // namespace rt

@@ -7,6 +7,8 @@ and the id of the object hit (-1 for a miss, whose UV and direction are 0).
 """
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass
 
 import numpy as np
@@ -147,7 +149,8 @@ def sphere_plane_poses(seed: int, views: int = 60, radius: float = 3.5, step_deg
 
 def sphere_plane_scene(seed: int, views: int = 60, width: int = 1920, height: int = 1080, fov_deg: float = 60.0,
                        plane_half: float = 4.0, view_range: tuple[int, int] | None = None,
-                       out: tuple[np.ndarray, np.ndarray, np.ndarray] | None = None) -> GBuffer:
+                       out: tuple[np.ndarray, np.ndarray, np.ndarray] | None = None,
+                       threads: int | None = None) -> GBuffer:
     """Unit sphere (id 0) plus ground plane (id 1) from `views` orbit poses,
     stacked view-major (view, row, column).  view_range selects a contiguous
     subset of the poses (for sharding across ranks); `out` supplies the
@@ -162,9 +165,18 @@ def sphere_plane_scene(seed: int, views: int = 60, width: int = 1920, height: in
         obj = np.empty(F, dtype=np.int32)
     else:
         uv, d, obj = out
-    for k, v in enumerate(range(lo, hi)):
+    def one(k):
         sl = slice(k * per, (k + 1) * per)
-        _sphere_plane_view(eyes[v], width, height, fov_deg, plane_half, uv[sl], d[sl], obj[sl])
+        _sphere_plane_view(eyes[lo + k], width, height, fov_deg, plane_half, uv[sl], d[sl], obj[sl])
+
+    # numpy releases the GIL inside large array operations, so views render in parallel threads
+    workers = max(1, min(hi - lo, threads or (os.cpu_count() or 1)))
+    if workers == 1:
+        for k in range(hi - lo):
+            one(k)
+    else:
+        with ThreadPoolExecutor(workers) as ex:
+            list(ex.map(one, range(hi - lo)))
     return GBuffer(uv, d, obj, width, height, hi - lo)
 
 
