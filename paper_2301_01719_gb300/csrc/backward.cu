@@ -6,6 +6,7 @@
 // one per tap of non-zero weight.  UV and direction gradients follow the chain
 // rule through the nested lerps, the Note's clamp (zero derivative where a
 // coordinate is clamped), Eq. 3 and Eq. 1b.
+#include "launch.h"
 #include "rt_device.cuh"
 #include "rt_filter.cuh"
 #include "rt_internal.h"
@@ -13,6 +14,10 @@
 namespace rt {
 
 constexpr int kBackThreads = 256;
+constexpr int kBackWarps = kBackThreads / 32;
+#ifndef RT_BACK_MIN_BLOCKS
+#define RT_BACK_MIN_BLOCKS 1
+#endif
 
 struct CoordGrad {
     float gu, gv, gs, gt;  // dL/d(weight coordinate) of the u, v, s, t axes
@@ -117,75 +122,80 @@ __device__ __forceinline__ float3 direction_grad(float Ix, float Iy, float Iz, f
 }
 
 template <int FILTER>
-__global__ void __launch_bounds__(kBackThreads) backward_kernel(
+__global__ void __launch_bounds__(kBackThreads, RT_BACK_MIN_BLOCKS) backward_kernel(
     const TexDesc* __restrict__ table, int n_obj, const float* __restrict__ uv, const float* __restrict__ dir,
     const int32_t* __restrict__ obj, int64_t F, const float* __restrict__ dL_dout, const __grid_constant__ GradTable grads,
     bool any_grad, float* __restrict__ dL_duv, float* __restrict__ dL_ddir, bool accumulate, unsigned* status) {
-    __shared__ GStage<kBackThreads> S;
-    const Frag q = stage_gbuffer<kBackThreads>(uv, dir, obj, F, S);
-    const int64_t f = (int64_t)blockIdx.x * kBackThreads + threadIdx.x;
-    if (f >= F) return;
+    __shared__ WarpStage<true> stages[kBackWarps];
     const bool coord_grads = (dL_duv != nullptr) || (dL_ddir != nullptr);
-    float2 guv = make_float2(0.f, 0.f);
-    float3 gdir = make_float3(0.f, 0.f, 0.f);
-    TexDesc d;
-    if (fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d)) {
-        const float4 go = __ldcs(reinterpret_cast<const float4*>(dL_dout) + f);
-        Lookup<FILTER> L = locate<FILTER>(d, q.u, q.v, q.x, q.y, q.z);
-        float* grad = any_grad ? grads.p[q.o] : nullptr;
-        CoordGrad cg = backward_any<FILTER>(d, L, go, grad, coord_grads);
-        if (FILTER == RT_QUADRILINEAR) {
-            float cu = fmaf(q.u, d.fW, -0.5f), cv = fmaf(q.v, d.fH, -0.5f);
-            guv.x = (cu > -1.0f && cu < d.fW) ? cg.gu * d.fW : 0.f;
-            guv.y = (cv > -1.0f && cv < d.fH) ? cg.gv * d.fH : 0.f;
+    for_each_fragment<kBackWarps, true>(uv, dir, obj, dL_dout, F, stages, [&](int64_t f, const Frag& q, float4 go) {
+        float2 guv = make_float2(0.f, 0.f);
+        float3 gdir = make_float3(0.f, 0.f, 0.f);
+        TexDesc d;
+        if (fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d)) {
+            Lookup<FILTER> L = locate<FILTER>(d, q.u, q.v, q.x, q.y, q.z);
+            float* grad = any_grad ? grads.p[q.o] : nullptr;
+            CoordGrad cg = backward_any<FILTER>(d, L, go, grad, coord_grads);
+            if (FILTER == RT_QUADRILINEAR) {
+                float cu = fmaf(q.u, d.fW, -0.5f), cv = fmaf(q.v, d.fH, -0.5f);
+                guv.x = (cu > -1.0f && cu < d.fW) ? cg.gu * d.fW : 0.f;
+                guv.y = (cv > -1.0f && cv < d.fH) ? cg.gv * d.fH : 0.f;
+            }
+            if (FILTER != RT_NEAREST && dL_ddir) {
+                float gBx = (L.B.x > d.lo && L.B.x < d.hi) ? cg.gs * d.half_n : 0.f;
+                float gBy = (L.B.y > d.lo && L.B.y < d.hi) ? cg.gt * d.half_n : 0.f;
+                gdir = direction_grad(q.x, q.y, q.z, gBx, gBy);
+            }
         }
-        if (FILTER != RT_NEAREST && dL_ddir) {
-            float gBx = (L.B.x > d.lo && L.B.x < d.hi) ? cg.gs * d.half_n : 0.f;
-            float gBy = (L.B.y > d.lo && L.B.y < d.hi) ? cg.gt * d.half_n : 0.f;
-            gdir = direction_grad(q.x, q.y, q.z, gBx, gBy);
+        if (f >= F) return;
+        if (dL_duv) {
+            float2* p = reinterpret_cast<float2*>(dL_duv) + f;
+            if (accumulate) {
+                float2 o = *p;
+                guv.x += o.x;
+                guv.y += o.y;
+            }
+            *p = guv;
         }
-    }
-    if (dL_duv) {
-        float2* p = reinterpret_cast<float2*>(dL_duv) + f;
-        if (accumulate) {
-            float2 o = *p;
-            guv.x += o.x;
-            guv.y += o.y;
+        if (dL_ddir) {
+            float* p = dL_ddir + 3 * f;
+            if (accumulate) {
+                gdir.x += p[0];
+                gdir.y += p[1];
+                gdir.z += p[2];
+            }
+            p[0] = gdir.x;
+            p[1] = gdir.y;
+            p[2] = gdir.z;
         }
-        *p = guv;
-    }
-    if (dL_ddir) {
-        float* p = dL_ddir + 3 * f;
-        if (accumulate) {
-            gdir.x += p[0];
-            gdir.y += p[1];
-            gdir.z += p[2];
-        }
-        p[0] = gdir.x;
-        p[1] = gdir.y;
-        p[2] = gdir.z;
-    }
+    });
+}
+
+template <int FILTER>
+static cudaError_t launch_backward_t(const TexDesc* table, int n_obj, const float* uv, const float* dir,
+                                     const int32_t* obj, int64_t F, const float* dL_dout, const GradTable& grads,
+                                     bool any_grad, float* dL_duv, float* dL_ddir, bool accumulate, unsigned* status,
+                                     cudaStream_t stream) {
+    const unsigned grid = persistent_grid(backward_kernel<FILTER>, kBackThreads, (F + kChunk - 1) / kChunk);
+    backward_kernel<FILTER><<<grid, kBackThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, dL_dout, grads,
+                                                               any_grad, dL_duv, dL_ddir, accumulate, status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_backward(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
                             int64_t F, int filter, const float* dL_dout, const GradTable& grads, bool any_grad,
                             float* dL_duv, float* dL_ddir, bool accumulate, unsigned* status, cudaStream_t stream) {
-    dim3 grid((unsigned)((F + kBackThreads - 1) / kBackThreads)), block(kBackThreads);
     switch (filter) {
         case RT_NEAREST:
-            backward_kernel<RT_NEAREST><<<grid, block, 0, stream>>>(table, n_obj, uv, dir, obj, F, dL_dout, grads,
-                                                                    any_grad, dL_duv, dL_ddir, accumulate, status);
-            break;
+            return launch_backward_t<RT_NEAREST>(table, n_obj, uv, dir, obj, F, dL_dout, grads, any_grad, dL_duv,
+                                                 dL_ddir, accumulate, status, stream);
         case RT_ANGULAR_BILINEAR:
-            backward_kernel<RT_ANGULAR_BILINEAR><<<grid, block, 0, stream>>>(
-                table, n_obj, uv, dir, obj, F, dL_dout, grads, any_grad, dL_duv, dL_ddir, accumulate, status);
-            break;
+            return launch_backward_t<RT_ANGULAR_BILINEAR>(table, n_obj, uv, dir, obj, F, dL_dout, grads, any_grad,
+                                                          dL_duv, dL_ddir, accumulate, status, stream);
         default:
-            backward_kernel<RT_QUADRILINEAR><<<grid, block, 0, stream>>>(
-                table, n_obj, uv, dir, obj, F, dL_dout, grads, any_grad, dL_duv, dL_ddir, accumulate, status);
-            break;
+            return launch_backward_t<RT_QUADRILINEAR>(table, n_obj, uv, dir, obj, F, dL_dout, grads, any_grad,
+                                                      dL_duv, dL_ddir, accumulate, status, stream);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace rt

@@ -73,17 +73,22 @@ __device__ __forceinline__ float4 filter_any(const TexDesc& d, const Lookup<FILT
     }
 }
 
-// G-buffer staging: a block of BLOCK threads shades BLOCK consecutive
-// fragments.  The block reads its slice of uv (BLOCK x 8 bytes), dir (BLOCK x
-// 12 bytes) and obj (BLOCK x 4 bytes) with 16-byte vector loads into shared
-// memory, then each thread takes one fragment.  The G-buffer is read once, so
-// the loads ask for early eviction (ld.global.cs) and leave the caches to the
-// texels.  Fragments past F are background.
-template <int BLOCK>
-struct GStage {
-    float uv[2 * BLOCK];
-    float dir[3 * BLOCK];
-    int obj[BLOCK];
+// G-buffer staging.  Kernels that walk fragments are persistent: each warp
+// takes 32-fragment chunks c, c + (warps in the grid), ...  and double-buffers
+// them in its own slice of shared memory.  While the warp filters chunk c, the
+// G-buffer of its next chunk (uv 256 B, dir 384 B, obj 128 B, and optionally a
+// 16-byte-per-fragment extra stream such as dL/dout) is already in flight with
+// 16-byte cp.async copies that bypass L1 -- so the DRAM latency of the
+// G-buffer overlaps the texel gather, and no block-wide barrier is needed.
+// Only __syncwarp orders the warp's own copies and reads.
+constexpr int kChunk = 32;
+
+template <bool EXTRA>
+struct WarpStage {
+    float uv[2][2 * kChunk];
+    float dir[2][3 * kChunk];
+    int obj[2][kChunk];
+    float4 extra[EXTRA ? 2 : 1][EXTRA ? kChunk : 1];
 };
 
 struct Frag {
@@ -91,34 +96,83 @@ struct Frag {
     int o;
 };
 
-template <int BLOCK>
-__device__ __forceinline__ Frag stage_gbuffer(const float* __restrict__ uv, const float* __restrict__ dir,
-                                              const int32_t* __restrict__ obj, int64_t F, GStage<BLOCK>& S) {
-    const int64_t f0 = (int64_t)blockIdx.x * BLOCK;
-    const int tid = threadIdx.x;
-    if (f0 + BLOCK <= F) {
-        const float4* uv4 = reinterpret_cast<const float4*>(uv + 2 * f0);
-        const float4* d4 = reinterpret_cast<const float4*>(dir + 3 * f0);
-        const int4* o4 = reinterpret_cast<const int4*>(obj + f0);
-        for (int k = tid; k < BLOCK / 2; k += BLOCK) reinterpret_cast<float4*>(S.uv)[k] = __ldcs(uv4 + k);
-        for (int k = tid; k < 3 * BLOCK / 4; k += BLOCK) reinterpret_cast<float4*>(S.dir)[k] = __ldcs(d4 + k);
-        for (int k = tid; k < BLOCK / 4; k += BLOCK) reinterpret_cast<int4*>(S.obj)[k] = __ldcs(o4 + k);
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Issues the copies of chunk `c` into buffer `b` (a partial last chunk is read
+// with plain bounded loads instead; fragments past F become background).
+template <bool EXTRA>
+__device__ __forceinline__ void stage_chunk(const float* __restrict__ uv, const float* __restrict__ dir,
+                                            const int32_t* __restrict__ obj, const float* __restrict__ extra,
+                                            int64_t F, int64_t c, int b, WarpStage<EXTRA>& S, int lane) {
+    const int64_t f0 = c * kChunk;
+    if (f0 + kChunk <= F) {
+        // 16 + 24 + 8 (+ 32) sixteen-byte pieces spread over the 32 lanes
+        if (lane < 16) cp_async16(&S.uv[b][4 * lane], uv + 2 * f0 + 4 * lane);
+        if (lane < 24) cp_async16(&S.dir[b][4 * lane], dir + 3 * f0 + 4 * lane);
+        if (lane < 8) cp_async16(&S.obj[b][4 * lane], obj + f0 + 4 * lane);
+        if (EXTRA) cp_async16(&S.extra[b][lane], extra + 4 * (f0 + lane));
     } else {
         const int count = (int)(F - f0);
-        for (int k = tid; k < 2 * BLOCK; k += BLOCK) S.uv[k] = k < 2 * count ? uv[2 * f0 + k] : 0.f;
-        for (int k = tid; k < 3 * BLOCK; k += BLOCK) S.dir[k] = k < 3 * count ? dir[3 * f0 + k] : 0.f;
-        for (int k = tid; k < BLOCK; k += BLOCK) S.obj[k] = k < count ? obj[f0 + k] : -1;
+        for (int k = lane; k < 2 * kChunk; k += 32) S.uv[b][k] = k < 2 * count ? uv[2 * f0 + k] : 0.f;
+        for (int k = lane; k < 3 * kChunk; k += 32) S.dir[b][k] = k < 3 * count ? dir[3 * f0 + k] : 0.f;
+        S.obj[b][lane] = lane < count ? obj[f0 + lane] : -1;
+        if (EXTRA)
+            S.extra[b][lane] = lane < count ? reinterpret_cast<const float4*>(extra)[f0 + lane]
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    __syncthreads();
+}
+
+template <bool EXTRA>
+__device__ __forceinline__ Frag read_frag(const WarpStage<EXTRA>& S, int b, int lane) {
     Frag r;
-    float2 q = reinterpret_cast<const float2*>(S.uv)[tid];
+    float2 q = reinterpret_cast<const float2*>(S.uv[b])[lane];
     r.u = q.x;
     r.v = q.y;
-    r.x = S.dir[3 * tid];
-    r.y = S.dir[3 * tid + 1];
-    r.z = S.dir[3 * tid + 2];
-    r.o = S.obj[tid];
+    r.x = S.dir[b][3 * lane];
+    r.y = S.dir[b][3 * lane + 1];
+    r.z = S.dir[b][3 * lane + 2];
+    r.o = S.obj[b][lane];
     return r;
+}
+
+// Runs body(f, frag, extra) with all 32 lanes of the warp, one fragment per
+// lane, persistent over the grid, with the G-buffer of the next chunk
+// prefetched.  Lanes past F get a background fragment and f >= F: the body
+// must not store for them.  WARPS = warps per block; the block's shared memory
+// holds WARPS stages.
+template <int WARPS, bool EXTRA, typename Body>
+__device__ __forceinline__ void for_each_fragment(const float* __restrict__ uv, const float* __restrict__ dir,
+                                                  const int32_t* __restrict__ obj, const float* __restrict__ extra,
+                                                  int64_t F, WarpStage<EXTRA>* stages, Body body) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    WarpStage<EXTRA>& S = stages[w];
+    const int64_t nchunks = (F + kChunk - 1) / kChunk;
+    const int64_t step = (int64_t)gridDim.x * WARPS;
+    int64_t c = (int64_t)blockIdx.x * WARPS + w;
+    int b = 0;
+    if (c < nchunks) stage_chunk<EXTRA>(uv, dir, obj, extra, F, c, 0, S, lane);
+    cp_async_commit();
+    for (; c < nchunks; c += step, b ^= 1) {
+        const int64_t next = c + step;
+        if (next < nchunks) stage_chunk<EXTRA>(uv, dir, obj, extra, F, next, b ^ 1, S, lane);
+        cp_async_commit();
+        cp_async_wait<1>();  // chunk c has landed (the newest group may still be in flight)
+        __syncwarp();
+        const Frag q = read_frag<EXTRA>(S, b, lane);
+        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (EXTRA) e = S.extra[EXTRA ? b : 0][EXTRA ? lane : 0];
+        __syncwarp();  // every lane has read buffer b before it is refilled
+        body(c * kChunk + lane, q, e);
+    }
+    cp_async_wait<0>();
 }
 
 // Validity of one fragment: 1 = shade it, 0 = background or invalid (status

@@ -1,11 +1,12 @@
 // shade.cu -- forward synthesis and lookup-coordinate kernels.
 //
-// One thread shades one fragment; each block stages its slice of the G-buffer
-// through shared memory with 16-byte vector loads, and every thread writes its
-// colour with one 16-byte store.  Texels are gathered through the
-// read-only path; consecutive fragments of a scanline fall in neighbouring
-// buckets, and in the PLANES layout neighbouring buckets at one in-bucket
-// texel are neighbours in memory, so a warp's taps share cache lines.
+// Persistent kernels: every warp walks 32-fragment chunks with the G-buffer of
+// its next chunk prefetched into shared memory (rt_filter.cuh), one fragment
+// per lane, and writes its colour with one 16-byte store.  Texels are gathered
+// through the read-only path; consecutive fragments of a scanline fall in
+// neighbouring buckets, and in the PLANES layout neighbouring buckets at one
+// in-bucket texel are neighbours in memory, so a warp's taps share cache lines.
+#include "launch.h"
 #include "rt_device.cuh"
 #include "rt_filter.cuh"
 #include "rt_internal.h"
@@ -13,24 +14,28 @@
 namespace rt {
 
 constexpr int kShadeThreads = 256;
+constexpr int kShadeWarps = kShadeThreads / 32;
+#ifndef RT_SHADE_MIN_BLOCKS
+#define RT_SHADE_MIN_BLOCKS 1
+#endif
 
 template <int FILTER>
-__global__ void __launch_bounds__(kShadeThreads) shade_kernel(const TexDesc* __restrict__ table, int n_obj,
+__global__ void __launch_bounds__(kShadeThreads, RT_SHADE_MIN_BLOCKS) shade_kernel(const TexDesc* __restrict__ table, int n_obj,
                                                               const float* __restrict__ uv,
                                                               const float* __restrict__ dir,
                                                               const int32_t* __restrict__ obj, int64_t F,
                                                               float* __restrict__ out, unsigned* status) {
-    __shared__ GStage<kShadeThreads> S;
-    const Frag q = stage_gbuffer<kShadeThreads>(uv, dir, obj, F, S);
-    const int64_t f = (int64_t)blockIdx.x * kShadeThreads + threadIdx.x;
-    if (f >= F) return;
-    float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
-    TexDesc d;
-    if (fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d)) {
-        Lookup<FILTER> L = locate<FILTER>(d, q.u, q.v, q.x, q.y, q.z);
-        res = filter_any<FILTER>(d, L);
-    }
-    __stcs(reinterpret_cast<float4*>(out) + f, res);
+    __shared__ WarpStage<false> stages[kShadeWarps];
+    for_each_fragment<kShadeWarps, false>(uv, dir, obj, nullptr, F, stages,
+                                          [&](int64_t f, const Frag& q, float4) {
+        float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
+        TexDesc d;
+        if (fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d)) {
+            Lookup<FILTER> L = locate<FILTER>(d, q.u, q.v, q.x, q.y, q.z);
+            res = filter_any<FILTER>(d, L);
+        }
+        if (f < F) __stcs(reinterpret_cast<float4*>(out) + f, res);
+    });
 }
 
 template <int FILTER>
@@ -40,59 +45,63 @@ __global__ void __launch_bounds__(kShadeThreads) locate_kernel(const TexDesc* __
                                                                const int32_t* __restrict__ obj, int64_t F,
                                                                int32_t* __restrict__ idx, float* __restrict__ coord,
                                                                unsigned* status) {
-    __shared__ GStage<kShadeThreads> S;
-    const Frag q = stage_gbuffer<kShadeThreads>(uv, dir, obj, F, S);
-    const int64_t f = (int64_t)blockIdx.x * kShadeThreads + threadIdx.x;
-    if (f >= F) return;
-    int4 I = make_int4(0, 0, 0, 0);
-    float4 C = make_float4(0.f, 0.f, 0.f, 0.f);
-    TexDesc d;
-    if (fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d)) {
-        Lookup<FILTER> L = locate<FILTER>(d, q.u, q.v, q.x, q.y, q.z);
-        I = make_int4(L.u.fl, L.v.fl, L.s.fl, L.t.fl);
-        C = make_float4(L.u.c, L.v.c, L.s.c, L.t.c);
-    }
-    reinterpret_cast<int4*>(idx)[f] = I;
-    reinterpret_cast<float4*>(coord)[f] = C;
+    __shared__ WarpStage<false> stages[kShadeWarps];
+    for_each_fragment<kShadeWarps, false>(uv, dir, obj, nullptr, F, stages,
+                                          [&](int64_t f, const Frag& q, float4) {
+        int4 I = make_int4(0, 0, 0, 0);
+        float4 C = make_float4(0.f, 0.f, 0.f, 0.f);
+        TexDesc d;
+        if (fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d)) {
+            Lookup<FILTER> L = locate<FILTER>(d, q.u, q.v, q.x, q.y, q.z);
+            I = make_int4(L.u.fl, L.v.fl, L.s.fl, L.t.fl);
+            C = make_float4(L.u.c, L.v.c, L.s.c, L.t.c);
+        }
+        if (f < F) {
+            reinterpret_cast<int4*>(idx)[f] = I;
+            reinterpret_cast<float4*>(coord)[f] = C;
+        }
+    });
 }
 
-static inline unsigned grid_for(int64_t F) { return (unsigned)((F + kShadeThreads - 1) / kShadeThreads); }
+template <int FILTER>
+static cudaError_t launch_shade_t(const TexDesc* table, int n_obj, const float* uv, const float* dir,
+                                  const int32_t* obj, int64_t F, float* out, unsigned* status, cudaStream_t stream) {
+    const unsigned grid = persistent_grid(shade_kernel<FILTER>, kShadeThreads, (F + kChunk - 1) / kChunk);
+    shade_kernel<FILTER><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, out, status);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_shade(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
                          int64_t F, int filter, float* out, unsigned* status, cudaStream_t stream) {
-    dim3 grid(grid_for(F)), block(kShadeThreads);
     switch (filter) {
         case RT_NEAREST:
-            shade_kernel<RT_NEAREST><<<grid, block, 0, stream>>>(table, n_obj, uv, dir, obj, F, out, status);
-            break;
+            return launch_shade_t<RT_NEAREST>(table, n_obj, uv, dir, obj, F, out, status, stream);
         case RT_ANGULAR_BILINEAR:
-            shade_kernel<RT_ANGULAR_BILINEAR><<<grid, block, 0, stream>>>(table, n_obj, uv, dir, obj, F, out,
-                                                                          status);
-            break;
+            return launch_shade_t<RT_ANGULAR_BILINEAR>(table, n_obj, uv, dir, obj, F, out, status, stream);
         default:
-            shade_kernel<RT_QUADRILINEAR><<<grid, block, 0, stream>>>(table, n_obj, uv, dir, obj, F, out, status);
-            break;
+            return launch_shade_t<RT_QUADRILINEAR>(table, n_obj, uv, dir, obj, F, out, status, stream);
     }
+}
+
+template <int FILTER>
+static cudaError_t launch_locate_t(const TexDesc* table, int n_obj, const float* uv, const float* dir,
+                                   const int32_t* obj, int64_t F, int32_t* idx, float* coord, unsigned* status,
+                                   cudaStream_t stream) {
+    const unsigned grid = persistent_grid(locate_kernel<FILTER>, kShadeThreads, (F + kChunk - 1) / kChunk);
+    locate_kernel<FILTER><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, idx, coord, status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_locate(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
                           int64_t F, int filter, int32_t* idx, float* coord, unsigned* status, cudaStream_t stream) {
-    dim3 grid(grid_for(F)), block(kShadeThreads);
     switch (filter) {
         case RT_NEAREST:
-            locate_kernel<RT_NEAREST><<<grid, block, 0, stream>>>(table, n_obj, uv, dir, obj, F, idx, coord, status);
-            break;
+            return launch_locate_t<RT_NEAREST>(table, n_obj, uv, dir, obj, F, idx, coord, status, stream);
         case RT_ANGULAR_BILINEAR:
-            locate_kernel<RT_ANGULAR_BILINEAR><<<grid, block, 0, stream>>>(table, n_obj, uv, dir, obj, F, idx,
-                                                                           coord, status);
-            break;
+            return launch_locate_t<RT_ANGULAR_BILINEAR>(table, n_obj, uv, dir, obj, F, idx, coord, status, stream);
         default:
-            locate_kernel<RT_QUADRILINEAR><<<grid, block, 0, stream>>>(table, n_obj, uv, dir, obj, F, idx, coord,
-                                                                       status);
-            break;
+            return launch_locate_t<RT_QUADRILINEAR>(table, n_obj, uv, dir, obj, F, idx, coord, status, stream);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace rt

@@ -1,5 +1,6 @@
 // texture.cu -- texture set-up kernels: encoding, read-back, lobe fill, layout
 // conversion, and the footprint counter used to compute algorithmic bytes.
+#include "launch.h"
 #include "rt_device.cuh"
 #include "rt_filter.cuh"
 #include "rt_internal.h"
@@ -216,40 +217,45 @@ __global__ void __launch_bounds__(kThreads) footprint_kernel(const TexDesc* __re
                                                             uint32_t* __restrict__ bitmap,
                                                             const int64_t* __restrict__ word_offset,
                                                             unsigned* status) {
-    __shared__ GStage<kThreads> S;
-    const Frag q = stage_gbuffer<kThreads>(uv, dir, obj, F, S);
-    const int64_t f = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (f >= F) return;
-    TexDesc d;
-    if (!fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d)) return;
-    Lookup<FILTER> L = locate<FILTER>(d, q.u, q.v, q.x, q.y, q.z);
-    const int64_t base = word_offset[q.o] * 32;
-    const int nu = FILTER == RT_QUADRILINEAR ? 2 : 1;
-    const int ns = FILTER == RT_NEAREST ? 1 : 2;
-    for (int b = 0; b < nu; ++b)
-        for (int a = 0; a < nu; ++a)
-            for (int t = 0; t < ns; ++t)
-                for (int p = 0; p < ns; ++p) {
-                    int64_t bit = base + texel_index<RT_LAYOUT_PLANES>(d, a ? L.u.k1 : L.u.k0, b ? L.v.k1 : L.v.k0,
-                                                                       p ? L.s.k1 : L.s.k0, t ? L.t.k1 : L.t.k0);
-                    atomicOr(bitmap + (bit >> 5), 1u << (bit & 31));
-                }
+    __shared__ WarpStage<false> stages[kThreads / 32];
+    for_each_fragment<kThreads / 32, false>(uv, dir, obj, nullptr, F, stages, [&](int64_t, const Frag& q, float4) {
+        TexDesc d;
+        if (!fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d)) return;
+        Lookup<FILTER> L = locate<FILTER>(d, q.u, q.v, q.x, q.y, q.z);
+        const int64_t base = word_offset[q.o] * 32;
+        const int nu = FILTER == RT_QUADRILINEAR ? 2 : 1;
+        const int ns = FILTER == RT_NEAREST ? 1 : 2;
+        for (int b = 0; b < nu; ++b)
+            for (int a = 0; a < nu; ++a)
+                for (int t = 0; t < ns; ++t)
+                    for (int p = 0; p < ns; ++p) {
+                        int64_t bit = base + texel_index<RT_LAYOUT_PLANES>(d, a ? L.u.k1 : L.u.k0,
+                                                                           b ? L.v.k1 : L.v.k0, p ? L.s.k1 : L.s.k0,
+                                                                           t ? L.t.k1 : L.t.k0);
+                        atomicOr(bitmap + (bit >> 5), 1u << (bit & 31));
+                    }
+    });
+}
+
+template <int FILTER>
+static cudaError_t launch_footprint_t(const TexDesc* table, int n_obj, const float* uv, const float* dir,
+                                      const int32_t* obj, int64_t F, uint32_t* bitmap, const int64_t* word_offset,
+                                      unsigned* status, cudaStream_t stream) {
+    const unsigned grid = persistent_grid(footprint_kernel<FILTER>, kThreads, (F + kChunk - 1) / kChunk);
+    footprint_kernel<FILTER><<<grid, kThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, bitmap, word_offset,
+                                                            status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_footprint_mark(const TexDesc* table, int n_obj, const float* uv, const float* dir,
                                   const int32_t* obj, int64_t F, int filter, uint32_t* bitmap,
                                   const int64_t* word_offset, unsigned* status, cudaStream_t stream) {
-    unsigned grid = blocks_for(F);
     if (filter == RT_NEAREST)
-        footprint_kernel<RT_NEAREST><<<grid, kThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, bitmap,
-                                                                    word_offset, status);
-    else if (filter == RT_ANGULAR_BILINEAR)
-        footprint_kernel<RT_ANGULAR_BILINEAR><<<grid, kThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, bitmap,
-                                                                             word_offset, status);
-    else
-        footprint_kernel<RT_QUADRILINEAR><<<grid, kThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, bitmap,
-                                                                         word_offset, status);
-    return cudaGetLastError();
+        return launch_footprint_t<RT_NEAREST>(table, n_obj, uv, dir, obj, F, bitmap, word_offset, status, stream);
+    if (filter == RT_ANGULAR_BILINEAR)
+        return launch_footprint_t<RT_ANGULAR_BILINEAR>(table, n_obj, uv, dir, obj, F, bitmap, word_offset, status,
+                                                       stream);
+    return launch_footprint_t<RT_QUADRILINEAR>(table, n_obj, uv, dir, obj, F, bitmap, word_offset, status, stream);
 }
 
 __global__ void popcount_kernel(const uint32_t* __restrict__ bitmap, int64_t words, unsigned long long* count) {
