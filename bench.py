@@ -311,9 +311,10 @@ def run_radtex(a):
     g = synth.sphere_plane_scene(SCENE_SEED + rank, views=a.views, width=a.width, height=a.height,
                                  out=(h_uv.numpy(), h_dir.numpy(), h_obj.numpy()))
     scene_s = time.perf_counter() - t0
-    uv = h_uv.to(dev)
-    dirs = h_dir.to(dev)
-    obj = h_obj.to(dev)
+    shape = (a.views, a.height, a.width)
+    uv = h_uv.to(dev).view(*shape, 2)
+    dirs = h_dir.to(dev).view(*shape, 3)
+    obj = h_obj.to(dev).view(*shape)
 
     ctx = api.Context(local)
     oids = []
@@ -323,16 +324,16 @@ def run_radtex(a):
         api.rt_fill_bucket_lobes(ctx, oid, params)
         oids.append(oid)
     torch.cuda.synchronize()
-    out = torch.empty((F, 4), dtype=torch.float32, device=dev)
-    duv = torch.empty((F, 2), dtype=torch.float32, device=dev)
-    ddir = torch.empty((F, 3), dtype=torch.float32, device=dev)
+    out = torch.empty((*shape, 4), dtype=torch.float32, device=dev)
+    duv = torch.empty((*shape, 2), dtype=torch.float32, device=dev)
+    ddir = torch.empty((*shape, 3), dtype=torch.float32, device=dev)
     dtex = {o: torch.empty((a.n, a.n, a.buckets, a.buckets, 4), dtype=torch.float32, device=dev) for o in oids}
 
     # Algorithmic bytes: distinct texels per frame (counted outside the timed region).
     distinct = 0
     for v in range(a.views):
-        sl = slice(v * per, (v + 1) * per)
-        counts = api.rt_footprint(ctx, uv[sl], dirs[sl], obj[sl], filt, len(oids))
+        counts = api.rt_footprint(ctx, uv[v].reshape(-1, 2), dirs[v].reshape(-1, 3), obj[v].reshape(-1), filt,
+                                  len(oids))
         distinct += sum(counts)
     tb = bytes_per_texel(a.storage)
     scale_bytes = 0  # E4M3 scales: 4 B per distinct bucket, counted as at most one per texel quad below
@@ -342,12 +343,14 @@ def run_radtex(a):
     bwd_bytes = (24 + 16 + 8 + 12) * F + distinct * (tb + 32) + scale_bytes
 
     stream = torch.cuda.current_stream(dev)
+    # screen tile of the batched kernels, picked by the library's autotuner on this workload
+    tile, tile_ms = api.rt_autotune(ctx, uv, dirs, obj, filt, out, reps=3)
 
     def step():
-        api.rt_shade(ctx, uv, dirs, obj, filt, out)
+        api.rt_shade_batched(ctx, uv, dirs, obj, filt, out)
         for t in dtex.values():
             t.zero_()
-        api.rt_shade_backward(ctx, uv, dirs, obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE)
+        api.rt_shade_batched_backward(ctx, uv, dirs, obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE)
 
     for _ in range(a.warmup):
         step()
@@ -368,12 +371,12 @@ def run_radtex(a):
         for k in range(a.steps):
             e = ev[k]
             e[0].record(stream)
-            api.rt_shade(ctx, uv, dirs, obj, filt, out)
+            api.rt_shade_batched(ctx, uv, dirs, obj, filt, out)
             e[1].record(stream)
             for t in dtex.values():
                 t.zero_()
             e[2].record(stream)
-            api.rt_shade_backward(ctx, uv, dirs, obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE)
+            api.rt_shade_batched_backward(ctx, uv, dirs, obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE)
             e[3].record(stream)
         end.record(stream)
         torch.cuda.synchronize()
@@ -400,19 +403,19 @@ def run_radtex(a):
     # the step, D2H of the image, every step.
     e2e = None
     if not a.no_e2e:
-        h_out = torch.empty((F, 4), dtype=torch.float32, pin_memory=True)
+        h_out = torch.empty((*shape, 4), dtype=torch.float32, pin_memory=True)
         d_uv = torch.empty_like(uv)
         d_dir = torch.empty_like(dirs)
         d_obj = torch.empty_like(obj)
 
         def e2e_step():
-            d_uv.copy_(h_uv, non_blocking=True)
-            d_dir.copy_(h_dir, non_blocking=True)
-            d_obj.copy_(h_obj, non_blocking=True)
-            api.rt_shade(ctx, d_uv, d_dir, d_obj, filt, out)
+            d_uv.copy_(h_uv.view(*shape, 2), non_blocking=True)
+            d_dir.copy_(h_dir.view(*shape, 3), non_blocking=True)
+            d_obj.copy_(h_obj.view(*shape), non_blocking=True)
+            api.rt_shade_batched(ctx, d_uv, d_dir, d_obj, filt, out)
             for t in dtex.values():
                 t.zero_()
-            api.rt_shade_backward(ctx, d_uv, d_dir, d_obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE)
+            api.rt_shade_batched_backward(ctx, d_uv, d_dir, d_obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE)
             h_out.copy_(out, non_blocking=True)
 
         e2e_step()
@@ -446,9 +449,8 @@ def run_radtex(a):
                 "traffic": recorded_traffic(kernel, wl), "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": int(nbytes), "kernel": kernel}
 
-    r_fwd = roof(fwd_gbs, "shade_kernel<QUADRILINEAR>" if filt == api.RT_QUADRILINEAR else "shade_kernel", fwd_bytes)
-    r_bwd = roof(bwd_gbs, "backward_kernel<QUADRILINEAR>" if filt == api.RT_QUADRILINEAR else "backward_kernel",
-                 bwd_bytes)
+    r_fwd = roof(fwd_gbs, f"shade_kernel<{a.filter}, tiled>", fwd_bytes)
+    r_bwd = roof(bwd_gbs, f"backward_kernel<{a.filter}, tiled>", bwd_bytes)
     dominant = r_bwd if bwd_ms >= fwd_ms else r_fwd
 
     result = {
@@ -460,7 +462,9 @@ def run_radtex(a):
                    "objects": len(oids), "texture_bytes": int(sum(api.rt_texture_info(ctx, o)["bytes"] for o in oids)),
                    "l2": "inputs larger than L2 (G-buffer %.1f GB, textures %.1f GB per rank)" % (
                        24 * F / 1e9, sum(api.rt_texture_info(ctx, o)["bytes"] for o in oids) / 1e9),
-                   "step": "rt_shade + zero texel grads + rt_shade_backward(RT_ACCUMULATE, dL/dout = out)",
+                   "step": ("rt_shade_batched + zero texel grads + rt_shade_batched_backward(RT_ACCUMULATE, "
+                            "dL/dout = out)"),
+                   "tile": {"tw": tile[0], "th": tile[1], "bx": tile[2], "by": tile[3], "autotune_ms": tile_ms},
                    "distinct_texels_per_step": int(distinct), "scene_gen_s": round(scene_s, 2)},
         "fwd_gfrag_s": F / (fwd_ms * 1e-3) / 1e9, "bwd_gfrag_s": F / (bwd_ms * 1e-3) / 1e9,
         "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "zero_grad_ms": zero_ms,

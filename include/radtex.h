@@ -91,7 +91,7 @@ rt_status rt_context_create(int cuda_device, rt_ctx** out);
 void rt_context_destroy(rt_ctx* ctx);
 
 /* Creates a radiance texture of w x h buckets of n x n texels (Section 2: the
- * bucket matrix, stored as w n x h n texels).  1 <= w, h <= 65536, 1 <= n <= 64.
+ * bucket matrix, stored as w n x h n texels).  1 <= w, h <= 65536, w h <= 2^30, 1 <= n <= 64.
  * src (device, FP32, 4 channels per texel, layout src_layout) gives the texel
  * values; NULL leaves an owned texture zero (fill it with rt_fill_bucket_lobes).
  * Without RT_BORROW the library allocates storage in RT_LAYOUT_PLANES and
@@ -163,6 +163,44 @@ rt_status rt_locate(rt_ctx* ctx, const float* uv, const float* dir, const int32_
 rt_status rt_shade_backward(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,
                             rt_filter filter, const float* dL_dout, float* const* dL_dtex, int32_t n_dtex,
                             float* dL_duv, float* dL_ddir, int32_t flags, rt_stream_t stream);
+
+/* Batched synthesis of views x height x width fragments: the same arrays as
+ * rt_shade with F = views * height * width, fragment (view, y, x) at index
+ * (view * height + y) * width + x (for instance every pose of a camera path,
+ * row-major images).  The frame shape lets the kernel walk screen tiles: each
+ * warp shades a tw x th tile, the warps of a block a compact block tile, so
+ * fragments that read the same buckets run together (Section 2: neighbouring
+ * fragments map to neighbouring buckets).  The tile shape is the context's
+ * current one for `filter` (rt_set_tile / rt_autotune); every shape gives
+ * bit-identical results.  0 <= height, width <= 65536. */
+rt_status rt_shade_batched(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int32_t views,
+                           int32_t height, int32_t width, rt_filter filter, float* out, rt_stream_t stream);
+
+/* Gradients of the batched synthesis; arguments and semantics as in
+ * rt_shade_backward, fragments laid out as in rt_shade_batched. */
+rt_status rt_shade_batched_backward(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int32_t views,
+                                    int32_t height, int32_t width, rt_filter filter, const float* dL_dout,
+                                    float* const* dL_dtex, int32_t n_dtex, float* dL_duv, float* dL_ddir,
+                                    int32_t flags, rt_stream_t stream);
+
+/* Sets the screen tile of the batched kernels for `filter`: warp tiles of
+ * tw x th fragments (tw * th = 32, tw a multiple of 4) arranged bx x by in a
+ * block tile (bx * by = 4).  The default is 8 x 4, 2 x 2.  RT_ERR_INVALID_ARG
+ * for other shapes.  Not a device call. */
+rt_status rt_set_tile(rt_ctx* ctx, rt_filter filter, int32_t tw, int32_t th, int32_t bx, int32_t by);
+
+/* The current tile of `filter`: tile4 = (tw, th, bx, by) (host, 4 ints). */
+rt_status rt_get_tile(rt_ctx* ctx, rt_filter filter, int32_t* tile4);
+
+/* Autotuner: times rt_shade_batched with each of the twelve tile shapes
+ * (tw, th) in {32x1, 16x2, 8x4, 4x8} x (bx, by) in {4x1, 2x2, 1x4}, `reps`
+ * launches each after one warm-up, on the caller's representative inputs
+ * (writing `out`), keeps the fastest for `filter` in the context and returns
+ * it in tile4 (host, 4 ints, may be NULL) with its mean launch time in best_ms
+ * (host, may be NULL).  Synchronises the stream; not capturable. */
+rt_status rt_autotune(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int32_t views,
+                      int32_t height, int32_t width, rt_filter filter, float* out, int32_t reps, rt_stream_t stream,
+                      int32_t* tile4, float* best_ms);
 
 /* Counts the distinct texels read by the F fragments (any tap of non-zero or
  * zero weight of the filter's footprint), per object: counts_host (host,

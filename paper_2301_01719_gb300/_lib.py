@@ -44,6 +44,13 @@ SIGNATURES = {
     "rt_shade": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, _P]),
     "rt_locate": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, _P, _P]),
     "rt_shade_backward": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, ctypes.POINTER(_P), _I32, _P, _P, _I32, _P]),
+    "rt_shade_batched": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, _P]),
+    "rt_shade_batched_backward": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, ctypes.POINTER(_P), _I32, _P,
+                                         _P, _I32, _P]),
+    "rt_set_tile": (_I32, [_P, _I32, _I32, _I32, _I32, _I32]),
+    "rt_get_tile": (_I32, [_P, _I32, ctypes.POINTER(_I32)]),
+    "rt_autotune": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, _I32, _P, ctypes.POINTER(_I32),
+                           ctypes.POINTER(ctypes.c_float)]),
     "rt_footprint": (_I32, [_P, _P, _P, _P, _I64, _I32, ctypes.POINTER(ctypes.c_uint64), _I32, _P]),
     "rt_convert_layout": (_I32, [_P, _I32, _P, _I32, _I32, _I32, _I32, _P]),
     "rt_get_error": (_I32, [_P, _P, ctypes.POINTER(_I32)]),

@@ -148,6 +148,64 @@ def rt_shade(ctx: Context, uv: torch.Tensor, dirs: torch.Tensor, obj: torch.Tens
     return out
 
 
+def _frames(uv, dirs, obj):
+    """(views, height, width) of G-buffer tensors shaped (V, H, W, k) / (V, H, W)."""
+    if obj.dim() != 3:
+        raise ValueError("batched G-buffers are shaped (views, height, width[, k])")
+    V, H, W = obj.shape
+    if tuple(uv.shape) != (V, H, W, 2) or tuple(dirs.shape) != (V, H, W, 3):
+        raise ValueError("uv must be (V, H, W, 2) and dir (V, H, W, 3)")
+    return V, H, W
+
+
+def rt_shade_batched(ctx: Context, uv, dirs, obj, filter: int = RT_QUADRILINEAR, out=None, stream=None):
+    """Synthesis of views x height x width fragments; uv (V, H, W, 2), dir (V, H, W, 3), obj (V, H, W)."""
+    F = _gbuffer(uv, dirs, obj)
+    V, H, W = _frames(uv, dirs, obj)
+    if out is None:
+        out = torch.empty((V, H, W, 4), dtype=torch.float32, device=uv.device)
+    _check(out, "out", torch.float32, 4)
+    if out.numel() != 4 * F:
+        raise ValueError("out must hold V x H x W x 4 floats")
+    _lib.call("rt_shade_batched", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(obj), V, H, W, int(filter), _ptr(out),
+              _stream(stream, uv.device))
+    return out
+
+
+def rt_shade_batched_backward(ctx: Context, uv, dirs, obj, filter: int, dL_dout, dL_dtex=None, dL_duv=None,
+                              dL_ddir=None, flags: int = 0, stream=None) -> None:
+    F = _gbuffer(uv, dirs, obj)
+    V, H, W = _frames(uv, dirs, obj)
+    arr, n_dtex = _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir)
+    _lib.call("rt_shade_batched_backward", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(obj), V, H, W, int(filter),
+              _ptr(dL_dout), arr, n_dtex, _ptr(dL_duv), _ptr(dL_ddir), int(flags), _stream(stream, uv.device))
+
+
+def rt_set_tile(ctx: Context, filter: int, tw: int, th: int, bx: int, by: int) -> None:
+    _lib.call("rt_set_tile", ctx.handle, int(filter), int(tw), int(th), int(bx), int(by))
+
+
+def rt_get_tile(ctx: Context, filter: int) -> tuple:
+    t = (ctypes.c_int32 * 4)()
+    _lib.call("rt_get_tile", ctx.handle, int(filter), t)
+    return tuple(int(x) for x in t)
+
+
+def rt_autotune(ctx: Context, uv, dirs, obj, filter: int = RT_QUADRILINEAR, out=None, reps: int = 3, stream=None):
+    """Picks the fastest screen tile for batched synthesis; returns ((tw, th, bx, by), mean ms)."""
+    F = _gbuffer(uv, dirs, obj)
+    V, H, W = _frames(uv, dirs, obj)
+    if out is None:
+        out = torch.empty((V, H, W, 4), dtype=torch.float32, device=uv.device)
+    if out.numel() != 4 * F:
+        raise ValueError("out must hold V x H x W x 4 floats")
+    t = (ctypes.c_int32 * 4)()
+    ms = ctypes.c_float()
+    _lib.call("rt_autotune", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(obj), V, H, W, int(filter), _ptr(out), int(reps),
+              _stream(stream, uv.device), t, ctypes.byref(ms))
+    return tuple(int(x) for x in t), float(ms.value)
+
+
 def rt_locate(ctx: Context, uv, dirs, obj, filter: int = RT_QUADRILINEAR, stream=None):
     """(idx (F, 4) int32 floors, coord (F, 4) float32 continuous coordinates)."""
     F = _gbuffer(uv, dirs, obj)
@@ -158,11 +216,7 @@ def rt_locate(ctx: Context, uv, dirs, obj, filter: int = RT_QUADRILINEAR, stream
     return idx, coord
 
 
-def rt_shade_backward(ctx: Context, uv, dirs, obj, filter: int, dL_dout: torch.Tensor, dL_dtex=None,
-                      dL_duv: torch.Tensor | None = None, dL_ddir: torch.Tensor | None = None, flags: int = 0,
-                      stream=None) -> None:
-    """dL_dtex: dict {object id: FP32 CUDA tensor in the object's storage layout} or None."""
-    F = _gbuffer(uv, dirs, obj)
+def _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir):
     _check(dL_dout, "dL_dout", torch.float32, 4)
     if dL_dout.numel() != 4 * F:
         raise ValueError("dL_dout must hold F x 4 floats")
@@ -185,6 +239,15 @@ def rt_shade_backward(ctx: Context, uv, dirs, obj, filter: int, dL_dout: torch.T
             if t.numel() != info["w"] * info["h"] * info["n"] ** 2 * 4:
                 raise ValueError(f"dL_dtex[{o}] must hold w h n^2 x 4 floats")
             arr[o] = t.data_ptr()
+    return arr, n_dtex
+
+
+def rt_shade_backward(ctx: Context, uv, dirs, obj, filter: int, dL_dout: torch.Tensor, dL_dtex=None,
+                      dL_duv: torch.Tensor | None = None, dL_ddir: torch.Tensor | None = None, flags: int = 0,
+                      stream=None) -> None:
+    """dL_dtex: dict {object id: FP32 CUDA tensor in the object's storage layout} or None."""
+    F = _gbuffer(uv, dirs, obj)
+    arr, n_dtex = _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir)
     _lib.call("rt_shade_backward", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(obj), F, int(filter), _ptr(dL_dout),
               arr, n_dtex, _ptr(dL_duv), _ptr(dL_ddir), int(flags), _stream(stream, uv.device))
 

@@ -23,6 +23,7 @@ struct rt_ctx {
     float* scales[RT_MAX_OBJECTS];       // E4M3 scales the library allocated
     int64_t bytes[RT_MAX_OBJECTS];
     int n_obj = 0;                       // one past the highest id ever used
+    int tile[3][4];                      // per filter: tw, th, bx, by of the batched kernels
 };
 
 namespace {
@@ -121,6 +122,12 @@ rt_status rt_context_create(int cuda_device, rt_ctx** out) {
     std::memset(ctx->owned, 0, sizeof(ctx->owned));
     std::memset(ctx->scales, 0, sizeof(ctx->scales));
     std::memset(ctx->bytes, 0, sizeof(ctx->bytes));
+    for (int f = 0; f < 3; ++f) {
+        ctx->tile[f][0] = 8;
+        ctx->tile[f][1] = 4;
+        ctx->tile[f][2] = 2;
+        ctx->tile[f][3] = 2;
+    }
     ctx->device = cuda_device;
     DeviceGuard g(cuda_device);
     if (!g.ok) {
@@ -166,6 +173,7 @@ rt_status rt_create_texture(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, rt_for
                             const float* src, int32_t flags, int32_t* obj_id_out) {
     if (!ctx || !obj_id_out) return RT_ERR_INVALID_ARG;
     if (w < 1 || h < 1 || n < 1 || w > 65536 || h > 65536 || n > 64) return RT_ERR_INVALID_ARG;
+    if ((int64_t)w * h > ((int64_t)1 << 30)) return RT_ERR_INVALID_ARG;  // spatial offsets are 32-bit
     if (texel_bytes(storage) == 0) return RT_ERR_INVALID_ARG;
     if (src_layout != RT_LAYOUT_ATLAS && src_layout != RT_LAYOUT_PLANES) return RT_ERR_INVALID_ARG;
     if (src && !aligned16(src)) return RT_ERR_INVALID_ARG;
@@ -311,8 +319,8 @@ rt_status rt_shade(rt_ctx* ctx, const float* uv, const float* dir, const int32_t
     if (!out || !aligned16(out)) return RT_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return RT_ERR_CUDA;
-    return cuda_status(rt::launch_shade(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, out, ctx->d_status,
-                                        (cudaStream_t)stream));
+    return cuda_status(rt::launch_shade(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, rt::flat_tiling(), out,
+                                        ctx->d_status, (cudaStream_t)stream));
 }
 
 rt_status rt_locate(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F, rt_filter filter,
@@ -328,9 +336,12 @@ rt_status rt_locate(rt_ctx* ctx, const float* uv, const float* dir, const int32_
                                          ctx->d_status, (cudaStream_t)stream));
 }
 
-rt_status rt_shade_backward(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,
-                            rt_filter filter, const float* dL_dout, float* const* dL_dtex, int32_t n_dtex,
-                            float* dL_duv, float* dL_ddir, int32_t flags, rt_stream_t stream) {
+}  // extern "C"
+
+static rt_status shade_backward_impl(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,
+                                     rt_filter filter, const rt::Tiling& T, const float* dL_dout,
+                                     float* const* dL_dtex, int32_t n_dtex, float* dL_duv, float* dL_ddir,
+                                     int32_t flags, rt_stream_t stream) {
     if (!ctx || !valid_filter(filter)) return RT_ERR_INVALID_ARG;
     rt_status st = check_gbuffer(uv, dir, obj, F);
     if (st != RT_OK) return st;
@@ -358,9 +369,121 @@ rt_status rt_shade_backward(rt_ctx* ctx, const float* uv, const float* dir, cons
                 e = cudaMemsetAsync(grads.p[o], 0, (size_t)16 * d.plane * d.n * d.n, s);
             }
     if (e == cudaSuccess && F > 0)
-        e = rt::launch_backward(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, dL_dout, grads, any, dL_duv,
+        e = rt::launch_backward(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any, dL_duv,
                                 dL_ddir, accumulate, ctx->d_status, s);
     return cuda_status(e);
+}
+
+static bool frames_tiling(rt_ctx* ctx, int32_t views, int32_t height, int32_t width, rt_filter filter,
+                          rt::Tiling* T) {
+    const int* t = ctx->tile[filter];
+    return rt::make_tiling(views, height, width, t[0], t[1], t[2], t[3], 4, T);
+}
+
+extern "C" {
+
+rt_status rt_shade_backward(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,
+                            rt_filter filter, const float* dL_dout, float* const* dL_dtex, int32_t n_dtex,
+                            float* dL_duv, float* dL_ddir, int32_t flags, rt_stream_t stream) {
+    return shade_backward_impl(ctx, uv, dir, obj, F, filter, rt::flat_tiling(), dL_dout, dL_dtex, n_dtex, dL_duv,
+                               dL_ddir, flags, stream);
+}
+
+rt_status rt_shade_batched(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int32_t views,
+                           int32_t height, int32_t width, rt_filter filter, float* out, rt_stream_t stream) {
+    if (!ctx || !valid_filter(filter) || views < 0 || height < 0 || width < 0 || height > 65536 || width > 65536)
+        return RT_ERR_INVALID_ARG;
+    const int64_t F = (int64_t)views * height * width;
+    rt_status st = check_gbuffer(uv, dir, obj, F);
+    if (st != RT_OK) return st;
+    if (F == 0) return RT_OK;
+    if (!out || !aligned16(out)) return RT_ERR_INVALID_ARG;
+    rt::Tiling T;
+    if (!frames_tiling(ctx, views, height, width, filter, &T)) return RT_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    return cuda_status(rt::launch_shade(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, T, out, ctx->d_status,
+                                        (cudaStream_t)stream));
+}
+
+rt_status rt_shade_batched_backward(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int32_t views,
+                                    int32_t height, int32_t width, rt_filter filter, const float* dL_dout,
+                                    float* const* dL_dtex, int32_t n_dtex, float* dL_duv, float* dL_ddir,
+                                    int32_t flags, rt_stream_t stream) {
+    if (!ctx || !valid_filter(filter) || views < 0 || height < 0 || width < 0 || height > 65536 || width > 65536)
+        return RT_ERR_INVALID_ARG;
+    const int64_t F = (int64_t)views * height * width;
+    rt::Tiling T = rt::flat_tiling();
+    if (F > 0 && !frames_tiling(ctx, views, height, width, filter, &T)) return RT_ERR_INVALID_ARG;
+    return shade_backward_impl(ctx, uv, dir, obj, F, filter, T, dL_dout, dL_dtex, n_dtex, dL_duv, dL_ddir, flags,
+                               stream);
+}
+
+rt_status rt_set_tile(rt_ctx* ctx, rt_filter filter, int32_t tw, int32_t th, int32_t bx, int32_t by) {
+    if (!ctx || !valid_filter(filter)) return RT_ERR_INVALID_ARG;
+    rt::Tiling T;
+    if (!rt::make_tiling(1, 1, 1, tw, th, bx, by, 4, &T)) return RT_ERR_INVALID_ARG;
+    ctx->tile[filter][0] = tw;
+    ctx->tile[filter][1] = th;
+    ctx->tile[filter][2] = bx;
+    ctx->tile[filter][3] = by;
+    return RT_OK;
+}
+
+rt_status rt_get_tile(rt_ctx* ctx, rt_filter filter, int32_t* tile4) {
+    if (!ctx || !valid_filter(filter) || !tile4) return RT_ERR_INVALID_ARG;
+    for (int k = 0; k < 4; ++k) tile4[k] = ctx->tile[filter][k];
+    return RT_OK;
+}
+
+rt_status rt_autotune(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int32_t views,
+                      int32_t height, int32_t width, rt_filter filter, float* out, int32_t reps, rt_stream_t stream,
+                      int32_t* tile4, float* best_ms) {
+    if (!ctx || !valid_filter(filter) || views < 1 || height < 1 || width < 1 || reps < 1) return RT_ERR_INVALID_ARG;
+    static const int kCand[][4] = {{32, 1, 4, 1}, {32, 1, 2, 2}, {32, 1, 1, 4}, {16, 2, 4, 1}, {16, 2, 2, 2},
+                                   {16, 2, 1, 4}, {8, 4, 4, 1},  {8, 4, 2, 2},  {8, 4, 1, 4},  {4, 8, 4, 1},
+                                   {4, 8, 2, 2},  {4, 8, 1, 4}};
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return RT_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return RT_ERR_CUDA;
+    }
+    int saved[4];
+    for (int k = 0; k < 4; ++k) saved[k] = ctx->tile[filter][k];
+    float best = 1e30f;
+    int best_k = -1;
+    rt_status st = RT_OK;
+    for (int c = 0; c < (int)(sizeof(kCand) / sizeof(kCand[0])) && st == RT_OK; ++c) {
+        for (int k = 0; k < 4; ++k) ctx->tile[filter][k] = kCand[c][k];
+        st = rt_shade_batched(ctx, uv, dir, obj, views, height, width, filter, out, stream);  // warm-up
+        if (st != RT_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == RT_OK; ++r)
+            st = rt_shade_batched(ctx, uv, dir, obj, views, height, width, filter, out, stream);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = RT_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (st == RT_OK && ms < best) {
+            best = ms;
+            best_k = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != RT_OK || best_k < 0) {
+        for (int k = 0; k < 4; ++k) ctx->tile[filter][k] = saved[k];
+        return st != RT_OK ? st : RT_ERR_CUDA;
+    }
+    for (int k = 0; k < 4; ++k) ctx->tile[filter][k] = kCand[best_k][k];
+    if (tile4)
+        for (int k = 0; k < 4; ++k) tile4[k] = kCand[best_k][k];
+    if (best_ms) *best_ms = best / (float)reps;
+    return RT_OK;
 }
 
 rt_status rt_footprint(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,

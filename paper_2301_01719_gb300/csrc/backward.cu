@@ -13,11 +13,8 @@
 
 namespace rt {
 
-constexpr int kBackThreads = 256;
+constexpr int kBackThreads = 128;
 constexpr int kBackWarps = kBackThreads / 32;
-#ifndef RT_BACK_MIN_BLOCKS
-#define RT_BACK_MIN_BLOCKS 1
-#endif
 
 struct CoordGrad {
     float gu, gv, gs, gt;  // dL/d(weight coordinate) of the u, v, s, t axes
@@ -121,14 +118,16 @@ __device__ __forceinline__ float3 direction_grad(float Ix, float Iy, float Iz, f
     return make_float3(k * gAx - m * Ix, k * gAy - m * Iy, -m * zp);
 }
 
-template <int FILTER>
-__global__ void __launch_bounds__(kBackThreads, RT_BACK_MIN_BLOCKS) backward_kernel(
+template <int FILTER, bool TILED>
+__global__ void __launch_bounds__(kBackThreads) backward_kernel(
     const TexDesc* __restrict__ table, int n_obj, const float* __restrict__ uv, const float* __restrict__ dir,
-    const int32_t* __restrict__ obj, int64_t F, const float* __restrict__ dL_dout, const __grid_constant__ GradTable grads,
-    bool any_grad, float* __restrict__ dL_duv, float* __restrict__ dL_ddir, bool accumulate, unsigned* status) {
+    const int32_t* __restrict__ obj, int64_t F, Tiling tiling, const float* __restrict__ dL_dout,
+    const __grid_constant__ GradTable grads, bool any_grad, float* __restrict__ dL_duv, float* __restrict__ dL_ddir,
+    bool accumulate, unsigned* status) {
     __shared__ WarpStage<true> stages[kBackWarps];
     const bool coord_grads = (dL_duv != nullptr) || (dL_ddir != nullptr);
-    for_each_fragment<kBackWarps, true>(uv, dir, obj, dL_dout, F, stages, [&](int64_t f, const Frag& q, float4 go) {
+    for_each_fragment<kBackWarps, true, TILED>(uv, dir, obj, dL_dout, F, tiling, stages,
+                                               [&](int64_t f, const Frag& q, float4 go) {
         float2 guv = make_float2(0.f, 0.f);
         float3 gdir = make_float3(0.f, 0.f, 0.f);
         TexDesc d;
@@ -147,7 +146,7 @@ __global__ void __launch_bounds__(kBackThreads, RT_BACK_MIN_BLOCKS) backward_ker
                 gdir = direction_grad(q.x, q.y, q.z, gBx, gBy);
             }
         }
-        if (f >= F) return;
+        if (f < 0) return;
         if (dL_duv) {
             float2* p = reinterpret_cast<float2*>(dL_duv) + f;
             if (accumulate) {
@@ -171,31 +170,47 @@ __global__ void __launch_bounds__(kBackThreads, RT_BACK_MIN_BLOCKS) backward_ker
     });
 }
 
-template <int FILTER>
+template <int FILTER, bool TILED>
 static cudaError_t launch_backward_t(const TexDesc* table, int n_obj, const float* uv, const float* dir,
-                                     const int32_t* obj, int64_t F, const float* dL_dout, const GradTable& grads,
-                                     bool any_grad, float* dL_duv, float* dL_ddir, bool accumulate, unsigned* status,
-                                     cudaStream_t stream) {
-    const unsigned grid = persistent_grid(backward_kernel<FILTER>, kBackThreads, (F + kChunk - 1) / kChunk);
-    backward_kernel<FILTER><<<grid, kBackThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, dL_dout, grads,
-                                                               any_grad, dL_duv, dL_ddir, accumulate, status);
+                                     const int32_t* obj, int64_t F, const Tiling& T, const float* dL_dout,
+                                     const GradTable& grads, bool any_grad, float* dL_duv, float* dL_ddir,
+                                     bool accumulate, unsigned* status, cudaStream_t stream) {
+    const unsigned grid = persistent_grid(backward_kernel<FILTER, TILED>, kBackThreads,
+                                          chunk_count_host(T, F, kBackWarps));
+    backward_kernel<FILTER, TILED><<<grid, kBackThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, T, dL_dout,
+                                                                      grads, any_grad, dL_duv, dL_ddir, accumulate,
+                                                                      status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_backward(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
-                            int64_t F, int filter, const float* dL_dout, const GradTable& grads, bool any_grad,
-                            float* dL_duv, float* dL_ddir, bool accumulate, unsigned* status, cudaStream_t stream) {
+template <bool TILED>
+static cudaError_t launch_backward_f(const TexDesc* table, int n_obj, const float* uv, const float* dir,
+                                     const int32_t* obj, int64_t F, int filter, const Tiling& T,
+                                     const float* dL_dout, const GradTable& grads, bool any_grad, float* dL_duv,
+                                     float* dL_ddir, bool accumulate, unsigned* status, cudaStream_t stream) {
     switch (filter) {
         case RT_NEAREST:
-            return launch_backward_t<RT_NEAREST>(table, n_obj, uv, dir, obj, F, dL_dout, grads, any_grad, dL_duv,
-                                                 dL_ddir, accumulate, status, stream);
+            return launch_backward_t<RT_NEAREST, TILED>(table, n_obj, uv, dir, obj, F, T, dL_dout, grads, any_grad,
+                                                        dL_duv, dL_ddir, accumulate, status, stream);
         case RT_ANGULAR_BILINEAR:
-            return launch_backward_t<RT_ANGULAR_BILINEAR>(table, n_obj, uv, dir, obj, F, dL_dout, grads, any_grad,
-                                                          dL_duv, dL_ddir, accumulate, status, stream);
+            return launch_backward_t<RT_ANGULAR_BILINEAR, TILED>(table, n_obj, uv, dir, obj, F, T, dL_dout, grads,
+                                                                 any_grad, dL_duv, dL_ddir, accumulate, status,
+                                                                 stream);
         default:
-            return launch_backward_t<RT_QUADRILINEAR>(table, n_obj, uv, dir, obj, F, dL_dout, grads, any_grad,
-                                                      dL_duv, dL_ddir, accumulate, status, stream);
+            return launch_backward_t<RT_QUADRILINEAR, TILED>(table, n_obj, uv, dir, obj, F, T, dL_dout, grads,
+                                                             any_grad, dL_duv, dL_ddir, accumulate, status, stream);
     }
+}
+
+cudaError_t launch_backward(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
+                            int64_t F, int filter, const Tiling& T, const float* dL_dout, const GradTable& grads,
+                            bool any_grad, float* dL_duv, float* dL_ddir, bool accumulate, unsigned* status,
+                            cudaStream_t stream) {
+    if (T.W > 0)
+        return launch_backward_f<true>(table, n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any_grad, dL_duv,
+                                       dL_ddir, accumulate, status, stream);
+    return launch_backward_f<false>(table, n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any_grad, dL_duv,
+                                    dL_ddir, accumulate, status, stream);
 }
 
 }  // namespace rt

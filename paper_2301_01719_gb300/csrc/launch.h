@@ -12,7 +12,7 @@ namespace rt {
 // chunks with `warps` warps per block, at most (SMs x resident blocks per SM).
 // The occupancy query is cached per kernel and device.
 template <typename Kernel>
-inline unsigned persistent_grid(Kernel kernel, int threads, int64_t chunks) {
+inline unsigned persistent_grid(Kernel kernel, int threads, int64_t chunks, size_t dynamic_smem = 0) {
     static std::mutex mu;
     static int cached_dev[64];
     static int cached_blocks[64];
@@ -31,7 +31,7 @@ inline unsigned persistent_grid(Kernel kernel, int threads, int64_t chunks) {
     if (total == 0) {
         int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, dynamic_smem);
         total = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
         std::lock_guard<std::mutex> lock(mu);
         if (dev >= 0 && dev < 64) {

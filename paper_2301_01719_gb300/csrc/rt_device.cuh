@@ -54,15 +54,16 @@ __device__ __forceinline__ bool finite3(float a, float b, float c) {
 // Eq. 1b followed by Eq. 3, B = A |A| / max(|A_x|, |A_y|) with
 // A = sqrt(2) I_xy / |(I_x, I_y, I_z + 1)|.  Since A is a positive multiple of
 // I_xy, B = sqrt(2) (I_xy / m) |I_xy| / |(I_x, I_y, I_z + 1)| with
-// m = max(|I_x|, |I_y|); dividing every component by m first keeps the sums
-// of squares away from underflow.  I_xy = 0 (also I = -N) gives B = 0, the
-// limit of Eq. 3; so does m < 1e-30, which moves B by less than 1e-30.
+// m = max(|I_x|, |I_y|).  Every component is divided by m first, so the sums of
+// squares neither underflow nor overflow (g2 lies in [1, 2]); a huge
+// (I_z + 1) / m gives B = 0, the limit.  I_xy = 0 (also I = -N) gives B = 0,
+// the limit of Eq. 3; so does m < 1e-18, which moves B by less than 1e-18.
 __device__ __forceinline__ float2 incidence_to_square(float Ix, float Iy, float Iz) {
     float m = fmaxf(fabsf(Ix), fabsf(Iy));
-    if (!(m >= 1e-30f)) return make_float2(0.f, 0.f);
+    if (!(m >= 1e-18f)) return make_float2(0.f, 0.f);
     float rm = 1.0f / m;
     float x = Ix * rm, y = Iy * rm, z = (Iz + 1.0f) * rm;
-    float g2 = x * x + y * y;  // in [1, 2]
+    float g2 = x * x + y * y;
     float D2 = g2 + z * z;
     float k = 1.41421356237f * sqrtf(g2 / D2);
     return make_float2(x * k, y * k);
@@ -214,6 +215,69 @@ __device__ __forceinline__ float4 sub4(float4 a, float4 b) {
 }
 
 __device__ __forceinline__ float dot4(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+
+// RGBA held as two packed FP32 pairs, filtered with the paired FP32 FMA of
+// sm_100+ (fma.rn.f32x2 / sub.rn.f32x2): the same roundings as the scalar
+// lerp a + w (b - a), at half the instruction count.
+typedef unsigned long long f32x2;
+struct P4 {
+    f32x2 rg, ba;
+};
+
+__device__ __forceinline__ f32x2 pack2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 unpack2(f32x2 v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ f32x2 lerp2(f32x2 a, f32x2 b, f32x2 w) {
+    f32x2 d, r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(b), "l"(a));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(w), "l"(d), "l"(a));
+    return r;
+}
+__device__ __forceinline__ P4 lerpP(const P4& a, const P4& b, f32x2 w) { return {lerp2(a.rg, b.rg, w), lerp2(a.ba, b.ba, w)}; }
+__device__ __forceinline__ float4 toF4(const P4& p) {
+    float2 a = unpack2(p.rg), b = unpack2(p.ba);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+template <int FMT>
+__device__ __forceinline__ P4 load_texelP(const void* base, int64_t idx, float scale);
+
+template <>
+__device__ __forceinline__ P4 load_texelP<RT_F32>(const void* base, int64_t idx, float) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(base) + idx);
+    return {pack2(v.x, v.y), pack2(v.z, v.w)};
+}
+
+template <>
+__device__ __forceinline__ P4 load_texelP<RT_F16>(const void* base, int64_t idx, float) {
+    uint2 r = __ldg(reinterpret_cast<const uint2*>(base) + idx);
+    float2 fa = __half22float2(*reinterpret_cast<__half2*>(&r.x));
+    float2 fb = __half22float2(*reinterpret_cast<__half2*>(&r.y));
+    return {pack2(fa.x, fa.y), pack2(fb.x, fb.y)};
+}
+
+template <>
+__device__ __forceinline__ P4 load_texelP<RT_BF16>(const void* base, int64_t idx, float) {
+    uint2 r = __ldg(reinterpret_cast<const uint2*>(base) + idx);
+    float2 fa = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&r.x));
+    float2 fb = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&r.y));
+    return {pack2(fa.x, fa.y), pack2(fb.x, fb.y)};
+}
+
+template <>
+__device__ __forceinline__ P4 load_texelP<RT_E4M3_BUCKET_SCALE>(const void* base, int64_t idx, float scale) {
+    unsigned r = __ldg(reinterpret_cast<const unsigned*>(base) + idx);
+    float2 a = e4m3x2_to_float2((unsigned short)(r & 0xFFFFu));
+    float2 b = e4m3x2_to_float2((unsigned short)(r >> 16));
+    return {pack2(a.x * scale, a.y * scale), pack2(b.x * scale, b.y * scale)};
+}
 
 // Vector reduction of four floats into global memory (one 16-byte atomic).
 __device__ __forceinline__ void red_add_v4(float* addr, float4 v) {

@@ -24,35 +24,78 @@ __device__ __forceinline__ void load_quad(const TexDesc& d, int i, int j, const 
     t11 = load_texel<FMT>(d.base, texel_index<LAYOUT>(d, i, j, s.k1, t.k1), sc);
 }
 
+// Addresses of the taps.  PLANES: the four in-bucket texels (s0|s1, t0|t1)
+// select four planes (64-bit base indices), the (up to) four buckets select
+// spatial offsets j w + i inside a plane (32-bit, w h < 2^31).
+template <int FMT, int LAYOUT>
+__device__ __forceinline__ void load_quadP(const TexDesc& d, int i, int j, const Axis& s, const Axis& t, P4& t00,
+                                           P4& t10, P4& t01, P4& t11) {
+    float sc = 1.0f;
+    if (FMT == RT_E4M3_BUCKET_SCALE) sc = __ldg(d.scale + (int64_t)j * d.W + i);
+    t00 = load_texelP<FMT>(d.base, texel_index<LAYOUT>(d, i, j, s.k0, t.k0), sc);
+    t10 = load_texelP<FMT>(d.base, texel_index<LAYOUT>(d, i, j, s.k1, t.k0), sc);
+    t01 = load_texelP<FMT>(d.base, texel_index<LAYOUT>(d, i, j, s.k0, t.k1), sc);
+    t11 = load_texelP<FMT>(d.base, texel_index<LAYOUT>(d, i, j, s.k1, t.k1), sc);
+}
+
+template <int FMT>
+__device__ __forceinline__ P4 quadrilinear_planes(const TexDesc& d, const Axis& U, const Axis& V, const Axis& S,
+                                                  const Axis& T) {
+    const int64_t P = d.plane;
+    const int64_t p00 = (int64_t)(T.k0 * d.n + S.k0) * P;
+    const int64_t ds = (int64_t)(S.k1 - S.k0) * P, dt = (int64_t)(T.k1 - T.k0) * d.n * P;
+    const int64_t pl[4] = {p00, p00 + ds, p00 + dt, p00 + dt + ds};
+    const int o[4] = {V.k0 * d.W + U.k0, V.k0 * d.W + U.k1, V.k1 * d.W + U.k0, V.k1 * d.W + U.k1};
+    float sc[4] = {1.f, 1.f, 1.f, 1.f};
+    if (FMT == RT_E4M3_BUCKET_SCALE) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sc[k] = __ldg(d.scale + o[k]);
+    }
+    P4 q[4][4];  // [bucket][texel]
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[b][k] = load_texelP<FMT>(d.base, pl[k] + o[b], sc[b]);
+    const f32x2 ws = pack2(S.w, S.w), wt = pack2(T.w, T.w), wu = pack2(U.w, U.w), wv = pack2(V.w, V.w);
+    P4 c[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) c[b] = lerpP(lerpP(q[b][0], q[b][1], ws), lerpP(q[b][2], q[b][3], ws), wt);
+    return lerpP(lerpP(c[0], c[1], wu), lerpP(c[2], c[3], wu), wv);
+}
+
 template <int FILTER, int FMT, int LAYOUT>
 __device__ __forceinline__ float4 filter_taps(const TexDesc& d, const Lookup<FILTER>& L) {
     if (FILTER == RT_NEAREST) {
         float sc = 1.0f;
         if (FMT == RT_E4M3_BUCKET_SCALE) sc = __ldg(d.scale + (int64_t)L.v.k0 * d.W + L.u.k0);
-        return load_texel<FMT>(d.base, texel_index<LAYOUT>(d, L.u.k0, L.v.k0, L.s.k0, L.t.k0), sc);
+        return toF4(load_texelP<FMT>(d.base, texel_index<LAYOUT>(d, L.u.k0, L.v.k0, L.s.k0, L.t.k0), sc));
     } else if (FILTER == RT_ANGULAR_BILINEAR) {
-        float4 a, b, c, e;
-        load_quad<FMT, LAYOUT>(d, L.u.k0, L.v.k0, L.s, L.t, a, b, c, e);
-        return lerp4(lerp4(a, b, L.s.w), lerp4(c, e, L.s.w), L.t.w);
+        P4 a, b, c, e;
+        load_quadP<FMT, LAYOUT>(d, L.u.k0, L.v.k0, L.s, L.t, a, b, c, e);
+        const f32x2 ws = pack2(L.s.w, L.s.w), wt = pack2(L.t.w, L.t.w);
+        return toF4(lerpP(lerpP(a, b, ws), lerpP(c, e, ws), wt));
+    } else if (LAYOUT == RT_LAYOUT_PLANES) {
+        return toF4(quadrilinear_planes<FMT>(d, L.u, L.v, L.s, L.t));
     } else {
-        float4 q[2][2][4];
+        P4 q[2][2][4];
 #pragma unroll
         for (int bv = 0; bv < 2; ++bv)
 #pragma unroll
             for (int au = 0; au < 2; ++au)
-                load_quad<FMT, LAYOUT>(d, au ? L.u.k1 : L.u.k0, bv ? L.v.k1 : L.v.k0, L.s, L.t, q[bv][au][0],
-                                       q[bv][au][1], q[bv][au][2], q[bv][au][3]);
-        float4 y[2];
+                load_quadP<FMT, LAYOUT>(d, au ? L.u.k1 : L.u.k0, bv ? L.v.k1 : L.v.k0, L.s, L.t, q[bv][au][0],
+                                        q[bv][au][1], q[bv][au][2], q[bv][au][3]);
+        const f32x2 ws = pack2(L.s.w, L.s.w), wt = pack2(L.t.w, L.t.w), wu = pack2(L.u.w, L.u.w),
+                    wv = pack2(L.v.w, L.v.w);
+        P4 y[2];
 #pragma unroll
         for (int bv = 0; bv < 2; ++bv) {
-            float4 c[2];
+            P4 c[2];
 #pragma unroll
             for (int au = 0; au < 2; ++au)
-                c[au] = lerp4(lerp4(q[bv][au][0], q[bv][au][1], L.s.w), lerp4(q[bv][au][2], q[bv][au][3], L.s.w),
-                              L.t.w);
-            y[bv] = lerp4(c[0], c[1], L.u.w);
+                c[au] = lerpP(lerpP(q[bv][au][0], q[bv][au][1], ws), lerpP(q[bv][au][2], q[bv][au][3], ws), wt);
+            y[bv] = lerpP(c[0], c[1], wu);
         }
-        return lerp4(y[0], y[1], L.v.w);
+        return toF4(lerpP(y[0], y[1], wv));
     }
 }
 
@@ -81,7 +124,53 @@ __device__ __forceinline__ float4 filter_any(const TexDesc& d, const Lookup<FILT
 // 16-byte cp.async copies that bypass L1 -- so the DRAM latency of the
 // G-buffer overlaps the texel gather, and no block-wide barrier is needed.
 // Only __syncwarp orders the warp's own copies and reads.
+//
+// A chunk is either 32 consecutive fragments of the flat stream (rt_shade), or
+// a tw x th screen tile of a batch of frames (rt_shade_batched): fragment
+// (view, y, x) of views x H x W frames.  A block's warps take the tw x th
+// sub-tiles of one bx x by block tile, so the warps that share an SM's L1 work
+// on one compact screen region: vertically adjacent fragments read the same
+// bucket rows.  Block tiles are visited in raster order, frame after frame.
 constexpr int kChunk = 32;
+
+// Division of a non-negative 31-bit integer by a fixed divisor d >= 1 with a
+// multiply and a shift (the divisor's "magic" reciprocal is prepared on the
+// host): q = umulhi(n, mul) >> shift, with shift = ceil(log2 d) and
+// mul = ceil(2^(32 + shift) / d) - 2^32 handled as below for d = 1.
+struct FastDiv {
+    uint32_t d, mul, shift;
+    __host__ __device__ __forceinline__ uint32_t div(uint32_t n) const {
+        // q = (umulhi(n, mul) + n) >> shift, with the 33-bit sum taken in 64 bits
+#ifdef __CUDA_ARCH__
+        const uint32_t hi = __umulhi(n, mul);
+#else
+        const uint32_t hi = (uint32_t)(((uint64_t)n * mul) >> 32);
+#endif
+        return (uint32_t)(((uint64_t)hi + n) >> shift);
+    }
+};
+
+// Prepares a FastDiv for divisor d >= 1 (exact for every n < 2^31).
+__host__ __device__ inline FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f;
+    f.d = d;
+    uint32_t s = 0;
+    while (s < 32 && (1ull << s) < d) ++s;
+    f.shift = s;
+    // mul = floor(2^32 (2^s - d) / d) + 1
+    f.mul = (uint32_t)((((1ull << s) - d) << 32) / d + 1);
+    return f;
+}
+
+struct Tiling {
+    int32_t W, H, views;  // frame size and count; W = H = 0 selects the flat stream
+    int32_t tw, th;       // warp tile, tw * th = 32, tw a multiple of 4
+    int32_t bx, by;       // block tile in warp tiles, bx * by = warps per block
+    int32_t btx, bty;     // block tiles per frame row / column
+    int32_t tw_log2, bx_log2;
+    FastDiv div_btx, div_frame;  // by btx, by btx * bty
+    int64_t frame;        // W * H
+};
 
 template <bool EXTRA>
 struct WarpStage {
@@ -106,27 +195,84 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Issues the copies of chunk `c` into buffer `b` (a partial last chunk is read
-// with plain bounded loads instead; fragments past F become background).
+// Geometry of one chunk: the first fragment of each of its rows, whether the
+// whole chunk can be copied with aligned 16-byte pieces, and this lane's
+// fragment (-1 = none).
+struct ChunkGeom {
+    int64_t row0;    // fragment index of (x0, y0)
+    int64_t pitch;   // fragment stride between rows
+    int tw, th;
+    bool fast;
+    int64_t f;       // this lane's fragment, -1 outside the frame / stream
+};
+
+template <int WARPS, bool TILED>
+__device__ __forceinline__ ChunkGeom chunk_geom(const Tiling& T, int64_t F, int64_t c, int lane) {
+    ChunkGeom g;
+    if (!TILED) {
+        g.row0 = c * kChunk;
+        g.pitch = kChunk;
+        g.tw = kChunk;
+        g.th = 1;
+        g.fast = g.row0 + kChunk <= F;
+        g.f = g.row0 + lane < F ? g.row0 + lane : -1;
+        return g;
+    }
+    // block tile bt, sub-tile w; chunk indices of the tiled walk fit 31 bits
+    const uint32_t cc = (uint32_t)c;
+    const uint32_t bt = cc / WARPS, w = cc % WARPS;
+    const uint32_t view = T.div_frame.div(bt);
+    const uint32_t r = bt - view * T.div_frame.d;
+    const uint32_t tyb = T.div_btx.div(r), txb = r - tyb * T.div_btx.d;
+    const int x0 = (int)((txb * T.bx + (w & (T.bx - 1))) << T.tw_log2);
+    const int y0 = (int)((tyb * T.by + (w >> T.bx_log2)) * T.th);
+    g.tw = T.tw;
+    g.th = T.th;
+    g.pitch = T.W;
+    g.row0 = (int64_t)view * T.frame + (int64_t)y0 * T.W + x0;
+    g.fast = (x0 + T.tw <= T.W) && (y0 + T.th <= T.H) && ((T.W & 3) == 0);
+    const int ly = lane >> T.tw_log2, lx = lane & (T.tw - 1);
+    g.f = (x0 + lx < T.W && y0 + ly < T.H) ? g.row0 + (int64_t)ly * T.W + lx : -1;
+    return g;
+}
+
+// Issues the copies of one chunk into buffer `b` (a chunk that is not entirely
+// inside the frame or not 16-byte aligned is read with plain bounded loads
+// instead; lanes without a fragment become background).
 template <bool EXTRA>
 __device__ __forceinline__ void stage_chunk(const float* __restrict__ uv, const float* __restrict__ dir,
                                             const int32_t* __restrict__ obj, const float* __restrict__ extra,
-                                            int64_t F, int64_t c, int b, WarpStage<EXTRA>& S, int lane) {
-    const int64_t f0 = c * kChunk;
-    if (f0 + kChunk <= F) {
-        // 16 + 24 + 8 (+ 32) sixteen-byte pieces spread over the 32 lanes
-        if (lane < 16) cp_async16(&S.uv[b][4 * lane], uv + 2 * f0 + 4 * lane);
-        if (lane < 24) cp_async16(&S.dir[b][4 * lane], dir + 3 * f0 + 4 * lane);
-        if (lane < 8) cp_async16(&S.obj[b][4 * lane], obj + f0 + 4 * lane);
-        if (EXTRA) cp_async16(&S.extra[b][lane], extra + 4 * (f0 + lane));
+                                            const ChunkGeom& g, int b, WarpStage<EXTRA>& S, int lane) {
+    if (g.fast) {
+        // per row: tw/2 pieces of uv, 3 tw/4 of dir, tw/4 of obj (48 per chunk)
+        const int nuv = g.tw >> 1, ndir = (3 * g.tw) >> 2, npr = (3 * g.tw) >> 1;
+        for (int p = lane; p < 48; p += 32) {
+            const int k = p / npr, q = p - k * npr;
+            const int64_t fk = g.row0 + (int64_t)k * g.pitch;
+            if (q < nuv)
+                cp_async16(&S.uv[b][2 * g.tw * k + 4 * q], uv + 2 * fk + 4 * q);
+            else if (q < nuv + ndir)
+                cp_async16(&S.dir[b][3 * g.tw * k + 4 * (q - nuv)], dir + 3 * fk + 4 * (q - nuv));
+            else
+                cp_async16(&S.obj[b][g.tw * k + 4 * (q - nuv - ndir)], obj + fk + 4 * (q - nuv - ndir));
+        }
+        if (EXTRA) cp_async16(&S.extra[b][lane], extra + 4 * g.f);
     } else {
-        const int count = (int)(F - f0);
-        for (int k = lane; k < 2 * kChunk; k += 32) S.uv[b][k] = k < 2 * count ? uv[2 * f0 + k] : 0.f;
-        for (int k = lane; k < 3 * kChunk; k += 32) S.dir[b][k] = k < 3 * count ? dir[3 * f0 + k] : 0.f;
-        S.obj[b][lane] = lane < count ? obj[f0 + lane] : -1;
+        const int64_t f = g.f;
+        if (f >= 0) {
+            S.uv[b][2 * lane] = uv[2 * f];
+            S.uv[b][2 * lane + 1] = uv[2 * f + 1];
+            S.dir[b][3 * lane] = dir[3 * f];
+            S.dir[b][3 * lane + 1] = dir[3 * f + 1];
+            S.dir[b][3 * lane + 2] = dir[3 * f + 2];
+            S.obj[b][lane] = obj[f];
+        } else {
+            S.uv[b][2 * lane] = S.uv[b][2 * lane + 1] = 0.f;
+            S.dir[b][3 * lane] = S.dir[b][3 * lane + 1] = S.dir[b][3 * lane + 2] = 0.f;
+            S.obj[b][lane] = -1;
+        }
         if (EXTRA)
-            S.extra[b][lane] = lane < count ? reinterpret_cast<const float4*>(extra)[f0 + lane]
-                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+            S.extra[b][lane] = f >= 0 ? reinterpret_cast<const float4*>(extra)[f] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -143,26 +289,34 @@ __device__ __forceinline__ Frag read_frag(const WarpStage<EXTRA>& S, int b, int 
     return r;
 }
 
+template <bool TILED>
+__device__ __forceinline__ int64_t chunk_count(const Tiling& T, int64_t F, int warps) {
+    if (!TILED) return (F + kChunk - 1) / kChunk;
+    return (int64_t)T.btx * T.bty * T.views * warps;
+}
+
 // Runs body(f, frag, extra) with all 32 lanes of the warp, one fragment per
 // lane, persistent over the grid, with the G-buffer of the next chunk
-// prefetched.  Lanes past F get a background fragment and f >= F: the body
-// must not store for them.  WARPS = warps per block; the block's shared memory
-// holds WARPS stages.
-template <int WARPS, bool EXTRA, typename Body>
+// prefetched.  Lanes without a fragment get a background fragment and f = -1:
+// the body must not store for them.  WARPS = warps per block; the block's
+// shared memory holds WARPS stages.
+template <int WARPS, bool EXTRA, bool TILED, typename Body>
 __device__ __forceinline__ void for_each_fragment(const float* __restrict__ uv, const float* __restrict__ dir,
                                                   const int32_t* __restrict__ obj, const float* __restrict__ extra,
-                                                  int64_t F, WarpStage<EXTRA>* stages, Body body) {
+                                                  int64_t F, const Tiling& T, WarpStage<EXTRA>* stages, Body body) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     WarpStage<EXTRA>& S = stages[w];
-    const int64_t nchunks = (F + kChunk - 1) / kChunk;
+    const int64_t nchunks = chunk_count<TILED>(T, F, WARPS);
     const int64_t step = (int64_t)gridDim.x * WARPS;
     int64_t c = (int64_t)blockIdx.x * WARPS + w;
     int b = 0;
-    if (c < nchunks) stage_chunk<EXTRA>(uv, dir, obj, extra, F, c, 0, S, lane);
+    ChunkGeom g = chunk_geom<WARPS, TILED>(T, F, c, lane);
+    if (c < nchunks) stage_chunk<EXTRA>(uv, dir, obj, extra, g, 0, S, lane);
     cp_async_commit();
     for (; c < nchunks; c += step, b ^= 1) {
         const int64_t next = c + step;
-        if (next < nchunks) stage_chunk<EXTRA>(uv, dir, obj, extra, F, next, b ^ 1, S, lane);
+        const ChunkGeom gn = chunk_geom<WARPS, TILED>(T, F, next, lane);
+        if (next < nchunks) stage_chunk<EXTRA>(uv, dir, obj, extra, gn, b ^ 1, S, lane);
         cp_async_commit();
         cp_async_wait<1>();  // chunk c has landed (the newest group may still be in flight)
         __syncwarp();
@@ -170,7 +324,8 @@ __device__ __forceinline__ void for_each_fragment(const float* __restrict__ uv, 
         float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
         if (EXTRA) e = S.extra[EXTRA ? b : 0][EXTRA ? lane : 0];
         __syncwarp();  // every lane has read buffer b before it is refilled
-        body(c * kChunk + lane, q, e);
+        body(g.f, q, e);
+        g = gn;
     }
     cp_async_wait<0>();
 }

@@ -6,8 +6,55 @@
 
 #include "radtex.h"
 
+#include "rt_filter.cuh"
+
 namespace rt {
 struct TexDesc;
+
+// The flat stream (no frame shape).
+__host__ __device__ inline Tiling flat_tiling() {
+    Tiling t{};
+    t.tw = 32;
+    t.th = 1;
+    t.bx = 1;
+    t.by = 1;
+    return t;
+}
+
+// Screen tiling of views x h x w frames with tw x th warp tiles arranged bx x by
+// in a block tile; false if the shape is not usable (tw * th != 32, tw not a
+// multiple of 4, bx * by != warps).
+inline int log2_exact(int x) {
+    int k = 0;
+    while ((1 << k) < x) ++k;
+    return (1 << k) == x ? k : -1;
+}
+
+inline bool make_tiling(int views, int h, int w, int tw, int th, int bx, int by, int warps, Tiling* t) {
+    if (views < 1 || h < 1 || w < 1 || tw * th != 32 || (tw & 3) != 0 || bx * by != warps) return false;
+    if (log2_exact(tw) < 0 || log2_exact(bx) < 0) return false;
+    t->W = w;
+    t->H = h;
+    t->views = views;
+    t->tw = tw;
+    t->th = th;
+    t->bx = bx;
+    t->by = by;
+    t->btx = (w + bx * tw - 1) / (bx * tw);
+    t->bty = (h + by * th - 1) / (by * th);
+    t->frame = (int64_t)w * h;
+    t->tw_log2 = log2_exact(tw);
+    t->bx_log2 = log2_exact(bx);
+    t->div_btx = make_fastdiv((uint32_t)t->btx);
+    t->div_frame = make_fastdiv((uint32_t)((int64_t)t->btx * t->bty));
+    // the tiled walk indexes chunks with 31-bit integers
+    return (int64_t)t->btx * t->bty * views * warps < ((int64_t)1 << 31);
+}
+
+inline int64_t chunk_count_host(const Tiling& T, int64_t F, int warps) {
+    if (T.W <= 0) return (F + 31) / 32;
+    return (int64_t)T.btx * T.bty * T.views * warps;
+}
 
 // Pointers to the FP32 texel-gradient buffers, indexed by object id, passed by
 // value as a kernel parameter (no device allocation, capturable in a graph).
@@ -16,12 +63,13 @@ struct GradTable {
 };
 
 cudaError_t launch_shade(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
-                         int64_t F, int filter, float* out, unsigned* status, cudaStream_t stream);
+                         int64_t F, int filter, const Tiling& T, float* out, unsigned* status, cudaStream_t stream);
 cudaError_t launch_locate(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
                           int64_t F, int filter, int32_t* idx, float* coord, unsigned* status, cudaStream_t stream);
 cudaError_t launch_backward(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
-                            int64_t F, int filter, const float* dL_dout, const GradTable& grads, bool any_grad,
-                            float* dL_duv, float* dL_ddir, bool accumulate, unsigned* status, cudaStream_t stream);
+                            int64_t F, int filter, const Tiling& T, const float* dL_dout, const GradTable& grads,
+                            bool any_grad, float* dL_duv, float* dL_ddir, bool accumulate, unsigned* status,
+                            cudaStream_t stream);
 
 cudaError_t launch_encode(const float* src, int src_layout, void* dst, float* scale, int W, int H, int n, int fmt,
                           cudaStream_t stream);

@@ -1,11 +1,12 @@
 // shade.cu -- forward synthesis and lookup-coordinate kernels.
 //
-// Persistent kernels: every warp walks 32-fragment chunks with the G-buffer of
-// its next chunk prefetched into shared memory (rt_filter.cuh), one fragment
-// per lane, and writes its colour with one 16-byte store.  Texels are gathered
-// through the read-only path; consecutive fragments of a scanline fall in
-// neighbouring buckets, and in the PLANES layout neighbouring buckets at one
-// in-bucket texel are neighbours in memory, so a warp's taps share cache lines.
+// Persistent kernels: every warp walks 32-fragment chunks (a run of the flat
+// stream, or a screen tile of a batch of frames) with the G-buffer of its next
+// chunk prefetched into shared memory (rt_filter.cuh), one fragment per lane,
+// and writes its colour with one 16-byte store.  Texels are gathered through
+// the read-only path; fragments that are close on screen fall in neighbouring
+// buckets, and in the PLANES layout neighbouring buckets at one in-bucket texel
+// are neighbours in memory, so a warp's taps share cache lines.
 #include "launch.h"
 #include "rt_device.cuh"
 #include "rt_filter.cuh"
@@ -13,41 +14,39 @@
 
 namespace rt {
 
-constexpr int kShadeThreads = 256;
+constexpr int kShadeThreads = 128;
 constexpr int kShadeWarps = kShadeThreads / 32;
-#ifndef RT_SHADE_MIN_BLOCKS
-#define RT_SHADE_MIN_BLOCKS 1
-#endif
 
-template <int FILTER>
-__global__ void __launch_bounds__(kShadeThreads, RT_SHADE_MIN_BLOCKS) shade_kernel(const TexDesc* __restrict__ table, int n_obj,
+template <int FILTER, bool TILED>
+__global__ void __launch_bounds__(kShadeThreads) shade_kernel(const TexDesc* __restrict__ table, int n_obj,
                                                               const float* __restrict__ uv,
                                                               const float* __restrict__ dir,
                                                               const int32_t* __restrict__ obj, int64_t F,
-                                                              float* __restrict__ out, unsigned* status) {
+                                                              Tiling tiling, float* __restrict__ out,
+                                                              unsigned* status) {
     __shared__ WarpStage<false> stages[kShadeWarps];
-    for_each_fragment<kShadeWarps, false>(uv, dir, obj, nullptr, F, stages,
-                                          [&](int64_t f, const Frag& q, float4) {
+    for_each_fragment<kShadeWarps, false, TILED>(uv, dir, obj, nullptr, F, tiling, stages,
+                                                 [&](int64_t f, const Frag& q, float4) {
         float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
         TexDesc d;
         if (fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d)) {
             Lookup<FILTER> L = locate<FILTER>(d, q.u, q.v, q.x, q.y, q.z);
             res = filter_any<FILTER>(d, L);
         }
-        if (f < F) __stcs(reinterpret_cast<float4*>(out) + f, res);
+        if (f >= 0) __stcs(reinterpret_cast<float4*>(out) + f, res);
     });
 }
 
-template <int FILTER>
+template <int FILTER, bool TILED>
 __global__ void __launch_bounds__(kShadeThreads) locate_kernel(const TexDesc* __restrict__ table, int n_obj,
                                                                const float* __restrict__ uv,
                                                                const float* __restrict__ dir,
                                                                const int32_t* __restrict__ obj, int64_t F,
-                                                               int32_t* __restrict__ idx, float* __restrict__ coord,
-                                                               unsigned* status) {
+                                                               Tiling tiling, int32_t* __restrict__ idx,
+                                                               float* __restrict__ coord, unsigned* status) {
     __shared__ WarpStage<false> stages[kShadeWarps];
-    for_each_fragment<kShadeWarps, false>(uv, dir, obj, nullptr, F, stages,
-                                          [&](int64_t f, const Frag& q, float4) {
+    for_each_fragment<kShadeWarps, false, TILED>(uv, dir, obj, nullptr, F, tiling, stages,
+                                                 [&](int64_t f, const Frag& q, float4) {
         int4 I = make_int4(0, 0, 0, 0);
         float4 C = make_float4(0.f, 0.f, 0.f, 0.f);
         TexDesc d;
@@ -56,51 +55,66 @@ __global__ void __launch_bounds__(kShadeThreads) locate_kernel(const TexDesc* __
             I = make_int4(L.u.fl, L.v.fl, L.s.fl, L.t.fl);
             C = make_float4(L.u.c, L.v.c, L.s.c, L.t.c);
         }
-        if (f < F) {
+        if (f >= 0) {
             reinterpret_cast<int4*>(idx)[f] = I;
             reinterpret_cast<float4*>(coord)[f] = C;
         }
     });
 }
 
-template <int FILTER>
+template <int FILTER, bool TILED>
 static cudaError_t launch_shade_t(const TexDesc* table, int n_obj, const float* uv, const float* dir,
-                                  const int32_t* obj, int64_t F, float* out, unsigned* status, cudaStream_t stream) {
-    const unsigned grid = persistent_grid(shade_kernel<FILTER>, kShadeThreads, (F + kChunk - 1) / kChunk);
-    shade_kernel<FILTER><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, out, status);
+                                  const int32_t* obj, int64_t F, const Tiling& T, float* out, unsigned* status,
+                                  cudaStream_t stream) {
+    const unsigned grid = persistent_grid(shade_kernel<FILTER, TILED>, kShadeThreads,
+                                          chunk_count_host(T, F, kShadeWarps));
+    shade_kernel<FILTER, TILED><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, T, out, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_shade(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
-                         int64_t F, int filter, float* out, unsigned* status, cudaStream_t stream) {
+template <bool TILED>
+static cudaError_t launch_shade_f(const TexDesc* table, int n_obj, const float* uv, const float* dir,
+                                  const int32_t* obj, int64_t F, int filter, const Tiling& T, float* out,
+                                  unsigned* status, cudaStream_t stream) {
     switch (filter) {
         case RT_NEAREST:
-            return launch_shade_t<RT_NEAREST>(table, n_obj, uv, dir, obj, F, out, status, stream);
+            return launch_shade_t<RT_NEAREST, TILED>(table, n_obj, uv, dir, obj, F, T, out, status, stream);
         case RT_ANGULAR_BILINEAR:
-            return launch_shade_t<RT_ANGULAR_BILINEAR>(table, n_obj, uv, dir, obj, F, out, status, stream);
+            return launch_shade_t<RT_ANGULAR_BILINEAR, TILED>(table, n_obj, uv, dir, obj, F, T, out, status, stream);
         default:
-            return launch_shade_t<RT_QUADRILINEAR>(table, n_obj, uv, dir, obj, F, out, status, stream);
+            return launch_shade_t<RT_QUADRILINEAR, TILED>(table, n_obj, uv, dir, obj, F, T, out, status, stream);
     }
 }
 
-template <int FILTER>
+cudaError_t launch_shade(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
+                         int64_t F, int filter, const Tiling& T, float* out, unsigned* status, cudaStream_t stream) {
+    if (T.W > 0) return launch_shade_f<true>(table, n_obj, uv, dir, obj, F, filter, T, out, status, stream);
+    return launch_shade_f<false>(table, n_obj, uv, dir, obj, F, filter, T, out, status, stream);
+}
+
+template <int FILTER, bool TILED>
 static cudaError_t launch_locate_t(const TexDesc* table, int n_obj, const float* uv, const float* dir,
-                                   const int32_t* obj, int64_t F, int32_t* idx, float* coord, unsigned* status,
-                                   cudaStream_t stream) {
-    const unsigned grid = persistent_grid(locate_kernel<FILTER>, kShadeThreads, (F + kChunk - 1) / kChunk);
-    locate_kernel<FILTER><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, idx, coord, status);
+                                   const int32_t* obj, int64_t F, const Tiling& T, int32_t* idx, float* coord,
+                                   unsigned* status, cudaStream_t stream) {
+    const unsigned grid = persistent_grid(locate_kernel<FILTER, TILED>, kShadeThreads,
+                                          chunk_count_host(T, F, kShadeWarps));
+    locate_kernel<FILTER, TILED><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, T, idx, coord,
+                                                                     status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_locate(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
                           int64_t F, int filter, int32_t* idx, float* coord, unsigned* status, cudaStream_t stream) {
+    const Tiling T = flat_tiling();
     switch (filter) {
         case RT_NEAREST:
-            return launch_locate_t<RT_NEAREST>(table, n_obj, uv, dir, obj, F, idx, coord, status, stream);
+            return launch_locate_t<RT_NEAREST, false>(table, n_obj, uv, dir, obj, F, T, idx, coord, status, stream);
         case RT_ANGULAR_BILINEAR:
-            return launch_locate_t<RT_ANGULAR_BILINEAR>(table, n_obj, uv, dir, obj, F, idx, coord, status, stream);
+            return launch_locate_t<RT_ANGULAR_BILINEAR, false>(table, n_obj, uv, dir, obj, F, T, idx, coord, status,
+                                                               stream);
         default:
-            return launch_locate_t<RT_QUADRILINEAR>(table, n_obj, uv, dir, obj, F, idx, coord, status, stream);
+            return launch_locate_t<RT_QUADRILINEAR, false>(table, n_obj, uv, dir, obj, F, T, idx, coord, status,
+                                                           stream);
     }
 }
 

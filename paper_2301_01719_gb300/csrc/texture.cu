@@ -218,7 +218,9 @@ __global__ void __launch_bounds__(kThreads) footprint_kernel(const TexDesc* __re
                                                             const int64_t* __restrict__ word_offset,
                                                             unsigned* status) {
     __shared__ WarpStage<false> stages[kThreads / 32];
-    for_each_fragment<kThreads / 32, false>(uv, dir, obj, nullptr, F, stages, [&](int64_t, const Frag& q, float4) {
+    const Tiling flat = flat_tiling();
+    for_each_fragment<kThreads / 32, false, false>(uv, dir, obj, nullptr, F, flat, stages,
+                                                   [&](int64_t, const Frag& q, float4) {
         TexDesc d;
         if (!fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d)) return;
         Lookup<FILTER> L = locate<FILTER>(d, q.u, q.v, q.x, q.y, q.z);

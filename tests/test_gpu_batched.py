@@ -1,0 +1,113 @@
+"""GPU: the batched (screen-tiled) entry points against the flat ones and the oracle.
+
+Every tile shape walks the same per-fragment arithmetic, so colours, UV and
+direction gradients must be bit-identical to rt_shade / rt_shade_backward;
+texel gradients differ only in the order of FP32 atomic additions."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_2301_01719_gb300 import api
+from parity_util import COLOUR_TOL, ORACLE_FMT, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TILES = [(32, 1, 4, 1), (32, 1, 2, 2), (32, 1, 1, 4), (16, 2, 4, 1), (16, 2, 2, 2), (16, 2, 1, 4), (8, 4, 4, 1),
+         (8, 4, 2, 2), (8, 4, 1, 4), (4, 8, 4, 1), (4, 8, 2, 2), (4, 8, 1, 4)]
+
+
+@pytest.fixture(scope="module")
+def scene():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2301_01719_gb300 import build
+
+    build.build()
+    ctx = api.Context(0)
+    W = H = 48
+    n = 8
+    texs, oids = [], []
+    for k, fmt in enumerate((api.RT_F16, api.RT_F32)):
+        atlas = oracle.fill_field(W, H, n, synth.field_lobes(700 + k))
+        oids.append(api.rt_create_texture(ctx, W, H, n, fmt, api.RT_LAYOUT_ATLAS, to_dev(atlas)))
+        texs.append(oracle.Texture.from_f32(atlas, W, H, n, ORACLE_FMT[fmt]))
+    yield ctx, oids, texs, (W, H, n)
+    ctx.close()
+
+
+def frames(views, height, width, oids):
+    g = synth.sphere_plane_scene(1002, views=views, width=width, height=height)
+    obj = np.where(g.obj >= 0, np.array(oids, np.int32)[np.maximum(g.obj, 0)], -1).astype(np.int32)
+    uv = to_dev(g.uv).reshape(views, height, width, 2)
+    d = to_dev(g.dir).reshape(views, height, width, 3)
+    o = to_dev(obj).reshape(views, height, width)
+    return g, obj, uv, d, o
+
+
+@pytest.mark.parametrize("shape", [(3, 72, 96), (2, 50, 60), (1, 33, 201), (2, 1, 4), (1, 7, 3)])
+def test_batched_equals_flat_every_tile(scene, shape):
+    ctx, oids, texs, _ = scene
+    V, Hh, Ww = shape
+    g, obj, uv, d, o = frames(V, Hh, Ww, oids)
+    for filt in (api.RT_NEAREST, api.RT_ANGULAR_BILINEAR, api.RT_QUADRILINEAR):
+        flat = api.rt_shade(ctx, uv.reshape(-1, 2), d.reshape(-1, 3), o.reshape(-1), filt).cpu().numpy()
+        for t in TILES:
+            api.rt_set_tile(ctx, filt, *t)
+            assert api.rt_get_tile(ctx, filt) == t
+            out = api.rt_shade_batched(ctx, uv, d, o, filt).reshape(-1, 4).cpu().numpy()
+            np.testing.assert_array_equal(out, flat, err_msg=f"tile {t} filter {filt}")
+    assert api.rt_get_error(ctx) == api.RT_OK
+    # against the oracle on the quadrilinear colours
+    ref, _ = oracle.shade(texs, g.uv, g.dir, obj, oracle.QUADRILINEAR)
+    assert np.abs(flat - ref).max() <= COLOUR_TOL
+
+
+def test_batched_backward_equals_flat(scene):
+    ctx, oids, texs, (W, H, n) = scene
+    V, Hh, Ww = 2, 64, 80
+    g, obj, uv, d, o = frames(V, Hh, Ww, oids)
+    rng = np.random.default_rng(1)
+    gout = to_dev(rng.normal(size=(V, Hh, Ww, 4)).astype(np.float32))
+    filt = api.RT_QUADRILINEAR
+
+    def run(batched):
+        duv = torch.empty_like(uv)
+        ddir = torch.empty_like(d)
+        dt = {o_: torch.empty((n, n, H, W, 4), device=uv.device) for o_ in oids}
+        if batched:
+            api.rt_shade_batched_backward(ctx, uv, d, o, filt, gout, dt, duv, ddir)
+        else:
+            api.rt_shade_backward(ctx, uv.reshape(-1, 2), d.reshape(-1, 3), o.reshape(-1), filt, gout.reshape(-1, 4),
+                                  dt, duv.reshape(-1, 2), ddir.reshape(-1, 3))
+        return duv.cpu().numpy(), ddir.cpu().numpy(), {k: v.cpu().numpy() for k, v in dt.items()}
+
+    a = run(False)
+    for t in ((8, 4, 2, 2), (32, 1, 4, 1), (4, 8, 1, 4)):
+        api.rt_set_tile(ctx, filt, *t)
+        b = run(True)
+        np.testing.assert_array_equal(a[0], b[0])
+        np.testing.assert_array_equal(a[1], b[1])
+        for k in a[2]:
+            scale = np.abs(a[2][k]).max()
+            assert np.abs(a[2][k] - b[2][k]).max() <= 1e-5 * max(scale, 1.0)
+    assert api.rt_get_error(ctx) == api.RT_OK
+
+
+def test_autotune_and_invalid_tiles(scene):
+    ctx, oids, _, _ = scene
+    g, obj, uv, d, o = frames(2, 90, 128, oids)
+    tile, ms = api.rt_autotune(ctx, uv, d, o, api.RT_QUADRILINEAR, reps=2)
+    assert tile in TILES and ms > 0
+    assert api.rt_get_tile(ctx, api.RT_QUADRILINEAR) == tile
+    flat = api.rt_shade(ctx, uv.reshape(-1, 2), d.reshape(-1, 3), o.reshape(-1), api.RT_QUADRILINEAR)
+    out = api.rt_shade_batched(ctx, uv, d, o, api.RT_QUADRILINEAR)
+    assert torch.equal(out.reshape(-1, 4), flat)
+    for bad in ((32, 2, 4, 1), (6, 5, 4, 1), (2, 16, 4, 1), (8, 4, 2, 1), (8, 4, 4, 4)):
+        with pytest.raises(api.RadtexError):
+            api.rt_set_tile(ctx, api.RT_QUADRILINEAR, *bad)
+    # empty batches are no-ops
+    e3 = torch.empty((0, 4, 4, 3), device=uv.device)
+    api.rt_shade_batched(ctx, torch.empty((0, 4, 4, 2), device=uv.device), e3,
+                         torch.empty((0, 4, 4), dtype=torch.int32, device=uv.device), api.RT_QUADRILINEAR)
