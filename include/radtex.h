@@ -209,6 +209,29 @@ rt_status rt_autotune(rt_ctx* ctx, const float* uv, const float* dir, const int3
 rt_status rt_footprint(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,
                        rt_filter filter, uint64_t* counts_host, int32_t n_counts, rt_stream_t stream);
 
+/* Largest texel count, summed over a context's objects, that
+ * rt_footprint_noalloc accepts (its bitmap holds one bit per texel: 8 MiB). */
+#define RT_FOOTPRINT_NOALLOC_MAX_TEXELS (1ll << 26)
+
+/* rt_footprint without any device allocation.  The paper has no counterpart:
+ * this is a service of the library.  It is meant for callers that must not
+ * allocate device memory themselves: an application or framework that owns all
+ * device memory through its own allocator or budget, or a per-frame loop in
+ * which cudaMalloc / cudaFree would synchronise the device.  The scratch bitmap
+ * (and a table of per-object offsets) lives in file-scope device arrays that
+ * every GPU loading the library keeps until the process exits; the contexts'
+ * objects may hold at most RT_FOOTPRINT_NOALLOC_MAX_TEXELS texels in total
+ * (RT_ERR_INVALID_ARG otherwise).  counts_dev (device, n_counts uint64 entries,
+ * 8-byte aligned, indexed by object id) receives the distinct-texel counts,
+ * asynchronously on `stream`; nothing is read back to the host.  The first
+ * call on a device looks the arrays' device addresses up (a host-side set-up
+ * done once per device): make that first call before any stream capture.  All
+ * calls share the arrays, and each clears what it uses first, so calls whose
+ * work overlaps on the GPU (other streams, other threads) race and must be
+ * ordered by the caller. */
+rt_status rt_footprint_noalloc(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,
+                               rt_filter filter, uint64_t* counts_dev, int32_t n_counts, rt_stream_t stream);
+
 /* Converts an FP32 4-channel texture buffer of w x h buckets of n x n texels
  * between layouts (device src and dst, which must not overlap). */
 rt_status rt_convert_layout(const float* src, rt_layout src_layout, float* dst, rt_layout dst_layout, int32_t w,

@@ -52,6 +52,7 @@ SIGNATURES = {
     "rt_autotune": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, _I32, _P, ctypes.POINTER(_I32),
                            ctypes.POINTER(ctypes.c_float)]),
     "rt_footprint": (_I32, [_P, _P, _P, _P, _I64, _I32, ctypes.POINTER(ctypes.c_uint64), _I32, _P]),
+    "rt_footprint_noalloc": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, _I32, _P]),
     "rt_convert_layout": (_I32, [_P, _I32, _P, _I32, _I32, _I32, _I32, _P]),
     "rt_get_error": (_I32, [_P, _P, ctypes.POINTER(_I32)]),
     "rt_status_string": (ctypes.c_char_p, [_I32]),

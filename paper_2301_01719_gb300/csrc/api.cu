@@ -86,6 +86,14 @@ rt_status upload_table(rt_ctx* ctx) {
 
 }  // namespace
 
+const rt::TexDesc* rt_internal_host_table(rt_ctx* ctx, int* n_obj) {
+    *n_obj = ctx->n_obj;
+    return ctx->table;
+}
+const rt::TexDesc* rt_internal_device_table(rt_ctx* ctx) { return ctx->d_table; }
+unsigned* rt_internal_status(rt_ctx* ctx) { return ctx->d_status; }
+int rt_internal_device(rt_ctx* ctx) { return ctx->device; }
+
 extern "C" {
 
 const char* rt_status_string(rt_status s) {

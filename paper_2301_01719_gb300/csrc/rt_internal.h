@@ -84,3 +84,9 @@ cudaError_t launch_footprint_mark(const TexDesc* table, int n_obj, const float* 
 cudaError_t launch_popcount(const uint32_t* bitmap, int64_t words, unsigned long long* count, cudaStream_t stream);
 
 }  // namespace rt
+
+// Read-only views of a context for entry points defined outside api.cu.
+const rt::TexDesc* rt_internal_host_table(rt_ctx* ctx, int* n_obj);
+const rt::TexDesc* rt_internal_device_table(rt_ctx* ctx);
+unsigned* rt_internal_status(rt_ctx* ctx);
+int rt_internal_device(rt_ctx* ctx);
