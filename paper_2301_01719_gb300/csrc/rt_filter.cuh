@@ -201,7 +201,7 @@ __device__ __forceinline__ void cp_async_wait() {
 struct ChunkGeom {
     int64_t row0;    // fragment index of (x0, y0)
     int64_t pitch;   // fragment stride between rows
-    int tw, th;
+    int tw, th, tw_log2;
     bool fast;
     int64_t f;       // this lane's fragment, -1 outside the frame / stream
 };
@@ -214,6 +214,7 @@ __device__ __forceinline__ ChunkGeom chunk_geom(const Tiling& T, int64_t F, int6
         g.pitch = kChunk;
         g.tw = kChunk;
         g.th = 1;
+        g.tw_log2 = 5;
         g.fast = g.row0 + kChunk <= F;
         g.f = g.row0 + lane < F ? g.row0 + lane : -1;
         return g;
@@ -228,6 +229,7 @@ __device__ __forceinline__ ChunkGeom chunk_geom(const Tiling& T, int64_t F, int6
     const int y0 = (int)((tyb * T.by + (w >> T.bx_log2)) * T.th);
     g.tw = T.tw;
     g.th = T.th;
+    g.tw_log2 = T.tw_log2;
     g.pitch = T.W;
     g.row0 = (int64_t)view * T.frame + (int64_t)y0 * T.W + x0;
     g.fast = (x0 + T.tw <= T.W) && (y0 + T.th <= T.H) && ((T.W & 3) == 0);
@@ -244,17 +246,22 @@ __device__ __forceinline__ void stage_chunk(const float* __restrict__ uv, const 
                                             const int32_t* __restrict__ obj, const float* __restrict__ extra,
                                             const ChunkGeom& g, int b, WarpStage<EXTRA>& S, int lane) {
     if (g.fast) {
-        // per row: tw/2 pieces of uv, 3 tw/4 of dir, tw/4 of obj (48 per chunk)
-        const int nuv = g.tw >> 1, ndir = (3 * g.tw) >> 2, npr = (3 * g.tw) >> 1;
-        for (int p = lane; p < 48; p += 32) {
-            const int k = p / npr, q = p - k * npr;
-            const int64_t fk = g.row0 + (int64_t)k * g.pitch;
-            if (q < nuv)
-                cp_async16(&S.uv[b][2 * g.tw * k + 4 * q], uv + 2 * fk + 4 * q);
-            else if (q < nuv + ndir)
-                cp_async16(&S.dir[b][3 * g.tw * k + 4 * (q - nuv)], dir + 3 * fk + 4 * (q - nuv));
-            else
-                cp_async16(&S.obj[b][g.tw * k + 4 * (q - nuv - ndir)], obj + fk + 4 * (q - nuv - ndir));
+        // 24 pieces of dir, 16 of uv, 8 of obj: lanes 0-23 take dir, 16-31 uv,
+        // 24-31 obj.  Shared memory holds the chunk in lane order (lane = row
+        // tw + column), so piece q covers shared floats 4q..4q+3 of its stream,
+        // all in one row: row k = (first lane of the piece) >> log2(tw).
+        const int lg = g.tw_log2;
+        if (lane < 24) {
+            const int m = 4 * lane, k = (m / 3) >> lg;
+            cp_async16(&S.dir[b][m], dir + 3 * (g.row0 + (int64_t)k * g.pitch) + (m - 3 * (k << lg)));
+        }
+        if (lane >= 16) {
+            const int m = 4 * (lane - 16), k = (m >> 1) >> lg;
+            cp_async16(&S.uv[b][m], uv + 2 * (g.row0 + (int64_t)k * g.pitch) + (m - 2 * (k << lg)));
+        }
+        if (lane >= 24) {
+            const int m = 4 * (lane - 24), k = m >> lg;
+            cp_async16(&S.obj[b][m], obj + (g.row0 + (int64_t)k * g.pitch) + (m - (k << lg)));
         }
         if (EXTRA) cp_async16(&S.extra[b][lane], extra + 4 * g.f);
     } else {
@@ -344,7 +351,9 @@ __device__ __forceinline__ bool fragment_valid(const TexDesc* __restrict__ table
         atomicOr(status, ST_BAD_OBJ);
         return false;
     }
-    if (!(isfinite(u) && isfinite(v) && finite3(x, y, z))) {
+    // 0 * t is 0 for finite t and NaN for an infinity or a NaN: one test covers all five inputs
+    const float probe = fmaf(z, 0.f, fmaf(y, 0.f, fmaf(x, 0.f, fmaf(v, 0.f, u * 0.f))));
+    if (probe != 0.f) {
         atomicOr(status, ST_NONFINITE);
         return false;
     }
