@@ -62,6 +62,28 @@ def dist_info():
     return rank, world, local
 
 
+def rank_scene_seed(rank: int) -> int:
+    """Every rank renders its own orbit batch of the same size (weak scaling)."""
+    return SCENE_SEED + rank
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """Max of a per-rank scalar (the step time) over all ranks; identity without a process group."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(fragments_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput in Gfrag/s: all ranks' fragments over the slowest rank's time."""
+    return world * fragments_per_rank / (ms * 1e-3) / 1e9
+
+
 def workload_name(a) -> str:
     return (f"sphere+plane {a.width}x{a.height} x {a.views} poses, 2 objects x {a.buckets}^2 buckets x {a.n}^2 "
             f"directions {a.storage.upper()}, {a.filter}")
@@ -308,7 +330,7 @@ def run_radtex(a):
     h_dir = torch.empty((F, 3), dtype=torch.float32, pin_memory=True)
     h_obj = torch.empty((F,), dtype=torch.int32, pin_memory=True)
     t0 = time.perf_counter()
-    g = synth.sphere_plane_scene(SCENE_SEED + rank, views=a.views, width=a.width, height=a.height,
+    g = synth.sphere_plane_scene(rank_scene_seed(rank), views=a.views, width=a.width, height=a.height,
                                  out=(h_uv.numpy(), h_dir.numpy(), h_obj.numpy()))
     scene_s = time.perf_counter() - t0
     shape = (a.views, a.height, a.width)
@@ -387,14 +409,9 @@ def run_radtex(a):
     fwd_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
     zero_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
     bwd_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in ev]))
-    if world > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(total_ms, dev)
     ms_per_step = total_ms / a.steps
-    value = world * F / (ms_per_step * 1e-3) / 1e9
+    value = whole_job_rate(F, world, ms_per_step)
     st = api.rt_get_error(ctx)
     if st != api.RT_OK:
         raise RuntimeError(f"device status after timing: {api.rt_status_string(st)}")
@@ -427,14 +444,8 @@ def run_radtex(a):
             e2e_step()
         s1.record(stream)
         torch.cuda.synchronize()
-        e_ms = s0.elapsed_time(s1) / a.e2e_steps
-        if world > 1:
-            import torch.distributed as dist
-
-            tt = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e_ms = float(tt.item())
-        e2e = {"value": world * F / (e_ms * 1e-3) / 1e9, "unit": "Gfrag/s", "ms_per_step": e_ms,
+        e_ms = max_over_ranks(s0.elapsed_time(s1) / a.e2e_steps, dev)
+        e2e = {"value": whole_job_rate(F, world, e_ms), "unit": "Gfrag/s", "ms_per_step": e_ms,
                "h2d_bytes_per_step": int(h_uv.nbytes + h_dir.nbytes + h_obj.nbytes),
                "d2h_bytes_per_step": int(h_out.nbytes)}
         del h_out
