@@ -79,6 +79,7 @@ typedef enum { RT_LAYOUT_ATLAS = 0, RT_LAYOUT_PLANES = 1 } rt_layout;
 #define RT_BORROW 1          /* use the caller's FP32 buffer in place; no copy */
 /* rt_shade_backward flags */
 #define RT_ACCUMULATE 1      /* add into dL_dtex / dL_duv / dL_ddir instead of overwriting */
+#define RT_DETERMINISTIC 2   /* bit-reproducible texel gradients (fixed-point sums; see rt_prepare_deterministic) */
 
 #define RT_MAX_OBJECTS 1024
 
@@ -157,12 +158,25 @@ rt_status rt_locate(rt_ctx* ctx, const float* uv, const float* dir, const int32_
  *            the filter weights, the Note's clamp, Eq. 3 and Eq. 1b.
  * Without RT_ACCUMULATE the per-fragment outputs are overwritten and each
  * dL_dtex buffer is zeroed first (a full write of the buffer); with it, all
- * outputs are added to.  Subgradients: the floor branch at integer
+ * outputs are added to.  With RT_DETERMINISTIC the texel gradients are summed
+ * in fixed point (rt_prepare_deterministic, which must have been called after
+ * the objects were created) and are bit-identical from run to run; the UV and
+ * direction gradients are per fragment and always deterministic.  Subgradients: the floor branch at integer
  * coordinates, zero where a coordinate is clamped, the |A_x| >= |A_y| branch
  * of Eq. 3 on its diagonal, the identity at A = 0. */
 rt_status rt_shade_backward(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,
                             rt_filter filter, const float* dL_dout, float* const* dL_dtex, int32_t n_dtex,
                             float* dL_duv, float* dL_ddir, int32_t flags, rt_stream_t stream);
+
+/* Prepares the deterministic backward mode (RT_DETERMINISTIC): allocates, for
+ * every live object that has none yet, a buffer of 32 bytes per texel in which
+ * rt_shade_backward sums texel gradients as signed 64-bit fixed-point numbers
+ * with 32 fractional bits (each contribution w * dL/dout rounded once to
+ * nearest; integer addition is associative, so the sums -- and the FP32
+ * gradients converted from them -- do not depend on the order in which the
+ * GPU schedules fragments).  Range |sum| < 2^31, resolution 2^-32.  A
+ * synchronous set-up call; RT_ERR_OOM when the buffers do not fit. */
+rt_status rt_prepare_deterministic(rt_ctx* ctx);
 
 /* Batched synthesis of views x height x width fragments: the same arrays as
  * rt_shade with F = views * height * width, fragment (view, y, x) at index
@@ -231,6 +245,23 @@ rt_status rt_footprint(rt_ctx* ctx, const float* uv, const float* dir, const int
  * ordered by the caller. */
 rt_status rt_footprint_noalloc(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,
                                rt_filter filter, uint64_t* counts_dev, int32_t n_counts, rt_stream_t stream);
+
+/* Texture fitting (no counterpart in the paper, which fills textures by ray
+ * tracing, Eq. 4b; here a texture is fitted to target renders by gradient
+ * descent).  L2 loss of F output colours against targets: dL_dout (device,
+ * F x 4, may be NULL) = scale (out - target) on fragments with obj >= 0 and 0
+ * on background; sums (device, 2 doubles, may be NULL) accumulates the sum of
+ * |out - target|^2 over shaded fragments and their count (the caller zeroes
+ * it).  out, target, dL_dout 16-byte aligned. */
+rt_status rt_l2_loss_grad(const float* out, const float* target, const int32_t* obj, int64_t F, float scale,
+                          float* dL_dout, double* sums, rt_stream_t stream);
+
+/* One Adam step (bias-corrected; step >= 1 is the 1-based step number) on
+ * `count` FP32 values (a multiple of 4): m = b1 m + (1 - b1) g,
+ * v = b2 v + (1 - b2) g^2, param -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * All four arrays device, 16-byte aligned. */
+rt_status rt_adam_step(float* param, const float* grad, float* m, float* v, int64_t count, float lr, float beta1,
+                       float beta2, float eps, int32_t step, rt_stream_t stream);
 
 /* Converts an FP32 4-channel texture buffer of w x h buckets of n x n texels
  * between layouts (device src and dst, which must not overlap). */

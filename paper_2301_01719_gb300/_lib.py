@@ -26,6 +26,7 @@ RT_NEAREST, RT_ANGULAR_BILINEAR, RT_QUADRILINEAR = range(3)
 RT_LAYOUT_ATLAS, RT_LAYOUT_PLANES = range(2)
 RT_BORROW = 1
 RT_ACCUMULATE = 1
+RT_DETERMINISTIC = 2
 RT_MAX_OBJECTS = 1024
 
 _P = ctypes.c_void_p
@@ -47,12 +48,16 @@ SIGNATURES = {
     "rt_shade_batched": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, _P]),
     "rt_shade_batched_backward": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, ctypes.POINTER(_P), _I32, _P,
                                          _P, _I32, _P]),
+    "rt_prepare_deterministic": (_I32, [_P]),
     "rt_set_tile": (_I32, [_P, _I32, _I32, _I32, _I32, _I32]),
     "rt_get_tile": (_I32, [_P, _I32, ctypes.POINTER(_I32)]),
     "rt_autotune": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, _I32, _P, ctypes.POINTER(_I32),
                            ctypes.POINTER(ctypes.c_float)]),
     "rt_footprint": (_I32, [_P, _P, _P, _P, _I64, _I32, ctypes.POINTER(ctypes.c_uint64), _I32, _P]),
     "rt_footprint_noalloc": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, _I32, _P]),
+    "rt_l2_loss_grad": (_I32, [_P, _P, _P, _I64, ctypes.c_float, _P, _P, _P]),
+    "rt_adam_step": (_I32, [_P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                            _I32, _P]),
     "rt_convert_layout": (_I32, [_P, _I32, _P, _I32, _I32, _I32, _I32, _P]),
     "rt_get_error": (_I32, [_P, _P, ctypes.POINTER(_I32)]),
     "rt_status_string": (ctypes.c_char_p, [_I32]),

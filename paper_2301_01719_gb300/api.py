@@ -13,7 +13,7 @@ import torch
 
 from . import _lib
 from ._lib import (RT_ACCUMULATE, RT_ANGULAR_BILINEAR, RT_BF16, RT_BORROW, RT_E4M3_BUCKET_SCALE,  # noqa: F401
-                   RT_ERR_BAD_OBJ_ID, RT_ERR_CUDA, RT_ERR_INVALID_ARG, RT_ERR_NONFINITE, RT_ERR_OOM, RT_ERR_TIMEOUT,
+                   RT_DETERMINISTIC, RT_ERR_BAD_OBJ_ID, RT_ERR_CUDA, RT_ERR_INVALID_ARG, RT_ERR_NONFINITE, RT_ERR_OOM, RT_ERR_TIMEOUT,
                    RT_ERR_UNSUPPORTED, RT_F16, RT_F32, RT_LAYOUT_ATLAS, RT_LAYOUT_PLANES, RT_MAX_OBJECTS, RT_NEAREST,
                    RT_OK, RT_QUADRILINEAR, RadtexError)
 
@@ -181,6 +181,10 @@ def rt_shade_batched_backward(ctx: Context, uv, dirs, obj, filter: int, dL_dout,
               _ptr(dL_dout), arr, n_dtex, _ptr(dL_duv), _ptr(dL_ddir), int(flags), _stream(stream, uv.device))
 
 
+def rt_prepare_deterministic(ctx: Context) -> None:
+    _lib.call("rt_prepare_deterministic", ctx.handle)
+
+
 def rt_set_tile(ctx: Context, filter: int, tw: int, th: int, bx: int, by: int) -> None:
     _lib.call("rt_set_tile", ctx.handle, int(filter), int(tw), int(th), int(bx), int(by))
 
@@ -276,6 +280,37 @@ def rt_convert_layout(src: torch.Tensor, src_layout: int, dst_layout: int, w: in
     _lib.call("rt_convert_layout", _ptr(src), int(src_layout), _ptr(dst), int(dst_layout), int(w), int(h), int(n),
               _stream(stream, src.device))
     return dst
+
+
+def rt_l2_loss_grad(out: torch.Tensor, target: torch.Tensor, obj: torch.Tensor, scale: float,
+                    dL_dout: torch.Tensor | None = None, sums: torch.Tensor | None = None, stream=None) -> None:
+    """dL/dout = scale (out - target) on shaded fragments; sums (float64[2]) += (sum of squares, count)."""
+    F = obj.numel()
+    _check(out, "out", torch.float32, 4)
+    _check(target, "target", torch.float32, 4)
+    _check(obj, "obj", torch.int32)
+    if out.numel() != 4 * F or target.numel() != 4 * F:
+        raise ValueError("out and target must hold F x 4 floats")
+    if dL_dout is not None:
+        _check(dL_dout, "dL_dout", torch.float32, 4)
+        if dL_dout.numel() != 4 * F:
+            raise ValueError("dL_dout must hold F x 4 floats")
+    if sums is not None:
+        _check(sums, "sums", torch.float64)
+        if sums.numel() < 2:
+            raise ValueError("sums holds 2 doubles")
+    _lib.call("rt_l2_loss_grad", _ptr(out), _ptr(target), _ptr(obj), F, float(scale), _ptr(dL_dout), _ptr(sums),
+              _stream(stream, out.device))
+
+
+def rt_adam_step(param: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, lr: float, beta1: float,
+                 beta2: float, eps: float, step: int, stream=None) -> None:
+    for name, t in (("param", param), ("grad", grad), ("m", m), ("v", v)):
+        _check(t, name, torch.float32)
+        if t.numel() != param.numel():
+            raise ValueError("param, grad, m and v must have the same size")
+    _lib.call("rt_adam_step", _ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), float(lr), float(beta1),
+              float(beta2), float(eps), int(step), _stream(stream, param.device))
 
 
 def rt_get_error(ctx: Context, stream=None) -> int:

@@ -24,6 +24,7 @@ struct rt_ctx {
     int64_t bytes[RT_MAX_OBJECTS];
     int n_obj = 0;                       // one past the highest id ever used
     int tile[3][4];                      // per filter: tw, th, bx, by of the batched kernels
+    long long* det[RT_MAX_OBJECTS];      // fixed-point gradient sums of the deterministic mode
 };
 
 namespace {
@@ -130,6 +131,7 @@ rt_status rt_context_create(int cuda_device, rt_ctx** out) {
     std::memset(ctx->owned, 0, sizeof(ctx->owned));
     std::memset(ctx->scales, 0, sizeof(ctx->scales));
     std::memset(ctx->bytes, 0, sizeof(ctx->bytes));
+    std::memset(ctx->det, 0, sizeof(ctx->det));
     for (int f = 0; f < 3; ++f) {
         ctx->tile[f][0] = 8;
         ctx->tile[f][1] = 4;
@@ -169,6 +171,7 @@ void rt_context_destroy(rt_ctx* ctx) {
         for (int o = 0; o < RT_MAX_OBJECTS; ++o) {
             if (ctx->owned[o]) cudaFree(ctx->owned[o]);
             if (ctx->scales[o]) cudaFree(ctx->scales[o]);
+            if (ctx->det[o]) cudaFree(ctx->det[o]);
         }
         cudaFree(ctx->d_table);
         cudaFree(ctx->d_status);
@@ -270,8 +273,10 @@ rt_status rt_destroy_texture(rt_ctx* ctx, int32_t obj_id) {
     cudaError_t e = cudaDeviceSynchronize();
     if (ctx->owned[obj_id]) cudaFree(ctx->owned[obj_id]);
     if (ctx->scales[obj_id]) cudaFree(ctx->scales[obj_id]);
+    if (ctx->det[obj_id]) cudaFree(ctx->det[obj_id]);
     ctx->owned[obj_id] = nullptr;
     ctx->scales[obj_id] = nullptr;
+    ctx->det[obj_id] = nullptr;
     ctx->bytes[obj_id] = 0;
     std::memset(&ctx->table[obj_id], 0, sizeof(TexDesc));
     rt_status st = upload_table(ctx);
@@ -357,28 +362,40 @@ static rt_status shade_backward_impl(rt_ctx* ctx, const float* uv, const float* 
     if ((dL_duv && !aligned16(dL_duv)) || (dL_ddir && !aligned16(dL_ddir))) return RT_ERR_INVALID_ARG;
     if (F > 0 && (!dL_dout || !aligned16(dL_dout))) return RT_ERR_INVALID_ARG;
     const bool accumulate = (flags & RT_ACCUMULATE) != 0;
+    const bool deterministic = (flags & RT_DETERMINISTIC) != 0;
     rt::GradTable grads;
     std::memset(&grads, 0, sizeof(grads));
     bool any = false;
     for (int o = 0; o < n_dtex; ++o) {
         if (!dL_dtex[o]) continue;
         if (o >= RT_MAX_OBJECTS || !ctx->table[o].live || !aligned16(dL_dtex[o])) return RT_ERR_INVALID_ARG;
-        grads.p[o] = dL_dtex[o];
+        if (deterministic && !ctx->det[o]) return RT_ERR_INVALID_ARG;  // rt_prepare_deterministic first
+        grads.p[o] = deterministic ? static_cast<void*>(ctx->det[o]) : static_cast<void*>(dL_dtex[o]);
         any = true;
     }
     DeviceGuard g(ctx->device);
     if (!g.ok) return RT_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
-    if (!accumulate)
+    for (int o = 0; o < n_dtex && e == cudaSuccess; ++o) {
+        if (!grads.p[o]) continue;
+        const TexDesc& d = ctx->table[o];
+        const size_t texels = (size_t)d.plane * d.n * d.n;
+        if (deterministic)
+            e = cudaMemsetAsync(ctx->det[o], 0, 32 * texels, s);
+        else if (!accumulate)
+            e = cudaMemsetAsync(dL_dtex[o], 0, 16 * texels, s);
+    }
+    if (e == cudaSuccess && F > 0)
+        e = rt::launch_backward(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any, dL_duv,
+                                dL_ddir, accumulate, deterministic, ctx->d_status, s);
+    if (deterministic)
         for (int o = 0; o < n_dtex && e == cudaSuccess; ++o)
             if (grads.p[o]) {
                 const TexDesc& d = ctx->table[o];
-                e = cudaMemsetAsync(grads.p[o], 0, (size_t)16 * d.plane * d.n * d.n, s);
+                e = rt::launch_fixed_to_float(ctx->det[o], dL_dtex[o], (int64_t)d.plane * d.n * d.n * 4, accumulate,
+                                              s);
             }
-    if (e == cudaSuccess && F > 0)
-        e = rt::launch_backward(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any, dL_duv,
-                                dL_ddir, accumulate, ctx->d_status, s);
     return cuda_status(e);
 }
 
@@ -425,6 +442,21 @@ rt_status rt_shade_batched_backward(rt_ctx* ctx, const float* uv, const float* d
     if (F > 0 && !frames_tiling(ctx, views, height, width, filter, &T)) return RT_ERR_INVALID_ARG;
     return shade_backward_impl(ctx, uv, dir, obj, F, filter, T, dL_dout, dL_dtex, n_dtex, dL_duv, dL_ddir, flags,
                                stream);
+}
+
+rt_status rt_prepare_deterministic(rt_ctx* ctx) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    for (int o = 0; o < ctx->n_obj; ++o) {
+        const TexDesc& d = ctx->table[o];
+        if (!d.live || ctx->det[o]) continue;
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, (size_t)32 * d.plane * d.n * d.n);
+        if (e != cudaSuccess) return cuda_status(e);
+        ctx->det[o] = static_cast<long long*>(p);
+    }
+    return RT_OK;
 }
 
 rt_status rt_set_tile(rt_ctx* ctx, rt_filter filter, int32_t tw, int32_t th, int32_t bx, int32_t by) {

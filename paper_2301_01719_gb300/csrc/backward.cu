@@ -20,8 +20,21 @@ struct CoordGrad {
     float gu, gv, gs, gt;  // dL/d(weight coordinate) of the u, v, s, t axes
 };
 
-template <int FILTER, int FMT, int LAYOUT>
-__device__ __forceinline__ CoordGrad backward_taps(const TexDesc& d, const Lookup<FILTER>& L, float4 g, float* grad,
+// Deterministic mode: each contribution w g_c is rounded once to a signed
+// 64-bit fixed-point number with 32 fractional bits and added with integer
+// atomics, which are associative, so the sums do not depend on the order in
+// which fragments arrive.
+constexpr float kFixedScale = 4294967296.0f;  // 2^32
+
+__device__ __forceinline__ void red_add_fixed4(unsigned long long* addr, float4 v) {
+    atomicAdd(addr + 0, (unsigned long long)__float2ll_rn(v.x * kFixedScale));
+    atomicAdd(addr + 1, (unsigned long long)__float2ll_rn(v.y * kFixedScale));
+    atomicAdd(addr + 2, (unsigned long long)__float2ll_rn(v.z * kFixedScale));
+    atomicAdd(addr + 3, (unsigned long long)__float2ll_rn(v.w * kFixedScale));
+}
+
+template <int FILTER, int FMT, int LAYOUT, bool DET>
+__device__ __forceinline__ CoordGrad backward_taps(const TexDesc& d, const Lookup<FILTER>& L, float4 g, void* grad,
                                                    bool coord_grads) {
     CoordGrad cg = {0.f, 0.f, 0.f, 0.f};
     const float wu[2] = {1.f - L.u.w, L.u.w}, wv[2] = {1.f - L.v.w, L.v.w};
@@ -37,7 +50,11 @@ __device__ __forceinline__ CoordGrad backward_taps(const TexDesc& d, const Looku
                         if (w == 0.f) continue;
                         int64_t idx = texel_index<LAYOUT>(d, a ? L.u.k1 : L.u.k0, b ? L.v.k1 : L.v.k0,
                                                           p ? L.s.k1 : L.s.k0, q ? L.t.k1 : L.t.k0);
-                        red_add_v4(grad + 4 * idx, make_float4(w * g.x, w * g.y, w * g.z, w * g.w));
+                        const float4 c = make_float4(w * g.x, w * g.y, w * g.z, w * g.w);
+                        if (DET)
+                            red_add_fixed4(static_cast<unsigned long long*>(grad) + 4 * idx, c);
+                        else
+                            red_add_v4(static_cast<float*>(grad) + 4 * idx, c);
                     }
     }
     if (FILTER == RT_NEAREST || !coord_grads) return cg;
@@ -69,20 +86,20 @@ __device__ __forceinline__ CoordGrad backward_taps(const TexDesc& d, const Looku
     return cg;
 }
 
-template <int FILTER>
-__device__ __forceinline__ CoordGrad backward_any(const TexDesc& d, const Lookup<FILTER>& L, float4 g, float* grad,
+template <int FILTER, bool DET>
+__device__ __forceinline__ CoordGrad backward_any(const TexDesc& d, const Lookup<FILTER>& L, float4 g, void* grad,
                                                   bool coord_grads) {
     switch (d.fmt) {
         case RT_F16:
-            return backward_taps<FILTER, RT_F16, RT_LAYOUT_PLANES>(d, L, g, grad, coord_grads);
+            return backward_taps<FILTER, RT_F16, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
         case RT_BF16:
-            return backward_taps<FILTER, RT_BF16, RT_LAYOUT_PLANES>(d, L, g, grad, coord_grads);
+            return backward_taps<FILTER, RT_BF16, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
         case RT_E4M3_BUCKET_SCALE:
-            return backward_taps<FILTER, RT_E4M3_BUCKET_SCALE, RT_LAYOUT_PLANES>(d, L, g, grad, coord_grads);
+            return backward_taps<FILTER, RT_E4M3_BUCKET_SCALE, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
         default:
             if (d.layout == RT_LAYOUT_ATLAS)
-                return backward_taps<FILTER, RT_F32, RT_LAYOUT_ATLAS>(d, L, g, grad, coord_grads);
-            return backward_taps<FILTER, RT_F32, RT_LAYOUT_PLANES>(d, L, g, grad, coord_grads);
+                return backward_taps<FILTER, RT_F32, RT_LAYOUT_ATLAS, DET>(d, L, g, grad, coord_grads);
+            return backward_taps<FILTER, RT_F32, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
     }
 }
 
@@ -118,7 +135,7 @@ __device__ __forceinline__ float3 direction_grad(float Ix, float Iy, float Iz, f
     return make_float3(k * gAx - m * Ix, k * gAy - m * Iy, -m * zp);
 }
 
-template <int FILTER, bool TILED>
+template <int FILTER, bool TILED, bool DET>
 __global__ void __launch_bounds__(kBackThreads) backward_kernel(
     const TexDesc* __restrict__ table, int n_obj, const float* __restrict__ uv, const float* __restrict__ dir,
     const int32_t* __restrict__ obj, int64_t F, Tiling tiling, const float* __restrict__ dL_dout,
@@ -133,8 +150,8 @@ __global__ void __launch_bounds__(kBackThreads) backward_kernel(
         TexDesc d;
         if (fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d)) {
             Lookup<FILTER> L = locate<FILTER>(d, q.u, q.v, q.x, q.y, q.z);
-            float* grad = any_grad ? grads.p[q.o] : nullptr;
-            CoordGrad cg = backward_any<FILTER>(d, L, go, grad, coord_grads);
+            void* grad = any_grad ? grads.p[q.o] : nullptr;
+            CoordGrad cg = backward_any<FILTER, DET>(d, L, go, grad, coord_grads);
             if (FILTER == RT_QUADRILINEAR) {
                 float cu = fmaf(q.u, d.fW, -0.5f), cv = fmaf(q.v, d.fH, -0.5f);
                 guv.x = (cu > -1.0f && cu < d.fW) ? cg.gu * d.fW : 0.f;
@@ -170,47 +187,72 @@ __global__ void __launch_bounds__(kBackThreads) backward_kernel(
     });
 }
 
-template <int FILTER, bool TILED>
+template <int FILTER, bool TILED, bool DET>
 static cudaError_t launch_backward_t(const TexDesc* table, int n_obj, const float* uv, const float* dir,
                                      const int32_t* obj, int64_t F, const Tiling& T, const float* dL_dout,
                                      const GradTable& grads, bool any_grad, float* dL_duv, float* dL_ddir,
                                      bool accumulate, unsigned* status, cudaStream_t stream) {
-    const unsigned grid = persistent_grid(backward_kernel<FILTER, TILED>, kBackThreads,
+    const unsigned grid = persistent_grid(backward_kernel<FILTER, TILED, DET>, kBackThreads,
                                           chunk_count_host(T, F, kBackWarps));
-    backward_kernel<FILTER, TILED><<<grid, kBackThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, T, dL_dout,
-                                                                      grads, any_grad, dL_duv, dL_ddir, accumulate,
-                                                                      status);
+    backward_kernel<FILTER, TILED, DET><<<grid, kBackThreads, 0, stream>>>(
+        table, n_obj, uv, dir, obj, F, T, dL_dout, grads, any_grad, dL_duv, dL_ddir, accumulate, status);
     return cudaGetLastError();
 }
 
-template <bool TILED>
+template <bool TILED, bool DET>
 static cudaError_t launch_backward_f(const TexDesc* table, int n_obj, const float* uv, const float* dir,
                                      const int32_t* obj, int64_t F, int filter, const Tiling& T,
                                      const float* dL_dout, const GradTable& grads, bool any_grad, float* dL_duv,
                                      float* dL_ddir, bool accumulate, unsigned* status, cudaStream_t stream) {
     switch (filter) {
         case RT_NEAREST:
-            return launch_backward_t<RT_NEAREST, TILED>(table, n_obj, uv, dir, obj, F, T, dL_dout, grads, any_grad,
-                                                        dL_duv, dL_ddir, accumulate, status, stream);
-        case RT_ANGULAR_BILINEAR:
-            return launch_backward_t<RT_ANGULAR_BILINEAR, TILED>(table, n_obj, uv, dir, obj, F, T, dL_dout, grads,
-                                                                 any_grad, dL_duv, dL_ddir, accumulate, status,
-                                                                 stream);
-        default:
-            return launch_backward_t<RT_QUADRILINEAR, TILED>(table, n_obj, uv, dir, obj, F, T, dL_dout, grads,
+            return launch_backward_t<RT_NEAREST, TILED, DET>(table, n_obj, uv, dir, obj, F, T, dL_dout, grads,
                                                              any_grad, dL_duv, dL_ddir, accumulate, status, stream);
+        case RT_ANGULAR_BILINEAR:
+            return launch_backward_t<RT_ANGULAR_BILINEAR, TILED, DET>(table, n_obj, uv, dir, obj, F, T, dL_dout,
+                                                                      grads, any_grad, dL_duv, dL_ddir, accumulate,
+                                                                      status, stream);
+        default:
+            return launch_backward_t<RT_QUADRILINEAR, TILED, DET>(table, n_obj, uv, dir, obj, F, T, dL_dout, grads,
+                                                                  any_grad, dL_duv, dL_ddir, accumulate, status,
+                                                                  stream);
     }
 }
 
 cudaError_t launch_backward(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
                             int64_t F, int filter, const Tiling& T, const float* dL_dout, const GradTable& grads,
-                            bool any_grad, float* dL_duv, float* dL_ddir, bool accumulate, unsigned* status,
-                            cudaStream_t stream) {
-    if (T.W > 0)
-        return launch_backward_f<true>(table, n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any_grad, dL_duv,
-                                       dL_ddir, accumulate, status, stream);
-    return launch_backward_f<false>(table, n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any_grad, dL_duv,
-                                    dL_ddir, accumulate, status, stream);
+                            bool any_grad, float* dL_duv, float* dL_ddir, bool accumulate, bool deterministic,
+                            unsigned* status, cudaStream_t stream) {
+    if (T.W > 0) {
+        if (deterministic)
+            return launch_backward_f<true, true>(table, n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any_grad,
+                                                 dL_duv, dL_ddir, accumulate, status, stream);
+        return launch_backward_f<true, false>(table, n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any_grad,
+                                              dL_duv, dL_ddir, accumulate, status, stream);
+    }
+    if (deterministic)
+        return launch_backward_f<false, true>(table, n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any_grad,
+                                              dL_duv, dL_ddir, accumulate, status, stream);
+    return launch_backward_f<false, false>(table, n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any_grad,
+                                           dL_duv, dL_ddir, accumulate, status, stream);
+}
+
+// Fixed-point sums (deterministic mode) -> FP32 gradients, added to or overwriting dst.
+__global__ void fixed_to_float_kernel(const long long* __restrict__ acc, float* __restrict__ dst, int64_t count,
+                                      bool accumulate) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
+        float v = (float)((double)acc[k] * (1.0 / 4294967296.0));
+        dst[k] = accumulate ? dst[k] + v : v;
+    }
+}
+
+cudaError_t launch_fixed_to_float(const long long* acc, float* dst, int64_t count, bool accumulate,
+                                  cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    int64_t blocks = (count + 255) / 256;
+    fixed_to_float_kernel<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, stream>>>(acc, dst, count,
+                                                                                          accumulate);
+    return cudaGetLastError();
 }
 
 }  // namespace rt

@@ -59,7 +59,7 @@ inline int64_t chunk_count_host(const Tiling& T, int64_t F, int warps) {
 // Pointers to the FP32 texel-gradient buffers, indexed by object id, passed by
 // value as a kernel parameter (no device allocation, capturable in a graph).
 struct GradTable {
-    float* p[RT_MAX_OBJECTS];
+    void* p[RT_MAX_OBJECTS];  // float* (FP32 sums) or long long* (fixed-point sums, deterministic mode)
 };
 
 cudaError_t launch_shade(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
@@ -68,8 +68,10 @@ cudaError_t launch_locate(const TexDesc* table, int n_obj, const float* uv, cons
                           int64_t F, int filter, int32_t* idx, float* coord, unsigned* status, cudaStream_t stream);
 cudaError_t launch_backward(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
                             int64_t F, int filter, const Tiling& T, const float* dL_dout, const GradTable& grads,
-                            bool any_grad, float* dL_duv, float* dL_ddir, bool accumulate, unsigned* status,
-                            cudaStream_t stream);
+                            bool any_grad, float* dL_duv, float* dL_ddir, bool accumulate, bool deterministic,
+                            unsigned* status, cudaStream_t stream);
+cudaError_t launch_fixed_to_float(const long long* acc, float* dst, int64_t count, bool accumulate,
+                                  cudaStream_t stream);
 
 cudaError_t launch_encode(const float* src, int src_layout, void* dst, float* scale, int W, int H, int n, int fmt,
                           cudaStream_t stream);

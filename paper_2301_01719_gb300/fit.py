@@ -1,0 +1,167 @@
+"""Fitting a radiance texture to target renders by gradient descent.
+
+The paper fills radiance textures from ray-traced data (Eq. 4b); this module
+fits one to a set of target views instead, which is what the differentiable
+lookup is for.  A step is: forward synthesis of every view (rt_shade_batched),
+the L2 loss and its gradient (rt_l2_loss_grad), the backward pass into the
+texel gradients (rt_shade_batched_backward) and an Adam update
+(rt_adam_step) -- all in libradtex's kernels, on the FP32 texture the context
+borrows (RT_BORROW) in the planes layout.  Checkpoints hold the texture, the
+Adam moments, the step count and a hash of the configuration; with
+deterministic=True (fixed-point texel gradients) a run resumed from a
+checkpoint is bit-identical to an uninterrupted one.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+
+import torch
+
+from . import api
+
+
+class TextureFit:
+    def __init__(self, ctx: api.Context, w: int, h: int, n: int, init: float = 0.0, lr: float = 1e-2,
+                 betas=(0.9, 0.999), eps: float = 1e-8, filt: int = api.RT_QUADRILINEAR, deterministic: bool = False):
+        dev = torch.device("cuda", ctx.device)
+        self.ctx = ctx
+        self.w, self.h, self.n = int(w), int(h), int(n)
+        self.lr, self.betas, self.eps, self.filt = float(lr), tuple(betas), float(eps), int(filt)
+        self.deterministic = bool(deterministic)
+        self.tex = torch.full((n, n, h, w, 4), float(init), dtype=torch.float32, device=dev)
+        self.oid = api.rt_create_texture(ctx, w, h, n, api.RT_F32, api.RT_LAYOUT_PLANES, self.tex, api.RT_BORROW)
+        self.grad = torch.zeros_like(self.tex)
+        self.m = torch.zeros_like(self.tex)
+        self.v = torch.zeros_like(self.tex)
+        self.step_count = 0
+        self.sums = torch.zeros(2, dtype=torch.float64, device=dev)
+        if self.deterministic:
+            api.rt_prepare_deterministic(ctx)
+
+    def config(self) -> dict:
+        return {"w": self.w, "h": self.h, "n": self.n, "lr": self.lr, "betas": list(self.betas), "eps": self.eps,
+                "filter": self.filt, "deterministic": self.deterministic}
+
+    def config_hash(self) -> str:
+        return hashlib.sha256(json.dumps(self.config(), sort_keys=True).encode()).hexdigest()[:16]
+
+    def shaded_count(self, obj: torch.Tensor) -> int:
+        """Number of fragments with an object (the loss's normaliser), counted by the loss kernel."""
+        s = torch.zeros(2, dtype=torch.float64, device=obj.device)
+        z = torch.zeros((*obj.shape, 4), dtype=torch.float32, device=obj.device)
+        api.rt_l2_loss_grad(z, z, obj, 0.0, None, s)
+        return int(s[1].item())
+
+    def step(self, uv, dirs, obj, target, count: int, out=None, dL_dout=None):
+        """One fitting step over a batch of views (tensors shaped (V, H, W, k)); the
+        G-buffer's object ids name this fitter's texture (self.oid) or background.
+        L = 1/(2 * 4 count) sum over shaded fragments and channels of (out - target)^2.
+        Returns the loss as a device tensor (no synchronisation)."""
+        if out is None:
+            out = torch.empty((*obj.shape, 4), dtype=torch.float32, device=obj.device)
+        if dL_dout is None:
+            dL_dout = torch.empty_like(out)
+        api.rt_shade_batched(self.ctx, uv, dirs, obj, self.filt, out)
+        self.sums.zero_()
+        scale = 1.0 / (4.0 * max(count, 1))
+        api.rt_l2_loss_grad(out, target, obj, scale, dL_dout, self.sums)
+        flags = api.RT_DETERMINISTIC if self.deterministic else 0
+        api.rt_shade_batched_backward(self.ctx, uv, dirs, obj, self.filt, dL_dout, {self.oid: self.grad}, None, None,
+                                      flags)
+        self.step_count += 1
+        api.rt_adam_step(self.tex, self.grad, self.m, self.v, self.lr, self.betas[0], self.betas[1], self.eps,
+                         self.step_count)
+        return 0.5 * self.sums[0] * scale
+
+    def render(self, uv, dirs, obj):
+        return api.rt_shade_batched(self.ctx, uv, dirs, obj, self.filt)
+
+    @staticmethod
+    def psnr(out: torch.Tensor, target: torch.Tensor, obj: torch.Tensor, peak: float = 1.0) -> float:
+        mask = (obj >= 0).unsqueeze(-1)
+        se = ((out.double() - target.double()) ** 2 * mask).sum().item()
+        cnt = 4 * mask.sum().item()
+        mse = se / max(cnt, 1)
+        return float("inf") if mse == 0 else 10.0 * torch.log10(torch.tensor(peak * peak / mse)).item()
+
+    def state_dict(self) -> dict:
+        return {"tex": self.tex.detach().cpu().clone(), "m": self.m.cpu().clone(), "v": self.v.cpu().clone(),
+                "step": self.step_count, "config": self.config(), "config_hash": self.config_hash()}
+
+    def save(self, path: str) -> None:
+        torch.save(self.state_dict(), path)
+
+    def load(self, path: str) -> None:
+        st = torch.load(path, map_location="cpu", weights_only=False)
+        if st["config_hash"] != self.config_hash():
+            raise ValueError("checkpoint was written by a different fitting configuration")
+        # the context keeps reading self.tex in place: copy into it, do not rebind it
+        self.tex.copy_(st["tex"])
+        self.m.copy_(st["m"])
+        self.v.copy_(st["v"])
+        self.step_count = int(st["step"])
+
+
+def main(argv=None):
+    """The fitting workload: a w x h x n^2 FP32 texture fitted to `views` target
+    renders of the quad from a hidden multi-lobe field; prints one JSON line with
+    the step throughput and the PSNR before and after."""
+    import argparse
+    import time
+
+    import numpy as np
+
+    import synth
+
+    p = argparse.ArgumentParser(description=main.__doc__.split(";")[0])
+    p.add_argument("--buckets", type=int, default=512)
+    p.add_argument("--n", type=int, default=16)
+    p.add_argument("--views", type=int, default=32)
+    p.add_argument("--size", type=int, default=1024)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--lr", type=float, default=1e-2)
+    p.add_argument("--seed", type=int, default=5005)
+    p.add_argument("--deterministic", action="store_true")
+    a = p.parse_args(argv)
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    g = synth.quad_views(a.seed, a.views, a.size, a.size)
+    lobes = synth.field_lobes(a.seed + 777)
+    target = np.zeros((g.F, 4), np.float32)
+    hit = g.obj >= 0
+    target[hit] = synth.eval_field_lobes(lobes, g.uv[hit], g.dir[hit]).astype(np.float32)
+    shape = (a.views, a.size, a.size)
+    uv = torch.from_numpy(g.uv).to(dev).view(*shape, 2)
+    d = torch.from_numpy(g.dir).to(dev).view(*shape, 3)
+    o = torch.from_numpy(g.obj).to(dev).view(*shape)
+    t = torch.from_numpy(target).to(dev).view(*shape, 4)
+    setup_s = time.perf_counter() - t0
+    ctx = api.Context(0)
+    fit = TextureFit(ctx, a.buckets, a.buckets, a.n, lr=a.lr, deterministic=a.deterministic)
+    o = torch.where(o >= 0, torch.full_like(o, fit.oid), o)
+    count = fit.shaded_count(o)
+    out = torch.empty((*shape, 4), dtype=torch.float32, device=dev)
+    dL = torch.empty_like(out)
+    psnr0 = TextureFit.psnr(fit.render(uv, d, o), t, o)
+    fit.step(uv, d, o, t, count, out, dL)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps - 1):
+        loss = fit.step(uv, d, o, t, count, out, dL)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(a.steps - 1, 1)
+    psnr1 = TextureFit.psnr(fit.render(uv, d, o), t, o)
+    F = int(np.prod(shape))
+    print(json.dumps({"workload": f"fit {a.buckets}^2 x {a.n}^2 FP32 texture to {a.views} views of {a.size}^2",
+                      "steps": a.steps, "ms_per_step": ms, "gfrag_per_s_fwd_bwd": F / (ms * 1e-3) / 1e9,
+                      "fragments_per_step": F, "shaded_fragments": count, "loss": float(loss),
+                      "psnr_start_db": psnr0, "psnr_end_db": psnr1, "deterministic": a.deterministic,
+                      "setup_s": setup_s}))
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -8,5 +8,6 @@ projection, no disc-to-square mapping, no filtering.  All draws use numpy's
 PCG64 generator with the seed given by the caller, and geometry is computed in
 FP64 then rounded to FP32, the G-buffer precision.
 """
-from .scenes import GBuffer, quad_scene, sphere_plane_scene, sphere_plane_poses, voronoi_planes_scene  # noqa: F401
-from .fields import field_lobes, bucket_lobe_params  # noqa: F401
+from .scenes import (GBuffer, quad_scene, quad_views, sphere_plane_poses, sphere_plane_scene,  # noqa: F401
+                     voronoi_planes_scene)
+from .fields import field_lobes, bucket_lobe_params, eval_field_lobes  # noqa: F401

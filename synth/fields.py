@@ -77,3 +77,24 @@ def bucket_lobe_params(seed: int, W: int, H: int, cells: int = 8, jitter: float 
     out[..., 3:6] = d
     out[..., 6] = p
     return out
+
+
+def eval_field_lobes(lobes: np.ndarray, uv: np.ndarray, dirs: np.ndarray, chunk: int = 1 << 20) -> np.ndarray:
+    """The multi-lobe field at arbitrary (u, v, I) in FP64 (target renders of the
+    fitting workload): F x 4."""
+    lobes = np.asarray(lobes, dtype=np.float64).reshape(-1, 11)
+    uv = np.asarray(uv)
+    dirs = np.asarray(dirs)
+    out = np.zeros((uv.shape[0], 4))
+    for a in range(0, uv.shape[0], chunk):
+        u = uv[a:a + chunk, 0].astype(np.float64)
+        v = uv[a:a + chunk, 1].astype(np.float64)
+        I = dirs[a:a + chunk].astype(np.float64)
+        acc = np.zeros((u.shape[0], 4))
+        for P in lobes:
+            spatial = 0.5 + 0.5 * np.cos(2.0 * np.pi * (P[4] * u + P[5] * v) + P[6])
+            c = I @ P[7:10]
+            lobe = np.where(c > 0.0, np.maximum(c, 0.0) ** P[10], 0.0)
+            acc += P[None, 0:4] * (spatial * lobe)[:, None]
+        out[a:a + chunk] = acc
+    return out

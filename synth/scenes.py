@@ -262,3 +262,11 @@ def voronoi_planes_scene(seed: int, n_objects: int = 64, views: int = 4, width: 
         d[sl] = dd
         obj[sl] = oo
     return GBuffer(uv, d, obj, width, height, hi - lo)
+
+
+def quad_views(seed: int, views: int, width: int, height: int, fov_deg: float = 50.0) -> GBuffer:
+    """`views` pinhole views of the quad (each drawn like quad_scene with seed
+    seed + k), stacked view-major."""
+    gs = [quad_scene(seed + k, width, height, fov_deg) for k in range(views)]
+    return GBuffer(np.concatenate([g.uv for g in gs]), np.concatenate([g.dir for g in gs]),
+                   np.concatenate([g.obj for g in gs]), width, height, views)
