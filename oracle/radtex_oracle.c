@@ -288,6 +288,7 @@ static double decode_e4m3(uint8_t c) { return unpack_format(c, &FMT_E4M3, 0); }
 
 /* Encode `count` FP32 values to F32 (copy), F16 or BF16 codes. */
 void oracle_encode(int32_t fmt, int64_t count, const float* x, void* codes) {
+#pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < count; ++k) {
         if (fmt == OR_F32)
             ((float*)codes)[k] = x[k];
@@ -302,6 +303,7 @@ void oracle_encode(int32_t fmt, int64_t count, const float* x, void* codes) {
 
 /* Decode `count` codes of a format to FP64, exactly. */
 void oracle_decode(int32_t fmt, int64_t count, const void* codes, double* out) {
+#pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < count; ++k) {
         if (fmt == OR_F32)
             out[k] = (double)((const float*)codes)[k];

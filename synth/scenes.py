@@ -202,7 +202,8 @@ def voronoi_planes_scene(seed: int, n_objects: int = 64, views: int = 4, width: 
     aspect = width / height
     xs = (2.0 * (np.arange(width) + 0.5) / width - 1.0) * th * aspect
     ys = (1.0 - 2.0 * (np.arange(height) + 0.5) / height) * th
-    for k, v in enumerate(range(lo, hi)):
+    def one(k):
+        v = lo + k
         sl = slice(k * per, (k + 1) * per)
         # Voronoi region of every pixel (screen coordinates in [0, 1]^2), chunked by rows.
         region = np.empty((height, width), dtype=np.int32)
@@ -261,6 +262,10 @@ def voronoi_planes_scene(seed: int, n_objects: int = 64, views: int = 4, width: 
         uv[sl] = uvv
         d[sl] = dd
         obj[sl] = oo
+
+    # numpy releases the GIL inside large array operations: views render in parallel threads
+    with ThreadPoolExecutor(max(1, min(hi - lo, os.cpu_count() or 1))) as ex:
+        list(ex.map(one, range(hi - lo)))
     return GBuffer(uv, d, obj, width, height, hi - lo)
 
 

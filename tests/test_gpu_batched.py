@@ -111,3 +111,40 @@ def test_autotune_and_invalid_tiles(scene):
     e3 = torch.empty((0, 4, 4, 3), device=uv.device)
     api.rt_shade_batched(ctx, torch.empty((0, 4, 4, 2), device=uv.device), e3,
                          torch.empty((0, 4, 4), dtype=torch.int32, device=uv.device), api.RT_QUADRILINEAR)
+
+
+def test_cuda_graph_capture_replays_identically(scene):
+    """A step (forward, backward with zeroed texel gradients) captured in a CUDA graph
+    replays to the same results as eager launches: the entry points neither allocate
+    nor synchronise."""
+    ctx, oids, _, (W, H, n) = scene
+    g, obj, uv, d, o = frames(2, 72, 96, oids)
+    filt = api.RT_QUADRILINEAR
+    out = torch.empty((2, 72, 96, 4), device=uv.device)
+    duv = torch.empty_like(uv)
+    ddir = torch.empty_like(d)
+    dt = {k: torch.empty((n, n, H, W, 4), device=uv.device) for k in oids}
+
+    def step(stream=None):
+        api.rt_shade_batched(ctx, uv, d, o, filt, out, stream=stream)
+        api.rt_shade_batched_backward(ctx, uv, d, o, filt, out, dt, duv, ddir, 0, stream=stream)
+
+    step()
+    torch.cuda.synchronize()
+    eager = [out.clone(), duv.clone(), ddir.clone()]
+    eager_dt = {k: v.clone() for k, v in dt.items()}
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            step(s)
+    for t in (out, duv, ddir, *dt.values()):
+        t.zero_()
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    for a_, b_ in zip(eager, (out, duv, ddir)):
+        assert torch.equal(a_, b_)
+    for k in dt:
+        assert torch.allclose(eager_dt[k], dt[k], rtol=1e-5, atol=1e-6)
+    assert api.rt_get_error(ctx) == api.RT_OK

@@ -1,0 +1,113 @@
+"""GPU parity at the benchmark's full size and launch configuration: the sphere +
+ground plane, 1920x1080 x 60 poses (124.4 M fragments), two 1024^2 x 16^2 FP16
+textures, quadrilinear, through rt_shade_batched / rt_shade_batched_backward
+with the autotuned tile -- exactly what bench.py times.
+
+The oracle cannot shade 124 M fragments in a test, so it checks samples one by
+one: 200 000 random fragments plus every fragment of a few 64 x 64 screen tiles.
+Properties that hold at any size are checked on the whole step: the texel
+gradients of every channel sum to the sum of dL/dout over shaded fragments, and
+background fragments get zero colour and zero gradients."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_2301_01719_gb300 import api
+from parity_util import COLOUR_TOL, compare_indices, index_taus
+
+pytestmark = pytest.mark.gpu
+
+VIEWS, HEIGHT, WIDTH, BUCKETS, N = 60, 1080, 1920, 1024, 16
+SCENE_SEED, TEX_SEEDS = 1002, (2001, 2002)
+
+
+@pytest.fixture(scope="module")
+def full():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2301_01719_gb300 import build
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    ctx = api.Context(0)
+    textures, oids = [], []
+    for seed in TEX_SEEDS:
+        atlas = oracle.fill_bucket_lobes(BUCKETS, BUCKETS, N, synth.bucket_lobe_params(seed, BUCKETS, BUCKETS))
+        src = torch.from_numpy(atlas).to(dev)
+        oids.append(api.rt_create_texture(ctx, BUCKETS, BUCKETS, N, api.RT_F16, api.RT_LAYOUT_ATLAS, src))
+        del src
+        textures.append(oracle.Texture.from_f32(atlas, BUCKETS, BUCKETS, N, oracle.F16))
+        del atlas
+    assert oids == [0, 1]
+    g = synth.sphere_plane_scene(SCENE_SEED, views=VIEWS, width=WIDTH, height=HEIGHT)
+    shape = (VIEWS, HEIGHT, WIDTH)
+    uv = torch.from_numpy(g.uv).to(dev).view(*shape, 2)
+    d = torch.from_numpy(g.dir).to(dev).view(*shape, 3)
+    o = torch.from_numpy(g.obj).to(dev).view(*shape)
+    out = torch.empty((*shape, 4), device=dev)
+    tile, _ = api.rt_autotune(ctx, uv, d, o, api.RT_QUADRILINEAR, out, reps=2)
+    api.rt_shade_batched(ctx, uv, d, o, api.RT_QUADRILINEAR, out)
+    assert api.rt_get_error(ctx) == api.RT_OK
+    rng = np.random.default_rng(7)
+    sel = [rng.choice(g.F, 200000, replace=False)]
+    per = HEIGHT * WIDTH
+    for view, y0, x0 in ((0, 500, 900), (17, 700, 300), (33, 100, 1700), (59, 1016, 1856)):
+        yy, xx = np.meshgrid(np.arange(y0, y0 + 64), np.arange(x0, x0 + 64), indexing="ij")
+        sel.append(view * per + (yy * WIDTH + xx).reshape(-1))
+    sel = np.unique(np.concatenate(sel))
+    yield dict(ctx=ctx, textures=textures, g=g, uv=uv, d=d, o=o, out=out, sel=sel, tile=tile)
+    ctx.close()
+
+
+def test_fullsize_colours_and_indices(full):
+    g, sel = full["g"], full["sel"]
+    out = full["out"].view(-1, 4)[torch.from_numpy(sel).to(full["out"].device)].cpu().numpy()
+    ref, flags = oracle.shade(full["textures"], g.uv[sel], g.dir[sel], g.obj[sel], oracle.QUADRILINEAR)
+    assert flags == 0
+    assert np.abs(out - ref).max() <= COLOUR_TOL
+    # indices of the sample through rt_locate, against the oracle's
+    uv = torch.from_numpy(g.uv[sel]).to(full["out"].device)
+    d = torch.from_numpy(g.dir[sel]).to(full["out"].device)
+    o = torch.from_numpy(g.obj[sel]).to(full["out"].device)
+    idx, coord = api.rt_locate(full["ctx"], uv, d, o, api.RT_QUADRILINEAR)
+    oi, oc, _ = oracle.locate(full["textures"], g.uv[sel], g.dir[sel], g.obj[sel], oracle.QUADRILINEAR)
+    _, band = compare_indices(idx.cpu().numpy(), coord.cpu().numpy().astype(np.float64), oi, oc,
+                              index_taus(BUCKETS, BUCKETS, N), mask=g.obj[sel] >= 0)
+    assert band <= 0.01 * int((g.obj[sel] >= 0).sum())  # about 0.4 % expected from the band widths
+    # background fragments of the whole step are exactly zero
+    bg = full["o"] < 0
+    assert torch.count_nonzero(full["out"][bg]) == 0
+
+
+def test_fullsize_backward(full):
+    ctx, g, sel = full["ctx"], full["g"], full["sel"]
+    uv, d, o, out = full["uv"], full["d"], full["o"], full["out"]
+    dev = out.device
+    dtex = {k: torch.empty((N, N, BUCKETS, BUCKETS, 4), device=dev) for k in (0, 1)}
+    duv = torch.empty_like(uv)
+    ddir = torch.empty_like(d)
+    api.rt_shade_batched_backward(ctx, uv, d, o, api.RT_QUADRILINEAR, out, dtex, duv, ddir)
+    assert api.rt_get_error(ctx) == api.RT_OK
+    # sum rule over the whole step: sum over texels == sum of dL/dout (= out) over shaded fragments
+    shaded = (o >= 0).unsqueeze(-1)
+    for k in (0, 1):
+        lhs = dtex[k].double().sum(dim=(0, 1, 2, 3))
+        rhs = (out.double() * (o == k).unsqueeze(-1)).sum(dim=(0, 1, 2))
+        torch.testing.assert_close(lhs, rhs, rtol=1e-4, atol=1e-3)
+    assert torch.count_nonzero(duv * ~shaded) == 0 and torch.count_nonzero(ddir * ~shaded) == 0
+    # per-fragment UV and direction gradients of the sample, against the oracle
+    gout = out.view(-1, 4)[torch.from_numpy(sel).to(dev)].cpu().numpy().astype(np.float64)
+    _, guv, gdir, _ = oracle.shade_backward(full["textures"], g.uv[sel], g.dir[sel], g.obj[sel],
+                                            oracle.QUADRILINEAR, gout, want_tex=False)
+    got_uv = duv.view(-1, 2)[torch.from_numpy(sel).to(dev)].cpu().numpy()
+    got_dir = ddir.view(-1, 3)[torch.from_numpy(sel).to(dev)].cpu().numpy()
+    _, oc, _ = oracle.locate(full["textures"], g.uv[sel], g.dir[sel], g.obj[sel], oracle.QUADRILINEAR)
+    far = (np.abs(oc - np.round(oc)) > 1e-3).all(axis=1) & (g.obj[sel] >= 0)
+    B = oracle.squarify(oracle.equisolid(g.dir[sel].astype(np.float64)))
+    far &= (np.abs(np.abs(B) - (1 - 1.0 / N)) > 1e-3).all(axis=1)
+    assert far.sum() > 50000
+    for got_c, ref_c in ((got_uv, guv), (got_dir, gdir)):
+        scale = np.abs(ref_c[far]).max()
+        assert np.all(np.abs(got_c[far] - ref_c[far]) <= 1e-3 * np.abs(ref_c[far]) + 1e-5 * scale)
