@@ -33,6 +33,65 @@ __device__ __forceinline__ void red_add_fixed4(unsigned long long* addr, float4 
     atomicAdd(addr + 3, (unsigned long long)__float2ll_rn(v.w * kFixedScale));
 }
 
+// QUADRILINEAR on the PLANES layout: the four in-bucket texels select four
+// planes (64-bit bases), the four buckets four spatial offsets (32-bit), shared
+// by the 16 reductions and the 16 loads.
+template <int FMT, bool DET>
+__device__ __forceinline__ CoordGrad backward_quadrilinear_planes(const TexDesc& d, const Lookup<RT_QUADRILINEAR>& L,
+                                                                  float4 g, void* grad, bool coord_grads) {
+    const int64_t P = d.plane;
+    const int64_t p00 = (int64_t)(L.t.k0 * d.n + L.s.k0) * P;
+    const int64_t ds = (int64_t)(L.s.k1 - L.s.k0) * P, dt = (int64_t)(L.t.k1 - L.t.k0) * d.n * P;
+    const int64_t pl[4] = {p00, p00 + ds, p00 + dt, p00 + dt + ds};  // (s0,t0) (s1,t0) (s0,t1) (s1,t1)
+    const int o[4] = {L.v.k0 * d.W + L.u.k0, L.v.k0 * d.W + L.u.k1, L.v.k1 * d.W + L.u.k0,
+                      L.v.k1 * d.W + L.u.k1};  // (u0,v0) (u1,v0) (u0,v1) (u1,v1)
+    const float wu[2] = {1.f - L.u.w, L.u.w}, wv[2] = {1.f - L.v.w, L.v.w};
+    const float ws[2] = {1.f - L.s.w, L.s.w}, wt[2] = {1.f - L.t.w, L.t.w};
+    if (grad) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float w = wu[b & 1] * wv[b >> 1] * ws[k & 1] * wt[k >> 1];
+                if (w == 0.f) continue;
+                const int64_t idx = pl[k] + o[b];
+                const float4 c = make_float4(w * g.x, w * g.y, w * g.z, w * g.w);
+                if (DET)
+                    red_add_fixed4(static_cast<unsigned long long*>(grad) + 4 * idx, c);
+                else
+                    red_add_v4(static_cast<float*>(grad) + 4 * idx, c);
+            }
+    }
+    CoordGrad cg = {0.f, 0.f, 0.f, 0.f};
+    if (!coord_grads) return cg;
+    const f32x2 g_rg = pack2(g.x, g.y), g_ba = pack2(g.z, g.w);
+    auto lerpf = [](float a, float b, float w) { return fmaf(w, b - a, a); };
+    float c[4], cs[4], ct[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const float sc = FMT == RT_E4M3_BUCKET_SCALE ? __ldg(d.scale + o[b]) : 1.0f;
+        float p[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const P4 T = load_texelP<FMT>(d.base, pl[k] + o[b], sc);
+            f32x2 q;
+            asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(q) : "l"(T.rg), "l"(g_rg));
+            asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(q) : "l"(T.ba), "l"(g_ba), "l"(q));
+            const float2 h = unpack2(q);
+            p[k] = h.x + h.y;
+        }
+        const float x0 = lerpf(p[0], p[1], L.s.w), x1 = lerpf(p[2], p[3], L.s.w);
+        c[b] = lerpf(x0, x1, L.t.w);
+        cs[b] = lerpf(p[1] - p[0], p[3] - p[2], L.t.w);
+        ct[b] = x1 - x0;
+    }
+    cg.gu = lerpf(c[1] - c[0], c[3] - c[2], L.v.w);
+    cg.gv = lerpf(c[2], c[3], L.u.w) - lerpf(c[0], c[1], L.u.w);
+    cg.gs = lerpf(lerpf(cs[0], cs[1], L.u.w), lerpf(cs[2], cs[3], L.u.w), L.v.w);
+    cg.gt = lerpf(lerpf(ct[0], ct[1], L.u.w), lerpf(ct[2], ct[3], L.u.w), L.v.w);
+    return cg;
+}
+
 template <int FILTER, int FMT, int LAYOUT, bool DET>
 __device__ __forceinline__ CoordGrad backward_taps(const TexDesc& d, const Lookup<FILTER>& L, float4 g, void* grad,
                                                    bool coord_grads) {
@@ -58,37 +117,64 @@ __device__ __forceinline__ CoordGrad backward_taps(const TexDesc& d, const Looku
                     }
     }
     if (FILTER == RT_NEAREST || !coord_grads) return cg;
+    // Coordinate gradients need only g . T per texel: every derivative of the
+    // colour is a weighted sum of texels, so each texel is projected onto g as
+    // soon as it is loaded and the lerps run on scalars.
+    const f32x2 g_rg = pack2(g.x, g.y), g_ba = pack2(g.z, g.w);
+    auto proj = [&](const P4& T) {
+        f32x2 p;
+        asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(p) : "l"(T.rg), "l"(g_rg));
+        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(p) : "l"(T.ba), "l"(g_ba), "l"(p));
+        const float2 q = unpack2(p);
+        return q.x + q.y;
+    };
+    auto lerpf = [](float a, float b, float w) { return fmaf(w, b - a, a); };
     if (FILTER == RT_ANGULAR_BILINEAR) {
-        float4 t00, t10, t01, t11;
-        load_quad<FMT, LAYOUT>(d, L.u.k0, L.v.k0, L.s, L.t, t00, t10, t01, t11);
-        float4 x0 = lerp4(t00, t10, L.s.w), x1 = lerp4(t01, t11, L.s.w);
-        cg.gs = dot4(g, lerp4(sub4(t10, t00), sub4(t11, t01), L.t.w));
-        cg.gt = dot4(g, sub4(x1, x0));
+        P4 t00, t10, t01, t11;
+        load_quadP<FMT, LAYOUT>(d, L.u.k0, L.v.k0, L.s, L.t, t00, t10, t01, t11);
+        const float p00 = proj(t00), p10 = proj(t10), p01 = proj(t01), p11 = proj(t11);
+        cg.gs = lerpf(p10 - p00, p11 - p01, L.t.w);
+        cg.gt = lerpf(p01, p11, L.s.w) - lerpf(p00, p10, L.s.w);
         return cg;
     }
-    float4 c[2][2], ds[2][2], dt[2][2];
+    // bucket (a, b) of the 2 x 2 spatial footprint: value c_ab, d/ds, d/dt (all projected on g)
+    float c[2][2], cs[2][2], ct[2][2];
 #pragma unroll
     for (int b = 0; b < 2; ++b)
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
-            float4 t00, t10, t01, t11;
-            load_quad<FMT, LAYOUT>(d, a ? L.u.k1 : L.u.k0, b ? L.v.k1 : L.v.k0, L.s, L.t, t00, t10, t01, t11);
-            float4 x0 = lerp4(t00, t10, L.s.w), x1 = lerp4(t01, t11, L.s.w);
-            c[b][a] = lerp4(x0, x1, L.t.w);
-            ds[b][a] = lerp4(sub4(t10, t00), sub4(t11, t01), L.t.w);
-            dt[b][a] = sub4(x1, x0);
+            P4 t00, t10, t01, t11;
+            load_quadP<FMT, LAYOUT>(d, a ? L.u.k1 : L.u.k0, b ? L.v.k1 : L.v.k0, L.s, L.t, t00, t10, t01, t11);
+            const float p00 = proj(t00), p10 = proj(t10), p01 = proj(t01), p11 = proj(t11);
+            const float x0 = lerpf(p00, p10, L.s.w), x1 = lerpf(p01, p11, L.s.w);
+            c[b][a] = lerpf(x0, x1, L.t.w);
+            cs[b][a] = lerpf(p10 - p00, p11 - p01, L.t.w);
+            ct[b][a] = x1 - x0;
         }
-    float4 y0 = lerp4(c[0][0], c[0][1], L.u.w), y1 = lerp4(c[1][0], c[1][1], L.u.w);
-    cg.gu = dot4(g, lerp4(sub4(c[0][1], c[0][0]), sub4(c[1][1], c[1][0]), L.v.w));
-    cg.gv = dot4(g, sub4(y1, y0));
-    cg.gs = dot4(g, lerp4(lerp4(ds[0][0], ds[0][1], L.u.w), lerp4(ds[1][0], ds[1][1], L.u.w), L.v.w));
-    cg.gt = dot4(g, lerp4(lerp4(dt[0][0], dt[0][1], L.u.w), lerp4(dt[1][0], dt[1][1], L.u.w), L.v.w));
+    cg.gu = lerpf(c[0][1] - c[0][0], c[1][1] - c[1][0], L.v.w);
+    cg.gv = lerpf(c[1][0], c[1][1], L.u.w) - lerpf(c[0][0], c[0][1], L.u.w);
+    cg.gs = lerpf(lerpf(cs[0][0], cs[0][1], L.u.w), lerpf(cs[1][0], cs[1][1], L.u.w), L.v.w);
+    cg.gt = lerpf(lerpf(ct[0][0], ct[0][1], L.u.w), lerpf(ct[1][0], ct[1][1], L.u.w), L.v.w);
     return cg;
 }
 
 template <int FILTER, bool DET>
 __device__ __forceinline__ CoordGrad backward_any(const TexDesc& d, const Lookup<FILTER>& L, float4 g, void* grad,
                                                   bool coord_grads) {
+    if constexpr (FILTER == RT_QUADRILINEAR) {
+        if (d.layout == RT_LAYOUT_PLANES) {
+            switch (d.fmt) {
+                case RT_F16:
+                    return backward_quadrilinear_planes<RT_F16, DET>(d, L, g, grad, coord_grads);
+                case RT_BF16:
+                    return backward_quadrilinear_planes<RT_BF16, DET>(d, L, g, grad, coord_grads);
+                case RT_E4M3_BUCKET_SCALE:
+                    return backward_quadrilinear_planes<RT_E4M3_BUCKET_SCALE, DET>(d, L, g, grad, coord_grads);
+                default:
+                    return backward_quadrilinear_planes<RT_F32, DET>(d, L, g, grad, coord_grads);
+            }
+        }
+    }
     switch (d.fmt) {
         case RT_F16:
             return backward_taps<FILTER, RT_F16, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
