@@ -71,6 +71,9 @@ def lib() -> ctypes.CDLL:
                 "oracle_eval_field": (None, [P, I32, I64, P, P, P]),
                 "oracle_fill_field": (None, [I32, I32, I32, P, I32, P]),
                 "oracle_fill_bucket_lobes": (None, [I32, I32, I32, P, P]),
+                "oracle_bake": (None, [I32, I32, I32, I32, P, ctypes.c_double, P, P, P]),
+                "oracle_bake_ray": (None, [I32, I32, P, ctypes.c_double, ctypes.c_double, I32, I32, P, P, P]),
+                "oracle_trace": (None, [P, I64, P, P, P]),
                 "oracle_num_threads": (I32, []),
                 "oracle_set_num_threads": (None, [I32]),
             }
@@ -309,3 +312,62 @@ def num_threads() -> int:
 
 def set_num_threads(k: int) -> None:
     lib().oracle_set_num_threads(int(k))
+
+
+# --------------------------------------------------------------------------
+# Baking (Section 2.2, Eq. 4a, Eq. 4b): texel centre -> reflection vector ->
+# ray traced through an analytic sphere + plane + sky scene (reading R10).
+# --------------------------------------------------------------------------
+
+SURFACE_SPHERE, SURFACE_PLANE = 0, 1
+# (key, width) in the order of the oracle's flat parameter array
+_SCENE_KEYS = (("sphere_centre", 3), ("sphere_radius", 1), ("plane_height", 1), ("plane_half_extent", 1),
+               ("sphere_albedo", 3), ("sphere_reflectance", 1), ("plane_albedo", 3), ("plane_reflectance", 1),
+               ("plane_frequency", 1), ("sun_direction", 3), ("sun_rgb", 3), ("sun_exponent", 1),
+               ("sky_zenith", 3), ("sky_horizon", 3), ("ambient", 1), ("fog", 1), ("ray_offset", 1))
+
+
+def scene_array(scene: dict) -> np.ndarray:
+    """The scene dictionary as the oracle's flat parameter array (31 doubles)."""
+    out = []
+    for key, width in _SCENE_KEYS:
+        v = np.atleast_1d(np.asarray(scene[key], np.float64))
+        assert v.size == width, key
+        out.extend(v.tolist())
+    return np.array(out, np.float64)
+
+
+def bake(W: int, H: int, n: int, surface: int, scene: dict, delta: float | None = None):
+    """Baked texture as an FP64 atlas ((H n) x (W n) x 4), following Eq. 4a and
+    Eq. 4b per texel centre.  With `delta`, also the per-texel range (lo, hi) of
+    the value over rays perturbed by +-delta (origin along T, B; direction along
+    T, B, N, renormalised)."""
+    S = scene_array(scene)
+    val = np.empty((H * n, W * n, 4))
+    lo = hi = None
+    if delta is not None:
+        lo = np.empty_like(val)
+        hi = np.empty_like(val)
+    lib().oracle_bake(W, H, n, surface, _p(S), float(delta or 0.0), _p(val), _p(lo), _p(hi))
+    return val if delta is None else (val, lo, hi)
+
+
+def bake_ray(n: int, surface: int, scene: dict, u: float, v: float, s: int, t: int):
+    """World-space origin P, direction d of the reflection ray of texel (s, t) at
+    (u, v), and the tangent frame (rows T, B, N)."""
+    S = scene_array(scene)
+    P = np.empty(3)
+    d = np.empty(3)
+    F = np.empty((3, 3))
+    lib().oracle_bake_ray(n, surface, _p(S), float(u), float(v), int(s), int(t), _p(P), _p(d), _p(F))
+    return P, d, F
+
+
+def trace(scene: dict, P, d) -> np.ndarray:
+    """Radiance and fog transmittance (k x 4) along rays P + t d (rows of 3)."""
+    S = scene_array(scene)
+    P = _c(P, np.float64).reshape(-1, 3)
+    d = _c(d, np.float64).reshape(-1, 3)
+    out = np.empty((P.shape[0], 4))
+    lib().oracle_trace(_p(S), P.shape[0], _p(P), _p(d), _p(out))
+    return out

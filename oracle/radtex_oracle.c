@@ -767,6 +767,232 @@ void oracle_fill_bucket_lobes(int32_t W, int32_t H, int32_t n, const float* para
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Baking (Section 2.2, Eq. 4a and Eq. 4b).  Each texel centre B of a bucket  */
+/* goes back to the equisolid vector A (Eq. 4a) and to the reflection vector  */
+/* R (Eq. 4b); the ray from the bucket's surface point along R, taken to      */
+/* world space with the surface's tangent frame, is traced through an        */
+/* analytic scene and the radiance it brings back is stored.  The paper       */
+/* fixes only the direction; reading R10 fixes the scene and its shading, all */
+/* smooth so that the hit decisions are the only discontinuities:             */
+/*   lit(N)    = a + (1 - a) max(0, N . L)                                     */
+/*   sky(d)    = K_h + (K_z - K_h)(1/2 + d_y/2) + S max(0, d . L)^p            */
+/*   albedo    : sphere rho_s; plane rho_p (3/4 + cos(w x) cos(w z) / 4)       */
+/*   trace(P,d): nearest of the sphere's entering root and the plane hit with  */
+/*               t > eps; a miss gives (sky(d), 0), a hit at t gives          */
+/*               (f C + (1 - f) sky(d), f), f = exp(-k t), C = albedo lit(N_h) */
+/*   texel     = (albedo(P) lit(N(P)) + rho_r trace_rgb(P, R), trace_alpha).   */
+/* The bucket's surface point is the bucket centre ((i+1/2)/w, (j+1/2)/h) on  */
+/* the sphere (lat-long: phi = 2 pi u - pi, theta = pi v, frame T along       */
+/* dP/dphi, B along dP/dtheta, N outward) or on the plane y = h_p (x = 2 e u  */
+/* - e, z = 2 e v - e, frame (+x, +z, +y)).                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Scene parameters, one flat array of doubles. */
+enum {
+    BK_SPHERE_C = 0, BK_SPHERE_R = 3, BK_PLANE_Y = 4, BK_PLANE_E = 5, BK_SPHERE_ALB = 6, BK_SPHERE_REFL = 9,
+    BK_PLANE_ALB = 10, BK_PLANE_REFL = 13, BK_PLANE_FREQ = 14, BK_SUN_DIR = 15, BK_SUN_RGB = 18, BK_SUN_EXP = 21,
+    BK_SKY_ZEN = 22, BK_SKY_HOR = 25, BK_AMBIENT = 28, BK_FOG = 29, BK_EPS = 30, BK_COUNT = 31
+};
+#define OR_SURFACE_SPHERE 0
+#define OR_SURFACE_PLANE 1
+
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static double lit(const double* S, const double N[3]) {
+    double c = dot3(N, S + BK_SUN_DIR);
+    return S[BK_AMBIENT] + (1.0 - S[BK_AMBIENT]) * (c > 0.0 ? c : 0.0);
+}
+
+static void sky(const double* S, const double d[3], double out[3]) {
+    double h = 0.5 + 0.5 * d[1];
+    double c = dot3(d, S + BK_SUN_DIR);
+    double sun = c > 0.0 ? pow(c, S[BK_SUN_EXP]) : 0.0;
+    for (int k = 0; k < 3; ++k)
+        out[k] = S[BK_SKY_HOR + k] + (S[BK_SKY_ZEN + k] - S[BK_SKY_HOR + k]) * h + S[BK_SUN_RGB + k] * sun;
+}
+
+static void plane_albedo(const double* S, const double x[3], double out[3]) {
+    double w = S[BK_PLANE_FREQ];
+    double m = 0.75 + 0.25 * cos(w * x[0]) * cos(w * x[2]);
+    for (int k = 0; k < 3; ++k) out[k] = S[BK_PLANE_ALB + k] * m;
+}
+
+/* Surface point and tangent frame F = (T, B, N) of bucket coordinate (u, v). */
+static void surface_frame(const double* S, int surface, double u, double v, double P[3], double F[3][3]) {
+    static const double PI = 3.14159265358979323846264338327950288;
+    if (surface == OR_SURFACE_SPHERE) {
+        double phi = 2.0 * PI * u - PI, theta = PI * v;
+        double r = S[BK_SPHERE_R];
+        double N[3] = {sin(theta) * cos(phi), cos(theta), sin(theta) * sin(phi)};
+        double T[3] = {-sin(phi), 0.0, cos(phi)};
+        double B[3] = {cos(theta) * cos(phi), -sin(theta), cos(theta) * sin(phi)};
+        for (int k = 0; k < 3; ++k) {
+            P[k] = S[BK_SPHERE_C + k] + r * N[k];
+            F[0][k] = T[k];
+            F[1][k] = B[k];
+            F[2][k] = N[k];
+        }
+    } else {
+        double e = S[BK_PLANE_E];
+        P[0] = 2.0 * e * u - e;
+        P[1] = S[BK_PLANE_Y];
+        P[2] = 2.0 * e * v - e;
+        double T[3] = {1.0, 0.0, 0.0}, B[3] = {0.0, 0.0, 1.0}, N[3] = {0.0, 1.0, 0.0};
+        for (int k = 0; k < 3; ++k) {
+            F[0][k] = T[k];
+            F[1][k] = B[k];
+            F[2][k] = N[k];
+        }
+    }
+}
+
+/* Own (view-independent) colour of a surface point. */
+static void surface_base(const double* S, int surface, const double P[3], const double N[3], double out[3]) {
+    double l = lit(S, N);
+    if (surface == OR_SURFACE_SPHERE) {
+        for (int k = 0; k < 3; ++k) out[k] = S[BK_SPHERE_ALB + k] * l;
+    } else {
+        plane_albedo(S, P, out);
+        for (int k = 0; k < 3; ++k) out[k] *= l;
+    }
+}
+
+/* Radiance along the ray P + t d (d unit), and its fog transmittance. */
+static void trace(const double* S, const double P[3], const double d[3], double out[4]) {
+    double eps = S[BK_EPS];
+    double t_best = INFINITY;
+    int hit = -1;
+    /* sphere: |P + t d - c|^2 = r^2, entering root t = -b - sqrt(b^2 - q) */
+    double o[3] = {P[0] - S[BK_SPHERE_C], P[1] - S[BK_SPHERE_C + 1], P[2] - S[BK_SPHERE_C + 2]};
+    double b = dot3(o, d);
+    double q = dot3(o, o) - S[BK_SPHERE_R] * S[BK_SPHERE_R];
+    double disc = b * b - q;
+    if (disc > 0.0) {
+        double t = -b - sqrt(disc);
+        if (t > eps) {
+            t_best = t;
+            hit = OR_SURFACE_SPHERE;
+        }
+    }
+    /* plane y = h_p, from above or below */
+    if (d[1] != 0.0) {
+        double t = (S[BK_PLANE_Y] - P[1]) / d[1];
+        if (t > eps && t < t_best) {
+            t_best = t;
+            hit = OR_SURFACE_PLANE;
+        }
+    }
+    double K[3];
+    sky(S, d, K);
+    if (hit < 0) {
+        for (int k = 0; k < 3; ++k) out[k] = K[k];
+        out[3] = 0.0;
+        return;
+    }
+    double X[3] = {P[0] + t_best * d[0], P[1] + t_best * d[1], P[2] + t_best * d[2]};
+    double C[3];
+    if (hit == OR_SURFACE_SPHERE) {
+        double r = S[BK_SPHERE_R];
+        double Nh[3] = {(X[0] - S[BK_SPHERE_C]) / r, (X[1] - S[BK_SPHERE_C + 1]) / r, (X[2] - S[BK_SPHERE_C + 2]) / r};
+        double l = lit(S, Nh);
+        for (int k = 0; k < 3; ++k) C[k] = S[BK_SPHERE_ALB + k] * l;
+    } else {
+        double up[3] = {0.0, 1.0, 0.0};
+        double l = lit(S, up);
+        plane_albedo(S, X, C);
+        for (int k = 0; k < 3; ++k) C[k] *= l;
+    }
+    double f = exp(-S[BK_FOG] * t_best);
+    for (int k = 0; k < 3; ++k) out[k] = f * C[k] + (1.0 - f) * K[k];
+    out[3] = f;
+}
+
+static void normalize3(double v[3]) {
+    double m = sqrt(dot3(v, v));
+    v[0] /= m;
+    v[1] /= m;
+    v[2] /= m;
+}
+
+/* Bakes one object: val[(atlas texel) * 4 + c] in the atlas order of reading
+ * R4.  With lo/hi non-NULL it also returns, per texel and channel, the range
+ * of the texel over ten perturbed rays (origin moved by +-delta along T and B,
+ * direction tilted by +-delta along T, B and N and renormalised): the spread
+ * of the exact value over inputs one FP32 rounding chain away, which marks
+ * texels whose ray grazes a hit decision. */
+void oracle_bake(int32_t W, int32_t H, int32_t n, int32_t surface, const double* S, double delta, double* val,
+                 double* lo, double* hi) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t bk = 0; bk < (int64_t)W * H; ++bk) {
+        int64_t i = bk % W, j = bk / W;
+        double u = ((double)i + 0.5) / W, v = ((double)j + 0.5) / H;
+        double P[3], F[3][3], base[3];
+        surface_frame(S, surface, u, v, P, F);
+        surface_base(S, surface, P, F[2], base);
+        double refl = surface == OR_SURFACE_SPHERE ? S[BK_SPHERE_REFL] : S[BK_PLANE_REFL];
+        for (int64_t t = 0; t < n; ++t)
+            for (int64_t s = 0; s < n; ++s) {
+                double B[2] = {texel_centre(s, n), texel_centre(t, n)};
+                double A[2], R[3];
+                unsquarify(B, A);  /* Eq. 4a */
+                reflection(A, R);  /* Eq. 4b, tangent space */
+                double d[3];
+                for (int k = 0; k < 3; ++k) d[k] = R[0] * F[0][k] + R[1] * F[1][k] + R[2] * F[2][k];
+                double tr[4], out[4];
+                trace(S, P, d, tr);
+                for (int k = 0; k < 3; ++k) out[k] = base[k] + refl * tr[k];
+                out[3] = tr[3];
+                int64_t e = ((j * n + t) * (int64_t)W * n + (i * n + s)) * 4;
+                for (int c = 0; c < 4; ++c) val[e + c] = out[c];
+                if (!lo) continue;
+                double mn[4], mx[4];
+                for (int c = 0; c < 4; ++c) mn[c] = mx[c] = out[c];
+                for (int m = 0; m < 10; ++m) {
+                    double Pp[3] = {P[0], P[1], P[2]}, dp[3] = {d[0], d[1], d[2]};
+                    double sg = (m & 1) ? -delta : delta;
+                    if (m < 4) {
+                        for (int k = 0; k < 3; ++k) Pp[k] += sg * F[m >> 1][k];
+                    } else {
+                        for (int k = 0; k < 3; ++k) dp[k] += sg * F[(m - 4) >> 1][k];
+                        normalize3(dp);
+                    }
+                    double tp[4];
+                    trace(S, Pp, dp, tp);
+                    double o4[4] = {base[0] + refl * tp[0], base[1] + refl * tp[1], base[2] + refl * tp[2], tp[3]};
+                    for (int c = 0; c < 4; ++c) {
+                        if (o4[c] < mn[c]) mn[c] = o4[c];
+                        if (o4[c] > mx[c]) mx[c] = o4[c];
+                    }
+                }
+                for (int c = 0; c < 4; ++c) {
+                    lo[e + c] = mn[c];
+                    hi[e + c] = mx[c];
+                }
+            }
+    }
+}
+
+/* The world-space reflection ray of texel (s, t) at bucket coordinate (u, v):
+ * origin P, direction d and the frame rows T, B, N (9 doubles), for the pins. */
+void oracle_bake_ray(int32_t n, int32_t surface, const double* S, double u, double v, int32_t s, int32_t t,
+                     double* P, double* d, double* frame) {
+    double F[3][3];
+    surface_frame(S, surface, u, v, P, F);
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) frame[3 * r + k] = F[r][k];
+    double B[2] = {texel_centre(s, n), texel_centre(t, n)};
+    double A[2], R[3];
+    unsquarify(B, A);
+    reflection(A, R);
+    for (int k = 0; k < 3; ++k) d[k] = R[0] * F[0][k] + R[1] * F[1][k] + R[2] * F[2][k];
+}
+
+/* trace() for given rays (rows of 3): out count x 4. */
+void oracle_trace(const double* S, int64_t count, const double* P, const double* d, double* out) {
+    for (int64_t k = 0; k < count; ++k) trace(S, P + 3 * k, d + 3 * k, out + 4 * k);
+}
+
 int32_t oracle_num_threads(void) {
 #ifdef _OPENMP
     return (int32_t)omp_get_max_threads();
