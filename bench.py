@@ -53,8 +53,9 @@ def parse_args(argv=None):
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--workload", choices=["sphere-plane", "voronoi64"], default="sphere-plane",
-                   help="voronoi64: 64 objects of uneven sizes, 4 views of 3840x2160, forward in a CUDA graph")
+    p.add_argument("--workload", choices=["sphere-plane", "voronoi64", "bake"], default="sphere-plane",
+                   help="voronoi64: 64 objects of uneven sizes, 4 views of 3840x2160, forward in a CUDA graph; "
+                        "bake: rt_bake of the sphere-plane workload's two textures")
     p.add_argument("--objects", type=int, default=64)
     p.add_argument("--mem-fraction", type=float, default=0.7,
                    help="voronoi64: largest share of free device memory the textures may take")
@@ -522,6 +523,203 @@ def run_radtex(a):
         torch.distributed.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# Bake workload: rt_bake of the sphere-plane workload's two textures.
+# ---------------------------------------------------------------------------
+
+BAKE_METRIC = "baked texels/s (Gtexel/s), sphere + plane textures"
+BAKE_SCENE_SEED = 2001
+# FP32 operations per texel of the bake, counted from its formulas (add, mul,
+# compare = 1, FMA = 2, each sqrt / divide / pow / exp / cos = 1): Eq. 4a and
+# Eq. 2c/4b 21, rotation to world space 15, the traced ray 86 (sphere and plane
+# tests 26, sky 24, hit point and its shading 26, fog and blend 10), final
+# combination 6.
+BAKE_FLOPS_PER_TEXEL = 128
+SMS, FP32_LANES_PER_SM, NOMINAL_SM_MHZ = 152, 128, 2070.0
+
+
+def bake_name(a) -> str:
+    return f"bake 2 objects (sphere, plane) x {a.buckets}^2 buckets x {a.n}^2 directions {a.storage.upper()}"
+
+
+def bake_cpu_baseline(a, scene, seconds: float, steps: int | None = None):
+    """The oracle's bake on a bounded random sample of texels of both objects."""
+    import oracle
+
+    rng = np.random.default_rng(9)
+    W = H = a.buckets
+    n = a.n
+
+    def sample(k):
+        return np.stack([rng.integers(0, W, k), rng.integers(0, H, k), rng.integers(0, n, k),
+                         rng.integers(0, n, k)], 1).astype(np.int32)
+
+    probe = sample(20000)
+    t0 = time.perf_counter()
+    oracle.bake_texels(W, H, n, oracle.SURFACE_SPHERE, scene, probe, None)
+    rate = probe.shape[0] / max(time.perf_counter() - t0, 1e-6)
+    k = int(max(20000, rate * seconds / 2))
+    q = sample(k)
+    times = []
+    for _ in range(steps or 1):
+        t0 = time.perf_counter()
+        for surf in (oracle.SURFACE_SPHERE, oracle.SURFACE_PLANE):
+            oracle.bake_texels(W, H, n, surf, scene, q, None)
+        times.append(time.perf_counter() - t0)
+    return 2 * k, times, oracle.num_threads()
+
+
+def run_bake(a):
+    import torch
+
+    import synth
+    from paper_2301_01719_gb300 import api, build
+
+    rank, world, local = dist_info()
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        scene = synth.bake_scene(BAKE_SCENE_SEED)
+        count, times, cores = bake_cpu_baseline(a, scene, 2.0, a.warmup + a.steps)
+        mean = float(np.mean(times[a.warmup:]))
+        value = count / mean / 1e9
+        print(json.dumps({
+            "impl": "reference", "metric": BAKE_METRIC, "value": value, "unit": "Gtexel/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": bake_name(a), "sample_texels": count},
+            "cpu_baseline": {"value": value, "unit": "Gtexel/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{count} random texels of the two textures per step"},
+            "e2e": {"value": value, "unit": "Gtexel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+            flush=True)
+        return
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device; libradtex has no CPU path")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    fmt = api.FORMAT_NAMES[a.storage]
+    W = H = a.buckets
+    n = a.n
+    scene = synth.bake_scene(BAKE_SCENE_SEED + rank)
+    ctx = api.Context(local)
+    oids = [api.rt_create_texture(ctx, W, H, n, fmt) for _ in range(2)]
+    surfaces = (api.RT_SURFACE_SPHERE, api.RT_SURFACE_PLANE)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for oid, surf in zip(oids, surfaces):
+            api.rt_bake(ctx, oid, surf, scene, stream)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(a.steps)]
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        clk.mark_start()
+        start.record(stream)
+        for k in range(a.steps):
+            e = ev[k]
+            e[0].record(stream)
+            api.rt_bake(ctx, oids[0], surfaces[0], scene, stream)
+            e[1].record(stream)
+            api.rt_bake(ctx, oids[1], surfaces[1], scene, stream)
+            e[2].record(stream)
+        end.record(stream)
+        torch.cuda.synchronize()
+        clk.mark_end()
+    if world > 1:
+        torch.distributed.barrier()
+    st = api.rt_get_error(ctx)
+    if st != api.RT_OK:
+        raise RuntimeError(f"device status after timing: {api.rt_status_string(st)}")
+    ms_per_step = max_over_ranks(start.elapsed_time(end) / a.steps, dev)
+    texels = W * H * n * n
+    value = 2 * texels * world / (ms_per_step * 1e-3) / 1e9
+    sphere_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    plane_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    launch_ms = (sphere_ms + plane_ms) / 2
+    clocks = clk.summary()
+    sm_max = clocks.get("sm_max_mhz") or NOMINAL_SM_MHZ
+    peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = BAKE_FLOPS_PER_TEXEL * texels / (launch_ms * 1e-3) / 1e12
+    tb = bytes_per_texel(a.storage)
+    write_gbs = texels * tb / (launch_ms * 1e-3) / 1e9
+    hbm_peak, hbm_kind = measured_peak()
+
+    # End to end through the public API: the baked textures are read back to
+    # pinned host memory every step (the scene struct is the only input).
+    e2e = None
+    if not a.no_e2e:
+        info = api.rt_texture_info(ctx, oids[0])
+        host = [torch.empty((n, n, H, W, 4), dtype=api.CODE_DTYPE[fmt], pin_memory=True) for _ in oids]
+
+        def e2e_step():
+            for k, (oid, surf) in enumerate(zip(oids, surfaces)):
+                api.rt_bake(ctx, oid, surf, scene, stream)
+                codes, _ = api.rt_read_texture(ctx, oid, api.RT_LAYOUT_PLANES, stream)
+                host[k].copy_(codes, non_blocking=True)
+            torch.cuda.current_stream(dev).synchronize()
+
+        e2e_step()
+        s0 = time.perf_counter()
+        for _ in range(a.e2e_steps):
+            e2e_step()
+        e_ms = max_over_ranks((time.perf_counter() - s0) * 1e3 / a.e2e_steps, dev)
+        e2e = {"value": 2 * texels * world / (e_ms * 1e-3) / 1e9, "unit": "Gtexel/s", "ms_per_step": e_ms,
+               "h2d_bytes_per_step": 2 * int(ctypes_sizeof_scene()),
+               "d2h_bytes_per_step": int(sum(h.nbytes for h in host)),
+               "texture_bytes_per_object": int(info["bytes"])}
+        del host
+
+    result = {
+        "metric": BAKE_METRIC, "value": value, "unit": "Gtexel/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": bake_name(a), "texels_per_step": 2 * texels * world, "buckets": a.buckets, "n": n,
+                   "storage": a.storage, "l2": "outputs larger than L2 (%.1f GB written per step per rank)" % (
+                       2 * texels * tb / 1e9)},
+        "sphere_ms": sphere_ms, "plane_ms": plane_ms,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "peak_source": f"{SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+                     "algorithmic_flops_per_texel": BAKE_FLOPS_PER_TEXEL, "kernel": "bake_kernel",
+                     "write_gbs": write_gbs, "write_frac_of_hbm": write_gbs / hbm_peak, "hbm_peak_source": hbm_kind},
+        "gpu_launches": 2 * a.steps,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        count, times, cores = bake_cpu_baseline(a, scene, a.cpu_seconds)
+        result["cpu_baseline"] = {"value": count / times[0] / 1e9, "unit": "Gtexel/s", "cores": cores,
+                                  "kind": "oracle", "sample": f"{count} random texels of the two textures"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def ctypes_sizeof_scene() -> int:
+    import ctypes
+
+    from paper_2301_01719_gb300 import _lib
+
+    return ctypes.sizeof(_lib.BakeScene)
+
+
 VORONOI_SCENE_SEED, VORONOI_SIZE_SEED = 7007, 4004
 
 
@@ -638,7 +836,9 @@ def run_voronoi(a):
 
 def main(argv=None):
     a = parse_args(argv)
-    if a.impl == "reference":
+    if a.workload == "bake":
+        run_bake(a)
+    elif a.impl == "reference":
         run_reference(a)
     elif a.workload == "voronoi64":
         run_voronoi(a)

@@ -132,6 +132,59 @@ rt_status rt_read_texture(rt_ctx* ctx, int32_t obj_id, rt_layout dst_layout, voi
  * RT_ERR_UNSUPPORTED for a borrowed texture. */
 rt_status rt_fill_bucket_lobes(rt_ctx* ctx, int32_t obj_id, const float* params, rt_stream_t stream);
 
+/* Baking (Section 2.2, Eq. 4a and Eq. 4b).  The scene that is ray traced into
+ * a texture: a sphere, the ground plane y = plane_height and a sky.  The paper
+ * names only the reflection vector; the shading below is this library's
+ * (smooth everywhere but at the hit decisions):
+ *   lit(N)     = ambient + (1 - ambient) max(0, N . sun_direction)
+ *   sky(d)     = sky_horizon + (sky_zenith - sky_horizon)(1/2 + d_y/2)
+ *                + sun_rgb max(0, d . sun_direction)^sun_exponent
+ *   albedo     = sphere_albedo on the sphere; on the plane
+ *                plane_albedo (3/4 + cos(f x) cos(f z) / 4), f = plane_frequency
+ *   trace(P,d) = nearest hit at t > ray_offset of the sphere's entering root
+ *                and the plane: (g C + (1 - g) sky(d), g) with g = exp(-fog t),
+ *                C = albedo lit(normal at the hit); a miss gives (sky(d), 0).
+ * All values are plain floats; the struct is read on the host during the call. */
+typedef struct rt_bake_scene {
+    float sphere_centre[3];
+    float sphere_radius;      /* > 0 */
+    float plane_height;       /* the plane y = plane_height */
+    float plane_half_extent;  /* > 0: the plane's UV square is x, z in [-e, e] */
+    float sphere_albedo[3];
+    float sphere_reflectance;
+    float plane_albedo[3];
+    float plane_reflectance;
+    float plane_frequency;
+    float sun_direction[3];   /* unit, towards the sun */
+    float sun_rgb[3];
+    float sun_exponent;       /* >= 0 */
+    float sky_zenith[3];
+    float sky_horizon[3];
+    float ambient;
+    float fog;                /* >= 0 */
+    float ray_offset;         /* >= 0: hits at t <= ray_offset are ignored */
+} rt_bake_scene;
+
+/* The surface that carries a baked texture, and its UV parametrisation.
+ * SPHERE: lat-long, phi = 2 pi u - pi, theta = pi v (polar angle from +y),
+ *   P = c + r (sin theta cos phi, cos theta, sin theta sin phi); tangent frame
+ *   x = (-sin phi, 0, cos phi) (along dP/du), y = (cos theta cos phi,
+ *   -sin theta, cos theta sin phi) (along dP/dv), z = outward normal.
+ * PLANE: P = (2 e u - e, plane_height, 2 e v - e); frame (+x, +z, +y). */
+typedef enum { RT_SURFACE_SPHERE = 0, RT_SURFACE_PLANE = 1 } rt_surface;
+
+/* Bakes object obj_id from the scene (Section 2.2): for every texel (i, j, s, t)
+ * the bucket centre (u, v) = ((i + 1/2)/w, (j + 1/2)/h) gives the surface point
+ * P and frame; the texel centre B = ((2s+1)/n - 1, (2t+1)/n - 1) goes to A by
+ * Eq. 4a and to the reflection vector R by Eq. 4b; d = R in world space; the
+ * texel is (albedo(P) lit(N) + reflectance trace_rgb(P, d), trace_alpha(P, d)),
+ * with the albedo and reflectance of `surface`.  Computed in FP32 and encoded
+ * as rt_create_texture does (owned textures, any format), or written as FP32
+ * into a borrowed buffer in its layout.  scene (host) is validated: finite
+ * values, radius and extent > 0, fog, exponent and offset >= 0, else
+ * RT_ERR_INVALID_ARG.  Asynchronous on `stream`; allocates nothing. */
+rt_status rt_bake(rt_ctx* ctx, int32_t obj_id, rt_surface surface, const rt_bake_scene* scene, rt_stream_t stream);
+
 /* Forward synthesis of F >= 0 fragments (Section 2, Eq. 1b, Eq. 3, the Note's
  * clamp), filtered with `filter` in FP32: out (device, F x 4 float, RGBA).
  * Spatial addressing clamps to the edge; nearest indices take floor (an exact

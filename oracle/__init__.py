@@ -74,6 +74,7 @@ def lib() -> ctypes.CDLL:
                 "oracle_bake": (None, [I32, I32, I32, I32, P, ctypes.c_double, P, P, P]),
                 "oracle_bake_ray": (None, [I32, I32, P, ctypes.c_double, ctypes.c_double, I32, I32, P, P, P]),
                 "oracle_trace": (None, [P, I64, P, P, P]),
+                "oracle_bake_texels": (None, [I32, I32, I32, I32, P, ctypes.c_double, I64, P, P, P, P]),
                 "oracle_num_threads": (I32, []),
                 "oracle_set_num_threads": (None, [I32]),
             }
@@ -349,6 +350,20 @@ def bake(W: int, H: int, n: int, surface: int, scene: dict, delta: float | None 
         lo = np.empty_like(val)
         hi = np.empty_like(val)
     lib().oracle_bake(W, H, n, surface, _p(S), float(delta or 0.0), _p(val), _p(lo), _p(hi))
+    return val if delta is None else (val, lo, hi)
+
+
+def bake_texels(W: int, H: int, n: int, surface: int, scene: dict, ijst, delta: float | None = 2.0 ** -17):
+    """Baked values of selected texels (rows i, j, s, t) and their perturbed-ray
+    range: (val, lo, hi), each k x 4; with delta None only val."""
+    S = scene_array(scene)
+    q = _c(ijst, np.int32).reshape(-1, 4)
+    val = np.empty((q.shape[0], 4))
+    lo = hi = None
+    if delta is not None:
+        lo, hi = np.empty_like(val), np.empty_like(val)
+    lib().oracle_bake_texels(W, H, n, surface, _p(S), float(delta or 0.0), q.shape[0], _p(q), _p(val), _p(lo),
+                             _p(hi))
     return val if delta is None else (val, lo, hi)
 
 

@@ -915,61 +915,73 @@ static void normalize3(double v[3]) {
     v[2] /= m;
 }
 
-/* Bakes one object: val[(atlas texel) * 4 + c] in the atlas order of reading
- * R4.  With lo/hi non-NULL it also returns, per texel and channel, the range
- * of the texel over ten perturbed rays (origin moved by +-delta along T and B,
- * direction tilted by +-delta along T, B and N and renormalised): the spread
- * of the exact value over inputs one FP32 rounding chain away, which marks
- * texels whose ray grazes a hit decision. */
+/* One texel (i, j, s, t) of a w x h x n x n bake: value out[4] and, with lo
+ * non-NULL, the range lo[4], hi[4] of the value over ten perturbed rays
+ * (origin moved by +-delta along T and B, direction tilted by +-delta along
+ * T, B and N and renormalised): the spread of the exact value over inputs one
+ * FP32 rounding chain away, which marks rays that graze a hit decision. */
+static void bake_texel(const double* S, int surface, int64_t W, int64_t H, int64_t n, int64_t i, int64_t j,
+                       int64_t s, int64_t t, double delta, double out[4], double* lo, double* hi) {
+    double u = ((double)i + 0.5) / W, v = ((double)j + 0.5) / H;
+    double P[3], F[3][3], base[3];
+    surface_frame(S, surface, u, v, P, F);
+    surface_base(S, surface, P, F[2], base);
+    double refl = surface == OR_SURFACE_SPHERE ? S[BK_SPHERE_REFL] : S[BK_PLANE_REFL];
+    double B[2] = {texel_centre(s, n), texel_centre(t, n)};
+    double A[2], R[3];
+    unsquarify(B, A); /* Eq. 4a */
+    reflection(A, R); /* Eq. 4b, tangent space */
+    double d[3];
+    for (int k = 0; k < 3; ++k) d[k] = R[0] * F[0][k] + R[1] * F[1][k] + R[2] * F[2][k];
+    double tr[4];
+    trace(S, P, d, tr);
+    for (int k = 0; k < 3; ++k) out[k] = base[k] + refl * tr[k];
+    out[3] = tr[3];
+    if (!lo) return;
+    for (int c = 0; c < 4; ++c) lo[c] = hi[c] = out[c];
+    for (int m = 0; m < 10; ++m) {
+        double Pp[3] = {P[0], P[1], P[2]}, dp[3] = {d[0], d[1], d[2]};
+        double sg = (m & 1) ? -delta : delta;
+        if (m < 4) {
+            for (int k = 0; k < 3; ++k) Pp[k] += sg * F[m >> 1][k];
+        } else {
+            for (int k = 0; k < 3; ++k) dp[k] += sg * F[(m - 4) >> 1][k];
+            normalize3(dp);
+        }
+        double tp[4];
+        trace(S, Pp, dp, tp);
+        double o4[4] = {base[0] + refl * tp[0], base[1] + refl * tp[1], base[2] + refl * tp[2], tp[3]};
+        for (int c = 0; c < 4; ++c) {
+            if (o4[c] < lo[c]) lo[c] = o4[c];
+            if (o4[c] > hi[c]) hi[c] = o4[c];
+        }
+    }
+}
+
+/* Bakes one object into val (atlas order of reading R4, 4 doubles a texel);
+ * lo / hi (same shape, or NULL) receive the perturbed-ray range. */
 void oracle_bake(int32_t W, int32_t H, int32_t n, int32_t surface, const double* S, double delta, double* val,
                  double* lo, double* hi) {
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t bk = 0; bk < (int64_t)W * H; ++bk) {
         int64_t i = bk % W, j = bk / W;
-        double u = ((double)i + 0.5) / W, v = ((double)j + 0.5) / H;
-        double P[3], F[3][3], base[3];
-        surface_frame(S, surface, u, v, P, F);
-        surface_base(S, surface, P, F[2], base);
-        double refl = surface == OR_SURFACE_SPHERE ? S[BK_SPHERE_REFL] : S[BK_PLANE_REFL];
         for (int64_t t = 0; t < n; ++t)
             for (int64_t s = 0; s < n; ++s) {
-                double B[2] = {texel_centre(s, n), texel_centre(t, n)};
-                double A[2], R[3];
-                unsquarify(B, A);  /* Eq. 4a */
-                reflection(A, R);  /* Eq. 4b, tangent space */
-                double d[3];
-                for (int k = 0; k < 3; ++k) d[k] = R[0] * F[0][k] + R[1] * F[1][k] + R[2] * F[2][k];
-                double tr[4], out[4];
-                trace(S, P, d, tr);
-                for (int k = 0; k < 3; ++k) out[k] = base[k] + refl * tr[k];
-                out[3] = tr[3];
                 int64_t e = ((j * n + t) * (int64_t)W * n + (i * n + s)) * 4;
-                for (int c = 0; c < 4; ++c) val[e + c] = out[c];
-                if (!lo) continue;
-                double mn[4], mx[4];
-                for (int c = 0; c < 4; ++c) mn[c] = mx[c] = out[c];
-                for (int m = 0; m < 10; ++m) {
-                    double Pp[3] = {P[0], P[1], P[2]}, dp[3] = {d[0], d[1], d[2]};
-                    double sg = (m & 1) ? -delta : delta;
-                    if (m < 4) {
-                        for (int k = 0; k < 3; ++k) Pp[k] += sg * F[m >> 1][k];
-                    } else {
-                        for (int k = 0; k < 3; ++k) dp[k] += sg * F[(m - 4) >> 1][k];
-                        normalize3(dp);
-                    }
-                    double tp[4];
-                    trace(S, Pp, dp, tp);
-                    double o4[4] = {base[0] + refl * tp[0], base[1] + refl * tp[1], base[2] + refl * tp[2], tp[3]};
-                    for (int c = 0; c < 4; ++c) {
-                        if (o4[c] < mn[c]) mn[c] = o4[c];
-                        if (o4[c] > mx[c]) mx[c] = o4[c];
-                    }
-                }
-                for (int c = 0; c < 4; ++c) {
-                    lo[e + c] = mn[c];
-                    hi[e + c] = mx[c];
-                }
+                bake_texel(S, surface, W, H, n, i, j, s, t, delta, val + e, lo ? lo + e : NULL, hi ? hi + e : NULL);
             }
+    }
+}
+
+/* The same for a list of texels ijst (count x 4 int32: i, j, s, t): rows of 4
+ * doubles in val / lo / hi. */
+void oracle_bake_texels(int32_t W, int32_t H, int32_t n, int32_t surface, const double* S, double delta,
+                        int64_t count, const int32_t* ijst, double* val, double* lo, double* hi) {
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < count; ++k) {
+        const int32_t* q = ijst + 4 * k;
+        bake_texel(S, surface, W, H, n, q[0], q[1], q[2], q[3], delta, val + 4 * k, lo ? lo + 4 * k : NULL,
+                   hi ? hi + 4 * k : NULL);
     }
 }
 

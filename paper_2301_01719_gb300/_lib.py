@@ -28,6 +28,19 @@ RT_BORROW = 1
 RT_ACCUMULATE = 1
 RT_DETERMINISTIC = 2
 RT_MAX_OBJECTS = 1024
+RT_SURFACE_SPHERE, RT_SURFACE_PLANE = range(2)
+
+
+class BakeScene(ctypes.Structure):
+    """rt_bake_scene: the analytic scene that rt_bake ray traces (all floats)."""
+    _fields_ = [("sphere_centre", ctypes.c_float * 3), ("sphere_radius", ctypes.c_float),
+                ("plane_height", ctypes.c_float), ("plane_half_extent", ctypes.c_float),
+                ("sphere_albedo", ctypes.c_float * 3), ("sphere_reflectance", ctypes.c_float),
+                ("plane_albedo", ctypes.c_float * 3), ("plane_reflectance", ctypes.c_float),
+                ("plane_frequency", ctypes.c_float), ("sun_direction", ctypes.c_float * 3),
+                ("sun_rgb", ctypes.c_float * 3), ("sun_exponent", ctypes.c_float),
+                ("sky_zenith", ctypes.c_float * 3), ("sky_horizon", ctypes.c_float * 3),
+                ("ambient", ctypes.c_float), ("fog", ctypes.c_float), ("ray_offset", ctypes.c_float)]
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -42,6 +55,7 @@ SIGNATURES = {
                                ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
     "rt_read_texture": (_I32, [_P, _I32, _I32, _P, _P, _P]),
     "rt_fill_bucket_lobes": (_I32, [_P, _I32, _P, _P]),
+    "rt_bake": (_I32, [_P, _I32, _I32, _P, _P]),
     "rt_shade": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, _P]),
     "rt_locate": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, _P, _P]),
     "rt_shade_backward": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, ctypes.POINTER(_P), _I32, _P, _P, _I32, _P]),

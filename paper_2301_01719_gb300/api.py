@@ -15,7 +15,7 @@ from . import _lib
 from ._lib import (RT_ACCUMULATE, RT_ANGULAR_BILINEAR, RT_BF16, RT_BORROW, RT_E4M3_BUCKET_SCALE,  # noqa: F401
                    RT_DETERMINISTIC, RT_ERR_BAD_OBJ_ID, RT_ERR_CUDA, RT_ERR_INVALID_ARG, RT_ERR_NONFINITE, RT_ERR_OOM, RT_ERR_TIMEOUT,
                    RT_ERR_UNSUPPORTED, RT_F16, RT_F32, RT_LAYOUT_ATLAS, RT_LAYOUT_PLANES, RT_MAX_OBJECTS, RT_NEAREST,
-                   RT_OK, RT_QUADRILINEAR, RadtexError)
+                   RT_OK, RT_QUADRILINEAR, RT_SURFACE_PLANE, RT_SURFACE_SPHERE, RadtexError)
 
 FORMAT_BYTES = {RT_F32: 16, RT_F16: 8, RT_BF16: 8, RT_E4M3_BUCKET_SCALE: 4}
 CODE_DTYPE = {RT_F32: torch.float32, RT_F16: torch.int16, RT_BF16: torch.int16, RT_E4M3_BUCKET_SCALE: torch.uint8}
@@ -122,6 +122,29 @@ def rt_fill_bucket_lobes(ctx: Context, obj_id: int, params: torch.Tensor, stream
     if params.numel() != info["w"] * info["h"] * 8:
         raise ValueError(f"params must hold h x w x 8 = {info['h']} x {info['w']} x 8 floats")
     _lib.call("rt_fill_bucket_lobes", ctx.handle, int(obj_id), _ptr(params), _stream(stream, params.device))
+
+
+def bake_scene_struct(scene: dict) -> _lib.BakeScene:
+    """The scene dictionary (keys as rt_bake_scene's fields) as the C struct."""
+    S = _lib.BakeScene()
+    for name, ctype in _lib.BakeScene._fields_:
+        value = scene[name]
+        if hasattr(ctype, "_length_"):
+            vals = [float(x) for x in value]
+            if len(vals) != ctype._length_:
+                raise ValueError(f"{name} needs {ctype._length_} values")
+            setattr(S, name, ctype(*vals))
+        else:
+            setattr(S, name, float(value))
+    return S
+
+
+def rt_bake(ctx: Context, obj_id: int, surface: int, scene: dict, stream=None) -> None:
+    """Bakes object obj_id from the analytic scene (Eq. 4a, Eq. 4b, one traced
+    ray per texel); surface is RT_SURFACE_SPHERE or RT_SURFACE_PLANE."""
+    S = bake_scene_struct(scene)
+    dev = torch.device("cuda", ctx.device)
+    _lib.call("rt_bake", ctx.handle, int(obj_id), int(surface), ctypes.byref(S), _stream(stream, dev))
 
 
 def _gbuffer(uv, dirs, obj):

@@ -2,6 +2,7 @@
 // texture table, argument validation, kernel launches and the status model.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -321,6 +322,25 @@ rt_status rt_fill_bucket_lobes(rt_ctx* ctx, int32_t obj_id, const float* params,
     if (!g.ok) return RT_ERR_CUDA;
     return cuda_status(rt::launch_fill_lobes(params, ctx->owned[obj_id], ctx->scales[obj_id], d.W, d.H, d.n, d.fmt,
                                              (cudaStream_t)stream));
+}
+
+static bool valid_scene(const rt_bake_scene* S) {
+    const float* f = reinterpret_cast<const float*>(S);
+    for (size_t k = 0; k < sizeof(rt_bake_scene) / sizeof(float); ++k)
+        if (!std::isfinite(f[k])) return false;
+    return S->sphere_radius > 0.f && S->plane_half_extent > 0.f && S->fog >= 0.f && S->sun_exponent >= 0.f &&
+           S->ray_offset >= 0.f;
+}
+
+rt_status rt_bake(rt_ctx* ctx, int32_t obj_id, rt_surface surface, const rt_bake_scene* scene, rt_stream_t stream) {
+    if (!ctx || obj_id < 0 || obj_id >= RT_MAX_OBJECTS || !ctx->table[obj_id].live || !scene ||
+        (surface != RT_SURFACE_SPHERE && surface != RT_SURFACE_PLANE) || !valid_scene(scene))
+        return RT_ERR_INVALID_ARG;
+    const TexDesc& d = ctx->table[obj_id];
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    return cuda_status(rt::launch_bake(*scene, (int)surface, const_cast<void*>(d.base), ctx->scales[obj_id], d.W, d.H,
+                                       d.n, d.fmt, d.layout, (cudaStream_t)stream));
 }
 
 rt_status rt_shade(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F, rt_filter filter,

@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kBackThreads) backward_kernel(
     bool accumulate, unsigned* status) {
     __shared__ WarpStage<true> stages[kBackWarps];
     const bool coord_grads = (dL_duv != nullptr) || (dL_ddir != nullptr);
-    for_each_fragment<kBackWarps, true, TILED>(uv, dir, obj, dL_dout, F, tiling, stages,
+    for_each_fragment<kBackWarps, true, TILED, 2>(uv, dir, obj, dL_dout, F, tiling, stages,
                                                [&](int64_t f, const Frag& q, float4 go) {
         float2 guv = make_float2(0.f, 0.f);
         float3 gdir = make_float3(0.f, 0.f, 0.f);

@@ -1,0 +1,197 @@
+// bake.cu -- baking a radiance texture from a ray-traced analytic scene
+// (Section 2.2, Eq. 4a and Eq. 4b).
+//
+// One thread per bucket.  A block covers 128 consecutive buckets (bucket
+// b = j w + i), so at every in-bucket texel (s, t) its stores are 128
+// consecutive texels of one PLANES plane: coalesced.  The grid's y dimension
+// splits the n^2 planes of a bucket among blocks when there are too few
+// buckets to fill the GPU; FP8 E4M3 keeps a bucket in one thread, which
+// evaluates the bucket twice (its amax sets the bucket's scale, then the
+// codes).  The per-texel work is the reflection vector (Eq. 4a, Eq. 4b), its
+// rotation to world space, one ray against the sphere and the plane, and the
+// sky and shading functions: ALU work, about 150 instructions per texel.
+#include <math.h>
+
+#include "rt_encode.cuh"
+#include "rt_internal.h"
+
+namespace rt {
+
+constexpr int kBakeThreads = 128;
+
+struct Ray {
+    float3 P, T, B, N;  // surface point and tangent frame
+    float3 base;        // the surface's own lit colour
+    float refl;
+};
+
+__device__ __forceinline__ float3 mk(const float* a) { return make_float3(a[0], a[1], a[2]); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 axpy(float a, float3 x, float3 y) {
+    return make_float3(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z));
+}
+__device__ __forceinline__ float3 scale3(float a, float3 x) { return make_float3(a * x.x, a * x.y, a * x.z); }
+
+__device__ __forceinline__ float lit(const rt_bake_scene& S, float3 N) {
+    return S.ambient + (1.0f - S.ambient) * fmaxf(dot3(N, mk(S.sun_direction)), 0.0f);
+}
+
+__device__ __forceinline__ float3 sky(const rt_bake_scene& S, float3 d) {
+    const float h = 0.5f + 0.5f * d.y;
+    const float c = dot3(d, mk(S.sun_direction));
+    const float sun = c > 0.0f ? powf(c, S.sun_exponent) : 0.0f;
+    float3 r;
+    r.x = S.sky_horizon[0] + (S.sky_zenith[0] - S.sky_horizon[0]) * h + S.sun_rgb[0] * sun;
+    r.y = S.sky_horizon[1] + (S.sky_zenith[1] - S.sky_horizon[1]) * h + S.sun_rgb[1] * sun;
+    r.z = S.sky_horizon[2] + (S.sky_zenith[2] - S.sky_horizon[2]) * h + S.sun_rgb[2] * sun;
+    return r;
+}
+
+__device__ __forceinline__ float3 plane_albedo(const rt_bake_scene& S, float x, float z) {
+    const float m = 0.75f + 0.25f * cosf(S.plane_frequency * x) * cosf(S.plane_frequency * z);
+    return scale3(m, mk(S.plane_albedo));
+}
+
+// Radiance along P + t d and its fog transmittance (0 for a miss).
+__device__ __forceinline__ float4 trace(const rt_bake_scene& S, float3 P, float3 d) {
+    const float3 c = mk(S.sphere_centre);
+    const float3 o = make_float3(P.x - c.x, P.y - c.y, P.z - c.z);
+    const float b = dot3(o, d);
+    const float q = dot3(o, o) - S.sphere_radius * S.sphere_radius;
+    const float disc = b * b - q;
+    float tb = INFINITY;
+    int hit = -1;
+    if (disc > 0.0f) {
+        const float t = -b - sqrtf(disc);  // entering root
+        if (t > S.ray_offset) {
+            tb = t;
+            hit = RT_SURFACE_SPHERE;
+        }
+    }
+    if (d.y != 0.0f) {
+        const float t = (S.plane_height - P.y) / d.y;
+        if (t > S.ray_offset && t < tb) {
+            tb = t;
+            hit = RT_SURFACE_PLANE;
+        }
+    }
+    const float3 K = sky(S, d);
+    if (hit < 0) return make_float4(K.x, K.y, K.z, 0.0f);
+    const float3 X = axpy(tb, d, P);
+    float3 C;
+    if (hit == RT_SURFACE_SPHERE) {
+        const float ir = 1.0f / S.sphere_radius;
+        const float3 Nh = make_float3((X.x - c.x) * ir, (X.y - c.y) * ir, (X.z - c.z) * ir);
+        C = scale3(lit(S, Nh), mk(S.sphere_albedo));
+    } else {
+        C = scale3(lit(S, make_float3(0.0f, 1.0f, 0.0f)), plane_albedo(S, X.x, X.z));
+    }
+    const float g = expf(-S.fog * tb);
+    return make_float4(g * C.x + (1.0f - g) * K.x, g * C.y + (1.0f - g) * K.y, g * C.z + (1.0f - g) * K.z, g);
+}
+
+// Surface point, frame and own colour at the centre of bucket (i, j).
+__device__ __forceinline__ Ray bucket_ray(const rt_bake_scene& S, int surface, int i, int j, int W, int H) {
+    const float u = ((float)i + 0.5f) / (float)W, v = ((float)j + 0.5f) / (float)H;
+    Ray r;
+    if (surface == RT_SURFACE_SPHERE) {
+        float sp, cp, st, ct;
+        sincospif(2.0f * u - 1.0f, &sp, &cp);  // phi = 2 pi u - pi
+        sincospif(v, &st, &ct);                // theta = pi v
+        r.N = make_float3(st * cp, ct, st * sp);
+        r.T = make_float3(-sp, 0.0f, cp);
+        r.B = make_float3(ct * cp, -st, ct * sp);
+        r.P = axpy(S.sphere_radius, r.N, mk(S.sphere_centre));
+        r.base = scale3(lit(S, r.N), mk(S.sphere_albedo));
+        r.refl = S.sphere_reflectance;
+    } else {
+        const float e = S.plane_half_extent;
+        r.P = make_float3(2.0f * e * u - e, S.plane_height, 2.0f * e * v - e);
+        r.T = make_float3(1.0f, 0.0f, 0.0f);
+        r.B = make_float3(0.0f, 0.0f, 1.0f);
+        r.N = make_float3(0.0f, 1.0f, 0.0f);
+        r.base = scale3(lit(S, r.N), plane_albedo(S, r.P.x, r.P.z));
+        r.refl = S.plane_reflectance;
+    }
+    return r;
+}
+
+// Texel (s, t) of the bucket: Eq. 4a and Eq. 4b give R; d = R in world space.
+__device__ __forceinline__ float4 bake_texel(const rt_bake_scene& S, const Ray& r, int s, int t, int n) {
+    const float3 R = texel_reflection(s, t, n);
+    const float3 d = axpy(R.z, r.N, axpy(R.y, r.B, scale3(R.x, r.T)));
+    const float4 tr = trace(S, r.P, d);
+    return make_float4(fmaf(r.refl, tr.x, r.base.x), fmaf(r.refl, tr.y, r.base.y), fmaf(r.refl, tr.z, r.base.z),
+                       tr.w);
+}
+
+template <int FMT, int LAYOUT>
+__global__ void __launch_bounds__(kBakeThreads) bake_kernel(rt_bake_scene S, int surface, void* __restrict__ dst,
+                                                            float* __restrict__ scale, int W, int H, int n) {
+    const int64_t b = (int64_t)blockIdx.x * kBakeThreads + threadIdx.x;
+    if (b >= (int64_t)W * H) return;
+    const int j = (int)(b / W), i = (int)(b - (int64_t)j * W);
+    const Ray r = bucket_ray(S, surface, i, j, W, H);
+    const int planes = n * n;
+    const int p0 = (int)((int64_t)blockIdx.y * planes / gridDim.y);
+    const int p1 = (int)((int64_t)(blockIdx.y + 1) * planes / gridDim.y);
+    float sc = 1.0f;
+    if (FMT == RT_E4M3_BUCKET_SCALE) {
+        float amax = 0.0f;
+        for (int p = 0; p < planes; ++p) amax = fmaxf(amax, amax4(bake_texel(S, r, p % n, p / n, n)));
+        sc = bucket_scale(amax);
+        scale[b] = sc;
+    }
+    for (int p = p0; p < p1; ++p) {
+        const int t = p / n, s = p - t * n;
+        const float4 v = bake_texel(S, r, s, t, n);
+        const int64_t idx = index_in(LAYOUT, W, H, n, i, j, s, t);
+        if (FMT == RT_F32)
+            reinterpret_cast<float4*>(dst)[idx] = v;
+        else if (FMT == RT_F16)
+            reinterpret_cast<uint2*>(dst)[idx] = pack_f16(v);
+        else if (FMT == RT_BF16)
+            reinterpret_cast<uint2*>(dst)[idx] = pack_bf16(v);
+        else
+            reinterpret_cast<unsigned*>(dst)[idx] = pack_e4m3(v, sc);
+    }
+}
+
+template <int FMT, int LAYOUT>
+static cudaError_t launch_bake_t(const rt_bake_scene& S, int surface, void* dst, float* scale, int W, int H, int n,
+                                 cudaStream_t stream) {
+    const int64_t buckets = (int64_t)W * H;
+    const unsigned gx = (unsigned)((buckets + kBakeThreads - 1) / kBakeThreads);
+    // enough blocks for 8 per SM; E4M3 needs the whole bucket in one thread
+    unsigned gy = 1;
+    if (FMT != RT_E4M3_BUCKET_SCALE) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t want = (int64_t)sms * 8;
+        if ((int64_t)gx < want) gy = (unsigned)((want + gx - 1) / gx);
+        if (gy > (unsigned)(n * n)) gy = (unsigned)(n * n);
+    }
+    bake_kernel<FMT, LAYOUT><<<dim3(gx, gy), kBakeThreads, 0, stream>>>(S, surface, dst, scale, W, H, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bake(const rt_bake_scene& S, int surface, void* dst, float* scale, int W, int H, int n, int fmt,
+                        int layout, cudaStream_t stream) {
+    if (layout == RT_LAYOUT_ATLAS) {
+        if (fmt != RT_F32) return cudaErrorInvalidValue;
+        return launch_bake_t<RT_F32, RT_LAYOUT_ATLAS>(S, surface, dst, scale, W, H, n, stream);
+    }
+    switch (fmt) {
+        case RT_F32:
+            return launch_bake_t<RT_F32, RT_LAYOUT_PLANES>(S, surface, dst, scale, W, H, n, stream);
+        case RT_F16:
+            return launch_bake_t<RT_F16, RT_LAYOUT_PLANES>(S, surface, dst, scale, W, H, n, stream);
+        case RT_BF16:
+            return launch_bake_t<RT_BF16, RT_LAYOUT_PLANES>(S, surface, dst, scale, W, H, n, stream);
+        default:
+            return launch_bake_t<RT_E4M3_BUCKET_SCALE, RT_LAYOUT_PLANES>(S, surface, dst, scale, W, H, n, stream);
+    }
+}
+
+}  // namespace rt

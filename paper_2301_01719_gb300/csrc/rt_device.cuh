@@ -263,12 +263,12 @@ __device__ __forceinline__ P4 load_texelP<RT_F16>(const void* base, int64_t idx,
     return {pack2(fa.x, fa.y), pack2(fb.x, fb.y)};
 }
 
+// BF16 is the upper half of an FP32: widening is a 16-bit shift (exact).
 template <>
 __device__ __forceinline__ P4 load_texelP<RT_BF16>(const void* base, int64_t idx, float) {
     uint2 r = __ldg(reinterpret_cast<const uint2*>(base) + idx);
-    float2 fa = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&r.x));
-    float2 fb = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&r.y));
-    return {pack2(fa.x, fa.y), pack2(fb.x, fb.y)};
+    return {pack2(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xFFFF0000u)),
+            pack2(__uint_as_float(r.y << 16), __uint_as_float(r.y & 0xFFFF0000u))};
 }
 
 template <>

@@ -172,12 +172,14 @@ struct Tiling {
     int64_t frame;        // W * H
 };
 
-template <bool EXTRA>
+// A warp's G-buffer buffers: the chunk being processed plus STAGES - 1
+// prefetched ones.
+template <bool EXTRA, int STAGES = 2>
 struct WarpStage {
-    float uv[2][2 * kChunk];
-    float dir[2][3 * kChunk];
-    int obj[2][kChunk];
-    float4 extra[EXTRA ? 2 : 1][EXTRA ? kChunk : 1];
+    float uv[STAGES][2 * kChunk];
+    float dir[STAGES][3 * kChunk];
+    int obj[STAGES][kChunk];
+    float4 extra[EXTRA ? STAGES : 1][EXTRA ? kChunk : 1];
 };
 
 struct Frag {
@@ -241,10 +243,10 @@ __device__ __forceinline__ ChunkGeom chunk_geom(const Tiling& T, int64_t F, int6
 // Issues the copies of one chunk into buffer `b` (a chunk that is not entirely
 // inside the frame or not 16-byte aligned is read with plain bounded loads
 // instead; lanes without a fragment become background).
-template <bool EXTRA>
+template <bool EXTRA, int STAGES>
 __device__ __forceinline__ void stage_chunk(const float* __restrict__ uv, const float* __restrict__ dir,
                                             const int32_t* __restrict__ obj, const float* __restrict__ extra,
-                                            const ChunkGeom& g, int b, WarpStage<EXTRA>& S, int lane) {
+                                            const ChunkGeom& g, int b, WarpStage<EXTRA, STAGES>& S, int lane) {
     if (g.fast) {
         // 24 pieces of dir, 16 of uv, 8 of obj: lanes 0-23 take dir, 16-31 uv,
         // 24-31 obj.  Shared memory holds the chunk in lane order (lane = row
@@ -283,8 +285,8 @@ __device__ __forceinline__ void stage_chunk(const float* __restrict__ uv, const 
     }
 }
 
-template <bool EXTRA>
-__device__ __forceinline__ Frag read_frag(const WarpStage<EXTRA>& S, int b, int lane) {
+template <bool EXTRA, int STAGES>
+__device__ __forceinline__ Frag read_frag(const WarpStage<EXTRA, STAGES>& S, int b, int lane) {
     Frag r;
     float2 q = reinterpret_cast<const float2*>(S.uv[b])[lane];
     r.u = q.x;
@@ -303,36 +305,48 @@ __device__ __forceinline__ int64_t chunk_count(const Tiling& T, int64_t F, int w
 }
 
 // Runs body(f, frag, extra) with all 32 lanes of the warp, one fragment per
-// lane, persistent over the grid, with the G-buffer of the next chunk
-// prefetched.  Lanes without a fragment get a background fragment and f = -1:
-// the body must not store for them.  WARPS = warps per block; the block's
-// shared memory holds WARPS stages.
-template <int WARPS, bool EXTRA, bool TILED, typename Body>
+// lane, persistent over the grid, with the G-buffer of the next STAGES - 1
+// chunks prefetched.  Lanes without a fragment get a background fragment and
+// f = -1: the body must not store for them.  WARPS = warps per block; the
+// block's shared memory holds WARPS stages.
+template <int WARPS, bool EXTRA, bool TILED, int STAGES, typename Body>
 __device__ __forceinline__ void for_each_fragment(const float* __restrict__ uv, const float* __restrict__ dir,
                                                   const int32_t* __restrict__ obj, const float* __restrict__ extra,
-                                                  int64_t F, const Tiling& T, WarpStage<EXTRA>* stages, Body body) {
+                                                  int64_t F, const Tiling& T, WarpStage<EXTRA, STAGES>* stages,
+                                                  Body body) {
+    constexpr int kStages = STAGES;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    WarpStage<EXTRA>& S = stages[w];
+    WarpStage<EXTRA, STAGES>& S = stages[w];
     const int64_t nchunks = chunk_count<TILED>(T, F, WARPS);
     const int64_t step = (int64_t)gridDim.x * WARPS;
     int64_t c = (int64_t)blockIdx.x * WARPS + w;
-    int b = 0;
-    ChunkGeom g = chunk_geom<WARPS, TILED>(T, F, c, lane);
-    if (c < nchunks) stage_chunk<EXTRA>(uv, dir, obj, extra, g, 0, S, lane);
-    cp_async_commit();
-    for (; c < nchunks; c += step, b ^= 1) {
-        const int64_t next = c + step;
-        const ChunkGeom gn = chunk_geom<WARPS, TILED>(T, F, next, lane);
-        if (next < nchunks) stage_chunk<EXTRA>(uv, dir, obj, extra, gn, b ^ 1, S, lane);
+    // fk[k]: this lane's fragment of chunk c + k * step, staged in buffer (b + k) % kStages
+    int64_t fk[kStages];
+#pragma unroll
+    for (int k = 0; k < kStages - 1; ++k) {
+        const ChunkGeom g = chunk_geom<WARPS, TILED>(T, F, c + k * step, lane);
+        if (c + k * step < nchunks) stage_chunk<EXTRA, STAGES>(uv, dir, obj, extra, g, k, S, lane);
         cp_async_commit();
-        cp_async_wait<1>();  // chunk c has landed (the newest group may still be in flight)
+        fk[k] = g.f;
+    }
+    int b = 0;
+    for (; c < nchunks; c += step) {
+        const int64_t ahead = c + (kStages - 1) * step;
+        const int bl = b + kStages - 1 >= kStages ? b - 1 : b + kStages - 1;  // (b + kStages - 1) % kStages
+        const ChunkGeom g = chunk_geom<WARPS, TILED>(T, F, ahead, lane);
+        if (ahead < nchunks) stage_chunk<EXTRA, STAGES>(uv, dir, obj, extra, g, bl, S, lane);
+        cp_async_commit();
+        fk[kStages - 1] = g.f;
+        cp_async_wait<kStages - 1>();  // chunk c has landed (newer groups may still be in flight)
         __syncwarp();
-        const Frag q = read_frag<EXTRA>(S, b, lane);
+        const Frag q = read_frag<EXTRA, STAGES>(S, b, lane);
         float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
         if (EXTRA) e = S.extra[EXTRA ? b : 0][EXTRA ? lane : 0];
         __syncwarp();  // every lane has read buffer b before it is refilled
-        body(g.f, q, e);
-        g = gn;
+        body(fk[0], q, e);
+#pragma unroll
+        for (int k = 0; k < kStages - 1; ++k) fk[k] = fk[k + 1];
+        b = b + 1 == kStages ? 0 : b + 1;
     }
     cp_async_wait<0>();
 }

@@ -76,6 +76,8 @@ cudaError_t launch_fixed_to_float(const long long* acc, float* dst, int64_t coun
 cudaError_t launch_encode(const float* src, int src_layout, void* dst, float* scale, int W, int H, int n, int fmt,
                           cudaStream_t stream);
 cudaError_t launch_read(const void* src, int fmt, int W, int H, int n, int dst_layout, void* dst, cudaStream_t stream);
+cudaError_t launch_bake(const rt_bake_scene& S, int surface, void* dst, float* scale, int W, int H, int n, int fmt,
+                        int layout, cudaStream_t stream);
 cudaError_t launch_fill_lobes(const float* params, void* dst, float* scale, int W, int H, int n, int fmt,
                               cudaStream_t stream);
 cudaError_t launch_convert(const float* src, int src_layout, float* dst, int dst_layout, int W, int H, int n,

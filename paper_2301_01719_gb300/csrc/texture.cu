@@ -3,6 +3,7 @@
 #include "launch.h"
 #include "rt_device.cuh"
 #include "rt_filter.cuh"
+#include "rt_encode.cuh"
 #include "rt_internal.h"
 
 namespace rt {
@@ -10,46 +11,6 @@ namespace rt {
 constexpr int kThreads = 256;
 
 static inline unsigned blocks_for(int64_t items) { return (unsigned)((items + kThreads - 1) / kThreads); }
-
-// (i, j, s, t) of texel `idx` in the PLANES layout.
-__device__ __forceinline__ void planes_coords(int64_t idx, int W, int H, int n, int& i, int& j, int& s, int& t) {
-    int64_t plane = (int64_t)W * H;
-    int64_t p = idx / plane, r = idx - p * plane;
-    j = (int)(r / W);
-    i = (int)(r - (int64_t)j * W);
-    t = (int)(p / n);
-    s = (int)(p - (int64_t)t * n);
-}
-
-__device__ __forceinline__ int64_t index_in(int layout, int W, int H, int n, int i, int j, int s, int t) {
-    if (layout == RT_LAYOUT_PLANES) return ((int64_t)t * n + s) * ((int64_t)W * H) + (int64_t)j * W + i;
-    return ((int64_t)j * n + t) * ((int64_t)W * n) + (int64_t)i * n + s;
-}
-
-__device__ __forceinline__ uint2 pack_f16(float4 v) {
-    __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
-    return make_uint2(*reinterpret_cast<unsigned*>(&a), *reinterpret_cast<unsigned*>(&b));
-}
-
-__device__ __forceinline__ uint2 pack_bf16(float4 v) {
-    __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
-    return make_uint2(*reinterpret_cast<unsigned*>(&a), *reinterpret_cast<unsigned*>(&b));
-}
-
-// E4M3 codes of v / scale, round to nearest even with saturation; channel 0 in the low byte.
-__device__ __forceinline__ unsigned pack_e4m3(float4 v, float scale) {
-    float2 lo = make_float2(__fdiv_rn(v.x, scale), __fdiv_rn(v.y, scale));
-    float2 hi = make_float2(__fdiv_rn(v.z, scale), __fdiv_rn(v.w, scale));
-    unsigned a = __nv_cvt_float2_to_fp8x2(lo, __NV_SATFINITE, __NV_E4M3);
-    unsigned b = __nv_cvt_float2_to_fp8x2(hi, __NV_SATFINITE, __NV_E4M3);
-    return (a & 0xFFFFu) | (b << 16);
-}
-
-__device__ __forceinline__ float bucket_scale(float amax) { return amax == 0.0f ? 1.0f : __fdiv_rn(amax, 448.0f); }
-
-__device__ __forceinline__ float amax4(float4 v) {
-    return fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
-}
 
 // FP32 source (any layout) -> FP32 / FP16 / BF16 storage in PLANES, one thread per texel.
 __global__ void encode_elementwise(const float4* __restrict__ src, int src_layout, void* __restrict__ dst, int W,
@@ -123,24 +84,6 @@ cudaError_t launch_read(const void* src, int fmt, int W, int H, int n, int dst_l
         read_codes<uint2><<<g, kThreads, 0, stream>>>(reinterpret_cast<const uint2*>(src),
                                                       reinterpret_cast<uint2*>(dst), W, H, n, dst_layout, total);
     return cudaGetLastError();
-}
-
-// Direction of the centre of texel (s, t): B = ((2s+1)/n - 1, (2t+1)/n - 1),
-// A = Eq. 4a(B) = B max(|B_x|, |B_y|) / |B|, I = Eq. 2c(A) =
-// (A_x sqrt(2 - |A|^2), A_y sqrt(2 - |A|^2), 1 - |A|^2).
-__device__ __forceinline__ float3 texel_centre_direction(int s, int t, int n) {
-    float Bx = (float)(2 * s + 1) / (float)n - 1.0f;
-    float By = (float)(2 * t + 1) / (float)n - 1.0f;
-    float r = sqrtf(Bx * Bx + By * By);
-    float Ax = 0.f, Ay = 0.f;
-    if (r > 0.f) {
-        float k = fmaxf(fabsf(Bx), fabsf(By)) / r;
-        Ax = Bx * k;
-        Ay = By * k;
-    }
-    float a2 = Ax * Ax + Ay * Ay;
-    float q = sqrtf(fmaxf(2.0f - a2, 0.0f));
-    return make_float3(Ax * q, Ay * q, 1.0f - a2);
 }
 
 __device__ __forceinline__ float4 lobe_value(const float* P, float3 I) {
@@ -219,7 +162,7 @@ __global__ void __launch_bounds__(kThreads) footprint_kernel(const TexDesc* __re
                                                             unsigned* status) {
     __shared__ WarpStage<false> stages[kThreads / 32];
     const Tiling flat = flat_tiling();
-    for_each_fragment<kThreads / 32, false, false>(uv, dir, obj, nullptr, F, flat, stages,
+    for_each_fragment<kThreads / 32, false, false, 2>(uv, dir, obj, nullptr, F, flat, stages,
                                                    [&](int64_t, const Frag& q, float4) {
         TexDesc d;
         if (!fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d)) return;
