@@ -75,6 +75,9 @@ def lib() -> ctypes.CDLL:
                 "oracle_bake_ray": (None, [I32, I32, P, ctypes.c_double, ctypes.c_double, I32, I32, P, P, P]),
                 "oracle_trace": (None, [P, I64, P, P, P]),
                 "oracle_bake_texels": (None, [I32, I32, I32, I32, P, ctypes.c_double, I64, P, P, P, P]),
+                "oracle_palette_expand": (None, [I32, I32, I32, I32, I32, P, P, P, P, P]),
+                "oracle_kmeans_assign": (None, [I64, I64, P, I64, P, P, P, P]),
+                "oracle_kmeans_update": (None, [I64, I64, P, I64, P, P, P]),
                 "oracle_num_threads": (I32, []),
                 "oracle_set_num_threads": (None, [I32]),
             }
@@ -386,3 +389,52 @@ def trace(scene: dict, P, d) -> np.ndarray:
     out = np.empty((P.shape[0], 4))
     lib().oracle_trace(_p(S), P.shape[0], _p(P), _p(d), _p(out))
     return out
+
+
+# --------------------------------------------------------------------------
+# Bucket compression (Section 2; reading R11): palette + index map, k-means.
+# --------------------------------------------------------------------------
+
+def palette_expand(palette: "Texture", index, W: int, H: int) -> "Texture":
+    """The dense texture a palette texture stands for: bucket (i, j) = palette
+    bucket index[j, i].  palette: a K x 1 texture (its codes an n x K n atlas)."""
+    n, K = palette.n, palette.W
+    assert palette.H == 1
+    index = _c(index, np.uint32).reshape(H, W)
+    assert index.max(initial=0) < K
+    dense = np.empty((H * n, W * n, 4), dtype=palette.codes.dtype)
+    scales = np.empty((H, W), np.float32) if palette.scales is not None else None
+    lib().oracle_palette_expand(W, H, n, K, palette.codes.dtype.itemsize, _p(palette.codes), _p(palette.scales),
+                                _p(index), _p(dense), _p(scales))
+    return Texture(W, H, n, palette.fmt, dense, scales)
+
+
+def bucket_vectors(values: np.ndarray, W: int, H: int, n: int) -> np.ndarray:
+    """Atlas-layout texel values ((H n) x (W n) x 4) -> one row per bucket
+    (row b = j W + i), the n^2 x 4 values in (t, s, channel) order."""
+    v = np.asarray(values, np.float64).reshape(H, n, W, n, 4)
+    return np.ascontiguousarray(v.transpose(0, 2, 1, 3, 4).reshape(H * W, n * n * 4))
+
+
+def kmeans_assign(X, C, all_distances: bool = False):
+    """Nearest centroid of every row of X (B x D) among C (K x D), ties to the
+    lowest index: (index, squared distance[, all squared distances B x K])."""
+    X = _c(X, np.float64)
+    C = _c(C, np.float64)
+    B, D = X.shape
+    K = C.shape[0]
+    index = np.empty(B, np.uint32)
+    dist = np.empty(B)
+    dall = np.empty((B, K)) if all_distances else None
+    lib().oracle_kmeans_assign(B, D, _p(X), K, _p(C), _p(index), _p(dist), _p(dall))
+    return (index, dist, dall) if all_distances else (index, dist)
+
+
+def kmeans_update(X, index, C_prev):
+    """Means of the rows of X per assigned centroid; empty centroids keep C_prev."""
+    X = _c(X, np.float64)
+    C = np.array(C_prev, dtype=np.float64, copy=True, order="C")
+    index = _c(index, np.uint32)
+    counts = np.empty(C.shape[0], np.int64)
+    lib().oracle_kmeans_update(X.shape[0], X.shape[1], _p(X), C.shape[0], _p(index), _p(C), _p(counts))
+    return C, counts

@@ -1005,6 +1005,79 @@ void oracle_trace(const double* S, int64_t count, const double* P, const double*
     for (int64_t k = 0; k < count; ++k) trace(S, P + 3 * k, d + 3 * k, out + 4 * k);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Bucket compression (Section 2: buckets are highly repetitive and change  */
+/* only slightly from one to another, "a great case for a simple            */
+/* compression").  Reading R11: a palette of K buckets and an index map;    */
+/* bucket (i, j) holds palette bucket index[j w + i].  The encoder is        */
+/* k-means over the buckets as vectors of n^2 x 4 values (Lloyd's steps).   */
+/* ------------------------------------------------------------------------ */
+
+/* The dense texture a palette texture stands for (its definition): codes of
+ * bucket (i, j) = codes of palette bucket index[j w + i].  Palette codes are a
+ * K x 1 atlas (n rows of K n texels), elem_bytes per channel code; E4M3
+ * scales follow their palette bucket. */
+void oracle_palette_expand(int32_t W, int32_t H, int32_t n, int32_t K, int32_t elem_bytes, const void* palette,
+                           const float* palette_scales, const uint32_t* index, void* dense, float* dense_scales) {
+    const uint8_t* P = (const uint8_t*)palette;
+    uint8_t* D = (uint8_t*)dense;
+    int64_t texel = 4 * (int64_t)elem_bytes;
+    for (int64_t j = 0; j < H; ++j)
+        for (int64_t i = 0; i < W; ++i) {
+            int64_t k = index[j * W + i];
+            if (dense_scales) dense_scales[j * W + i] = palette_scales[k];
+            for (int64_t t = 0; t < n; ++t)
+                for (int64_t s = 0; s < n; ++s) {
+                    int64_t src = (t * (int64_t)K * n + k * n + s) * texel;
+                    int64_t dst = ((j * n + t) * (int64_t)W * n + i * n + s) * texel;
+                    memcpy(D + dst, P + src, (size_t)texel);
+                }
+        }
+}
+
+/* k-means assignment: for every row x_b of X (B x D), the nearest centroid
+ * index[b] = argmin_k |x_b - c_k|^2 (ties to the lowest k) and that squared
+ * distance; all distances in dist_all (B x K) when non-NULL. */
+void oracle_kmeans_assign(int64_t B, int64_t D, const double* X, int64_t K, const double* C, uint32_t* index,
+                          double* dist, double* dist_all) {
+#pragma omp parallel for schedule(static)
+    for (int64_t b = 0; b < B; ++b) {
+        double best = INFINITY;
+        int64_t arg = 0;
+        for (int64_t k = 0; k < K; ++k) {
+            double acc = 0.0;
+            for (int64_t d = 0; d < D; ++d) {
+                double e = X[b * D + d] - C[k * D + d];
+                acc += e * e;
+            }
+            if (dist_all) dist_all[b * K + k] = acc;
+            if (acc < best) {
+                best = acc;
+                arg = k;
+            }
+        }
+        index[b] = (uint32_t)arg;
+        if (dist) dist[b] = best;
+    }
+}
+
+/* k-means update: c_k = mean of the rows assigned to k; a centroid with no
+ * rows keeps its previous value (C holds the previous centroids on entry). */
+void oracle_kmeans_update(int64_t B, int64_t D, const double* X, int64_t K, const uint32_t* index, double* C,
+                          int64_t* counts) {
+    double* sum = (double*)calloc((size_t)(K * D), sizeof(double));
+    for (int64_t k = 0; k < K; ++k) counts[k] = 0;
+    for (int64_t b = 0; b < B; ++b) {
+        int64_t k = index[b];
+        counts[k] += 1;
+        for (int64_t d = 0; d < D; ++d) sum[k * D + d] += X[b * D + d];
+    }
+    for (int64_t k = 0; k < K; ++k)
+        if (counts[k] > 0)
+            for (int64_t d = 0; d < D; ++d) C[k * D + d] = sum[k * D + d] / (double)counts[k];
+    free(sum);
+}
+
 int32_t oracle_num_threads(void) {
 #ifdef _OPENMP
     return (int32_t)omp_get_max_threads();
