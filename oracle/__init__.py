@@ -78,6 +78,11 @@ def lib() -> ctypes.CDLL:
                 "oracle_palette_expand": (None, [I32, I32, I32, I32, I32, P, P, P, P, P]),
                 "oracle_kmeans_assign": (None, [I64, I64, P, I64, P, P, P, P]),
                 "oracle_kmeans_update": (None, [I64, I64, P, I64, P, P, P]),
+                "oracle_locate_world": (U32, [P, P, I32, I64, P, P, P, P, I32, P, P]),
+                "oracle_shade_world": (U32, [P, P, P, I32, I64, P, P, P, P, I32, P]),
+                "oracle_shade_world64": (U32, [P, P, P, I32, I64, P, P, P, P, I32, P]),
+                "oracle_shade_world_backward": (U32, [P, P, P, I32, I64, P, P, P, P, I32, P, P, P, P, P]),
+                "oracle_shade_world_backward64": (U32, [P, P, P, I32, I64, P, P, P, P, I32, P, P, P, P, P]),
                 "oracle_num_threads": (I32, []),
                 "oracle_set_num_threads": (None, [I32]),
             }
@@ -187,8 +192,10 @@ def encode_e4m3_buckets(atlas: np.ndarray, W: int, H: int, n: int):
 class Texture:
     """A texture as the oracle sees it: stored codes in the atlas layout plus E4M3 scales."""
 
-    def __init__(self, W: int, H: int, n: int, fmt: int, codes: np.ndarray, scales: np.ndarray | None = None):
+    def __init__(self, W: int, H: int, n: int, fmt: int, codes: np.ndarray, scales: np.ndarray | None = None,
+                 wrap: int = 0):
         self.W, self.H, self.n, self.fmt = int(W), int(H), int(n), int(fmt)
+        self.wrap = int(wrap)  # reading R12: bit 0 repeats u, bit 1 repeats v
         self.codes = _c(codes, _CODE_DTYPE[fmt])
         assert self.codes.shape == (H * n, W * n, 4), self.codes.shape
         self.scales = None if scales is None else _c(scales, np.float32)
@@ -218,7 +225,7 @@ def _tables(textures):
     for o, T in enumerate(textures):
         if T is None:
             continue
-        dims[o] = (T.W, T.H, T.n, T.fmt)
+        dims[o] = (T.W, T.H, T.n, T.fmt | (getattr(T, "wrap", 0) << 8))
         codes[o] = T.codes.ctypes.data
         scales[o] = None if T.scales is None else T.scales.ctypes.data
     return dims, codes, scales
@@ -279,6 +286,64 @@ def shade_backward(textures, uv, dirs, obj, filt: int, dL_dout, want_tex=True, w
     flags = fn(_p(dims), codes, scales, len(textures), F, _p(uv), _p(dirs), _p(obj), filt, _p(g),
                gptr if want_tex else None, _p(guv), _p(gdir))
     return (gtex if want_tex else None), guv, gdir, int(flags)
+
+
+# --------------------------------------------------------------------------
+# World-space variant (Eq. 1a with a per-fragment normal).
+# --------------------------------------------------------------------------
+
+def _normals(nrm, F, dtype):
+    nrm = _c(nrm, dtype).reshape(-1, 3)
+    assert nrm.shape[0] == F
+    return nrm
+
+
+def locate_world(textures, uv, dirs, nrm, obj, filt: int):
+    """Floors and continuous coordinates with A from Eq. 1a (I, N in one frame)."""
+    uv, dirs, obj = _gbuf(uv, dirs, obj, np.float32)
+    nrm = _normals(nrm, obj.shape[0], np.float32)
+    dims, codes, _ = _tables(textures)
+    idx = np.empty((obj.shape[0], 4), dtype=np.int32)
+    coord = np.empty((obj.shape[0], 4))
+    flags = lib().oracle_locate_world(_p(dims), codes, len(textures), obj.shape[0], _p(uv), _p(dirs), _p(nrm),
+                                      _p(obj), filt, _p(idx), _p(coord))
+    return idx, coord, int(flags)
+
+
+def shade_world(textures, uv, dirs, nrm, obj, filt: int, precise_inputs: bool = False):
+    """World-space synthesis: like shade, with A the first two entries of Eq. 1a."""
+    dtype = np.float64 if precise_inputs else np.float32
+    uv, dirs, obj = _gbuf(uv, dirs, obj, dtype)
+    nrm = _normals(nrm, obj.shape[0], dtype)
+    dims, codes, scales = _tables(textures)
+    out = np.empty((obj.shape[0], 4))
+    fn = lib().oracle_shade_world64 if precise_inputs else lib().oracle_shade_world
+    flags = fn(_p(dims), codes, scales, len(textures), obj.shape[0], _p(uv), _p(dirs), _p(nrm), _p(obj), filt,
+               _p(out))
+    return out, int(flags)
+
+
+def shade_world_backward(textures, uv, dirs, nrm, obj, filt: int, dL_dout, want_tex=True,
+                         precise_inputs: bool = False):
+    """(dL/dtex list, dL/duv, dL/ddir, dL/dnrm, flags) of the world-space synthesis."""
+    dtype = np.float64 if precise_inputs else np.float32
+    uv, dirs, obj = _gbuf(uv, dirs, obj, dtype)
+    nrm = _normals(nrm, obj.shape[0], dtype)
+    dims, codes, scales = _tables(textures)
+    g = _c(dL_dout, np.float64).reshape(-1, 4)
+    F = obj.shape[0]
+    gtex = [None] * len(textures)
+    gptr = (ctypes.c_void_p * max(len(textures), 1))()
+    if want_tex:
+        for o, T in enumerate(textures):
+            if T is not None:
+                gtex[o] = np.zeros((T.H * T.n, T.W * T.n, 4))
+                gptr[o] = gtex[o].ctypes.data
+    guv, gdir, gnrm = np.empty((F, 2)), np.empty((F, 3)), np.empty((F, 3))
+    fn = lib().oracle_shade_world_backward64 if precise_inputs else lib().oracle_shade_world_backward
+    flags = fn(_p(dims), codes, scales, len(textures), F, _p(uv), _p(dirs), _p(nrm), _p(obj), filt, _p(g),
+               gptr if want_tex else None, _p(guv), _p(gdir), _p(gnrm))
+    return (gtex if want_tex else None), guv, gdir, gnrm, int(flags)
 
 
 # --------------------------------------------------------------------------

@@ -352,6 +352,7 @@ void oracle_encode_e4m3_buckets(int32_t W, int32_t H, int32_t n, const float* at
 typedef struct {
     int64_t W, H, n;
     int32_t fmt;
+    int32_t wrap; /* reading R12: bit 0 repeats u, bit 1 repeats v (else clamp to edge) */
     const void* codes;
     const float* scale;
 } tex_t;
@@ -394,8 +395,27 @@ typedef struct {
 
 static int64_t clampi(int64_t x, int64_t lo, int64_t hi) { return x < lo ? lo : (x > hi ? hi : x); }
 
-/* Spatial axis (reading R5); size = w or h, x = u or v. */
-static void spatial_axis(double x, int64_t size, int bilinear, axis_t* a) {
+static int64_t wrapi(int64_t x, int64_t size) {
+    int64_t r = x % size;
+    return r < 0 ? r + size : r;
+}
+
+/* Spatial axis (reading R5, and R12 for the repeat address mode); size = w or
+ * h, x = u or v.  Repeat: c = x size (- 1/2 when bilinear) is not clamped;
+ * the taps are its floor (and floor + 1) modulo size. */
+static void spatial_axis(double x, int64_t size, int bilinear, int wrap, axis_t* a) {
+    if (wrap) {
+        double c = x * (double)size - (bilinear ? 0.5 : 0.0);
+        double f = floor(c);
+        a->c = c;
+        a->fl = (int64_t)f;
+        a->tap[0] = wrapi(a->fl, size);
+        a->tap[1] = bilinear ? wrapi(a->fl + 1, size) : a->tap[0];
+        a->w[1] = bilinear ? c - f : 0.0;
+        a->w[0] = 1.0 - a->w[1];
+        a->dc = bilinear ? (double)size : 0.0;
+        return;
+    }
     if (bilinear) {
         double c = x * (double)size - 0.5;
         a->dc = (c > -1.0 && c < (double)size) ? (double)size : 0.0;
@@ -452,12 +472,22 @@ typedef struct {
     double A[2], B[2];
 } lookup_t;
 
-static void locate_one(const tex_t* T, double u, double v, const double I[3], int filter, lookup_t* L) {
+/* N == NULL: I is in the tangent frame, Eq. 1b.  Otherwise I and N are in one
+ * (world) frame and A is the first two entries of Eq. 1a. */
+static void locate_one(const tex_t* T, double u, double v, const double I[3], const double* N, int filter,
+                       lookup_t* L) {
     int spatial_bilinear = (filter == OR_QUADRILINEAR);
     int angular_bilinear = (filter != OR_NEAREST);
-    spatial_axis(u, T->W, spatial_bilinear, &L->u);
-    spatial_axis(v, T->H, spatial_bilinear, &L->v);
-    equisolid_ts(I, L->A);  /* Eq. 1b */
+    spatial_axis(u, T->W, spatial_bilinear, T->wrap & 1, &L->u);
+    spatial_axis(v, T->H, spatial_bilinear, (T->wrap >> 1) & 1, &L->v);
+    if (N) {
+        double A3[3];
+        equisolid_normal(I, N, A3); /* Eq. 1a */
+        L->A[0] = A3[0];
+        L->A[1] = A3[1];
+    } else {
+        equisolid_ts(I, L->A); /* Eq. 1b */
+    }
     squarify(L->A, L->B);   /* Eq. 3 */
     angular_axis(L->B[0], T->n, angular_bilinear, &L->s);
     angular_axis(L->B[1], T->n, angular_bilinear, &L->t);
@@ -484,19 +514,21 @@ static void make_tex(const int32_t* dims, const void* const* codes, const float*
     T->W = dims[4 * o + 0];
     T->H = dims[4 * o + 1];
     T->n = dims[4 * o + 2];
-    T->fmt = dims[4 * o + 3];
+    T->fmt = dims[4 * o + 3] & 0xff;
+    T->wrap = (dims[4 * o + 3] >> 8) & 3;
     T->codes = codes[o];
     T->scale = scales ? scales[o] : NULL;
 }
 
 /* Validity of a fragment: 0 = background, 1 = shade, otherwise an error flag. */
 static uint32_t classify(int32_t o, int32_t n_obj, const void* const* codes, double u, double v,
-                         const double I[3], int* shade) {
+                         const double I[3], const double* N, int* shade) {
     *shade = 0;
     if (o < 0) return 0;
     if (o >= n_obj || codes[o] == NULL) return OR_FLAG_BAD_OBJ;
     if (!isfinite(u) || !isfinite(v) || !isfinite(I[0]) || !isfinite(I[1]) || !isfinite(I[2]))
         return OR_FLAG_NONFINITE;
+    if (N && (!isfinite(N[0]) || !isfinite(N[1]) || !isfinite(N[2]))) return OR_FLAG_NONFINITE;
     *shade = 1;
     return 0;
 }
@@ -504,15 +536,20 @@ static uint32_t classify(int32_t o, int32_t n_obj, const void* const* codes, dou
 /* Continuous coordinates and floors of every fragment (for index parity).
  * coord[4f..4f+3] = (c_u, c_v, c_s, c_t), idx likewise (floors); background
  * and invalid fragments get zeros. */
-uint32_t oracle_locate(const int32_t* dims, const void* const* codes, int32_t n_obj, int64_t F, const float* uv,
-                       const float* dir, const int32_t* obj, int32_t filter, int32_t* idx, double* coord) {
+static uint32_t locate_core(const int32_t* dims, const void* const* codes, int32_t n_obj, int64_t F,
+                            const float* uv, const float* dir, const float* nrm, const int32_t* obj, int32_t filter,
+                            int32_t* idx, double* coord) {
     uint32_t flags = 0;
 #pragma omp parallel for schedule(static) reduction(| : flags)
     for (int64_t f = 0; f < F; ++f) {
         double u = uv[2 * f], v = uv[2 * f + 1];
         double I[3] = {dir[3 * f], dir[3 * f + 1], dir[3 * f + 2]};
+        double Nw[3] = {0.0, 0.0, 0.0};
+        if (nrm)
+            for (int k = 0; k < 3; ++k) Nw[k] = nrm[3 * f + k];
+        const double* N = nrm ? Nw : NULL;
         int shade;
-        flags |= classify(obj[f], n_obj, codes, u, v, I, &shade);
+        flags |= classify(obj[f], n_obj, codes, u, v, I, N, &shade);
         for (int k = 0; k < 4; ++k) {
             idx[4 * f + k] = 0;
             coord[4 * f + k] = 0.0;
@@ -521,7 +558,7 @@ uint32_t oracle_locate(const int32_t* dims, const void* const* codes, int32_t n_
         tex_t T;
         make_tex(dims, codes, NULL, obj[f], &T);
         lookup_t L;
-        locate_one(&T, u, v, I, filter, &L);
+        locate_one(&T, u, v, I, N, filter, &L);
         const axis_t* ax[4] = {&L.u, &L.v, &L.s, &L.t};
         for (int k = 0; k < 4; ++k) {
             idx[4 * f + k] = (int32_t)ax[k]->fl;
@@ -531,30 +568,56 @@ uint32_t oracle_locate(const int32_t* dims, const void* const* codes, int32_t n_
     return flags;
 }
 
+uint32_t oracle_locate(const int32_t* dims, const void* const* codes, int32_t n_obj, int64_t F, const float* uv,
+                       const float* dir, const int32_t* obj, int32_t filter, int32_t* idx, double* coord) {
+    return locate_core(dims, codes, n_obj, F, uv, dir, NULL, obj, filter, idx, coord);
+}
+
+/* The world-space lookup (Eq. 1a with a per-fragment normal nrm, F x 3). */
+uint32_t oracle_locate_world(const int32_t* dims, const void* const* codes, int32_t n_obj, int64_t F,
+                             const float* uv, const float* dir, const float* nrm, const int32_t* obj, int32_t filter,
+                             int32_t* idx, double* coord) {
+    return locate_core(dims, codes, n_obj, F, uv, dir, nrm, obj, filter, idx, coord);
+}
+
+/* Reads fragment f of an FP32 or FP64 G-buffer; returns the normal pointer
+ * (NULL without a normal stream). */
+static const double* read_fragment(int64_t f, const float* uv32, const float* dir32, const float* nrm32,
+                                   const double* uv64, const double* dir64, const double* nrm64, double* u, double* v,
+                                   double I[3], double N[3]) {
+    if (uv64) {
+        *u = uv64[2 * f];
+        *v = uv64[2 * f + 1];
+        for (int k = 0; k < 3; ++k) I[k] = dir64[3 * f + k];
+        if (!nrm64) return NULL;
+        for (int k = 0; k < 3; ++k) N[k] = nrm64[3 * f + k];
+        return N;
+    }
+    *u = uv32[2 * f];
+    *v = uv32[2 * f + 1];
+    for (int k = 0; k < 3; ++k) I[k] = dir32[3 * f + k];
+    if (!nrm32) return NULL;
+    for (int k = 0; k < 3; ++k) N[k] = nrm32[3 * f + k];
+    return N;
+}
+
 static uint32_t shade_core(const int32_t* dims, const void* const* codes, const float* const* scales,
-                           int32_t n_obj, int64_t F, const float* uv32, const float* dir32, const double* uv64,
-                           const double* dir64, const int32_t* obj, int32_t filter, double* out) {
+                           int32_t n_obj, int64_t F, const float* uv32, const float* dir32, const float* nrm32,
+                           const double* uv64, const double* dir64, const double* nrm64, const int32_t* obj,
+                           int32_t filter, double* out) {
     uint32_t flags = 0;
 #pragma omp parallel for schedule(static) reduction(| : flags)
     for (int64_t f = 0; f < F; ++f) {
-        double u, v, I[3];
-        if (uv64) {
-            u = uv64[2 * f];
-            v = uv64[2 * f + 1];
-            for (int k = 0; k < 3; ++k) I[k] = dir64[3 * f + k];
-        } else {
-            u = uv32[2 * f];
-            v = uv32[2 * f + 1];
-            for (int k = 0; k < 3; ++k) I[k] = dir32[3 * f + k];
-        }
+        double u, v, I[3], Nb[3];
+        const double* N = read_fragment(f, uv32, dir32, nrm32, uv64, dir64, nrm64, &u, &v, I, Nb);
         int shade;
-        flags |= classify(obj[f], n_obj, codes, u, v, I, &shade);
+        flags |= classify(obj[f], n_obj, codes, u, v, I, N, &shade);
         for (int c = 0; c < 4; ++c) out[4 * f + c] = 0.0;
         if (!shade) continue;
         tex_t T;
         make_tex(dims, codes, scales, obj[f], &T);
         lookup_t L;
-        locate_one(&T, u, v, I, filter, &L);
+        locate_one(&T, u, v, I, N, filter, &L);
         colour_one(&T, &L, out + 4 * f);
     }
     return flags;
@@ -567,14 +630,27 @@ static uint32_t shade_core(const int32_t* dims, const void* const* codes, const 
 uint32_t oracle_shade(const int32_t* dims, const void* const* codes, const float* const* scales, int32_t n_obj,
                       int64_t F, const float* uv, const float* dir, const int32_t* obj, int32_t filter,
                       double* out) {
-    return shade_core(dims, codes, scales, n_obj, F, uv, dir, NULL, NULL, obj, filter, out);
+    return shade_core(dims, codes, scales, n_obj, F, uv, dir, NULL, NULL, NULL, NULL, obj, filter, out);
 }
 
 /* The same with an FP64 G-buffer (finite-difference pins). */
 uint32_t oracle_shade64(const int32_t* dims, const void* const* codes, const float* const* scales, int32_t n_obj,
                         int64_t F, const double* uv, const double* dir, const int32_t* obj, int32_t filter,
                         double* out) {
-    return shade_core(dims, codes, scales, n_obj, F, NULL, NULL, uv, dir, obj, filter, out);
+    return shade_core(dims, codes, scales, n_obj, F, NULL, NULL, NULL, uv, dir, NULL, obj, filter, out);
+}
+
+/* World-space synthesis: dir (I) and nrm (N) in one frame, A from Eq. 1a. */
+uint32_t oracle_shade_world(const int32_t* dims, const void* const* codes, const float* const* scales,
+                            int32_t n_obj, int64_t F, const float* uv, const float* dir, const float* nrm,
+                            const int32_t* obj, int32_t filter, double* out) {
+    return shade_core(dims, codes, scales, n_obj, F, uv, dir, nrm, NULL, NULL, NULL, obj, filter, out);
+}
+
+uint32_t oracle_shade_world64(const int32_t* dims, const void* const* codes, const float* const* scales,
+                              int32_t n_obj, int64_t F, const double* uv, const double* dir, const double* nrm,
+                              const int32_t* obj, int32_t filter, double* out) {
+    return shade_core(dims, codes, scales, n_obj, F, NULL, NULL, NULL, uv, dir, nrm, obj, filter, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -621,32 +697,40 @@ static void equisolid_jacobian(const double I[3], double J[2][3]) {
         for (int c = 0; c < 3; ++c) J[r][c] = SQRT2 * ((r == c ? 1.0 / D : 0.0) - I[r] * g[c] / D3);
 }
 
+/* Jacobian of Eq. 1a's first two entries with respect to I (and equally N):
+ * with h = I + N, L = |h|: dA_r/dh_c = sqrt(2) (delta_rc / L - h_r h_c / L^3). */
+static void equisolid_normal_jacobian(const double I[3], const double N[3], double J[2][3]) {
+    double h[3] = {I[0] + N[0], I[1] + N[1], I[2] + N[2]};
+    double L = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+    if (L == 0.0) {
+        memset(J, 0, sizeof(double) * 6);
+        return;
+    }
+    double L3 = L * L * L;
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 3; ++c) J[r][c] = SQRT2 * ((r == c ? 1.0 / L : 0.0) - h[r] * h[c] / L3);
+}
+
 static uint32_t backward_core(const int32_t* dims, const void* const* codes, const float* const* scales,
-                              int32_t n_obj, int64_t F, const float* uv32, const float* dir32, const double* uv64,
-                              const double* dir64, const int32_t* obj, int32_t filter, const double* dL_dout,
-                              double* const* dL_dtex, double* dL_duv, double* dL_ddir) {
+                              int32_t n_obj, int64_t F, const float* uv32, const float* dir32, const float* nrm32,
+                              const double* uv64, const double* dir64, const double* nrm64, const int32_t* obj,
+                              int32_t filter, const double* dL_dout, double* const* dL_dtex, double* dL_duv,
+                              double* dL_ddir, double* dL_dnrm) {
     uint32_t flags = 0;
     /* Texel gradients are summed serially, in fragment order. */
     for (int64_t f = 0; f < F; ++f) {
-        double u, v, I[3];
-        if (uv64) {
-            u = uv64[2 * f];
-            v = uv64[2 * f + 1];
-            for (int k = 0; k < 3; ++k) I[k] = dir64[3 * f + k];
-        } else {
-            u = uv32[2 * f];
-            v = uv32[2 * f + 1];
-            for (int k = 0; k < 3; ++k) I[k] = dir32[3 * f + k];
-        }
+        double u, v, I[3], Nb[3];
+        const double* N = read_fragment(f, uv32, dir32, nrm32, uv64, dir64, nrm64, &u, &v, I, Nb);
         if (dL_duv) dL_duv[2 * f] = dL_duv[2 * f + 1] = 0.0;
         if (dL_ddir) dL_ddir[3 * f] = dL_ddir[3 * f + 1] = dL_ddir[3 * f + 2] = 0.0;
+        if (dL_dnrm) dL_dnrm[3 * f] = dL_dnrm[3 * f + 1] = dL_dnrm[3 * f + 2] = 0.0;
         int shade;
-        flags |= classify(obj[f], n_obj, codes, u, v, I, &shade);
+        flags |= classify(obj[f], n_obj, codes, u, v, I, N, &shade);
         if (!shade) continue;
         tex_t T;
         make_tex(dims, codes, scales, obj[f], &T);
         lookup_t L;
-        locate_one(&T, u, v, I, filter, &L);
+        locate_one(&T, u, v, I, N, filter, &L);
         const double* g = dL_dout + 4 * f;
         const double dw[2] = {-1.0, 1.0}; /* d(weight of tap k)/dc for a bilinear axis */
         double gu = 0.0, gv = 0.0, gs = 0.0, gt = 0.0;
@@ -669,13 +753,20 @@ static uint32_t backward_core(const int32_t* dims, const void* const* codes, con
             dL_duv[2 * f] = gu * L.u.dc;
             dL_duv[2 * f + 1] = gv * L.v.dc;
         }
-        if (dL_ddir) {
+        if (dL_ddir || dL_dnrm) {
             double gB[2] = {gs * L.s.dc, gt * L.t.dc};
             double J3[2][2], J1[2][3];
             squarify_jacobian(L.A, J3);
-            equisolid_jacobian(I, J1);
+            if (N)
+                equisolid_normal_jacobian(I, N, J1); /* dA/dI = dA/dN */
+            else
+                equisolid_jacobian(I, J1);
             double gA[2] = {gB[0] * J3[0][0] + gB[1] * J3[1][0], gB[0] * J3[0][1] + gB[1] * J3[1][1]};
-            for (int c = 0; c < 3; ++c) dL_ddir[3 * f + c] = gA[0] * J1[0][c] + gA[1] * J1[1][c];
+            for (int c = 0; c < 3; ++c) {
+                double gI = gA[0] * J1[0][c] + gA[1] * J1[1][c];
+                if (dL_ddir) dL_ddir[3 * f + c] = gI;
+                if (dL_dnrm && N) dL_dnrm[3 * f + c] = gI;
+            }
         }
     }
     return flags;
@@ -688,16 +779,34 @@ uint32_t oracle_shade_backward(const int32_t* dims, const void* const* codes, co
                                int32_t n_obj, int64_t F, const float* uv, const float* dir, const int32_t* obj,
                                int32_t filter, const double* dL_dout, double* const* dL_dtex, double* dL_duv,
                                double* dL_ddir) {
-    return backward_core(dims, codes, scales, n_obj, F, uv, dir, NULL, NULL, obj, filter, dL_dout, dL_dtex, dL_duv,
-                         dL_ddir);
+    return backward_core(dims, codes, scales, n_obj, F, uv, dir, NULL, NULL, NULL, NULL, obj, filter, dL_dout, dL_dtex,
+                         dL_duv, dL_ddir, NULL);
 }
 
 uint32_t oracle_shade_backward64(const int32_t* dims, const void* const* codes, const float* const* scales,
                                  int32_t n_obj, int64_t F, const double* uv, const double* dir, const int32_t* obj,
                                  int32_t filter, const double* dL_dout, double* const* dL_dtex, double* dL_duv,
                                  double* dL_ddir) {
-    return backward_core(dims, codes, scales, n_obj, F, NULL, NULL, uv, dir, obj, filter, dL_dout, dL_dtex, dL_duv,
-                         dL_ddir);
+    return backward_core(dims, codes, scales, n_obj, F, NULL, NULL, NULL, uv, dir, NULL, obj, filter, dL_dout, dL_dtex,
+                         dL_duv, dL_ddir, NULL);
+}
+
+/* World-space gradients: additionally dL/dN (F x 3; equal to dL/dI, since A
+ * depends on I + N only). */
+uint32_t oracle_shade_world_backward(const int32_t* dims, const void* const* codes, const float* const* scales,
+                                     int32_t n_obj, int64_t F, const float* uv, const float* dir, const float* nrm,
+                                     const int32_t* obj, int32_t filter, const double* dL_dout,
+                                     double* const* dL_dtex, double* dL_duv, double* dL_ddir, double* dL_dnrm) {
+    return backward_core(dims, codes, scales, n_obj, F, uv, dir, nrm, NULL, NULL, NULL, obj, filter, dL_dout, dL_dtex,
+                         dL_duv, dL_ddir, dL_dnrm);
+}
+
+uint32_t oracle_shade_world_backward64(const int32_t* dims, const void* const* codes, const float* const* scales,
+                                       int32_t n_obj, int64_t F, const double* uv, const double* dir,
+                                       const double* nrm, const int32_t* obj, int32_t filter, const double* dL_dout,
+                                       double* const* dL_dtex, double* dL_duv, double* dL_ddir, double* dL_dnrm) {
+    return backward_core(dims, codes, scales, n_obj, F, NULL, NULL, NULL, uv, dir, nrm, obj, filter, dL_dout,
+                         dL_dtex, dL_duv, dL_ddir, dL_dnrm);
 }
 
 /* ------------------------------------------------------------------------ */
