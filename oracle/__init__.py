@@ -19,7 +19,7 @@ import threading
 
 import numpy as np
 
-F32, F16, BF16, E4M3, F64 = 0, 1, 2, 3, 4
+F32, F16, BF16, E4M3, F64, BIT1 = 0, 1, 2, 3, 4, 5
 NEAREST, ANGULAR_BILINEAR, QUADRILINEAR = 0, 1, 2
 FLAG_BAD_OBJ, FLAG_NONFINITE = 1, 2
 
@@ -29,7 +29,7 @@ _LIB = os.path.join(_HERE, "libradtex_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-_CODE_DTYPE = {F32: np.float32, F16: np.uint16, BF16: np.uint16, E4M3: np.uint8, F64: np.float64}
+_CODE_DTYPE = {F32: np.float32, F16: np.uint16, BF16: np.uint16, E4M3: np.uint8, F64: np.float64, BIT1: np.uint8}
 
 
 def build(force: bool = False) -> str:
@@ -83,6 +83,8 @@ def lib() -> ctypes.CDLL:
                 "oracle_shade_world64": (U32, [P, P, P, I32, I64, P, P, P, P, I32, P]),
                 "oracle_shade_world_backward": (U32, [P, P, P, I32, I64, P, P, P, P, I32, P, P, P, P, P]),
                 "oracle_shade_world_backward64": (U32, [P, P, P, I32, I64, P, P, P, P, I32, P, P, P, P, P]),
+                "oracle_bake_shadow": (None, [I32, I32, I32, I32, P, ctypes.c_double, P, P]),
+                "oracle_bake_shadow_texels": (None, [I32, I32, I32, I32, P, ctypes.c_double, I64, P, P, P]),
                 "oracle_num_threads": (I32, []),
                 "oracle_set_num_threads": (None, [I32]),
             }
@@ -503,3 +505,33 @@ def kmeans_update(X, index, C_prev):
     counts = np.empty(C.shape[0], np.int64)
     lib().oracle_kmeans_update(X.shape[0], X.shape[1], _p(X), C.shape[0], _p(index), _p(C), _p(counts))
     return C, counts
+
+
+# --------------------------------------------------------------------------
+# Shadow textures (Section 5, "Shadowing"; reading R13).
+# --------------------------------------------------------------------------
+
+def bake_shadow(W: int, H: int, n: int, surface: int, scene: dict, delta: float = 2.0 ** -17):
+    """Visibility bits ((H n) x (W n) uint8, atlas order) towards every texel
+    direction (Eq. 4a, Eq. 2c), and the band of texels whose bit changes under
+    perturbed rays."""
+    S = scene_array(scene)
+    vis = np.empty((H * n, W * n), np.uint8)
+    band = np.empty_like(vis)
+    lib().oracle_bake_shadow(W, H, n, surface, _p(S), float(delta), _p(vis), _p(band))
+    return vis, band.astype(bool)
+
+
+def bake_shadow_texels(W: int, H: int, n: int, surface: int, scene: dict, ijst, delta: float = 2.0 ** -17):
+    S = scene_array(scene)
+    q = _c(ijst, np.int32).reshape(-1, 4)
+    vis = np.empty(q.shape[0], np.uint8)
+    band = np.empty_like(vis)
+    lib().oracle_bake_shadow_texels(W, H, n, surface, _p(S), float(delta), q.shape[0], _p(q), _p(vis), _p(band))
+    return vis, band.astype(bool)
+
+
+def bit_texture(bits: np.ndarray, W: int, H: int, n: int) -> "Texture":
+    """A 1-bit texture from per-texel bits ((H n) x (W n)), value in every channel."""
+    b = np.asarray(bits, np.uint8).reshape(H * n, W * n)
+    return Texture(W, H, n, BIT1, np.repeat(b[..., None], 4, axis=2))

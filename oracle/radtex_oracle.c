@@ -63,7 +63,8 @@
 #define OR_F16 1
 #define OR_BF16 2
 #define OR_E4M3 3
-#define OR_F64 4 /* oracle-only exact format, used by the pins */
+#define OR_F64 4  /* oracle-only exact format, used by the pins */
+#define OR_BIT1 5 /* 1-bit payload (reading R13): code 0 or 1, the texel value in every channel */
 
 #define OR_NEAREST 0
 #define OR_ANGULAR_BILINEAR 1
@@ -374,6 +375,8 @@ static double texel(const tex_t* T, int64_t i, int64_t j, int64_t s, int64_t t, 
             return decode_bf16(((const uint16_t*)T->codes)[e]);
         case OR_E4M3:
             return decode_e4m3(((const uint8_t*)T->codes)[e]) * (double)T->scale[j * T->W + i];
+        case OR_BIT1:
+            return (double)(((const uint8_t*)T->codes)[e] & 1u);
         default:
             return ((const double*)T->codes)[e];
     }
@@ -1091,6 +1094,80 @@ void oracle_bake_texels(int32_t W, int32_t H, int32_t n, int32_t surface, const 
         const int32_t* q = ijst + 4 * k;
         bake_texel(S, surface, W, H, n, q[0], q[1], q[2], q[3], delta, val + 4 * k, lo ? lo + 4 * k : NULL,
                    hi ? hi + 4 * k : NULL);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Shadow textures (Section 5, "Shadowing"; reading R13): a 1-bit radiance   */
+/* texture keyed by the light direction.  The bit of texel (i, j, s, t) says  */
+/* whether the ray from the bucket's surface point towards the direction of  */
+/* texel (s, t) -- Eq. 4a then Eq. 2c, taken to world space -- reaches the   */
+/* sky (1) or is blocked by the sphere or the plane at t > eps (0).           */
+/* ------------------------------------------------------------------------ */
+
+/* Occlusion of the ray P + t d (d unit), written geometrically: the sphere
+ * blocks it when the ray passes within r of the centre and its entry point
+ * lies ahead (t > eps); the plane when it is crossed at t > eps. */
+static int occluded(const double* S, const double P[3], const double d[3]) {
+    double eps = S[BK_EPS], r = S[BK_SPHERE_R];
+    double oc[3] = {S[BK_SPHERE_C] - P[0], S[BK_SPHERE_C + 1] - P[1], S[BK_SPHERE_C + 2] - P[2]};
+    double tc = dot3(oc, d); /* closest approach along the ray */
+    double x[3] = {oc[0] - tc * d[0], oc[1] - tc * d[1], oc[2] - tc * d[2]};
+    double m2 = dot3(x, x);
+    if (m2 < r * r && tc - sqrt(r * r - m2) > eps) return 1;
+    if (d[1] != 0.0 && (S[BK_PLANE_Y] - P[1]) / d[1] > eps) return 1;
+    return 0;
+}
+
+/* Visibility bit of one texel, and whether it changes under the ten perturbed
+ * rays of bake_texel (a ray grazing an occluder: either bit is correct). */
+static void shadow_texel(const double* S, int surface, int64_t W, int64_t H, int64_t n, int64_t i, int64_t j,
+                         int64_t s, int64_t t, double delta, uint8_t* vis, uint8_t* band) {
+    double u = ((double)i + 0.5) / W, v = ((double)j + 0.5) / H;
+    double P[3], F[3][3], I[3];
+    surface_frame(S, surface, u, v, P, F);
+    texel_direction(s, t, n, I); /* Eq. 4a then Eq. 2c */
+    double d[3];
+    for (int k = 0; k < 3; ++k) d[k] = I[0] * F[0][k] + I[1] * F[1][k] + I[2] * F[2][k];
+    int o = occluded(S, P, d);
+    *vis = (uint8_t)(o ? 0 : 1);
+    if (!band) return;
+    *band = 0;
+    for (int m = 0; m < 10 && !*band; ++m) {
+        double Pp[3] = {P[0], P[1], P[2]}, dp[3] = {d[0], d[1], d[2]};
+        double sg = (m & 1) ? -delta : delta;
+        if (m < 4) {
+            for (int k = 0; k < 3; ++k) Pp[k] += sg * F[m >> 1][k];
+        } else {
+            for (int k = 0; k < 3; ++k) dp[k] += sg * F[(m - 4) >> 1][k];
+            normalize3(dp);
+        }
+        if (occluded(S, Pp, dp) != o) *band = 1;
+    }
+}
+
+/* Shadow bake of a w x h x n x n texture: vis and band (NULL to skip), one
+ * byte per texel in the atlas order of reading R4. */
+void oracle_bake_shadow(int32_t W, int32_t H, int32_t n, int32_t surface, const double* S, double delta,
+                        uint8_t* vis, uint8_t* band) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t bk = 0; bk < (int64_t)W * H; ++bk) {
+        int64_t i = bk % W, j = bk / W;
+        for (int64_t t = 0; t < n; ++t)
+            for (int64_t s = 0; s < n; ++s) {
+                int64_t e = (j * n + t) * (int64_t)W * n + (i * n + s);
+                shadow_texel(S, surface, W, H, n, i, j, s, t, delta, vis + e, band ? band + e : NULL);
+            }
+    }
+}
+
+/* The same for a list of texels ijst (count x 4 int32). */
+void oracle_bake_shadow_texels(int32_t W, int32_t H, int32_t n, int32_t surface, const double* S, double delta,
+                               int64_t count, const int32_t* ijst, uint8_t* vis, uint8_t* band) {
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < count; ++k) {
+        const int32_t* q = ijst + 4 * k;
+        shadow_texel(S, surface, W, H, n, q[0], q[1], q[2], q[3], delta, vis + k, band ? band + k : NULL);
     }
 }
 
