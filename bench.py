@@ -57,6 +57,9 @@ def parse_args(argv=None):
                    help="voronoi64: 64 objects of uneven sizes, 4 views of 3840x2160, forward in a CUDA graph; "
                         "bake: rt_bake of the sphere-plane workload's two textures")
     p.add_argument("--objects", type=int, default=64)
+    p.add_argument("--palette", type=int, default=0,
+                   help="sphere-plane: compress each texture to a K-bucket palette (k-means) before timing")
+    p.add_argument("--palette-iters", type=int, default=4, help="Lloyd steps of the palette encoder")
     p.add_argument("--mem-fraction", type=float, default=0.7,
                    help="voronoi64: largest share of free device memory the textures may take")
     return p.parse_args(argv)
@@ -92,8 +95,59 @@ def whole_job_rate(fragments_per_rank: int, world: int, ms: float) -> float:
 
 
 def workload_name(a) -> str:
+    pal = f", palette K={a.palette}" if getattr(a, "palette", 0) else ""
     return (f"sphere+plane {a.width}x{a.height} x {a.views} poses, 2 objects x {a.buckets}^2 buckets x {a.n}^2 "
-            f"directions {a.storage.upper()}, {a.filter}")
+            f"directions {a.storage.upper()}{pal}, {a.filter}")
+
+
+def encode_palettes(a, api, ctx, oids, uv, dirs, obj, dev, h_obj):
+    """k-means palettes of the dense textures (timed), the palette textures that
+    replace them, and the PSNR of their shading against the dense textures' on
+    the first pose."""
+    import torch
+
+    K = a.palette
+    B = a.buckets * a.buckets
+    D = a.n * a.n * 4
+    new_ids, sse, times = [], [], []
+    ref = api.rt_shade(ctx, uv[0].reshape(-1, 2), dirs[0].reshape(-1, 3), obj[0].reshape(-1),
+                       api.FILTER_NAMES[a.filter])
+    assign_ms = []
+    for k, oid in enumerate(oids):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        C, index, e = api.palette_encode(ctx, oid, K, a.palette_iters, seed=k)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        sse.append(e)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        api.rt_kmeans_assign(ctx, oid, K, C, index)
+        s1.record()
+        torch.cuda.synchronize()
+        assign_ms.append(s0.elapsed_time(s1))
+        pid = api.rt_create_palette_texture(ctx, a.buckets, a.buckets, a.n, K, api.FORMAT_NAMES[a.storage],
+                                            api.RT_LAYOUT_PLANES, C, index)
+        new_ids.append(pid)
+    # the palette ids replace the dense ones in the G-buffer (ids 0, 1 -> the new ids)
+    remap = torch.full((max(oids) + 1,), -1, dtype=torch.int32, device=dev)
+    for o, p in zip(oids, new_ids):
+        remap[o] = p
+    valid = obj >= 0
+    obj.copy_(torch.where(valid, remap[obj.clamp(min=0).long()], obj))
+    h_obj.copy_(obj.reshape(-1).cpu())
+    for o in oids:
+        api.rt_destroy_texture(ctx, o)
+    out = api.rt_shade(ctx, uv[0].reshape(-1, 2), dirs[0].reshape(-1, 3), obj[0].reshape(-1),
+                       api.FILTER_NAMES[a.filter])
+    mse = float(((out - ref) ** 2)[obj[0].reshape(-1) >= 0].mean())
+    ms = float(np.mean(assign_ms))
+    info = {"K": K, "iterations": a.palette_iters, "encode_s": [round(t, 3) for t in times],
+            "sse_first_last": [[x[0], x[-1]] for x in sse],
+            "assign_ms": ms, "assign_tflops": 2.0 * B * K * D / (ms * 1e-3) / 1e12,
+            "texture_bytes": int(sum(api.rt_texture_info(ctx, p)["bytes"] for p in new_ids)),
+            "psnr_vs_dense_db": float(10 * np.log10(1.0 / mse)) if mse > 0 else None}
+    return info, new_ids
 
 
 def bytes_per_texel(storage: str) -> int:
@@ -353,10 +407,14 @@ def run_radtex(a):
         api.rt_fill_bucket_lobes(ctx, oid, params)
         oids.append(oid)
     torch.cuda.synchronize()
+    palette = None
+    if a.palette:
+        palette, oids = encode_palettes(a, api, ctx, oids, uv, dirs, obj, dev, h_obj)
     out = torch.empty((*shape, 4), dtype=torch.float32, device=dev)
     duv = torch.empty((*shape, 2), dtype=torch.float32, device=dev)
     ddir = torch.empty((*shape, 3), dtype=torch.float32, device=dev)
-    dtex = {o: torch.empty((a.n, a.n, a.buckets, a.buckets, 4), dtype=torch.float32, device=dev) for o in oids}
+    stored = (a.palette,) if a.palette else (a.buckets, a.buckets)
+    dtex = {o: torch.empty((a.n, a.n, *stored, 4), dtype=torch.float32, device=dev) for o in oids}
 
     # Algorithmic bytes: distinct texels per frame (counted outside the timed region).
     distinct = 0
@@ -368,8 +426,9 @@ def run_radtex(a):
     scale_bytes = 0  # E4M3 scales: 4 B per distinct bucket, counted as at most one per texel quad below
     if a.storage == "e4m3":
         scale_bytes = distinct // (a.n * a.n) * 4
-    fwd_bytes = 40 * F + distinct * tb + scale_bytes
-    bwd_bytes = (24 + 16 + 8 + 12) * F + distinct * (tb + 32) + scale_bytes
+    index_bytes = sum(4 * a.buckets * a.buckets for _ in oids) if a.palette else 0  # whole index maps, an upper bound
+    fwd_bytes = 40 * F + distinct * tb + scale_bytes + index_bytes
+    bwd_bytes = (24 + 16 + 8 + 12) * F + distinct * (tb + 32) + scale_bytes + index_bytes
 
     stream = torch.cuda.current_stream(dev)
     # screen tile of the batched kernels, picked by the library's autotuner on this workload
@@ -506,7 +565,8 @@ def run_radtex(a):
                    "step": ("rt_shade_batched + zero texel grads + rt_shade_batched_backward(RT_ACCUMULATE, "
                             "dL/dout = out)"),
                    "tile": {"tw": tile[0], "th": tile[1], "bx": tile[2], "by": tile[3], "autotune_ms": tile_ms},
-                   "distinct_texels_per_step": int(distinct), "scene_gen_s": round(scene_s, 2)},
+                   "distinct_texels_per_step": int(distinct), "scene_gen_s": round(scene_s, 2),
+                   "palette": palette},
         "fwd_gfrag_s": F / (fwd_ms * 1e-3) / 1e9, "bwd_gfrag_s": F / (bwd_ms * 1e-3) / 1e9,
         "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "zero_grad_ms": zero_ms,
         "roofline": dominant, "roofline_fwd": r_fwd, "roofline_bwd": r_bwd,

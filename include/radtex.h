@@ -64,7 +64,10 @@ typedef enum {
     RT_F32 = 0,              /* 16 bytes per texel */
     RT_F16 = 1,              /* 8 bytes per texel, round to nearest even */
     RT_BF16 = 2,             /* 8 bytes per texel, round to nearest even */
-    RT_E4M3_BUCKET_SCALE = 3 /* 4 bytes per texel: OCP FP8 E4M3 codes of v / s, s = (bucket amax) / 448 */
+    RT_E4M3_BUCKET_SCALE = 3, /* 4 bytes per texel: OCP FP8 E4M3 codes of v / s, s = (bucket amax) / 448 */
+    RT_BIT1 = 4               /* 1 bit per texel (shadow textures, Section 5): bit k of 32-bit word k >> 5 holds
+                                 texel k of the PLANES numbering; the value (0 or 1) fills every channel.
+                                 Created from FP32 by channel 0 >= 1/2, or by rt_bake_shadow */
 } rt_format;
 
 typedef enum {
@@ -75,8 +78,10 @@ typedef enum {
 
 typedef enum { RT_LAYOUT_ATLAS = 0, RT_LAYOUT_PLANES = 1 } rt_layout;
 
-/* rt_create_texture flags */
+/* rt_create_texture / rt_create_palette_texture flags */
 #define RT_BORROW 1          /* use the caller's FP32 buffer in place; no copy */
+#define RT_WRAP_U 2          /* repeat in u: taps floor(c) mod w instead of clamp to edge (|u| w < 2^30) */
+#define RT_WRAP_V 4          /* repeat in v likewise */
 /* rt_shade_backward flags */
 #define RT_ACCUMULATE 1      /* add into dL_dtex / dL_duv / dL_ddir instead of overwriting */
 #define RT_DETERMINISTIC 2   /* bit-reproducible texel gradients (fixed-point sums; see rt_prepare_deterministic) */
@@ -113,7 +118,8 @@ rt_status rt_create_texture(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, rt_for
 rt_status rt_destroy_texture(rt_ctx* ctx, int32_t obj_id);
 
 /* Properties of an object (any output pointer may be NULL).  bytes = texel
- * storage plus scales. */
+ * storage plus scales (plus the index map of a palette texture); layout is
+ * 2 for a palette texture (w, h are then its bucket matrix). */
 rt_status rt_texture_info(rt_ctx* ctx, int32_t obj_id, int32_t* w, int32_t* h, int32_t* n, int32_t* storage,
                           int32_t* layout, int64_t* bytes);
 
@@ -131,6 +137,56 @@ rt_status rt_read_texture(rt_ctx* ctx, int32_t obj_id, rt_layout dst_layout, voi
  * per bucket (rho_r, rho_g, rho_b, d_x, d_y, d_z, p, unused), row-major.
  * RT_ERR_UNSUPPORTED for a borrowed texture. */
 rt_status rt_fill_bucket_lobes(rt_ctx* ctx, int32_t obj_id, const float* params, rt_stream_t stream);
+
+/* Palette textures: bucket compression.  Section 2 notes that buckets are
+ * highly repetitive and change only slightly from one to another, which
+ * suits a simple compression.  A palette texture stores K palette buckets of
+ * n x n texels plus a w x h index map; bucket (i, j) reads palette bucket
+ * index[j w + i].  Shading, lookup, footprint and backward accept palette
+ * textures unchanged.  Their texel gradients are per palette texel: dL_dtex
+ * holds K n^2 texels in PLANES order (n, n, K, 4).  rt_fill_bucket_lobes and
+ * rt_bake return RT_ERR_UNSUPPORTED for them.
+ * palette (device, FP32): the K buckets as a K x 1 texture in src_layout,
+ * i.e. n x K n texels (ATLAS) or (n, n, K, 4) (PLANES), encoded into
+ * `storage`.  E4M3 has one scale per palette bucket.
+ * index (device, h x w uint32): every entry must be < K, else
+ * RT_ERR_INVALID_ARG.  The map is copied.
+ * RT_BORROW (FP32, PLANES only) uses the caller's palette buffer in place.
+ * 1 <= K <= 2^30.  Synchronous; allocates the palette (unless borrowed) and
+ * the index map. */
+rt_status rt_create_palette_texture(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, int32_t K, rt_format storage,
+                                    rt_layout src_layout, const float* palette, const uint32_t* index, int32_t flags,
+                                    int32_t* obj_id_out);
+
+/* *K = the palette size of obj_id, 0 for a dense texture.  rt_read_texture of
+ * a palette texture returns its palette as a K x 1 texture. */
+rt_status rt_palette_size(rt_ctx* ctx, int32_t obj_id, int32_t* K);
+
+/* The palette encoder: Lloyd's k-means over the buckets of a dense texture
+ * (owned, or borrowed FP32), each bucket a vector x_b of n^2 x 4 decoded
+ * texel values, b = j w + i.  Centroids are FP32 in a K x 1 texture's PLANES
+ * order: centroid k, texel (s, t) at float4 (t n + s) K + k.  So a centroid
+ * buffer is a valid `palette` for rt_create_palette_texture with
+ * RT_LAYOUT_PLANES, and the assignment is its index map.  1 <= K <= 2^24.
+ * All three calls are asynchronous on `stream` and allocate nothing.
+ *
+ * rt_kmeans_init: centroid k = x_{buckets[k]}.  buckets is device int32 x K.
+ * An entry outside [0, w h) is clamped and raises RT_ERR_INVALID_ARG in
+ * rt_get_error.
+ *
+ * rt_kmeans_assign: index[b] = argmin_k |x_b - c_k|^2, ties to the lower k.
+ * Computed in FP32 as |c_k|^2 - 2 x_b . c_k.  dist (device FP32 x w h, may
+ * be NULL) receives that squared distance.
+ *
+ * rt_kmeans_update: c_k = mean of the x_b with index[b] = k, summed in FP64.
+ * A centroid with no member keeps its value.  scratch: device uint32,
+ * w h + 3 K + 1 entries. */
+rt_status rt_kmeans_init(rt_ctx* ctx, int32_t obj_id, int32_t K, const int32_t* buckets, float* centroids,
+                         rt_stream_t stream);
+rt_status rt_kmeans_assign(rt_ctx* ctx, int32_t obj_id, int32_t K, const float* centroids, uint32_t* index,
+                           float* dist, rt_stream_t stream);
+rt_status rt_kmeans_update(rt_ctx* ctx, int32_t obj_id, int32_t K, const uint32_t* index, float* centroids,
+                           uint32_t* scratch, rt_stream_t stream);
 
 /* Baking (Section 2.2, Eq. 4a and Eq. 4b).  The scene that is ray traced into
  * a texture: a sphere, the ground plane y = plane_height and a sky.  The paper
@@ -230,6 +286,43 @@ rt_status rt_shade_backward(rt_ctx* ctx, const float* uv, const float* dir, cons
  * GPU schedules fragments).  Range |sum| < 2^31, resolution 2^-32.  A
  * synchronous set-up call; RT_ERR_OOM when the buffers do not fit. */
 rt_status rt_prepare_deterministic(rt_ctx* ctx);
+
+/* Shadow bake (Section 5, "Shadowing"): fills an owned RT_BIT1 texture with
+ * the visibility of the sky from the bucket centre's surface point (the
+ * parametrisations of rt_bake) towards every texel's direction:
+ * B_k = (2k+1)/n - 1, A = Eq. 4a(B), L = Eq. 2c(A), rotated to world space.
+ * The bit is 1 when the ray P + t L meets neither the sphere (entering root)
+ * nor the plane at t > ray_offset.  At shading time the light direction, in
+ * the tangent frame, takes the place of the view direction.  Asynchronous;
+ * RT_ERR_UNSUPPORTED for textures that are not owned RT_BIT1. */
+rt_status rt_bake_shadow(rt_ctx* ctx, int32_t obj_id, rt_surface surface, const rt_bake_scene* scene,
+                         rt_stream_t stream);
+
+/* Several lookups per fragment, averaged: out[f] = (1/S) sum_k lookup(uv[f],
+ * dirs[f S + k]), with dirs F x S x 3 (16-byte aligned) and S = samples >= 1.
+ * With a shadow texture and S light directions spread over an area light this
+ * gives area (soft) shadows ("more than one sample per bucket", Section 5).
+ * Flat fragment stream. */
+rt_status rt_shade_multi(rt_ctx* ctx, const float* uv, const float* dirs, int32_t samples, const int32_t* obj,
+                         int64_t F, rt_filter filter, float* out, rt_stream_t stream);
+
+/* World-space variant (Eq. 1a).  The incidence I (dir, F x 3) and a
+ * per-fragment normal N (nrm, F x 3, 16-byte aligned) are given in one frame,
+ * with no tangent transform.  A is the first two entries of
+ * sqrt(2) (I + N) / |I + N|.  With N = +z this is Eq. 1b, the tangent-space
+ * form.  Eq. 3, the Note's clamp and the filter follow as in rt_shade.  A
+ * non-finite normal raises RT_ERR_NONFINITE and gives a zero fragment.
+ * rt_locate_world is rt_locate for this lookup.  rt_shade_world_backward is
+ * rt_shade_backward for it: dL_dnrm (F x 3 or NULL) receives dL/dN, which
+ * equals dL/dI.  These run on the flat fragment stream (no screen tiling). */
+rt_status rt_shade_world(rt_ctx* ctx, const float* uv, const float* dir, const float* nrm, const int32_t* obj,
+                         int64_t F, rt_filter filter, float* out, rt_stream_t stream);
+rt_status rt_locate_world(rt_ctx* ctx, const float* uv, const float* dir, const float* nrm, const int32_t* obj,
+                          int64_t F, rt_filter filter, int32_t* idx, float* coord, rt_stream_t stream);
+rt_status rt_shade_world_backward(rt_ctx* ctx, const float* uv, const float* dir, const float* nrm,
+                                  const int32_t* obj, int64_t F, rt_filter filter, const float* dL_dout,
+                                  float* const* dL_dtex, int32_t n_dtex, float* dL_duv, float* dL_ddir,
+                                  float* dL_dnrm, int32_t flags, rt_stream_t stream);
 
 /* Batched synthesis of views x height x width fragments: the same arrays as
  * rt_shade with F = views * height * width, fragment (view, y, x) at index

@@ -19,12 +19,14 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "radtex.h")
 RT_OK, RT_ERR_INVALID_ARG, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_BAD_OBJ_ID, RT_ERR_NONFINITE, RT_ERR_TIMEOUT, \
     RT_ERR_UNSUPPORTED = range(8)
 # rt_format
-RT_F32, RT_F16, RT_BF16, RT_E4M3_BUCKET_SCALE = range(4)
+RT_F32, RT_F16, RT_BF16, RT_E4M3_BUCKET_SCALE, RT_BIT1 = range(5)
 # rt_filter
 RT_NEAREST, RT_ANGULAR_BILINEAR, RT_QUADRILINEAR = range(3)
 # rt_layout
-RT_LAYOUT_ATLAS, RT_LAYOUT_PLANES = range(2)
+RT_LAYOUT_ATLAS, RT_LAYOUT_PLANES, RT_LAYOUT_PALETTE = range(3)  # PALETTE: reported by rt_texture_info
 RT_BORROW = 1
+RT_WRAP_U = 2
+RT_WRAP_V = 4
 RT_ACCUMULATE = 1
 RT_DETERMINISTIC = 2
 RT_MAX_OBJECTS = 1024
@@ -56,6 +58,16 @@ SIGNATURES = {
     "rt_read_texture": (_I32, [_P, _I32, _I32, _P, _P, _P]),
     "rt_fill_bucket_lobes": (_I32, [_P, _I32, _P, _P]),
     "rt_bake": (_I32, [_P, _I32, _I32, _P, _P]),
+    "rt_shade_world": (_I32, [_P, _P, _P, _P, _P, _I64, _I32, _P, _P]),
+    "rt_bake_shadow": (_I32, [_P, _I32, _I32, _P, _P]),
+    "rt_shade_multi": (_I32, [_P, _P, _P, _I32, _P, _I64, _I32, _P, _P]),
+    "rt_locate_world": (_I32, [_P, _P, _P, _P, _P, _I64, _I32, _P, _P, _P]),
+    "rt_shade_world_backward": (_I32, [_P, _P, _P, _P, _P, _I64, _I32, _P, _P, _I32, _P, _P, _P, _I32, _P]),
+    "rt_create_palette_texture": (_I32, [_P, _I32, _I32, _I32, _I32, _I32, _I32, _P, _P, _I32, _P]),
+    "rt_palette_size": (_I32, [_P, _I32, _P]),
+    "rt_kmeans_init": (_I32, [_P, _I32, _I32, _P, _P, _P]),
+    "rt_kmeans_assign": (_I32, [_P, _I32, _I32, _P, _P, _P, _P]),
+    "rt_kmeans_update": (_I32, [_P, _I32, _I32, _P, _P, _P, _P]),
     "rt_shade": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, _P]),
     "rt_locate": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, _P, _P]),
     "rt_shade_backward": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, ctypes.POINTER(_P), _I32, _P, _P, _I32, _P]),

@@ -12,14 +12,15 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import (RT_ACCUMULATE, RT_ANGULAR_BILINEAR, RT_BF16, RT_BORROW, RT_E4M3_BUCKET_SCALE,  # noqa: F401
+from ._lib import (RT_ACCUMULATE, RT_ANGULAR_BILINEAR, RT_BF16, RT_BIT1, RT_BORROW, RT_E4M3_BUCKET_SCALE,  # noqa: F401
                    RT_DETERMINISTIC, RT_ERR_BAD_OBJ_ID, RT_ERR_CUDA, RT_ERR_INVALID_ARG, RT_ERR_NONFINITE, RT_ERR_OOM, RT_ERR_TIMEOUT,
-                   RT_ERR_UNSUPPORTED, RT_F16, RT_F32, RT_LAYOUT_ATLAS, RT_LAYOUT_PLANES, RT_MAX_OBJECTS, RT_NEAREST,
-                   RT_OK, RT_QUADRILINEAR, RT_SURFACE_PLANE, RT_SURFACE_SPHERE, RadtexError)
+                   RT_ERR_UNSUPPORTED, RT_F16, RT_F32, RT_LAYOUT_ATLAS, RT_LAYOUT_PALETTE, RT_LAYOUT_PLANES, RT_MAX_OBJECTS, RT_NEAREST,
+                   RT_OK, RT_QUADRILINEAR, RT_SURFACE_PLANE, RT_SURFACE_SPHERE, RT_WRAP_U, RT_WRAP_V, RadtexError)
 
-FORMAT_BYTES = {RT_F32: 16, RT_F16: 8, RT_BF16: 8, RT_E4M3_BUCKET_SCALE: 4}
-CODE_DTYPE = {RT_F32: torch.float32, RT_F16: torch.int16, RT_BF16: torch.int16, RT_E4M3_BUCKET_SCALE: torch.uint8}
-FORMAT_NAMES = {"f32": RT_F32, "f16": RT_F16, "bf16": RT_BF16, "e4m3": RT_E4M3_BUCKET_SCALE}
+FORMAT_BYTES = {RT_F32: 16, RT_F16: 8, RT_BF16: 8, RT_E4M3_BUCKET_SCALE: 4, RT_BIT1: 1 / 8}
+CODE_DTYPE = {RT_F32: torch.float32, RT_F16: torch.int16, RT_BF16: torch.int16, RT_E4M3_BUCKET_SCALE: torch.uint8,
+              RT_BIT1: torch.uint8}
+FORMAT_NAMES = {"f32": RT_F32, "f16": RT_F16, "bf16": RT_BF16, "e4m3": RT_E4M3_BUCKET_SCALE, "bit1": RT_BIT1}
 FILTER_NAMES = {"nearest": RT_NEAREST, "angular_bilinear": RT_ANGULAR_BILINEAR, "quadrilinear": RT_QUADRILINEAR}
 
 
@@ -87,6 +88,104 @@ def rt_create_texture(ctx: Context, w: int, h: int, n: int, storage: int = RT_F3
     return out.value
 
 
+def rt_create_palette_texture(ctx: Context, w: int, h: int, n: int, K: int, storage: int, src_layout: int,
+                              palette: torch.Tensor, index: torch.Tensor, flags: int = 0) -> int:
+    """Palette texture (bucket compression): palette = FP32 CUDA tensor of K x n x n x 4
+    values (a K x 1 texture in src_layout), index = CUDA int32/uint32 (h, w) map of
+    palette buckets.  Returns the object id."""
+    _check(palette, "palette", torch.float32)
+    if palette.numel() != K * n * n * 4:
+        raise ValueError(f"palette has {palette.numel()} elements, expected {K * n * n * 4}")
+    if index.dtype not in (torch.int32, torch.uint32) or not index.is_cuda or not index.is_contiguous():
+        raise ValueError("index must be a contiguous CUDA int32 / uint32 tensor")
+    if index.numel() != w * h:
+        raise ValueError(f"index has {index.numel()} entries, expected {w * h}")
+    out = ctypes.c_int32(-1)
+    _lib.call("rt_create_palette_texture", ctx.handle, int(w), int(h), int(n), int(K), int(storage),
+              int(src_layout), _ptr(palette), _ptr(index), int(flags), ctypes.byref(out))
+    return out.value
+
+
+def rt_palette_size(ctx: Context, obj_id: int) -> int:
+    K = ctypes.c_int32(0)
+    _lib.call("rt_palette_size", ctx.handle, int(obj_id), ctypes.byref(K))
+    return K.value
+
+
+def rt_kmeans_init(ctx: Context, obj_id: int, K: int, buckets: torch.Tensor, centroids: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    """Centroids (n, n, K, 4) FP32 initialised from the buckets numbered `buckets` (CUDA int32, K)."""
+    info = rt_texture_info(ctx, obj_id)
+    n = info["n"]
+    _check(buckets, "buckets", torch.int32)
+    if buckets.numel() != K:
+        raise ValueError("buckets must hold K bucket numbers")
+    if centroids is None:
+        centroids = torch.empty((n, n, K, 4), dtype=torch.float32, device=buckets.device)
+    _check(centroids, "centroids", torch.float32, 4)
+    _lib.call("rt_kmeans_init", ctx.handle, int(obj_id), int(K), _ptr(buckets), _ptr(centroids),
+              _stream(stream, buckets.device))
+    return centroids
+
+
+def rt_kmeans_assign(ctx: Context, obj_id: int, K: int, centroids: torch.Tensor, index: torch.Tensor | None = None,
+                     dist: torch.Tensor | None = None, want_dist: bool = False, stream=None):
+    """Nearest centroid of every bucket: index (h, w) int32 [, squared distance (h, w) FP32]."""
+    info = rt_texture_info(ctx, obj_id)
+    _check(centroids, "centroids", torch.float32, 4)
+    if centroids.numel() != K * info["n"] ** 2 * 4:
+        raise ValueError("centroids must hold K x n x n x 4 values")
+    dev = centroids.device
+    if index is None:
+        index = torch.empty((info["h"], info["w"]), dtype=torch.int32, device=dev)
+    if want_dist and dist is None:
+        dist = torch.empty((info["h"], info["w"]), dtype=torch.float32, device=dev)
+    _lib.call("rt_kmeans_assign", ctx.handle, int(obj_id), int(K), _ptr(centroids), _ptr(index), _ptr(dist),
+              _stream(stream, dev))
+    return (index, dist) if want_dist else index
+
+
+def rt_kmeans_update(ctx: Context, obj_id: int, K: int, index: torch.Tensor, centroids: torch.Tensor,
+                     scratch: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Centroids <- means of their members (in place); empty centroids are kept."""
+    info = rt_texture_info(ctx, obj_id)
+    B = info["w"] * info["h"]
+    _check(centroids, "centroids", torch.float32, 4)
+    if index.numel() != B:
+        raise ValueError("index must hold one entry per bucket")
+    if scratch is None:
+        scratch = torch.empty(B + 3 * K + 1, dtype=torch.int32, device=centroids.device)
+    if scratch.numel() < B + 3 * K + 1:
+        raise ValueError("scratch needs w h + 3 K + 1 entries")
+    _lib.call("rt_kmeans_update", ctx.handle, int(obj_id), int(K), _ptr(index), _ptr(centroids), _ptr(scratch),
+              _stream(stream, centroids.device))
+    return centroids
+
+
+def palette_encode(ctx: Context, obj_id: int, K: int, iterations: int, seed: int = 0, stream=None):
+    """k-means palette of a dense texture: K centroids seeded at K distinct random
+    buckets, `iterations` Lloyd steps.  Returns (centroids (n, n, K, 4), index (h, w),
+    per-step sums of squared distances)."""
+    import numpy as np
+
+    info = rt_texture_info(ctx, obj_id)
+    B = info["w"] * info["h"]
+    dev = torch.device("cuda", ctx.device)
+    pick = np.random.default_rng(seed).choice(B, size=K, replace=False).astype(np.int32)
+    C = rt_kmeans_init(ctx, obj_id, K, torch.from_numpy(pick).to(dev), stream=stream)
+    scratch = torch.empty(B + 3 * K + 1, dtype=torch.int32, device=dev)
+    index = torch.empty((info["h"], info["w"]), dtype=torch.int32, device=dev)
+    dist = torch.empty((info["h"], info["w"]), dtype=torch.float32, device=dev)
+    sse = []
+    for _ in range(iterations):
+        rt_kmeans_assign(ctx, obj_id, K, C, index, dist, stream=stream)
+        sse.append(dist.double().sum())
+        rt_kmeans_update(ctx, obj_id, K, index, C, scratch, stream=stream)
+    rt_kmeans_assign(ctx, obj_id, K, C, index, dist, stream=stream)
+    sse.append(dist.double().sum())
+    return C, index, [float(x) for x in sse]
+
+
 def rt_destroy_texture(ctx: Context, obj_id: int) -> None:
     _lib.call("rt_destroy_texture", ctx.handle, int(obj_id))
 
@@ -106,8 +205,13 @@ def rt_read_texture(ctx: Context, obj_id: int, dst_layout: int = RT_LAYOUT_ATLAS
     float32 (F32), int16 bit patterns (F16 / BF16) or uint8 (E4M3)."""
     info = rt_texture_info(ctx, obj_id)
     w, h, n, fmt = info["w"], info["h"], info["n"], info["storage"]
+    K = rt_palette_size(ctx, obj_id)
+    if K:  # a palette reads as its K x 1 texture
+        w, h = K, 1
     dev = torch.device("cuda", ctx.device)
     shape = (h * n, w * n, 4) if dst_layout == RT_LAYOUT_ATLAS else (n, n, h, w, 4)
+    if fmt == RT_BIT1:  # one byte (0 or 1) per texel, no channels
+        shape = shape[:-1]
     codes = torch.empty(shape, dtype=CODE_DTYPE[fmt], device=dev)
     scales = torch.empty((h, w), dtype=torch.float32, device=dev) if fmt == RT_E4M3_BUCKET_SCALE else None
     _lib.call("rt_read_texture", ctx.handle, int(obj_id), int(dst_layout), _ptr(codes), _ptr(scales),
@@ -263,8 +367,9 @@ def _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir):
         for o, t in dL_dtex.items():
             _check(t, f"dL_dtex[{o}]", torch.float32)
             info = rt_texture_info(ctx, o)
-            if t.numel() != info["w"] * info["h"] * info["n"] ** 2 * 4:
-                raise ValueError(f"dL_dtex[{o}] must hold w h n^2 x 4 floats")
+            buckets = rt_palette_size(ctx, o) or info["w"] * info["h"]
+            if t.numel() != buckets * info["n"] ** 2 * 4:
+                raise ValueError(f"dL_dtex[{o}] must hold (w h or K) n^2 x 4 floats")
             arr[o] = t.data_ptr()
     return arr, n_dtex
 
@@ -277,6 +382,73 @@ def rt_shade_backward(ctx: Context, uv, dirs, obj, filter: int, dL_dout: torch.T
     arr, n_dtex = _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir)
     _lib.call("rt_shade_backward", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(obj), F, int(filter), _ptr(dL_dout),
               arr, n_dtex, _ptr(dL_duv), _ptr(dL_ddir), int(flags), _stream(stream, uv.device))
+
+
+def rt_bake_shadow(ctx: Context, obj_id: int, surface: int, scene: dict, stream=None) -> None:
+    """Visibility bits of an RT_BIT1 texture towards every texel direction (Section 5)."""
+    S = bake_scene_struct(scene)
+    dev = torch.device("cuda", ctx.device)
+    _lib.call("rt_bake_shadow", ctx.handle, int(obj_id), int(surface), ctypes.byref(S), _stream(stream, dev))
+
+
+def rt_shade_multi(ctx: Context, uv, dirs, obj, filter: int = RT_QUADRILINEAR, out: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    """Mean of S lookups per fragment: dirs (F, S, 3).  Returns (F, 4)."""
+    _check(uv, "uv", torch.float32, 2)
+    _check(dirs, "dirs", torch.float32, 3)
+    _check(obj, "obj", torch.int32)
+    F = obj.numel()
+    if uv.numel() != 2 * F or dirs.numel() % (3 * max(F, 1)) != 0:
+        raise ValueError("uv must hold F x 2 and dirs F x S x 3 floats")
+    S = dirs.numel() // (3 * F) if F else 1
+    if out is None:
+        out = torch.empty((F, 4), dtype=torch.float32, device=uv.device)
+    _check(out, "out", torch.float32, 4)
+    _lib.call("rt_shade_multi", ctx.handle, _ptr(uv), _ptr(dirs), int(S), _ptr(obj), F, int(filter), _ptr(out),
+              _stream(stream, uv.device))
+    return out
+
+
+def _normals(nrm, F):
+    _check(nrm, "nrm", torch.float32, 3)
+    if nrm.numel() != 3 * F:
+        raise ValueError("nrm must hold F x 3 floats")
+
+
+def rt_shade_world(ctx: Context, uv, dirs, nrm, obj, filter: int = RT_QUADRILINEAR, out: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    """World-space synthesis (Eq. 1a, I and N in one frame): (F, 4) float32 colours."""
+    F = _gbuffer(uv, dirs, obj)
+    _normals(nrm, F)
+    if out is None:
+        out = torch.empty((F, 4), dtype=torch.float32, device=uv.device)
+    _check(out, "out", torch.float32, 4)
+    _lib.call("rt_shade_world", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(nrm), _ptr(obj), F, int(filter), _ptr(out),
+              _stream(stream, uv.device))
+    return out
+
+
+def rt_locate_world(ctx: Context, uv, dirs, nrm, obj, filter: int = RT_QUADRILINEAR, stream=None):
+    F = _gbuffer(uv, dirs, obj)
+    _normals(nrm, F)
+    idx = torch.empty((F, 4), dtype=torch.int32, device=uv.device)
+    coord = torch.empty((F, 4), dtype=torch.float32, device=uv.device)
+    _lib.call("rt_locate_world", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(nrm), _ptr(obj), F, int(filter), _ptr(idx),
+              _ptr(coord), _stream(stream, uv.device))
+    return idx, coord
+
+
+def rt_shade_world_backward(ctx: Context, uv, dirs, nrm, obj, filter: int, dL_dout: torch.Tensor, dL_dtex=None,
+                            dL_duv: torch.Tensor | None = None, dL_ddir: torch.Tensor | None = None,
+                            dL_dnrm: torch.Tensor | None = None, flags: int = 0, stream=None) -> None:
+    F = _gbuffer(uv, dirs, obj)
+    _normals(nrm, F)
+    arr, n_dtex = _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir)
+    if dL_dnrm is not None:
+        _normals(dL_dnrm, F)
+    _lib.call("rt_shade_world_backward", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(nrm), _ptr(obj), F, int(filter),
+              _ptr(dL_dout), arr, n_dtex, _ptr(dL_duv), _ptr(dL_ddir), _ptr(dL_dnrm), int(flags),
+              _stream(stream, uv.device))
 
 
 def rt_footprint(ctx: Context, uv, dirs, obj, filter: int = RT_QUADRILINEAR, n_counts: int = RT_MAX_OBJECTS,

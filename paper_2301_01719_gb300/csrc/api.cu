@@ -26,6 +26,7 @@ struct rt_ctx {
     int n_obj = 0;                       // one past the highest id ever used
     int tile[3][4];                      // per filter: tw, th, bx, by of the batched kernels
     long long* det[RT_MAX_OBJECTS];      // fixed-point gradient sums of the deterministic mode
+    uint32_t* index[RT_MAX_OBJECTS];     // palette index maps the library copied
 };
 
 namespace {
@@ -59,10 +60,19 @@ inline int texel_bytes(int fmt) {
             return 8;
         case RT_E4M3_BUCKET_SCALE:
             return 4;
+        case RT_BIT1:
+            return 1;  // storage: texels / 8 bytes, rounded up to whole 32-bit words (storage_bytes)
         default:
             return 0;
     }
 }
+
+// Bytes of the texel storage of `texels` texels.
+inline int64_t storage_bytes(int fmt, int64_t texels) {
+    if (fmt == RT_BIT1) return (texels + 31) / 32 * 4;
+    return texels * texel_bytes(fmt);
+}
+
 
 inline rt_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return RT_OK;
@@ -133,6 +143,7 @@ rt_status rt_context_create(int cuda_device, rt_ctx** out) {
     std::memset(ctx->scales, 0, sizeof(ctx->scales));
     std::memset(ctx->bytes, 0, sizeof(ctx->bytes));
     std::memset(ctx->det, 0, sizeof(ctx->det));
+    std::memset(ctx->index, 0, sizeof(ctx->index));
     for (int f = 0; f < 3; ++f) {
         ctx->tile[f][0] = 8;
         ctx->tile[f][1] = 4;
@@ -173,6 +184,7 @@ void rt_context_destroy(rt_ctx* ctx) {
             if (ctx->owned[o]) cudaFree(ctx->owned[o]);
             if (ctx->scales[o]) cudaFree(ctx->scales[o]);
             if (ctx->det[o]) cudaFree(ctx->det[o]);
+            if (ctx->index[o]) cudaFree(ctx->index[o]);
         }
         cudaFree(ctx->d_table);
         cudaFree(ctx->d_status);
@@ -181,16 +193,23 @@ void rt_context_destroy(rt_ctx* ctx) {
     delete ctx;
 }
 
-rt_status rt_create_texture(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, rt_format storage, rt_layout src_layout,
-                            const float* src, int32_t flags, int32_t* obj_id_out) {
+// Creates a dense texture (K = 0) or a palette texture (K palette buckets
+// stored as a K x 1 texture, plus a copy of the w x h index map).
+static rt_status create_object(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, int32_t K, rt_format storage,
+                               rt_layout src_layout, const float* src, const uint32_t* index, int32_t flags,
+                               int32_t* obj_id_out) {
     if (!ctx || !obj_id_out) return RT_ERR_INVALID_ARG;
     if (w < 1 || h < 1 || n < 1 || w > 65536 || h > 65536 || n > 64) return RT_ERR_INVALID_ARG;
     if ((int64_t)w * h > ((int64_t)1 << 30)) return RT_ERR_INVALID_ARG;  // spatial offsets are 32-bit
     if (texel_bytes(storage) == 0) return RT_ERR_INVALID_ARG;
     if (src_layout != RT_LAYOUT_ATLAS && src_layout != RT_LAYOUT_PLANES) return RT_ERR_INVALID_ARG;
     if (src && !aligned16(src)) return RT_ERR_INVALID_ARG;
+    const bool palette = K > 0;
+    if (palette && (K > (1 << 30) || !index || !src)) return RT_ERR_INVALID_ARG;
     const bool borrow = (flags & RT_BORROW) != 0;
     if (borrow && (storage != RT_F32 || !src)) return RT_ERR_INVALID_ARG;
+    if (borrow && palette && src_layout != RT_LAYOUT_PLANES) return RT_ERR_UNSUPPORTED;
+    if (palette && storage == RT_BIT1) return RT_ERR_UNSUPPORTED;
     int o = -1;
     for (int k = 0; k < RT_MAX_OBJECTS; ++k)
         if (!ctx->table[k].live) {
@@ -200,38 +219,60 @@ rt_status rt_create_texture(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, rt_for
     if (o < 0) return RT_ERR_OOM;
     DeviceGuard g(ctx->device);
     if (!g.ok) return RT_ERR_CUDA;
-    // src may have been written on any stream of the device.
+    // src and index may have been written on any stream of the device.
     if (cudaDeviceSynchronize() != cudaSuccess) return RT_ERR_CUDA;
 
-    const int64_t texels = (int64_t)w * h * n * n;
+    // the stored buckets: the w x h matrix, or the K x 1 palette
+    const int32_t sw = palette ? K : w, sh = palette ? 1 : h;
+    const int64_t texels = (int64_t)sw * sh * n * n;
     TexDesc d;
     std::memset(&d, 0, sizeof(d));
     d.W = w;
     d.H = h;
     d.n = n;
-    d.fmt = storage;
-    d.plane = (int64_t)w * h;
+    d.fmt = (int8_t)storage;
+    d.plane = (int64_t)sw * sh;
     d.fW = (float)w;
     d.fH = (float)h;
     d.half_n = 0.5f * (float)n;
-    d.lo = 1.0f / (float)n - 1.0f;
     d.hi = 1.0f - 1.0f / (float)n;
     d.live = 1;
+    d.wrap = (int8_t)(((flags & RT_WRAP_U) ? 1 : 0) | ((flags & RT_WRAP_V) ? 2 : 0));
     void* storage_ptr = nullptr;
     float* scale_ptr = nullptr;
+    uint32_t* index_ptr = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (palette) {
+        // copy and check the index map: every entry < K
+        const size_t ib = sizeof(uint32_t) * (size_t)w * h;
+        unsigned* bad = nullptr;
+        e = cudaMalloc(&index_ptr, ib);
+        if (e == cudaSuccess) e = cudaMalloc(&bad, sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemset(bad, 0, sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemcpy(index_ptr, index, ib, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess) e = rt::launch_check_index(index_ptr, (int64_t)w * h, (uint32_t)K, bad, 0);
+        unsigned h_bad = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&h_bad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost);
+        cudaFree(bad);
+        if (e != cudaSuccess || h_bad) {
+            cudaFree(index_ptr);
+            return e != cudaSuccess ? cuda_status(e) : RT_ERR_INVALID_ARG;
+        }
+        d.index = index_ptr;
+    }
     if (borrow) {
         d.base = src;
-        d.layout = src_layout;
+        d.layout = (int8_t)(palette ? rt::kLayoutPalette : src_layout);
         ctx->bytes[o] = texels * 16;
     } else {
-        d.layout = RT_LAYOUT_PLANES;
-        const int64_t bytes = texels * texel_bytes(storage);
-        cudaError_t e = cudaMalloc(&storage_ptr, (size_t)bytes);
+        d.layout = (int8_t)(palette ? rt::kLayoutPalette : RT_LAYOUT_PLANES);
+        const int64_t bytes = storage_bytes(storage, texels);
+        e = cudaMalloc(&storage_ptr, (size_t)bytes);
         if (e == cudaSuccess && storage == RT_E4M3_BUCKET_SCALE)
             e = cudaMalloc(&scale_ptr, sizeof(float) * (size_t)d.plane);
         if (e == cudaSuccess) {
             if (src) {
-                e = rt::launch_encode(src, src_layout, storage_ptr, scale_ptr, w, h, n, storage, 0);
+                e = rt::launch_encode(src, src_layout, storage_ptr, scale_ptr, sw, sh, n, storage, 0);
             } else {
                 e = cudaMemset(storage_ptr, 0, (size_t)bytes);
                 if (e == cudaSuccess && scale_ptr) {
@@ -244,6 +285,7 @@ rt_status rt_create_texture(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, rt_for
         if (e != cudaSuccess) {
             cudaFree(storage_ptr);
             cudaFree(scale_ptr);
+            cudaFree(index_ptr);
             return cuda_status(e);
         }
         d.base = storage_ptr;
@@ -252,6 +294,8 @@ rt_status rt_create_texture(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, rt_for
         ctx->scales[o] = scale_ptr;
         ctx->bytes[o] = bytes + (scale_ptr ? (int64_t)sizeof(float) * d.plane : 0);
     }
+    ctx->index[o] = index_ptr;
+    if (index_ptr) ctx->bytes[o] += (int64_t)sizeof(uint32_t) * w * h;
     ctx->table[o] = d;
     if (o + 1 > ctx->n_obj) ctx->n_obj = o + 1;
     rt_status st = upload_table(ctx);
@@ -259,11 +303,32 @@ rt_status rt_create_texture(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, rt_for
         ctx->table[o].live = 0;
         cudaFree(storage_ptr);
         cudaFree(scale_ptr);
+        cudaFree(index_ptr);
         ctx->owned[o] = nullptr;
         ctx->scales[o] = nullptr;
+        ctx->index[o] = nullptr;
         return st;
     }
     *obj_id_out = o;
+    return RT_OK;
+}
+
+rt_status rt_create_texture(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, rt_format storage, rt_layout src_layout,
+                            const float* src, int32_t flags, int32_t* obj_id_out) {
+    return create_object(ctx, w, h, n, 0, storage, src_layout, src, nullptr, flags, obj_id_out);
+}
+
+rt_status rt_create_palette_texture(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, int32_t K, rt_format storage,
+                                    rt_layout src_layout, const float* palette, const uint32_t* index, int32_t flags,
+                                    int32_t* obj_id_out) {
+    if (K < 1) return RT_ERR_INVALID_ARG;
+    return create_object(ctx, w, h, n, K, storage, src_layout, palette, index, flags, obj_id_out);
+}
+
+rt_status rt_palette_size(rt_ctx* ctx, int32_t obj_id, int32_t* K) {
+    if (!ctx || !K || obj_id < 0 || obj_id >= RT_MAX_OBJECTS || !ctx->table[obj_id].live) return RT_ERR_INVALID_ARG;
+    const TexDesc& d = ctx->table[obj_id];
+    *K = d.layout == rt::kLayoutPalette ? (int32_t)d.plane : 0;
     return RT_OK;
 }
 
@@ -275,6 +340,8 @@ rt_status rt_destroy_texture(rt_ctx* ctx, int32_t obj_id) {
     if (ctx->owned[obj_id]) cudaFree(ctx->owned[obj_id]);
     if (ctx->scales[obj_id]) cudaFree(ctx->scales[obj_id]);
     if (ctx->det[obj_id]) cudaFree(ctx->det[obj_id]);
+    if (ctx->index[obj_id]) cudaFree(ctx->index[obj_id]);
+    ctx->index[obj_id] = nullptr;
     ctx->owned[obj_id] = nullptr;
     ctx->scales[obj_id] = nullptr;
     ctx->det[obj_id] = nullptr;
@@ -303,11 +370,13 @@ rt_status rt_read_texture(rt_ctx* ctx, int32_t obj_id, rt_layout dst_layout, voi
         return RT_ERR_INVALID_ARG;
     if (dst_layout != RT_LAYOUT_ATLAS && dst_layout != RT_LAYOUT_PLANES) return RT_ERR_INVALID_ARG;
     const TexDesc& d = ctx->table[obj_id];
-    if (d.layout != RT_LAYOUT_PLANES) return RT_ERR_UNSUPPORTED;
+    if (d.layout == RT_LAYOUT_ATLAS) return RT_ERR_UNSUPPORTED;
     DeviceGuard g(ctx->device);
     if (!g.ok) return RT_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = rt::launch_read(d.base, d.fmt, d.W, d.H, d.n, dst_layout, codes_dst, s);
+    const bool pal = d.layout == rt::kLayoutPalette;  // a palette reads as its K x 1 texture
+    cudaError_t e = rt::launch_read(d.base, d.fmt, pal ? (int)d.plane : d.W, pal ? 1 : d.H, d.n, dst_layout,
+                                    codes_dst, s);
     if (e == cudaSuccess && scales_dst && d.scale)
         e = cudaMemcpyAsync(scales_dst, d.scale, sizeof(float) * (size_t)d.plane, cudaMemcpyDeviceToDevice, s);
     return cuda_status(e);
@@ -317,7 +386,7 @@ rt_status rt_fill_bucket_lobes(rt_ctx* ctx, int32_t obj_id, const float* params,
     if (!ctx || obj_id < 0 || obj_id >= RT_MAX_OBJECTS || !ctx->table[obj_id].live || !params || !aligned16(params))
         return RT_ERR_INVALID_ARG;
     const TexDesc& d = ctx->table[obj_id];
-    if (!ctx->owned[obj_id]) return RT_ERR_UNSUPPORTED;
+    if (!ctx->owned[obj_id] || d.layout == rt::kLayoutPalette || d.fmt == RT_BIT1) return RT_ERR_UNSUPPORTED;
     DeviceGuard g(ctx->device);
     if (!g.ok) return RT_ERR_CUDA;
     return cuda_status(rt::launch_fill_lobes(params, ctx->owned[obj_id], ctx->scales[obj_id], d.W, d.H, d.n, d.fmt,
@@ -337,10 +406,45 @@ rt_status rt_bake(rt_ctx* ctx, int32_t obj_id, rt_surface surface, const rt_bake
         (surface != RT_SURFACE_SPHERE && surface != RT_SURFACE_PLANE) || !valid_scene(scene))
         return RT_ERR_INVALID_ARG;
     const TexDesc& d = ctx->table[obj_id];
+    if (d.layout == rt::kLayoutPalette || d.fmt == RT_BIT1) return RT_ERR_UNSUPPORTED;
     DeviceGuard g(ctx->device);
     if (!g.ok) return RT_ERR_CUDA;
     return cuda_status(rt::launch_bake(*scene, (int)surface, const_cast<void*>(d.base), ctx->scales[obj_id], d.W, d.H,
                                        d.n, d.fmt, d.layout, (cudaStream_t)stream));
+}
+
+static bool kmeans_source(rt_ctx* ctx, int32_t obj_id, int32_t K) {
+    if (!ctx || obj_id < 0 || obj_id >= RT_MAX_OBJECTS || !ctx->table[obj_id].live) return false;
+    const TexDesc& d = ctx->table[obj_id];
+    return K >= 1 && K <= (1 << 24) && d.fmt != RT_BIT1 &&
+           (d.layout == RT_LAYOUT_PLANES || d.layout == RT_LAYOUT_ATLAS);
+}
+
+rt_status rt_kmeans_init(rt_ctx* ctx, int32_t obj_id, int32_t K, const int32_t* buckets, float* centroids,
+                         rt_stream_t stream) {
+    if (!kmeans_source(ctx, obj_id, K) || !buckets || !centroids || !aligned16(centroids)) return RT_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    return cuda_status(rt::launch_kmeans_init(ctx->table[obj_id], K, buckets, centroids, ctx->d_status,
+                                              (cudaStream_t)stream));
+}
+
+rt_status rt_kmeans_assign(rt_ctx* ctx, int32_t obj_id, int32_t K, const float* centroids, uint32_t* index,
+                           float* dist, rt_stream_t stream) {
+    if (!kmeans_source(ctx, obj_id, K) || !centroids || !aligned16(centroids) || !index) return RT_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    return cuda_status(rt::launch_kmeans_assign(ctx->table[obj_id], K, centroids, index, dist, (cudaStream_t)stream));
+}
+
+rt_status rt_kmeans_update(rt_ctx* ctx, int32_t obj_id, int32_t K, const uint32_t* index, float* centroids,
+                           uint32_t* scratch, rt_stream_t stream) {
+    if (!kmeans_source(ctx, obj_id, K) || !index || !centroids || !aligned16(centroids) || !scratch)
+        return RT_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    return cuda_status(rt::launch_kmeans_update(ctx->table[obj_id], K, index, centroids, scratch, ctx->d_status,
+                                                (cudaStream_t)stream));
 }
 
 rt_status rt_shade(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F, rt_filter filter,
@@ -371,13 +475,19 @@ rt_status rt_locate(rt_ctx* ctx, const float* uv, const float* dir, const int32_
 
 }  // extern "C"
 
+// nrm == NULL: tangent-space backward on tiling T; otherwise world-space
+// (Eq. 1a) on the flat stream, with dL/dN into dL_dnrm.
 static rt_status shade_backward_impl(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,
                                      rt_filter filter, const rt::Tiling& T, const float* dL_dout,
                                      float* const* dL_dtex, int32_t n_dtex, float* dL_duv, float* dL_ddir,
-                                     int32_t flags, rt_stream_t stream) {
+                                     int32_t flags, rt_stream_t stream, const float* nrm = nullptr,
+                                     float* dL_dnrm = nullptr) {
     if (!ctx || !valid_filter(filter)) return RT_ERR_INVALID_ARG;
     rt_status st = check_gbuffer(uv, dir, obj, F);
     if (st != RT_OK) return st;
+    if (nrm == nullptr && dL_dnrm != nullptr) return RT_ERR_INVALID_ARG;
+    if (F > 0 && nrm && !aligned16(nrm)) return RT_ERR_INVALID_ARG;
+    if (dL_dnrm && !aligned16(dL_dnrm)) return RT_ERR_INVALID_ARG;
     if (n_dtex < 0 || n_dtex > RT_MAX_OBJECTS || (n_dtex > 0 && !dL_dtex)) return RT_ERR_INVALID_ARG;
     if ((dL_duv && !aligned16(dL_duv)) || (dL_ddir && !aligned16(dL_ddir))) return RT_ERR_INVALID_ARG;
     if (F > 0 && (!dL_dout || !aligned16(dL_dout))) return RT_ERR_INVALID_ARG;
@@ -390,6 +500,7 @@ static rt_status shade_backward_impl(rt_ctx* ctx, const float* uv, const float* 
         if (!dL_dtex[o]) continue;
         if (o >= RT_MAX_OBJECTS || !ctx->table[o].live || !aligned16(dL_dtex[o])) return RT_ERR_INVALID_ARG;
         if (deterministic && !ctx->det[o]) return RT_ERR_INVALID_ARG;  // rt_prepare_deterministic first
+        if (ctx->table[o].fmt == RT_BIT1) return RT_ERR_UNSUPPORTED;   // bits have no texel gradient
         grads.p[o] = deterministic ? static_cast<void*>(ctx->det[o]) : static_cast<void*>(dL_dtex[o]);
         any = true;
     }
@@ -406,9 +517,14 @@ static rt_status shade_backward_impl(rt_ctx* ctx, const float* uv, const float* 
         else if (!accumulate)
             e = cudaMemsetAsync(dL_dtex[o], 0, 16 * texels, s);
     }
-    if (e == cudaSuccess && F > 0)
-        e = rt::launch_backward(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any, dL_duv,
-                                dL_ddir, accumulate, deterministic, ctx->d_status, s);
+    if (e == cudaSuccess && F > 0) {
+        if (nrm)
+            e = rt::launch_world_backward(ctx->d_table, ctx->n_obj, uv, dir, nrm, obj, F, filter, dL_dout, grads, any,
+                                          dL_duv, dL_ddir, dL_dnrm, accumulate, deterministic, ctx->d_status, s);
+        else
+            e = rt::launch_backward(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any,
+                                    dL_duv, dL_ddir, accumulate, deterministic, ctx->d_status, s);
+    }
     if (deterministic)
         for (int o = 0; o < n_dtex && e == cudaSuccess; ++o)
             if (grads.p[o]) {
@@ -432,6 +548,68 @@ rt_status rt_shade_backward(rt_ctx* ctx, const float* uv, const float* dir, cons
                             float* dL_duv, float* dL_ddir, int32_t flags, rt_stream_t stream) {
     return shade_backward_impl(ctx, uv, dir, obj, F, filter, rt::flat_tiling(), dL_dout, dL_dtex, n_dtex, dL_duv,
                                dL_ddir, flags, stream);
+}
+
+rt_status rt_bake_shadow(rt_ctx* ctx, int32_t obj_id, rt_surface surface, const rt_bake_scene* scene,
+                         rt_stream_t stream) {
+    if (!ctx || obj_id < 0 || obj_id >= RT_MAX_OBJECTS || !ctx->table[obj_id].live || !scene ||
+        (surface != RT_SURFACE_SPHERE && surface != RT_SURFACE_PLANE) || !valid_scene(scene))
+        return RT_ERR_INVALID_ARG;
+    const TexDesc& d = ctx->table[obj_id];
+    if (d.fmt != RT_BIT1 || !ctx->owned[obj_id] || d.layout != RT_LAYOUT_PLANES) return RT_ERR_UNSUPPORTED;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    return cuda_status(rt::launch_bake_shadow(*scene, (int)surface, ctx->owned[obj_id], d.W, d.H, d.n,
+                                              (cudaStream_t)stream));
+}
+
+rt_status rt_shade_multi(rt_ctx* ctx, const float* uv, const float* dirs, int32_t samples, const int32_t* obj,
+                         int64_t F, rt_filter filter, float* out, rt_stream_t stream) {
+    if (!ctx || !valid_filter(filter) || samples < 1) return RT_ERR_INVALID_ARG;
+    rt_status st = check_gbuffer(uv, dirs, obj, F);
+    if (st != RT_OK) return st;
+    if (F == 0) return RT_OK;
+    if (!out || !aligned16(out)) return RT_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    return cuda_status(rt::launch_multi_shade(ctx->d_table, ctx->n_obj, uv, dirs, samples, obj, F, filter, out,
+                                              ctx->d_status, (cudaStream_t)stream));
+}
+
+rt_status rt_shade_world(rt_ctx* ctx, const float* uv, const float* dir, const float* nrm, const int32_t* obj,
+                         int64_t F, rt_filter filter, float* out, rt_stream_t stream) {
+    if (!ctx || !valid_filter(filter)) return RT_ERR_INVALID_ARG;
+    rt_status st = check_gbuffer(uv, dir, obj, F);
+    if (st != RT_OK) return st;
+    if (F == 0) return RT_OK;
+    if (!nrm || !aligned16(nrm) || !out || !aligned16(out)) return RT_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    return cuda_status(rt::launch_world_shade(ctx->d_table, ctx->n_obj, uv, dir, nrm, obj, F, filter, out, nullptr,
+                                              nullptr, ctx->d_status, (cudaStream_t)stream));
+}
+
+rt_status rt_locate_world(rt_ctx* ctx, const float* uv, const float* dir, const float* nrm, const int32_t* obj,
+                          int64_t F, rt_filter filter, int32_t* idx, float* coord, rt_stream_t stream) {
+    if (!ctx || !valid_filter(filter)) return RT_ERR_INVALID_ARG;
+    rt_status st = check_gbuffer(uv, dir, obj, F);
+    if (st != RT_OK) return st;
+    if (F == 0) return RT_OK;
+    if (!nrm || !aligned16(nrm) || !idx || !coord || !aligned16(idx) || !aligned16(coord)) return RT_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    return cuda_status(rt::launch_world_shade(ctx->d_table, ctx->n_obj, uv, dir, nrm, obj, F, filter, nullptr, idx,
+                                              coord, ctx->d_status, (cudaStream_t)stream));
+}
+
+rt_status rt_shade_world_backward(rt_ctx* ctx, const float* uv, const float* dir, const float* nrm,
+                                  const int32_t* obj, int64_t F, rt_filter filter, const float* dL_dout,
+                                  float* const* dL_dtex, int32_t n_dtex, float* dL_duv, float* dL_ddir,
+                                  float* dL_dnrm, int32_t flags, rt_stream_t stream) {
+    if (F > 0 && !nrm) return RT_ERR_INVALID_ARG;
+    static const float kNone[4] = {0.f, 0.f, 0.f, 0.f};  // an unused non-null marker for F = 0
+    return shade_backward_impl(ctx, uv, dir, obj, F, filter, rt::flat_tiling(), dL_dout, dL_dtex, n_dtex, dL_duv,
+                               dL_ddir, flags, stream, nrm ? nrm : kNone, dL_dnrm);
 }
 
 rt_status rt_shade_batched(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int32_t views,
@@ -612,6 +790,7 @@ rt_status rt_get_error(rt_ctx* ctx, rt_stream_t stream, rt_status* device_status
     *device_status = (bits & rt::ST_BAD_OBJ)     ? RT_ERR_BAD_OBJ_ID
                      : (bits & rt::ST_NONFINITE) ? RT_ERR_NONFINITE
                      : (bits & rt::ST_TIMEOUT)   ? RT_ERR_TIMEOUT
+                     : (bits & rt::ST_BAD_ARG)   ? RT_ERR_INVALID_ARG
                                                  : RT_OK;
     return RT_OK;
 }

@@ -36,15 +36,16 @@ __device__ __forceinline__ void red_add_fixed4(unsigned long long* addr, float4 
 // QUADRILINEAR on the PLANES layout: the four in-bucket texels select four
 // planes (64-bit bases), the four buckets four spatial offsets (32-bit), shared
 // by the 16 reductions and the 16 loads.
-template <int FMT, bool DET>
+template <int FMT, int LAYOUT, bool DET>
 __device__ __forceinline__ CoordGrad backward_quadrilinear_planes(const TexDesc& d, const Lookup<RT_QUADRILINEAR>& L,
                                                                   float4 g, void* grad, bool coord_grads) {
     const int64_t P = d.plane;
     const int64_t p00 = (int64_t)(L.t.k0 * d.n + L.s.k0) * P;
     const int64_t ds = (int64_t)(L.s.k1 - L.s.k0) * P, dt = (int64_t)(L.t.k1 - L.t.k0) * d.n * P;
     const int64_t pl[4] = {p00, p00 + ds, p00 + dt, p00 + dt + ds};  // (s0,t0) (s1,t0) (s0,t1) (s1,t1)
-    const int o[4] = {L.v.k0 * d.W + L.u.k0, L.v.k0 * d.W + L.u.k1, L.v.k1 * d.W + L.u.k0,
-                      L.v.k1 * d.W + L.u.k1};  // (u0,v0) (u1,v0) (u0,v1) (u1,v1)
+    const int o[4] = {bucket_slot<LAYOUT>(d, L.u.k0, L.v.k0), bucket_slot<LAYOUT>(d, L.u.k1, L.v.k0),
+                      bucket_slot<LAYOUT>(d, L.u.k0, L.v.k1),
+                      bucket_slot<LAYOUT>(d, L.u.k1, L.v.k1)};  // (u0,v0) (u1,v0) (u0,v1) (u1,v1)
     const float wu[2] = {1.f - L.u.w, L.u.w}, wv[2] = {1.f - L.v.w, L.v.w};
     const float ws[2] = {1.f - L.s.w, L.s.w}, wt[2] = {1.f - L.t.w, L.t.w};
     if (grad) {
@@ -158,34 +159,38 @@ __device__ __forceinline__ CoordGrad backward_taps(const TexDesc& d, const Looku
     return cg;
 }
 
+template <int FILTER, int FMT, int LAYOUT, bool DET>
+__device__ __forceinline__ CoordGrad backward_layout(const TexDesc& d, const Lookup<FILTER>& L, float4 g, void* grad,
+                                                     bool coord_grads) {
+    if constexpr (FILTER == RT_QUADRILINEAR && LAYOUT != RT_LAYOUT_ATLAS)
+        return backward_quadrilinear_planes<FMT, LAYOUT, DET>(d, L, g, grad, coord_grads);
+    else
+        return backward_taps<FILTER, FMT, LAYOUT, DET>(d, L, g, grad, coord_grads);
+}
+
 template <int FILTER, bool DET>
 __device__ __forceinline__ CoordGrad backward_any(const TexDesc& d, const Lookup<FILTER>& L, float4 g, void* grad,
                                                   bool coord_grads) {
-    if constexpr (FILTER == RT_QUADRILINEAR) {
-        if (d.layout == RT_LAYOUT_PLANES) {
-            switch (d.fmt) {
-                case RT_F16:
-                    return backward_quadrilinear_planes<RT_F16, DET>(d, L, g, grad, coord_grads);
-                case RT_BF16:
-                    return backward_quadrilinear_planes<RT_BF16, DET>(d, L, g, grad, coord_grads);
-                case RT_E4M3_BUCKET_SCALE:
-                    return backward_quadrilinear_planes<RT_E4M3_BUCKET_SCALE, DET>(d, L, g, grad, coord_grads);
-                default:
-                    return backward_quadrilinear_planes<RT_F32, DET>(d, L, g, grad, coord_grads);
-            }
-        }
-    }
+    const bool pal = d.layout == kLayoutPalette;
     switch (d.fmt) {
         case RT_F16:
-            return backward_taps<FILTER, RT_F16, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
+            return pal ? backward_layout<FILTER, RT_F16, kLayoutPalette, DET>(d, L, g, grad, coord_grads)
+                       : backward_layout<FILTER, RT_F16, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
         case RT_BF16:
-            return backward_taps<FILTER, RT_BF16, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
+            return pal ? backward_layout<FILTER, RT_BF16, kLayoutPalette, DET>(d, L, g, grad, coord_grads)
+                       : backward_layout<FILTER, RT_BF16, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
+        case RT_BIT1:  // no texel gradients (rejected on the host); coordinate gradients only
+            return pal ? backward_layout<FILTER, RT_BIT1, kLayoutPalette, DET>(d, L, g, nullptr, coord_grads)
+                       : backward_layout<FILTER, RT_BIT1, RT_LAYOUT_PLANES, DET>(d, L, g, nullptr, coord_grads);
         case RT_E4M3_BUCKET_SCALE:
-            return backward_taps<FILTER, RT_E4M3_BUCKET_SCALE, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
+            return pal ? backward_layout<FILTER, RT_E4M3_BUCKET_SCALE, kLayoutPalette, DET>(d, L, g, grad, coord_grads)
+                       : backward_layout<FILTER, RT_E4M3_BUCKET_SCALE, RT_LAYOUT_PLANES, DET>(d, L, g, grad,
+                                                                                              coord_grads);
         default:
             if (d.layout == RT_LAYOUT_ATLAS)
-                return backward_taps<FILTER, RT_F32, RT_LAYOUT_ATLAS, DET>(d, L, g, grad, coord_grads);
-            return backward_taps<FILTER, RT_F32, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
+                return backward_layout<FILTER, RT_F32, RT_LAYOUT_ATLAS, DET>(d, L, g, grad, coord_grads);
+            return pal ? backward_layout<FILTER, RT_F32, kLayoutPalette, DET>(d, L, g, grad, coord_grads)
+                       : backward_layout<FILTER, RT_F32, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
     }
 }
 
@@ -194,7 +199,9 @@ __device__ __forceinline__ CoordGrad backward_any(const TexDesc& d, const Lookup
 //    dB/dA = [[1, q], [-q^3, 1 + 2 q^2]] / sqrt(1 + q^2)   (rows B_x, B_y)
 //  and symmetrically on the y branch; the identity at A = 0.
 //  Eq. 1b: dA_r/dI_c = sqrt(2) (delta_rc / D - I_r g_c / D^3), g = (I_x, I_y, I_z + 1), D = |g|.
-__device__ __forceinline__ float3 direction_grad(float Ix, float Iy, float Iz, float gBx, float gBy) {
+//  The same holds for any half-way vector h in place of g (Eq. 1a: h = I + N,
+//  and dA/dI = dA/dN = dA/dh).
+__device__ __forceinline__ float3 half_grad(float Ix, float Iy, float zp, float gBx, float gBy) {
     float ax = fabsf(Ix), ay = fabsf(Iy);
     float gAx, gAy;
     if (!(fmaxf(ax, ay) >= 1e-30f)) {
@@ -211,7 +218,6 @@ __device__ __forceinline__ float3 direction_grad(float Ix, float Iy, float Iz, f
         gAy = (gBy - gBx * p * p * p) * r;
         gAx = (gBy * p + gBx * fmaf(2.0f * p, p, 1.0f)) * r;
     }
-    float zp = Iz + 1.0f;
     float D2 = Ix * Ix + Iy * Iy + zp * zp;
     if (!(D2 > 1e-30f)) return make_float3(0.f, 0.f, 0.f);
     float invD = 1.0f / sqrtf(D2);
@@ -219,6 +225,19 @@ __device__ __forceinline__ float3 direction_grad(float Ix, float Iy, float Iz, f
     float k3 = k * invD * invD;
     float m = k3 * (gAx * Ix + gAy * Iy);
     return make_float3(k * gAx - m * Ix, k * gAy - m * Iy, -m * zp);
+}
+
+__device__ __forceinline__ float3 direction_grad(float Ix, float Iy, float Iz, float gBx, float gBy) {
+    return half_grad(Ix, Iy, Iz + 1.0f, gBx, gBy);
+}
+
+// dL/du, dL/dv of a bilinear spatial lookup: zero where clamp to edge holds c fixed.
+__device__ __forceinline__ float2 uv_grad(const TexDesc& d, float u, float v, float gu, float gv) {
+    const float cu = fmaf(u, d.fW, -0.5f), cv = fmaf(v, d.fH, -0.5f);
+    float2 r;
+    r.x = ((d.wrap & 1) || (cu > -1.0f && cu < d.fW)) ? gu * d.fW : 0.f;
+    r.y = ((d.wrap & 2) || (cv > -1.0f && cv < d.fH)) ? gv * d.fH : 0.f;
+    return r;
 }
 
 template <int FILTER, bool TILED, bool DET>
@@ -238,14 +257,10 @@ __global__ void __launch_bounds__(kBackThreads) backward_kernel(
             Lookup<FILTER> L = locate<FILTER>(d, q.u, q.v, q.x, q.y, q.z);
             void* grad = any_grad ? grads.p[q.o] : nullptr;
             CoordGrad cg = backward_any<FILTER, DET>(d, L, go, grad, coord_grads);
-            if (FILTER == RT_QUADRILINEAR) {
-                float cu = fmaf(q.u, d.fW, -0.5f), cv = fmaf(q.v, d.fH, -0.5f);
-                guv.x = (cu > -1.0f && cu < d.fW) ? cg.gu * d.fW : 0.f;
-                guv.y = (cv > -1.0f && cv < d.fH) ? cg.gv * d.fH : 0.f;
-            }
+            if (FILTER == RT_QUADRILINEAR) guv = uv_grad(d, q.u, q.v, cg.gu, cg.gv);
             if (FILTER != RT_NEAREST && dL_ddir) {
-                float gBx = (L.B.x > d.lo && L.B.x < d.hi) ? cg.gs * d.half_n : 0.f;
-                float gBy = (L.B.y > d.lo && L.B.y < d.hi) ? cg.gt * d.half_n : 0.f;
+                float gBx = (L.B.x > -d.hi && L.B.x < d.hi) ? cg.gs * d.half_n : 0.f;
+                float gBy = (L.B.y > -d.hi && L.B.y < d.hi) ? cg.gt * d.half_n : 0.f;
                 gdir = direction_grad(q.x, q.y, q.z, gBx, gBy);
             }
         }
@@ -321,6 +336,102 @@ cudaError_t launch_backward(const TexDesc* table, int n_obj, const float* uv, co
                                               dL_duv, dL_ddir, accumulate, status, stream);
     return launch_backward_f<false, false>(table, n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any_grad,
                                            dL_duv, dL_ddir, accumulate, status, stream);
+}
+
+// World-space backward (Eq. 1a with a per-fragment normal): one fragment per
+// thread, grid-stride.  dL/dI = dL/dN, since A depends on h = I + N only.
+template <int FILTER, bool DET>
+__global__ void __launch_bounds__(kBackThreads) world_backward_kernel(
+    const TexDesc* __restrict__ table, int n_obj, const float* __restrict__ uv, const float* __restrict__ dir,
+    const float* __restrict__ nrm, const int32_t* __restrict__ obj, int64_t F, const float* __restrict__ dL_dout,
+    const __grid_constant__ GradTable grads, bool any_grad, float* __restrict__ dL_duv, float* __restrict__ dL_ddir,
+    float* __restrict__ dL_dnrm, bool accumulate, unsigned* status) {
+    const bool coord_grads = dL_duv || dL_ddir || dL_dnrm;
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
+        const float2 q = reinterpret_cast<const float2*>(uv)[f];
+        const float3 I = make_float3(dir[3 * f], dir[3 * f + 1], dir[3 * f + 2]);
+        const float3 N = make_float3(nrm[3 * f], nrm[3 * f + 1], nrm[3 * f + 2]);
+        float2 guv = make_float2(0.f, 0.f);
+        float3 gh = make_float3(0.f, 0.f, 0.f);
+        TexDesc d;
+        if (fragment_valid(table, n_obj, obj[f], q.x, q.y, I.x, I.y, I.z, status, d) &&
+            normal_valid(N, status)) {
+            const Lookup<FILTER> L = locate_world<FILTER>(d, q.x, q.y, I, N);
+            const float4 go = reinterpret_cast<const float4*>(dL_dout)[f];
+            void* grad = any_grad ? grads.p[obj[f]] : nullptr;
+            const CoordGrad cg = backward_any<FILTER, DET>(d, L, go, grad, coord_grads);
+            if (FILTER == RT_QUADRILINEAR) guv = uv_grad(d, q.x, q.y, cg.gu, cg.gv);
+            if (FILTER != RT_NEAREST && (dL_ddir || dL_dnrm)) {
+                const float gBx = (L.B.x > -d.hi && L.B.x < d.hi) ? cg.gs * d.half_n : 0.f;
+                const float gBy = (L.B.y > -d.hi && L.B.y < d.hi) ? cg.gt * d.half_n : 0.f;
+                gh = half_grad(I.x + N.x, I.y + N.y, I.z + N.z, gBx, gBy);
+            }
+        }
+        if (dL_duv) {
+            float2* p = reinterpret_cast<float2*>(dL_duv) + f;
+            if (accumulate) {
+                const float2 o = *p;
+                guv.x += o.x;
+                guv.y += o.y;
+            }
+            *p = guv;
+        }
+        float* outs[2] = {dL_ddir, dL_dnrm};
+        for (int k = 0; k < 2; ++k) {
+            float* p = outs[k];
+            if (!p) continue;
+            p += 3 * f;
+            p[0] = accumulate ? p[0] + gh.x : gh.x;
+            p[1] = accumulate ? p[1] + gh.y : gh.y;
+            p[2] = accumulate ? p[2] + gh.z : gh.z;
+        }
+    }
+}
+
+template <int FILTER, bool DET>
+static cudaError_t launch_world_backward_t(const TexDesc* table, int n_obj, const float* uv, const float* dir,
+                                           const float* nrm, const int32_t* obj, int64_t F, const float* dL_dout,
+                                           const GradTable& grads, bool any_grad, float* dL_duv, float* dL_ddir,
+                                           float* dL_dnrm, bool accumulate, unsigned* status, cudaStream_t stream) {
+    const unsigned grid = persistent_grid(world_backward_kernel<FILTER, DET>, kBackThreads,
+                                          (F + kBackThreads - 1) / kBackThreads);
+    world_backward_kernel<FILTER, DET><<<grid, kBackThreads, 0, stream>>>(
+        table, n_obj, uv, dir, nrm, obj, F, dL_dout, grads, any_grad, dL_duv, dL_ddir, dL_dnrm, accumulate, status);
+    return cudaGetLastError();
+}
+
+template <bool DET>
+static cudaError_t launch_world_backward_d(const TexDesc* table, int n_obj, const float* uv, const float* dir,
+                                           const float* nrm, const int32_t* obj, int64_t F, int filter,
+                                           const float* dL_dout, const GradTable& grads, bool any_grad,
+                                           float* dL_duv, float* dL_ddir, float* dL_dnrm, bool accumulate,
+                                           unsigned* status, cudaStream_t stream) {
+    switch (filter) {
+        case RT_NEAREST:
+            return launch_world_backward_t<RT_NEAREST, DET>(table, n_obj, uv, dir, nrm, obj, F, dL_dout, grads,
+                                                            any_grad, dL_duv, dL_ddir, dL_dnrm, accumulate, status,
+                                                            stream);
+        case RT_ANGULAR_BILINEAR:
+            return launch_world_backward_t<RT_ANGULAR_BILINEAR, DET>(table, n_obj, uv, dir, nrm, obj, F, dL_dout,
+                                                                     grads, any_grad, dL_duv, dL_ddir, dL_dnrm,
+                                                                     accumulate, status, stream);
+        default:
+            return launch_world_backward_t<RT_QUADRILINEAR, DET>(table, n_obj, uv, dir, nrm, obj, F, dL_dout, grads,
+                                                                 any_grad, dL_duv, dL_ddir, dL_dnrm, accumulate,
+                                                                 status, stream);
+    }
+}
+
+cudaError_t launch_world_backward(const TexDesc* table, int n_obj, const float* uv, const float* dir,
+                                  const float* nrm, const int32_t* obj, int64_t F, int filter, const float* dL_dout,
+                                  const GradTable& grads, bool any_grad, float* dL_duv, float* dL_ddir,
+                                  float* dL_dnrm, bool accumulate, bool deterministic, unsigned* status,
+                                  cudaStream_t stream) {
+    if (deterministic)
+        return launch_world_backward_d<true>(table, n_obj, uv, dir, nrm, obj, F, filter, dL_dout, grads, any_grad,
+                                             dL_duv, dL_ddir, dL_dnrm, accumulate, status, stream);
+    return launch_world_backward_d<false>(table, n_obj, uv, dir, nrm, obj, F, filter, dL_dout, grads, any_grad,
+                                          dL_duv, dL_ddir, dL_dnrm, accumulate, status, stream);
 }
 
 // Fixed-point sums (deterministic mode) -> FP32 gradients, added to or overwriting dst.

@@ -194,4 +194,74 @@ cudaError_t launch_bake(const rt_bake_scene& S, int surface, void* dst, float* s
     }
 }
 
+// ---------------------------------------------------------------------------
+// Shadow bake (Section 5, "Shadowing"): a 1-bit texture keyed by the light
+// direction.  Bit (i, j, s, t) = the ray from bucket (i, j)'s surface point
+// towards texel (s, t)'s direction (Eq. 4a, Eq. 2c, in world space) reaches
+// the sky.  One thread per 32-bit word of the PLANES bit numbering, so every
+// word is written once, whole.
+// ---------------------------------------------------------------------------
+
+// The sphere's entering root or the plane crossing at t > ray_offset.
+__device__ __forceinline__ bool occluded(const rt_bake_scene& S, float3 P, float3 d) {
+    const float3 c = mk(S.sphere_centre);
+    const float3 o = make_float3(P.x - c.x, P.y - c.y, P.z - c.z);
+    const float b = dot3(o, d);
+    const float q = dot3(o, o) - S.sphere_radius * S.sphere_radius;
+    const float disc = b * b - q;
+    if (disc > 0.0f && -b - sqrtf(disc) > S.ray_offset) return true;
+    return d.y != 0.0f && (S.plane_height - P.y) / d.y > S.ray_offset;
+}
+
+// Surface point and frame of bucket (i, j) (the geometry of bucket_ray).
+__device__ __forceinline__ void bucket_frame(const rt_bake_scene& S, int surface, int i, int j, int W, int H,
+                                             float3& P, float3& T, float3& B, float3& N) {
+    const float u = ((float)i + 0.5f) / (float)W, v = ((float)j + 0.5f) / (float)H;
+    if (surface == RT_SURFACE_SPHERE) {
+        float sp, cp, st, ct;
+        sincospif(2.0f * u - 1.0f, &sp, &cp);
+        sincospif(v, &st, &ct);
+        N = make_float3(st * cp, ct, st * sp);
+        T = make_float3(-sp, 0.0f, cp);
+        B = make_float3(ct * cp, -st, ct * sp);
+        P = axpy(S.sphere_radius, N, mk(S.sphere_centre));
+    } else {
+        const float e = S.plane_half_extent;
+        P = make_float3(2.0f * e * u - e, S.plane_height, 2.0f * e * v - e);
+        T = make_float3(1.0f, 0.0f, 0.0f);
+        B = make_float3(0.0f, 0.0f, 1.0f);
+        N = make_float3(0.0f, 1.0f, 0.0f);
+    }
+}
+
+__global__ void __launch_bounds__(kBakeThreads) shadow_bake_kernel(rt_bake_scene S, int surface,
+                                                                   unsigned* __restrict__ dst, int W, int H, int n) {
+    const int64_t plane = (int64_t)W * H, total = plane * n * n;
+    const int64_t w = (int64_t)blockIdx.x * kBakeThreads + threadIdx.x;
+    if (w * 32 >= total) return;
+    unsigned word = 0;
+    for (int k = 0; k < 32; ++k) {
+        const int64_t e = w * 32 + k;
+        if (e >= total) break;
+        const int p = (int)(e / plane);
+        const int64_t b = e - (int64_t)p * plane;
+        const int j = (int)(b / W), i = (int)(b - (int64_t)j * W);
+        const int t = p / n, s = p - t * n;
+        float3 P, T, B, N;
+        bucket_frame(S, surface, i, j, W, H, P, T, B, N);
+        const float3 I = texel_centre_direction(s, t, n);
+        const float3 d = axpy(I.z, N, axpy(I.y, B, scale3(I.x, T)));
+        if (!occluded(S, P, d)) word |= 1u << k;
+    }
+    dst[w] = word;
+}
+
+cudaError_t launch_bake_shadow(const rt_bake_scene& S, int surface, void* dst, int W, int H, int n,
+                               cudaStream_t stream) {
+    const int64_t words = ((int64_t)W * H * n * n + 31) / 32;
+    shadow_bake_kernel<<<(unsigned)((words + kBakeThreads - 1) / kBakeThreads), kBakeThreads, 0, stream>>>(
+        S, surface, static_cast<unsigned*>(dst), W, H, n);
+    return cudaGetLastError();
+}
+
 }  // namespace rt

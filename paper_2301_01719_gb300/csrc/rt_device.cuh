@@ -19,19 +19,20 @@
 
 namespace rt {
 
-enum : unsigned { ST_BAD_OBJ = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u };
+enum : unsigned { ST_BAD_OBJ = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u, ST_BAD_ARG = 8u };
 
 // One object of the texture table (64 bytes).  Built on the host when the
 // texture is created; read by every kernel through the read-only path.
 struct __align__(16) TexDesc {
-    const void* base;    // texel storage
-    const float* scale;  // per-bucket scale, row-major h x w (E4M3 only)
-    int64_t plane;       // texels per direction plane, w * h
-    int32_t W, H, n, fmt;
-    int16_t layout, live;
-    float fW, fH;        // w, h as float
-    float half_n;        // n / 2
-    float lo, hi;        // clamp range of B: 1/n - 1, 1 - 1/n
+    const void* base;       // texel storage
+    const float* scale;     // per-bucket scale (E4M3 only): h x w, or one per palette bucket
+    const uint32_t* index;  // palette textures: bucket (i, j) -> palette bucket index[j w + i]; else null
+    int64_t plane;          // texels per direction plane: w * h, or the palette size K
+    int32_t W, H, n;
+    int8_t fmt, layout, live, wrap;  // wrap: bit 0 u, bit 1 v (repeat instead of clamp to edge)
+    float fW, fH;           // w, h as float
+    float half_n;           // n / 2
+    float hi;               // clamp range of B: [-hi, hi], hi = 1 - 1/n
 };
 static_assert(sizeof(TexDesc) == 64, "TexDesc is 64 bytes");
 
@@ -51,22 +52,28 @@ __device__ __forceinline__ bool finite3(float a, float b, float c) {
     return isfinite(a) && isfinite(b) && isfinite(c);
 }
 
-// Eq. 1b followed by Eq. 3, B = A |A| / max(|A_x|, |A_y|) with
-// A = sqrt(2) I_xy / |(I_x, I_y, I_z + 1)|.  Since A is a positive multiple of
-// I_xy, B = sqrt(2) (I_xy / m) |I_xy| / |(I_x, I_y, I_z + 1)| with
-// m = max(|I_x|, |I_y|).  Every component is divided by m first, so the sums of
-// squares neither underflow nor overflow (g2 lies in [1, 2]); a huge
-// (I_z + 1) / m gives B = 0, the limit.  I_xy = 0 (also I = -N) gives B = 0,
-// the limit of Eq. 3; so does m < 1e-18, which moves B by less than 1e-18.
-__device__ __forceinline__ float2 incidence_to_square(float Ix, float Iy, float Iz) {
-    float m = fmaxf(fabsf(Ix), fabsf(Iy));
+// Eq. 3 applied to A = sqrt(2) h_xy / |h|, the equisolid projection of a
+// half-way vector h: h = (I_x, I_y, I_z + 1) in the tangent frame (Eq. 1b) or
+// h = I + N in any frame (Eq. 1a).  Since A is a positive multiple of h_xy,
+// B = A |A| / max(|A_x|, |A_y|) = sqrt(2) (h_xy / m) |h_xy| / |h| with
+// m = max(|h_x|, |h_y|).  Every component is divided by m first, so the sums of
+// squares neither underflow nor overflow (g2 lies in [1, 2]); a huge h_z / m
+// gives B = 0, the limit.  h_xy = 0 (also I = -N) gives B = 0, the limit of
+// Eq. 3; so does m < 1e-18, which moves B by less than 1e-18.
+__device__ __forceinline__ float2 square_from_half(float hx, float hy, float hz) {
+    float m = fmaxf(fabsf(hx), fabsf(hy));
     if (!(m >= 1e-18f)) return make_float2(0.f, 0.f);
     float rm = 1.0f / m;
-    float x = Ix * rm, y = Iy * rm, z = (Iz + 1.0f) * rm;
+    float x = hx * rm, y = hy * rm, z = hz * rm;
     float g2 = x * x + y * y;
     float D2 = g2 + z * z;
     float k = 1.41421356237f * sqrtf(g2 / D2);
     return make_float2(x * k, y * k);
+}
+
+// Eq. 1b followed by Eq. 3 (tangent-space incidence).
+__device__ __forceinline__ float2 incidence_to_square(float Ix, float Iy, float Iz) {
+    return square_from_half(Ix, Iy, Iz + 1.0f);
 }
 
 // Continuous coordinate of a spatial axis and its two taps (clamp to edge).
@@ -87,6 +94,35 @@ __device__ __forceinline__ Axis spatial_axis_bilinear(float x, float size, int i
     a.w = c - f;
     a.k0 = min(max(a.fl, 0), isize - 1);
     a.k1 = min(max(a.fl + 1, 0), isize - 1);
+    return a;
+}
+
+// Repeat address mode: c is not clamped; the taps are floor(c) (and
+// floor(c) + 1) modulo the size.  Valid while |c| < 2^30.
+__device__ __forceinline__ int wrap_index(int x, int size) {
+    const int r = x % size;
+    return r < 0 ? r + size : r;
+}
+
+__device__ __forceinline__ Axis spatial_axis_bilinear_wrap(float x, float size, int isize) {
+    Axis a;
+    float c = fmaf(x, size, -0.5f);
+    float f = floorf(c);
+    a.c = c;
+    a.fl = (int)f;
+    a.w = c - f;
+    a.k0 = wrap_index(a.fl, isize);
+    a.k1 = a.k0 + 1 == isize ? 0 : a.k0 + 1;
+    return a;
+}
+
+__device__ __forceinline__ Axis spatial_axis_nearest_wrap(float x, float size, int isize) {
+    Axis a;
+    float c = x * size;
+    a.c = c;
+    a.fl = (int)floorf(c);
+    a.k0 = a.k1 = wrap_index(a.fl, isize);
+    a.w = 0.0f;
     return a;
 }
 
@@ -133,40 +169,77 @@ struct Lookup {
     float2 B;
 };
 
+// The lookup from B (any incidence mapping): spatial axes from (u, v) with the
+// texture's address mode, in-bucket axes from B.
 template <int FILTER>
-__device__ __forceinline__ Lookup<FILTER> locate(const TexDesc& d, float u, float v, float Ix, float Iy, float Iz) {
+__device__ __forceinline__ Lookup<FILTER> locate_from_square(const TexDesc& d, float u, float v, float2 B) {
     Lookup<FILTER> L;
     if (FILTER == RT_QUADRILINEAR) {
-        L.u = spatial_axis_bilinear(u, d.fW, d.W);
-        L.v = spatial_axis_bilinear(v, d.fH, d.H);
+        L.u = (d.wrap & 1) ? spatial_axis_bilinear_wrap(u, d.fW, d.W) : spatial_axis_bilinear(u, d.fW, d.W);
+        L.v = (d.wrap & 2) ? spatial_axis_bilinear_wrap(v, d.fH, d.H) : spatial_axis_bilinear(v, d.fH, d.H);
     } else {
-        L.u = spatial_axis_nearest(u, d.fW, d.W);
-        L.v = spatial_axis_nearest(v, d.fH, d.H);
+        L.u = (d.wrap & 1) ? spatial_axis_nearest_wrap(u, d.fW, d.W) : spatial_axis_nearest(u, d.fW, d.W);
+        L.v = (d.wrap & 2) ? spatial_axis_nearest_wrap(v, d.fH, d.H) : spatial_axis_nearest(v, d.fH, d.H);
     }
-    L.B = incidence_to_square(Ix, Iy, Iz);
+    L.B = B;
     if (FILTER == RT_NEAREST) {
-        L.s = angular_axis_nearest(L.B.x, d.lo, d.hi, d.half_n, d.n);
-        L.t = angular_axis_nearest(L.B.y, d.lo, d.hi, d.half_n, d.n);
+        L.s = angular_axis_nearest(L.B.x, -d.hi, d.hi, d.half_n, d.n);
+        L.t = angular_axis_nearest(L.B.y, -d.hi, d.hi, d.half_n, d.n);
     } else {
-        L.s = angular_axis_bilinear(L.B.x, d.lo, d.hi, d.half_n, d.n);
-        L.t = angular_axis_bilinear(L.B.y, d.lo, d.hi, d.half_n, d.n);
+        L.s = angular_axis_bilinear(L.B.x, -d.hi, d.hi, d.half_n, d.n);
+        L.t = angular_axis_bilinear(L.B.y, -d.hi, d.hi, d.half_n, d.n);
     }
     return L;
+}
+
+// Tangent-space lookup: Eq. 1b, Eq. 3, the Note's clamp.
+template <int FILTER>
+__device__ __forceinline__ Lookup<FILTER> locate(const TexDesc& d, float u, float v, float Ix, float Iy, float Iz) {
+    return locate_from_square<FILTER>(d, u, v, incidence_to_square(Ix, Iy, Iz));
+}
+
+// World-space lookup: A from the first two entries of Eq. 1a, h = I + N.
+template <int FILTER>
+__device__ __forceinline__ Lookup<FILTER> locate_world(const TexDesc& d, float u, float v, float3 I, float3 N) {
+    return locate_from_square<FILTER>(d, u, v, square_from_half(I.x + N.x, I.y + N.y, I.z + N.z));
 }
 
 // ---------------------------------------------------------------------------
 // Texel addressing and decoding.
 // ---------------------------------------------------------------------------
 
+// Internal layout of palette textures: PLANES storage of K palette buckets
+// (plane = K) reached through the index map, bucket (i, j) -> index[j w + i].
+constexpr int kLayoutPalette = 2;
+
+// Spatial offset of bucket (i, j) inside a direction plane.
+template <int LAYOUT>
+__device__ __forceinline__ int bucket_slot(const TexDesc& d, int i, int j) {
+    const int b = j * d.W + i;
+    if (LAYOUT == kLayoutPalette) return (int)__ldg(d.index + b);
+    return b;
+}
+
 template <int LAYOUT>
 __device__ __forceinline__ int64_t texel_index(const TexDesc& d, int i, int j, int s, int t) {
-    if (LAYOUT == RT_LAYOUT_PLANES)
-        return (int64_t)(t * d.n + s) * d.plane + (int64_t)j * d.W + i;
-    return ((int64_t)j * d.n + t) * ((int64_t)d.W * d.n) + (int64_t)i * d.n + s;
+    if (LAYOUT == RT_LAYOUT_ATLAS) return ((int64_t)j * d.n + t) * ((int64_t)d.W * d.n) + (int64_t)i * d.n + s;
+    return (int64_t)(t * d.n + s) * d.plane + bucket_slot<LAYOUT>(d, i, j);
 }
 
 template <int FMT>
 __device__ __forceinline__ float4 load_texel(const void* base, int64_t idx, float scale);
+
+// 1-bit texels: bit idx of the packed words.
+__device__ __forceinline__ float bit_texel(const void* base, int64_t idx) {
+    const unsigned w = __ldg(reinterpret_cast<const unsigned*>(base) + (idx >> 5));
+    return (float)((w >> (unsigned)(idx & 31)) & 1u);
+}
+
+template <>
+__device__ __forceinline__ float4 load_texel<RT_BIT1>(const void* base, int64_t idx, float) {
+    const float v = bit_texel(base, idx);
+    return make_float4(v, v, v, v);
+}
 
 template <>
 __device__ __forceinline__ float4 load_texel<RT_F32>(const void* base, int64_t idx, float) {
@@ -261,6 +334,12 @@ __device__ __forceinline__ P4 load_texelP<RT_F16>(const void* base, int64_t idx,
     float2 fa = __half22float2(*reinterpret_cast<__half2*>(&r.x));
     float2 fb = __half22float2(*reinterpret_cast<__half2*>(&r.y));
     return {pack2(fa.x, fa.y), pack2(fb.x, fb.y)};
+}
+
+template <>
+__device__ __forceinline__ P4 load_texelP<RT_BIT1>(const void* base, int64_t idx, float) {
+    const float v = bit_texel(base, idx);
+    return {pack2(v, v), pack2(v, v)};
 }
 
 // BF16 is the upper half of an FP32: widening is a 16-bit shift (exact).

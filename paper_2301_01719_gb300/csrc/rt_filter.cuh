@@ -17,7 +17,7 @@ template <int FMT, int LAYOUT>
 __device__ __forceinline__ void load_quad(const TexDesc& d, int i, int j, const Axis& s, const Axis& t, float4& t00,
                                           float4& t10, float4& t01, float4& t11) {
     float sc = 1.0f;
-    if (FMT == RT_E4M3_BUCKET_SCALE) sc = __ldg(d.scale + (int64_t)j * d.W + i);
+    if (FMT == RT_E4M3_BUCKET_SCALE) sc = __ldg(d.scale + bucket_slot<LAYOUT>(d, i, j));
     t00 = load_texel<FMT>(d.base, texel_index<LAYOUT>(d, i, j, s.k0, t.k0), sc);
     t10 = load_texel<FMT>(d.base, texel_index<LAYOUT>(d, i, j, s.k1, t.k0), sc);
     t01 = load_texel<FMT>(d.base, texel_index<LAYOUT>(d, i, j, s.k0, t.k1), sc);
@@ -31,21 +31,22 @@ template <int FMT, int LAYOUT>
 __device__ __forceinline__ void load_quadP(const TexDesc& d, int i, int j, const Axis& s, const Axis& t, P4& t00,
                                            P4& t10, P4& t01, P4& t11) {
     float sc = 1.0f;
-    if (FMT == RT_E4M3_BUCKET_SCALE) sc = __ldg(d.scale + (int64_t)j * d.W + i);
+    if (FMT == RT_E4M3_BUCKET_SCALE) sc = __ldg(d.scale + bucket_slot<LAYOUT>(d, i, j));
     t00 = load_texelP<FMT>(d.base, texel_index<LAYOUT>(d, i, j, s.k0, t.k0), sc);
     t10 = load_texelP<FMT>(d.base, texel_index<LAYOUT>(d, i, j, s.k1, t.k0), sc);
     t01 = load_texelP<FMT>(d.base, texel_index<LAYOUT>(d, i, j, s.k0, t.k1), sc);
     t11 = load_texelP<FMT>(d.base, texel_index<LAYOUT>(d, i, j, s.k1, t.k1), sc);
 }
 
-template <int FMT>
+template <int FMT, int LAYOUT>
 __device__ __forceinline__ P4 quadrilinear_planes(const TexDesc& d, const Axis& U, const Axis& V, const Axis& S,
                                                   const Axis& T) {
     const int64_t P = d.plane;
     const int64_t p00 = (int64_t)(T.k0 * d.n + S.k0) * P;
     const int64_t ds = (int64_t)(S.k1 - S.k0) * P, dt = (int64_t)(T.k1 - T.k0) * d.n * P;
     const int64_t pl[4] = {p00, p00 + ds, p00 + dt, p00 + dt + ds};
-    const int o[4] = {V.k0 * d.W + U.k0, V.k0 * d.W + U.k1, V.k1 * d.W + U.k0, V.k1 * d.W + U.k1};
+    const int o[4] = {bucket_slot<LAYOUT>(d, U.k0, V.k0), bucket_slot<LAYOUT>(d, U.k1, V.k0),
+                      bucket_slot<LAYOUT>(d, U.k0, V.k1), bucket_slot<LAYOUT>(d, U.k1, V.k1)};
     float sc[4] = {1.f, 1.f, 1.f, 1.f};
     if (FMT == RT_E4M3_BUCKET_SCALE) {
 #pragma unroll
@@ -67,15 +68,15 @@ template <int FILTER, int FMT, int LAYOUT>
 __device__ __forceinline__ float4 filter_taps(const TexDesc& d, const Lookup<FILTER>& L) {
     if (FILTER == RT_NEAREST) {
         float sc = 1.0f;
-        if (FMT == RT_E4M3_BUCKET_SCALE) sc = __ldg(d.scale + (int64_t)L.v.k0 * d.W + L.u.k0);
+        if (FMT == RT_E4M3_BUCKET_SCALE) sc = __ldg(d.scale + bucket_slot<LAYOUT>(d, L.u.k0, L.v.k0));
         return toF4(load_texelP<FMT>(d.base, texel_index<LAYOUT>(d, L.u.k0, L.v.k0, L.s.k0, L.t.k0), sc));
     } else if (FILTER == RT_ANGULAR_BILINEAR) {
         P4 a, b, c, e;
         load_quadP<FMT, LAYOUT>(d, L.u.k0, L.v.k0, L.s, L.t, a, b, c, e);
         const f32x2 ws = pack2(L.s.w, L.s.w), wt = pack2(L.t.w, L.t.w);
         return toF4(lerpP(lerpP(a, b, ws), lerpP(c, e, ws), wt));
-    } else if (LAYOUT == RT_LAYOUT_PLANES) {
-        return toF4(quadrilinear_planes<FMT>(d, L.u, L.v, L.s, L.t));
+    } else if (LAYOUT != RT_LAYOUT_ATLAS) {
+        return toF4(quadrilinear_planes<FMT, LAYOUT>(d, L.u, L.v, L.s, L.t));
     } else {
         P4 q[2][2][4];
 #pragma unroll
@@ -100,19 +101,27 @@ __device__ __forceinline__ float4 filter_taps(const TexDesc& d, const Lookup<FIL
 }
 
 // Dispatch on the object's storage format and layout (owned textures are
-// PLANES; a borrowed FP32 buffer may be either).
+// PLANES or palettes; a borrowed FP32 buffer may be any of the three).
 template <int FILTER>
 __device__ __forceinline__ float4 filter_any(const TexDesc& d, const Lookup<FILTER>& L) {
+    const bool pal = d.layout == kLayoutPalette;
     switch (d.fmt) {
         case RT_F16:
-            return filter_taps<FILTER, RT_F16, RT_LAYOUT_PLANES>(d, L);
+            return pal ? filter_taps<FILTER, RT_F16, kLayoutPalette>(d, L)
+                       : filter_taps<FILTER, RT_F16, RT_LAYOUT_PLANES>(d, L);
         case RT_BF16:
-            return filter_taps<FILTER, RT_BF16, RT_LAYOUT_PLANES>(d, L);
+            return pal ? filter_taps<FILTER, RT_BF16, kLayoutPalette>(d, L)
+                       : filter_taps<FILTER, RT_BF16, RT_LAYOUT_PLANES>(d, L);
         case RT_E4M3_BUCKET_SCALE:
-            return filter_taps<FILTER, RT_E4M3_BUCKET_SCALE, RT_LAYOUT_PLANES>(d, L);
+            return pal ? filter_taps<FILTER, RT_E4M3_BUCKET_SCALE, kLayoutPalette>(d, L)
+                       : filter_taps<FILTER, RT_E4M3_BUCKET_SCALE, RT_LAYOUT_PLANES>(d, L);
+        case RT_BIT1:
+            return pal ? filter_taps<FILTER, RT_BIT1, kLayoutPalette>(d, L)
+                       : filter_taps<FILTER, RT_BIT1, RT_LAYOUT_PLANES>(d, L);
         default:
             if (d.layout == RT_LAYOUT_ATLAS) return filter_taps<FILTER, RT_F32, RT_LAYOUT_ATLAS>(d, L);
-            return filter_taps<FILTER, RT_F32, RT_LAYOUT_PLANES>(d, L);
+            return pal ? filter_taps<FILTER, RT_F32, kLayoutPalette>(d, L)
+                       : filter_taps<FILTER, RT_F32, RT_LAYOUT_PLANES>(d, L);
     }
 }
 
@@ -367,6 +376,16 @@ __device__ __forceinline__ bool fragment_valid(const TexDesc* __restrict__ table
     }
     // 0 * t is 0 for finite t and NaN for an infinity or a NaN: one test covers all five inputs
     const float probe = fmaf(z, 0.f, fmaf(y, 0.f, fmaf(x, 0.f, fmaf(v, 0.f, u * 0.f))));
+    if (probe != 0.f) {
+        atomicOr(status, ST_NONFINITE);
+        return false;
+    }
+    return true;
+}
+
+// A world-space fragment's normal must be finite (status bit otherwise).
+__device__ __forceinline__ bool normal_valid(float3 N, unsigned* status) {
+    const float probe = fmaf(N.z, 0.f, fmaf(N.y, 0.f, N.x * 0.f));
     if (probe != 0.f) {
         atomicOr(status, ST_NONFINITE);
         return false;

@@ -76,6 +76,26 @@ cudaError_t launch_fixed_to_float(const long long* acc, float* dst, int64_t coun
 cudaError_t launch_encode(const float* src, int src_layout, void* dst, float* scale, int W, int H, int n, int fmt,
                           cudaStream_t stream);
 cudaError_t launch_read(const void* src, int fmt, int W, int H, int n, int dst_layout, void* dst, cudaStream_t stream);
+cudaError_t launch_bake_shadow(const rt_bake_scene& S, int surface, void* dst, int W, int H, int n,
+                               cudaStream_t stream);
+cudaError_t launch_multi_shade(const TexDesc* table, int n_obj, const float* uv, const float* dirs, int S,
+                               const int32_t* obj, int64_t F, int filter, float* out, unsigned* status,
+                               cudaStream_t stream);
+cudaError_t launch_world_shade(const TexDesc* table, int n_obj, const float* uv, const float* dir, const float* nrm,
+                               const int32_t* obj, int64_t F, int filter, float* out, int32_t* idx, float* coord,
+                               unsigned* status, cudaStream_t stream);
+cudaError_t launch_world_backward(const TexDesc* table, int n_obj, const float* uv, const float* dir,
+                                  const float* nrm, const int32_t* obj, int64_t F, int filter, const float* dL_dout,
+                                  const GradTable& grads, bool any_grad, float* dL_duv, float* dL_ddir,
+                                  float* dL_dnrm, bool accumulate, bool deterministic, unsigned* status,
+                                  cudaStream_t stream);
+cudaError_t launch_kmeans_init(const TexDesc& d, int K, const int32_t* buckets, float* C, unsigned* status,
+                               cudaStream_t stream);
+cudaError_t launch_kmeans_assign(const TexDesc& d, int K, const float* C, uint32_t* index, float* dist,
+                                 cudaStream_t stream);
+cudaError_t launch_kmeans_update(const TexDesc& d, int K, const uint32_t* index, float* C, uint32_t* scratch,
+                                 unsigned* status, cudaStream_t stream);
+cudaError_t launch_check_index(const uint32_t* index, int64_t count, uint32_t K, unsigned* bad, cudaStream_t stream);
 cudaError_t launch_bake(const rt_bake_scene& S, int surface, void* dst, float* scale, int W, int H, int n, int fmt,
                         int layout, cudaStream_t stream);
 cudaError_t launch_fill_lobes(const float* params, void* dst, float* scale, int W, int H, int n, int fmt,

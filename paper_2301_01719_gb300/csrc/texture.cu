@@ -45,9 +45,29 @@ __global__ void encode_e4m3_buckets(const float4* __restrict__ src, int src_layo
                 pack_e4m3(src[index_in(src_layout, W, H, n, i, j, s, t)], sc);
 }
 
+// FP32 source -> 1-bit storage: bit = (channel 0 >= 1/2); one thread per 32-bit word.
+__global__ void encode_bits(const float4* __restrict__ src, int src_layout, unsigned* __restrict__ dst, int W, int H,
+                            int n, int64_t total) {
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w * 32 >= total) return;
+    unsigned word = 0;
+    for (int k = 0; k < 32; ++k) {
+        const int64_t idx = w * 32 + k;
+        if (idx >= total) break;
+        int i, j, s, t;
+        planes_coords(idx, W, H, n, i, j, s, t);
+        if (src[index_in(src_layout, W, H, n, i, j, s, t)].x >= 0.5f) word |= 1u << k;
+    }
+    dst[w] = word;
+}
+
 cudaError_t launch_encode(const float* src, int src_layout, void* dst, float* scale, int W, int H, int n, int fmt,
                           cudaStream_t stream) {
-    if (fmt == RT_E4M3_BUCKET_SCALE) {
+    if (fmt == RT_BIT1) {
+        const int64_t total = (int64_t)W * H * n * n;
+        encode_bits<<<blocks_for((total + 31) / 32), kThreads, 0, stream>>>(
+            reinterpret_cast<const float4*>(src), src_layout, reinterpret_cast<unsigned*>(dst), W, H, n, total);
+    } else if (fmt == RT_E4M3_BUCKET_SCALE) {
         int64_t buckets = (int64_t)W * H;
         encode_e4m3_buckets<<<blocks_for(buckets), kThreads, 0, stream>>>(
             reinterpret_cast<const float4*>(src), src_layout, reinterpret_cast<unsigned*>(dst), scale, W, H, n);
@@ -70,11 +90,25 @@ __global__ void read_codes(const T* __restrict__ src, T* __restrict__ dst, int W
     dst[index_in(dst_layout, W, H, n, i, j, s, t)] = src[idx];
 }
 
+// 1-bit storage -> one byte (0 or 1) per texel in dst_layout.
+__global__ void read_bits(const unsigned* __restrict__ src, uint8_t* __restrict__ dst, int W, int H, int n,
+                          int dst_layout, int64_t total) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    int i, j, s, t;
+    planes_coords(idx, W, H, n, i, j, s, t);
+    int64_t o = index_in(dst_layout, W, H, n, i, j, s, t);
+    dst[o] = (uint8_t)((src[idx >> 5] >> (unsigned)(idx & 31)) & 1u);
+}
+
 cudaError_t launch_read(const void* src, int fmt, int W, int H, int n, int dst_layout, void* dst,
                         cudaStream_t stream) {
     int64_t total = (int64_t)W * H * n * n;
     unsigned g = blocks_for(total);
-    if (fmt == RT_F32)
+    if (fmt == RT_BIT1)
+        read_bits<<<g, kThreads, 0, stream>>>(reinterpret_cast<const unsigned*>(src), reinterpret_cast<uint8_t*>(dst),
+                                              W, H, n, dst_layout, total);
+    else if (fmt == RT_F32)
         read_codes<float4><<<g, kThreads, 0, stream>>>(reinterpret_cast<const float4*>(src),
                                                        reinterpret_cast<float4*>(dst), W, H, n, dst_layout, total);
     else if (fmt == RT_E4M3_BUCKET_SCALE)
@@ -141,6 +175,17 @@ __global__ void convert_kernel(const float4* __restrict__ src, int src_layout, f
     dst[index_in(dst_layout, W, H, n, i, j, s, t)] = src[index_in(src_layout, W, H, n, i, j, s, t)];
 }
 
+__global__ void check_index_kernel(const uint32_t* __restrict__ index, int64_t count, uint32_t K, unsigned* bad) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < count && index[k] >= K) atomicOr(bad, 1u);
+}
+
+cudaError_t launch_check_index(const uint32_t* index, int64_t count, uint32_t K, unsigned* bad, cudaStream_t stream) {
+    if (count == 0) return cudaSuccess;
+    check_index_kernel<<<blocks_for(count), kThreads, 0, stream>>>(index, count, K, bad);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_convert(const float* src, int src_layout, float* dst, int dst_layout, int W, int H, int n,
                            cudaStream_t stream) {
     int64_t total = (int64_t)W * H * n * n;
@@ -174,9 +219,11 @@ __global__ void __launch_bounds__(kThreads) footprint_kernel(const TexDesc* __re
             for (int a = 0; a < nu; ++a)
                 for (int t = 0; t < ns; ++t)
                     for (int p = 0; p < ns; ++p) {
-                        int64_t bit = base + texel_index<RT_LAYOUT_PLANES>(d, a ? L.u.k1 : L.u.k0,
-                                                                           b ? L.v.k1 : L.v.k0, p ? L.s.k1 : L.s.k0,
-                                                                           t ? L.t.k1 : L.t.k0);
+                        const int i = a ? L.u.k1 : L.u.k0, j = b ? L.v.k1 : L.v.k0;
+                        const int s = p ? L.s.k1 : L.s.k0, tt = t ? L.t.k1 : L.t.k0;
+                        int64_t bit = base + (d.layout == kLayoutPalette
+                                                  ? texel_index<kLayoutPalette>(d, i, j, s, tt)
+                                                  : texel_index<RT_LAYOUT_PLANES>(d, i, j, s, tt));
                         atomicOr(bitmap + (bit >> 5), 1u << (bit & 31));
                     }
     });
