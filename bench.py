@@ -53,7 +53,9 @@ def parse_args(argv=None):
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--workload", choices=["sphere-plane", "voronoi64", "bake"], default="sphere-plane",
+    p.add_argument("--samples", type=int, default=4, help="shadow: light samples per fragment")
+    p.add_argument("--workload", choices=["sphere-plane", "voronoi64", "bake", "world", "shadow"],
+                   default="sphere-plane",
                    help="voronoi64: 64 objects of uneven sizes, 4 views of 3840x2160, forward in a CUDA graph; "
                         "bake: rt_bake of the sphere-plane workload's two textures")
     p.add_argument("--objects", type=int, default=64)
@@ -780,6 +782,157 @@ def ctypes_sizeof_scene() -> int:
     return ctypes.sizeof(_lib.BakeScene)
 
 
+# ---------------------------------------------------------------------------
+# Variant workloads on the sphere-plane G-buffer: world-space lookups with a
+# per-fragment normal, and area shadows over 1-bit shadow textures.
+# ---------------------------------------------------------------------------
+
+def variant_inputs(a, torch, dev, g_uv, g_dir, samples: int, seed: int):
+    """Seeded per-fragment extra inputs made on the device (input synthesis
+    only).  World-space workload: unit normals tilted from +z by a smooth
+    bump pattern of the surface UV (a normal-mapped surface).  Shadow
+    workload: `samples` light directions per fragment, the G-buffer direction
+    plus one of `samples` fixed seeded offsets (an area light seen through the
+    same sample pattern at every fragment)."""
+    F = g_dir.shape[0]
+    if samples == 0:
+        two_pi = 6.283185307179586
+        N = torch.stack([0.3 * torch.sin(two_pi * 8.0 * g_uv[:, 0]), 0.3 * torch.cos(two_pi * 8.0 * g_uv[:, 1]),
+                         torch.ones(F, device=dev)], dim=1)
+        return (N / N.norm(dim=1, keepdim=True)).contiguous()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    offsets = 0.1 * torch.randn((1, samples, 3), generator=gen, device=dev)
+    L = g_dir[:, None, :] + offsets
+    L[..., 2] = L[..., 2].abs()
+    return (L / L.norm(dim=2, keepdim=True)).contiguous()
+
+
+def run_variant(a):
+    """--workload world | shadow on the sphere-plane G-buffer (flat fragment stream)."""
+    import torch
+
+    import synth
+    from paper_2301_01719_gb300 import api, build
+
+    rank, world, local = dist_info()
+    if a.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the oracle on the "
+                              "default workload; the variant workloads report their oracle baseline inline"}))
+        return
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device; libradtex has no CPU path")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    filt = api.FILTER_NAMES[a.filter]
+    F = a.views * a.width * a.height
+    g = synth.sphere_plane_scene(rank_scene_seed(rank), views=a.views, width=a.width, height=a.height)
+    uv = torch.from_numpy(g.uv).to(dev)
+    dirs = torch.from_numpy(g.dir).to(dev)
+    ctx = api.Context(local)
+    oids = []
+    shadow = a.workload == "shadow"
+    scene = synth.bake_scene(BAKE_SCENE_SEED + rank)
+    bake_ms = None
+    if shadow:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for surf in (api.RT_SURFACE_SPHERE, api.RT_SURFACE_PLANE):
+            oids.append(api.rt_create_texture(ctx, a.buckets, a.buckets, a.n, api.RT_BIT1))
+        for _ in range(2):  # warm, then timed
+            ev0.record()
+            for oid, surf in zip(oids, (api.RT_SURFACE_SPHERE, api.RT_SURFACE_PLANE)):
+                api.rt_bake_shadow(ctx, oid, surf, scene)
+            ev1.record()
+            torch.cuda.synchronize()
+        bake_ms = ev0.elapsed_time(ev1)
+    else:
+        for seed in TEX_SEEDS:
+            oid = api.rt_create_texture(ctx, a.buckets, a.buckets, a.n, api.FORMAT_NAMES[a.storage])
+            api.rt_fill_bucket_lobes(ctx, oid, torch.from_numpy(synth.bucket_lobe_params(seed, a.buckets,
+                                                                                          a.buckets)).to(dev))
+            oids.append(oid)
+    remap = torch.tensor(oids, dtype=torch.int32, device=dev)
+    obj_np = torch.from_numpy(g.obj).to(dev)
+    obj = torch.where(obj_np >= 0, remap[obj_np.clamp(min=0).long()], obj_np).contiguous()
+    del g
+    extra = variant_inputs(a, torch, dev, uv, dirs, a.samples if shadow else 0, 77 + rank)
+    out = torch.empty((F, 4), dtype=torch.float32, device=dev)
+    duv = torch.empty_like(uv)
+    ddir = torch.empty_like(dirs)
+    dnrm = torch.empty_like(dirs)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        if shadow:
+            api.rt_shade_multi(ctx, uv, extra, obj, filt, out)
+        else:
+            api.rt_shade_world(ctx, uv, dirs, extra, obj, filt, out)
+            api.rt_shade_world_backward(ctx, uv, dirs, extra, obj, filt, out, None, duv, ddir, dnrm)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        clk.mark_start()
+        start.record(stream)
+        for _ in range(a.steps):
+            step()
+        end.record(stream)
+        torch.cuda.synchronize()
+        clk.mark_end()
+    st = api.rt_get_error(ctx)
+    if st != api.RT_OK:
+        raise RuntimeError(f"device status after timing: {api.rt_status_string(st)}")
+    ms = max_over_ranks(start.elapsed_time(end) / a.steps, dev)
+    value = whole_job_rate(F, world, ms)
+    peak, peak_kind = measured_peak()
+    if shadow:
+        nbytes = F * (8 + 12 * a.samples + 4 + 16)  # uv, S directions, obj, colour; the bits stay in L2
+        kernel, metric = "multi_shade_kernel", "area-shadow lookups (Gfrag/s, S light samples per fragment)"
+    else:
+        nbytes = F * ((8 + 12 + 12 + 4 + 16) + (8 + 12 + 12 + 4 + 16 + 8 + 12 + 12))  # fwd + bwd streams
+        kernel, metric = "world_shade_kernel + world_backward_kernel", "world-space lookups (Gfrag/s), fwd + bwd"
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    result = {
+        "metric": metric, "value": value, "unit": "Gfrag/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{a.workload}: sphere+plane {a.width}x{a.height} x {a.views} poses, 2 objects x "
+                               f"{a.buckets}^2 x {a.n}^2 " + (f"BIT1, S={a.samples}" if shadow else
+                                                             f"{a.storage.upper()}, bumpy normals"),
+                   "filter": a.filter, "fragments_per_step": F * world,
+                   "l2": "inputs larger than L2 (G-buffer %.1f GB per rank)" % (nbytes / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": peak_kind, "algorithmic_bytes_per_step": int(nbytes),
+                     "kernel": kernel},
+        "gpu_launches": (1 if shadow else 2) * a.steps,
+        "clocks": clk.summary(),
+        "e2e": None,
+    }
+    if shadow:
+        result["lookups_per_s"] = value * a.samples
+        result["shadow_bake_ms"] = bake_ms
+        result["shadow_bake_gtexel_s"] = 2 * a.buckets * a.buckets * a.n * a.n / (bake_ms * 1e-3) / 1e9
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 VORONOI_SCENE_SEED, VORONOI_SIZE_SEED = 7007, 4004
 
 
@@ -898,6 +1051,8 @@ def main(argv=None):
     a = parse_args(argv)
     if a.workload == "bake":
         run_bake(a)
+    elif a.workload in ("world", "shadow"):
+        run_variant(a)
     elif a.impl == "reference":
         run_reference(a)
     elif a.workload == "voronoi64":

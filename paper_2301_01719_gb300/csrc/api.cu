@@ -27,6 +27,7 @@ struct rt_ctx {
     int tile[3][4];                      // per filter: tw, th, bx, by of the batched kernels
     long long* det[RT_MAX_OBJECTS];      // fixed-point gradient sums of the deterministic mode
     uint32_t* index[RT_MAX_OBJECTS];     // palette index maps the library copied
+    int spec = -1;                       // the format shared by all objects (dense PLANES, clamp), else -1
 };
 
 namespace {
@@ -90,7 +91,23 @@ rt_status check_gbuffer(const float* uv, const float* dir, const int32_t* obj, i
     return RT_OK;
 }
 
+// The single-format specialisation the tiled kernels may use for this table.
+int table_spec(const rt_ctx* ctx) {
+    int spec = -2;
+    for (int o = 0; o < ctx->n_obj; ++o) {
+        const TexDesc& d = ctx->table[o];
+        if (!d.live) continue;
+        if (d.layout != RT_LAYOUT_PLANES || d.wrap || d.fmt == RT_BIT1) return -1;
+        if (spec == -2)
+            spec = d.fmt;
+        else if (spec != d.fmt)
+            return -1;
+    }
+    return spec < 0 ? -1 : spec;
+}
+
 rt_status upload_table(rt_ctx* ctx) {
+    ctx->spec = table_spec(ctx);
     cudaError_t e = cudaMemcpy(ctx->d_table, ctx->table, sizeof(TexDesc) * RT_MAX_OBJECTS, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return cuda_status(e);
@@ -456,7 +473,7 @@ rt_status rt_shade(rt_ctx* ctx, const float* uv, const float* dir, const int32_t
     if (!out || !aligned16(out)) return RT_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return RT_ERR_CUDA;
-    return cuda_status(rt::launch_shade(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, rt::flat_tiling(), out,
+    return cuda_status(rt::launch_shade(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, rt::flat_tiling(), ctx->spec, out,
                                         ctx->d_status, (cudaStream_t)stream));
 }
 
@@ -522,7 +539,7 @@ static rt_status shade_backward_impl(rt_ctx* ctx, const float* uv, const float* 
             e = rt::launch_world_backward(ctx->d_table, ctx->n_obj, uv, dir, nrm, obj, F, filter, dL_dout, grads, any,
                                           dL_duv, dL_ddir, dL_dnrm, accumulate, deterministic, ctx->d_status, s);
         else
-            e = rt::launch_backward(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any,
+            e = rt::launch_backward(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, T, ctx->spec, dL_dout, grads, any,
                                     dL_duv, dL_ddir, accumulate, deterministic, ctx->d_status, s);
     }
     if (deterministic)
@@ -625,7 +642,7 @@ rt_status rt_shade_batched(rt_ctx* ctx, const float* uv, const float* dir, const
     if (!frames_tiling(ctx, views, height, width, filter, &T)) return RT_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return RT_ERR_CUDA;
-    return cuda_status(rt::launch_shade(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, T, out, ctx->d_status,
+    return cuda_status(rt::launch_shade(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, T, ctx->spec, out, ctx->d_status,
                                         (cudaStream_t)stream));
 }
 

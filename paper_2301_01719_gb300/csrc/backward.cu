@@ -240,7 +240,17 @@ __device__ __forceinline__ float2 uv_grad(const TexDesc& d, float u, float v, fl
     return r;
 }
 
-template <int FILTER, bool TILED, bool DET>
+// SPEC as in filter_spec: one format for every object, or -1 (dispatch).
+template <int FILTER, bool DET, int SPEC>
+__device__ __forceinline__ CoordGrad backward_spec(const TexDesc& d, const Lookup<FILTER>& L, float4 g, void* grad,
+                                                   bool coord_grads) {
+    if constexpr (SPEC < 0)
+        return backward_any<FILTER, DET>(d, L, g, grad, coord_grads);
+    else
+        return backward_layout<FILTER, SPEC, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
+}
+
+template <int FILTER, bool TILED, bool DET, int SPEC>
 __global__ void __launch_bounds__(kBackThreads) backward_kernel(
     const TexDesc* __restrict__ table, int n_obj, const float* __restrict__ uv, const float* __restrict__ dir,
     const int32_t* __restrict__ obj, int64_t F, Tiling tiling, const float* __restrict__ dL_dout,
@@ -254,9 +264,9 @@ __global__ void __launch_bounds__(kBackThreads) backward_kernel(
         float3 gdir = make_float3(0.f, 0.f, 0.f);
         TexDesc d;
         if (fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d)) {
-            Lookup<FILTER> L = locate<FILTER>(d, q.u, q.v, q.x, q.y, q.z);
+            Lookup<FILTER> L = locate<FILTER, (SPEC < 0)>(d, q.u, q.v, q.x, q.y, q.z);
             void* grad = any_grad ? grads.p[q.o] : nullptr;
-            CoordGrad cg = backward_any<FILTER, DET>(d, L, go, grad, coord_grads);
+            CoordGrad cg = backward_spec<FILTER, DET, SPEC>(d, L, go, grad, coord_grads);
             if (FILTER == RT_QUADRILINEAR) guv = uv_grad(d, q.u, q.v, cg.gu, cg.gv);
             if (FILTER != RT_NEAREST && dL_ddir) {
                 float gBx = (L.B.x > -d.hi && L.B.x < d.hi) ? cg.gs * d.half_n : 0.f;
@@ -288,85 +298,98 @@ __global__ void __launch_bounds__(kBackThreads) backward_kernel(
     });
 }
 
-template <int FILTER, bool TILED, bool DET>
+template <int FILTER, bool TILED, bool DET, int SPEC>
 static cudaError_t launch_backward_t(const TexDesc* table, int n_obj, const float* uv, const float* dir,
                                      const int32_t* obj, int64_t F, const Tiling& T, const float* dL_dout,
                                      const GradTable& grads, bool any_grad, float* dL_duv, float* dL_ddir,
                                      bool accumulate, unsigned* status, cudaStream_t stream) {
-    const unsigned grid = persistent_grid(backward_kernel<FILTER, TILED, DET>, kBackThreads,
+    const unsigned grid = persistent_grid(backward_kernel<FILTER, TILED, DET, SPEC>, kBackThreads,
                                           chunk_count_host(T, F, kBackWarps));
-    backward_kernel<FILTER, TILED, DET><<<grid, kBackThreads, 0, stream>>>(
+    backward_kernel<FILTER, TILED, DET, SPEC><<<grid, kBackThreads, 0, stream>>>(
         table, n_obj, uv, dir, obj, F, T, dL_dout, grads, any_grad, dL_duv, dL_ddir, accumulate, status);
     return cudaGetLastError();
 }
 
-template <bool TILED, bool DET>
+template <bool TILED, bool DET, int SPEC>
 static cudaError_t launch_backward_f(const TexDesc* table, int n_obj, const float* uv, const float* dir,
                                      const int32_t* obj, int64_t F, int filter, const Tiling& T,
                                      const float* dL_dout, const GradTable& grads, bool any_grad, float* dL_duv,
                                      float* dL_ddir, bool accumulate, unsigned* status, cudaStream_t stream) {
     switch (filter) {
         case RT_NEAREST:
-            return launch_backward_t<RT_NEAREST, TILED, DET>(table, n_obj, uv, dir, obj, F, T, dL_dout, grads,
-                                                             any_grad, dL_duv, dL_ddir, accumulate, status, stream);
+            return launch_backward_t<RT_NEAREST, TILED, DET, SPEC>(table, n_obj, uv, dir, obj, F, T, dL_dout, grads,
+                                                                   any_grad, dL_duv, dL_ddir, accumulate, status,
+                                                                   stream);
         case RT_ANGULAR_BILINEAR:
-            return launch_backward_t<RT_ANGULAR_BILINEAR, TILED, DET>(table, n_obj, uv, dir, obj, F, T, dL_dout,
-                                                                      grads, any_grad, dL_duv, dL_ddir, accumulate,
-                                                                      status, stream);
+            return launch_backward_t<RT_ANGULAR_BILINEAR, TILED, DET, SPEC>(table, n_obj, uv, dir, obj, F, T,
+                                                                            dL_dout, grads, any_grad, dL_duv,
+                                                                            dL_ddir, accumulate, status, stream);
         default:
-            return launch_backward_t<RT_QUADRILINEAR, TILED, DET>(table, n_obj, uv, dir, obj, F, T, dL_dout, grads,
-                                                                  any_grad, dL_duv, dL_ddir, accumulate, status,
-                                                                  stream);
+            return launch_backward_t<RT_QUADRILINEAR, TILED, DET, SPEC>(table, n_obj, uv, dir, obj, F, T, dL_dout,
+                                                                        grads, any_grad, dL_duv, dL_ddir,
+                                                                        accumulate, status, stream);
     }
 }
 
+// The screen-tiled, non-deterministic path has a single-format instantiation
+// per storage format (spec); the others run the dispatching kernels.
 cudaError_t launch_backward(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
-                            int64_t F, int filter, const Tiling& T, const float* dL_dout, const GradTable& grads,
-                            bool any_grad, float* dL_duv, float* dL_ddir, bool accumulate, bool deterministic,
-                            unsigned* status, cudaStream_t stream) {
+                            int64_t F, int filter, const Tiling& T, int spec, const float* dL_dout,
+                            const GradTable& grads, bool any_grad, float* dL_duv, float* dL_ddir, bool accumulate,
+                            bool deterministic, unsigned* status, cudaStream_t stream) {
+#define RT_BWD(TILED, DET, SPEC)                                                                                 \
+    launch_backward_f<TILED, DET, SPEC>(table, n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any_grad, dL_duv, \
+                                        dL_ddir, accumulate, status, stream)
     if (T.W > 0) {
-        if (deterministic)
-            return launch_backward_f<true, true>(table, n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any_grad,
-                                                 dL_duv, dL_ddir, accumulate, status, stream);
-        return launch_backward_f<true, false>(table, n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any_grad,
-                                              dL_duv, dL_ddir, accumulate, status, stream);
+        if (deterministic) return RT_BWD(true, true, -1);
+        switch (spec) {
+            case RT_F16:
+                return RT_BWD(true, false, RT_F16);
+            case RT_BF16:
+                return RT_BWD(true, false, RT_BF16);
+            case RT_F32:
+                return RT_BWD(true, false, RT_F32);
+            case RT_E4M3_BUCKET_SCALE:
+                return RT_BWD(true, false, RT_E4M3_BUCKET_SCALE);
+            default:
+                return RT_BWD(true, false, -1);
+        }
     }
-    if (deterministic)
-        return launch_backward_f<false, true>(table, n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any_grad,
-                                              dL_duv, dL_ddir, accumulate, status, stream);
-    return launch_backward_f<false, false>(table, n_obj, uv, dir, obj, F, filter, T, dL_dout, grads, any_grad,
-                                           dL_duv, dL_ddir, accumulate, status, stream);
+    if (deterministic) return RT_BWD(false, true, -1);
+    return RT_BWD(false, false, -1);
+#undef RT_BWD
 }
 
-// World-space backward (Eq. 1a with a per-fragment normal): one fragment per
-// thread, grid-stride.  dL/dI = dL/dN, since A depends on h = I + N only.
+// World-space backward (Eq. 1a with a per-fragment normal): the streamer of
+// the tangent-space backward with the normal as a fourth staged stream, over
+// the flat fragment stream.  dL/dI = dL/dN, since A depends on h = I + N only.
 template <int FILTER, bool DET>
 __global__ void __launch_bounds__(kBackThreads) world_backward_kernel(
     const TexDesc* __restrict__ table, int n_obj, const float* __restrict__ uv, const float* __restrict__ dir,
     const float* __restrict__ nrm, const int32_t* __restrict__ obj, int64_t F, const float* __restrict__ dL_dout,
     const __grid_constant__ GradTable grads, bool any_grad, float* __restrict__ dL_duv, float* __restrict__ dL_ddir,
     float* __restrict__ dL_dnrm, bool accumulate, unsigned* status) {
+    __shared__ WarpStage<true, 2, true> stages[kBackWarps];
     const bool coord_grads = dL_duv || dL_ddir || dL_dnrm;
-    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
-        const float2 q = reinterpret_cast<const float2*>(uv)[f];
-        const float3 I = make_float3(dir[3 * f], dir[3 * f + 1], dir[3 * f + 2]);
-        const float3 N = make_float3(nrm[3 * f], nrm[3 * f + 1], nrm[3 * f + 2]);
+    const Tiling flat = flat_tiling();
+    for_each_fragment<kBackWarps, true, false, 2, true>(uv, dir, obj, dL_dout, F, flat, stages,
+                                                        [&](int64_t f, const Frag& q, float4 go) {
         float2 guv = make_float2(0.f, 0.f);
         float3 gh = make_float3(0.f, 0.f, 0.f);
         TexDesc d;
-        if (fragment_valid(table, n_obj, obj[f], q.x, q.y, I.x, I.y, I.z, status, d) &&
-            normal_valid(N, status)) {
-            const Lookup<FILTER> L = locate_world<FILTER>(d, q.x, q.y, I, N);
-            const float4 go = reinterpret_cast<const float4*>(dL_dout)[f];
-            void* grad = any_grad ? grads.p[obj[f]] : nullptr;
+        const float3 I = make_float3(q.x, q.y, q.z), N = make_float3(q.nx, q.ny, q.nz);
+        if (fragment_valid(table, n_obj, q.o, q.u, q.v, I.x, I.y, I.z, status, d) && normal_valid(N, status)) {
+            const Lookup<FILTER> L = locate_world<FILTER>(d, q.u, q.v, I, N);
+            void* grad = any_grad ? grads.p[q.o] : nullptr;
             const CoordGrad cg = backward_any<FILTER, DET>(d, L, go, grad, coord_grads);
-            if (FILTER == RT_QUADRILINEAR) guv = uv_grad(d, q.x, q.y, cg.gu, cg.gv);
+            if (FILTER == RT_QUADRILINEAR) guv = uv_grad(d, q.u, q.v, cg.gu, cg.gv);
             if (FILTER != RT_NEAREST && (dL_ddir || dL_dnrm)) {
                 const float gBx = (L.B.x > -d.hi && L.B.x < d.hi) ? cg.gs * d.half_n : 0.f;
                 const float gBy = (L.B.y > -d.hi && L.B.y < d.hi) ? cg.gt * d.half_n : 0.f;
                 gh = half_grad(I.x + N.x, I.y + N.y, I.z + N.z, gBx, gBy);
             }
         }
+        if (f < 0) return;
         if (dL_duv) {
             float2* p = reinterpret_cast<float2*>(dL_duv) + f;
             if (accumulate) {
@@ -377,6 +400,7 @@ __global__ void __launch_bounds__(kBackThreads) world_backward_kernel(
             *p = guv;
         }
         float* outs[2] = {dL_ddir, dL_dnrm};
+#pragma unroll
         for (int k = 0; k < 2; ++k) {
             float* p = outs[k];
             if (!p) continue;
@@ -385,7 +409,7 @@ __global__ void __launch_bounds__(kBackThreads) world_backward_kernel(
             p[1] = accumulate ? p[1] + gh.y : gh.y;
             p[2] = accumulate ? p[2] + gh.z : gh.z;
         }
-    }
+    }, nrm);
 }
 
 template <int FILTER, bool DET>
@@ -393,8 +417,7 @@ static cudaError_t launch_world_backward_t(const TexDesc* table, int n_obj, cons
                                            const float* nrm, const int32_t* obj, int64_t F, const float* dL_dout,
                                            const GradTable& grads, bool any_grad, float* dL_duv, float* dL_ddir,
                                            float* dL_dnrm, bool accumulate, unsigned* status, cudaStream_t stream) {
-    const unsigned grid = persistent_grid(world_backward_kernel<FILTER, DET>, kBackThreads,
-                                          (F + kBackThreads - 1) / kBackThreads);
+    const unsigned grid = persistent_grid(world_backward_kernel<FILTER, DET>, kBackThreads, (F + kChunk - 1) / kChunk);
     world_backward_kernel<FILTER, DET><<<grid, kBackThreads, 0, stream>>>(
         table, n_obj, uv, dir, nrm, obj, F, dL_dout, grads, any_grad, dL_duv, dL_ddir, dL_dnrm, accumulate, status);
     return cudaGetLastError();

@@ -171,15 +171,16 @@ struct Lookup {
 
 // The lookup from B (any incidence mapping): spatial axes from (u, v) with the
 // texture's address mode, in-bucket axes from B.
-template <int FILTER>
+// WRAP = false: the caller knows that no object repeats (clamp to edge only).
+template <int FILTER, bool WRAP = true>
 __device__ __forceinline__ Lookup<FILTER> locate_from_square(const TexDesc& d, float u, float v, float2 B) {
     Lookup<FILTER> L;
     if (FILTER == RT_QUADRILINEAR) {
-        L.u = (d.wrap & 1) ? spatial_axis_bilinear_wrap(u, d.fW, d.W) : spatial_axis_bilinear(u, d.fW, d.W);
-        L.v = (d.wrap & 2) ? spatial_axis_bilinear_wrap(v, d.fH, d.H) : spatial_axis_bilinear(v, d.fH, d.H);
+        L.u = (WRAP && (d.wrap & 1)) ? spatial_axis_bilinear_wrap(u, d.fW, d.W) : spatial_axis_bilinear(u, d.fW, d.W);
+        L.v = (WRAP && (d.wrap & 2)) ? spatial_axis_bilinear_wrap(v, d.fH, d.H) : spatial_axis_bilinear(v, d.fH, d.H);
     } else {
-        L.u = (d.wrap & 1) ? spatial_axis_nearest_wrap(u, d.fW, d.W) : spatial_axis_nearest(u, d.fW, d.W);
-        L.v = (d.wrap & 2) ? spatial_axis_nearest_wrap(v, d.fH, d.H) : spatial_axis_nearest(v, d.fH, d.H);
+        L.u = (WRAP && (d.wrap & 1)) ? spatial_axis_nearest_wrap(u, d.fW, d.W) : spatial_axis_nearest(u, d.fW, d.W);
+        L.v = (WRAP && (d.wrap & 2)) ? spatial_axis_nearest_wrap(v, d.fH, d.H) : spatial_axis_nearest(v, d.fH, d.H);
     }
     L.B = B;
     if (FILTER == RT_NEAREST) {
@@ -193,9 +194,9 @@ __device__ __forceinline__ Lookup<FILTER> locate_from_square(const TexDesc& d, f
 }
 
 // Tangent-space lookup: Eq. 1b, Eq. 3, the Note's clamp.
-template <int FILTER>
+template <int FILTER, bool WRAP = true>
 __device__ __forceinline__ Lookup<FILTER> locate(const TexDesc& d, float u, float v, float Ix, float Iy, float Iz) {
-    return locate_from_square<FILTER>(d, u, v, incidence_to_square(Ix, Iy, Iz));
+    return locate_from_square<FILTER, WRAP>(d, u, v, incidence_to_square(Ix, Iy, Iz));
 }
 
 // World-space lookup: A from the first two entries of Eq. 1a, h = I + N.

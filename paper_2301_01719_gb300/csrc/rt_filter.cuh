@@ -125,6 +125,18 @@ __device__ __forceinline__ float4 filter_any(const TexDesc& d, const Lookup<FILT
     }
 }
 
+// SPEC: -1 = any objects (format, layout, palette and repeat mode dispatched
+// per fragment); a format = every object of the table is a dense PLANES
+// texture of that format in clamp mode, so the fragment code is one path
+// (the host picks the instantiation from the table).
+template <int FILTER, int SPEC>
+__device__ __forceinline__ float4 filter_spec(const TexDesc& d, const Lookup<FILTER>& L) {
+    if constexpr (SPEC < 0)
+        return filter_any<FILTER>(d, L);
+    else
+        return filter_taps<FILTER, SPEC, RT_LAYOUT_PLANES>(d, L);
+}
+
 // G-buffer staging.  Kernels that walk fragments are persistent: each warp
 // takes 32-fragment chunks c, c + (warps in the grid), ...  and double-buffers
 // them in its own slice of shared memory.  While the warp filters chunk c, the
@@ -183,17 +195,21 @@ struct Tiling {
 
 // A warp's G-buffer buffers: the chunk being processed plus STAGES - 1
 // prefetched ones.
-template <bool EXTRA, int STAGES = 2>
+// NRM adds a second three-float stream (the per-fragment normal of the
+// world-space lookup), staged like dir.
+template <bool EXTRA, int STAGES = 2, bool NRM = false>
 struct WarpStage {
     float uv[STAGES][2 * kChunk];
     float dir[STAGES][3 * kChunk];
     int obj[STAGES][kChunk];
     float4 extra[EXTRA ? STAGES : 1][EXTRA ? kChunk : 1];
+    float nrm[NRM ? STAGES : 1][NRM ? 3 * kChunk : 1];
 };
 
 struct Frag {
     float u, v, x, y, z;
     int o;
+    float nx, ny, nz;  // NRM streams only
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -252,10 +268,11 @@ __device__ __forceinline__ ChunkGeom chunk_geom(const Tiling& T, int64_t F, int6
 // Issues the copies of one chunk into buffer `b` (a chunk that is not entirely
 // inside the frame or not 16-byte aligned is read with plain bounded loads
 // instead; lanes without a fragment become background).
-template <bool EXTRA, int STAGES>
+template <bool EXTRA, int STAGES, bool NRM>
 __device__ __forceinline__ void stage_chunk(const float* __restrict__ uv, const float* __restrict__ dir,
                                             const int32_t* __restrict__ obj, const float* __restrict__ extra,
-                                            const ChunkGeom& g, int b, WarpStage<EXTRA, STAGES>& S, int lane) {
+                                            const float* __restrict__ nrm, const ChunkGeom& g, int b,
+                                            WarpStage<EXTRA, STAGES, NRM>& S, int lane) {
     if (g.fast) {
         // 24 pieces of dir, 16 of uv, 8 of obj: lanes 0-23 take dir, 16-31 uv,
         // 24-31 obj.  Shared memory holds the chunk in lane order (lane = row
@@ -264,7 +281,9 @@ __device__ __forceinline__ void stage_chunk(const float* __restrict__ uv, const 
         const int lg = g.tw_log2;
         if (lane < 24) {
             const int m = 4 * lane, k = (m / 3) >> lg;
-            cp_async16(&S.dir[b][m], dir + 3 * (g.row0 + (int64_t)k * g.pitch) + (m - 3 * (k << lg)));
+            const int64_t src = 3 * (g.row0 + (int64_t)k * g.pitch) + (m - 3 * (k << lg));
+            cp_async16(&S.dir[b][m], dir + src);
+            if (NRM) cp_async16(&S.nrm[NRM ? b : 0][NRM ? m : 0], nrm + src);
         }
         if (lane >= 16) {
             const int m = 4 * (lane - 16), k = (m >> 1) >> lg;
@@ -284,18 +303,26 @@ __device__ __forceinline__ void stage_chunk(const float* __restrict__ uv, const 
             S.dir[b][3 * lane + 1] = dir[3 * f + 1];
             S.dir[b][3 * lane + 2] = dir[3 * f + 2];
             S.obj[b][lane] = obj[f];
+            if (NRM) {
+                S.nrm[NRM ? b : 0][NRM ? 3 * lane : 0] = nrm[3 * f];
+                S.nrm[NRM ? b : 0][NRM ? 3 * lane + 1 : 0] = nrm[3 * f + 1];
+                S.nrm[NRM ? b : 0][NRM ? 3 * lane + 2 : 0] = nrm[3 * f + 2];
+            }
         } else {
             S.uv[b][2 * lane] = S.uv[b][2 * lane + 1] = 0.f;
             S.dir[b][3 * lane] = S.dir[b][3 * lane + 1] = S.dir[b][3 * lane + 2] = 0.f;
             S.obj[b][lane] = -1;
+            if (NRM)
+                S.nrm[NRM ? b : 0][NRM ? 3 * lane : 0] = S.nrm[NRM ? b : 0][NRM ? 3 * lane + 1 : 0] =
+                    S.nrm[NRM ? b : 0][NRM ? 3 * lane + 2 : 0] = 0.f;
         }
         if (EXTRA)
             S.extra[b][lane] = f >= 0 ? reinterpret_cast<const float4*>(extra)[f] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
-template <bool EXTRA, int STAGES>
-__device__ __forceinline__ Frag read_frag(const WarpStage<EXTRA, STAGES>& S, int b, int lane) {
+template <bool EXTRA, int STAGES, bool NRM>
+__device__ __forceinline__ Frag read_frag(const WarpStage<EXTRA, STAGES, NRM>& S, int b, int lane) {
     Frag r;
     float2 q = reinterpret_cast<const float2*>(S.uv[b])[lane];
     r.u = q.x;
@@ -304,6 +331,12 @@ __device__ __forceinline__ Frag read_frag(const WarpStage<EXTRA, STAGES>& S, int
     r.y = S.dir[b][3 * lane + 1];
     r.z = S.dir[b][3 * lane + 2];
     r.o = S.obj[b][lane];
+    r.nx = r.ny = r.nz = 0.f;
+    if (NRM) {
+        r.nx = S.nrm[NRM ? b : 0][NRM ? 3 * lane : 0];
+        r.ny = S.nrm[NRM ? b : 0][NRM ? 3 * lane + 1 : 0];
+        r.nz = S.nrm[NRM ? b : 0][NRM ? 3 * lane + 2 : 0];
+    }
     return r;
 }
 
@@ -318,14 +351,14 @@ __device__ __forceinline__ int64_t chunk_count(const Tiling& T, int64_t F, int w
 // chunks prefetched.  Lanes without a fragment get a background fragment and
 // f = -1: the body must not store for them.  WARPS = warps per block; the
 // block's shared memory holds WARPS stages.
-template <int WARPS, bool EXTRA, bool TILED, int STAGES, typename Body>
+template <int WARPS, bool EXTRA, bool TILED, int STAGES, bool NRM = false, typename Body>
 __device__ __forceinline__ void for_each_fragment(const float* __restrict__ uv, const float* __restrict__ dir,
                                                   const int32_t* __restrict__ obj, const float* __restrict__ extra,
-                                                  int64_t F, const Tiling& T, WarpStage<EXTRA, STAGES>* stages,
-                                                  Body body) {
+                                                  int64_t F, const Tiling& T, WarpStage<EXTRA, STAGES, NRM>* stages,
+                                                  Body body, const float* __restrict__ nrm = nullptr) {
     constexpr int kStages = STAGES;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    WarpStage<EXTRA, STAGES>& S = stages[w];
+    WarpStage<EXTRA, STAGES, NRM>& S = stages[w];
     const int64_t nchunks = chunk_count<TILED>(T, F, WARPS);
     const int64_t step = (int64_t)gridDim.x * WARPS;
     int64_t c = (int64_t)blockIdx.x * WARPS + w;
@@ -334,7 +367,7 @@ __device__ __forceinline__ void for_each_fragment(const float* __restrict__ uv, 
 #pragma unroll
     for (int k = 0; k < kStages - 1; ++k) {
         const ChunkGeom g = chunk_geom<WARPS, TILED>(T, F, c + k * step, lane);
-        if (c + k * step < nchunks) stage_chunk<EXTRA, STAGES>(uv, dir, obj, extra, g, k, S, lane);
+        if (c + k * step < nchunks) stage_chunk<EXTRA, STAGES, NRM>(uv, dir, obj, extra, nrm, g, k, S, lane);
         cp_async_commit();
         fk[k] = g.f;
     }
@@ -343,12 +376,12 @@ __device__ __forceinline__ void for_each_fragment(const float* __restrict__ uv, 
         const int64_t ahead = c + (kStages - 1) * step;
         const int bl = b + kStages - 1 >= kStages ? b - 1 : b + kStages - 1;  // (b + kStages - 1) % kStages
         const ChunkGeom g = chunk_geom<WARPS, TILED>(T, F, ahead, lane);
-        if (ahead < nchunks) stage_chunk<EXTRA, STAGES>(uv, dir, obj, extra, g, bl, S, lane);
+        if (ahead < nchunks) stage_chunk<EXTRA, STAGES, NRM>(uv, dir, obj, extra, nrm, g, bl, S, lane);
         cp_async_commit();
         fk[kStages - 1] = g.f;
         cp_async_wait<kStages - 1>();  // chunk c has landed (newer groups may still be in flight)
         __syncwarp();
-        const Frag q = read_frag<EXTRA, STAGES>(S, b, lane);
+        const Frag q = read_frag<EXTRA, STAGES, NRM>(S, b, lane);
         float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
         if (EXTRA) e = S.extra[EXTRA ? b : 0][EXTRA ? lane : 0];
         __syncwarp();  // every lane has read buffer b before it is refilled

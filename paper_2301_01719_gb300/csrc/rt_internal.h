@@ -62,14 +62,17 @@ struct GradTable {
     void* p[RT_MAX_OBJECTS];  // float* (FP32 sums) or long long* (fixed-point sums, deterministic mode)
 };
 
+// spec: the storage format shared by every object of the table (dense PLANES,
+// clamp mode), or -1; selects a single-format instantiation of the tiled kernels.
 cudaError_t launch_shade(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
-                         int64_t F, int filter, const Tiling& T, float* out, unsigned* status, cudaStream_t stream);
+                         int64_t F, int filter, const Tiling& T, int spec, float* out, unsigned* status,
+                         cudaStream_t stream);
 cudaError_t launch_locate(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
                           int64_t F, int filter, int32_t* idx, float* coord, unsigned* status, cudaStream_t stream);
 cudaError_t launch_backward(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
-                            int64_t F, int filter, const Tiling& T, const float* dL_dout, const GradTable& grads,
-                            bool any_grad, float* dL_duv, float* dL_ddir, bool accumulate, bool deterministic,
-                            unsigned* status, cudaStream_t stream);
+                            int64_t F, int filter, const Tiling& T, int spec, const float* dL_dout,
+                            const GradTable& grads, bool any_grad, float* dL_duv, float* dL_ddir, bool accumulate,
+                            bool deterministic, unsigned* status, cudaStream_t stream);
 cudaError_t launch_fixed_to_float(const long long* acc, float* dst, int64_t count, bool accumulate,
                                   cudaStream_t stream);
 

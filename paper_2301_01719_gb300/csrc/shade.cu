@@ -24,7 +24,7 @@ constexpr int kShadeWarps = kShadeThreads / 32;
 template <bool TILED>
 constexpr int shade_stages() { return TILED ? 3 : 2; }
 
-template <int FILTER, bool TILED>
+template <int FILTER, bool TILED, int SPEC>
 __global__ void __launch_bounds__(kShadeThreads, TILED ? 8 : 1) shade_kernel(const TexDesc* __restrict__ table, int n_obj,
                                                               const float* __restrict__ uv,
                                                               const float* __restrict__ dir,
@@ -37,8 +37,8 @@ __global__ void __launch_bounds__(kShadeThreads, TILED ? 8 : 1) shade_kernel(con
         float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
         TexDesc d;
         if (fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d)) {
-            Lookup<FILTER> L = locate<FILTER>(d, q.u, q.v, q.x, q.y, q.z);
-            res = filter_any<FILTER>(d, L);
+            Lookup<FILTER> L = locate<FILTER, (SPEC < 0)>(d, q.u, q.v, q.x, q.y, q.z);
+            res = filter_spec<FILTER, SPEC>(d, L);
         }
         if (f >= 0) __stcs(reinterpret_cast<float4*>(out) + f, res);
     });
@@ -69,9 +69,9 @@ __global__ void __launch_bounds__(kShadeThreads) locate_kernel(const TexDesc* __
     });
 }
 
-// World-space forward and lookup (Eq. 1a with a per-fragment normal): one
-// fragment per thread, grid-stride; the G-buffer has a fourth stream, the
-// normal, and no screen tiling.
+// World-space forward and lookup (Eq. 1a with a per-fragment normal): the
+// streamer of the tangent-space kernels with a fourth staged stream, the
+// normal, over the flat fragment stream.
 template <int FILTER>
 __global__ void __launch_bounds__(kShadeThreads) world_shade_kernel(const TexDesc* __restrict__ table, int n_obj,
                                                                     const float* __restrict__ uv,
@@ -80,30 +80,59 @@ __global__ void __launch_bounds__(kShadeThreads) world_shade_kernel(const TexDes
                                                                     const int32_t* __restrict__ obj, int64_t F,
                                                                     float* __restrict__ out, int32_t* __restrict__ idx,
                                                                     float* __restrict__ coord, unsigned* status) {
-    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
-        const float2 q = reinterpret_cast<const float2*>(uv)[f];
-        const float3 I = make_float3(dir[3 * f], dir[3 * f + 1], dir[3 * f + 2]);
-        const float3 N = make_float3(nrm[3 * f], nrm[3 * f + 1], nrm[3 * f + 2]);
+    __shared__ WarpStage<false, 2, true> stages[kShadeWarps];
+    const Tiling flat = flat_tiling();
+    for_each_fragment<kShadeWarps, false, false, 2, true>(uv, dir, obj, nullptr, F, flat, stages,
+                                                          [&](int64_t f, const Frag& q, float4) {
         float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
         int4 Ix = make_int4(0, 0, 0, 0);
         float4 C = make_float4(0.f, 0.f, 0.f, 0.f);
         TexDesc d;
-        if (fragment_valid(table, n_obj, obj[f], q.x, q.y, I.x, I.y, I.z, status, d) && normal_valid(N, status)) {
-            const Lookup<FILTER> L = locate_world<FILTER>(d, q.x, q.y, I, N);
+        const float3 N = make_float3(q.nx, q.ny, q.nz);
+        if (fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d) && normal_valid(N, status)) {
+            const Lookup<FILTER> L = locate_world<FILTER>(d, q.u, q.v, make_float3(q.x, q.y, q.z), N);
             if (out) res = filter_any<FILTER>(d, L);
             Ix = make_int4(L.u.fl, L.v.fl, L.s.fl, L.t.fl);
             C = make_float4(L.u.c, L.v.c, L.s.c, L.t.c);
         }
+        if (f < 0) return;
         if (out) __stcs(reinterpret_cast<float4*>(out) + f, res);
         if (idx) {
             reinterpret_cast<int4*>(idx)[f] = Ix;
             reinterpret_cast<float4*>(coord)[f] = C;
         }
+    }, nrm);
+}
+
+cudaError_t launch_world_shade(const TexDesc* table, int n_obj, const float* uv, const float* dir, const float* nrm,
+                               const int32_t* obj, int64_t F, int filter, float* out, int32_t* idx, float* coord,
+                               unsigned* status, cudaStream_t stream) {
+    const int64_t items = (F + kChunk - 1) / kChunk;  // chunks of the flat stream
+    switch (filter) {
+        case RT_NEAREST: {
+            const unsigned grid = persistent_grid(world_shade_kernel<RT_NEAREST>, kShadeThreads, items);
+            world_shade_kernel<RT_NEAREST><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dir, nrm, obj, F,
+                                                                               out, idx, coord, status);
+            break;
+        }
+        case RT_ANGULAR_BILINEAR: {
+            const unsigned grid = persistent_grid(world_shade_kernel<RT_ANGULAR_BILINEAR>, kShadeThreads, items);
+            world_shade_kernel<RT_ANGULAR_BILINEAR><<<grid, kShadeThreads, 0, stream>>>(
+                table, n_obj, uv, dir, nrm, obj, F, out, idx, coord, status);
+            break;
+        }
+        default: {
+            const unsigned grid = persistent_grid(world_shade_kernel<RT_QUADRILINEAR>, kShadeThreads, items);
+            world_shade_kernel<RT_QUADRILINEAR><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dir, nrm, obj,
+                                                                                    F, out, idx, coord, status);
+        }
     }
+    return cudaGetLastError();
 }
 
 // S lookups per fragment, averaged (area lights over a shadow texture, Section
 // 5: "more than one sample per bucket"): dirs holds S directions per fragment.
+// General S: one fragment per thread, the samples in a loop.
 template <int FILTER>
 __global__ void __launch_bounds__(kShadeThreads) multi_shade_kernel(const TexDesc* __restrict__ table, int n_obj,
                                                                     const float* __restrict__ uv,
@@ -132,86 +161,128 @@ __global__ void __launch_bounds__(kShadeThreads) multi_shade_kernel(const TexDes
     }
 }
 
+// S a power of two <= 32: one lookup per lane, lanes f S .. f S + S - 1 of a
+// warp share fragment f (coalesced direction loads, 32 lookups in flight per
+// warp) and sum by butterfly shuffles.
+template <int FILTER>
+__global__ void __launch_bounds__(kShadeThreads) multi_shade_lanes_kernel(const TexDesc* __restrict__ table,
+                                                                          int n_obj, const float* __restrict__ uv,
+                                                                          const float* __restrict__ dirs, int S,
+                                                                          const int32_t* __restrict__ obj, int64_t F,
+                                                                          float* __restrict__ out, unsigned* status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = F * S;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp0 * 32; base < total; base += warps * 32) {
+        const int64_t e = base + lane;
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        int bad = 0;
+        if (e < total) {
+            const int64_t f = e / S;
+            const float2 q = reinterpret_cast<const float2*>(uv)[f];
+            const float* I = dirs + 3 * e;
+            TexDesc d;
+            if (fragment_valid(table, n_obj, obj[f], q.x, q.y, I[0], I[1], I[2], status, d))
+                c = filter_any<FILTER>(d, locate<FILTER>(d, q.x, q.y, I[0], I[1], I[2]));
+            else
+                bad = obj[f] >= 0;  // an invalid sample zeroes its fragment
+        }
+        for (int off = 1; off < S; off <<= 1) {
+            c.x += __shfl_xor_sync(0xffffffffu, c.x, off);
+            c.y += __shfl_xor_sync(0xffffffffu, c.y, off);
+            c.z += __shfl_xor_sync(0xffffffffu, c.z, off);
+            c.w += __shfl_xor_sync(0xffffffffu, c.w, off);
+            bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+        }
+        if (e < total && (lane & (S - 1)) == 0) {
+            const float inv = 1.0f / (float)S;
+            const float4 r = bad ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                 : make_float4(c.x * inv, c.y * inv, c.z * inv, c.w * inv);
+            __stcs(reinterpret_cast<float4*>(out) + e / S, r);
+        }
+    }
+}
+
+template <int FILTER>
+static void launch_multi_t(const TexDesc* table, int n_obj, const float* uv, const float* dirs, int S,
+                           const int32_t* obj, int64_t F, float* out, unsigned* status, cudaStream_t stream) {
+    if (S <= 32 && (S & (S - 1)) == 0) {
+        const unsigned grid = persistent_grid(multi_shade_lanes_kernel<FILTER>, kShadeThreads, (F * S + 31) / 32);
+        multi_shade_lanes_kernel<FILTER><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dirs, S, obj, F, out,
+                                                                              status);
+    } else {
+        const unsigned grid = persistent_grid(multi_shade_kernel<FILTER>, kShadeThreads,
+                                              (F + kShadeThreads - 1) / kShadeThreads);
+        multi_shade_kernel<FILTER><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dirs, S, obj, F, out,
+                                                                        status);
+    }
+}
+
 cudaError_t launch_multi_shade(const TexDesc* table, int n_obj, const float* uv, const float* dirs, int S,
                                const int32_t* obj, int64_t F, int filter, float* out, unsigned* status,
                                cudaStream_t stream) {
-    const int64_t items = (F + kShadeThreads - 1) / kShadeThreads;
     switch (filter) {
-        case RT_NEAREST: {
-            const unsigned grid = persistent_grid(multi_shade_kernel<RT_NEAREST>, kShadeThreads, items);
-            multi_shade_kernel<RT_NEAREST><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dirs, S, obj, F,
-                                                                               out, status);
+        case RT_NEAREST:
+            launch_multi_t<RT_NEAREST>(table, n_obj, uv, dirs, S, obj, F, out, status, stream);
             break;
-        }
-        case RT_ANGULAR_BILINEAR: {
-            const unsigned grid = persistent_grid(multi_shade_kernel<RT_ANGULAR_BILINEAR>, kShadeThreads, items);
-            multi_shade_kernel<RT_ANGULAR_BILINEAR><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dirs, S,
-                                                                                        obj, F, out, status);
+        case RT_ANGULAR_BILINEAR:
+            launch_multi_t<RT_ANGULAR_BILINEAR>(table, n_obj, uv, dirs, S, obj, F, out, status, stream);
             break;
-        }
-        default: {
-            const unsigned grid = persistent_grid(multi_shade_kernel<RT_QUADRILINEAR>, kShadeThreads, items);
-            multi_shade_kernel<RT_QUADRILINEAR><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dirs, S, obj,
-                                                                                    F, out, status);
-        }
+        default:
+            launch_multi_t<RT_QUADRILINEAR>(table, n_obj, uv, dirs, S, obj, F, out, status, stream);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_world_shade(const TexDesc* table, int n_obj, const float* uv, const float* dir, const float* nrm,
-                               const int32_t* obj, int64_t F, int filter, float* out, int32_t* idx, float* coord,
-                               unsigned* status, cudaStream_t stream) {
-    const int64_t items = (F + kShadeThreads - 1) / kShadeThreads;
-    switch (filter) {
-        case RT_NEAREST: {
-            const unsigned grid = persistent_grid(world_shade_kernel<RT_NEAREST>, kShadeThreads, items);
-            world_shade_kernel<RT_NEAREST><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dir, nrm, obj, F,
-                                                                               out, idx, coord, status);
-            break;
-        }
-        case RT_ANGULAR_BILINEAR: {
-            const unsigned grid = persistent_grid(world_shade_kernel<RT_ANGULAR_BILINEAR>, kShadeThreads, items);
-            world_shade_kernel<RT_ANGULAR_BILINEAR><<<grid, kShadeThreads, 0, stream>>>(
-                table, n_obj, uv, dir, nrm, obj, F, out, idx, coord, status);
-            break;
-        }
-        default: {
-            const unsigned grid = persistent_grid(world_shade_kernel<RT_QUADRILINEAR>, kShadeThreads, items);
-            world_shade_kernel<RT_QUADRILINEAR><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dir, nrm, obj,
-                                                                                    F, out, idx, coord, status);
-        }
-    }
-    return cudaGetLastError();
-}
-
-template <int FILTER, bool TILED>
+template <int FILTER, bool TILED, int SPEC>
 static cudaError_t launch_shade_t(const TexDesc* table, int n_obj, const float* uv, const float* dir,
                                   const int32_t* obj, int64_t F, const Tiling& T, float* out, unsigned* status,
                                   cudaStream_t stream) {
-    const unsigned grid = persistent_grid(shade_kernel<FILTER, TILED>, kShadeThreads,
+    const unsigned grid = persistent_grid(shade_kernel<FILTER, TILED, SPEC>, kShadeThreads,
                                           chunk_count_host(T, F, kShadeWarps));
-    shade_kernel<FILTER, TILED><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, T, out, status);
+    shade_kernel<FILTER, TILED, SPEC><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dir, obj, F, T, out,
+                                                                          status);
     return cudaGetLastError();
 }
 
-template <bool TILED>
+template <bool TILED, int SPEC>
 static cudaError_t launch_shade_f(const TexDesc* table, int n_obj, const float* uv, const float* dir,
                                   const int32_t* obj, int64_t F, int filter, const Tiling& T, float* out,
                                   unsigned* status, cudaStream_t stream) {
     switch (filter) {
         case RT_NEAREST:
-            return launch_shade_t<RT_NEAREST, TILED>(table, n_obj, uv, dir, obj, F, T, out, status, stream);
+            return launch_shade_t<RT_NEAREST, TILED, SPEC>(table, n_obj, uv, dir, obj, F, T, out, status, stream);
         case RT_ANGULAR_BILINEAR:
-            return launch_shade_t<RT_ANGULAR_BILINEAR, TILED>(table, n_obj, uv, dir, obj, F, T, out, status, stream);
+            return launch_shade_t<RT_ANGULAR_BILINEAR, TILED, SPEC>(table, n_obj, uv, dir, obj, F, T, out, status,
+                                                                    stream);
         default:
-            return launch_shade_t<RT_QUADRILINEAR, TILED>(table, n_obj, uv, dir, obj, F, T, out, status, stream);
+            return launch_shade_t<RT_QUADRILINEAR, TILED, SPEC>(table, n_obj, uv, dir, obj, F, T, out, status,
+                                                                stream);
     }
 }
 
+// The screen-tiled path has a single-format instantiation per storage format
+// (spec = that format); everything else runs the dispatching kernels.
 cudaError_t launch_shade(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
-                         int64_t F, int filter, const Tiling& T, float* out, unsigned* status, cudaStream_t stream) {
-    if (T.W > 0) return launch_shade_f<true>(table, n_obj, uv, dir, obj, F, filter, T, out, status, stream);
-    return launch_shade_f<false>(table, n_obj, uv, dir, obj, F, filter, T, out, status, stream);
+                         int64_t F, int filter, const Tiling& T, int spec, float* out, unsigned* status,
+                         cudaStream_t stream) {
+    if (T.W > 0) {
+        switch (spec) {
+            case RT_F16:
+                return launch_shade_f<true, RT_F16>(table, n_obj, uv, dir, obj, F, filter, T, out, status, stream);
+            case RT_BF16:
+                return launch_shade_f<true, RT_BF16>(table, n_obj, uv, dir, obj, F, filter, T, out, status, stream);
+            case RT_F32:
+                return launch_shade_f<true, RT_F32>(table, n_obj, uv, dir, obj, F, filter, T, out, status, stream);
+            case RT_E4M3_BUCKET_SCALE:
+                return launch_shade_f<true, RT_E4M3_BUCKET_SCALE>(table, n_obj, uv, dir, obj, F, filter, T, out,
+                                                                  status, stream);
+            default:
+                return launch_shade_f<true, -1>(table, n_obj, uv, dir, obj, F, filter, T, out, status, stream);
+        }
+    }
+    return launch_shade_f<false, -1>(table, n_obj, uv, dir, obj, F, filter, T, out, status, stream);
 }
 
 template <int FILTER, bool TILED>
