@@ -48,19 +48,51 @@ __device__ __forceinline__ CoordGrad backward_quadrilinear_planes(const TexDesc&
                       bucket_slot<LAYOUT>(d, L.u.k1, L.v.k1)};  // (u0,v0) (u1,v0) (u0,v1) (u1,v1)
     const float wu[2] = {1.f - L.u.w, L.u.w}, wv[2] = {1.f - L.v.w, L.v.w};
     const float ws[2] = {1.f - L.s.w, L.s.w}, wt[2] = {1.f - L.t.w, L.t.w};
-    if (grad) {
+    if (DET) {
+        if (grad) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float w = wu[b & 1] * wv[b >> 1] * ws[k & 1] * wt[k >> 1];
+                    if (w == 0.f) continue;
+                    const int64_t idx = pl[k] + o[b];
+                    red_add_fixed4(static_cast<unsigned long long*>(grad) + 4 * idx,
+                                   make_float4(w * g.x, w * g.y, w * g.z, w * g.w));
+                }
+        }
+    } else {
+        // Neighbouring fragments often update the same texel through the same
+        // tap: lanes 2m and 2m + 1 (horizontal neighbours on screen) compare
+        // their tap addresses, and on a match the odd lane hands its
+        // contribution to the even lane, which issues one reduction for both.
+        const unsigned active = __activemask();
+        const int lane = threadIdx.x & 31;
+        const bool partner = (active >> (lane ^ 1)) & 1u;
 #pragma unroll
         for (int b = 0; b < 4; ++b)
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float w = wu[b & 1] * wv[b >> 1] * ws[k & 1] * wt[k >> 1];
-                if (w == 0.f) continue;
+                const float w = grad ? wu[b & 1] * wv[b >> 1] * ws[k & 1] * wt[k >> 1] : 0.f;
                 const int64_t idx = pl[k] + o[b];
-                const float4 c = make_float4(w * g.x, w * g.y, w * g.z, w * g.w);
-                if (DET)
-                    red_add_fixed4(static_cast<unsigned long long*>(grad) + 4 * idx, c);
-                else
-                    red_add_v4(static_cast<float*>(grad) + 4 * idx, c);
+                float* addr = grad ? static_cast<float*>(grad) + 4 * idx : nullptr;
+                // a lane with nothing to add gets a key no other lane has
+                const unsigned long long key =
+                    w != 0.f ? (unsigned long long)addr : (~0ull - (unsigned long long)lane);
+                float4 c = make_float4(w * g.x, w * g.y, w * g.z, w * g.w);
+                const unsigned klo = (unsigned)key, khi = (unsigned)(key >> 32);
+                const unsigned plo = __shfl_xor_sync(active, klo, 1), phi = __shfl_xor_sync(active, khi, 1);
+                const float px = __shfl_xor_sync(active, c.x, 1), py = __shfl_xor_sync(active, c.y, 1);
+                const float pz = __shfl_xor_sync(active, c.z, 1), pw = __shfl_xor_sync(active, c.w, 1);
+                const bool same = partner && plo == klo && phi == khi;
+                if (same && (lane & 1)) continue;  // handed to the even lane
+                if (same) {
+                    c.x += px;
+                    c.y += py;
+                    c.z += pz;
+                    c.w += pw;
+                }
+                if (w != 0.f) red_add_v4(addr, c);
             }
     }
     CoordGrad cg = {0.f, 0.f, 0.f, 0.f};
