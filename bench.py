@@ -166,10 +166,14 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# The sources the forward and backward shading kernels are compiled from.
+SHADING_SOURCES = ("backward.cu", "launch.h", "rt_device.cuh", "rt_filter.cuh", "rt_internal.h", "shade.cu")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2301_01719_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in SHADING_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]

@@ -116,18 +116,29 @@ __device__ __forceinline__ Ray bucket_ray(const rt_bake_scene& S, int surface, i
     return r;
 }
 
-// Texel (s, t) of the bucket: Eq. 4a and Eq. 4b give R; d = R in world space.
-__device__ __forceinline__ float4 bake_texel(const rt_bake_scene& S, const Ray& r, int s, int t, int n) {
-    const float3 R = texel_reflection(s, t, n);
+// Texel p of the bucket with tangent-space reflection vector R (Eq. 4a then
+// Eq. 4b at the texel centre, from the block's table); d = R in world space.
+__device__ __forceinline__ float4 bake_texel(const rt_bake_scene& S, const Ray& r, float3 R) {
     const float3 d = axpy(R.z, r.N, axpy(R.y, r.B, scale3(R.x, r.T)));
     const float4 tr = trace(S, r.P, d);
     return make_float4(fmaf(r.refl, tr.x, r.base.x), fmaf(r.refl, tr.y, r.base.y), fmaf(r.refl, tr.z, r.base.z),
                        tr.w);
 }
 
+// The n^2 tangent-space vectors of the in-bucket texels (Eq. 4a, then Eq. 4b or
+// Eq. 2c), computed once per block into shared memory (n <= 64: at most 48 KiB).
+template <bool REFLECT>
+__device__ __forceinline__ void texel_vector_table(float3* tab, int n) {
+    for (int p = threadIdx.x; p < n * n; p += blockDim.x)
+        tab[p] = REFLECT ? texel_reflection(p % n, p / n, n) : texel_centre_direction(p % n, p / n, n);
+    __syncthreads();
+}
+
 template <int FMT, int LAYOUT>
 __global__ void __launch_bounds__(kBakeThreads) bake_kernel(rt_bake_scene S, int surface, void* __restrict__ dst,
                                                             float* __restrict__ scale, int W, int H, int n) {
+    extern __shared__ float3 Rtab[];
+    texel_vector_table<true>(Rtab, n);
     const int64_t b = (int64_t)blockIdx.x * kBakeThreads + threadIdx.x;
     if (b >= (int64_t)W * H) return;
     const int j = (int)(b / W), i = (int)(b - (int64_t)j * W);
@@ -138,13 +149,13 @@ __global__ void __launch_bounds__(kBakeThreads) bake_kernel(rt_bake_scene S, int
     float sc = 1.0f;
     if (FMT == RT_E4M3_BUCKET_SCALE) {
         float amax = 0.0f;
-        for (int p = 0; p < planes; ++p) amax = fmaxf(amax, amax4(bake_texel(S, r, p % n, p / n, n)));
+        for (int p = 0; p < planes; ++p) amax = fmaxf(amax, amax4(bake_texel(S, r, Rtab[p])));
         sc = bucket_scale(amax);
         scale[b] = sc;
     }
     for (int p = p0; p < p1; ++p) {
         const int t = p / n, s = p - t * n;
-        const float4 v = bake_texel(S, r, s, t, n);
+        const float4 v = bake_texel(S, r, Rtab[p]);
         const int64_t idx = index_in(LAYOUT, W, H, n, i, j, s, t);
         if (FMT == RT_F32)
             reinterpret_cast<float4*>(dst)[idx] = v;
@@ -172,7 +183,8 @@ static cudaError_t launch_bake_t(const rt_bake_scene& S, int surface, void* dst,
         if ((int64_t)gx < want) gy = (unsigned)((want + gx - 1) / gx);
         if (gy > (unsigned)(n * n)) gy = (unsigned)(n * n);
     }
-    bake_kernel<FMT, LAYOUT><<<dim3(gx, gy), kBakeThreads, 0, stream>>>(S, surface, dst, scale, W, H, n);
+    const size_t smem = sizeof(float3) * (size_t)n * n;
+    bake_kernel<FMT, LAYOUT><<<dim3(gx, gy), kBakeThreads, smem, stream>>>(S, surface, dst, scale, W, H, n);
     return cudaGetLastError();
 }
 
@@ -256,8 +268,39 @@ __global__ void __launch_bounds__(kBakeThreads) shadow_bake_kernel(rt_bake_scene
     dst[w] = word;
 }
 
+// w h a multiple of 32: a warp takes 32 consecutive buckets (one 32-bit word
+// of every plane), computes each bucket's frame once, and forms every plane's
+// word with a ballot of the lanes' visibility bits.
+__global__ void __launch_bounds__(kBakeThreads) shadow_bake_ballot_kernel(rt_bake_scene S, int surface,
+                                                                          unsigned* __restrict__ dst, int W, int H,
+                                                                          int n) {
+    extern __shared__ float3 Dtab[];
+    texel_vector_table<false>(Dtab, n);
+    const int64_t plane = (int64_t)W * H;
+    const int64_t b = (int64_t)blockIdx.x * kBakeThreads + threadIdx.x;  // plane % 32 == 0: warps stay in range
+    if (b - (threadIdx.x & 31) >= plane) return;                        // whole warps only
+    const int lane = threadIdx.x & 31;
+    const bool valid = b < plane;
+    float3 P, T, B, N;
+    const int j = valid ? (int)(b / W) : 0, i = valid ? (int)(b - (int64_t)j * W) : 0;
+    bucket_frame(S, surface, i, j, W, H, P, T, B, N);
+    for (int p = 0; p < n * n; ++p) {
+        const float3 I = Dtab[p];
+        const float3 d = axpy(I.z, N, axpy(I.y, B, scale3(I.x, T)));
+        const unsigned word = __ballot_sync(0xffffffffu, valid && !occluded(S, P, d));
+        if (lane == 0) dst[(p * plane + b) >> 5] = word;
+    }
+}
+
 cudaError_t launch_bake_shadow(const rt_bake_scene& S, int surface, void* dst, int W, int H, int n,
                                cudaStream_t stream) {
+    const int64_t plane = (int64_t)W * H;
+    if (plane % 32 == 0) {
+        const size_t smem = sizeof(float3) * (size_t)n * n;
+        shadow_bake_ballot_kernel<<<(unsigned)((plane + kBakeThreads - 1) / kBakeThreads), kBakeThreads, smem,
+                                    stream>>>(S, surface, static_cast<unsigned*>(dst), W, H, n);
+        return cudaGetLastError();
+    }
     const int64_t words = ((int64_t)W * H * n * n + 31) / 32;
     shadow_bake_kernel<<<(unsigned)((words + kBakeThreads - 1) / kBakeThreads), kBakeThreads, 0, stream>>>(
         S, surface, static_cast<unsigned*>(dst), W, H, n);

@@ -38,7 +38,7 @@ __device__ __forceinline__ float dot4f(float4 a, float4 b) {
 }
 
 template <int FMT, int LAYOUT>
-__global__ void __launch_bounds__(kAThreads) kmeans_assign_kernel(TexDesc d, int K, const float4* __restrict__ C,
+__global__ void __launch_bounds__(kAThreads, 2) kmeans_assign_kernel(TexDesc d, int K, const float4* __restrict__ C,
                                                                   uint32_t* __restrict__ index,
                                                                   float* __restrict__ dist) {
     __shared__ float4 Xs[kAP][kAM];
@@ -96,18 +96,15 @@ __global__ void __launch_bounds__(kAThreads) kmeans_assign_kernel(TexDesc d, int
             __syncthreads();
 #pragma unroll
             for (int q = 0; q < kAP; ++q) {
-                float4 x[8], c[4];
-#pragma unroll
-                for (int r = 0; r < 8; ++r) x[r] = Xs[q][ty * 8 + r];
+                float4 c[4];
 #pragma unroll
                 for (int cc = 0; cc < 4; ++cc) c[cc] = Cs[q][tx + 16 * cc];
 #pragma unroll
-                for (int r = 0; r < 8; ++r)
+                for (int r = 0; r < 8; ++r) {
+                    const float4 x = Xs[q][ty * 8 + r];
 #pragma unroll
-                    for (int cc = 0; cc < 4; ++cc) acc[r][cc] += dot4f(x[r], c[cc]);
-                if (k0 == 0 && tx == 0) {
-#pragma unroll
-                    for (int r = 0; r < 8; ++r) xn[r] += dot4f(x[r], x[r]);
+                    for (int cc = 0; cc < 4; ++cc) acc[r][cc] += dot4f(x, c[cc]);
+                    if (k0 == 0 && tx == 0) xn[r] += dot4f(x, x);
                 }
             }
         }
