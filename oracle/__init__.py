@@ -32,24 +32,36 @@ _lib = None
 _CODE_DTYPE = {F32: np.float32, F16: np.uint16, BF16: np.uint16, E4M3: np.uint8, F64: np.float64, BIT1: np.uint8}
 
 
+# The mutation tests point the package at a deliberately broken build of the
+# oracle through this variable, to check that the pins catch each mistake.
+_OVERRIDE = os.environ.get("RADTEX_ORACLE_LIB")
+
+
+def compile_oracle(src: str, out: str) -> str:
+    """gcc -std=c11 -O2, FP contraction off, OpenMP: src -> shared library out."""
+    tmp = out + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC",
+           "-Wall", "-Wextra", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (C11, FP contraction off, OpenMP)."""
+    if _OVERRIDE:
+        return _OVERRIDE
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
-    tmp = _LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC",
-           "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    return compile_oracle(_SRC, _LIB)
 
 
 def lib() -> ctypes.CDLL:
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = ctypes.CDLL(_LIB)
+            path = build()
+            L = ctypes.CDLL(path)
             P, I32, I64, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
             sig = {
                 "oracle_equisolid": (None, [I64, P, P]),

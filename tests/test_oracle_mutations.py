@@ -1,0 +1,68 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of the oracle's C source: a sign, an
+index, a swapped operand, an off-by-half-texel centre, a missing clamp, a
+wrong tie rule, a wrong constant.  The copy is built on the CPU, and the pin
+files that cover that part of the oracle run against it in a subprocess.  At
+least one pin must fail; a mutant that passes every pin would mean its part
+of the oracle is not pinned."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "radtex_oracle.c")
+
+PINS = "tests/test_oracle_pins.py"
+BAKE = "tests/test_oracle_bake.py"
+PALETTE = "tests/test_oracle_palette.py"
+WORLD = "tests/test_oracle_world.py"
+SHADOW = "tests/test_oracle_shadow.py"
+
+# (name, original text, mutated text, pin files expected to catch it)
+MUTATIONS = [
+    ("eq1b_sign", "double zp = I[2] + 1.0;", "double zp = I[2] - 1.0;", [PINS]),
+    ("eq3_inverted_ratio", "B[0] = A[0] * r / m;", "B[0] = A[0] * m / r;", [PINS]),
+    ("texel_centre_half_off", "return (2.0 * (double)k + 1.0) / (double)n - 1.0;",
+     "return (2.0 * (double)k) / (double)n - 1.0;", [PINS]),
+    ("spatial_half_texel", "double c = x * (double)size - 0.5;", "double c = x * (double)size;", [PINS]),
+    ("missing_note_clamp", "double lo = 1.0 / (double)n - 1.0, hi = 1.0 - 1.0 / (double)n;",
+     "double lo = -1.0, hi = 1.0;", [PINS]),
+    ("atlas_s_t_swapped", "int64_t X = i * T->n + s, Y = j * T->n + t;",
+     "int64_t X = i * T->n + t, Y = j * T->n + s;", [PINS]),
+    ("e4m3_wrong_max", "amax / 448.0f", "amax / 240.0f", [PINS]),
+    ("grad_wrong_index", "gu += dw[a] * L.v.w[b]", "gu += dw[b] * L.v.w[b]", [PINS]),
+    ("eq4b_sign", "R[2] = 1.0 - a2;", "R[2] = a2 - 1.0;", [PINS, BAKE]),
+    ("bake_fog", "double f = exp(-S[BK_FOG] * t_best);", "double f = exp(-0.5 * S[BK_FOG] * t_best);", [BAKE]),
+    ("bake_sun_exponent", "double sun = c > 0.0 ? pow(c, S[BK_SUN_EXP]) : 0.0;",
+     "double sun = c > 0.0 ? pow(c, S[BK_SUN_EXP] + 1.0) : 0.0;", [BAKE]),
+    ("kmeans_tie_to_higher", "if (acc < best) {", "if (acc <= best) {", [PALETTE]),
+    ("palette_index_transposed", "int64_t k = index[j * W + i];", "int64_t k = index[(i * H + j) % (W * H)];",
+     [PALETTE]),
+    ("shadow_shrunk_occluder", "if (m2 < r * r && tc - sqrt(r * r - m2) > eps) return 1;",
+     "if (m2 < 0.81 * r * r && tc - sqrt(r * r - m2) > eps) return 1;", [SHADOW]),
+    ("shadow_plane_sign", "if (d[1] != 0.0 && (S[BK_PLANE_Y] - P[1]) / d[1] > eps) return 1;",
+     "if (d[1] != 0.0 && (P[1] - S[BK_PLANE_Y]) / d[1] > eps) return 1;", [SHADOW]),
+    ("eq1a_minus_normal", "double h[3] = {I[0] + N[0], I[1] + N[1], I[2] + N[2]};",
+     "double h[3] = {I[0] - N[0], I[1] - N[1], I[2] + N[2]};", [PINS, WORLD]),
+    ("repeat_negative_modulo", "return r < 0 ? r + size : r;", "return r < 0 ? -r : r;", [WORLD]),
+]
+
+
+@pytest.mark.parametrize("name,old,new,files", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_the_mutation(tmp_path, name, old, new, files):
+    text = open(SRC).read()
+    assert text.count(old) >= 1, f"{name}: the original text is not in the oracle"
+    mutated = text.replace(old, new, 1)
+    src = tmp_path / "mutant.c"
+    src.write_text(mutated)
+    lib = oracle.compile_oracle(str(src), str(tmp_path / "libmutant.so"))
+    env = dict(os.environ, RADTEX_ORACLE_LIB=lib)
+    run = subprocess.run([sys.executable, "-m", "pytest", *files, "-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider"],
+                         cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert run.returncode == 1 and " failed" in run.stdout, (
+        f"mutation {name} was not caught by {files}:\n{run.stdout[-1500:]}\n{run.stderr[-500:]}")

@@ -550,3 +550,23 @@ def test_quantisation_error_bounds(orc, fmt, rel):
     q, _ = orc.shade([T], uv, d, np.zeros(F, np.int32), 2)
     x, _ = orc.shade([orc.Texture(W, H, n, orc.F64, atlas.astype(np.float64))], uv, d, np.zeros(F, np.int32), 2)
     assert np.max(np.abs(q - x)) <= err.max() + 1e-15
+
+
+def test_note_clamp_keeps_lookups_inside_the_texel_centres(orc):
+    """The Note after Eq. 3 clamps B to [1/n - 1, 1 - 1/n], the first and last
+    texel centres: the in-bucket coordinate of every direction lies in [0, n-1]
+    (bilinear) or [1/2, n - 1/2] (nearest), and grazing directions, whose B
+    reaches the edge of the square, land exactly on the outer centre."""
+    n = 8
+    T = orc.Texture(2, 2, n, orc.F64, np.zeros((2 * n, 2 * n, 4)))
+    rng = np.random.default_rng(40)
+    d = unit_dirs(rng, 2000, lower=True).astype(np.float32)
+    phi = rng.uniform(0, 2 * np.pi, 200)
+    d[:200] = np.stack([np.cos(phi), np.sin(phi), np.zeros(200)], 1)  # on the horizon: |B|_inf = 1
+    uv = np.full((2000, 2), 0.5, np.float32)
+    obj = np.zeros(2000, np.int32)
+    for filt, lo, hi in ((1, 0.0, n - 1.0), (0, 0.5, n - 0.5)):
+        idx, c, _ = orc.locate([T], uv, d, obj, filt)
+        assert (c[:, 2:] >= lo).all() and (c[:, 2:] <= hi).all()
+        edge = np.abs(c[:200, 2:] - np.where(c[:200, 2:] > n / 2, hi, lo)).min(axis=1)
+        assert (edge == 0).all()
