@@ -62,6 +62,8 @@ def parse_args(argv=None):
     p.add_argument("--palette", type=int, default=0,
                    help="sphere-plane: compress each texture to a K-bucket palette (k-means) before timing")
     p.add_argument("--palette-iters", type=int, default=4, help="Lloyd steps of the palette encoder")
+    p.add_argument("--palette-fp32", action="store_true",
+                   help="palette encoder: assign on the CUDA cores in FP32 instead of the tensor cores")
     p.add_argument("--mem-fraction", type=float, default=0.7,
                    help="voronoi64: largest share of free device memory the textures may take")
     return p.parse_args(argv)
@@ -118,16 +120,23 @@ def encode_palettes(a, api, ctx, oids, uv, dirs, obj, dev, h_obj):
     for k, oid in enumerate(oids):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        C, index, e = api.palette_encode(ctx, oid, K, a.palette_iters, seed=k)
+        tc = not a.palette_fp32
+        C, index, e = api.palette_encode(ctx, oid, K, a.palette_iters, seed=k, tensor_cores=tc)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
         sse.append(e)
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record()
-        api.rt_kmeans_assign(ctx, oid, K, C, index)
-        s1.record()
-        torch.cuda.synchronize()
+        scratch = api.TcScratch(api.rt_kmeans_tc_scratch_bytes(a.buckets, a.buckets, a.n, K), dev) if tc else None
+        for rep_ in range(2):  # warm, then timed
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            if tc:
+                api.rt_kmeans_assign_tc(ctx, oid, K, C, index, scratch=scratch)
+            else:
+                api.rt_kmeans_assign(ctx, oid, K, C, index)
+            s1.record()
+            torch.cuda.synchronize()
         assign_ms.append(s0.elapsed_time(s1))
+        del scratch
         pid = api.rt_create_palette_texture(ctx, a.buckets, a.buckets, a.n, K, api.FORMAT_NAMES[a.storage],
                                             api.RT_LAYOUT_PLANES, C, index)
         new_ids.append(pid)
@@ -147,6 +156,7 @@ def encode_palettes(a, api, ctx, oids, uv, dirs, obj, dev, h_obj):
     info = {"K": K, "iterations": a.palette_iters, "encode_s": [round(t, 3) for t in times],
             "sse_first_last": [[x[0], x[-1]] for x in sse],
             "assign_ms": ms, "assign_tflops": 2.0 * B * K * D / (ms * 1e-3) / 1e12,
+            "assign_path": "CUDA cores, FP32" if a.palette_fp32 else "tensor cores (tcgen05, FP16 operands, FP32 accumulation; includes the FP16 operand conversion)",
             "texture_bytes": int(sum(api.rt_texture_info(ctx, p)["bytes"] for p in new_ids)),
             "psnr_vs_dense_db": float(10 * np.log10(1.0 / mse)) if mse > 0 else None}
     return info, new_ids

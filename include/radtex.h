@@ -181,6 +181,20 @@ rt_status rt_palette_size(rt_ctx* ctx, int32_t obj_id, int32_t* K);
  * rt_kmeans_update: c_k = mean of the x_b with index[b] = k, summed in FP64.
  * A centroid with no member keeps its value.  scratch: device uint32,
  * w h + 3 K + 1 entries. */
+/* rt_kmeans_assign on the tensor cores: the distance contraction x_b . c_k is
+ * a dense FP16 GEMM (tcgen05.mma, FP32 accumulation in tensor memory, TMA
+ * operand staging) and the argmin is taken in its epilogue.  The bucket
+ * vectors and centroids are rounded to FP16 (exact for FP16 textures), |c_k|^2
+ * and |x_b|^2 are summed in FP32 from those values, so a chosen centroid is a
+ * nearest one up to about 2^-10 (|x|^2 + |c|^2).  scratch: device,
+ * 1024-byte aligned, at least rt_kmeans_tc_scratch_bytes(w, h, n, K) bytes
+ * (the FP16 operands and the norms).  Ties go to the lower k.  Asynchronous;
+ * allocates nothing; RT_ERR_UNSUPPORTED when the driver lacks tensor-map
+ * encoding; a stalled pipeline raises RT_ERR_TIMEOUT in rt_get_error. */
+int64_t rt_kmeans_tc_scratch_bytes(int32_t w, int32_t h, int32_t n, int32_t K);
+rt_status rt_kmeans_assign_tc(rt_ctx* ctx, int32_t obj_id, int32_t K, const float* centroids, uint32_t* index,
+                              float* dist, void* scratch, int64_t scratch_bytes, rt_stream_t stream);
+
 rt_status rt_kmeans_init(rt_ctx* ctx, int32_t obj_id, int32_t K, const int32_t* buckets, float* centroids,
                          rt_stream_t stream);
 rt_status rt_kmeans_assign(rt_ctx* ctx, int32_t obj_id, int32_t K, const float* centroids, uint32_t* index,

@@ -66,6 +66,8 @@ SIGNATURES = {
     "rt_create_palette_texture": (_I32, [_P, _I32, _I32, _I32, _I32, _I32, _I32, _P, _P, _I32, _P]),
     "rt_palette_size": (_I32, [_P, _I32, _P]),
     "rt_kmeans_init": (_I32, [_P, _I32, _I32, _P, _P, _P]),
+    "rt_kmeans_tc_scratch_bytes": (_I64, [_I32, _I32, _I32, _I32]),
+    "rt_kmeans_assign_tc": (_I32, [_P, _I32, _I32, _P, _P, _P, _P, _I64, _P]),
     "rt_kmeans_assign": (_I32, [_P, _I32, _I32, _P, _P, _P, _P]),
     "rt_kmeans_update": (_I32, [_P, _I32, _I32, _P, _P, _P, _P]),
     "rt_shade": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, _P]),
@@ -104,7 +106,7 @@ def header_symbols() -> list[str]:
     """Every function the public header declares."""
     with open(HEADER) as fh:
         text = fh.read()
-    return sorted(set(re.findall(r"^\s*(?:rt_status|void|const char\*)\s+(rt_\w+)\s*\(", text, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:rt_status|void|int64_t|const char\*)\s+(rt_\w+)\s*\(", text, flags=re.M)))
 
 
 def lib() -> ctypes.CDLL:

@@ -145,6 +145,39 @@ def rt_kmeans_assign(ctx: Context, obj_id: int, K: int, centroids: torch.Tensor,
     return (index, dist) if want_dist else index
 
 
+class TcScratch:
+    """Device scratch of rt_kmeans_assign_tc, 1024-byte aligned."""
+
+    def __init__(self, nbytes: int, device):
+        self.buf = torch.empty(nbytes + 1024, dtype=torch.uint8, device=device)
+        self.ptr = (self.buf.data_ptr() + 1023) & ~1023
+        self.nbytes = nbytes
+
+
+def rt_kmeans_tc_scratch_bytes(w: int, h: int, n: int, K: int) -> int:
+    return int(_lib.lib().rt_kmeans_tc_scratch_bytes(int(w), int(h), int(n), int(K)))
+
+
+def rt_kmeans_assign_tc(ctx: Context, obj_id: int, K: int, centroids: torch.Tensor, index: torch.Tensor | None = None,
+                        dist: torch.Tensor | None = None, want_dist: bool = False, scratch: TcScratch | None = None,
+                        stream=None):
+    """rt_kmeans_assign on the tensor cores (FP16 operands, FP32 accumulation)."""
+    info = rt_texture_info(ctx, obj_id)
+    _check(centroids, "centroids", torch.float32, 4)
+    if centroids.numel() != K * info["n"] ** 2 * 4:
+        raise ValueError("centroids must hold K x n x n x 4 values")
+    dev = centroids.device
+    if index is None:
+        index = torch.empty((info["h"], info["w"]), dtype=torch.int32, device=dev)
+    if want_dist and dist is None:
+        dist = torch.empty((info["h"], info["w"]), dtype=torch.float32, device=dev)
+    if scratch is None:
+        scratch = TcScratch(rt_kmeans_tc_scratch_bytes(info["w"], info["h"], info["n"], K), dev)
+    _lib.call("rt_kmeans_assign_tc", ctx.handle, int(obj_id), int(K), _ptr(centroids), _ptr(index), _ptr(dist),
+              ctypes.c_void_p(scratch.ptr), int(scratch.nbytes), _stream(stream, dev))
+    return (index, dist) if want_dist else index
+
+
 def rt_kmeans_update(ctx: Context, obj_id: int, K: int, index: torch.Tensor, centroids: torch.Tensor,
                      scratch: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """Centroids <- means of their members (in place); empty centroids are kept."""
@@ -162,7 +195,8 @@ def rt_kmeans_update(ctx: Context, obj_id: int, K: int, index: torch.Tensor, cen
     return centroids
 
 
-def palette_encode(ctx: Context, obj_id: int, K: int, iterations: int, seed: int = 0, stream=None):
+def palette_encode(ctx: Context, obj_id: int, K: int, iterations: int, seed: int = 0, stream=None,
+                   tensor_cores: bool = False):
     """k-means palette of a dense texture: K centroids seeded at K distinct random
     buckets, `iterations` Lloyd steps.  Returns (centroids (n, n, K, 4), index (h, w),
     per-step sums of squared distances)."""
@@ -177,11 +211,19 @@ def palette_encode(ctx: Context, obj_id: int, K: int, iterations: int, seed: int
     index = torch.empty((info["h"], info["w"]), dtype=torch.int32, device=dev)
     dist = torch.empty((info["h"], info["w"]), dtype=torch.float32, device=dev)
     sse = []
+    tc = TcScratch(rt_kmeans_tc_scratch_bytes(info["w"], info["h"], info["n"], K), dev) if tensor_cores else None
+
+    def assign():
+        if tensor_cores:
+            rt_kmeans_assign_tc(ctx, obj_id, K, C, index, dist, scratch=tc, stream=stream)
+        else:
+            rt_kmeans_assign(ctx, obj_id, K, C, index, dist, stream=stream)
+
     for _ in range(iterations):
-        rt_kmeans_assign(ctx, obj_id, K, C, index, dist, stream=stream)
+        assign()
         sse.append(dist.double().sum())
         rt_kmeans_update(ctx, obj_id, K, index, C, scratch, stream=stream)
-    rt_kmeans_assign(ctx, obj_id, K, C, index, dist, stream=stream)
+    assign()
     sse.append(dist.double().sum())
     return C, index, [float(x) for x in sse]
 

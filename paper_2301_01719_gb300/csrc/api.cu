@@ -454,6 +454,25 @@ rt_status rt_kmeans_assign(rt_ctx* ctx, int32_t obj_id, int32_t K, const float* 
     return cuda_status(rt::launch_kmeans_assign(ctx->table[obj_id], K, centroids, index, dist, (cudaStream_t)stream));
 }
 
+int64_t rt_kmeans_tc_scratch_bytes(int32_t w, int32_t h, int32_t n, int32_t K) {
+    if (w < 1 || h < 1 || n < 1 || n > 64 || K < 1) return -1;
+    return rt::kmeans_tc_scratch_bytes(w, h, n, K);
+}
+
+rt_status rt_kmeans_assign_tc(rt_ctx* ctx, int32_t obj_id, int32_t K, const float* centroids, uint32_t* index,
+                              float* dist, void* scratch, int64_t scratch_bytes, rt_stream_t stream) {
+    if (!kmeans_source(ctx, obj_id, K) || !centroids || !aligned16(centroids) || !index || !scratch ||
+        (reinterpret_cast<uintptr_t>(scratch) & 1023u) != 0)
+        return RT_ERR_INVALID_ARG;
+    const TexDesc& d = ctx->table[obj_id];
+    if (scratch_bytes < rt::kmeans_tc_scratch_bytes(d.W, d.H, d.n, K)) return RT_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    cudaError_t e = rt::launch_kmeans_assign_tc(d, K, centroids, index, dist, scratch, ctx->d_status,
+                                                (cudaStream_t)stream);
+    return e == cudaErrorNotSupported ? RT_ERR_UNSUPPORTED : cuda_status(e);
+}
+
 rt_status rt_kmeans_update(rt_ctx* ctx, int32_t obj_id, int32_t K, const uint32_t* index, float* centroids,
                            uint32_t* scratch, rt_stream_t stream) {
     if (!kmeans_source(ctx, obj_id, K) || !index || !centroids || !aligned16(centroids) || !scratch)

@@ -226,3 +226,30 @@ def test_palette_encode_full_size_sampled(ctx):
     tau = 2.0 ** -14 * ((X ** 2).sum(1) + (Cr ** 2).sum(1)[gi])
     assert np.all(dall[np.arange(len(sample)), gi] <= od + tau)
     api.rt_destroy_texture(ctx, oid)
+
+
+@pytest.mark.parametrize("shape", [(53, 37, 4, 300), (40, 20, 16, 70), (17, 9, 3, 5)])
+def test_kmeans_tensor_core_assign_matches_oracle(ctx, shape):
+    """The tcgen05 assignment (FP16 operands, FP32 accumulation in tensor memory):
+    every choice is a nearest centroid in FP64 up to the FP16 rounding of the
+    operands, 2^-9 (|x|^2 + |c|^2); it agrees with the FP32 kernel on almost
+    every bucket.  Shapes: two 256-centroid tiles with a ragged bucket tile; 16
+    K-chunks; a vector length (3^2 x 4 = 36) padded to 64."""
+    W, H, n, K = shape
+    oid, X = dense_texture(ctx, W, H, n, api.RT_F16, 62)
+    B = W * H
+    pick = np.random.default_rng(9).choice(B, K, replace=False).astype(np.int32)
+    C = api.rt_kmeans_init(ctx, oid, K, to_dev(pick))
+    ti, td = api.rt_kmeans_assign_tc(ctx, oid, K, C, want_dist=True)
+    assert api.rt_get_error(ctx) == api.RT_OK
+    fi = api.rt_kmeans_assign(ctx, oid, K, C)
+    gi = ti.cpu().numpy().reshape(-1).astype(np.int64)
+    gd = td.cpu().numpy().reshape(-1).astype(np.float64)
+    Cr = centroid_rows(C, K, n)
+    _, od, dall = oracle.kmeans_assign(X, Cr, all_distances=True)
+    assert gi.min() >= 0 and gi.max() < K
+    tau = 2.0 ** -9 * ((X ** 2).sum(1) + (Cr ** 2).sum(1)[gi])
+    assert np.all(dall[np.arange(B), gi] <= od + tau)
+    assert np.all(np.abs(gd - dall[np.arange(B), gi]) <= tau)
+    assert (gi == fi.cpu().numpy().reshape(-1)).mean() > 0.95
+    api.rt_destroy_texture(ctx, oid)
