@@ -196,10 +196,11 @@ def rt_kmeans_update(ctx: Context, obj_id: int, K: int, index: torch.Tensor, cen
 
 
 def palette_encode(ctx: Context, obj_id: int, K: int, iterations: int, seed: int = 0, stream=None,
-                   tensor_cores: bool = False):
+                   tensor_cores: bool = True):
     """k-means palette of a dense texture: K centroids seeded at K distinct random
-    buckets, `iterations` Lloyd steps.  Returns (centroids (n, n, K, 4), index (h, w),
-    per-step sums of squared distances)."""
+    buckets, `iterations` Lloyd steps, assignments on the tensor cores (FP16
+    operands) unless tensor_cores is False (FP32 on the CUDA cores).  Returns
+    (centroids (n, n, K, 4), index (h, w), per-step sums of squared distances)."""
     import numpy as np
 
     info = rt_texture_info(ctx, obj_id)

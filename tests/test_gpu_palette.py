@@ -206,8 +206,9 @@ def test_palette_rejects_bad_index(ctx):
 
 def test_palette_encode_full_size_sampled(ctx):
     """k-means on the 1024^2 x 16^2 FP16 lobe texture of the sphere-plane workload
-    (K = 256, 3 Lloyd steps): the error falls, and 1500 sampled buckets are
-    assigned to a nearest centroid in FP64 up to the FP32 bound."""
+    (K = 256, 3 Lloyd steps, assignments on the tensor cores): the error falls,
+    and 1500 sampled buckets are assigned to a nearest centroid in FP64 up to
+    the FP16 operand bound."""
     W = H = 1024
     n, K = 16, 256
     oid = api.rt_create_texture(ctx, W, H, n, api.RT_F16)
@@ -223,7 +224,7 @@ def test_palette_encode_full_size_sampled(ctx):
     Cr = centroid_rows(C, K, n)
     gi = index.reshape(-1)[st].cpu().numpy().astype(np.int64)
     _, od, dall = oracle.kmeans_assign(X, Cr, all_distances=True)
-    tau = 2.0 ** -14 * ((X ** 2).sum(1) + (Cr ** 2).sum(1)[gi])
+    tau = 2.0 ** -9 * ((X ** 2).sum(1) + (Cr ** 2).sum(1)[gi])
     assert np.all(dall[np.arange(len(sample)), gi] <= od + tau)
     api.rt_destroy_texture(ctx, oid)
 
