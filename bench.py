@@ -513,15 +513,16 @@ def run_radtex(a):
         chunk = max(1, a.e2e_chunk)
         bounds = [(v, min(a.views, v + chunk)) for v in range(0, a.views, chunk)]
 
+        consumed = [None] * len(bounds)  # the last step's kernels are done with chunk j's inputs
+
         def e2e_step():
             comp = torch.cuda.current_stream(dev)
             for t in dtex.values():
                 t.zero_()
-            zeroed = torch.cuda.Event()
-            zeroed.record(comp)
-            done_out = []
-            for lo, hi in bounds:
+            for j, (lo, hi) in enumerate(bounds):
                 with torch.cuda.stream(s_in):
+                    if consumed[j] is not None:
+                        s_in.wait_event(consumed[j])  # do not overwrite inputs still being read
                     d_uv[lo:hi].copy_(hv_uv[lo:hi], non_blocking=True)
                     d_dir[lo:hi].copy_(hv_dir[lo:hi], non_blocking=True)
                     d_obj[lo:hi].copy_(hv_obj[lo:hi], non_blocking=True)
@@ -533,6 +534,7 @@ def run_radtex(a):
                                               dtex, duv[lo:hi], ddir[lo:hi], api.RT_ACCUMULATE)
                 shaded = torch.cuda.Event()
                 shaded.record(comp)
+                consumed[j] = shaded
                 with torch.cuda.stream(s_out):
                     s_out.wait_event(shaded)
                     h_out[lo:hi].copy_(out[lo:hi], non_blocking=True)
