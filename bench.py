@@ -449,6 +449,11 @@ def run_radtex(a):
     stream = torch.cuda.current_stream(dev)
     # screen tile of the batched kernels, picked by the library's autotuner on this workload
     tile, tile_ms = api.rt_autotune(ctx, uv, dirs, obj, filt, out, reps=3)
+    # and of the backward, timed as the step runs it (the gradients it leaves are cleared by every step)
+    for t in dtex.values():
+        t.zero_()
+    btile, btile_ms = api.rt_autotune_backward(ctx, uv, dirs, obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE,
+                                               reps=2)
 
     def step():
         api.rt_shade_batched(ctx, uv, dirs, obj, filt, out)
@@ -583,6 +588,8 @@ def run_radtex(a):
                    "step": ("rt_shade_batched + zero texel grads + rt_shade_batched_backward(RT_ACCUMULATE, "
                             "dL/dout = out)"),
                    "tile": {"tw": tile[0], "th": tile[1], "bx": tile[2], "by": tile[3], "autotune_ms": tile_ms},
+                   "backward_tile": {"tw": btile[0], "th": btile[1], "bx": btile[2], "by": btile[3],
+                                     "autotune_ms": btile_ms},
                    "distinct_texels_per_step": int(distinct), "scene_gen_s": round(scene_s, 2),
                    "palette": palette},
         "fwd_gfrag_s": F / (fwd_ms * 1e-3) / 1e9, "bwd_gfrag_s": F / (bwd_ms * 1e-3) / 1e9,

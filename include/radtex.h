@@ -357,14 +357,20 @@ rt_status rt_shade_batched_backward(rt_ctx* ctx, const float* uv, const float* d
                                     float* const* dL_dtex, int32_t n_dtex, float* dL_duv, float* dL_ddir,
                                     int32_t flags, rt_stream_t stream);
 
-/* Sets the screen tile of the batched kernels for `filter`: warp tiles of
- * tw x th fragments (tw * th = 32, tw a multiple of 4) arranged bx x by in a
- * block tile (bx * by = 4).  The default is 8 x 4, 2 x 2.  RT_ERR_INVALID_ARG
- * for other shapes.  Not a device call. */
+/* Sets the screen tile of the batched kernels for `filter`, forward and
+ * backward: warp tiles of tw x th fragments (tw * th = 32, tw a multiple of 4)
+ * arranged bx x by in a block tile (bx * by = 4).  The default is 8 x 4,
+ * 2 x 2.  RT_ERR_INVALID_ARG for other shapes.  Not a device call. */
 rt_status rt_set_tile(rt_ctx* ctx, rt_filter filter, int32_t tw, int32_t th, int32_t bx, int32_t by);
 
-/* The current tile of `filter`: tile4 = (tw, th, bx, by) (host, 4 ints). */
+/* As rt_set_tile, for the backward (rt_shade_batched_backward) only. */
+rt_status rt_set_backward_tile(rt_ctx* ctx, rt_filter filter, int32_t tw, int32_t th, int32_t bx, int32_t by);
+
+/* The current forward tile of `filter`: tile4 = (tw, th, bx, by) (host, 4 ints). */
 rt_status rt_get_tile(rt_ctx* ctx, rt_filter filter, int32_t* tile4);
+
+/* The current backward tile of `filter`, as rt_get_tile. */
+rt_status rt_get_backward_tile(rt_ctx* ctx, rt_filter filter, int32_t* tile4);
 
 /* Autotuner: times rt_shade_batched with each of the twelve tile shapes
  * (tw, th) in {32x1, 16x2, 8x4, 4x8} x (bx, by) in {4x1, 2x2, 1x4}, `reps`
@@ -375,6 +381,18 @@ rt_status rt_get_tile(rt_ctx* ctx, rt_filter filter, int32_t* tile4);
 rt_status rt_autotune(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int32_t views,
                       int32_t height, int32_t width, rt_filter filter, float* out, int32_t reps, rt_stream_t stream,
                       int32_t* tile4, float* best_ms);
+
+/* The autotuner of the backward: times rt_shade_batched_backward with the same
+ * twelve tiles and keeps the fastest as the backward tile of `filter`
+ * (rt_shade_batched's tile is left alone).  The arguments from dL_dout to
+ * flags are those of rt_shade_batched_backward, and the gradient buffers end
+ * up holding the results of the timed launches (with RT_ACCUMULATE, their
+ * sum), so a caller clears them before real use.  tile4, best_ms, reps and
+ * the synchronisation as in rt_autotune. */
+rt_status rt_autotune_backward(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int32_t views,
+                               int32_t height, int32_t width, rt_filter filter, const float* dL_dout,
+                               float* const* dL_dtex, int32_t n_dtex, float* dL_duv, float* dL_ddir, int32_t flags,
+                               int32_t reps, rt_stream_t stream, int32_t* tile4, float* best_ms);
 
 /* Counts the distinct texels read by the F fragments (any tap of non-zero or
  * zero weight of the filter's footprint), per object: counts_host (host,

@@ -78,9 +78,13 @@ SIGNATURES = {
                                          _P, _I32, _P]),
     "rt_prepare_deterministic": (_I32, [_P]),
     "rt_set_tile": (_I32, [_P, _I32, _I32, _I32, _I32, _I32]),
+    "rt_set_backward_tile": (_I32, [_P, _I32, _I32, _I32, _I32, _I32]),
     "rt_get_tile": (_I32, [_P, _I32, ctypes.POINTER(_I32)]),
+    "rt_get_backward_tile": (_I32, [_P, _I32, ctypes.POINTER(_I32)]),
     "rt_autotune": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, _I32, _P, ctypes.POINTER(_I32),
                            ctypes.POINTER(ctypes.c_float)]),
+    "rt_autotune_backward": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, ctypes.POINTER(_P), _I32, _P, _P,
+                                    _I32, _I32, _P, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)]),
     "rt_footprint": (_I32, [_P, _P, _P, _P, _I64, _I32, ctypes.POINTER(ctypes.c_uint64), _I32, _P]),
     "rt_footprint_noalloc": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, _I32, _P]),
     "rt_l2_loss_grad": (_I32, [_P, _P, _P, _I64, ctypes.c_float, _P, _P, _P]),

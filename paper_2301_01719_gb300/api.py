@@ -359,9 +359,19 @@ def rt_set_tile(ctx: Context, filter: int, tw: int, th: int, bx: int, by: int) -
     _lib.call("rt_set_tile", ctx.handle, int(filter), int(tw), int(th), int(bx), int(by))
 
 
+def rt_set_backward_tile(ctx: Context, filter: int, tw: int, th: int, bx: int, by: int) -> None:
+    _lib.call("rt_set_backward_tile", ctx.handle, int(filter), int(tw), int(th), int(bx), int(by))
+
+
 def rt_get_tile(ctx: Context, filter: int) -> tuple:
     t = (ctypes.c_int32 * 4)()
     _lib.call("rt_get_tile", ctx.handle, int(filter), t)
+    return tuple(int(x) for x in t)
+
+
+def rt_get_backward_tile(ctx: Context, filter: int) -> tuple:
+    t = (ctypes.c_int32 * 4)()
+    _lib.call("rt_get_backward_tile", ctx.handle, int(filter), t)
     return tuple(int(x) for x in t)
 
 
@@ -376,6 +386,21 @@ def rt_autotune(ctx: Context, uv, dirs, obj, filter: int = RT_QUADRILINEAR, out=
     t = (ctypes.c_int32 * 4)()
     ms = ctypes.c_float()
     _lib.call("rt_autotune", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(obj), V, H, W, int(filter), _ptr(out), int(reps),
+              _stream(stream, uv.device), t, ctypes.byref(ms))
+    return tuple(int(x) for x in t), float(ms.value)
+
+
+def rt_autotune_backward(ctx: Context, uv, dirs, obj, filter: int, dL_dout, dL_dtex=None, dL_duv=None, dL_ddir=None,
+                         flags: int = 0, reps: int = 3, stream=None):
+    """Picks the fastest screen tile for the batched backward; returns ((tw, th, bx, by), mean ms).
+    The gradient buffers are left holding the timed launches' results: clear them before use."""
+    F = _gbuffer(uv, dirs, obj)
+    V, H, W = _frames(uv, dirs, obj)
+    arr, n_dtex = _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir)
+    t = (ctypes.c_int32 * 4)()
+    ms = ctypes.c_float()
+    _lib.call("rt_autotune_backward", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(obj), V, H, W, int(filter),
+              _ptr(dL_dout), arr, n_dtex, _ptr(dL_duv), _ptr(dL_ddir), int(flags), int(reps),
               _stream(stream, uv.device), t, ctypes.byref(ms))
     return tuple(int(x) for x in t), float(ms.value)
 

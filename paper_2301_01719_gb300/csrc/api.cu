@@ -24,7 +24,7 @@ struct rt_ctx {
     float* scales[RT_MAX_OBJECTS];       // E4M3 scales the library allocated
     int64_t bytes[RT_MAX_OBJECTS];
     int n_obj = 0;                       // one past the highest id ever used
-    int tile[3][4];                      // per filter: tw, th, bx, by of the batched kernels
+    int tile[2][3][4];                   // per pass (forward, backward) and filter: tw, th, bx, by of the batched kernels
     long long* det[RT_MAX_OBJECTS];      // fixed-point gradient sums of the deterministic mode
     uint32_t* index[RT_MAX_OBJECTS];     // palette index maps the library copied
     int spec = -1;                       // the format shared by all objects (dense PLANES, clamp), else -1
@@ -161,12 +161,13 @@ rt_status rt_context_create(int cuda_device, rt_ctx** out) {
     std::memset(ctx->bytes, 0, sizeof(ctx->bytes));
     std::memset(ctx->det, 0, sizeof(ctx->det));
     std::memset(ctx->index, 0, sizeof(ctx->index));
-    for (int f = 0; f < 3; ++f) {
-        ctx->tile[f][0] = 8;
-        ctx->tile[f][1] = 4;
-        ctx->tile[f][2] = 2;
-        ctx->tile[f][3] = 2;
-    }
+    for (int p = 0; p < 2; ++p)
+        for (int f = 0; f < 3; ++f) {
+            ctx->tile[p][f][0] = 8;
+            ctx->tile[p][f][1] = 4;
+            ctx->tile[p][f][2] = 2;
+            ctx->tile[p][f][3] = 2;
+        }
     ctx->device = cuda_device;
     DeviceGuard g(cuda_device);
     if (!g.ok) {
@@ -571,10 +572,72 @@ static rt_status shade_backward_impl(rt_ctx* ctx, const float* uv, const float* 
     return cuda_status(e);
 }
 
-static bool frames_tiling(rt_ctx* ctx, int32_t views, int32_t height, int32_t width, rt_filter filter,
+enum { kForward = 0, kBackward = 1 };
+
+static bool frames_tiling(rt_ctx* ctx, int pass, int32_t views, int32_t height, int32_t width, rt_filter filter,
                           rt::Tiling* T) {
-    const int* t = ctx->tile[filter];
+    const int* t = ctx->tile[pass][filter];
     return rt::make_tiling(views, height, width, t[0], t[1], t[2], t[3], 4, T);
+}
+
+static rt_status set_tile(rt_ctx* ctx, int pass, rt_filter filter, int32_t tw, int32_t th, int32_t bx, int32_t by) {
+    if (!ctx || !valid_filter(filter)) return RT_ERR_INVALID_ARG;
+    rt::Tiling T;
+    if (!rt::make_tiling(1, 1, 1, tw, th, bx, by, 4, &T)) return RT_ERR_INVALID_ARG;
+    for (int p = 0; p < 2; ++p) {
+        if (pass >= 0 && p != pass) continue;
+        ctx->tile[p][filter][0] = tw;
+        ctx->tile[p][filter][1] = th;
+        ctx->tile[p][filter][2] = bx;
+        ctx->tile[p][filter][3] = by;
+    }
+    return RT_OK;
+}
+
+// Times `run` (one launch of a batched pass) with each candidate tile written
+// into `tile`, `reps` launches after one warm-up, and keeps the fastest.
+template <class Run>
+static rt_status tune_tile(int (&tile)[4], Run run, int reps, cudaStream_t s, int32_t* tile4, float* best_ms) {
+    static const int kCand[][4] = {{32, 1, 4, 1}, {32, 1, 2, 2}, {32, 1, 1, 4}, {16, 2, 4, 1}, {16, 2, 2, 2},
+                                   {16, 2, 1, 4}, {8, 4, 4, 1},  {8, 4, 2, 2},  {8, 4, 1, 4},  {4, 8, 4, 1},
+                                   {4, 8, 2, 2},  {4, 8, 1, 4}};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return RT_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return RT_ERR_CUDA;
+    }
+    int saved[4];
+    for (int k = 0; k < 4; ++k) saved[k] = tile[k];
+    float best = 1e30f;
+    int best_k = -1;
+    rt_status st = RT_OK;
+    for (int c = 0; c < (int)(sizeof(kCand) / sizeof(kCand[0])) && st == RT_OK; ++c) {
+        for (int k = 0; k < 4; ++k) tile[k] = kCand[c][k];
+        st = run();  // warm-up
+        if (st != RT_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == RT_OK; ++r) st = run();
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = RT_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (st == RT_OK && ms < best) {
+            best = ms;
+            best_k = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != RT_OK || best_k < 0) {
+        for (int k = 0; k < 4; ++k) tile[k] = saved[k];
+        return st != RT_OK ? st : RT_ERR_CUDA;
+    }
+    for (int k = 0; k < 4; ++k) tile[k] = kCand[best_k][k];
+    if (tile4)
+        for (int k = 0; k < 4; ++k) tile4[k] = kCand[best_k][k];
+    if (best_ms) *best_ms = best / (float)reps;
+    return RT_OK;
 }
 
 extern "C" {
@@ -658,7 +721,7 @@ rt_status rt_shade_batched(rt_ctx* ctx, const float* uv, const float* dir, const
     if (F == 0) return RT_OK;
     if (!out || !aligned16(out)) return RT_ERR_INVALID_ARG;
     rt::Tiling T;
-    if (!frames_tiling(ctx, views, height, width, filter, &T)) return RT_ERR_INVALID_ARG;
+    if (!frames_tiling(ctx, kForward, views, height, width, filter, &T)) return RT_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return RT_ERR_CUDA;
     return cuda_status(rt::launch_shade(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, T, ctx->spec, out, ctx->d_status,
@@ -673,7 +736,7 @@ rt_status rt_shade_batched_backward(rt_ctx* ctx, const float* uv, const float* d
         return RT_ERR_INVALID_ARG;
     const int64_t F = (int64_t)views * height * width;
     rt::Tiling T = rt::flat_tiling();
-    if (F > 0 && !frames_tiling(ctx, views, height, width, filter, &T)) return RT_ERR_INVALID_ARG;
+    if (F > 0 && !frames_tiling(ctx, kBackward, views, height, width, filter, &T)) return RT_ERR_INVALID_ARG;
     return shade_backward_impl(ctx, uv, dir, obj, F, filter, T, dL_dout, dL_dtex, n_dtex, dL_duv, dL_ddir, flags,
                                stream);
 }
@@ -694,19 +757,22 @@ rt_status rt_prepare_deterministic(rt_ctx* ctx) {
 }
 
 rt_status rt_set_tile(rt_ctx* ctx, rt_filter filter, int32_t tw, int32_t th, int32_t bx, int32_t by) {
-    if (!ctx || !valid_filter(filter)) return RT_ERR_INVALID_ARG;
-    rt::Tiling T;
-    if (!rt::make_tiling(1, 1, 1, tw, th, bx, by, 4, &T)) return RT_ERR_INVALID_ARG;
-    ctx->tile[filter][0] = tw;
-    ctx->tile[filter][1] = th;
-    ctx->tile[filter][2] = bx;
-    ctx->tile[filter][3] = by;
-    return RT_OK;
+    return set_tile(ctx, -1, filter, tw, th, bx, by);
+}
+
+rt_status rt_set_backward_tile(rt_ctx* ctx, rt_filter filter, int32_t tw, int32_t th, int32_t bx, int32_t by) {
+    return set_tile(ctx, kBackward, filter, tw, th, bx, by);
 }
 
 rt_status rt_get_tile(rt_ctx* ctx, rt_filter filter, int32_t* tile4) {
     if (!ctx || !valid_filter(filter) || !tile4) return RT_ERR_INVALID_ARG;
-    for (int k = 0; k < 4; ++k) tile4[k] = ctx->tile[filter][k];
+    for (int k = 0; k < 4; ++k) tile4[k] = ctx->tile[kForward][filter][k];
+    return RT_OK;
+}
+
+rt_status rt_get_backward_tile(rt_ctx* ctx, rt_filter filter, int32_t* tile4) {
+    if (!ctx || !valid_filter(filter) || !tile4) return RT_ERR_INVALID_ARG;
+    for (int k = 0; k < 4; ++k) tile4[k] = ctx->tile[kBackward][filter][k];
     return RT_OK;
 }
 
@@ -714,50 +780,24 @@ rt_status rt_autotune(rt_ctx* ctx, const float* uv, const float* dir, const int3
                       int32_t height, int32_t width, rt_filter filter, float* out, int32_t reps, rt_stream_t stream,
                       int32_t* tile4, float* best_ms) {
     if (!ctx || !valid_filter(filter) || views < 1 || height < 1 || width < 1 || reps < 1) return RT_ERR_INVALID_ARG;
-    static const int kCand[][4] = {{32, 1, 4, 1}, {32, 1, 2, 2}, {32, 1, 1, 4}, {16, 2, 4, 1}, {16, 2, 2, 2},
-                                   {16, 2, 1, 4}, {8, 4, 4, 1},  {8, 4, 2, 2},  {8, 4, 1, 4},  {4, 8, 4, 1},
-                                   {4, 8, 2, 2},  {4, 8, 1, 4}};
     DeviceGuard g(ctx->device);
     if (!g.ok) return RT_ERR_CUDA;
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess) return RT_ERR_CUDA;
-    if (cudaEventCreate(&e1) != cudaSuccess) {
-        cudaEventDestroy(e0);
-        return RT_ERR_CUDA;
-    }
-    int saved[4];
-    for (int k = 0; k < 4; ++k) saved[k] = ctx->tile[filter][k];
-    float best = 1e30f;
-    int best_k = -1;
-    rt_status st = RT_OK;
-    for (int c = 0; c < (int)(sizeof(kCand) / sizeof(kCand[0])) && st == RT_OK; ++c) {
-        for (int k = 0; k < 4; ++k) ctx->tile[filter][k] = kCand[c][k];
-        st = rt_shade_batched(ctx, uv, dir, obj, views, height, width, filter, out, stream);  // warm-up
-        if (st != RT_OK) break;
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < reps && st == RT_OK; ++r)
-            st = rt_shade_batched(ctx, uv, dir, obj, views, height, width, filter, out, stream);
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) st = RT_ERR_CUDA;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (st == RT_OK && ms < best) {
-            best = ms;
-            best_k = c;
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (st != RT_OK || best_k < 0) {
-        for (int k = 0; k < 4; ++k) ctx->tile[filter][k] = saved[k];
-        return st != RT_OK ? st : RT_ERR_CUDA;
-    }
-    for (int k = 0; k < 4; ++k) ctx->tile[filter][k] = kCand[best_k][k];
-    if (tile4)
-        for (int k = 0; k < 4; ++k) tile4[k] = kCand[best_k][k];
-    if (best_ms) *best_ms = best / (float)reps;
-    return RT_OK;
+    auto run = [&]() { return rt_shade_batched(ctx, uv, dir, obj, views, height, width, filter, out, stream); };
+    return tune_tile(ctx->tile[kForward][filter], run, reps, (cudaStream_t)stream, tile4, best_ms);
+}
+
+rt_status rt_autotune_backward(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int32_t views,
+                               int32_t height, int32_t width, rt_filter filter, const float* dL_dout,
+                               float* const* dL_dtex, int32_t n_dtex, float* dL_duv, float* dL_ddir, int32_t flags,
+                               int32_t reps, rt_stream_t stream, int32_t* tile4, float* best_ms) {
+    if (!ctx || !valid_filter(filter) || views < 1 || height < 1 || width < 1 || reps < 1) return RT_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    auto run = [&]() {
+        return rt_shade_batched_backward(ctx, uv, dir, obj, views, height, width, filter, dL_dout, dL_dtex, n_dtex,
+                                         dL_duv, dL_ddir, flags, stream);
+    };
+    return tune_tile(ctx->tile[kBackward][filter], run, reps, (cudaStream_t)stream, tile4, best_ms);
 }
 
 rt_status rt_footprint(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,

@@ -84,8 +84,15 @@ def test_batched_backward_equals_flat(scene):
         return duv.cpu().numpy(), ddir.cpu().numpy(), {k: v.cpu().numpy() for k, v in dt.items()}
 
     a = run(False)
-    for t in ((8, 4, 2, 2), (32, 1, 4, 1), (4, 8, 1, 4)):
-        api.rt_set_tile(ctx, filt, *t)
+    for t, fwd_only in (((8, 4, 2, 2), False), ((32, 1, 4, 1), False), ((4, 8, 1, 4), False), ((16, 2, 1, 4), True)):
+        if fwd_only:  # the backward's own tile; the forward keeps its tile
+            api.rt_set_tile(ctx, filt, 8, 4, 2, 2)
+            api.rt_set_backward_tile(ctx, filt, *t)
+            assert api.rt_get_tile(ctx, filt) == (8, 4, 2, 2)
+        else:
+            api.rt_set_tile(ctx, filt, *t)
+            assert api.rt_get_tile(ctx, filt) == t
+        assert api.rt_get_backward_tile(ctx, filt) == t
         b = run(True)
         np.testing.assert_array_equal(a[0], b[0])
         np.testing.assert_array_equal(a[1], b[1])
@@ -107,6 +114,23 @@ def test_autotune_and_invalid_tiles(scene):
     for bad in ((32, 2, 4, 1), (6, 5, 4, 1), (2, 16, 4, 1), (8, 4, 2, 1), (8, 4, 4, 4)):
         with pytest.raises(api.RadtexError):
             api.rt_set_tile(ctx, api.RT_QUADRILINEAR, *bad)
+        with pytest.raises(api.RadtexError):
+            api.rt_set_backward_tile(ctx, api.RT_QUADRILINEAR, *bad)
+    # the backward's autotuner sets the backward tile only; every tile gives the same coordinate gradients
+    W, H, n = scene[3]
+    gout = torch.ones((*o.shape, 4), device=uv.device)
+    dt = {o_: torch.zeros((n, n, H, W, 4), device=uv.device) for o_ in oids}
+    duv, ddir = torch.empty_like(uv), torch.empty_like(d)
+    api.rt_shade_batched_backward(ctx, uv, d, o, api.RT_QUADRILINEAR, gout, None, duv, ddir)
+    before = api.rt_get_tile(ctx, api.RT_QUADRILINEAR)
+    btile, bms = api.rt_autotune_backward(ctx, uv, d, o, api.RT_QUADRILINEAR, gout, dt, None, None,
+                                          api.RT_ACCUMULATE, reps=2)
+    assert btile in TILES and bms > 0
+    assert api.rt_get_backward_tile(ctx, api.RT_QUADRILINEAR) == btile
+    assert api.rt_get_tile(ctx, api.RT_QUADRILINEAR) == before
+    duv2, ddir2 = torch.empty_like(uv), torch.empty_like(d)
+    api.rt_shade_batched_backward(ctx, uv, d, o, api.RT_QUADRILINEAR, gout, None, duv2, ddir2)
+    assert torch.equal(duv, duv2) and torch.equal(ddir, ddir2)
     # empty batches are no-ops
     e3 = torch.empty((0, 4, 4, 3), device=uv.device)
     api.rt_shade_batched(ctx, torch.empty((0, 4, 4, 2), device=uv.device), e3,
