@@ -97,6 +97,11 @@ def lib() -> ctypes.CDLL:
                 "oracle_shade_world_backward64": (U32, [P, P, P, I32, I64, P, P, P, P, I32, P, P, P, P, P]),
                 "oracle_bake_shadow": (None, [I32, I32, I32, I32, P, ctypes.c_double, P, P]),
                 "oracle_bake_shadow_texels": (None, [I32, I32, I32, I32, P, ctypes.c_double, I64, P, P, P]),
+                "oracle_bake_deferred": (None, [I32, I32, I32, I32, P, I32, P, ctypes.c_double, P, P, P]),
+                "oracle_bake_deferred_texels": (None, [I32, I32, I32, I32, P, I32, P, ctypes.c_double, I64, P, P,
+                                                       P, P]),
+                "oracle_ambient_occlusion": (None, [P, I64, P, P, I32, P, P]),
+                "oracle_onb": (None, [I64, P, P, P]),
                 "oracle_num_threads": (I32, []),
                 "oracle_set_num_threads": (None, [I32]),
             }
@@ -541,6 +546,64 @@ def bake_shadow_texels(W: int, H: int, n: int, surface: int, scene: dict, ijst, 
     band = np.empty_like(vis)
     lib().oracle_bake_shadow_texels(W, H, n, surface, _p(S), float(delta), q.shape[0], _p(q), _p(vis), _p(band))
     return vis, band.astype(bool)
+
+
+# --------------------------------------------------------------------------
+# Deferred payloads (Section 1: deferred ambient occlusion and reflections;
+# reading R15).
+# --------------------------------------------------------------------------
+
+def _dirs(dirs) -> np.ndarray:
+    d = _c(dirs, np.float64).reshape(-1, 3)
+    assert 1 <= d.shape[0]
+    return d
+
+
+def bake_deferred(W: int, H: int, n: int, surface: int, scene: dict, dirs, delta: float | None = 2.0 ** -17):
+    """Deferred payload of every texel ((H n) x (W n) x 4, atlas order): the unlit albedo
+    of the reflected ray's first hit and the ambient occlusion there over the K local
+    directions dirs (K x 3); (0, 0, 0, 1) where the ray reaches the sky.  With delta, also
+    the range [lo, hi] over perturbed rays and ambiguous AO directions."""
+    S = scene_array(scene)
+    d = _dirs(dirs)
+    val = np.empty((H * n, W * n, 4))
+    if delta is None:
+        lib().oracle_bake_deferred(W, H, n, surface, _p(S), d.shape[0], _p(d), 0.0, _p(val), None, None)
+        return val
+    lo, hi = np.empty_like(val), np.empty_like(val)
+    lib().oracle_bake_deferred(W, H, n, surface, _p(S), d.shape[0], _p(d), float(delta), _p(val), _p(lo), _p(hi))
+    return val, lo, hi
+
+
+def bake_deferred_texels(W: int, H: int, n: int, surface: int, scene: dict, dirs, ijst,
+                         delta: float = 2.0 ** -17):
+    """bake_deferred for a list of texels ijst (count x 4: i, j, s, t): val, lo, hi rows."""
+    S = scene_array(scene)
+    d = _dirs(dirs)
+    q = _c(ijst, np.int32).reshape(-1, 4)
+    val, lo, hi = (np.empty((q.shape[0], 4)) for _ in range(3))
+    lib().oracle_bake_deferred_texels(W, H, n, surface, _p(S), d.shape[0], _p(d), float(delta), q.shape[0], _p(q),
+                                      _p(val), _p(lo), _p(hi))
+    return val, lo, hi
+
+
+def ambient_occlusion(scene: dict, X, N, dirs) -> np.ndarray:
+    """Fraction of the K local directions (frame of the unit normal N) unblocked from X."""
+    S = scene_array(scene)
+    X = _c(X, np.float64).reshape(-1, 3)
+    N = _c(N, np.float64).reshape(-1, 3)
+    d = _dirs(dirs)
+    out = np.empty(X.shape[0])
+    lib().oracle_ambient_occlusion(_p(S), X.shape[0], _p(X), _p(N), d.shape[0], _p(d), _p(out))
+    return out
+
+
+def onb(N):
+    """The orthonormal basis (b1, b2) the deferred payload uses around unit normals N."""
+    N = _c(N, np.float64).reshape(-1, 3)
+    b1, b2 = np.empty_like(N), np.empty_like(N)
+    lib().oracle_onb(N.shape[0], _p(N), _p(b1), _p(b2))
+    return b1, b2
 
 
 def bit_texture(bits: np.ndarray, W: int, H: int, n: int) -> "Texture":

@@ -1171,6 +1171,225 @@ void oracle_bake_shadow_texels(int32_t W, int32_t H, int32_t n, int32_t surface,
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Deferred payloads (Section 1: a texel may hold data for deferred          */
+/* rendering, such as ambient occlusion or reflections, instead of the final */
+/* colour; reading R15).  Texel (i, j, s, t) follows the ray of the radiance */
+/* bake (Eq. 4a, Eq. 4b) to its first hit X and stores                       */
+/*     (albedo(X), AO(X)),   AO(X) = (1/K) sum_k [ray X + t w_k unblocked],  */
+/* the albedo unlit; a ray that reaches the sky stores (0, 0, 0, 1).  The K  */
+/* directions w_k are given in the local frame of the hit: z along the       */
+/* surface normal that faces the arriving ray, x and y the orthonormal basis */
+/* of Duff et al., "Building an Orthonormal Basis, Revisited" (JCGT 6(1),    */
+/* 2017) built from that normal.                                             */
+/* ------------------------------------------------------------------------ */
+
+/* Orthonormal b1, b2 with (b1, b2, N) right-handed, for unit N (Duff et al.,
+ * the branch-free form) with the sign choice sg = +-1 (either is a valid
+ * basis when N_z is not -sg). */
+static void onb_signed(const double N[3], double sg, double b1[3], double b2[3]) {
+    double a = -1.0 / (sg + N[2]);
+    double b = N[0] * N[1] * a;
+    b1[0] = 1.0 + sg * N[0] * N[0] * a;
+    b1[1] = sg * b;
+    b1[2] = -sg * N[0];
+    b2[0] = b;
+    b2[1] = sg + N[1] * N[1] * a;
+    b2[2] = -N[1];
+}
+
+/* The basis Duff et al. take: sg = the sign of N_z, +1 for +0. */
+static void onb_duff(const double N[3], double b1[3], double b2[3]) { onb_signed(N, copysign(1.0, N[2]), b1, b2); }
+
+/* World direction of local w in the frame (b1, b2, N). */
+static void local_to_world(const double b1[3], const double b2[3], const double N[3], const double w[3],
+                           double out[3]) {
+    for (int k = 0; k < 3; ++k) out[k] = w[0] * b1[k] + w[1] * b2[k] + w[2] * N[k];
+}
+
+/* Unblocked directions among the K at X with normal N, given the basis.
+ * With amb non-NULL, *amb counts the directions whose test changes when X is
+ * moved by +-delta along b1, b2, N or the direction is tilted by +-delta
+ * along b1, b2 (grazing an occluder), and *amb_vis how many of those were
+ * unblocked. */
+static int visible_count(const double* S, const double X[3], const double N[3], const double b1[3],
+                         const double b2[3], int K, const double* dirs, double delta, int* amb, int* amb_vis) {
+    int vis = 0;
+    if (amb) *amb = *amb_vis = 0;
+    for (int k = 0; k < K; ++k) {
+        double w[3];
+        local_to_world(b1, b2, N, dirs + 3 * k, w);
+        int o = occluded(S, X, w);
+        vis += !o;
+        if (!amb) continue;
+        const double* ax[3] = {b1, b2, N};
+        int flips = 0;
+        for (int m = 0; m < 10 && !flips; ++m) {
+            double sg = (m & 1) ? -delta : delta;
+            double Xp[3] = {X[0], X[1], X[2]}, wp[3] = {w[0], w[1], w[2]};
+            if (m < 6) {
+                for (int c = 0; c < 3; ++c) Xp[c] += sg * ax[m >> 1][c];
+            } else {
+                for (int c = 0; c < 3; ++c) wp[c] += sg * ax[(m - 6) >> 1][c];
+                normalize3(wp);
+            }
+            flips = occluded(S, Xp, wp) != o;
+        }
+        if (flips) {
+            ++*amb;
+            *amb_vis += !o;
+        }
+    }
+    return vis;
+}
+
+/* First hit of the ray P + t d (t > eps): surface (-1 for the sky), point X,
+ * the normal N facing the ray and the unlit albedo. */
+static int first_hit(const double* S, const double P[3], const double d[3], double X[3], double N[3],
+                     double alb[3]) {
+    double eps = S[BK_EPS], r = S[BK_SPHERE_R];
+    double t_best = INFINITY;
+    int hit = -1;
+    double o[3] = {P[0] - S[BK_SPHERE_C], P[1] - S[BK_SPHERE_C + 1], P[2] - S[BK_SPHERE_C + 2]};
+    double b = dot3(o, d), q = dot3(o, o) - r * r, disc = b * b - q;
+    if (disc > 0.0) {
+        double t = -b - sqrt(disc);
+        if (t > eps) {
+            t_best = t;
+            hit = OR_SURFACE_SPHERE;
+        }
+    }
+    if (d[1] != 0.0) {
+        double t = (S[BK_PLANE_Y] - P[1]) / d[1];
+        if (t > eps && t < t_best) {
+            t_best = t;
+            hit = OR_SURFACE_PLANE;
+        }
+    }
+    if (hit < 0) return hit;
+    for (int k = 0; k < 3; ++k) X[k] = P[k] + t_best * d[k];
+    if (hit == OR_SURFACE_SPHERE) {
+        for (int k = 0; k < 3; ++k) {
+            N[k] = (X[k] - S[BK_SPHERE_C + k]) / r;
+            alb[k] = S[BK_SPHERE_ALB + k];
+        }
+    } else {
+        N[0] = N[2] = 0.0;
+        N[1] = d[1] < 0.0 ? 1.0 : -1.0;
+        plane_albedo(S, X, alb);
+    }
+    return hit;
+}
+
+/* The deferred payload of the ray P + d; with lo / hi non-NULL, widened by its
+ * ambiguous AO directions and by the basis of the opposite sign choice when
+ * the hit normal's z lies within 2^-16 of 0. */
+static void deferred_ray(const double* S, const double P[3], const double d[3], int K, const double* dirs,
+                         double delta, double out[4], double* lo, double* hi) {
+    double X[3], N[3], alb[3];
+    if (first_hit(S, P, d, X, N, alb) < 0) {
+        out[0] = out[1] = out[2] = 0.0;
+        out[3] = 1.0;
+        if (lo)
+            for (int c = 0; c < 4; ++c) lo[c] = hi[c] = out[c];
+        return;
+    }
+    double b1[3], b2[3];
+    onb_duff(N, b1, b2);
+    int amb = 0, amb_vis = 0;
+    int vis = visible_count(S, X, N, b1, b2, K, dirs, delta, lo ? &amb : NULL, &amb_vis);
+    for (int k = 0; k < 3; ++k) out[k] = alb[k];
+    out[3] = (double)vis / K;
+    if (!lo) return;
+    for (int c = 0; c < 3; ++c) lo[c] = hi[c] = out[c];
+    lo[3] = (double)(vis - amb_vis) / K;
+    hi[3] = (double)(vis + (amb - amb_vis)) / K;
+    if (fabs(N[2]) < 0x1p-16) { /* FP32 may see the other sign of N_z, hence the other basis */
+        double c1[3], c2[3];
+        onb_signed(N, -copysign(1.0, N[2]), c1, c2);
+        double other = (double)visible_count(S, X, N, c1, c2, K, dirs, delta, NULL, NULL) / K;
+        if (other < lo[3]) lo[3] = other;
+        if (other > hi[3]) hi[3] = other;
+    }
+}
+
+/* One deferred texel: value, and with lo non-NULL the range over the ten
+ * perturbed primary rays of bake_texel and the ambiguous AO directions. */
+static void deferred_texel(const double* S, int surface, int64_t W, int64_t H, int64_t n, int64_t i, int64_t j,
+                           int64_t s, int64_t t, int K, const double* dirs, double delta, double out[4], double* lo,
+                           double* hi) {
+    double u = ((double)i + 0.5) / W, v = ((double)j + 0.5) / H;
+    double P[3], F[3][3];
+    surface_frame(S, surface, u, v, P, F);
+    double B[2] = {texel_centre(s, n), texel_centre(t, n)};
+    double A[2], R[3];
+    unsquarify(B, A); /* Eq. 4a */
+    reflection(A, R); /* Eq. 4b */
+    double d[3];
+    for (int k = 0; k < 3; ++k) d[k] = R[0] * F[0][k] + R[1] * F[1][k] + R[2] * F[2][k];
+    deferred_ray(S, P, d, K, dirs, delta, out, lo, hi);
+    if (!lo) return;
+    for (int m = 0; m < 10; ++m) {
+        double Pp[3] = {P[0], P[1], P[2]}, dp[3] = {d[0], d[1], d[2]};
+        double sg = (m & 1) ? -delta : delta;
+        if (m < 4) {
+            for (int k = 0; k < 3; ++k) Pp[k] += sg * F[m >> 1][k];
+        } else {
+            for (int k = 0; k < 3; ++k) dp[k] += sg * F[(m - 4) >> 1][k];
+            normalize3(dp);
+        }
+        double o4[4];
+        deferred_ray(S, Pp, dp, K, dirs, delta, o4, NULL, NULL);
+        for (int c = 0; c < 4; ++c) {
+            if (o4[c] < lo[c]) lo[c] = o4[c];
+            if (o4[c] > hi[c]) hi[c] = o4[c];
+        }
+    }
+}
+
+/* Deferred bake of a w x h x n x n texture (atlas order of reading R4, 4
+ * doubles a texel); lo / hi as in oracle_bake. dirs: K local directions. */
+void oracle_bake_deferred(int32_t W, int32_t H, int32_t n, int32_t surface, const double* S, int32_t K,
+                          const double* dirs, double delta, double* val, double* lo, double* hi) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t bk = 0; bk < (int64_t)W * H; ++bk) {
+        int64_t i = bk % W, j = bk / W;
+        for (int64_t t = 0; t < n; ++t)
+            for (int64_t s = 0; s < n; ++s) {
+                int64_t e = ((j * n + t) * (int64_t)W * n + (i * n + s)) * 4;
+                deferred_texel(S, surface, W, H, n, i, j, s, t, K, dirs, delta, val + e, lo ? lo + e : NULL,
+                               hi ? hi + e : NULL);
+            }
+    }
+}
+
+/* The same for a list of texels ijst (count x 4 int32). */
+void oracle_bake_deferred_texels(int32_t W, int32_t H, int32_t n, int32_t surface, const double* S, int32_t K,
+                                 const double* dirs, double delta, int64_t count, const int32_t* ijst, double* val,
+                                 double* lo, double* hi) {
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < count; ++k) {
+        const int32_t* q = ijst + 4 * k;
+        deferred_texel(S, surface, W, H, n, q[0], q[1], q[2], q[3], K, dirs, delta, val + 4 * k,
+                       lo ? lo + 4 * k : NULL, hi ? hi + 4 * k : NULL);
+    }
+}
+
+/* AO at given points X (rows of 3) with unit normals N: out[count]. */
+void oracle_ambient_occlusion(const double* S, int64_t count, const double* X, const double* N, int32_t K,
+                              const double* dirs, double* out) {
+    for (int64_t k = 0; k < count; ++k) {
+        double b1[3], b2[3];
+        onb_duff(N + 3 * k, b1, b2);
+        out[k] = (double)visible_count(S, X + 3 * k, N + 3 * k, b1, b2, K, dirs, 0.0, NULL, NULL) / K;
+    }
+}
+
+/* The basis of onb_duff for given unit normals (rows of 3): b1, b2. */
+void oracle_onb(int64_t count, const double* N, double* b1, double* b2) {
+    for (int64_t k = 0; k < count; ++k) onb_duff(N + 3 * k, b1 + 3 * k, b2 + 3 * k);
+}
+
 /* The world-space reflection ray of texel (s, t) at bucket coordinate (u, v):
  * origin P, direction d and the frame rows T, B, N (9 doubles), for the pins. */
 void oracle_bake_ray(int32_t n, int32_t surface, const double* S, double u, double v, int32_t s, int32_t t,

@@ -11,4 +11,4 @@ FP64 then rounded to FP32, the G-buffer precision.
 from .scenes import (GBuffer, quad_scene, quad_views, sphere_plane_poses, sphere_plane_scene,  # noqa: F401
                      voronoi_planes_scene)
 from .fields import field_lobes, bucket_lobe_params, eval_field_lobes  # noqa: F401
-from .bake import bake_scene  # noqa: F401
+from .bake import ao_directions, bake_scene  # noqa: F401

@@ -32,3 +32,21 @@ def bake_scene(seed: int, plane_height: float = -1.0, sphere_radius: float = 1.0
         "fog": float(rng.uniform(0.05, 0.15)),
         "ray_offset": 1e-4,
     }
+
+
+def ao_directions(seed: int, K: int) -> np.ndarray:
+    """K unit directions of the upper hemisphere (z >= 0), cosine-distributed and
+    stratified (jittered cells of a near-square grid), FP32: the sample set of an
+    ambient-occlusion estimate, drawn once and passed to the bake as an input."""
+    rng = np.random.default_rng(seed)
+    a = int(np.floor(np.sqrt(K)))
+    while K % a:
+        a -= 1
+    b = K // a
+    cells = np.stack(np.meshgrid(np.arange(a), np.arange(b), indexing="ij"), -1).reshape(-1, 2)
+    u1 = (cells[:, 0] + rng.uniform(size=K)) / a
+    u2 = (cells[:, 1] + rng.uniform(size=K)) / b
+    r, phi = np.sqrt(u1), 2.0 * np.pi * u2
+    d = np.stack([r * np.cos(phi), r * np.sin(phi), np.sqrt(np.maximum(1.0 - u1, 0.0))], 1)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return d.astype(np.float32)

@@ -22,6 +22,7 @@ BAKE = "tests/test_oracle_bake.py"
 PALETTE = "tests/test_oracle_palette.py"
 WORLD = "tests/test_oracle_world.py"
 SHADOW = "tests/test_oracle_shadow.py"
+DEFERRED = "tests/test_oracle_deferred.py"
 
 # (name, original text, mutated text, pin files expected to catch it)
 MUTATIONS = [
@@ -50,6 +51,14 @@ MUTATIONS = [
     ("eq1a_minus_normal", "double h[3] = {I[0] + N[0], I[1] + N[1], I[2] + N[2]};",
      "double h[3] = {I[0] - N[0], I[1] - N[1], I[2] + N[2]};", [PINS, WORLD]),
     ("repeat_negative_modulo", "return r < 0 ? r + size : r;", "return r < 0 ? -r : r;", [WORLD]),
+    ("deferred_wrong_albedo", "alb[k] = S[BK_SPHERE_ALB + k];", "alb[k] = S[BK_PLANE_ALB + k];", [DEFERRED]),
+    ("deferred_plane_normal_side", "N[1] = d[1] < 0.0 ? 1.0 : -1.0;", "N[1] = d[1] < 0.0 ? -1.0 : 1.0;",
+     [DEFERRED]),
+    ("onb_flipped_b2", "    b2[2] = -N[1];", "    b2[2] = N[1];", [DEFERRED]),
+    ("ao_counts_blocked", "vis += !o;", "vis += o;", [DEFERRED]),
+    ("deferred_sky_occluded", "out[3] = 1.0;\n        if (lo)", "out[3] = 0.0;\n        if (lo)", [DEFERRED]),
+    ("deferred_from_origin_side", "for (int k = 0; k < 3; ++k) X[k] = P[k] + t_best * d[k];",
+     "for (int k = 0; k < 3; ++k) X[k] = P[k] + 0.5 * t_best * d[k];", [DEFERRED]),
 ]
 
 
