@@ -100,7 +100,7 @@ def lib() -> ctypes.CDLL:
                 "oracle_bake_deferred": (None, [I32, I32, I32, I32, P, I32, P, ctypes.c_double, P, P, P]),
                 "oracle_bake_deferred_texels": (None, [I32, I32, I32, I32, P, I32, P, ctypes.c_double, I64, P, P,
                                                        P, P]),
-                "oracle_ambient_occlusion": (None, [P, I64, P, P, I32, P, P]),
+                "oracle_ambient_occlusion": (None, [P, I32, I64, P, P, I32, P, P]),
                 "oracle_onb": (None, [I64, P, P, P]),
                 "oracle_num_threads": (I32, []),
                 "oracle_set_num_threads": (None, [I32]),
@@ -576,25 +576,33 @@ def bake_deferred(W: int, H: int, n: int, surface: int, scene: dict, dirs, delta
 
 
 def bake_deferred_texels(W: int, H: int, n: int, surface: int, scene: dict, dirs, ijst,
-                         delta: float = 2.0 ** -17):
-    """bake_deferred for a list of texels ijst (count x 4: i, j, s, t): val, lo, hi rows."""
+                         delta: float | None = 2.0 ** -17):
+    """bake_deferred for a list of texels ijst (count x 4: i, j, s, t): val, lo, hi rows
+    (val alone when delta is None)."""
     S = scene_array(scene)
     d = _dirs(dirs)
     q = _c(ijst, np.int32).reshape(-1, 4)
-    val, lo, hi = (np.empty((q.shape[0], 4)) for _ in range(3))
+    val = np.empty((q.shape[0], 4))
+    if delta is None:
+        lib().oracle_bake_deferred_texels(W, H, n, surface, _p(S), d.shape[0], _p(d), 0.0, q.shape[0], _p(q),
+                                          _p(val), None, None)
+        return val
+    lo, hi = np.empty_like(val), np.empty_like(val)
     lib().oracle_bake_deferred_texels(W, H, n, surface, _p(S), d.shape[0], _p(d), float(delta), q.shape[0], _p(q),
                                       _p(val), _p(lo), _p(hi))
     return val, lo, hi
 
 
-def ambient_occlusion(scene: dict, X, N, dirs) -> np.ndarray:
-    """Fraction of the K local directions (frame of the unit normal N) unblocked from X."""
+def ambient_occlusion(scene: dict, X, N, dirs, surface: int = -1) -> np.ndarray:
+    """Fraction of the K local directions (frame of the unit normal N) unblocked from X;
+    `surface` (SURFACE_SPHERE / SURFACE_PLANE) is the one X lies on, which the rays skip
+    (-1: both surfaces are tested)."""
     S = scene_array(scene)
     X = _c(X, np.float64).reshape(-1, 3)
     N = _c(N, np.float64).reshape(-1, 3)
     d = _dirs(dirs)
     out = np.empty(X.shape[0])
-    lib().oracle_ambient_occlusion(_p(S), X.shape[0], _p(X), _p(N), d.shape[0], _p(d), _p(out))
+    lib().oracle_ambient_occlusion(_p(S), int(surface), X.shape[0], _p(X), _p(N), d.shape[0], _p(d), _p(out))
     return out
 
 

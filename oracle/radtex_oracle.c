@@ -1177,6 +1177,7 @@ void oracle_bake_shadow_texels(int32_t W, int32_t H, int32_t n, int32_t surface,
 /* colour; reading R15).  Texel (i, j, s, t) follows the ray of the radiance */
 /* bake (Eq. 4a, Eq. 4b) to its first hit X and stores                       */
 /*     (albedo(X), AO(X)),   AO(X) = (1/K) sum_k [ray X + t w_k unblocked],  */
+/* the AO rays tested against the other surface than the one X lies on.      */
 /* the albedo unlit; a ray that reaches the sky stores (0, 0, 0, 1).  The K  */
 /* directions w_k are given in the local frame of the hit: z along the       */
 /* surface normal that faces the arriving ray, x and y the orthonormal basis */
@@ -1207,19 +1208,36 @@ static void local_to_world(const double b1[3], const double b2[3], const double 
     for (int k = 0; k < 3; ++k) out[k] = w[0] * b1[k] + w[1] * b2[k] + w[2] * N[k];
 }
 
+/* occluded() by the other surface than `self` only: a ray leaving a point of
+ * the plane into the half-space of its normal cannot meet the plane again, nor
+ * one leaving the convex sphere outward meet the sphere, so the AO rays skip
+ * the surface they start on (exact, and free of the ray offset there). */
+static int occluded_by_other(const double* S, int self, const double P[3], const double d[3]) {
+    double eps = S[BK_EPS], r = S[BK_SPHERE_R];
+    if (self != OR_SURFACE_SPHERE) {
+        double oc[3] = {S[BK_SPHERE_C] - P[0], S[BK_SPHERE_C + 1] - P[1], S[BK_SPHERE_C + 2] - P[2]};
+        double tc = dot3(oc, d);
+        double x[3] = {oc[0] - tc * d[0], oc[1] - tc * d[1], oc[2] - tc * d[2]};
+        double m2 = dot3(x, x);
+        if (m2 < r * r && tc - sqrt(r * r - m2) > eps) return 1;
+    }
+    if (self != OR_SURFACE_PLANE && d[1] != 0.0 && (S[BK_PLANE_Y] - P[1]) / d[1] > eps) return 1;
+    return 0;
+}
+
 /* Unblocked directions among the K at X with normal N, given the basis.
  * With amb non-NULL, *amb counts the directions whose test changes when X is
  * moved by +-delta along b1, b2, N or the direction is tilted by +-delta
  * along b1, b2 (grazing an occluder), and *amb_vis how many of those were
  * unblocked. */
-static int visible_count(const double* S, const double X[3], const double N[3], const double b1[3],
+static int visible_count(const double* S, int self, const double X[3], const double N[3], const double b1[3],
                          const double b2[3], int K, const double* dirs, double delta, int* amb, int* amb_vis) {
     int vis = 0;
     if (amb) *amb = *amb_vis = 0;
     for (int k = 0; k < K; ++k) {
         double w[3];
         local_to_world(b1, b2, N, dirs + 3 * k, w);
-        int o = occluded(S, X, w);
+        int o = occluded_by_other(S, self, X, w);
         vis += !o;
         if (!amb) continue;
         const double* ax[3] = {b1, b2, N};
@@ -1233,7 +1251,7 @@ static int visible_count(const double* S, const double X[3], const double N[3], 
                 for (int c = 0; c < 3; ++c) wp[c] += sg * ax[(m - 6) >> 1][c];
                 normalize3(wp);
             }
-            flips = occluded(S, Xp, wp) != o;
+            flips = occluded_by_other(S, self, Xp, wp) != o;
         }
         if (flips) {
             ++*amb;
@@ -1282,12 +1300,13 @@ static int first_hit(const double* S, const double P[3], const double d[3], doub
 }
 
 /* The deferred payload of the ray P + d; with lo / hi non-NULL, widened by its
- * ambiguous AO directions and by the basis of the opposite sign choice when
- * the hit normal's z lies within 2^-16 of 0. */
+ * ambiguous AO directions and, on the sphere, by the basis of the opposite
+ * sign choice when the hit normal's z lies within 2^-16 of 0. */
 static void deferred_ray(const double* S, const double P[3], const double d[3], int K, const double* dirs,
                          double delta, double out[4], double* lo, double* hi) {
     double X[3], N[3], alb[3];
-    if (first_hit(S, P, d, X, N, alb) < 0) {
+    int hit = first_hit(S, P, d, X, N, alb);
+    if (hit < 0) {
         out[0] = out[1] = out[2] = 0.0;
         out[3] = 1.0;
         if (lo)
@@ -1297,17 +1316,19 @@ static void deferred_ray(const double* S, const double P[3], const double d[3], 
     double b1[3], b2[3];
     onb_duff(N, b1, b2);
     int amb = 0, amb_vis = 0;
-    int vis = visible_count(S, X, N, b1, b2, K, dirs, delta, lo ? &amb : NULL, &amb_vis);
+    int vis = visible_count(S, hit, X, N, b1, b2, K, dirs, delta, lo ? &amb : NULL, &amb_vis);
     for (int k = 0; k < 3; ++k) out[k] = alb[k];
     out[3] = (double)vis / K;
     if (!lo) return;
     for (int c = 0; c < 3; ++c) lo[c] = hi[c] = out[c];
     lo[3] = (double)(vis - amb_vis) / K;
     hi[3] = (double)(vis + (amb - amb_vis)) / K;
-    if (fabs(N[2]) < 0x1p-16) { /* FP32 may see the other sign of N_z, hence the other basis */
+    if (hit == OR_SURFACE_SPHERE && fabs(N[2]) < 0x1p-16) {
+        /* a computed N_z this small may have the other sign in FP32, hence the other basis (the
+         * plane's normal has an exact zero z on both sides) */
         double c1[3], c2[3];
         onb_signed(N, -copysign(1.0, N[2]), c1, c2);
-        double other = (double)visible_count(S, X, N, c1, c2, K, dirs, delta, NULL, NULL) / K;
+        double other = (double)visible_count(S, hit, X, N, c1, c2, K, dirs, delta, NULL, NULL) / K;
         if (other < lo[3]) lo[3] = other;
         if (other > hi[3]) hi[3] = other;
     }
@@ -1375,13 +1396,14 @@ void oracle_bake_deferred_texels(int32_t W, int32_t H, int32_t n, int32_t surfac
     }
 }
 
-/* AO at given points X (rows of 3) with unit normals N: out[count]. */
-void oracle_ambient_occlusion(const double* S, int64_t count, const double* X, const double* N, int32_t K,
-                              const double* dirs, double* out) {
+/* AO at given points X (rows of 3) of surface `self` (the surface the rays
+ * leave, or -1 to test both) with unit normals N: out[count]. */
+void oracle_ambient_occlusion(const double* S, int32_t self, int64_t count, const double* X, const double* N,
+                              int32_t K, const double* dirs, double* out) {
     for (int64_t k = 0; k < count; ++k) {
         double b1[3], b2[3];
         onb_duff(N + 3 * k, b1, b2);
-        out[k] = (double)visible_count(S, X + 3 * k, N + 3 * k, b1, b2, K, dirs, 0.0, NULL, NULL) / K;
+        out[k] = (double)visible_count(S, self, X + 3 * k, N + 3 * k, b1, b2, K, dirs, 0.0, NULL, NULL) / K;
     }
 }
 
