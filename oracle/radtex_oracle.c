@@ -1323,6 +1323,20 @@ static void deferred_ray(const double* S, const double P[3], const double d[3], 
     for (int c = 0; c < 3; ++c) lo[c] = hi[c] = out[c];
     lo[3] = (double)(vis - amb_vis) / K;
     hi[3] = (double)(vis + (amb - amb_vis)) / K;
+    if (hit == OR_SURFACE_PLANE) {
+        /* A grazing ray meets the plane far away: a direction error of 2^-20 (a
+         * few FP32 roundings) moves the hit by t 2^-20 / |d_y| along the plane.
+         * Past a tenth of a radian of the pattern's phase the albedo is not
+         * determined by FP32 inputs: the range becomes the pattern's whole
+         * range, albedo x [1/2, 1]. */
+        double t = sqrt((X[0] - P[0]) * (X[0] - P[0]) + (X[1] - P[1]) * (X[1] - P[1]) +
+                        (X[2] - P[2]) * (X[2] - P[2]));
+        if (S[BK_PLANE_FREQ] * t * 0x1p-20 / fabs(d[1]) > 0.1)
+            for (int c = 0; c < 3; ++c) {
+                lo[c] = fmin(lo[c], 0.5 * S[BK_PLANE_ALB + c]);
+                hi[c] = fmax(hi[c], S[BK_PLANE_ALB + c]);
+            }
+    }
     if (hit == OR_SURFACE_SPHERE && fabs(N[2]) < 0x1p-16) {
         /* a computed N_z this small may have the other sign in FP32, hence the other basis (the
          * plane's normal has an exact zero z on both sides) */
