@@ -54,6 +54,8 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--samples", type=int, default=4, help="shadow: light samples per fragment")
+    p.add_argument("--deferred", type=int, default=0,
+                   help="bake: the deferred payload (albedo + ambient occlusion) over this many AO directions")
     p.add_argument("--workload", choices=["sphere-plane", "voronoi64", "bake", "world", "shadow"],
                    default="sphere-plane",
                    help="voronoi64: 64 objects of uneven sizes, 4 views of 3840x2160, forward in a CUDA graph; "
@@ -620,11 +622,31 @@ BAKE_SCENE_SEED = 2001
 # tests 26, sky 24, hit point and its shading 26, fog and blend 10), final
 # combination 6.
 BAKE_FLOPS_PER_TEXEL = 128
+# Deferred payload, counted from its formulas.  Every texel: Eq. 4a/4b 21, world
+# rotation 15, first hit with its normal and albedo 45.  A texel whose ray hits
+# a surface adds the hit's basis 12, the projections of the test's fixed vector
+# on it 15 and the AO divide 1; then per direction, from a plane hit (the sphere
+# object's texels) the projected dot product 5 and the sphere test 7, from a
+# sphere hit (the plane object's) the dot product 5 and the plane test 3.  Sky
+# texels end after the first hit.
+DEFERRED_FLOPS_TEXEL, DEFERRED_FLOPS_HIT = 81, 28
+DEFERRED_FLOPS_DIR = {"sphere": 12, "plane": 8}
+AO_DIRS_SEED = 4242
 SMS, FP32_LANES_PER_SM, NOMINAL_SM_MHZ = 152, 128, 2070.0
 
 
 def bake_name(a) -> str:
-    return f"bake 2 objects (sphere, plane) x {a.buckets}^2 buckets x {a.n}^2 directions {a.storage.upper()}"
+    what = f"deferred payload (albedo + AO over {a.deferred} directions)" if a.deferred else "radiance"
+    return (f"bake {what}, 2 objects (sphere, plane) x {a.buckets}^2 buckets x {a.n}^2 directions "
+            f"{a.storage.upper()}")
+
+
+def deferred_flops(K: int, hit_fraction: dict) -> float:
+    """Formula flops of the deferred payload per texel, averaged over the two
+    objects given each object's share of texels whose ray hits a surface."""
+    per = [DEFERRED_FLOPS_TEXEL + h * (DEFERRED_FLOPS_HIT + K * DEFERRED_FLOPS_DIR[obj])
+           for obj, h in hit_fraction.items()]
+    return float(np.mean(per))
 
 
 def bake_cpu_baseline(a, scene, seconds: float, steps: int | None = None):
@@ -639,9 +661,20 @@ def bake_cpu_baseline(a, scene, seconds: float, steps: int | None = None):
         return np.stack([rng.integers(0, W, k), rng.integers(0, H, k), rng.integers(0, n, k),
                          rng.integers(0, n, k)], 1).astype(np.int32)
 
+    if a.deferred:
+        import synth
+
+        dirs = synth.ao_directions(AO_DIRS_SEED, a.deferred)
+
+        def bake(surf, q):
+            oracle.bake_deferred_texels(W, H, n, surf, scene, dirs, q, None)
+    else:
+        def bake(surf, q):
+            oracle.bake_texels(W, H, n, surf, scene, q, None)
+
     probe = sample(20000)
     t0 = time.perf_counter()
-    oracle.bake_texels(W, H, n, oracle.SURFACE_SPHERE, scene, probe, None)
+    bake(oracle.SURFACE_SPHERE, probe)
     rate = probe.shape[0] / max(time.perf_counter() - t0, 1e-6)
     k = int(max(20000, rate * seconds / 2))
     q = sample(k)
@@ -649,7 +682,7 @@ def bake_cpu_baseline(a, scene, seconds: float, steps: int | None = None):
     for _ in range(steps or 1):
         t0 = time.perf_counter()
         for surf in (oracle.SURFACE_SPHERE, oracle.SURFACE_PLANE):
-            oracle.bake_texels(W, H, n, surf, scene, q, None)
+            bake(surf, q)
         times.append(time.perf_counter() - t0)
     return 2 * k, times, oracle.num_threads()
 
@@ -698,10 +731,18 @@ def run_bake(a):
     oids = [api.rt_create_texture(ctx, W, H, n, fmt) for _ in range(2)]
     surfaces = (api.RT_SURFACE_SPHERE, api.RT_SURFACE_PLANE)
     stream = torch.cuda.current_stream(dev)
+    if a.deferred:
+        ao_dirs = torch.from_numpy(synth.ao_directions(AO_DIRS_SEED, a.deferred)).to(dev)
+
+        def bake_one(oid, surf):
+            api.rt_bake_deferred(ctx, oid, surf, scene, ao_dirs, stream)
+    else:
+        def bake_one(oid, surf):
+            api.rt_bake(ctx, oid, surf, scene, stream)
 
     def step():
         for oid, surf in zip(oids, surfaces):
-            api.rt_bake(ctx, oid, surf, scene, stream)
+            bake_one(oid, surf)
 
     for _ in range(a.warmup):
         step()
@@ -718,9 +759,9 @@ def run_bake(a):
         for k in range(a.steps):
             e = ev[k]
             e[0].record(stream)
-            api.rt_bake(ctx, oids[0], surfaces[0], scene, stream)
+            bake_one(oids[0], surfaces[0])
             e[1].record(stream)
-            api.rt_bake(ctx, oids[1], surfaces[1], scene, stream)
+            bake_one(oids[1], surfaces[1])
             e[2].record(stream)
         end.record(stream)
         torch.cuda.synchronize()
@@ -739,7 +780,18 @@ def run_bake(a):
     clocks = clk.summary()
     sm_max = clocks.get("sm_max_mhz") or NOMINAL_SM_MHZ
     peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    achieved = BAKE_FLOPS_PER_TEXEL * texels / (launch_ms * 1e-3) / 1e12
+    hit_fraction = None
+    if a.deferred:
+        # sky texels hold (0, 0, 0, 1) and every hit a positive albedo: count the hits on the device
+        hit_fraction = {}
+        for name, oid in zip(("sphere", "plane"), oids):
+            codes, _ = api.rt_read_texture(ctx, oid, api.RT_LAYOUT_PLANES, stream)
+            hit_fraction[name] = float((codes[..., :3] != 0).any(-1).float().mean())
+            del codes
+        flops_per_texel = deferred_flops(a.deferred, hit_fraction)
+    else:
+        flops_per_texel = BAKE_FLOPS_PER_TEXEL
+    achieved = flops_per_texel * texels / (launch_ms * 1e-3) / 1e12
     tb = bytes_per_texel(a.storage)
     write_gbs = texels * tb / (launch_ms * 1e-3) / 1e9
     hbm_peak, hbm_kind = measured_peak()
@@ -753,7 +805,7 @@ def run_bake(a):
 
         def e2e_step():
             for k, (oid, surf) in enumerate(zip(oids, surfaces)):
-                api.rt_bake(ctx, oid, surf, scene, stream)
+                bake_one(oid, surf)
                 codes, _ = api.rt_read_texture(ctx, oid, api.RT_LAYOUT_PLANES, stream)
                 host[k].copy_(codes, non_blocking=True)
             torch.cuda.current_stream(dev).synchronize()
@@ -780,7 +832,8 @@ def run_bake(a):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": None,
                      "peak_source": f"{SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
-                     "algorithmic_flops_per_texel": BAKE_FLOPS_PER_TEXEL, "kernel": "bake_kernel",
+                     "algorithmic_flops_per_texel": flops_per_texel, "hit_fraction": hit_fraction,
+                     "kernel": "bake_kernel",
                      "write_gbs": write_gbs, "write_frac_of_hbm": write_gbs / hbm_peak, "hbm_peak_source": hbm_kind},
         "gpu_launches": 2 * a.steps,
         "clocks": clocks,

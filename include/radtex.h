@@ -255,6 +255,27 @@ typedef enum { RT_SURFACE_SPHERE = 0, RT_SURFACE_PLANE = 1 } rt_surface;
  * RT_ERR_INVALID_ARG.  Asynchronous on `stream`; allocates nothing. */
 rt_status rt_bake(rt_ctx* ctx, int32_t obj_id, rt_surface surface, const rt_bake_scene* scene, rt_stream_t stream);
 
+/* Largest direction count of rt_bake_deferred. */
+#define RT_MAX_AO_DIRECTIONS 1024
+
+/* Bakes a deferred payload into object obj_id (Section 1: a texel may hold
+ * data for deferred rendering, such as ambient occlusion or reflections,
+ * instead of the final colour).  The ray of each texel is rt_bake's (Eq. 4a,
+ * Eq. 4b); at its first hit X (the sphere's entering root or the plane, at
+ * t > ray_offset) the texel holds (albedo(X) unlit, AO(X)), AO = the fraction
+ * of the K directions for which the ray from X meets neither occluder at
+ * t > ray_offset.  ao_dirs (device, K x 3 floats, row-major, 4-byte aligned,
+ * caller-owned, read during the call only) are unit vectors in the local frame
+ * of the hit: z along the normal facing the arriving ray (the sphere's outward
+ * normal; +y or -y on the plane), x and y the orthonormal basis of Duff et al.,
+ * "Building an Orthonormal Basis, Revisited" (JCGT 6(1), 2017) built from it;
+ * cosine-distributed directions make AO the usual cosine-weighted estimate.
+ * A ray that reaches the sky gives (0, 0, 0, 1).  1 <= K <=
+ * RT_MAX_AO_DIRECTIONS; scene, format and layout rules and errors as rt_bake.
+ * Asynchronous on `stream`; allocates nothing. */
+rt_status rt_bake_deferred(rt_ctx* ctx, int32_t obj_id, rt_surface surface, const rt_bake_scene* scene,
+                           const float* ao_dirs, int32_t K, rt_stream_t stream);
+
 /* Forward synthesis of F >= 0 fragments (Section 2, Eq. 1b, Eq. 3, the Note's
  * clamp), filtered with `filter` in FP32: out (device, F x 4 float, RGBA).
  * Spatial addressing clamps to the edge; nearest indices take floor (an exact

@@ -30,6 +30,7 @@ RT_WRAP_V = 4
 RT_ACCUMULATE = 1
 RT_DETERMINISTIC = 2
 RT_MAX_OBJECTS = 1024
+RT_MAX_AO_DIRECTIONS = 1024
 RT_SURFACE_SPHERE, RT_SURFACE_PLANE = range(2)
 
 
@@ -58,6 +59,7 @@ SIGNATURES = {
     "rt_read_texture": (_I32, [_P, _I32, _I32, _P, _P, _P]),
     "rt_fill_bucket_lobes": (_I32, [_P, _I32, _P, _P]),
     "rt_bake": (_I32, [_P, _I32, _I32, _P, _P]),
+    "rt_bake_deferred": (_I32, [_P, _I32, _I32, _P, _P, _I32, _P]),
     "rt_shade_world": (_I32, [_P, _P, _P, _P, _P, _I64, _I32, _P, _P]),
     "rt_bake_shadow": (_I32, [_P, _I32, _I32, _P, _P]),
     "rt_shade_multi": (_I32, [_P, _P, _P, _I32, _P, _I64, _I32, _P, _P]),

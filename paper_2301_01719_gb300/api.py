@@ -13,9 +13,10 @@ import torch
 
 from . import _lib
 from ._lib import (RT_ACCUMULATE, RT_ANGULAR_BILINEAR, RT_BF16, RT_BIT1, RT_BORROW, RT_E4M3_BUCKET_SCALE,  # noqa: F401
-                   RT_DETERMINISTIC, RT_ERR_BAD_OBJ_ID, RT_ERR_CUDA, RT_ERR_INVALID_ARG, RT_ERR_NONFINITE, RT_ERR_OOM, RT_ERR_TIMEOUT,
-                   RT_ERR_UNSUPPORTED, RT_F16, RT_F32, RT_LAYOUT_ATLAS, RT_LAYOUT_PALETTE, RT_LAYOUT_PLANES, RT_MAX_OBJECTS, RT_NEAREST,
-                   RT_OK, RT_QUADRILINEAR, RT_SURFACE_PLANE, RT_SURFACE_SPHERE, RT_WRAP_U, RT_WRAP_V, RadtexError)
+                   RT_DETERMINISTIC, RT_ERR_BAD_OBJ_ID, RT_ERR_CUDA, RT_ERR_INVALID_ARG, RT_ERR_NONFINITE, RT_ERR_OOM,
+                   RT_ERR_TIMEOUT, RT_ERR_UNSUPPORTED, RT_F16, RT_F32, RT_LAYOUT_ATLAS, RT_LAYOUT_PALETTE,
+                   RT_LAYOUT_PLANES, RT_MAX_AO_DIRECTIONS, RT_MAX_OBJECTS, RT_NEAREST, RT_OK, RT_QUADRILINEAR,
+                   RT_SURFACE_PLANE, RT_SURFACE_SPHERE, RT_WRAP_U, RT_WRAP_V, RadtexError)
 
 FORMAT_BYTES = {RT_F32: 16, RT_F16: 8, RT_BF16: 8, RT_E4M3_BUCKET_SCALE: 4, RT_BIT1: 1 / 8}
 CODE_DTYPE = {RT_F32: torch.float32, RT_F16: torch.int16, RT_BF16: torch.int16, RT_E4M3_BUCKET_SCALE: torch.uint8,
@@ -292,6 +293,19 @@ def rt_bake(ctx: Context, obj_id: int, surface: int, scene: dict, stream=None) -
     S = bake_scene_struct(scene)
     dev = torch.device("cuda", ctx.device)
     _lib.call("rt_bake", ctx.handle, int(obj_id), int(surface), ctypes.byref(S), _stream(stream, dev))
+
+
+def rt_bake_deferred(ctx: Context, obj_id: int, surface: int, scene: dict, ao_dirs: torch.Tensor,
+                     stream=None) -> None:
+    """Bakes the deferred payload (unlit albedo and ambient occlusion of the reflected
+    ray's first hit) into object obj_id; ao_dirs: (K, 3) float32 local unit directions
+    on the object's device."""
+    S = bake_scene_struct(scene)
+    _check(ao_dirs, "ao_dirs", torch.float32, 3)
+    if ao_dirs.device != torch.device("cuda", ctx.device):
+        raise ValueError("ao_dirs must live on the context's device")
+    _lib.call("rt_bake_deferred", ctx.handle, int(obj_id), int(surface), ctypes.byref(S), _ptr(ao_dirs),
+              int(ao_dirs.numel() // 3), _stream(stream, ao_dirs.device))
 
 
 def _gbuffer(uv, dirs, obj):

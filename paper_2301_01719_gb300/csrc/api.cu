@@ -428,7 +428,21 @@ rt_status rt_bake(rt_ctx* ctx, int32_t obj_id, rt_surface surface, const rt_bake
     DeviceGuard g(ctx->device);
     if (!g.ok) return RT_ERR_CUDA;
     return cuda_status(rt::launch_bake(*scene, (int)surface, const_cast<void*>(d.base), ctx->scales[obj_id], d.W, d.H,
-                                       d.n, d.fmt, d.layout, (cudaStream_t)stream));
+                                       d.n, d.fmt, d.layout, nullptr, 0, (cudaStream_t)stream));
+}
+
+rt_status rt_bake_deferred(rt_ctx* ctx, int32_t obj_id, rt_surface surface, const rt_bake_scene* scene,
+                           const float* ao_dirs, int32_t K, rt_stream_t stream) {
+    if (!ctx || obj_id < 0 || obj_id >= RT_MAX_OBJECTS || !ctx->table[obj_id].live || !scene ||
+        (surface != RT_SURFACE_SPHERE && surface != RT_SURFACE_PLANE) || !valid_scene(scene) || !ao_dirs ||
+        K < 1 || K > RT_MAX_AO_DIRECTIONS || (reinterpret_cast<uintptr_t>(ao_dirs) & 3))
+        return RT_ERR_INVALID_ARG;
+    const TexDesc& d = ctx->table[obj_id];
+    if (d.layout == rt::kLayoutPalette || d.fmt == RT_BIT1) return RT_ERR_UNSUPPORTED;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    return cuda_status(rt::launch_bake(*scene, (int)surface, const_cast<void*>(d.base), ctx->scales[obj_id], d.W, d.H,
+                                       d.n, d.fmt, d.layout, ao_dirs, K, (cudaStream_t)stream));
 }
 
 static bool kmeans_source(rt_ctx* ctx, int32_t obj_id, int32_t K) {

@@ -90,6 +90,96 @@ __device__ __forceinline__ float4 trace(const rt_bake_scene& S, float3 P, float3
     return make_float4(g * C.x + (1.0f - g) * K.x, g * C.y + (1.0f - g) * K.y, g * C.z + (1.0f - g) * K.z, g);
 }
 
+// The sphere's entering root or the plane crossing at t > ray_offset.
+__device__ __forceinline__ bool occluded(const rt_bake_scene& S, float3 P, float3 d) {
+    const float3 c = mk(S.sphere_centre);
+    const float3 o = make_float3(P.x - c.x, P.y - c.y, P.z - c.z);
+    const float b = dot3(o, d);
+    const float q = dot3(o, o) - S.sphere_radius * S.sphere_radius;
+    const float disc = b * b - q;
+    if (disc > 0.0f && -b - sqrtf(disc) > S.ray_offset) return true;
+    return d.y != 0.0f && (S.plane_height - P.y) / d.y > S.ray_offset;
+}
+
+// Deferred payload (Section 1: ambient occlusion and reflections for deferred
+// rendering): the first hit X of the reflected ray, its unlit albedo and the
+// share of the K local directions (frame of the hit normal facing the ray, x
+// and y from the orthonormal basis of Duff et al., JCGT 6(1) 2017) that leave
+// X unblocked; (0, 0, 0, 1) when the ray reaches the sky.  An AO ray is tested
+// against the other surface only: leaving the plane into its normal's
+// half-space it cannot meet the plane again, nor leaving the convex sphere
+// outward the sphere.
+__device__ __forceinline__ float4 deferred_payload(const rt_bake_scene& S, float3 P, float3 d, const float3* dirs,
+                                                   int K) {
+    const float3 c = mk(S.sphere_centre);
+    const float3 o = make_float3(P.x - c.x, P.y - c.y, P.z - c.z);
+    const float b = dot3(o, d);
+    const float q = dot3(o, o) - S.sphere_radius * S.sphere_radius;
+    const float disc = b * b - q;
+    float tb = INFINITY;
+    int hit = -1;
+    if (disc > 0.0f) {
+        const float t = -b - sqrtf(disc);
+        if (t > S.ray_offset) {
+            tb = t;
+            hit = RT_SURFACE_SPHERE;
+        }
+    }
+    if (d.y != 0.0f) {
+        const float t = (S.plane_height - P.y) / d.y;
+        if (t > S.ray_offset && t < tb) {
+            tb = t;
+            hit = RT_SURFACE_PLANE;
+        }
+    }
+    if (hit < 0) return make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+    const float3 X = axpy(tb, d, P);
+    float3 N, alb;
+    if (hit == RT_SURFACE_SPHERE) {
+        const float ir = 1.0f / S.sphere_radius;
+        N = make_float3((X.x - c.x) * ir, (X.y - c.y) * ir, (X.z - c.z) * ir);
+        alb = mk(S.sphere_albedo);
+    } else {
+        N = make_float3(0.0f, d.y < 0.0f ? 1.0f : -1.0f, 0.0f);
+        alb = plane_albedo(S, X.x, X.z);
+    }
+    // basis (b1, b2, N), right-handed
+    const float sg = copysignf(1.0f, N.z);
+    const float a = -1.0f / (sg + N.z);
+    const float bb = N.x * N.y * a;
+    const float3 b1 = make_float3(fmaf(sg * N.x * N.x, a, 1.0f), sg * bb, -sg * N.x);
+    const float3 b2 = make_float3(bb, fmaf(N.y * N.y, a, sg), -N.y);
+    // Each test needs one component of the world direction b1 w.x + b2 w.y + N w.z
+    // along a fixed vector, so that vector is projected on the basis once per hit
+    // and a direction costs three FMAs; the tests are written without division
+    // or square root (the same decisions up to rounding at the threshold).
+    const float eps = S.ray_offset;
+    int vis = 0;
+    if (hit == RT_SURFACE_SPHERE) {
+        // only the plane can block: the crossing t = h / w_y lies beyond eps
+        const float h = S.plane_height - X.y;
+        for (int k = 0; k < K; ++k) {
+            const float3 w = dirs[k];
+            const float wy = fmaf(w.z, N.y, fmaf(w.y, b2.y, w.x * b1.y));
+            const float e = eps * wy;
+            vis += ((wy > 0.0f && h > e) || (wy < 0.0f && h < e)) ? 0 : 1;
+        }
+    } else {
+        // only the sphere can block: b = (X - c).w, entering root -b - sqrt(b^2 - q) > eps
+        const float3 oX = make_float3(X.x - c.x, X.y - c.y, X.z - c.z);
+        const float qX = dot3(oX, oX) - S.sphere_radius * S.sphere_radius;
+        const float o1 = dot3(oX, b1), o2 = dot3(oX, b2), o3 = dot3(oX, N);
+        for (int k = 0; k < K; ++k) {
+            const float3 w = dirs[k];
+            const float bw = fmaf(w.z, o3, fmaf(w.y, o2, w.x * o1));
+            const float dw = fmaf(bw, bw, -qX);  // the ray meets the sphere when dw > 0
+            const float m = -bw - eps;            // and enters ahead when m > sqrt(dw)
+            vis += (dw > 0.0f && m > 0.0f && m * m > dw) ? 0 : 1;
+        }
+    }
+    return make_float4(alb.x, alb.y, alb.z, (float)vis / (float)K);
+}
+
 // Surface point, frame and own colour at the centre of bucket (i, j).
 __device__ __forceinline__ Ray bucket_ray(const rt_bake_scene& S, int surface, int i, int j, int W, int H) {
     const float u = ((float)i + 0.5f) / (float)W, v = ((float)j + 0.5f) / (float)H;
@@ -118,8 +208,11 @@ __device__ __forceinline__ Ray bucket_ray(const rt_bake_scene& S, int surface, i
 
 // Texel p of the bucket with tangent-space reflection vector R (Eq. 4a then
 // Eq. 4b at the texel centre, from the block's table); d = R in world space.
-__device__ __forceinline__ float4 bake_texel(const rt_bake_scene& S, const Ray& r, float3 R) {
+// The radiance payload, or with K > 0 the deferred one over the K directions.
+__device__ __forceinline__ float4 bake_texel(const rt_bake_scene& S, const Ray& r, float3 R, const float3* dirs,
+                                             int K) {
     const float3 d = axpy(R.z, r.N, axpy(R.y, r.B, scale3(R.x, r.T)));
+    if (K > 0) return deferred_payload(S, r.P, d, dirs, K);
     const float4 tr = trace(S, r.P, d);
     return make_float4(fmaf(r.refl, tr.x, r.base.x), fmaf(r.refl, tr.y, r.base.y), fmaf(r.refl, tr.z, r.base.z),
                        tr.w);
@@ -134,11 +227,17 @@ __device__ __forceinline__ void texel_vector_table(float3* tab, int n) {
     __syncthreads();
 }
 
+// K = 0: radiance texels; K > 0: deferred payloads over the K local
+// directions ao_dirs (device, K x 3 floats), staged after the vector table.
 template <int FMT, int LAYOUT>
 __global__ void __launch_bounds__(kBakeThreads) bake_kernel(rt_bake_scene S, int surface, void* __restrict__ dst,
-                                                            float* __restrict__ scale, int W, int H, int n) {
+                                                            float* __restrict__ scale, int W, int H, int n,
+                                                            const float* __restrict__ ao_dirs, int K) {
     extern __shared__ float3 Rtab[];
-    texel_vector_table<true>(Rtab, n);
+    float3* dirs = Rtab + n * n;
+    for (int k = threadIdx.x; k < K; k += blockDim.x)
+        dirs[k] = make_float3(ao_dirs[3 * k], ao_dirs[3 * k + 1], ao_dirs[3 * k + 2]);
+    texel_vector_table<true>(Rtab, n);  // ends with the block barrier
     const int64_t b = (int64_t)blockIdx.x * kBakeThreads + threadIdx.x;
     if (b >= (int64_t)W * H) return;
     const int j = (int)(b / W), i = (int)(b - (int64_t)j * W);
@@ -149,13 +248,13 @@ __global__ void __launch_bounds__(kBakeThreads) bake_kernel(rt_bake_scene S, int
     float sc = 1.0f;
     if (FMT == RT_E4M3_BUCKET_SCALE) {
         float amax = 0.0f;
-        for (int p = 0; p < planes; ++p) amax = fmaxf(amax, amax4(bake_texel(S, r, Rtab[p])));
+        for (int p = 0; p < planes; ++p) amax = fmaxf(amax, amax4(bake_texel(S, r, Rtab[p], dirs, K)));
         sc = bucket_scale(amax);
         scale[b] = sc;
     }
     for (int p = p0; p < p1; ++p) {
         const int t = p / n, s = p - t * n;
-        const float4 v = bake_texel(S, r, Rtab[p]);
+        const float4 v = bake_texel(S, r, Rtab[p], dirs, K);
         const int64_t idx = index_in(LAYOUT, W, H, n, i, j, s, t);
         if (FMT == RT_F32)
             reinterpret_cast<float4*>(dst)[idx] = v;
@@ -170,7 +269,7 @@ __global__ void __launch_bounds__(kBakeThreads) bake_kernel(rt_bake_scene S, int
 
 template <int FMT, int LAYOUT>
 static cudaError_t launch_bake_t(const rt_bake_scene& S, int surface, void* dst, float* scale, int W, int H, int n,
-                                 cudaStream_t stream) {
+                                 const float* ao_dirs, int K, cudaStream_t stream) {
     const int64_t buckets = (int64_t)W * H;
     const unsigned gx = (unsigned)((buckets + kBakeThreads - 1) / kBakeThreads);
     // enough blocks for 8 per SM; E4M3 needs the whole bucket in one thread
@@ -183,26 +282,33 @@ static cudaError_t launch_bake_t(const rt_bake_scene& S, int surface, void* dst,
         if ((int64_t)gx < want) gy = (unsigned)((want + gx - 1) / gx);
         if (gy > (unsigned)(n * n)) gy = (unsigned)(n * n);
     }
-    const size_t smem = sizeof(float3) * (size_t)n * n;
-    bake_kernel<FMT, LAYOUT><<<dim3(gx, gy), kBakeThreads, smem, stream>>>(S, surface, dst, scale, W, H, n);
+    const size_t smem = sizeof(float3) * ((size_t)n * n + (size_t)K);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(bake_kernel<FMT, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    bake_kernel<FMT, LAYOUT><<<dim3(gx, gy), kBakeThreads, smem, stream>>>(S, surface, dst, scale, W, H, n, ao_dirs,
+                                                                            K);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bake(const rt_bake_scene& S, int surface, void* dst, float* scale, int W, int H, int n, int fmt,
-                        int layout, cudaStream_t stream) {
+                        int layout, const float* ao_dirs, int K, cudaStream_t stream) {
     if (layout == RT_LAYOUT_ATLAS) {
         if (fmt != RT_F32) return cudaErrorInvalidValue;
-        return launch_bake_t<RT_F32, RT_LAYOUT_ATLAS>(S, surface, dst, scale, W, H, n, stream);
+        return launch_bake_t<RT_F32, RT_LAYOUT_ATLAS>(S, surface, dst, scale, W, H, n, ao_dirs, K, stream);
     }
     switch (fmt) {
         case RT_F32:
-            return launch_bake_t<RT_F32, RT_LAYOUT_PLANES>(S, surface, dst, scale, W, H, n, stream);
+            return launch_bake_t<RT_F32, RT_LAYOUT_PLANES>(S, surface, dst, scale, W, H, n, ao_dirs, K, stream);
         case RT_F16:
-            return launch_bake_t<RT_F16, RT_LAYOUT_PLANES>(S, surface, dst, scale, W, H, n, stream);
+            return launch_bake_t<RT_F16, RT_LAYOUT_PLANES>(S, surface, dst, scale, W, H, n, ao_dirs, K, stream);
         case RT_BF16:
-            return launch_bake_t<RT_BF16, RT_LAYOUT_PLANES>(S, surface, dst, scale, W, H, n, stream);
+            return launch_bake_t<RT_BF16, RT_LAYOUT_PLANES>(S, surface, dst, scale, W, H, n, ao_dirs, K, stream);
         default:
-            return launch_bake_t<RT_E4M3_BUCKET_SCALE, RT_LAYOUT_PLANES>(S, surface, dst, scale, W, H, n, stream);
+            return launch_bake_t<RT_E4M3_BUCKET_SCALE, RT_LAYOUT_PLANES>(S, surface, dst, scale, W, H, n, ao_dirs, K,
+                                                                         stream);
     }
 }
 
@@ -213,17 +319,6 @@ cudaError_t launch_bake(const rt_bake_scene& S, int surface, void* dst, float* s
 // the sky.  One thread per 32-bit word of the PLANES bit numbering, so every
 // word is written once, whole.
 // ---------------------------------------------------------------------------
-
-// The sphere's entering root or the plane crossing at t > ray_offset.
-__device__ __forceinline__ bool occluded(const rt_bake_scene& S, float3 P, float3 d) {
-    const float3 c = mk(S.sphere_centre);
-    const float3 o = make_float3(P.x - c.x, P.y - c.y, P.z - c.z);
-    const float b = dot3(o, d);
-    const float q = dot3(o, o) - S.sphere_radius * S.sphere_radius;
-    const float disc = b * b - q;
-    if (disc > 0.0f && -b - sqrtf(disc) > S.ray_offset) return true;
-    return d.y != 0.0f && (S.plane_height - P.y) / d.y > S.ray_offset;
-}
 
 // Surface point and frame of bucket (i, j) (the geometry of bucket_ray).
 __device__ __forceinline__ void bucket_frame(const rt_bake_scene& S, int surface, int i, int j, int W, int H,

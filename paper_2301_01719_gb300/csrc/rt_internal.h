@@ -103,7 +103,7 @@ cudaError_t launch_kmeans_update(const TexDesc& d, int K, const uint32_t* index,
                                  unsigned* status, cudaStream_t stream);
 cudaError_t launch_check_index(const uint32_t* index, int64_t count, uint32_t K, unsigned* bad, cudaStream_t stream);
 cudaError_t launch_bake(const rt_bake_scene& S, int surface, void* dst, float* scale, int W, int H, int n, int fmt,
-                        int layout, cudaStream_t stream);
+                        int layout, const float* ao_dirs, int K, cudaStream_t stream);
 cudaError_t launch_fill_lobes(const float* params, void* dst, float* scale, int W, int H, int n, int fmt,
                               cudaStream_t stream);
 cudaError_t launch_convert(const float* src, int src_layout, float* dst, int dst_layout, int W, int H, int n,

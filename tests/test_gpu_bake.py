@@ -63,12 +63,12 @@ def decode(fmt, codes, scales, n):
     return oracle.decode(oracle.E4M3, codes) * s, s
 
 
-def check(gpu, val, lo, hi, fmt, scale=None):
+def check(gpu, val, lo, hi, fmt, scale=None, jump=JUMP, band_max=BAND_MAX):
     """Returns the fraction of band texels; asserts the per-texel bounds."""
     if scale is None:
         scale = np.zeros_like(val)
     M = np.maximum(hi - val, val - lo).max(axis=-1, keepdims=True)
-    band = (M > JUMP)[..., 0]
+    band = (M > jump)[..., 0]
     q = quant_bound(fmt, np.maximum(np.abs(lo), np.abs(hi)), scale)
     tol = TOL + M / 4 + q * (1 + TOL)
     err = np.abs(gpu - val)
@@ -79,7 +79,7 @@ def check(gpu, val, lo, hi, fmt, scale=None):
     widened = TOL + q
     inside = (gpu >= lo - widened) & (gpu <= hi + widened)
     assert inside[band].all(), f"{(~inside[band]).sum()} band texels outside their perturbed range"
-    assert band.mean() < BAND_MAX, band.mean()
+    assert band.mean() < band_max, band.mean()
     return float(band.mean())
 
 
