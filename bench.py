@@ -54,6 +54,8 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--samples", type=int, default=4, help="shadow: light samples per fragment")
+    p.add_argument("--fused", action="store_true",
+                   help="the step as one fused forward + L2 loss (zero target) + backward launch")
     p.add_argument("--deferred", type=int, default=0,
                    help="bake: the deferred payload (albedo + ambient occlusion) over this many AO directions")
     p.add_argument("--workload", choices=["sphere-plane", "voronoi64", "bake", "world", "shadow"],
@@ -179,7 +181,8 @@ def measured_peak():
 
 
 # The sources the forward and backward shading kernels are compiled from.
-SHADING_SOURCES = ("backward.cu", "launch.h", "rt_device.cuh", "rt_filter.cuh", "rt_internal.h", "shade.cu")
+SHADING_SOURCES = ("backward.cu", "fused.cu", "launch.h", "rt_backward.cuh", "rt_device.cuh", "rt_filter.cuh",
+                   "rt_internal.h", "shade.cu")
 
 
 def kernel_source_hash() -> str:
@@ -447,6 +450,11 @@ def run_radtex(a):
     index_bytes = sum(4 * a.buckets * a.buckets for _ in oids) if a.palette else 0  # whole index maps, an upper bound
     fwd_bytes = 40 * F + distinct * tb + scale_bytes + index_bytes
     bwd_bytes = (24 + 16 + 8 + 12) * F + distinct * (tb + 32) + scale_bytes + index_bytes
+    # the fused step: G-buffer and target in, colour and UV / direction gradients out, each texel read and its
+    # gradient read-modified-written once
+    fused_bytes = (24 + 16 + 16 + 8 + 12) * F + distinct * (tb + 32) + scale_bytes + index_bytes
+    target = torch.zeros_like(out) if a.fused else None
+    sums = torch.zeros(2, dtype=torch.float64, device=dev)
 
     stream = torch.cuda.current_stream(dev)
     # screen tile of the batched kernels, picked by the library's autotuner on this workload
@@ -458,6 +466,12 @@ def run_radtex(a):
                                                reps=2)
 
     def step():
+        if a.fused:
+            for t in dtex.values():
+                t.zero_()
+            api.rt_shade_batched_l2_step(ctx, uv, dirs, obj, filt, target, 1.0, out, sums, dtex, duv, ddir,
+                                         api.RT_ACCUMULATE)
+            return
         api.rt_shade_batched(ctx, uv, dirs, obj, filt, out)
         for t in dtex.values():
             t.zero_()
@@ -482,12 +496,17 @@ def run_radtex(a):
         for k in range(a.steps):
             e = ev[k]
             e[0].record(stream)
-            api.rt_shade_batched(ctx, uv, dirs, obj, filt, out)
+            if not a.fused:
+                api.rt_shade_batched(ctx, uv, dirs, obj, filt, out)
             e[1].record(stream)
             for t in dtex.values():
                 t.zero_()
             e[2].record(stream)
-            api.rt_shade_batched_backward(ctx, uv, dirs, obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE)
+            if a.fused:
+                api.rt_shade_batched_l2_step(ctx, uv, dirs, obj, filt, target, 1.0, out, sums, dtex, duv, ddir,
+                                             api.RT_ACCUMULATE)
+            else:
+                api.rt_shade_batched_backward(ctx, uv, dirs, obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE)
             e[3].record(stream)
         end.record(stream)
         torch.cuda.synchronize()
@@ -536,9 +555,14 @@ def run_radtex(a):
                     arrived = torch.cuda.Event()
                     arrived.record(s_in)
                 comp.wait_event(arrived)
-                api.rt_shade_batched(ctx, d_uv[lo:hi], d_dir[lo:hi], d_obj[lo:hi], filt, out[lo:hi])
-                api.rt_shade_batched_backward(ctx, d_uv[lo:hi], d_dir[lo:hi], d_obj[lo:hi], filt, out[lo:hi],
-                                              dtex, duv[lo:hi], ddir[lo:hi], api.RT_ACCUMULATE)
+                if a.fused:
+                    api.rt_shade_batched_l2_step(ctx, d_uv[lo:hi], d_dir[lo:hi], d_obj[lo:hi], filt, target[lo:hi],
+                                                 1.0, out[lo:hi], sums, dtex, duv[lo:hi], ddir[lo:hi],
+                                                 api.RT_ACCUMULATE)
+                else:
+                    api.rt_shade_batched(ctx, d_uv[lo:hi], d_dir[lo:hi], d_obj[lo:hi], filt, out[lo:hi])
+                    api.rt_shade_batched_backward(ctx, d_uv[lo:hi], d_dir[lo:hi], d_obj[lo:hi], filt, out[lo:hi],
+                                                  dtex, duv[lo:hi], ddir[lo:hi], api.RT_ACCUMULATE)
                 shaded = torch.cuda.Event()
                 shaded.record(comp)
                 consumed[j] = shaded
@@ -565,7 +589,7 @@ def run_radtex(a):
         del h_out
 
     peak, peak_kind = measured_peak()
-    fwd_gbs = fwd_bytes / (fwd_ms * 1e-3) / 1e9
+    fwd_gbs = fwd_bytes / (fwd_ms * 1e-3) / 1e9 if not a.fused else None
     bwd_gbs = bwd_bytes / (bwd_ms * 1e-3) / 1e9
     wl = workload_name(a)
 
@@ -574,9 +598,13 @@ def run_radtex(a):
                 "traffic": recorded_traffic(kernel, wl), "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": int(nbytes), "kernel": kernel}
 
-    r_fwd = roof(fwd_gbs, f"shade_kernel<{a.filter}, tiled>", fwd_bytes)
-    r_bwd = roof(bwd_gbs, f"backward_kernel<{a.filter}, tiled>", bwd_bytes)
-    dominant = r_bwd if bwd_ms >= fwd_ms else r_fwd
+    if a.fused:
+        r_fwd = r_bwd = None
+        dominant = roof(fused_bytes / (bwd_ms * 1e-3) / 1e9, f"fused_l2_kernel<{a.filter}, tiled>", fused_bytes)
+    else:
+        r_fwd = roof(fwd_gbs, f"shade_kernel<{a.filter}, tiled>", fwd_bytes)
+        r_bwd = roof(bwd_gbs, f"backward_kernel<{a.filter}, tiled>", bwd_bytes)
+        dominant = r_bwd if bwd_ms >= fwd_ms else r_fwd
 
     result = {
         "metric": METRIC, "value": value, "unit": "Gfrag/s", "n_gpus": world, "steps": a.steps,
@@ -587,17 +615,21 @@ def run_radtex(a):
                    "objects": len(oids), "texture_bytes": int(sum(api.rt_texture_info(ctx, o)["bytes"] for o in oids)),
                    "l2": "inputs larger than L2 (G-buffer %.1f GB, textures %.1f GB per rank)" % (
                        24 * F / 1e9, sum(api.rt_texture_info(ctx, o)["bytes"] for o in oids) / 1e9),
-                   "step": ("rt_shade_batched + zero texel grads + rt_shade_batched_backward(RT_ACCUMULATE, "
+                   "step": ("zero texel grads + rt_shade_batched_l2_step(target 0, scale 1, RT_ACCUMULATE): "
+                            "forward, dL/dout = out, backward in one launch" if a.fused else
+                            "rt_shade_batched + zero texel grads + rt_shade_batched_backward(RT_ACCUMULATE, "
                             "dL/dout = out)"),
                    "tile": {"tw": tile[0], "th": tile[1], "bx": tile[2], "by": tile[3], "autotune_ms": tile_ms},
                    "backward_tile": {"tw": btile[0], "th": btile[1], "bx": btile[2], "by": btile[3],
                                      "autotune_ms": btile_ms},
                    "distinct_texels_per_step": int(distinct), "scene_gen_s": round(scene_s, 2),
                    "palette": palette},
-        "fwd_gfrag_s": F / (fwd_ms * 1e-3) / 1e9, "bwd_gfrag_s": F / (bwd_ms * 1e-3) / 1e9,
-        "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "zero_grad_ms": zero_ms,
+        **({"fused_ms": bwd_ms, "fused_gfrag_s": F / (bwd_ms * 1e-3) / 1e9} if a.fused else
+           {"fwd_gfrag_s": F / (fwd_ms * 1e-3) / 1e9, "bwd_gfrag_s": F / (bwd_ms * 1e-3) / 1e9,
+            "fwd_ms": fwd_ms, "bwd_ms": bwd_ms}),
+        "zero_grad_ms": zero_ms,
         "roofline": dominant, "roofline_fwd": r_fwd, "roofline_bwd": r_bwd,
-        "gpu_launches": 2 * a.steps,
+        "gpu_launches": (1 if a.fused else 2) * a.steps,
         "clocks": clk.summary(),
         "e2e": e2e,
     }

@@ -378,6 +378,26 @@ rt_status rt_shade_batched_backward(rt_ctx* ctx, const float* uv, const float* d
                                     float* const* dL_dtex, int32_t n_dtex, float* dL_duv, float* dL_ddir,
                                     int32_t flags, rt_stream_t stream);
 
+/* One fused training step of the batched synthesis under an L2 loss: for every
+ * fragment, the colour of rt_shade_batched (written to `out` when non-NULL),
+ * dL/dout = scale (out - target) on fragments with obj >= 0 as rt_l2_loss_grad
+ * forms it (the same FP32 roundings), sums (device, 2 doubles, 8-byte aligned,
+ * may be NULL) accumulating the sum of |out - target|^2 and the count of those
+ * fragments (the caller zeroes it), and the gradients of
+ * rt_shade_batched_backward for that dL/dout (dL_dtex ... flags as there).
+ * Equivalent to rt_shade_batched, rt_l2_loss_grad and
+ * rt_shade_batched_backward in sequence (colours and UV / direction gradients
+ * bit-identical, texel gradients up to the order of FP32 atomic additions,
+ * sums up to the order of FP64 additions), in one pass: the G-buffer and target
+ * are read once and each fragment's taps are gathered once.  target (device,
+ * views x height x width x 4 floats, 16-byte aligned) is required when there
+ * are fragments; scale finite.  Uses the backward's tile (rt_set_backward_tile,
+ * rt_autotune_backward).  Asynchronous on `stream`. */
+rt_status rt_shade_batched_l2_step(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int32_t views,
+                                   int32_t height, int32_t width, rt_filter filter, const float* target, float scale,
+                                   float* out, double* sums, float* const* dL_dtex, int32_t n_dtex, float* dL_duv,
+                                   float* dL_ddir, int32_t flags, rt_stream_t stream);
+
 /* Sets the screen tile of the batched kernels for `filter`, forward and
  * backward: warp tiles of tw x th fragments (tw * th = 32, tw a multiple of 4)
  * arranged bx x by in a block tile (bx * by = 4).  The default is 8 x 4,

@@ -78,6 +78,8 @@ SIGNATURES = {
     "rt_shade_batched": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, _P]),
     "rt_shade_batched_backward": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, ctypes.POINTER(_P), _I32, _P,
                                          _P, _I32, _P]),
+    "rt_shade_batched_l2_step": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, ctypes.c_float, _P, _P,
+                                        ctypes.POINTER(_P), _I32, _P, _P, _I32, _P]),
     "rt_prepare_deterministic": (_I32, [_P]),
     "rt_set_tile": (_I32, [_P, _I32, _I32, _I32, _I32, _I32]),
     "rt_set_backward_tile": (_I32, [_P, _I32, _I32, _I32, _I32, _I32]),

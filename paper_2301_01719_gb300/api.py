@@ -365,6 +365,29 @@ def rt_shade_batched_backward(ctx: Context, uv, dirs, obj, filter: int, dL_dout,
               _ptr(dL_dout), arr, n_dtex, _ptr(dL_duv), _ptr(dL_ddir), int(flags), _stream(stream, uv.device))
 
 
+def rt_shade_batched_l2_step(ctx: Context, uv, dirs, obj, filter: int, target, scale: float = 1.0, out=None,
+                             sums=None, dL_dtex=None, dL_duv=None, dL_ddir=None, flags: int = 0, stream=None):
+    """Fused forward + L2 loss + backward over (V, H, W) frames: writes `out` (if given),
+    adds sum |out - target|^2 and the shaded count to `sums` (float64 (2,), if given) and
+    the gradients of dL/dout = scale (out - target).  Returns out."""
+    F = _gbuffer(uv, dirs, obj)
+    V, H, W = _frames(uv, dirs, obj)
+    _check(target, "target", torch.float32, 4)
+    if target.numel() != 4 * F:
+        raise ValueError("target must hold V x H x W x 4 floats")
+    if out is not None:
+        _check(out, "out", torch.float32, 4)
+        if out.numel() != 4 * F:
+            raise ValueError("out must hold V x H x W x 4 floats")
+    if sums is not None and (sums.dtype != torch.float64 or sums.numel() < 2 or not sums.is_cuda):
+        raise TypeError("sums must be a CUDA float64 tensor of 2 elements")
+    arr, n_dtex = _grad_args(ctx, F, target, dL_dtex, dL_duv, dL_ddir)
+    _lib.call("rt_shade_batched_l2_step", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(obj), V, H, W, int(filter),
+              _ptr(target), float(scale), _ptr(out), _ptr(sums), arr, n_dtex, _ptr(dL_duv), _ptr(dL_ddir),
+              int(flags), _stream(stream, uv.device))
+    return out
+
+
 def rt_prepare_deterministic(ctx: Context) -> None:
     _lib.call("rt_prepare_deterministic", ctx.handle)
 

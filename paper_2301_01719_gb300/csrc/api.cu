@@ -528,11 +528,20 @@ rt_status rt_locate(rt_ctx* ctx, const float* uv, const float* dir, const int32_
 
 // nrm == NULL: tangent-space backward on tiling T; otherwise world-space
 // (Eq. 1a) on the flat stream, with dL/dN into dL_dnrm.
+// The L2 step's extra arguments: with them the backward pass is the fused
+// forward + loss + backward kernel, which forms dL/dout itself.
+struct FusedL2 {
+    const float* target;
+    float scale;
+    float* out;
+    double* sums;
+};
+
 static rt_status shade_backward_impl(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,
                                      rt_filter filter, const rt::Tiling& T, const float* dL_dout,
                                      float* const* dL_dtex, int32_t n_dtex, float* dL_duv, float* dL_ddir,
                                      int32_t flags, rt_stream_t stream, const float* nrm = nullptr,
-                                     float* dL_dnrm = nullptr) {
+                                     float* dL_dnrm = nullptr, const FusedL2* fused = nullptr) {
     if (!ctx || !valid_filter(filter)) return RT_ERR_INVALID_ARG;
     rt_status st = check_gbuffer(uv, dir, obj, F);
     if (st != RT_OK) return st;
@@ -541,7 +550,14 @@ static rt_status shade_backward_impl(rt_ctx* ctx, const float* uv, const float* 
     if (dL_dnrm && !aligned16(dL_dnrm)) return RT_ERR_INVALID_ARG;
     if (n_dtex < 0 || n_dtex > RT_MAX_OBJECTS || (n_dtex > 0 && !dL_dtex)) return RT_ERR_INVALID_ARG;
     if ((dL_duv && !aligned16(dL_duv)) || (dL_ddir && !aligned16(dL_ddir))) return RT_ERR_INVALID_ARG;
-    if (F > 0 && (!dL_dout || !aligned16(dL_dout))) return RT_ERR_INVALID_ARG;
+    if (fused) {
+        if (F > 0 && (!fused->target || !aligned16(fused->target))) return RT_ERR_INVALID_ARG;
+        if ((fused->out && !aligned16(fused->out)) || (reinterpret_cast<uintptr_t>(fused->sums) & 7) ||
+            !std::isfinite(fused->scale))
+            return RT_ERR_INVALID_ARG;
+    } else if (F > 0 && (!dL_dout || !aligned16(dL_dout))) {
+        return RT_ERR_INVALID_ARG;
+    }
     const bool accumulate = (flags & RT_ACCUMULATE) != 0;
     const bool deterministic = (flags & RT_DETERMINISTIC) != 0;
     rt::GradTable grads;
@@ -572,6 +588,10 @@ static rt_status shade_backward_impl(rt_ctx* ctx, const float* uv, const float* 
         if (nrm)
             e = rt::launch_world_backward(ctx->d_table, ctx->n_obj, uv, dir, nrm, obj, F, filter, dL_dout, grads, any,
                                           dL_duv, dL_ddir, dL_dnrm, accumulate, deterministic, ctx->d_status, s);
+        else if (fused)
+            e = rt::launch_fused_l2(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, T, ctx->spec, fused->target,
+                                    fused->scale, fused->out, fused->sums, grads, any, dL_duv, dL_ddir, accumulate,
+                                    deterministic, ctx->d_status, s);
         else
             e = rt::launch_backward(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, T, ctx->spec, dL_dout, grads, any,
                                     dL_duv, dL_ddir, accumulate, deterministic, ctx->d_status, s);
@@ -753,6 +773,20 @@ rt_status rt_shade_batched_backward(rt_ctx* ctx, const float* uv, const float* d
     if (F > 0 && !frames_tiling(ctx, kBackward, views, height, width, filter, &T)) return RT_ERR_INVALID_ARG;
     return shade_backward_impl(ctx, uv, dir, obj, F, filter, T, dL_dout, dL_dtex, n_dtex, dL_duv, dL_ddir, flags,
                                stream);
+}
+
+rt_status rt_shade_batched_l2_step(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int32_t views,
+                                   int32_t height, int32_t width, rt_filter filter, const float* target, float scale,
+                                   float* out, double* sums, float* const* dL_dtex, int32_t n_dtex, float* dL_duv,
+                                   float* dL_ddir, int32_t flags, rt_stream_t stream) {
+    if (!ctx || !valid_filter(filter) || views < 0 || height < 0 || width < 0 || height > 65536 || width > 65536)
+        return RT_ERR_INVALID_ARG;
+    const int64_t F = (int64_t)views * height * width;
+    rt::Tiling T = rt::flat_tiling();
+    if (F > 0 && !frames_tiling(ctx, kBackward, views, height, width, filter, &T)) return RT_ERR_INVALID_ARG;
+    const FusedL2 fused = {target, scale, out, sums};
+    return shade_backward_impl(ctx, uv, dir, obj, F, filter, T, nullptr, dL_dtex, n_dtex, dL_duv, dL_ddir, flags,
+                               stream, nullptr, nullptr, &fused);
 }
 
 rt_status rt_prepare_deterministic(rt_ctx* ctx) {

@@ -7,280 +7,10 @@
 // rule through the nested lerps, the Note's clamp (zero derivative where a
 // coordinate is clamped), Eq. 3 and Eq. 1b.
 #include "launch.h"
-#include "rt_device.cuh"
-#include "rt_filter.cuh"
+#include "rt_backward.cuh"
 #include "rt_internal.h"
 
 namespace rt {
-
-constexpr int kBackThreads = 128;
-constexpr int kBackWarps = kBackThreads / 32;
-
-struct CoordGrad {
-    float gu, gv, gs, gt;  // dL/d(weight coordinate) of the u, v, s, t axes
-};
-
-// Deterministic mode: each contribution w g_c is rounded once to a signed
-// 64-bit fixed-point number with 32 fractional bits and added with integer
-// atomics, which are associative, so the sums do not depend on the order in
-// which fragments arrive.
-constexpr float kFixedScale = 4294967296.0f;  // 2^32
-
-__device__ __forceinline__ void red_add_fixed4(unsigned long long* addr, float4 v) {
-    atomicAdd(addr + 0, (unsigned long long)__float2ll_rn(v.x * kFixedScale));
-    atomicAdd(addr + 1, (unsigned long long)__float2ll_rn(v.y * kFixedScale));
-    atomicAdd(addr + 2, (unsigned long long)__float2ll_rn(v.z * kFixedScale));
-    atomicAdd(addr + 3, (unsigned long long)__float2ll_rn(v.w * kFixedScale));
-}
-
-// QUADRILINEAR on the PLANES layout: the four in-bucket texels select four
-// planes (64-bit bases), the four buckets four spatial offsets (32-bit), shared
-// by the 16 reductions and the 16 loads.
-template <int FMT, int LAYOUT, bool DET>
-__device__ __forceinline__ CoordGrad backward_quadrilinear_planes(const TexDesc& d, const Lookup<RT_QUADRILINEAR>& L,
-                                                                  float4 g, void* grad, bool coord_grads) {
-    const int64_t P = d.plane;
-    const int64_t p00 = (int64_t)(L.t.k0 * d.n + L.s.k0) * P;
-    const int64_t ds = (int64_t)(L.s.k1 - L.s.k0) * P, dt = (int64_t)(L.t.k1 - L.t.k0) * d.n * P;
-    const int64_t pl[4] = {p00, p00 + ds, p00 + dt, p00 + dt + ds};  // (s0,t0) (s1,t0) (s0,t1) (s1,t1)
-    const int o[4] = {bucket_slot<LAYOUT>(d, L.u.k0, L.v.k0), bucket_slot<LAYOUT>(d, L.u.k1, L.v.k0),
-                      bucket_slot<LAYOUT>(d, L.u.k0, L.v.k1),
-                      bucket_slot<LAYOUT>(d, L.u.k1, L.v.k1)};  // (u0,v0) (u1,v0) (u0,v1) (u1,v1)
-    const float wu[2] = {1.f - L.u.w, L.u.w}, wv[2] = {1.f - L.v.w, L.v.w};
-    const float ws[2] = {1.f - L.s.w, L.s.w}, wt[2] = {1.f - L.t.w, L.t.w};
-    if (DET) {
-        if (grad) {
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float w = wu[b & 1] * wv[b >> 1] * ws[k & 1] * wt[k >> 1];
-                    if (w == 0.f) continue;
-                    const int64_t idx = pl[k] + o[b];
-                    red_add_fixed4(static_cast<unsigned long long*>(grad) + 4 * idx,
-                                   make_float4(w * g.x, w * g.y, w * g.z, w * g.w));
-                }
-        }
-    } else {
-        // Neighbouring fragments often update the same texel through the same
-        // tap: lanes 2m and 2m + 1 (horizontal neighbours on screen) compare
-        // their tap addresses, and on a match the odd lane hands its
-        // contribution to the even lane, which issues one reduction for both.
-        const unsigned active = __activemask();
-        const int lane = threadIdx.x & 31;
-        const bool partner = (active >> (lane ^ 1)) & 1u;
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float w = grad ? wu[b & 1] * wv[b >> 1] * ws[k & 1] * wt[k >> 1] : 0.f;
-                const int64_t idx = pl[k] + o[b];
-                float* addr = grad ? static_cast<float*>(grad) + 4 * idx : nullptr;
-                // a lane with nothing to add gets a key no other lane has
-                const unsigned long long key =
-                    w != 0.f ? (unsigned long long)addr : (~0ull - (unsigned long long)lane);
-                float4 c = make_float4(w * g.x, w * g.y, w * g.z, w * g.w);
-                const unsigned klo = (unsigned)key, khi = (unsigned)(key >> 32);
-                const unsigned plo = __shfl_xor_sync(active, klo, 1), phi = __shfl_xor_sync(active, khi, 1);
-                const float px = __shfl_xor_sync(active, c.x, 1), py = __shfl_xor_sync(active, c.y, 1);
-                const float pz = __shfl_xor_sync(active, c.z, 1), pw = __shfl_xor_sync(active, c.w, 1);
-                const bool same = partner && plo == klo && phi == khi;
-                if (same && (lane & 1)) continue;  // handed to the even lane
-                if (same) {
-                    c.x += px;
-                    c.y += py;
-                    c.z += pz;
-                    c.w += pw;
-                }
-                if (w != 0.f) red_add_v4(addr, c);
-            }
-    }
-    CoordGrad cg = {0.f, 0.f, 0.f, 0.f};
-    if (!coord_grads) return cg;
-    const f32x2 g_rg = pack2(g.x, g.y), g_ba = pack2(g.z, g.w);
-    auto lerpf = [](float a, float b, float w) { return fmaf(w, b - a, a); };
-    float c[4], cs[4], ct[4];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        const float sc = FMT == RT_E4M3_BUCKET_SCALE ? __ldg(d.scale + o[b]) : 1.0f;
-        float p[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const P4 T = load_texelP<FMT>(d.base, pl[k] + o[b], sc);
-            f32x2 q;
-            asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(q) : "l"(T.rg), "l"(g_rg));
-            asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(q) : "l"(T.ba), "l"(g_ba), "l"(q));
-            const float2 h = unpack2(q);
-            p[k] = h.x + h.y;
-        }
-        const float x0 = lerpf(p[0], p[1], L.s.w), x1 = lerpf(p[2], p[3], L.s.w);
-        c[b] = lerpf(x0, x1, L.t.w);
-        cs[b] = lerpf(p[1] - p[0], p[3] - p[2], L.t.w);
-        ct[b] = x1 - x0;
-    }
-    cg.gu = lerpf(c[1] - c[0], c[3] - c[2], L.v.w);
-    cg.gv = lerpf(c[2], c[3], L.u.w) - lerpf(c[0], c[1], L.u.w);
-    cg.gs = lerpf(lerpf(cs[0], cs[1], L.u.w), lerpf(cs[2], cs[3], L.u.w), L.v.w);
-    cg.gt = lerpf(lerpf(ct[0], ct[1], L.u.w), lerpf(ct[2], ct[3], L.u.w), L.v.w);
-    return cg;
-}
-
-template <int FILTER, int FMT, int LAYOUT, bool DET>
-__device__ __forceinline__ CoordGrad backward_taps(const TexDesc& d, const Lookup<FILTER>& L, float4 g, void* grad,
-                                                   bool coord_grads) {
-    CoordGrad cg = {0.f, 0.f, 0.f, 0.f};
-    const float wu[2] = {1.f - L.u.w, L.u.w}, wv[2] = {1.f - L.v.w, L.v.w};
-    const float ws[2] = {1.f - L.s.w, L.s.w}, wt[2] = {1.f - L.t.w, L.t.w};
-    if (grad) {
-        const int nu = FILTER == RT_QUADRILINEAR ? 2 : 1;
-        const int ns = FILTER == RT_NEAREST ? 1 : 2;
-        for (int b = 0; b < nu; ++b)
-            for (int a = 0; a < nu; ++a)
-                for (int q = 0; q < ns; ++q)
-                    for (int p = 0; p < ns; ++p) {
-                        float w = (nu == 2 ? wu[a] * wv[b] : 1.f) * (ns == 2 ? ws[p] * wt[q] : 1.f);
-                        if (w == 0.f) continue;
-                        int64_t idx = texel_index<LAYOUT>(d, a ? L.u.k1 : L.u.k0, b ? L.v.k1 : L.v.k0,
-                                                          p ? L.s.k1 : L.s.k0, q ? L.t.k1 : L.t.k0);
-                        const float4 c = make_float4(w * g.x, w * g.y, w * g.z, w * g.w);
-                        if (DET)
-                            red_add_fixed4(static_cast<unsigned long long*>(grad) + 4 * idx, c);
-                        else
-                            red_add_v4(static_cast<float*>(grad) + 4 * idx, c);
-                    }
-    }
-    if (FILTER == RT_NEAREST || !coord_grads) return cg;
-    // Coordinate gradients need only g . T per texel: every derivative of the
-    // colour is a weighted sum of texels, so each texel is projected onto g as
-    // soon as it is loaded and the lerps run on scalars.
-    const f32x2 g_rg = pack2(g.x, g.y), g_ba = pack2(g.z, g.w);
-    auto proj = [&](const P4& T) {
-        f32x2 p;
-        asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(p) : "l"(T.rg), "l"(g_rg));
-        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(p) : "l"(T.ba), "l"(g_ba), "l"(p));
-        const float2 q = unpack2(p);
-        return q.x + q.y;
-    };
-    auto lerpf = [](float a, float b, float w) { return fmaf(w, b - a, a); };
-    if (FILTER == RT_ANGULAR_BILINEAR) {
-        P4 t00, t10, t01, t11;
-        load_quadP<FMT, LAYOUT>(d, L.u.k0, L.v.k0, L.s, L.t, t00, t10, t01, t11);
-        const float p00 = proj(t00), p10 = proj(t10), p01 = proj(t01), p11 = proj(t11);
-        cg.gs = lerpf(p10 - p00, p11 - p01, L.t.w);
-        cg.gt = lerpf(p01, p11, L.s.w) - lerpf(p00, p10, L.s.w);
-        return cg;
-    }
-    // bucket (a, b) of the 2 x 2 spatial footprint: value c_ab, d/ds, d/dt (all projected on g)
-    float c[2][2], cs[2][2], ct[2][2];
-#pragma unroll
-    for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            P4 t00, t10, t01, t11;
-            load_quadP<FMT, LAYOUT>(d, a ? L.u.k1 : L.u.k0, b ? L.v.k1 : L.v.k0, L.s, L.t, t00, t10, t01, t11);
-            const float p00 = proj(t00), p10 = proj(t10), p01 = proj(t01), p11 = proj(t11);
-            const float x0 = lerpf(p00, p10, L.s.w), x1 = lerpf(p01, p11, L.s.w);
-            c[b][a] = lerpf(x0, x1, L.t.w);
-            cs[b][a] = lerpf(p10 - p00, p11 - p01, L.t.w);
-            ct[b][a] = x1 - x0;
-        }
-    cg.gu = lerpf(c[0][1] - c[0][0], c[1][1] - c[1][0], L.v.w);
-    cg.gv = lerpf(c[1][0], c[1][1], L.u.w) - lerpf(c[0][0], c[0][1], L.u.w);
-    cg.gs = lerpf(lerpf(cs[0][0], cs[0][1], L.u.w), lerpf(cs[1][0], cs[1][1], L.u.w), L.v.w);
-    cg.gt = lerpf(lerpf(ct[0][0], ct[0][1], L.u.w), lerpf(ct[1][0], ct[1][1], L.u.w), L.v.w);
-    return cg;
-}
-
-template <int FILTER, int FMT, int LAYOUT, bool DET>
-__device__ __forceinline__ CoordGrad backward_layout(const TexDesc& d, const Lookup<FILTER>& L, float4 g, void* grad,
-                                                     bool coord_grads) {
-    if constexpr (FILTER == RT_QUADRILINEAR && LAYOUT != RT_LAYOUT_ATLAS)
-        return backward_quadrilinear_planes<FMT, LAYOUT, DET>(d, L, g, grad, coord_grads);
-    else
-        return backward_taps<FILTER, FMT, LAYOUT, DET>(d, L, g, grad, coord_grads);
-}
-
-template <int FILTER, bool DET>
-__device__ __forceinline__ CoordGrad backward_any(const TexDesc& d, const Lookup<FILTER>& L, float4 g, void* grad,
-                                                  bool coord_grads) {
-    const bool pal = d.layout == kLayoutPalette;
-    switch (d.fmt) {
-        case RT_F16:
-            return pal ? backward_layout<FILTER, RT_F16, kLayoutPalette, DET>(d, L, g, grad, coord_grads)
-                       : backward_layout<FILTER, RT_F16, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
-        case RT_BF16:
-            return pal ? backward_layout<FILTER, RT_BF16, kLayoutPalette, DET>(d, L, g, grad, coord_grads)
-                       : backward_layout<FILTER, RT_BF16, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
-        case RT_BIT1:  // no texel gradients (rejected on the host); coordinate gradients only
-            return pal ? backward_layout<FILTER, RT_BIT1, kLayoutPalette, DET>(d, L, g, nullptr, coord_grads)
-                       : backward_layout<FILTER, RT_BIT1, RT_LAYOUT_PLANES, DET>(d, L, g, nullptr, coord_grads);
-        case RT_E4M3_BUCKET_SCALE:
-            return pal ? backward_layout<FILTER, RT_E4M3_BUCKET_SCALE, kLayoutPalette, DET>(d, L, g, grad, coord_grads)
-                       : backward_layout<FILTER, RT_E4M3_BUCKET_SCALE, RT_LAYOUT_PLANES, DET>(d, L, g, grad,
-                                                                                              coord_grads);
-        default:
-            if (d.layout == RT_LAYOUT_ATLAS)
-                return backward_layout<FILTER, RT_F32, RT_LAYOUT_ATLAS, DET>(d, L, g, grad, coord_grads);
-            return pal ? backward_layout<FILTER, RT_F32, kLayoutPalette, DET>(d, L, g, grad, coord_grads)
-                       : backward_layout<FILTER, RT_F32, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
-    }
-}
-
-// dL/dI from dL/dB through Eq. 3 and Eq. 1b.
-//  Eq. 3 (x branch, |A_x| >= |A_y|, q = A_y / A_x = I_y / I_x):
-//    dB/dA = [[1, q], [-q^3, 1 + 2 q^2]] / sqrt(1 + q^2)   (rows B_x, B_y)
-//  and symmetrically on the y branch; the identity at A = 0.
-//  Eq. 1b: dA_r/dI_c = sqrt(2) (delta_rc / D - I_r g_c / D^3), g = (I_x, I_y, I_z + 1), D = |g|.
-//  The same holds for any half-way vector h in place of g (Eq. 1a: h = I + N,
-//  and dA/dI = dA/dN = dA/dh).
-__device__ __forceinline__ float3 half_grad(float Ix, float Iy, float zp, float gBx, float gBy) {
-    float ax = fabsf(Ix), ay = fabsf(Iy);
-    float gAx, gAy;
-    if (!(fmaxf(ax, ay) >= 1e-30f)) {
-        gAx = gBx;
-        gAy = gBy;
-    } else if (ax >= ay) {
-        float q = Iy / Ix;
-        float r = 1.0f / sqrtf(fmaf(q, q, 1.0f));
-        gAx = (gBx - gBy * q * q * q) * r;
-        gAy = (gBx * q + gBy * fmaf(2.0f * q, q, 1.0f)) * r;
-    } else {
-        float p = Ix / Iy;
-        float r = 1.0f / sqrtf(fmaf(p, p, 1.0f));
-        gAy = (gBy - gBx * p * p * p) * r;
-        gAx = (gBy * p + gBx * fmaf(2.0f * p, p, 1.0f)) * r;
-    }
-    float D2 = Ix * Ix + Iy * Iy + zp * zp;
-    if (!(D2 > 1e-30f)) return make_float3(0.f, 0.f, 0.f);
-    float invD = 1.0f / sqrtf(D2);
-    float k = 1.41421356237f * invD;
-    float k3 = k * invD * invD;
-    float m = k3 * (gAx * Ix + gAy * Iy);
-    return make_float3(k * gAx - m * Ix, k * gAy - m * Iy, -m * zp);
-}
-
-__device__ __forceinline__ float3 direction_grad(float Ix, float Iy, float Iz, float gBx, float gBy) {
-    return half_grad(Ix, Iy, Iz + 1.0f, gBx, gBy);
-}
-
-// dL/du, dL/dv of a bilinear spatial lookup: zero where clamp to edge holds c fixed.
-__device__ __forceinline__ float2 uv_grad(const TexDesc& d, float u, float v, float gu, float gv) {
-    const float cu = fmaf(u, d.fW, -0.5f), cv = fmaf(v, d.fH, -0.5f);
-    float2 r;
-    r.x = ((d.wrap & 1) || (cu > -1.0f && cu < d.fW)) ? gu * d.fW : 0.f;
-    r.y = ((d.wrap & 2) || (cv > -1.0f && cv < d.fH)) ? gv * d.fH : 0.f;
-    return r;
-}
-
-// SPEC as in filter_spec: one format for every object, or -1 (dispatch).
-template <int FILTER, bool DET, int SPEC>
-__device__ __forceinline__ CoordGrad backward_spec(const TexDesc& d, const Lookup<FILTER>& L, float4 g, void* grad,
-                                                   bool coord_grads) {
-    if constexpr (SPEC < 0)
-        return backward_any<FILTER, DET>(d, L, g, grad, coord_grads);
-    else
-        return backward_layout<FILTER, SPEC, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
-}
 
 // The single-format tiled kernels are held to 80 registers (6 blocks, 24 warps
 // per SM): measured 3 % faster than 95 registers at 5 blocks.
@@ -301,34 +31,10 @@ __global__ void __launch_bounds__(kBackThreads, (TILED && !DET && SPEC >= 0) ? 6
             Lookup<FILTER> L = locate<FILTER, (SPEC < 0)>(d, q.u, q.v, q.x, q.y, q.z);
             void* grad = any_grad ? grads.p[q.o] : nullptr;
             CoordGrad cg = backward_spec<FILTER, DET, SPEC>(d, L, go, grad, coord_grads);
-            if (FILTER == RT_QUADRILINEAR) guv = uv_grad(d, q.u, q.v, cg.gu, cg.gv);
-            if (FILTER != RT_NEAREST && dL_ddir) {
-                float gBx = (L.B.x > -d.hi && L.B.x < d.hi) ? cg.gs * d.half_n : 0.f;
-                float gBy = (L.B.y > -d.hi && L.B.y < d.hi) ? cg.gt * d.half_n : 0.f;
-                gdir = direction_grad(q.x, q.y, q.z, gBx, gBy);
-            }
+            coord_grads_of<FILTER>(d, L, q, cg, dL_ddir != nullptr, guv, gdir);
         }
         if (f < 0) return;
-        if (dL_duv) {
-            float2* p = reinterpret_cast<float2*>(dL_duv) + f;
-            if (accumulate) {
-                float2 o = *p;
-                guv.x += o.x;
-                guv.y += o.y;
-            }
-            *p = guv;
-        }
-        if (dL_ddir) {
-            float* p = dL_ddir + 3 * f;
-            if (accumulate) {
-                gdir.x += p[0];
-                gdir.y += p[1];
-                gdir.z += p[2];
-            }
-            p[0] = gdir.x;
-            p[1] = gdir.y;
-            p[2] = gdir.z;
-        }
+        store_coord_grads(f, guv, gdir, dL_duv, dL_ddir, accumulate);
     });
 }
 

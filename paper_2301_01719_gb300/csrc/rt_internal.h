@@ -73,6 +73,11 @@ cudaError_t launch_backward(const TexDesc* table, int n_obj, const float* uv, co
                             int64_t F, int filter, const Tiling& T, int spec, const float* dL_dout,
                             const GradTable& grads, bool any_grad, float* dL_duv, float* dL_ddir, bool accumulate,
                             bool deterministic, unsigned* status, cudaStream_t stream);
+cudaError_t launch_fused_l2(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
+                            int64_t F, int filter, const Tiling& T, int spec, const float* target, float scale,
+                            float* out, double* sums, const GradTable& grads, bool any_grad, float* dL_duv,
+                            float* dL_ddir, bool accumulate, bool deterministic, unsigned* status,
+                            cudaStream_t stream);
 cudaError_t launch_fixed_to_float(const long long* acc, float* dst, int64_t count, bool accumulate,
                                   cudaStream_t stream);
 

@@ -111,3 +111,35 @@ def test_fullsize_backward(full):
     for got_c, ref_c in ((got_uv, guv), (got_dir, gdir)):
         scale = np.abs(ref_c[far]).max()
         assert np.all(np.abs(got_c[far] - ref_c[far]) <= 1e-3 * np.abs(ref_c[far]) + 1e-5 * scale)
+
+
+def test_fullsize_fused_l2_step(full):
+    """The benchmark's fused step (forward, L2 loss against a zero target and
+    backward in one kernel) at full size: its colours are rt_shade_batched's bit
+    for bit, its UV and direction gradients the unfused backward's for the
+    same dL/dout, its texel gradients satisfy the sum rule and the loss is the
+    sum of squared colours."""
+    ctx, uv, d, o, out = full["ctx"], full["uv"], full["d"], full["o"], full["out"]
+    dev = out.device
+    api.rt_autotune_backward(ctx, uv, d, o, api.RT_QUADRILINEAR, out, None, torch.empty_like(uv), None, 0, reps=1)
+    target = torch.zeros_like(out)
+    out2 = torch.empty_like(out)
+    sums = torch.zeros(2, dtype=torch.float64, device=dev)
+    dtex = {k: torch.zeros((N, N, BUCKETS, BUCKETS, 4), device=dev) for k in (0, 1)}
+    duv, ddir = torch.zeros_like(uv), torch.zeros_like(d)  # RT_ACCUMULATE adds to them
+    api.rt_shade_batched_l2_step(ctx, uv, d, o, api.RT_QUADRILINEAR, target, 1.0, out2, sums, dtex, duv, ddir,
+                                 api.RT_ACCUMULATE)
+    assert api.rt_get_error(ctx) == api.RT_OK
+    assert torch.equal(out2, out)
+    shaded = (o >= 0).unsqueeze(-1)
+    ref_se = (out.double() ** 2 * shaded).sum().item()
+    assert abs(sums[0].item() - ref_se) <= 1e-9 * ref_se
+    assert sums[1].item() == shaded.sum().item()
+    for k in (0, 1):
+        lhs = dtex[k].double().sum(dim=(0, 1, 2, 3))
+        rhs = (out.double() * (o == k).unsqueeze(-1)).sum(dim=(0, 1, 2))
+        torch.testing.assert_close(lhs, rhs, rtol=1e-4, atol=1e-3)
+    del dtex
+    duv_ref, ddir_ref = torch.empty_like(uv), torch.empty_like(d)
+    api.rt_shade_batched_backward(ctx, uv, d, o, api.RT_QUADRILINEAR, out, None, duv_ref, ddir_ref)
+    assert torch.equal(duv, duv_ref) and torch.equal(ddir, ddir_ref)
