@@ -2,10 +2,10 @@
 
 The paper fills radiance textures from ray-traced data (Eq. 4b); this module
 fits one to a set of target views instead, which is what the differentiable
-lookup is for.  A step is: forward synthesis of every view (rt_shade_batched),
-the L2 loss and its gradient (rt_l2_loss_grad), the backward pass into the
-texel gradients (rt_shade_batched_backward) and an Adam update
-(rt_adam_step) -- all in libradtex's kernels, on the FP32 texture the context
+lookup is for.  A step is: forward synthesis of every view, the L2 loss and its
+gradient and the backward pass into the texel gradients, fused into one launch
+(rt_shade_batched_l2_step), then an Adam update (rt_adam_step) -- all in
+libradtex's kernels, on the FP32 texture the context
 borrows (RT_BORROW) in the planes layout.  Checkpoints hold the texture, the
 Adam moments, the step count and a hash of the configuration; with
 deterministic=True (fixed-point texel gradients) a run resumed from a
@@ -53,22 +53,17 @@ class TextureFit:
         api.rt_l2_loss_grad(z, z, obj, 0.0, None, s)
         return int(s[1].item())
 
-    def step(self, uv, dirs, obj, target, count: int, out=None, dL_dout=None):
+    def step(self, uv, dirs, obj, target, count: int, out=None):
         """One fitting step over a batch of views (tensors shaped (V, H, W, k)); the
         G-buffer's object ids name this fitter's texture (self.oid) or background.
         L = 1/(2 * 4 count) sum over shaded fragments and channels of (out - target)^2.
-        Returns the loss as a device tensor (no synchronisation)."""
-        if out is None:
-            out = torch.empty((*obj.shape, 4), dtype=torch.float32, device=obj.device)
-        if dL_dout is None:
-            dL_dout = torch.empty_like(out)
-        api.rt_shade_batched(self.ctx, uv, dirs, obj, self.filt, out)
+        `out` (optional) receives the rendered colours.  Returns the loss as a device
+        tensor (no synchronisation)."""
         self.sums.zero_()
         scale = 1.0 / (4.0 * max(count, 1))
-        api.rt_l2_loss_grad(out, target, obj, scale, dL_dout, self.sums)
         flags = api.RT_DETERMINISTIC if self.deterministic else 0
-        api.rt_shade_batched_backward(self.ctx, uv, dirs, obj, self.filt, dL_dout, {self.oid: self.grad}, None, None,
-                                      flags)
+        api.rt_shade_batched_l2_step(self.ctx, uv, dirs, obj, self.filt, target, scale, out, self.sums,
+                                     {self.oid: self.grad}, None, None, flags)
         self.step_count += 1
         api.rt_adam_step(self.tex, self.grad, self.m, self.v, self.lr, self.betas[0], self.betas[1], self.eps,
                          self.step_count)
@@ -142,14 +137,13 @@ def main(argv=None):
     o = torch.where(o >= 0, torch.full_like(o, fit.oid), o)
     count = fit.shaded_count(o)
     out = torch.empty((*shape, 4), dtype=torch.float32, device=dev)
-    dL = torch.empty_like(out)
     psnr0 = TextureFit.psnr(fit.render(uv, d, o), t, o)
-    fit.step(uv, d, o, t, count, out, dL)
+    fit.step(uv, d, o, t, count, out)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(a.steps - 1):
-        loss = fit.step(uv, d, o, t, count, out, dL)
+        loss = fit.step(uv, d, o, t, count, out)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(a.steps - 1, 1)
