@@ -137,3 +137,38 @@ def test_fused_arguments_and_edge_cases(scene):
     api.rt_shade_batched_l2_step(ctx, uv, d, bad, api.RT_QUADRILINEAR, target, 1.0, torch.empty_like(target))
     assert api.rt_get_error(ctx) == api.RT_ERR_BAD_OBJ_ID
     assert api.rt_get_error(ctx) == api.RT_OK
+
+
+@pytest.mark.parametrize("fmt", [api.RT_F16, api.RT_BF16, api.RT_E4M3_BUCKET_SCALE, api.RT_F32])
+@pytest.mark.parametrize("filt", FILTERS)
+def test_fused_single_format_kernels(fmt, filt):
+    """A context whose objects share one format runs that format's own kernel
+    instantiation (the benchmark's case); it must match the three calls too."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2301_01719_gb300 import build
+
+    build.build()
+    ctx = api.Context(0)
+    W = H = 32
+    n = 6
+    atlas = oracle.fill_field(W, H, n, synth.field_lobes(810))
+    oids = [api.rt_create_texture(ctx, W, H, n, fmt, api.RT_LAYOUT_ATLAS, to_dev(atlas)) for _ in range(2)]
+    g, obj, uv, d, o = frames(2, 45, 70, oids, seed=1004)
+    target = to_dev(np.random.default_rng(4).uniform(0, 1, (2, 45, 70, 4)).astype(np.float32))
+    dt_a = {k: torch.zeros((n, n, H, W, 4), device=uv.device) for k in oids}
+    out_a, sums_a, duv_a, ddir_a = unfused(ctx, uv, d, o, filt, target, 0.5, dt_a, api.RT_ACCUMULATE)
+    dt_b = {k: torch.zeros((n, n, H, W, 4), device=uv.device) for k in oids}
+    out_b = torch.empty_like(out_a)
+    sums_b = torch.zeros(2, dtype=torch.float64, device=uv.device)
+    duv_b, ddir_b = torch.zeros_like(uv), torch.zeros_like(d)
+    api.rt_shade_batched_l2_step(ctx, uv, d, o, filt, target, 0.5, out_b, sums_b, dt_b, duv_b, ddir_b,
+                                 api.RT_ACCUMULATE)
+    assert api.rt_get_error(ctx) == api.RT_OK
+    assert torch.equal(out_a, out_b)
+    assert torch.equal(duv_a, duv_b) and torch.equal(ddir_a, ddir_b)
+    for k in oids:
+        assert (dt_a[k] - dt_b[k]).abs().max().item() <= 1e-5 * max(dt_a[k].abs().max().item(), 1.0)
+    assert sums_a[1].item() == sums_b[1].item()
+    assert abs(sums_a[0].item() - sums_b[0].item()) <= 1e-12 * abs(sums_a[0].item())
+    ctx.close()
