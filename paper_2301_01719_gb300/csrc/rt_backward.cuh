@@ -169,33 +169,34 @@ __device__ __forceinline__ CoordGrad backward_taps(const TexDesc& d, const Looku
         return q.x + q.y;
     };
     auto lerpf = [](float a, float b, float w) { return fmaf(w, b - a, a); };
-    if (FILTER == RT_ANGULAR_BILINEAR) {
+    if constexpr (FILTER == RT_ANGULAR_BILINEAR) {
         P4 t00, t10, t01, t11;
         load_quadP<FMT, LAYOUT>(d, L.u.k0, L.v.k0, L.s, L.t, t00, t10, t01, t11);
         const float p00 = proj(t00), p10 = proj(t10), p01 = proj(t01), p11 = proj(t11);
         cg.gs = lerpf(p10 - p00, p11 - p01, L.t.w);
         cg.gt = lerpf(p01, p11, L.s.w) - lerpf(p00, p10, L.s.w);
         return cg;
+    } else {
+        // bucket (a, b) of the 2 x 2 spatial footprint: value c_ab, d/ds, d/dt (all projected on g)
+        float c[2][2], cs[2][2], ct[2][2];
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                P4 t00, t10, t01, t11;
+                load_quadP<FMT, LAYOUT>(d, a ? L.u.k1 : L.u.k0, b ? L.v.k1 : L.v.k0, L.s, L.t, t00, t10, t01, t11);
+                const float p00 = proj(t00), p10 = proj(t10), p01 = proj(t01), p11 = proj(t11);
+                const float x0 = lerpf(p00, p10, L.s.w), x1 = lerpf(p01, p11, L.s.w);
+                c[b][a] = lerpf(x0, x1, L.t.w);
+                cs[b][a] = lerpf(p10 - p00, p11 - p01, L.t.w);
+                ct[b][a] = x1 - x0;
+            }
+        cg.gu = lerpf(c[0][1] - c[0][0], c[1][1] - c[1][0], L.v.w);
+        cg.gv = lerpf(c[1][0], c[1][1], L.u.w) - lerpf(c[0][0], c[0][1], L.u.w);
+        cg.gs = lerpf(lerpf(cs[0][0], cs[0][1], L.u.w), lerpf(cs[1][0], cs[1][1], L.u.w), L.v.w);
+        cg.gt = lerpf(lerpf(ct[0][0], ct[0][1], L.u.w), lerpf(ct[1][0], ct[1][1], L.u.w), L.v.w);
+        return cg;
     }
-    // bucket (a, b) of the 2 x 2 spatial footprint: value c_ab, d/ds, d/dt (all projected on g)
-    float c[2][2], cs[2][2], ct[2][2];
-#pragma unroll
-    for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            P4 t00, t10, t01, t11;
-            load_quadP<FMT, LAYOUT>(d, a ? L.u.k1 : L.u.k0, b ? L.v.k1 : L.v.k0, L.s, L.t, t00, t10, t01, t11);
-            const float p00 = proj(t00), p10 = proj(t10), p01 = proj(t01), p11 = proj(t11);
-            const float x0 = lerpf(p00, p10, L.s.w), x1 = lerpf(p01, p11, L.s.w);
-            c[b][a] = lerpf(x0, x1, L.t.w);
-            cs[b][a] = lerpf(p10 - p00, p11 - p01, L.t.w);
-            ct[b][a] = x1 - x0;
-        }
-    cg.gu = lerpf(c[0][1] - c[0][0], c[1][1] - c[1][0], L.v.w);
-    cg.gv = lerpf(c[1][0], c[1][1], L.u.w) - lerpf(c[0][0], c[0][1], L.u.w);
-    cg.gs = lerpf(lerpf(cs[0][0], cs[0][1], L.u.w), lerpf(cs[1][0], cs[1][1], L.u.w), L.v.w);
-    cg.gt = lerpf(lerpf(ct[0][0], ct[0][1], L.u.w), lerpf(ct[1][0], ct[1][1], L.u.w), L.v.w);
-    return cg;
 }
 
 template <int FILTER, int FMT, int LAYOUT, bool DET>
