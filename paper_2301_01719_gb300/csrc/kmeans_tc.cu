@@ -10,9 +10,13 @@
 // from the FP16 values.  Bp, Dp, Kp are rounded up to 128, 64 and 256 with
 // zeros; padded centroids get |c|^2 = +inf and are never chosen.
 //
-// One CTA per 128 buckets, 192 threads: warp 0 issues the TMA loads (one
-// elected lane), warp 1 the MMAs (one elected lane), warps 2-5 (128 threads,
-// one per accumulator row) run the epilogue.  A 4-stage shared-memory ring of
+// Persistent: one CTA per SM walks the 128-bucket tiles m = blockIdx.x,
+// m + gridDim.x, ...; 192 threads: warp 0 issues the TMA loads (one elected
+// lane), warp 1 the MMAs (one elected lane), warps 2-5 (128 threads, one per
+// accumulator row) run the epilogue.  The three roles walk the same sequence of
+// (bucket tile, centroid tile) pairs, so the shared-memory ring and the two
+// accumulators stay busy across bucket tiles: the loads of the next tile
+// overlap the last MMAs of this one, its epilogue the next tile's MMAs.  A 4-stage shared-memory ring of
 // 128 x 64 (A) and 256 x 64 (B) FP16 tiles in the 128-byte swizzled K-major
 // layout feeds M = 128, N = 256, K = 16 MMAs; two 256-column accumulators in
 // tensor memory let the epilogue of one 256-centroid tile overlap the MMAs of
@@ -146,8 +150,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM;
     const int ntiles = Kp / BN, kchunks = Dp / BK;
+    const int mtiles = (B + BM - 1) / BM;
+    // this CTA's bucket tiles, times the centroid tiles of each
+    const int my_m = blockIdx.x < mtiles ? (mtiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int jobs = my_m * ntiles;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -177,7 +184,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (warp == 0 && lane == 0) {
         // producer: stage s of iteration `it` holds A rows m0.., B rows of tile t, values kc*BK..
         int it = 0;
-        for (int t = 0; t < ntiles && !timed_out; ++t)
+        for (int job = 0; job < jobs && !timed_out; ++job) {
+            const int t = job % ntiles, m0 = ((int)blockIdx.x + (job / ntiles) * (int)gridDim.x) * BM;
             for (int kc = 0; kc < kchunks; ++kc, ++it) {
                 const int s = it % STAGES;
                 const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
@@ -190,6 +198,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 tma_load_2d(sa, &tmA, kc * BK, m0, &full[s]);
                 tma_load_2d(sa + A_BYTES, &tmB, kc * BK, t * BN, &full[s]);
             }
+        }
         if (timed_out) {
             // let the copies already issued land before the CTA exits
             for (int k = 1; k <= STAGES && it - k >= 0; ++k) {
@@ -200,9 +209,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         int it = 0;
-        for (int t = 0; t < ntiles && !timed_out; ++t) {
-            const int a = t & 1;
-            if (!mbar_wait(&accempty[a], ((uint32_t)(t >> 1) & 1u) ^ 1u, abort_flag)) {
+        for (int job = 0; job < jobs && !timed_out; ++job) {
+            const int a = job & 1;
+            if (!mbar_wait(&accempty[a], ((uint32_t)(job >> 1) & 1u) ^ 1u, abort_flag)) {
                 timed_out = true;
                 break;
             }
@@ -237,9 +246,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int row = q * 32 + lane;
         float best = INFINITY;
         int bestk = 0;
-        for (int t = 0; t < ntiles; ++t) {
-            const int a = t & 1;
-            if (!mbar_wait(&accfull[a], (uint32_t)(t >> 1) & 1u, abort_flag)) {
+        for (int job = 0; job < jobs; ++job) {
+            const int t = job % ntiles, a = job & 1;
+            if (t == 0) {
+                best = INFINITY;
+                bestk = 0;
+            }
+            if (!mbar_wait(&accfull[a], (uint32_t)(job >> 1) & 1u, abort_flag)) {
                 timed_out = true;
                 break;
             }
@@ -260,11 +273,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             tc_fence_before();
             mbar_arrive(&accempty[a]);
-        }
-        const int b = m0 + row;
-        if (!timed_out && b < B) {
-            index[b] = (uint32_t)bestk;
-            if (dist) dist[b] = fmaxf(best + xn[b], 0.0f);
+            if (t == ntiles - 1) {
+                const int b = ((int)blockIdx.x + (job / ntiles) * (int)gridDim.x) * BM + row;
+                if (b < B) {
+                    index[b] = (uint32_t)bestk;
+                    if (dist) dist[b] = fmaxf(best + xn[b], 0.0f);
+                }
+            }
         }
     }
     if (timed_out) {
@@ -446,8 +461,13 @@ cudaError_t launch_kmeans_assign_tc(const TexDesc& d, int K, const float* C, uin
     if ((e = cudaFuncSetAttribute(assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)) !=
         cudaSuccess)
         return e;
-    assign_kernel<<<(unsigned)(L.Bp / BM), THREADS, SMEM_BYTES, stream>>>(tmA, tmB, d.W * d.H, (int)L.Dp, (int)L.Kp,
-                                                                         cn, xn, index, dist, status);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t mtiles = L.Bp / BM;
+    const unsigned grid = (unsigned)(mtiles < sms ? mtiles : sms);  // one CTA per SM (its shared memory)
+    assign_kernel<<<grid, THREADS, SMEM_BYTES, stream>>>(tmA, tmB, d.W * d.H, (int)L.Dp, (int)L.Kp, cn, xn, index,
+                                                         dist, status);
     return cudaGetLastError();
 }
 

@@ -229,15 +229,17 @@ def test_palette_encode_full_size_sampled(ctx):
     api.rt_destroy_texture(ctx, oid)
 
 
-@pytest.mark.parametrize("shape", [(53, 37, 4, 300), (40, 20, 16, 70), (17, 9, 3, 5), (10, 10, 4, 3)])
+@pytest.mark.parametrize("shape", [(53, 37, 4, 300), (40, 20, 16, 70), (17, 9, 3, 5), (10, 10, 4, 3),
+                                   (160, 161, 4, 300)])
 def test_kmeans_tensor_core_assign_matches_oracle(ctx, shape):
     """The tcgen05 assignment (FP16 operands, FP32 accumulation in tensor memory):
     every choice is a nearest centroid in FP64 up to the FP16 rounding of the
     operands, 2^-9 (|x|^2 + |c|^2); it agrees with the FP32 kernel on almost
     every bucket.  Shapes: two 256-centroid tiles with a ragged bucket tile; 16
-    K-chunks over an odd number (7) of bucket tiles, so the last cluster of two
-    CTAs has one past the end; a vector length (3^2 x 4 = 36) padded to 64; a
-    single bucket tile."""
+    K-chunks over 7 bucket tiles; a vector length (3^2 x 4 = 36) padded to 64; a
+    single bucket tile; 202 bucket tiles, more than the persistent grid's one CTA
+    per SM, so CTAs walk several tiles with the accumulators alternating across
+    them."""
     W, H, n, K = shape
     oid, X = dense_texture(ctx, W, H, n, api.RT_F16, 62)
     B = W * H
