@@ -328,8 +328,9 @@ def cpu_baseline(a, g, seconds: float):
     bwd = o[::sub].shape[0] / max(time.perf_counter() - t0, 1e-9)
     step = 1.0 / (1.0 / fwd + 1.0 / bwd)
     return {"value": step / 1e9, "unit": "Gfrag/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": (f"every {stride}th fragment of the {F}-fragment step ({o.shape[0]} forward, "
-                       f"{o[::sub].shape[0]} backward), same textures"),
+            "sample": ((f"every {stride}th fragment" if stride > 1 else "every fragment") +
+                       f" of the {F}-fragment step ({o.shape[0]} forward, every 10th of those backward: "
+                       f"{o[::sub].shape[0]}), same textures"),
             "fwd_gfrag_s": fwd / 1e9, "bwd_gfrag_s": bwd / 1e9}
 
 
