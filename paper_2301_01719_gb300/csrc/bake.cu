@@ -109,7 +109,7 @@ __device__ __forceinline__ bool occluded(const rt_bake_scene& S, float3 P, float
 // against the other surface only: leaving the plane into its normal's
 // half-space it cannot meet the plane again, nor leaving the convex sphere
 // outward the sphere.
-__device__ __forceinline__ float4 deferred_payload(const rt_bake_scene& S, float3 P, float3 d, const float3* dirs,
+__device__ __forceinline__ float4 deferred_payload(const rt_bake_scene& S, float3 P, float3 d, const float4* dirs,
                                                    int K) {
     const float3 c = mk(S.sphere_centre);
     const float3 o = make_float3(P.x - c.x, P.y - c.y, P.z - c.z);
@@ -158,8 +158,9 @@ __device__ __forceinline__ float4 deferred_payload(const rt_bake_scene& S, float
     if (hit == RT_SURFACE_SPHERE) {
         // only the plane can block: the crossing t = h / w_y lies beyond eps
         const float h = S.plane_height - X.y;
+#pragma unroll 4
         for (int k = 0; k < K; ++k) {
-            const float3 w = dirs[k];
+            const float4 w = dirs[k];
             const float wy = fmaf(w.z, N.y, fmaf(w.y, b2.y, w.x * b1.y));
             const float e = eps * wy;
             vis += ((wy > 0.0f && h > e) || (wy < 0.0f && h < e)) ? 0 : 1;
@@ -169,8 +170,9 @@ __device__ __forceinline__ float4 deferred_payload(const rt_bake_scene& S, float
         const float3 oX = make_float3(X.x - c.x, X.y - c.y, X.z - c.z);
         const float qX = dot3(oX, oX) - S.sphere_radius * S.sphere_radius;
         const float o1 = dot3(oX, b1), o2 = dot3(oX, b2), o3 = dot3(oX, N);
+#pragma unroll 4
         for (int k = 0; k < K; ++k) {
-            const float3 w = dirs[k];
+            const float4 w = dirs[k];
             const float bw = fmaf(w.z, o3, fmaf(w.y, o2, w.x * o1));
             const float dw = fmaf(bw, bw, -qX);  // the ray meets the sphere when dw > 0
             const float m = -bw - eps;            // and enters ahead when m > sqrt(dw)
@@ -209,7 +211,7 @@ __device__ __forceinline__ Ray bucket_ray(const rt_bake_scene& S, int surface, i
 // Texel p of the bucket with tangent-space reflection vector R (Eq. 4a then
 // Eq. 4b at the texel centre, from the block's table); d = R in world space.
 // The radiance payload, or with K > 0 the deferred one over the K directions.
-__device__ __forceinline__ float4 bake_texel(const rt_bake_scene& S, const Ray& r, float3 R, const float3* dirs,
+__device__ __forceinline__ float4 bake_texel(const rt_bake_scene& S, const Ray& r, float3 R, const float4* dirs,
                                              int K) {
     const float3 d = axpy(R.z, r.N, axpy(R.y, r.B, scale3(R.x, r.T)));
     if (K > 0) return deferred_payload(S, r.P, d, dirs, K);
@@ -234,9 +236,10 @@ __global__ void __launch_bounds__(kBakeThreads) bake_kernel(rt_bake_scene S, int
                                                             float* __restrict__ scale, int W, int H, int n,
                                                             const float* __restrict__ ao_dirs, int K) {
     extern __shared__ float3 Rtab[];
-    float3* dirs = Rtab + n * n;
+    // the directions as float4 (one 16-byte shared load each), after the vector table
+    float4* dirs = reinterpret_cast<float4*>(Rtab + ((n * n + 3) & ~3));
     for (int k = threadIdx.x; k < K; k += blockDim.x)
-        dirs[k] = make_float3(ao_dirs[3 * k], ao_dirs[3 * k + 1], ao_dirs[3 * k + 2]);
+        dirs[k] = make_float4(ao_dirs[3 * k], ao_dirs[3 * k + 1], ao_dirs[3 * k + 2], 0.0f);
     texel_vector_table<true>(Rtab, n);  // ends with the block barrier
     const int64_t b = (int64_t)blockIdx.x * kBakeThreads + threadIdx.x;
     if (b >= (int64_t)W * H) return;
@@ -282,7 +285,7 @@ static cudaError_t launch_bake_t(const rt_bake_scene& S, int surface, void* dst,
         if ((int64_t)gx < want) gy = (unsigned)((want + gx - 1) / gx);
         if (gy > (unsigned)(n * n)) gy = (unsigned)(n * n);
     }
-    const size_t smem = sizeof(float3) * ((size_t)n * n + (size_t)K);
+    const size_t smem = sizeof(float3) * (((size_t)n * n + 3) & ~(size_t)3) + sizeof(float4) * (size_t)K;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(bake_kernel<FMT, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);

@@ -118,7 +118,7 @@ def test_deferred_rejects_bad_arguments(ctx):
 
 
 def test_deferred_max_n_and_directions(ctx):
-    """n = 64 (48 KiB of reflection vectors) with 1024 directions: 60 KiB of
+    """n = 64 (48 KiB of reflection vectors) with 1024 directions: 64 KiB of
     shared memory, above the default per-block limit."""
     W, H, n = 3, 2, 64
     scene = synth.bake_scene(59)
