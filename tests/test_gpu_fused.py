@@ -172,3 +172,39 @@ def test_fused_single_format_kernels(fmt, filt):
     assert sums_a[1].item() == sums_b[1].item()
     assert abs(sums_a[0].item() - sums_b[0].item()) <= 1e-12 * abs(sums_a[0].item())
     ctx.close()
+
+
+def test_fused_palette_and_bits(scene):
+    """A palette texture (texel gradients per palette bucket) and a 1-bit texture
+    (no texel gradient; colours and coordinate gradients only) through the fused
+    step, against the three calls."""
+    ctx, _, _, _ = scene
+    from test_gpu_palette import palette_case
+
+    K, n, W, H = 9, 6, 30, 22
+    pal_atlas, index = palette_case(K, n, W, H, seed=61)
+    pid = api.rt_create_palette_texture(ctx, W, H, n, K, api.RT_F16, api.RT_LAYOUT_ATLAS, to_dev(pal_atlas),
+                                        to_dev(index.view(np.int32)))
+    rng = np.random.default_rng(62)
+    bid = api.rt_create_texture(ctx, W, H, n, api.RT_BIT1, api.RT_LAYOUT_ATLAS,
+                                to_dev(rng.uniform(0, 1, (H * n, W * n, 4)).astype(np.float32)))
+    g, obj, uv, d, o = frames(2, 40, 56, [pid, bid], seed=1005)
+    target = to_dev(rng.uniform(0, 1, (2, 40, 56, 4)).astype(np.float32))
+    dt_a = {pid: torch.zeros((n, n, K, 4), device=uv.device)}
+    out_a, sums_a, duv_a, ddir_a = unfused(ctx, uv, d, o, api.RT_QUADRILINEAR, target, 1.0, dt_a, api.RT_ACCUMULATE)
+    dt_b = {pid: torch.zeros((n, n, K, 4), device=uv.device)}
+    out_b = torch.empty_like(out_a)
+    duv_b, ddir_b = torch.zeros_like(uv), torch.zeros_like(d)
+    api.rt_shade_batched_l2_step(ctx, uv, d, o, api.RT_QUADRILINEAR, target, 1.0, out_b, None, dt_b, duv_b, ddir_b,
+                                 api.RT_ACCUMULATE)
+    assert api.rt_get_error(ctx) == api.RT_OK
+    assert torch.equal(out_a, out_b)
+    assert torch.equal(duv_a, duv_b) and torch.equal(ddir_a, ddir_b)
+    assert (dt_a[pid] - dt_b[pid]).abs().max().item() <= 1e-5 * max(dt_a[pid].abs().max().item(), 1.0)
+    # a texel gradient for the bit texture is refused, as by the backward
+    with pytest.raises(api.RadtexError) as e:
+        api.rt_shade_batched_l2_step(ctx, uv, d, o, api.RT_QUADRILINEAR, target, 1.0, None, None,
+                                     {bid: torch.zeros((n, n, H, W, 4), device=uv.device)})
+    assert e.value.status == api.RT_ERR_UNSUPPORTED
+    api.rt_destroy_texture(ctx, pid)
+    api.rt_destroy_texture(ctx, bid)
