@@ -19,7 +19,7 @@ import threading
 
 import numpy as np
 
-F32, F16, BF16, E4M3, F64, BIT1 = 0, 1, 2, 3, 4, 5
+F32, F16, BF16, E4M3, F64, BIT1, PATTERN = 0, 1, 2, 3, 4, 5, 6
 NEAREST, ANGULAR_BILINEAR, QUADRILINEAR = 0, 1, 2
 FLAG_BAD_OBJ, FLAG_NONFINITE = 1, 2
 
@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
                 "oracle_decode": (None, [I32, I64, P, P]),
                 "oracle_encode_e4m3_buckets": (None, [I32, I32, I32, P, P, P]),
                 "oracle_locate": (U32, [P, P, I32, I64, P, P, P, I32, P, P]),
+                "oracle_taps": (U32, [P, P, I32, I64, P, P, P, I32, P, P]),
                 "oracle_shade": (U32, [P, P, P, I32, I64, P, P, P, I32, P]),
                 "oracle_shade64": (U32, [P, P, P, I32, I64, P, P, P, I32, P]),
                 "oracle_shade_backward": (U32, [P, P, P, I32, I64, P, P, P, I32, P, P, P, P]),
@@ -237,6 +238,20 @@ class Texture:
         return v
 
 
+class PatternTexture:
+    """An oracle-only procedural texture for sizes whose atlas would not fit in
+    host memory (test infrastructure).  Channel c of atlas texel (X, Y) =
+    (i n + s, j n + t) is the triangle wave |((a_c X + b_c Y + k_c) mod 2m) - m| / m,
+    read by the same lookup as stored textures; no codes are held."""
+
+    def __init__(self, W: int, H: int, n: int, a, b, k, m: int):
+        self.W, self.H, self.n, self.fmt, self.wrap = int(W), int(H), int(n), PATTERN, 0
+        p = [int(x) for x in (*a, *b, *k, m)]
+        assert len(p) == 13 and min(p) >= 0 and p[12] >= 1
+        self.codes = np.array(p, dtype=np.int64)
+        self.scales = None
+
+
 def _tables(textures):
     dims = np.zeros((max(len(textures), 1), 4), dtype=np.int32)
     codes = (ctypes.c_void_p * max(len(textures), 1))()
@@ -282,6 +297,19 @@ def locate(textures, uv, dirs, obj, filt: int):
     flags = lib().oracle_locate(_p(dims), codes, len(textures), obj.shape[0], _p(uv), _p(dirs), _p(obj), filt,
                                 _p(idx), _p(coord))
     return idx, coord, int(flags)
+
+
+def taps(textures, uv, dirs, obj, filt: int):
+    """The taps the colour sums (Section 2, the filters of reading R5): F x 16
+    atlas texel indices Y (w n) + X (int64, -1 for no tap) and their FP64
+    weights w_u w_v w_s w_t, in (u, v, s, t) tap order."""
+    uv, dirs, obj = _gbuf(uv, dirs, obj, np.float32)
+    dims, codes, _ = _tables(textures)
+    index = np.empty((obj.shape[0], 16), dtype=np.int64)
+    weight = np.empty((obj.shape[0], 16))
+    flags = lib().oracle_taps(_p(dims), codes, len(textures), obj.shape[0], _p(uv), _p(dirs), _p(obj), filt,
+                              _p(index), _p(weight))
+    return index, weight, int(flags)
 
 
 def shade_backward(textures, uv, dirs, obj, filt: int, dL_dout, want_tex=True, want_uv=True, want_dir=True,

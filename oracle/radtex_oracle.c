@@ -65,6 +65,11 @@
 #define OR_E4M3 3
 #define OR_F64 4  /* oracle-only exact format, used by the pins */
 #define OR_BIT1 5 /* 1-bit payload (reading R13): code 0 or 1, the texel value in every channel */
+/* Oracle-only procedural texels, for textures too large to hold as an atlas in
+ * host memory: `codes` points at 13 int64 parameters a[4], b[4], k[4], m, and
+ * channel c of atlas texel (X, Y) is the triangle wave
+ * |((a_c X + b_c Y + k_c) mod 2m) - m| / m  (a value j / m, 0 <= j <= m). */
+#define OR_PATTERN 6
 
 #define OR_NEAREST 0
 #define OR_ANGULAR_BILINEAR 1
@@ -377,6 +382,12 @@ static double texel(const tex_t* T, int64_t i, int64_t j, int64_t s, int64_t t, 
             return decode_e4m3(((const uint8_t*)T->codes)[e]) * (double)T->scale[j * T->W + i];
         case OR_BIT1:
             return (double)(((const uint8_t*)T->codes)[e] & 1u);
+        case OR_PATTERN: {
+            const int64_t* p = (const int64_t*)T->codes;
+            const int64_t X = i * T->n + s, Y = j * T->n + t, m = p[12];
+            const int64_t q = (p[c] * X + p[4 + c] * Y + p[8 + c]) % (2 * m);
+            return (double)llabs(q - m) / (double)m;
+        }
         default:
             return ((const double*)T->codes)[e];
     }
@@ -574,6 +585,45 @@ static uint32_t locate_core(const int32_t* dims, const void* const* codes, int32
 uint32_t oracle_locate(const int32_t* dims, const void* const* codes, int32_t n_obj, int64_t F, const float* uv,
                        const float* dir, const int32_t* obj, int32_t filter, int32_t* idx, double* coord) {
     return locate_core(dims, codes, n_obj, F, uv, dir, NULL, obj, filter, idx, coord);
+}
+
+/* The taps of every fragment and their weights, as the colour sums them: 16
+ * entries per fragment in (u, v, s, t) tap order, each the atlas texel index
+ * Y (w n) + X of texel (X, Y) = (i n + s, j n + t) and the weight
+ * w_u w_v w_s w_t.  Zero-weight entries (the second tap of a nearest axis) and
+ * fragments that are not shaded have index -1 and weight 0.  The texel
+ * gradient of a loss is the sum over entries of weight x dL/dout. */
+uint32_t oracle_taps(const int32_t* dims, const void* const* codes, int32_t n_obj, int64_t F, const float* uv,
+                     const float* dir, const int32_t* obj, int32_t filter, int64_t* index, double* weight) {
+    uint32_t flags = 0;
+#pragma omp parallel for schedule(static) reduction(| : flags)
+    for (int64_t f = 0; f < F; ++f) {
+        double u = uv[2 * f], v = uv[2 * f + 1];
+        double I[3] = {dir[3 * f], dir[3 * f + 1], dir[3 * f + 2]};
+        int shade;
+        flags |= classify(obj[f], n_obj, codes, u, v, I, NULL, &shade);
+        for (int e = 0; e < 16; ++e) {
+            index[16 * f + e] = -1;
+            weight[16 * f + e] = 0.0;
+        }
+        if (!shade) continue;
+        tex_t T;
+        make_tex(dims, codes, NULL, obj[f], &T);
+        lookup_t L;
+        locate_one(&T, u, v, I, NULL, filter, &L);
+        int e = 0;
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int p = 0; p < 2; ++p)
+                    for (int q = 0; q < 2; ++q, ++e) {
+                        double w = L.u.w[a] * L.v.w[b] * L.s.w[p] * L.t.w[q];
+                        if (w == 0.0) continue;
+                        int64_t X = L.u.tap[a] * T.n + L.s.tap[p], Y = L.v.tap[b] * T.n + L.t.tap[q];
+                        index[16 * f + e] = Y * T.W * T.n + X;
+                        weight[16 * f + e] = w;
+                    }
+    }
+    return flags;
 }
 
 /* The world-space lookup (Eq. 1a with a per-fragment normal nrm, F x 3). */

@@ -10,5 +10,6 @@ FP64 then rounded to FP32, the G-buffer precision.
 """
 from .scenes import (GBuffer, quad_scene, quad_views, sphere_plane_poses, sphere_plane_scene,  # noqa: F401
                      voronoi_planes_scene)
-from .fields import field_lobes, bucket_lobe_params, eval_field_lobes  # noqa: F401
+from .fields import (PATTERN_A, PATTERN_B, PATTERN_K, PATTERN_M, bucket_lobe_params,  # noqa: F401
+                     eval_field_lobes, field_lobes, pattern_values)
 from .bake import ao_directions, bake_scene  # noqa: F401

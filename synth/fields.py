@@ -8,6 +8,9 @@ the texture (the oracle on the CPU, the fill kernel on the GPU):
   returned as rows of 11 numbers (a_0..a_3, alpha, beta, gamma, d_x, d_y, d_z, p).
 * ``bucket_lobe_params``: one cosine-power lobe per bucket for the large
   workloads, returned as h x w x 8 FP32 (rho_r, rho_g, rho_b, d_x, d_y, d_z, p, 0).
+
+and one texel pattern, ``pattern_values``, for textures too large to hold as
+a host-side atlas (the oracle evaluates it per texel instead of storing it).
 """
 from __future__ import annotations
 
@@ -98,3 +101,24 @@ def eval_field_lobes(lobes: np.ndarray, uv: np.ndarray, dirs: np.ndarray, chunk:
             acc += P[None, 0:4] * (spatial * lobe)[:, None]
         out[a:a + chunk] = acc
     return out
+
+
+# A texel pattern for textures too large for a host-side atlas: channel c of
+# atlas texel (X, Y) is the triangle wave |((a_c X + b_c Y + k_c) mod 2m) - m| / m.
+# Its values j / m (m = 2048) are exact in FP32, FP16 and BF16 alike, and its
+# slope (at most 7 / 2048 per texel) keeps the colour's sensitivity to FP32
+# coordinate rounding far below the colour tolerance, while a texel read from a
+# wrong address differs from the right one.
+PATTERN_A = (1, 3, 5, 7)
+PATTERN_B = (3, 1, 7, 5)
+PATTERN_K = (0, 517, 1031, 1543)
+PATTERN_M = 2048
+
+
+def pattern_values(X, Y, c: int):
+    """Channel c of the pattern at integer atlas coordinates X, Y (broadcastable
+    numpy arrays or torch tensors of a 64-bit integer type; only operators are
+    used, so the same code fills a host array or a device tensor)."""
+    m = PATTERN_M
+    q = (PATTERN_A[c] * X + PATTERN_B[c] * Y + PATTERN_K[c]) % (2 * m)
+    return abs(q - m) / m
