@@ -23,6 +23,7 @@ PALETTE = "tests/test_oracle_palette.py"
 WORLD = "tests/test_oracle_world.py"
 SHADOW = "tests/test_oracle_shadow.py"
 DEFERRED = "tests/test_oracle_deferred.py"
+PATTERN = "tests/test_oracle_pattern.py"
 
 # (name, original text, mutated text, pin files expected to catch it)
 MUTATIONS = [
@@ -59,6 +60,10 @@ MUTATIONS = [
     ("deferred_sky_occluded", "out[3] = 1.0;\n        if (lo)", "out[3] = 0.0;\n        if (lo)", [DEFERRED]),
     ("deferred_from_origin_side", "for (int k = 0; k < 3; ++k) X[k] = P[k] + t_best * d[k];",
      "for (int k = 0; k < 3; ++k) X[k] = P[k] + 0.5 * t_best * d[k];", [DEFERRED]),
+    ("pattern_x_y_swapped", "const int64_t q = (p[c] * X + p[4 + c] * Y + p[8 + c]) % (2 * m);",
+     "const int64_t q = (p[c] * Y + p[4 + c] * X + p[8 + c]) % (2 * m);", [PATTERN]),
+    ("taps_s_t_swapped", "int64_t X = L.u.tap[a] * T.n + L.s.tap[p], Y = L.v.tap[b] * T.n + L.t.tap[q];",
+     "int64_t X = L.u.tap[a] * T.n + L.t.tap[q], Y = L.v.tap[b] * T.n + L.s.tap[p];", [PATTERN]),
 ]
 
 
