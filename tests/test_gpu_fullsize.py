@@ -7,7 +7,8 @@ The oracle cannot shade 124 M fragments in a test, so it checks samples one by
 one: 200 000 random fragments plus every fragment of a few 64 x 64 screen tiles.
 Properties that hold at any size are checked on the whole step: the texel
 gradients of every channel sum to the sum of dL/dout over shaded fragments, and
-background fragments get zero colour and zero gradients."""
+background fragments get zero colour and zero gradients.  The fused step and
+the world-space variant run on the same frames and textures."""
 import numpy as np
 import pytest
 import torch
@@ -143,3 +144,46 @@ def test_fullsize_fused_l2_step(full):
     duv_ref, ddir_ref = torch.empty_like(uv), torch.empty_like(d)
     api.rt_shade_batched_backward(ctx, uv, d, o, api.RT_QUADRILINEAR, out, None, duv_ref, ddir_ref)
     assert torch.equal(duv, duv_ref) and torch.equal(ddir, ddir_ref)
+
+
+def test_fullsize_world_step(full):
+    """The world-space variant as the benchmark's world workload runs it: the same
+    frames with its bumpy per-fragment normals (bench.variant_inputs), one
+    rt_shade_world and one rt_shade_world_backward over all 124.4 M fragments.
+    The sample against the oracle's Eq. 1a lookup (colours, UV, direction and
+    normal gradients away from kinks), the texel-gradient sum rule on the whole
+    step."""
+    import bench
+
+    ctx, g, sel, textures = full["ctx"], full["g"], full["sel"], full["textures"]
+    dev = full["out"].device
+    uv, d, o = full["uv"].view(-1, 2), full["d"].view(-1, 3), full["o"].view(-1)
+    nrm = bench.variant_inputs(None, torch, dev, uv, d, 0, 0)
+    out = api.rt_shade_world(ctx, uv, d, nrm, o, api.RT_QUADRILINEAR)
+    dtex = {k: torch.empty((N, N, BUCKETS, BUCKETS, 4), device=dev) for k in (0, 1)}
+    duv, ddir, dnrm = torch.empty_like(uv), torch.empty_like(d), torch.empty_like(d)
+    api.rt_shade_world_backward(ctx, uv, d, nrm, o, api.RT_QUADRILINEAR, out, dtex, duv, ddir, dnrm)
+    assert api.rt_get_error(ctx) == api.RT_OK
+    for k in (0, 1):
+        lhs = dtex[k].double().sum(dim=(0, 1, 2, 3))
+        rhs = (out.double() * (o == k).unsqueeze(-1)).sum(dim=0)
+        torch.testing.assert_close(lhs, rhs, rtol=1e-4, atol=1e-3)
+    del dtex
+    t_sel = torch.from_numpy(sel).to(dev)
+    N_sel = nrm[t_sel].cpu().numpy()
+    got = out[t_sel].cpu().numpy()
+    ref, flags = oracle.shade_world(textures, g.uv[sel], g.dir[sel], N_sel, g.obj[sel], oracle.QUADRILINEAR)
+    assert flags == 0
+    assert np.abs(got - ref).max() <= COLOUR_TOL
+    gout = got.astype(np.float64)
+    _, guv, gdir, gnrm, _ = oracle.shade_world_backward(textures, g.uv[sel], g.dir[sel], N_sel, g.obj[sel],
+                                                        oracle.QUADRILINEAR, gout, want_tex=False)
+    _, oc, _ = oracle.locate_world(textures, g.uv[sel], g.dir[sel], N_sel, g.obj[sel], oracle.QUADRILINEAR)
+    far = (np.abs(oc - np.round(oc)) > 1e-3).all(axis=1) & (g.obj[sel] >= 0)
+    lo = 1.0 / N - 1.0
+    far &= (np.abs(np.abs((oc[:, 2:] + 0.5) * 2 / N - 1) - abs(lo)) > 1e-3).all(axis=1)
+    assert far.sum() > 50000
+    for got_c, ref_c in ((duv[t_sel].cpu().numpy(), guv), (ddir[t_sel].cpu().numpy(), gdir),
+                         (dnrm[t_sel].cpu().numpy(), gnrm)):
+        scale = np.abs(ref_c[far]).max()
+        assert np.all(np.abs(got_c[far] - ref_c[far]) <= 1e-3 * np.abs(ref_c[far]) + 1e-5 * scale)
