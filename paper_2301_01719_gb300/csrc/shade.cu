@@ -163,7 +163,9 @@ __global__ void __launch_bounds__(kShadeThreads) multi_shade_kernel(const TexDes
 
 // S a power of two <= 32: one lookup per lane, lanes f S .. f S + S - 1 of a
 // warp share fragment f (coalesced direction loads, 32 lookups in flight per
-// warp) and sum by butterfly shuffles.
+// warp) and sum by butterfly shuffles.  Each lane loads the inputs of its next
+// lookup before filtering the current one, so their DRAM latency overlaps the
+// gathers (which hit L1 and L2: a bit texture is small).
 template <int FILTER>
 __global__ void __launch_bounds__(kShadeThreads) multi_shade_lanes_kernel(const TexDesc* __restrict__ table,
                                                                           int n_obj, const float* __restrict__ uv,
@@ -171,22 +173,38 @@ __global__ void __launch_bounds__(kShadeThreads) multi_shade_lanes_kernel(const 
                                                                           const int32_t* __restrict__ obj, int64_t F,
                                                                           float* __restrict__ out, unsigned* status) {
     const int lane = threadIdx.x & 31;
+    const int lg = __ffs(S) - 1;  // S = 2^lg
     const int64_t total = F * S;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = warp0 * 32; base < total; base += warps * 32) {
+    const int64_t stride = (((int64_t)gridDim.x * blockDim.x) >> 5) * 32;
+    float2 q = make_float2(0.f, 0.f);
+    float ix = 0.f, iy = 0.f, iz = 0.f;
+    int32_t o = -1;
+    auto fetch = [&](int64_t e) {
+        if (e < total) {
+            const int64_t f = e >> lg;
+            q = reinterpret_cast<const float2*>(uv)[f];
+            o = obj[f];
+            ix = dirs[3 * e];
+            iy = dirs[3 * e + 1];
+            iz = dirs[3 * e + 2];
+        }
+    };
+    fetch(warp0 * 32 + lane);
+    for (int64_t base = warp0 * 32; base < total; base += stride) {
         const int64_t e = base + lane;
+        const float2 cq = q;
+        const float cx = ix, cy = iy, cz = iz;
+        const int32_t co = o;
+        fetch(e + stride);
         float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
         int bad = 0;
         if (e < total) {
-            const int64_t f = e / S;
-            const float2 q = reinterpret_cast<const float2*>(uv)[f];
-            const float* I = dirs + 3 * e;
             TexDesc d;
-            if (fragment_valid(table, n_obj, obj[f], q.x, q.y, I[0], I[1], I[2], status, d))
-                c = filter_any<FILTER>(d, locate<FILTER>(d, q.x, q.y, I[0], I[1], I[2]));
+            if (fragment_valid(table, n_obj, co, cq.x, cq.y, cx, cy, cz, status, d))
+                c = filter_any<FILTER>(d, locate<FILTER>(d, cq.x, cq.y, cx, cy, cz));
             else
-                bad = obj[f] >= 0;  // an invalid sample zeroes its fragment
+                bad = co >= 0;  // an invalid sample zeroes its fragment
         }
         for (int off = 1; off < S; off <<= 1) {
             c.x += __shfl_xor_sync(0xffffffffu, c.x, off);
@@ -199,7 +217,7 @@ __global__ void __launch_bounds__(kShadeThreads) multi_shade_lanes_kernel(const 
             const float inv = 1.0f / (float)S;
             const float4 r = bad ? make_float4(0.f, 0.f, 0.f, 0.f)
                                  : make_float4(c.x * inv, c.y * inv, c.z * inv, c.w * inv);
-            __stcs(reinterpret_cast<float4*>(out) + e / S, r);
+            __stcs(reinterpret_cast<float4*>(out) + (e >> lg), r);
         }
     }
 }
