@@ -980,12 +980,17 @@ def run_variant(a):
     dnrm = torch.empty_like(dirs)
     stream = torch.cuda.current_stream(dev)
 
+    frames = (a.views, a.height, a.width)
+    fv = [t.view(*frames, -1) for t in (uv, dirs, extra, out, duv, ddir, dnrm)] if not shadow else None
+    o_v = obj.view(*frames)
+
     def step():
         if shadow:
             api.rt_shade_multi(ctx, uv, extra, obj, filt, out)
-        else:
-            api.rt_shade_world(ctx, uv, dirs, extra, obj, filt, out)
-            api.rt_shade_world_backward(ctx, uv, dirs, extra, obj, filt, out, None, duv, ddir, dnrm)
+        else:  # the screen-tiled world-space calls
+            api.rt_shade_world_batched(ctx, fv[0], fv[1], fv[2], o_v, filt, fv[3])
+            api.rt_shade_world_batched_backward(ctx, fv[0], fv[1], fv[2], o_v, filt, fv[3], None, fv[4], fv[5],
+                                                fv[6])
 
     for _ in range(a.warmup):
         step()
@@ -1013,7 +1018,8 @@ def run_variant(a):
         kernel, metric = "multi_shade_kernel", "area-shadow lookups (Gfrag/s, S light samples per fragment)"
     else:
         nbytes = F * ((8 + 12 + 12 + 4 + 16) + (8 + 12 + 12 + 4 + 16 + 8 + 12 + 12))  # fwd + bwd streams
-        kernel, metric = "world_shade_kernel + world_backward_kernel", "world-space lookups (Gfrag/s), fwd + bwd"
+        kernel = "world_shade_kernel<tiled> + world_backward_kernel<tiled>"
+        metric = "world-space lookups (Gfrag/s), fwd + bwd"
     achieved = nbytes / (ms * 1e-3) / 1e9
     result = {
         "metric": metric, "value": value, "unit": "Gfrag/s", "n_gpus": world, "steps": a.steps,

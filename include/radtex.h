@@ -349,7 +349,8 @@ rt_status rt_shade_multi(rt_ctx* ctx, const float* uv, const float* dirs, int32_
  * non-finite normal raises RT_ERR_NONFINITE and gives a zero fragment.
  * rt_locate_world is rt_locate for this lookup.  rt_shade_world_backward is
  * rt_shade_backward for it: dL_dnrm (F x 3 or NULL) receives dL/dN, which
- * equals dL/dI.  These run on the flat fragment stream (no screen tiling). */
+ * equals dL/dI.  These run on the flat fragment stream; rt_shade_world_batched
+ * and rt_shade_world_batched_backward (below) walk screen tiles. */
 rt_status rt_shade_world(rt_ctx* ctx, const float* uv, const float* dir, const float* nrm, const int32_t* obj,
                          int64_t F, rt_filter filter, float* out, rt_stream_t stream);
 rt_status rt_locate_world(rt_ctx* ctx, const float* uv, const float* dir, const float* nrm, const int32_t* obj,
@@ -397,6 +398,23 @@ rt_status rt_shade_batched_l2_step(rt_ctx* ctx, const float* uv, const float* di
                                    int32_t height, int32_t width, rt_filter filter, const float* target, float scale,
                                    float* out, double* sums, float* const* dL_dtex, int32_t n_dtex, float* dL_duv,
                                    float* dL_ddir, int32_t flags, rt_stream_t stream);
+
+/* The world-space lookup (Eq. 1a, rt_shade_world) over a batch of frames:
+ * uv, dir, nrm (views x height x width x 2, 3, 3 floats) and obj laid out as
+ * in rt_shade_batched, walked in screen tiles of the context's forward tile
+ * for `filter` (the backward's tile for the gradients).  Results equal
+ * rt_shade_world / rt_shade_world_backward on the same arrays: colours and
+ * UV / direction / normal gradients bit for bit, texel gradients up to the
+ * order of FP32 atomic additions.  Arguments, alignment, flags and errors as
+ * there; 0 <= height, width <= 65536. */
+rt_status rt_shade_world_batched(rt_ctx* ctx, const float* uv, const float* dir, const float* nrm,
+                                 const int32_t* obj, int32_t views, int32_t height, int32_t width, rt_filter filter,
+                                 float* out, rt_stream_t stream);
+rt_status rt_shade_world_batched_backward(rt_ctx* ctx, const float* uv, const float* dir, const float* nrm,
+                                          const int32_t* obj, int32_t views, int32_t height, int32_t width,
+                                          rt_filter filter, const float* dL_dout, float* const* dL_dtex,
+                                          int32_t n_dtex, float* dL_duv, float* dL_ddir, float* dL_dnrm,
+                                          int32_t flags, rt_stream_t stream);
 
 /* Sets the screen tile of the batched kernels for `filter`, forward and
  * backward: warp tiles of tw x th fragments (tw * th = 32, tw a multiple of 4)

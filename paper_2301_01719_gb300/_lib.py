@@ -65,6 +65,9 @@ SIGNATURES = {
     "rt_shade_multi": (_I32, [_P, _P, _P, _I32, _P, _I64, _I32, _P, _P]),
     "rt_locate_world": (_I32, [_P, _P, _P, _P, _P, _I64, _I32, _P, _P, _P]),
     "rt_shade_world_backward": (_I32, [_P, _P, _P, _P, _P, _I64, _I32, _P, _P, _I32, _P, _P, _P, _I32, _P]),
+    "rt_shade_world_batched": (_I32, [_P, _P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, _P]),
+    "rt_shade_world_batched_backward": (_I32, [_P, _P, _P, _P, _P, _I32, _I32, _I32, _I32, _P, ctypes.POINTER(_P),
+                                               _I32, _P, _P, _P, _I32, _P]),
     "rt_create_palette_texture": (_I32, [_P, _I32, _I32, _I32, _I32, _I32, _I32, _P, _P, _I32, _P]),
     "rt_palette_size": (_I32, [_P, _I32, _P]),
     "rt_kmeans_init": (_I32, [_P, _I32, _I32, _P, _P, _P]),

@@ -556,6 +556,34 @@ def rt_shade_world_backward(ctx: Context, uv, dirs, nrm, obj, filter: int, dL_do
               _stream(stream, uv.device))
 
 
+def rt_shade_world_batched(ctx: Context, uv, dirs, nrm, obj, filter: int = RT_QUADRILINEAR, out=None, stream=None):
+    """World-space synthesis of views x height x width fragments in screen tiles; uv (V, H, W, 2), dir and
+    nrm (V, H, W, 3), obj (V, H, W); returns (V, H, W, 4) colours."""
+    F = _gbuffer(uv, dirs, obj)
+    V, H, W = _frames(uv, dirs, obj)
+    _normals(nrm, F)
+    if out is None:
+        out = torch.empty((V, H, W, 4), dtype=torch.float32, device=uv.device)
+    _check(out, "out", torch.float32, 4)
+    _lib.call("rt_shade_world_batched", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(nrm), _ptr(obj), V, H, W,
+              int(filter), _ptr(out), _stream(stream, uv.device))
+    return out
+
+
+def rt_shade_world_batched_backward(ctx: Context, uv, dirs, nrm, obj, filter: int, dL_dout: torch.Tensor,
+                                    dL_dtex=None, dL_duv=None, dL_ddir=None, dL_dnrm=None, flags: int = 0,
+                                    stream=None) -> None:
+    F = _gbuffer(uv, dirs, obj)
+    V, H, W = _frames(uv, dirs, obj)
+    _normals(nrm, F)
+    arr, n_dtex = _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir)
+    if dL_dnrm is not None:
+        _normals(dL_dnrm, F)
+    _lib.call("rt_shade_world_batched_backward", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(nrm), _ptr(obj), V, H, W,
+              int(filter), _ptr(dL_dout), arr, n_dtex, _ptr(dL_duv), _ptr(dL_ddir), _ptr(dL_dnrm), int(flags),
+              _stream(stream, uv.device))
+
+
 def rt_footprint(ctx: Context, uv, dirs, obj, filter: int = RT_QUADRILINEAR, n_counts: int = RT_MAX_OBJECTS,
                  stream=None) -> list[int]:
     """Distinct texels read, per object id (synchronises)."""

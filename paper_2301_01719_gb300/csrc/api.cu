@@ -586,8 +586,8 @@ static rt_status shade_backward_impl(rt_ctx* ctx, const float* uv, const float* 
     }
     if (e == cudaSuccess && F > 0) {
         if (nrm)
-            e = rt::launch_world_backward(ctx->d_table, ctx->n_obj, uv, dir, nrm, obj, F, filter, dL_dout, grads, any,
-                                          dL_duv, dL_ddir, dL_dnrm, accumulate, deterministic, ctx->d_status, s);
+            e = rt::launch_world_backward(ctx->d_table, ctx->n_obj, uv, dir, nrm, obj, F, filter, T, dL_dout, grads,
+                                          any, dL_duv, dL_ddir, dL_dnrm, accumulate, deterministic, ctx->d_status, s);
         else if (fused)
             e = rt::launch_fused_l2(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, T, ctx->spec, fused->target,
                                     fused->scale, fused->out, fused->sums, grads, any, dL_duv, dL_ddir, accumulate,
@@ -718,8 +718,9 @@ rt_status rt_shade_world(rt_ctx* ctx, const float* uv, const float* dir, const f
     if (!nrm || !aligned16(nrm) || !out || !aligned16(out)) return RT_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return RT_ERR_CUDA;
-    return cuda_status(rt::launch_world_shade(ctx->d_table, ctx->n_obj, uv, dir, nrm, obj, F, filter, out, nullptr,
-                                              nullptr, ctx->d_status, (cudaStream_t)stream));
+    return cuda_status(rt::launch_world_shade(ctx->d_table, ctx->n_obj, uv, dir, nrm, obj, F, filter,
+                                              rt::flat_tiling(), out, nullptr, nullptr, ctx->d_status,
+                                              (cudaStream_t)stream));
 }
 
 rt_status rt_locate_world(rt_ctx* ctx, const float* uv, const float* dir, const float* nrm, const int32_t* obj,
@@ -731,8 +732,9 @@ rt_status rt_locate_world(rt_ctx* ctx, const float* uv, const float* dir, const 
     if (!nrm || !aligned16(nrm) || !idx || !coord || !aligned16(idx) || !aligned16(coord)) return RT_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return RT_ERR_CUDA;
-    return cuda_status(rt::launch_world_shade(ctx->d_table, ctx->n_obj, uv, dir, nrm, obj, F, filter, nullptr, idx,
-                                              coord, ctx->d_status, (cudaStream_t)stream));
+    return cuda_status(rt::launch_world_shade(ctx->d_table, ctx->n_obj, uv, dir, nrm, obj, F, filter,
+                                              rt::flat_tiling(), nullptr, idx, coord, ctx->d_status,
+                                              (cudaStream_t)stream));
 }
 
 rt_status rt_shade_world_backward(rt_ctx* ctx, const float* uv, const float* dir, const float* nrm,
@@ -787,6 +789,40 @@ rt_status rt_shade_batched_l2_step(rt_ctx* ctx, const float* uv, const float* di
     const FusedL2 fused = {target, scale, out, sums};
     return shade_backward_impl(ctx, uv, dir, obj, F, filter, T, nullptr, dL_dtex, n_dtex, dL_duv, dL_ddir, flags,
                                stream, nullptr, nullptr, &fused);
+}
+
+rt_status rt_shade_world_batched(rt_ctx* ctx, const float* uv, const float* dir, const float* nrm,
+                                 const int32_t* obj, int32_t views, int32_t height, int32_t width, rt_filter filter,
+                                 float* out, rt_stream_t stream) {
+    if (!ctx || !valid_filter(filter) || views < 0 || height < 0 || width < 0 || height > 65536 || width > 65536)
+        return RT_ERR_INVALID_ARG;
+    const int64_t F = (int64_t)views * height * width;
+    rt_status st = check_gbuffer(uv, dir, obj, F);
+    if (st != RT_OK) return st;
+    if (F == 0) return RT_OK;
+    if (!nrm || !aligned16(nrm) || !out || !aligned16(out)) return RT_ERR_INVALID_ARG;
+    rt::Tiling T;
+    if (!frames_tiling(ctx, kForward, views, height, width, filter, &T)) return RT_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    return cuda_status(rt::launch_world_shade(ctx->d_table, ctx->n_obj, uv, dir, nrm, obj, F, filter, T, out, nullptr,
+                                              nullptr, ctx->d_status, (cudaStream_t)stream));
+}
+
+rt_status rt_shade_world_batched_backward(rt_ctx* ctx, const float* uv, const float* dir, const float* nrm,
+                                          const int32_t* obj, int32_t views, int32_t height, int32_t width,
+                                          rt_filter filter, const float* dL_dout, float* const* dL_dtex,
+                                          int32_t n_dtex, float* dL_duv, float* dL_ddir, float* dL_dnrm,
+                                          int32_t flags, rt_stream_t stream) {
+    if (!ctx || !valid_filter(filter) || views < 0 || height < 0 || width < 0 || height > 65536 || width > 65536)
+        return RT_ERR_INVALID_ARG;
+    const int64_t F = (int64_t)views * height * width;
+    if (F > 0 && !nrm) return RT_ERR_INVALID_ARG;
+    rt::Tiling T = rt::flat_tiling();
+    if (F > 0 && !frames_tiling(ctx, kBackward, views, height, width, filter, &T)) return RT_ERR_INVALID_ARG;
+    static const float kNone[4] = {0.f, 0.f, 0.f, 0.f};  // an unused non-null marker for F = 0
+    return shade_backward_impl(ctx, uv, dir, obj, F, filter, T, dL_dout, dL_dtex, n_dtex, dL_duv, dL_ddir, flags,
+                               stream, nrm ? nrm : kNone, dL_dnrm);
 }
 
 rt_status rt_prepare_deterministic(rt_ctx* ctx) {

@@ -102,17 +102,18 @@ cudaError_t launch_backward(const TexDesc* table, int n_obj, const float* uv, co
 
 // World-space backward (Eq. 1a with a per-fragment normal): the streamer of
 // the tangent-space backward with the normal as a fourth staged stream, over
-// the flat fragment stream.  dL/dI = dL/dN, since A depends on h = I + N only.
-template <int FILTER, bool DET>
+// the flat fragment stream or, TILED, over screen tiles of a batch of frames.
+// dL/dI = dL/dN, since A depends on h = I + N only.
+template <int FILTER, bool DET, bool TILED>
 __global__ void __launch_bounds__(kBackThreads) world_backward_kernel(
     const TexDesc* __restrict__ table, int n_obj, const float* __restrict__ uv, const float* __restrict__ dir,
-    const float* __restrict__ nrm, const int32_t* __restrict__ obj, int64_t F, const float* __restrict__ dL_dout,
+    const float* __restrict__ nrm, const int32_t* __restrict__ obj, int64_t F, Tiling tiling,
+    const float* __restrict__ dL_dout,
     const __grid_constant__ GradTable grads, bool any_grad, float* __restrict__ dL_duv, float* __restrict__ dL_ddir,
     float* __restrict__ dL_dnrm, bool accumulate, unsigned* status) {
     __shared__ WarpStage<true, 2, true> stages[kBackWarps];
     const bool coord_grads = dL_duv || dL_ddir || dL_dnrm;
-    const Tiling flat = flat_tiling();
-    for_each_fragment<kBackWarps, true, false, 2, true>(uv, dir, obj, dL_dout, F, flat, stages,
+    for_each_fragment<kBackWarps, true, TILED, 2, true>(uv, dir, obj, dL_dout, F, tiling, stages,
                                                         [&](int64_t f, const Frag& q, float4 go) {
         float2 guv = make_float2(0.f, 0.f);
         float3 gh = make_float3(0.f, 0.f, 0.f);
@@ -152,49 +153,51 @@ __global__ void __launch_bounds__(kBackThreads) world_backward_kernel(
     }, nrm);
 }
 
-template <int FILTER, bool DET>
+template <int FILTER, bool DET, bool TILED>
 static cudaError_t launch_world_backward_t(const TexDesc* table, int n_obj, const float* uv, const float* dir,
-                                           const float* nrm, const int32_t* obj, int64_t F, const float* dL_dout,
-                                           const GradTable& grads, bool any_grad, float* dL_duv, float* dL_ddir,
-                                           float* dL_dnrm, bool accumulate, unsigned* status, cudaStream_t stream) {
-    const unsigned grid = persistent_grid(world_backward_kernel<FILTER, DET>, kBackThreads, (F + kChunk - 1) / kChunk);
-    world_backward_kernel<FILTER, DET><<<grid, kBackThreads, 0, stream>>>(
-        table, n_obj, uv, dir, nrm, obj, F, dL_dout, grads, any_grad, dL_duv, dL_ddir, dL_dnrm, accumulate, status);
+                                           const float* nrm, const int32_t* obj, int64_t F, const Tiling& T,
+                                           const float* dL_dout, const GradTable& grads, bool any_grad, float* dL_duv,
+                                           float* dL_ddir, float* dL_dnrm, bool accumulate, unsigned* status,
+                                           cudaStream_t stream) {
+    const unsigned grid = persistent_grid(world_backward_kernel<FILTER, DET, TILED>, kBackThreads,
+                                          chunk_count_host(T, F, kBackWarps));
+    world_backward_kernel<FILTER, DET, TILED><<<grid, kBackThreads, 0, stream>>>(
+        table, n_obj, uv, dir, nrm, obj, F, T, dL_dout, grads, any_grad, dL_duv, dL_ddir, dL_dnrm, accumulate,
+        status);
     return cudaGetLastError();
 }
 
-template <bool DET>
+template <bool DET, bool TILED>
 static cudaError_t launch_world_backward_d(const TexDesc* table, int n_obj, const float* uv, const float* dir,
                                            const float* nrm, const int32_t* obj, int64_t F, int filter,
-                                           const float* dL_dout, const GradTable& grads, bool any_grad,
-                                           float* dL_duv, float* dL_ddir, float* dL_dnrm, bool accumulate,
-                                           unsigned* status, cudaStream_t stream) {
+                                           const Tiling& T, const float* dL_dout, const GradTable& grads,
+                                           bool any_grad, float* dL_duv, float* dL_ddir, float* dL_dnrm,
+                                           bool accumulate, unsigned* status, cudaStream_t stream) {
+#define RT_WBWD(FILT)                                                                                              \
+    launch_world_backward_t<FILT, DET, TILED>(table, n_obj, uv, dir, nrm, obj, F, T, dL_dout, grads, any_grad,      \
+                                              dL_duv, dL_ddir, dL_dnrm, accumulate, status, stream)
     switch (filter) {
         case RT_NEAREST:
-            return launch_world_backward_t<RT_NEAREST, DET>(table, n_obj, uv, dir, nrm, obj, F, dL_dout, grads,
-                                                            any_grad, dL_duv, dL_ddir, dL_dnrm, accumulate, status,
-                                                            stream);
+            return RT_WBWD(RT_NEAREST);
         case RT_ANGULAR_BILINEAR:
-            return launch_world_backward_t<RT_ANGULAR_BILINEAR, DET>(table, n_obj, uv, dir, nrm, obj, F, dL_dout,
-                                                                     grads, any_grad, dL_duv, dL_ddir, dL_dnrm,
-                                                                     accumulate, status, stream);
+            return RT_WBWD(RT_ANGULAR_BILINEAR);
         default:
-            return launch_world_backward_t<RT_QUADRILINEAR, DET>(table, n_obj, uv, dir, nrm, obj, F, dL_dout, grads,
-                                                                 any_grad, dL_duv, dL_ddir, dL_dnrm, accumulate,
-                                                                 status, stream);
+            return RT_WBWD(RT_QUADRILINEAR);
     }
+#undef RT_WBWD
 }
 
 cudaError_t launch_world_backward(const TexDesc* table, int n_obj, const float* uv, const float* dir,
-                                  const float* nrm, const int32_t* obj, int64_t F, int filter, const float* dL_dout,
-                                  const GradTable& grads, bool any_grad, float* dL_duv, float* dL_ddir,
-                                  float* dL_dnrm, bool accumulate, bool deterministic, unsigned* status,
-                                  cudaStream_t stream) {
-    if (deterministic)
-        return launch_world_backward_d<true>(table, n_obj, uv, dir, nrm, obj, F, filter, dL_dout, grads, any_grad,
-                                             dL_duv, dL_ddir, dL_dnrm, accumulate, status, stream);
-    return launch_world_backward_d<false>(table, n_obj, uv, dir, nrm, obj, F, filter, dL_dout, grads, any_grad,
-                                          dL_duv, dL_ddir, dL_dnrm, accumulate, status, stream);
+                                  const float* nrm, const int32_t* obj, int64_t F, int filter, const Tiling& T,
+                                  const float* dL_dout, const GradTable& grads, bool any_grad, float* dL_duv,
+                                  float* dL_ddir, float* dL_dnrm, bool accumulate, bool deterministic,
+                                  unsigned* status, cudaStream_t stream) {
+#define RT_WBWD_D(DET, TILED)                                                                                      \
+    launch_world_backward_d<DET, TILED>(table, n_obj, uv, dir, nrm, obj, F, filter, T, dL_dout, grads, any_grad,    \
+                                        dL_duv, dL_ddir, dL_dnrm, accumulate, status, stream)
+    if (T.W > 0) return deterministic ? RT_WBWD_D(true, true) : RT_WBWD_D(false, true);
+    return deterministic ? RT_WBWD_D(true, false) : RT_WBWD_D(false, false);
+#undef RT_WBWD_D
 }
 
 // Fixed-point sums (deterministic mode) -> FP32 gradients, added to or overwriting dst.

@@ -60,6 +60,9 @@ __device__ __forceinline__ void reduce_quadrilinear_taps(const Lookup<RT_QUADRIL
         // tap: lanes 2m and 2m + 1 (horizontal neighbours on screen) compare
         // their tap addresses, and on a match the odd lane hands its
         // contribution to the even lane, which issues one reduction for both.
+        // A lane without a gradient buffer leaves before the exchange (its
+        // partner sees it inactive and reduces alone).
+        if (!grad) return;
         const unsigned active = __activemask();
         const int lane = threadIdx.x & 31;
         const bool partner = (active >> (lane ^ 1)) & 1u;
@@ -67,9 +70,9 @@ __device__ __forceinline__ void reduce_quadrilinear_taps(const Lookup<RT_QUADRIL
         for (int b = 0; b < 4; ++b)
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float w = grad ? wu[b & 1] * wv[b >> 1] * ws[k & 1] * wt[k >> 1] : 0.f;
+                const float w = wu[b & 1] * wv[b >> 1] * ws[k & 1] * wt[k >> 1];
                 const int64_t idx = pl[k] + o[b];
-                float* addr = grad ? static_cast<float*>(grad) + 4 * idx : nullptr;
+                float* addr = static_cast<float*>(grad) + 4 * idx;
                 // a lane with nothing to add gets a key no other lane has
                 const unsigned long long key =
                     w != 0.f ? (unsigned long long)addr : (~0ull - (unsigned long long)lane);

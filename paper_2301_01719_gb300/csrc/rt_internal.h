@@ -89,14 +89,15 @@ cudaError_t launch_bake_shadow(const rt_bake_scene& S, int surface, void* dst, i
 cudaError_t launch_multi_shade(const TexDesc* table, int n_obj, const float* uv, const float* dirs, int S,
                                const int32_t* obj, int64_t F, int filter, float* out, unsigned* status,
                                cudaStream_t stream);
+// World-space kernels: T is flat_tiling() for the flat stream, or a screen tiling.
 cudaError_t launch_world_shade(const TexDesc* table, int n_obj, const float* uv, const float* dir, const float* nrm,
-                               const int32_t* obj, int64_t F, int filter, float* out, int32_t* idx, float* coord,
-                               unsigned* status, cudaStream_t stream);
+                               const int32_t* obj, int64_t F, int filter, const Tiling& T, float* out, int32_t* idx,
+                               float* coord, unsigned* status, cudaStream_t stream);
 cudaError_t launch_world_backward(const TexDesc* table, int n_obj, const float* uv, const float* dir,
-                                  const float* nrm, const int32_t* obj, int64_t F, int filter, const float* dL_dout,
-                                  const GradTable& grads, bool any_grad, float* dL_duv, float* dL_ddir,
-                                  float* dL_dnrm, bool accumulate, bool deterministic, unsigned* status,
-                                  cudaStream_t stream);
+                                  const float* nrm, const int32_t* obj, int64_t F, int filter, const Tiling& T,
+                                  const float* dL_dout, const GradTable& grads, bool any_grad, float* dL_duv,
+                                  float* dL_ddir, float* dL_dnrm, bool accumulate, bool deterministic,
+                                  unsigned* status, cudaStream_t stream);
 int64_t kmeans_tc_scratch_bytes(int W, int H, int n, int K);
 cudaError_t launch_kmeans_assign_tc(const TexDesc& d, int K, const float* C, uint32_t* index, float* dist,
                                     void* scratch, unsigned* status, cudaStream_t stream);

@@ -71,18 +71,19 @@ __global__ void __launch_bounds__(kShadeThreads) locate_kernel(const TexDesc* __
 
 // World-space forward and lookup (Eq. 1a with a per-fragment normal): the
 // streamer of the tangent-space kernels with a fourth staged stream, the
-// normal, over the flat fragment stream.
-template <int FILTER>
+// normal, over the flat fragment stream or, TILED, over screen tiles of a batch
+// of frames.
+template <int FILTER, bool TILED>
 __global__ void __launch_bounds__(kShadeThreads) world_shade_kernel(const TexDesc* __restrict__ table, int n_obj,
                                                                     const float* __restrict__ uv,
                                                                     const float* __restrict__ dir,
                                                                     const float* __restrict__ nrm,
                                                                     const int32_t* __restrict__ obj, int64_t F,
-                                                                    float* __restrict__ out, int32_t* __restrict__ idx,
+                                                                    Tiling tiling, float* __restrict__ out,
+                                                                    int32_t* __restrict__ idx,
                                                                     float* __restrict__ coord, unsigned* status) {
     __shared__ WarpStage<false, 2, true> stages[kShadeWarps];
-    const Tiling flat = flat_tiling();
-    for_each_fragment<kShadeWarps, false, false, 2, true>(uv, dir, obj, nullptr, F, flat, stages,
+    for_each_fragment<kShadeWarps, false, TILED, 2, true>(uv, dir, obj, nullptr, F, tiling, stages,
                                                           [&](int64_t f, const Frag& q, float4) {
         float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
         int4 Ix = make_int4(0, 0, 0, 0);
@@ -104,30 +105,43 @@ __global__ void __launch_bounds__(kShadeThreads) world_shade_kernel(const TexDes
     }, nrm);
 }
 
-cudaError_t launch_world_shade(const TexDesc* table, int n_obj, const float* uv, const float* dir, const float* nrm,
-                               const int32_t* obj, int64_t F, int filter, float* out, int32_t* idx, float* coord,
-                               unsigned* status, cudaStream_t stream) {
-    const int64_t items = (F + kChunk - 1) / kChunk;  // chunks of the flat stream
-    switch (filter) {
-        case RT_NEAREST: {
-            const unsigned grid = persistent_grid(world_shade_kernel<RT_NEAREST>, kShadeThreads, items);
-            world_shade_kernel<RT_NEAREST><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dir, nrm, obj, F,
-                                                                               out, idx, coord, status);
-            break;
-        }
-        case RT_ANGULAR_BILINEAR: {
-            const unsigned grid = persistent_grid(world_shade_kernel<RT_ANGULAR_BILINEAR>, kShadeThreads, items);
-            world_shade_kernel<RT_ANGULAR_BILINEAR><<<grid, kShadeThreads, 0, stream>>>(
-                table, n_obj, uv, dir, nrm, obj, F, out, idx, coord, status);
-            break;
-        }
-        default: {
-            const unsigned grid = persistent_grid(world_shade_kernel<RT_QUADRILINEAR>, kShadeThreads, items);
-            world_shade_kernel<RT_QUADRILINEAR><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dir, nrm, obj,
-                                                                                    F, out, idx, coord, status);
-        }
-    }
+template <int FILTER, bool TILED>
+static cudaError_t launch_world_shade_t(const TexDesc* table, int n_obj, const float* uv, const float* dir,
+                                        const float* nrm, const int32_t* obj, int64_t F, const Tiling& T, float* out,
+                                        int32_t* idx, float* coord, unsigned* status, cudaStream_t stream) {
+    const unsigned grid = persistent_grid(world_shade_kernel<FILTER, TILED>, kShadeThreads,
+                                          chunk_count_host(T, F, kShadeWarps));
+    world_shade_kernel<FILTER, TILED><<<grid, kShadeThreads, 0, stream>>>(table, n_obj, uv, dir, nrm, obj, F, T,
+                                                                          out, idx, coord, status);
     return cudaGetLastError();
+}
+
+template <bool TILED>
+static cudaError_t launch_world_shade_f(const TexDesc* table, int n_obj, const float* uv, const float* dir,
+                                        const float* nrm, const int32_t* obj, int64_t F, int filter, const Tiling& T,
+                                        float* out, int32_t* idx, float* coord, unsigned* status,
+                                        cudaStream_t stream) {
+    switch (filter) {
+        case RT_NEAREST:
+            return launch_world_shade_t<RT_NEAREST, TILED>(table, n_obj, uv, dir, nrm, obj, F, T, out, idx, coord,
+                                                           status, stream);
+        case RT_ANGULAR_BILINEAR:
+            return launch_world_shade_t<RT_ANGULAR_BILINEAR, TILED>(table, n_obj, uv, dir, nrm, obj, F, T, out, idx,
+                                                                    coord, status, stream);
+        default:
+            return launch_world_shade_t<RT_QUADRILINEAR, TILED>(table, n_obj, uv, dir, nrm, obj, F, T, out, idx,
+                                                                coord, status, stream);
+    }
+}
+
+cudaError_t launch_world_shade(const TexDesc* table, int n_obj, const float* uv, const float* dir, const float* nrm,
+                               const int32_t* obj, int64_t F, int filter, const Tiling& T, float* out, int32_t* idx,
+                               float* coord, unsigned* status, cudaStream_t stream) {
+    if (T.W > 0)
+        return launch_world_shade_f<true>(table, n_obj, uv, dir, nrm, obj, F, filter, T, out, idx, coord, status,
+                                          stream);
+    return launch_world_shade_f<false>(table, n_obj, uv, dir, nrm, obj, F, filter, T, out, idx, coord, status,
+                                       stream);
 }
 
 // S lookups per fragment, averaged (area lights over a shadow texture, Section

@@ -172,3 +172,67 @@ def test_cuda_graph_capture_replays_identically(scene):
     for k in dt:
         assert torch.allclose(eager_dt[k], dt[k], rtol=1e-5, atol=1e-6)
     assert api.rt_get_error(ctx) == api.RT_OK
+
+
+def bumpy(V, Hh, Ww, seed):
+    rng = np.random.default_rng(seed)
+    N = np.concatenate([rng.normal(scale=0.3, size=(V * Hh * Ww, 2)), np.ones((V * Hh * Ww, 1))], 1)
+    return to_dev((N / np.linalg.norm(N, axis=1, keepdims=True)).astype(np.float32)).reshape(V, Hh, Ww, 3)
+
+
+@pytest.mark.parametrize("shape", [(2, 50, 60), (1, 33, 201), (1, 7, 3)])
+def test_world_batched_equals_flat(scene, shape):
+    """rt_shade_world_batched / rt_shade_world_batched_backward against the flat
+    world-space calls: colours and UV, direction and normal gradients bit for
+    bit for every tile shape, texel gradients up to the order of atomic
+    additions (bit for bit in the deterministic mode)."""
+    ctx, oids, texs, (W, H, n) = scene
+    V, Hh, Ww = shape
+    g, obj, uv, d, o = frames(V, Hh, Ww, oids)
+    N = bumpy(V, Hh, Ww, 3)
+    flat_args = (uv.reshape(-1, 2), d.reshape(-1, 3), N.reshape(-1, 3), o.reshape(-1))
+    for filt in (api.RT_NEAREST, api.RT_ANGULAR_BILINEAR, api.RT_QUADRILINEAR):
+        flat = api.rt_shade_world(ctx, *flat_args, filt).cpu().numpy()
+        for t in TILES[::3]:
+            api.rt_set_tile(ctx, filt, *t)
+            out = api.rt_shade_world_batched(ctx, uv, d, N, o, filt).reshape(-1, 4).cpu().numpy()
+            np.testing.assert_array_equal(out, flat, err_msg=f"tile {t} filter {filt}")
+    ref, _ = oracle.shade_world(texs, g.uv, g.dir, N.reshape(-1, 3).cpu().numpy(), obj, oracle.QUADRILINEAR)
+    assert np.abs(flat - ref).max() <= COLOUR_TOL
+    gout = to_dev(np.random.default_rng(2).normal(size=(V, Hh, Ww, 4)).astype(np.float32))
+    filt = api.RT_QUADRILINEAR
+    api.rt_prepare_deterministic(ctx)
+
+    def run(batched, flags):
+        duv, ddir, dnrm = torch.empty_like(uv), torch.empty_like(d), torch.empty_like(d)
+        dt = {o_: torch.empty((n, n, H, W, 4), device=uv.device) for o_ in oids}
+        if batched:
+            api.rt_shade_world_batched_backward(ctx, uv, d, N, o, filt, gout, dt, duv, ddir, dnrm, flags)
+        else:
+            api.rt_shade_world_backward(ctx, *flat_args, filt, gout.reshape(-1, 4), dt, duv.reshape(-1, 2),
+                                        ddir.reshape(-1, 3), dnrm.reshape(-1, 3), flags)
+        return [x.cpu().numpy() for x in (duv, ddir, dnrm)], {k: v.cpu().numpy() for k, v in dt.items()}
+
+    for flags in (0, api.RT_DETERMINISTIC):
+        a = run(False, flags)
+        for t in ((8, 4, 2, 2), (32, 1, 4, 1), (4, 8, 1, 4)):
+            api.rt_set_backward_tile(ctx, filt, *t)
+            b = run(True, flags)
+            for x, y in zip(a[0], b[0]):
+                np.testing.assert_array_equal(x, y)
+            for k in a[1]:
+                if flags:
+                    np.testing.assert_array_equal(a[1][k], b[1][k])
+                else:
+                    assert np.abs(a[1][k] - b[1][k]).max() <= 1e-5 * max(np.abs(a[1][k]).max(), 1.0)
+    assert api.rt_get_error(ctx) == api.RT_OK
+
+
+def test_world_batched_rejects_bad_shapes(scene):
+    ctx, oids, _, _ = scene
+    g, obj, uv, d, o = frames(1, 8, 8, oids)
+    N = bumpy(1, 8, 8, 4)
+    with pytest.raises(ValueError):
+        api.rt_shade_world_batched(ctx, uv.reshape(-1, 2), d.reshape(-1, 3), N.reshape(-1, 3), o.reshape(-1))
+    with pytest.raises(ValueError):
+        api.rt_shade_world_batched(ctx, uv, d, N[:, :4], o)

@@ -149,7 +149,8 @@ def test_fullsize_fused_l2_step(full):
 def test_fullsize_world_step(full):
     """The world-space variant as the benchmark's world workload runs it: the same
     frames with its bumpy per-fragment normals (bench.variant_inputs), one
-    rt_shade_world and one rt_shade_world_backward over all 124.4 M fragments.
+    rt_shade_world_batched and one rt_shade_world_batched_backward (screen
+    tiles) over all 124.4 M fragments.
     The sample against the oracle's Eq. 1a lookup (colours, UV, direction and
     normal gradients away from kinks), the texel-gradient sum rule on the whole
     step."""
@@ -157,13 +158,15 @@ def test_fullsize_world_step(full):
 
     ctx, g, sel, textures = full["ctx"], full["g"], full["sel"], full["textures"]
     dev = full["out"].device
-    uv, d, o = full["uv"].view(-1, 2), full["d"].view(-1, 3), full["o"].view(-1)
-    nrm = bench.variant_inputs(None, torch, dev, uv, d, 0, 0)
-    out = api.rt_shade_world(ctx, uv, d, nrm, o, api.RT_QUADRILINEAR)
+    uv4, d4, o3 = full["uv"], full["d"], full["o"]
+    nrm4 = bench.variant_inputs(None, torch, dev, uv4.view(-1, 2), d4.view(-1, 3), 0, 0).view(d4.shape)
+    out4 = api.rt_shade_world_batched(ctx, uv4, d4, nrm4, o3, api.RT_QUADRILINEAR)
     dtex = {k: torch.empty((N, N, BUCKETS, BUCKETS, 4), device=dev) for k in (0, 1)}
-    duv, ddir, dnrm = torch.empty_like(uv), torch.empty_like(d), torch.empty_like(d)
-    api.rt_shade_world_backward(ctx, uv, d, nrm, o, api.RT_QUADRILINEAR, out, dtex, duv, ddir, dnrm)
+    duv4, ddir4, dnrm4 = torch.empty_like(uv4), torch.empty_like(d4), torch.empty_like(d4)
+    api.rt_shade_world_batched_backward(ctx, uv4, d4, nrm4, o3, api.RT_QUADRILINEAR, out4, dtex, duv4, ddir4, dnrm4)
     assert api.rt_get_error(ctx) == api.RT_OK
+    o, out, nrm = o3.view(-1), out4.view(-1, 4), nrm4.view(-1, 3)
+    duv, ddir, dnrm = duv4.view(-1, 2), ddir4.view(-1, 3), dnrm4.view(-1, 3)
     for k in (0, 1):
         lhs = dtex[k].double().sum(dim=(0, 1, 2, 3))
         rhs = (out.double() * (o == k).unsqueeze(-1)).sum(dim=0)
