@@ -60,6 +60,14 @@ MUTATIONS = [
     ("deferred_sky_occluded", "out[3] = 1.0;\n        if (lo)", "out[3] = 0.0;\n        if (lo)", [DEFERRED]),
     ("deferred_from_origin_side", "for (int k = 0; k < 3; ++k) X[k] = P[k] + t_best * d[k];",
      "for (int k = 0; k < 3; ++k) X[k] = P[k] + 0.5 * t_best * d[k];", [DEFERRED]),
+    ("nearest_angular_half_off", "double c = (Bc + 1.0) * (double)n / 2.0;",
+     "double c = (Bc + 1.0) * (double)n / 2.0 - 0.5;", [PINS]),
+    ("bf16_mantissa_bits", "static const fmt_t FMT_BF16 = {7, -126, 127, 8,",
+     "static const fmt_t FMT_BF16 = {8, -126, 127, 8,", [PINS]),
+    ("eq1a_without_sqrt2", "for (int k = 0; k < 3; ++k) A3[k] = SQRT2 * h[k] / L;",
+     "for (int k = 0; k < 3; ++k) A3[k] = h[k] / L;", [PINS, WORLD]),
+    ("kmeans_mean_off_by_one", "C[k * D + d] = sum[k * D + d] / (double)counts[k];",
+     "C[k * D + d] = sum[k * D + d] / (double)(counts[k] + 1);", [PALETTE]),
     ("pattern_x_y_swapped", "const int64_t q = (p[c] * X + p[4 + c] * Y + p[8 + c]) % (2 * m);",
      "const int64_t q = (p[c] * Y + p[4 + c] * X + p[8 + c]) % (2 * m);", [PATTERN]),
     ("taps_s_t_swapped", "int64_t X = L.u.tap[a] * T.n + L.s.tap[p], Y = L.v.tap[b] * T.n + L.t.tap[q];",
