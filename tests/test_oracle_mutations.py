@@ -68,6 +68,11 @@ MUTATIONS = [
      "for (int k = 0; k < 3; ++k) A3[k] = h[k] / L;", [PINS, WORLD]),
     ("kmeans_mean_off_by_one", "C[k * D + d] = sum[k * D + d] / (double)counts[k];",
      "C[k * D + d] = sum[k * D + d] / (double)(counts[k] + 1);", [PALETTE]),
+    ("rounding_half_up", "double q = rint(a / quantum) * quantum;", "double q = floor(a / quantum + 0.5) * quantum;",
+     [PINS]),
+    ("subnormal_quantum_lost", "if (ex < f->emin) ex = f->emin; /* subnormal quantum */",
+     "if (ex < f->emin - 1) ex = f->emin - 1; /* subnormal quantum */", [PINS]),
+    ("clamp_passes_gradient", "double inside = (B > lo && B < hi) ? 1.0 : 0.0;", "double inside = 1.0;", [PINS]),
     ("pattern_x_y_swapped", "const int64_t q = (p[c] * X + p[4 + c] * Y + p[8 + c]) % (2 * m);",
      "const int64_t q = (p[c] * Y + p[4 + c] * X + p[8 + c]) % (2 * m);", [PATTERN]),
     ("taps_s_t_swapped", "int64_t X = L.u.tap[a] * T.n + L.s.tap[p], Y = L.v.tap[b] * T.n + L.t.tap[q];",

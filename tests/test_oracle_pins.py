@@ -385,6 +385,50 @@ def test_gradient_uv_dir_vs_fd(orc, filt):
         np.testing.assert_allclose(gdir[ok, k], fd[ok], rtol=1e-6, atol=1e-6 * n)
 
 
+@pytest.mark.parametrize("filt", [1, 2])
+def test_gradient_zero_through_the_clamp(orc, filt):
+    """Inside the Note's clamp zone (|B| beyond the outer texel centre 1 - 1/n)
+    the colour does not change with the clamped component of B, so dL/ddir
+    equals central differences there too: the clamped axis contributes nothing,
+    the other axis its usual derivative (reading R6).  At the low clamp the
+    floor branch of the in-bucket coordinate would otherwise pass the texel
+    difference through."""
+    rng = np.random.default_rng(40 + filt)
+    W, H, n = 5, 4, 8
+    T = orc.Texture(W, H, n, orc.F64, rng.uniform(0, 1, (H * n, W * n, 4)))
+    F = 200
+    far = rng.uniform(0.9, 0.99, F) * rng.choice([-1.0, 1.0], F)  # beyond 1 - 1/n = 0.875
+    free = rng.uniform(-0.8, 0.8, F)
+    # keep the free component's in-bucket coordinate away from integers
+    c = (free + 1) * n / 2 - 0.5
+    free = np.where(np.abs(c - np.round(c)) < 0.05, free + 0.2 / n, free)
+    axis = rng.integers(0, 2, F)
+    B = np.where(axis[:, None] == 0, np.stack([far, free], 1), np.stack([free, far], 1))
+    d = orc.equisolid_inverse(orc.unsquarify(B))
+    assert np.all(d[:, 2] > 0.0)
+    uv = rng.uniform(0.05, 0.95, (F, 2))
+    cu, cv = uv[:, 0] * W - 0.5, uv[:, 1] * H - 0.5
+    uv[:, 0] += np.where(np.abs(cu - np.round(cu)) < 0.05, 0.1 / W, 0.0)
+    uv[:, 1] += np.where(np.abs(cv - np.round(cv)) < 0.05, 0.1 / H, 0.0)
+    g = rng.normal(size=(F, 4))
+    obj = np.zeros(F, np.int32)
+    _, _, gdir, flags = orc.shade_backward([T], uv, d, obj, filt, g, want_tex=False, precise_inputs=True)
+    assert flags == 0
+
+    def L(d_):
+        out, _ = orc.shade([T], uv, d_, obj, filt, precise_inputs=True)
+        return np.sum(out * g, 1)
+
+    eps = 1e-7
+    for k in range(3):
+        e = np.zeros_like(d)
+        e[:, k] = eps
+        fd = (L(d + e) - L(d - e)) / (2 * eps)
+        np.testing.assert_allclose(gdir[:, k], fd, rtol=1e-6, atol=1e-6 * n)
+    # not vacuous: the free axis still carries a gradient
+    assert np.abs(gdir).max() > 1e-3
+
+
 def test_gradient_nearest_is_zero(orc):
     rng = np.random.default_rng(30)
     W, H, n = 3, 3, 4
