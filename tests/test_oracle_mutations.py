@@ -73,6 +73,10 @@ MUTATIONS = [
     ("subnormal_quantum_lost", "if (ex < f->emin) ex = f->emin; /* subnormal quantum */",
      "if (ex < f->emin - 1) ex = f->emin - 1; /* subnormal quantum */", [PINS]),
     ("clamp_passes_gradient", "double inside = (B > lo && B < hi) ? 1.0 : 0.0;", "double inside = 1.0;", [PINS]),
+    ("sky_gradient_inverted", "double h = 0.5 + 0.5 * d[1];", "double h = 0.5 - 0.5 * d[1];", [BAKE]),
+    ("lit_ambient_unscaled", "return S[BK_AMBIENT] + (1.0 - S[BK_AMBIENT]) * (c > 0.0 ? c : 0.0);",
+     "return S[BK_AMBIENT] + (c > 0.0 ? c : 0.0);", [BAKE]),
+    ("plane_pattern_axis", "cos(w * x[0]) * cos(w * x[2])", "cos(w * x[0]) * cos(w * x[1])", [BAKE, DEFERRED]),
     ("pattern_x_y_swapped", "const int64_t q = (p[c] * X + p[4 + c] * Y + p[8 + c]) % (2 * m);",
      "const int64_t q = (p[c] * Y + p[4 + c] * X + p[8 + c]) % (2 * m);", [PATTERN]),
     ("taps_s_t_swapped", "int64_t X = L.u.tap[a] * T.n + L.s.tap[p], Y = L.v.tap[b] * T.n + L.t.tap[q];",
