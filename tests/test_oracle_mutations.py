@@ -77,6 +77,12 @@ MUTATIONS = [
     ("lit_ambient_unscaled", "return S[BK_AMBIENT] + (1.0 - S[BK_AMBIENT]) * (c > 0.0 ? c : 0.0);",
      "return S[BK_AMBIENT] + (c > 0.0 ? c : 0.0);", [BAKE]),
     ("plane_pattern_axis", "cos(w * x[0]) * cos(w * x[2])", "cos(w * x[0]) * cos(w * x[1])", [BAKE, DEFERRED]),
+    ("eq1b_jacobian_sign", "J[r][c] = SQRT2 * ((r == c ? 1.0 / D : 0.0) - I[r] * g[c] / D3);",
+     "J[r][c] = SQRT2 * ((r == c ? 1.0 / D : 0.0) + I[r] * g[c] / D3);", [PINS]),
+    ("spatial_derivative_scale", "a->dc = (c > -1.0 && c < (double)size) ? (double)size : 0.0;",
+     "a->dc = (c > -1.0 && c < (double)size) ? (double)(size - 1) : 0.0;", [PINS]),
+    ("eq1a_jacobian_power", "J[r][c] = SQRT2 * ((r == c ? 1.0 / L : 0.0) - h[r] * h[c] / L3);",
+     "J[r][c] = SQRT2 * ((r == c ? 1.0 / L : 0.0) - h[r] * h[c] / (L * L));", [WORLD]),
     ("pattern_x_y_swapped", "const int64_t q = (p[c] * X + p[4 + c] * Y + p[8 + c]) % (2 * m);",
      "const int64_t q = (p[c] * Y + p[4 + c] * X + p[8 + c]) % (2 * m);", [PATTERN]),
     ("taps_s_t_swapped", "int64_t X = L.u.tap[a] * T.n + L.s.tap[p], Y = L.v.tap[b] * T.n + L.t.tap[q];",
