@@ -440,3 +440,36 @@ def test_footprint_counts(ctx, filt):
                     keys.update(map(tuple, t))
     assert abs(counts[oid] - len(keys)) <= 16 * int(band.sum())
     api.rt_destroy_texture(ctx, oid)
+
+
+@pytest.mark.parametrize("filt", [api.RT_ANGULAR_BILINEAR, api.RT_QUADRILINEAR])
+def test_direction_gradient_at_eq3_ties(ctx, filt):
+    """Directions with |I_x| = |I_y| exactly (so |A_x| = |A_y| in FP32 and FP64
+    alike) sit on Eq. 3's kink; the kernel takes the x branch as the oracle does
+    (reading R6)."""
+    W, H, n = 6, 5, 8
+    rng = np.random.default_rng(77)
+    atlas = rng.uniform(0, 1, (H * n, W * n, 4)).astype(np.float32)
+    oid = api.rt_create_texture(ctx, W, H, n, api.RT_F32, api.RT_LAYOUT_ATLAS, to_dev(atlas))
+    F = 512
+    a = rng.uniform(0.15, 0.6, F).astype(np.float32)
+    sx, sy = rng.choice([-1.0, 1.0], F).astype(np.float32), rng.choice([-1.0, 1.0], F).astype(np.float32)
+    d = np.stack([sx * a, sy * a, np.sqrt(1 - 2 * a * a)], 1).astype(np.float32)
+    assert np.all(np.abs(d[:, 0]) == np.abs(d[:, 1]))
+    uv = rng.uniform(0.1, 0.9, (F, 2)).astype(np.float32)
+    obj = np.full(F, oid, np.int32)
+    g = rng.normal(size=(F, 4)).astype(np.float32)
+    ddir = torch.empty((F, 3), device="cuda")
+    api.rt_shade_backward(ctx, to_dev(uv), to_dev(d), to_dev(obj), filt, to_dev(g), None, None, ddir)
+    assert api.rt_get_error(ctx) == api.RT_OK
+    T = oracle.Texture.from_f32(atlas, W, H, n, oracle.F32)
+    table = [None] * oid + [T]
+    _, _, gdir, flags = oracle.shade_backward(table, uv, d, obj, filt, g.astype(np.float64), want_tex=False)
+    assert flags == 0
+    _, oc, _ = oracle.locate(table, uv, d, obj, filt)
+    far = (np.abs(oc - np.round(oc)) > 1e-3).all(axis=1)
+    assert far.sum() > F // 2
+    got = ddir.cpu().numpy()
+    scale = np.abs(gdir[far]).max()
+    assert np.all(np.abs(got[far] - gdir[far]) <= 1e-3 * np.abs(gdir[far]) + 1e-5 * scale)
+    api.rt_destroy_texture(ctx, oid)

@@ -429,6 +429,57 @@ def test_gradient_zero_through_the_clamp(orc, filt):
     assert np.abs(gdir).max() > 1e-3
 
 
+@pytest.mark.parametrize("filt", [1, 2])
+def test_gradient_at_eq3_ties_takes_the_x_branch(orc, filt):
+    """At |A_x| = |A_y| Eq. 3 has a kink; reading R6 takes the x branch
+    (B = A |A| / |A_x|).  The oracle's dL/ddir at exact ties equals central
+    differences taken just inside the x-dominant side, and differs from the
+    y-dominant side's."""
+    rng = np.random.default_rng(50 + filt)
+    W, H, n = 4, 4, 8
+    T = orc.Texture(W, H, n, orc.F64, rng.uniform(0, 1, (H * n, W * n, 4)))
+    F = 60
+    a = rng.uniform(0.15, 0.6, F)
+    sx, sy = rng.choice([-1.0, 1.0], F), rng.choice([-1.0, 1.0], F)
+    d = np.stack([sx * a, sy * a, np.sqrt(1 - 2 * a * a)], 1)
+    assert np.all(np.abs(d[:, 0]) == np.abs(d[:, 1]))
+    uv = rng.uniform(0.1, 0.9, (F, 2))
+    g = rng.normal(size=(F, 4))
+    obj = np.zeros(F, np.int32)
+    # keep every in-bucket coordinate away from integers and the clamp
+    B = orc.squarify(orc.equisolid(d))
+    c = (B + 1) * n / 2 - 0.5
+    keep = (np.abs(c - np.round(c)) > 0.02).all(1) & (np.abs(B) < 1 - 1.0 / n - 0.02).all(1)
+    d, uv, g, obj = d[keep], uv[keep], g[keep], obj[keep]
+    assert len(obj) > 20
+    _, _, gdir, flags = orc.shade_backward([T], uv, d, obj, filt, g, want_tex=False, precise_inputs=True)
+    assert flags == 0
+
+    def L(d_):
+        out, _ = orc.shade([T], uv, d_, obj, filt, precise_inputs=True)
+        return np.sum(out * g, 1)
+
+    delta, eps = 1e-6, 1e-9
+
+    def fd_at(shift):
+        base = d + shift
+        out = np.empty_like(d)
+        for k in range(3):
+            e = np.zeros_like(d)
+            e[:, k] = eps
+            out[:, k] = (L(base + e) - L(base - e)) / (2 * eps)
+        return out
+
+    x_side = np.zeros_like(d)
+    x_side[:, 0] = delta * np.sign(d[:, 0])  # |I_x| > |I_y|: |A_x| > |A_y|
+    y_side = np.zeros_like(d)
+    y_side[:, 1] = delta * np.sign(d[:, 1])
+    fx, fy = fd_at(x_side), fd_at(y_side)
+    scale = np.abs(fx).max()
+    np.testing.assert_allclose(gdir, fx, rtol=0, atol=1e-4 * scale)
+    assert np.abs(gdir - fy).max() > 1e-2 * scale
+
+
 def test_gradient_nearest_is_zero(orc):
     rng = np.random.default_rng(30)
     W, H, n = 3, 3, 4
