@@ -85,6 +85,8 @@ MUTATIONS = [
      "J[r][c] = SQRT2 * ((r == c ? 1.0 / L : 0.0) - h[r] * h[c] / (L * L));", [WORLD]),
     ("eq3_tie_takes_y_branch", "if (ax >= ay) { /* B = A r / |A_x| */", "if (ax > ay) { /* B = A r / |A_x| */",
      [PINS]),
+    ("bit_texel_inverted", "return (double)(((const uint8_t*)T->codes)[e] & 1u);",
+     "return (double)((((const uint8_t*)T->codes)[e] & 1u) ^ 1u);", [SHADOW]),
     ("pattern_x_y_swapped", "const int64_t q = (p[c] * X + p[4 + c] * Y + p[8 + c]) % (2 * m);",
      "const int64_t q = (p[c] * Y + p[4 + c] * X + p[8 + c]) % (2 * m);", [PATTERN]),
     ("taps_s_t_swapped", "int64_t X = L.u.tap[a] * T.n + L.s.tap[p], Y = L.v.tap[b] * T.n + L.t.tap[q];",
