@@ -87,6 +87,8 @@ MUTATIONS = [
      [PINS]),
     ("bit_texel_inverted", "return (double)(((const uint8_t*)T->codes)[e] & 1u);",
      "return (double)((((const uint8_t*)T->codes)[e] & 1u) ^ 1u);", [SHADOW]),
+    ("repeat_v_reads_u_flag", "spatial_axis(v, T->H, spatial_bilinear, (T->wrap >> 1) & 1, &L->v);",
+     "spatial_axis(v, T->H, spatial_bilinear, T->wrap & 1, &L->v);", [WORLD]),
     ("pattern_x_y_swapped", "const int64_t q = (p[c] * X + p[4 + c] * Y + p[8 + c]) % (2 * m);",
      "const int64_t q = (p[c] * Y + p[4 + c] * X + p[8 + c]) % (2 * m);", [PATTERN]),
     ("taps_s_t_swapped", "int64_t X = L.u.tap[a] * T.n + L.s.tap[p], Y = L.v.tap[b] * T.n + L.t.tap[q];",

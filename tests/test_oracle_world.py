@@ -186,3 +186,35 @@ def test_wrap_gradient_across_the_seam(orc):
         fd = ((lp - lm) * g).sum(1) / (2 * eps)
         np.testing.assert_allclose(guv[far, k], fd[far], rtol=1e-5, atol=1e-6)
     assert (np.abs(guv[:, 0]) > 0).any()
+
+
+@pytest.mark.parametrize("wrap", [1, 2])
+def test_wrap_one_axis_only(orc, wrap):
+    """Each repeat flag acts on its own axis (reading R12): with u repeating
+    and v clamped (wrap = 1) a shift of u by a whole period leaves the colour
+    unchanged while v beyond the edge reads the edge row; wrap = 2 the other
+    way round."""
+    W, H, n = 5, 3, 4
+    T, _ = textures(orc, W, H, n, 60 + wrap, wrap=wrap)
+    rng = np.random.default_rng(61)
+    F = 300
+    uv = rng.uniform(0.05, 0.95, (F, 2))
+    d = unit_dirs(rng, F)
+    obj = np.zeros(F, np.int32)
+    rep, clamp = (0, 1) if wrap == 1 else (1, 0)
+    base, _ = orc.shade([T], uv, d, obj, 2, precise_inputs=True)
+    shifted = uv.copy()
+    shifted[:, rep] += 3.0
+    got, _ = orc.shade([T], shifted, d, obj, 2, precise_inputs=True)
+    np.testing.assert_allclose(got, base, rtol=0, atol=1e-12)
+    # the clamped axis: every coordinate beyond the far edge reads the edge
+    far1, far2 = uv.copy(), uv.copy()
+    far1[:, clamp] = 1.5
+    far2[:, clamp] = 7.0
+    a, _ = orc.shade([T], far1, d, obj, 2, precise_inputs=True)
+    b, _ = orc.shade([T], far2, d, obj, 2, precise_inputs=True)
+    np.testing.assert_array_equal(a, b)
+    near = uv.copy()
+    near[:, clamp] = uv[:, clamp] + 3.0 / [W, H][clamp]
+    c, _ = orc.shade([T], near, d, obj, 2, precise_inputs=True)
+    assert np.abs(c - base).max() > 1e-3  # not periodic along the clamped axis
