@@ -89,6 +89,8 @@ MUTATIONS = [
      "return (double)((((const uint8_t*)T->codes)[e] & 1u) ^ 1u);", [SHADOW]),
     ("repeat_v_reads_u_flag", "spatial_axis(v, T->H, spatial_bilinear, (T->wrap >> 1) & 1, &L->v);",
      "spatial_axis(v, T->H, spatial_bilinear, T->wrap & 1, &L->v);", [WORLD]),
+    ("bucket_lobe_exponent", "double lobe = cosang > 0.0 ? pow(cosang, (double)P[6]) : 0.0;",
+     "double lobe = cosang > 0.0 ? pow(cosang, (double)P[6] + 1.0) : 0.0;", [PINS]),
     ("pattern_x_y_swapped", "const int64_t q = (p[c] * X + p[4 + c] * Y + p[8 + c]) % (2 * m);",
      "const int64_t q = (p[c] * Y + p[4 + c] * X + p[8 + c]) % (2 * m);", [PATTERN]),
     ("taps_s_t_swapped", "int64_t X = L.u.tap[a] * T.n + L.s.tap[p], Y = L.v.tap[b] * T.n + L.t.tap[q];",

@@ -665,3 +665,26 @@ def test_note_clamp_keeps_lookups_inside_the_texel_centres(orc):
         assert (c[:, 2:] >= lo).all() and (c[:, 2:] <= hi).all()
         edge = np.abs(c[:200, 2:] - np.where(c[:200, 2:] > n / 2, hi, lo)).min(axis=1)
         assert (edge == 0).all()
+
+
+def test_bucket_lobe_fill_against_numpy(orc):
+    """The per-bucket lobe fill of the large workloads (reading A11's form for
+    them: rho max(0, I . d)^p, alpha the lobe itself) against an independent
+    numpy evaluation at the texel-centre directions, atlas row j n + t, column
+    i n + s (R4); the directions themselves are pinned by the texel-centre pins."""
+    import synth
+
+    W, H, n = 5, 3, 4
+    params = synth.bucket_lobe_params(91, W, H)
+    got = orc.fill_bucket_lobes(W, H, n, params)
+    dirs = orc.texel_directions(n)  # [t, s, 3]
+    want = np.zeros((H * n, W * n, 4))
+    for j in range(H):
+        for i in range(W):
+            P = params[j, i].astype(np.float64)
+            cosang = dirs @ P[3:6]
+            lobe = np.where(cosang > 0, np.maximum(cosang, 0.0) ** P[6], 0.0)
+            for c in range(3):
+                want[j * n:(j + 1) * n, i * n:(i + 1) * n, c] = P[c] * lobe
+            want[j * n:(j + 1) * n, i * n:(i + 1) * n, 3] = lobe
+    np.testing.assert_allclose(got, want.astype(np.float32), rtol=2e-7, atol=1e-30)
