@@ -9,6 +9,11 @@
 // cudaFree would synchronise the device and stall the frame.  This entry point
 // keeps its scratch in file-scope device arrays instead: every GPU that loads
 // the library holds them (8 MiB + 8 KiB) until the process exits.
+//
+// Nothing of a call is read from host memory on the GPU side: the per-object
+// word offsets are computed on the device from the context's device-side
+// descriptor table, and one popcount launch reads them from there.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -25,14 +30,47 @@ namespace {
 constexpr int64_t kMaxTexels = RT_FOOTPRINT_NOALLOC_MAX_TEXELS;
 constexpr int64_t kMaxWords = kMaxTexels / 32;
 static __device__ __align__(256) uint32_t g_bitmap[kMaxWords];
-// First bitmap word of each object.
+// First bitmap word of each object, and the total after the last one.
 static __device__ __align__(256) int64_t g_word_offset[RT_MAX_OBJECTS + 1];
 
-// Device addresses of the two arrays, looked up once per device.  In host code
-// the arrays' names stand for host-side shadows, not device addresses, so they
-// are never passed to a kernel directly.
+// Word offsets of the objects 0 .. n_obj - 1 from the device table (a dead
+// slot takes no words), and zeros in the caller's counts.  One block; the
+// running sum is taken by thread 0 (at most RT_MAX_OBJECTS entries).
+__global__ void noalloc_offsets_kernel(const rt::TexDesc* __restrict__ table, int n_obj, int64_t* word_offset,
+                                       unsigned long long* counts, int n_counts) {
+    for (int o = threadIdx.x; o < n_counts; o += blockDim.x) counts[o] = 0ull;
+    if (threadIdx.x != 0) return;
+    int64_t acc = 0;
+    word_offset[0] = 0;
+    for (int o = 0; o < n_obj; ++o) {
+        const rt::TexDesc& d = table[o];
+        const int64_t texels = d.live ? d.plane * d.n * d.n : 0;
+        acc += (texels + 31) / 32;
+        word_offset[o + 1] = acc;
+    }
+}
+
+// Set bits of object blockIdx.y's words, added to counts[blockIdx.y].
+__global__ void noalloc_popcount_kernel(const uint32_t* __restrict__ bitmap,
+                                        const int64_t* __restrict__ word_offset, unsigned long long* counts) {
+    const int o = blockIdx.y;
+    const int64_t lo = word_offset[o], hi = word_offset[o + 1];
+    unsigned long long local = 0;
+    for (int64_t w = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < hi; w += (int64_t)gridDim.x * blockDim.x)
+        local += __popc(bitmap[w]);
+    for (int k = 16; k > 0; k >>= 1) local += __shfl_down_sync(0xFFFFFFFFu, local, k);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(counts + o, local);
+}
+
+// Device addresses of the two arrays.  In host code the arrays' names stand
+// for host-side shadows, not device addresses, so they are never passed to a
+// kernel directly.  The addresses are looked up once per device and context:
+// a device reset (cudaDeviceReset, or a framework tearing its context down)
+// makes a new primary context, whose module -- and arrays -- may sit
+// elsewhere, so the cache is keyed on the current context's unique id.
 struct StaticScratch {
     bool ready = false;
+    unsigned long long ctx_id = 0;
     uint32_t* bitmap = nullptr;
     int64_t* word_offset = nullptr;
 };
@@ -40,12 +78,39 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 StaticScratch g_scratch[kMaxDevices];
 
-// Called with `device` current.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// The current context's unique id, or false when the driver cannot tell.
+bool current_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(p);
+    });
+    CUcontext c = nullptr;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c) return false;
+    return get_id(c, id) == CUDA_SUCCESS;
+}
+
+// Called with `device` current (the runtime has made its primary context
+// current by then).
 cudaError_t scratch_for(int device, StaticScratch* out) {
     if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    unsigned long long id = 0;
+    const bool keyed = current_context_id(&id);
     std::lock_guard<std::mutex> lock(g_mu);
     StaticScratch& s = g_scratch[device];
-    if (!s.ready) {
+    if (!s.ready || !keyed || s.ctx_id != id) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_bitmap);
         if (e != cudaSuccess) return e;
@@ -53,7 +118,8 @@ cudaError_t scratch_for(int device, StaticScratch* out) {
         e = cudaGetSymbolAddress(&p, g_word_offset);
         if (e != cudaSuccess) return e;
         s.word_offset = static_cast<int64_t*>(p);
-        s.ready = true;
+        s.ctx_id = id;
+        s.ready = keyed;  // without a context id the addresses are looked up on every call
     }
     *out = s;
     return cudaSuccess;
@@ -66,22 +132,20 @@ extern "C" rt_status rt_footprint_noalloc(rt_ctx* ctx, const float* uv, const fl
                                           rt_stream_t stream) {
     if (!ctx || (filter != RT_NEAREST && filter != RT_ANGULAR_BILINEAR && filter != RT_QUADRILINEAR))
         return RT_ERR_INVALID_ARG;
-    if (n_counts < 0 || n_counts > RT_MAX_OBJECTS || (n_counts > 0 && !counts_dev)) return RT_ERR_INVALID_ARG;
+    // the G-buffer rules of every shading call (rt_footprint's included)
     if (F < 0 || (F > 0 && (!uv || !dir || !obj))) return RT_ERR_INVALID_ARG;
-    if (((uintptr_t)uv | (uintptr_t)dir | (uintptr_t)obj) & 15u) return RT_ERR_INVALID_ARG;
-    if (((uintptr_t)counts_dev) & 7u) return RT_ERR_INVALID_ARG;
+    if (F > 0 && (((uintptr_t)uv | (uintptr_t)dir | (uintptr_t)obj) & 15u)) return RT_ERR_INVALID_ARG;
+    if (n_counts < 0 || (n_counts > 0 && !counts_dev) || (((uintptr_t)counts_dev) & 7u)) return RT_ERR_INVALID_ARG;
 
     // Bitmap words of every object: the sum must fit the static bitmap.
     int n_obj = 0;
-    int64_t offset[RT_MAX_OBJECTS + 1];
-    offset[0] = 0;
     const rt::TexDesc* table = rt_internal_host_table(ctx, &n_obj);
+    int64_t words = 0;
     for (int o = 0; o < n_obj; ++o) {
         const rt::TexDesc& d = table[o];
         const int64_t texels = d.live ? d.plane * d.n * d.n : 0;
-        offset[o + 1] = offset[o] + (texels + 31) / 32;
+        words += (texels + 31) / 32;
     }
-    const int64_t words = offset[n_obj];
     if (words > kMaxWords) return RT_ERR_INVALID_ARG;  // more than RT_FOOTPRINT_NOALLOC_MAX_TEXELS texels
 
     int prev = -1, device = rt_internal_device(ctx);
@@ -90,18 +154,26 @@ extern "C" rt_status rt_footprint_noalloc(rt_ctx* ctx, const float* uv, const fl
     cudaStream_t s = (cudaStream_t)stream;
     StaticScratch sc;
     cudaError_t e = scratch_for(device, &sc);
-    // The arrays keep the previous call's contents: clear the outputs and the used words.
-    if (e == cudaSuccess && n_counts > 0) e = cudaMemsetAsync(counts_dev, 0, sizeof(uint64_t) * n_counts, s);
+    // The arrays keep the previous call's contents: the offsets are rewritten,
+    // the counts zeroed (entries past the last object stay zero) and the used
+    // bitmap words cleared before the marking pass.
+    unsigned long long* counts = reinterpret_cast<unsigned long long*>(counts_dev);
+    if (e == cudaSuccess) {
+        noalloc_offsets_kernel<<<1, 256, 0, s>>>(rt_internal_device_table(ctx), n_obj, sc.word_offset, counts,
+                                                 n_counts);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess && words > 0) e = cudaMemsetAsync(sc.bitmap, 0, sizeof(uint32_t) * (size_t)words, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(sc.word_offset, offset, sizeof(int64_t) * (size_t)(n_obj + 1), cudaMemcpyHostToDevice,
-                            s);
     if (e == cudaSuccess && F > 0)
         e = rt::launch_footprint_mark(rt_internal_device_table(ctx), n_obj, uv, dir, obj, F, filter, sc.bitmap,
                                       sc.word_offset, rt_internal_status(ctx), s);
-    for (int o = 0; o < n_counts && o < n_obj && e == cudaSuccess; ++o)
-        e = rt::launch_popcount(sc.bitmap + offset[o], offset[o + 1] - offset[o],
-                                reinterpret_cast<unsigned long long*>(counts_dev) + o, s);
+    const int n_pop = n_counts < n_obj ? n_counts : n_obj;
+    if (e == cudaSuccess && n_pop > 0 && words > 0) {
+        int64_t per = (words + 255) / 256;  // blocks to cover every word once, spread over the objects
+        const unsigned gx = (unsigned)(per < 1024 ? per : 1024);
+        noalloc_popcount_kernel<<<dim3(gx, (unsigned)n_pop), 256, 0, s>>>(sc.bitmap, sc.word_offset, counts);
+        e = cudaGetLastError();
+    }
     if (prev >= 0 && prev != device) cudaSetDevice(prev);
     if (e == cudaSuccess) return RT_OK;
     return e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA;
