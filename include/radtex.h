@@ -312,6 +312,15 @@ rt_status rt_shade_backward(rt_ctx* ctx, const float* uv, const float* dir, cons
                             rt_filter filter, const float* dL_dout, float* const* dL_dtex, int32_t n_dtex,
                             float* dL_duv, float* dL_ddir, int32_t flags, rt_stream_t stream);
 
+/* Zeroes texel-gradient buffers on `stream` (asynchronous, no allocation): for
+ * every non-NULL entry o < n_dtex of dL_dtex (host array of device pointers
+ * indexed by object id, as in rt_shade_backward), the object's full extent,
+ * (w h or K) x n^2 texels of 4 FP32 values.  The clear that a step which
+ * accumulates gradients (RT_ACCUMULATE) runs first; rt_shade_backward without
+ * RT_ACCUMULATE does the same itself.  RT_ERR_INVALID_ARG for a dead object, a
+ * buffer that is not 16-byte aligned or n_dtex outside [0, RT_MAX_OBJECTS]. */
+rt_status rt_zero_texture_grads(rt_ctx* ctx, float* const* dL_dtex, int32_t n_dtex, rt_stream_t stream);
+
 /* Prepares the deterministic backward mode (RT_DETERMINISTIC): allocates, for
  * every live object that has none yet, a buffer of 32 bytes per texel in which
  * rt_shade_backward sums texel gradients as signed 64-bit fixed-point numbers
@@ -473,13 +482,16 @@ rt_status rt_footprint(rt_ctx* ctx, const float* uv, const float* dir, const int
  * every GPU loading the library keeps until the process exits; the contexts'
  * objects may hold at most RT_FOOTPRINT_NOALLOC_MAX_TEXELS texels in total
  * (RT_ERR_INVALID_ARG otherwise).  counts_dev (device, n_counts uint64 entries,
- * 8-byte aligned, indexed by object id) receives the distinct-texel counts,
- * asynchronously on `stream`; nothing is read back to the host.  The first
- * call on a device looks the arrays' device addresses up (a host-side set-up
- * done once per device): make that first call before any stream capture.  All
- * calls share the arrays, and each clears what it uses first, so calls whose
- * work overlaps on the GPU (other streams, other threads) race and must be
- * ordered by the caller. */
+ * 8-byte aligned, indexed by object id; any n_counts >= 0, entries past the
+ * last object are set to zero) receives the distinct-texel counts,
+ * asynchronously on `stream`; nothing is read back to the host, and the
+ * per-object offsets are computed on the device from the context's own
+ * descriptor table (no host-to-device copy).  The G-buffer rules are
+ * rt_footprint's.  The first call on a device (and again after the device's
+ * context is reset) looks the arrays' device addresses up, a host-side set-up:
+ * make that first call before any stream capture.  All calls share the arrays,
+ * and each clears what it uses first, so calls whose work overlaps on the GPU
+ * (other streams, other threads) race and must be ordered by the caller. */
 rt_status rt_footprint_noalloc(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,
                                rt_filter filter, uint64_t* counts_dev, int32_t n_counts, rt_stream_t stream);
 

@@ -94,6 +94,7 @@ SIGNATURES = {
                                     _I32, _I32, _P, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)]),
     "rt_footprint": (_I32, [_P, _P, _P, _P, _I64, _I32, ctypes.POINTER(ctypes.c_uint64), _I32, _P]),
     "rt_footprint_noalloc": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, _I32, _P]),
+    "rt_zero_texture_grads": (_I32, [_P, _P, _I32, _P]),
     "rt_l2_loss_grad": (_I32, [_P, _P, _P, _I64, ctypes.c_float, _P, _P, _P]),
     "rt_adam_step": (_I32, [_P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                             _I32, _P]),

@@ -365,6 +365,24 @@ def rt_shade_batched_backward(ctx: Context, uv, dirs, obj, filter: int, dL_dout,
               _ptr(dL_dout), arr, n_dtex, _ptr(dL_duv), _ptr(dL_ddir), int(flags), _stream(stream, uv.device))
 
 
+def rt_zero_texture_grads(ctx: Context, dL_dtex: dict, stream=None) -> None:
+    """Zeroes each object's texel-gradient buffer ({object id: FP32 tensor}) on the stream."""
+    if not dL_dtex:
+        return
+    n_dtex = max(dL_dtex) + 1
+    arr = (ctypes.c_void_p * n_dtex)()
+    dev = None
+    for o, t in dL_dtex.items():
+        _check(t, f"dL_dtex[{o}]", torch.float32)
+        info = rt_texture_info(ctx, o)
+        buckets = rt_palette_size(ctx, o) or info["w"] * info["h"]
+        if t.numel() != buckets * info["n"] ** 2 * 4:
+            raise ValueError(f"dL_dtex[{o}] must hold (w h or K) n^2 x 4 floats")
+        arr[o] = t.data_ptr()
+        dev = t.device
+    _lib.call("rt_zero_texture_grads", ctx.handle, arr, n_dtex, _stream(stream, dev))
+
+
 def rt_shade_batched_l2_step(ctx: Context, uv, dirs, obj, filter: int, target, scale: float = 1.0, out=None,
                              sums=None, dL_dtex=None, dL_duv=None, dL_ddir=None, flags: int = 0, stream=None):
     """Fused forward + L2 loss + backward over (V, H, W) frames: writes `out` (if given),

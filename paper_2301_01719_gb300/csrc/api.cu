@@ -825,6 +825,21 @@ rt_status rt_shade_world_batched_backward(rt_ctx* ctx, const float* uv, const fl
                                stream, nrm ? nrm : kNone, dL_dnrm);
 }
 
+rt_status rt_zero_texture_grads(rt_ctx* ctx, float* const* dL_dtex, int32_t n_dtex, rt_stream_t stream) {
+    if (!ctx || n_dtex < 0 || n_dtex > RT_MAX_OBJECTS || (n_dtex > 0 && !dL_dtex)) return RT_ERR_INVALID_ARG;
+    for (int o = 0; o < n_dtex; ++o)
+        if (dL_dtex[o] && (!ctx->table[o].live || !aligned16(dL_dtex[o]))) return RT_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
+    for (int o = 0; o < n_dtex && e == cudaSuccess; ++o) {
+        if (!dL_dtex[o]) continue;
+        const TexDesc& d = ctx->table[o];
+        e = cudaMemsetAsync(dL_dtex[o], 0, (size_t)16 * d.plane * d.n * d.n, (cudaStream_t)stream);
+    }
+    return cuda_status(e);
+}
+
 rt_status rt_prepare_deterministic(rt_ctx* ctx) {
     if (!ctx) return RT_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);

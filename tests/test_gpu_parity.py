@@ -473,3 +473,36 @@ def test_direction_gradient_at_eq3_ties(ctx, filt):
     scale = np.abs(gdir[far]).max()
     assert np.all(np.abs(got[far] - gdir[far]) <= 1e-3 * np.abs(gdir[far]) + 1e-5 * scale)
     api.rt_destroy_texture(ctx, oid)
+
+
+def test_zero_texture_grads(ctx):
+    """rt_zero_texture_grads clears exactly each listed object's gradient extent on
+    the stream, leaves unlisted buffers alone, and rejects dead objects; with it,
+    clear + RT_ACCUMULATE equals the backward's own clear (no RT_ACCUMULATE)."""
+    W, H, n = 24, 16, 4
+    atlas, g, T = quad_workload(api.RT_F16, W, H, n, width=64, height=64)
+    a, _ = _new_texture(ctx, atlas, W, H, n, api.RT_F16)
+    b, _ = _new_texture(ctx, atlas, W, H, n, api.RT_F32)
+    size = n * n * H * W * 4
+    ga = torch.full((size + 4,), 7.0, device="cuda")  # 4 guard floats past the extent
+    gb = torch.full((size,), 3.0, device="cuda")
+    api.rt_zero_texture_grads(ctx, {a: ga[:size]})
+    torch.cuda.synchronize()
+    assert float(ga[:size].abs().max()) == 0.0 and bool((ga[size:] == 7.0).all())
+    assert bool((gb == 3.0).all())
+    obj_np = np.where(g.obj >= 0, a, -1).astype(np.int32)
+    uv, d, _ = gbuffer_to_dev(g)
+    o = to_dev(obj_np)
+    gout = torch.rand((g.F, 4), device="cuda")
+    own = torch.full((size,), 5.0, device="cuda")
+    api.rt_shade_backward(ctx, uv, d, o, api.RT_NEAREST, gout, {a: own})  # the backward's own clear
+    gb.fill_(9.0)
+    api.rt_zero_texture_grads(ctx, {a: gb})
+    api.rt_shade_backward(ctx, uv, d, o, api.RT_NEAREST, gout, {a: gb}, flags=api.RT_ACCUMULATE)
+    torch.cuda.synchronize()
+    assert float(own.abs().sum()) > 0
+    torch.testing.assert_close(gb, own, rtol=1e-5, atol=1e-6)  # equal up to the order of the atomic sums
+    api.rt_destroy_texture(ctx, b)
+    with pytest.raises(api.RadtexError):
+        api.rt_zero_texture_grads(ctx, {b: torch.zeros(size, device="cuda")})
+    api.rt_destroy_texture(ctx, a)
