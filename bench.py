@@ -300,82 +300,143 @@ def oracle_textures(a):
     return texs
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline lines."""
+    import subprocess
+
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_sample(a, g, seconds: float, texs, filt):
+    """A bounded, evenly spread sample of the workload's fragments: every k-th
+    fragment of all its poses, k chosen so the oracle's forward over the sample
+    takes about `seconds` on all host cores (probed on 1/500 of the fragments)."""
+    import oracle
+
+    F = g.obj.shape[0]
+    stride = max(1, F // 200000)
+    t0 = time.perf_counter()
+    oracle.shade(texs, g.uv[::stride], g.dir[::stride], g.obj[::stride], filt)
+    rate = g.obj[::stride].shape[0] / max(time.perf_counter() - t0, 1e-6)
+    count = int(min(F, max(20000, rate * seconds)))
+    stride = max(1, F // count)
+    return stride, g.uv[::stride], g.dir[::stride], g.obj[::stride]
+
+
+def single_thread_rate(texs, uv, d, o, filt, seconds: float = 1.0) -> float:
+    """The oracle's forward rate (fragments/s) on one host thread, on a part of the sample."""
+    import oracle
+
+    cores = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        k = max(1, o.shape[0] // 4000)
+        t0 = time.perf_counter()
+        oracle.shade(texs, uv[::k], d[::k], o[::k], filt)
+        probe = o[::k].shape[0] / max(time.perf_counter() - t0, 1e-6)
+        k = max(1, int(o.shape[0] // max(probe * seconds, 1)))
+        t0 = time.perf_counter()
+        oracle.shade(texs, uv[::k], d[::k], o[::k], filt)
+        return o[::k].shape[0] / max(time.perf_counter() - t0, 1e-9)
+    finally:
+        oracle.set_num_threads(cores)
+
+
+BACKWARD_SUBSAMPLE = 10  # the oracle's backward sums texel gradients serially: it runs on a tenth of the sample
+
+
 def cpu_baseline(a, g, seconds: float):
-    """The oracle as it stands, on a bounded sample of the workload's fragments."""
+    """The oracle as it stands, on a bounded sample of the workload's fragments:
+    the forward on the sample, the backward on every tenth of its fragments, both
+    on all host cores; the step rate combines the two per-fragment times.  The
+    forward's rate on one thread is reported beside it."""
     import oracle
 
     filt = {"nearest": oracle.NEAREST, "angular_bilinear": oracle.ANGULAR_BILINEAR,
             "quadrilinear": oracle.QUADRILINEAR}[a.filter]
     texs = oracle_textures(a)
     F = g.obj.shape[0]
-    # probe the rate on 1/500 of the fragments, then size the sample for `seconds`
-    stride = max(1, F // 200000)
-    t0 = time.perf_counter()
-    oracle.shade(texs, g.uv[::stride], g.dir[::stride], g.obj[::stride], filt)
-    rate = g.obj[::stride].shape[0] / max(time.perf_counter() - t0, 1e-6)
-    count = int(min(F, max(100000, rate * seconds)))
-    stride = max(1, F // count)
-    uv, d, o = g.uv[::stride], g.dir[::stride], g.obj[::stride]
+    stride, uv, d, o = oracle_sample(a, g, seconds, texs, filt)
     t0 = time.perf_counter()
     oracle.shade(texs, uv, d, o, filt)
-    dt = time.perf_counter() - t0
-    fwd = o.shape[0] / dt
-    # backward on a tenth of that sample (the texel-gradient sum is serial)
-    sub = 10
+    fwd = o.shape[0] / (time.perf_counter() - t0)
+    sub = BACKWARD_SUBSAMPLE
     gout = np.ones((o[::sub].shape[0], 4))
     t0 = time.perf_counter()
     oracle.shade_backward(texs, uv[::sub], d[::sub], o[::sub], filt, gout)
     bwd = o[::sub].shape[0] / max(time.perf_counter() - t0, 1e-9)
     step = 1.0 / (1.0 / fwd + 1.0 / bwd)
+    one = single_thread_rate(texs, uv, d, o, filt)
     return {"value": step / 1e9, "unit": "Gfrag/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": ((f"every {stride}th fragment" if stride > 1 else "every fragment") +
-                       f" of the {F}-fragment step ({o.shape[0]} forward, every 10th of those backward: "
+                       f" of the {F}-fragment step ({o.shape[0]} forward, every {sub}th of those backward: "
                        f"{o[::sub].shape[0]}), same textures"),
-            "fwd_gfrag_s": fwd / 1e9, "bwd_gfrag_s": bwd / 1e9}
+            "fwd_gfrag_s": fwd / 1e9, "bwd_gfrag_s": bwd / 1e9,
+            "fwd_gfrag_s_1_thread": one / 1e9, "cpu_model": cpu_model()}
 
 
 def run_reference(a):
-    """--impl reference: the FP64 CPU oracle on host cores, rank 0 only."""
+    """--impl reference: the FP64 CPU oracle on host cores, rank 0 only.  Each
+    step is the oracle's forward over a bounded sample of the workload (every
+    k-th fragment of all its poses) and its backward over every tenth fragment
+    of that sample; ms_per_step is the time those two calls took, and the rate
+    divides the sample by the time of a forward + backward over all of it (the
+    backward's time scaled by ten), reported as ms_per_step_normalised."""
     import synth
 
     rank, world, _ = dist_info()
     if rank != 0:
         return
-    g = synth.sphere_plane_scene(SCENE_SEED, views=min(a.views, 2), width=a.width, height=a.height)
+    g = synth.sphere_plane_scene(SCENE_SEED, views=a.views, width=a.width, height=a.height)
     import oracle
 
     filt = {"nearest": oracle.NEAREST, "angular_bilinear": oracle.ANGULAR_BILINEAR,
             "quadrilinear": oracle.QUADRILINEAR}[a.filter]
     texs = oracle_textures(a)
-    # each step is a bounded sample: every k-th fragment of two poses, sized to ~2 s of oracle work
-    stride = max(1, g.F // 200000)
-    t0 = time.perf_counter()
-    oracle.shade(texs, g.uv[::stride], g.dir[::stride], g.obj[::stride], filt)
-    rate = g.obj[::stride].shape[0] / max(time.perf_counter() - t0, 1e-6)
-    count = int(min(g.F, max(50000, rate * 2.0)))
-    stride = max(1, g.F // count)
-    uv, d, o = g.uv[::stride], g.dir[::stride], g.obj[::stride]
+    # about a minute of oracle work over the whole run, between 0.2 and 2 s of forward per step
+    per_step = min(2.0, max(0.2, 60.0 / max(a.steps + a.warmup, 1)))
+    stride, uv, d, o = oracle_sample(a, g, per_step, texs, filt)
+    sub = BACKWARD_SUBSAMPLE
     gout = np.ones((o.shape[0], 4))
-    sub = 10
-    times = []
+    run_ms, norm_ms = [], []
     for k in range(a.warmup + a.steps):
         t0 = time.perf_counter()
         oracle.shade(texs, uv, d, o, filt)
         t1 = time.perf_counter()
         oracle.shade_backward(texs, uv[::sub], d[::sub], o[::sub], filt, gout[::sub])
         t2 = time.perf_counter()
-        # normalise: forward over the sample + backward scaled to the same fragment count
-        times.append((t1 - t0) + (t2 - t1) * sub)
-    tt = times[a.warmup:]
-    mean = float(np.mean(tt))
-    value = o.shape[0] / mean / 1e9
+        run_ms.append((t2 - t0) * 1e3)
+        norm_ms.append(((t1 - t0) + (t2 - t1) * (o.shape[0] / max(o[::sub].shape[0], 1))) * 1e3)
+    ms = float(np.mean(run_ms[a.warmup:]))
+    ms_norm = float(np.mean(norm_ms[a.warmup:]))
+    value = o.shape[0] / (ms_norm * 1e-3) / 1e9
+    one = single_thread_rate(texs, uv, d, o, filt)
+    config = {"workload": workload_name(a), "fragments_per_step": int(g.F), "views": a.views, "width": a.width,
+              "height": a.height, "buckets": a.buckets, "n": a.n, "storage": a.storage, "filter": a.filter,
+              "objects": len(texs)}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gfrag/s", "n_gpus": a.gpus,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(a), "sample_fragments": int(o.shape[0])},
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "ms_per_step_normalised": ms_norm,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config,
             "cpu_baseline": {"value": value, "unit": "Gfrag/s", "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": f"every {stride}th fragment of 2 poses per step; backward on a tenth, "
-                                       "scaled"},
+                             "sample": (f"every {stride}th fragment of the {g.F}-fragment step ({o.shape[0]} "
+                                        f"forward, every {sub}th of those backward: {o[::sub].shape[0]}); "
+                                        "the rate scales the backward's time to the whole sample"),
+                             "fwd_gfrag_s_1_thread": one / 1e9, "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "Gfrag/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -36,6 +36,9 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "Gfrag/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+    # the measured time of the calls as run, and the rate from the backward's time scaled to the whole sample
+    assert d["ms_per_step_normalised"] >= d["ms_per_step"] > 0
+    assert d["cpu_baseline"]["fwd_gfrag_s_1_thread"] > 0 and d["cpu_baseline"]["cpu_model"]
 
 
 def test_reference_arm_other_ranks_stay_silent():
