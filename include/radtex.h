@@ -85,6 +85,7 @@ typedef enum { RT_LAYOUT_ATLAS = 0, RT_LAYOUT_PLANES = 1 } rt_layout;
 /* rt_shade_backward flags */
 #define RT_ACCUMULATE 1      /* add into dL_dtex / dL_duv / dL_ddir instead of overwriting */
 #define RT_DETERMINISTIC 2   /* bit-reproducible texel gradients (fixed-point sums; see rt_prepare_deterministic) */
+#define RT_FIXED_POINT_GRADS 4 /* dL_dtex entries are int64 buffers that receive the raw fixed-point sums (below) */
 
 #define RT_MAX_OBJECTS 1024
 
@@ -311,6 +312,23 @@ rt_status rt_locate(rt_ctx* ctx, const float* uv, const float* dir, const int32_
 rt_status rt_shade_backward(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,
                             rt_filter filter, const float* dL_dout, float* const* dL_dtex, int32_t n_dtex,
                             float* dL_duv, float* dL_ddir, int32_t flags, rt_stream_t stream);
+
+/* With RT_FIXED_POINT_GRADS (any backward or fused step), each non-NULL
+ * dL_dtex[o] is a device buffer of 4 int64 per texel (the object's layout,
+ * 16-byte aligned) that receives the texel gradients as the deterministic mode
+ * sums them -- signed 64-bit fixed point with 32 fractional bits, each
+ * contribution w * dL/dout rounded once to nearest -- without converting them
+ * to FP32: zeroed first unless RT_ACCUMULATE is set.  Integer sums are
+ * associative, so buffers filled from disjoint sets of fragments (views split
+ * across calls, streams or processes) add up, in any order, to exactly the
+ * buffer one call over all the fragments gives; rt_fixed_to_float converts
+ * the total.  No rt_prepare_deterministic is needed.  Range |sum| < 2^31. */
+
+/* FP32 values from fixed-point sums (RT_FIXED_POINT_GRADS): dst[k] =
+ * (float)(acc[k] * 2^-32) (the product exact in FP64, rounded once), for
+ * k < count; with RT_ACCUMULATE in flags added to dst[k] instead.  acc and dst
+ * device, 16-byte aligned. */
+rt_status rt_fixed_to_float(const int64_t* acc, float* dst, int64_t count, int32_t flags, rt_stream_t stream);
 
 /* Zeroes texel-gradient buffers on `stream` (asynchronous, no allocation): for
  * every non-NULL entry o < n_dtex of dL_dtex (host array of device pointers

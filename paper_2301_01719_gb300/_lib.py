@@ -29,6 +29,7 @@ RT_WRAP_U = 2
 RT_WRAP_V = 4
 RT_ACCUMULATE = 1
 RT_DETERMINISTIC = 2
+RT_FIXED_POINT_GRADS = 4
 RT_MAX_OBJECTS = 1024
 RT_MAX_AO_DIRECTIONS = 1024
 RT_SURFACE_SPHERE, RT_SURFACE_PLANE = range(2)
@@ -95,6 +96,7 @@ SIGNATURES = {
     "rt_footprint": (_I32, [_P, _P, _P, _P, _I64, _I32, ctypes.POINTER(ctypes.c_uint64), _I32, _P]),
     "rt_footprint_noalloc": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, _I32, _P]),
     "rt_zero_texture_grads": (_I32, [_P, _P, _I32, _P]),
+    "rt_fixed_to_float": (_I32, [_P, _P, _I64, _I32, _P]),
     "rt_l2_loss_grad": (_I32, [_P, _P, _P, _I64, ctypes.c_float, _P, _P, _P]),
     "rt_adam_step": (_I32, [_P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                             _I32, _P]),

@@ -13,7 +13,7 @@ import torch
 
 from . import _lib
 from ._lib import (RT_ACCUMULATE, RT_ANGULAR_BILINEAR, RT_BF16, RT_BIT1, RT_BORROW, RT_E4M3_BUCKET_SCALE,  # noqa: F401
-                   RT_DETERMINISTIC, RT_ERR_BAD_OBJ_ID, RT_ERR_CUDA, RT_ERR_INVALID_ARG, RT_ERR_NONFINITE, RT_ERR_OOM,
+                   RT_DETERMINISTIC, RT_ERR_BAD_OBJ_ID, RT_FIXED_POINT_GRADS, RT_ERR_CUDA, RT_ERR_INVALID_ARG, RT_ERR_NONFINITE, RT_ERR_OOM,
                    RT_ERR_TIMEOUT, RT_ERR_UNSUPPORTED, RT_F16, RT_F32, RT_LAYOUT_ATLAS, RT_LAYOUT_PALETTE,
                    RT_LAYOUT_PLANES, RT_MAX_AO_DIRECTIONS, RT_MAX_OBJECTS, RT_NEAREST, RT_OK, RT_QUADRILINEAR,
                    RT_SURFACE_PLANE, RT_SURFACE_SPHERE, RT_WRAP_U, RT_WRAP_V, RadtexError)
@@ -360,7 +360,7 @@ def rt_shade_batched_backward(ctx: Context, uv, dirs, obj, filter: int, dL_dout,
                               dL_ddir=None, flags: int = 0, stream=None) -> None:
     F = _gbuffer(uv, dirs, obj)
     V, H, W = _frames(uv, dirs, obj)
-    arr, n_dtex = _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir)
+    arr, n_dtex = _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir, flags)
     _lib.call("rt_shade_batched_backward", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(obj), V, H, W, int(filter),
               _ptr(dL_dout), arr, n_dtex, _ptr(dL_duv), _ptr(dL_ddir), int(flags), _stream(stream, uv.device))
 
@@ -399,7 +399,7 @@ def rt_shade_batched_l2_step(ctx: Context, uv, dirs, obj, filter: int, target, s
             raise ValueError("out must hold V x H x W x 4 floats")
     if sums is not None and (sums.dtype != torch.float64 or sums.numel() < 2 or not sums.is_cuda):
         raise TypeError("sums must be a CUDA float64 tensor of 2 elements")
-    arr, n_dtex = _grad_args(ctx, F, target, dL_dtex, dL_duv, dL_ddir)
+    arr, n_dtex = _grad_args(ctx, F, target, dL_dtex, dL_duv, dL_ddir, flags)
     _lib.call("rt_shade_batched_l2_step", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(obj), V, H, W, int(filter),
               _ptr(target), float(scale), _ptr(out), _ptr(sums), arr, n_dtex, _ptr(dL_duv), _ptr(dL_ddir),
               int(flags), _stream(stream, uv.device))
@@ -451,7 +451,7 @@ def rt_autotune_backward(ctx: Context, uv, dirs, obj, filter: int, dL_dout, dL_d
     The gradient buffers are left holding the timed launches' results: clear them before use."""
     F = _gbuffer(uv, dirs, obj)
     V, H, W = _frames(uv, dirs, obj)
-    arr, n_dtex = _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir)
+    arr, n_dtex = _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir, flags)
     t = (ctypes.c_int32 * 4)()
     ms = ctypes.c_float()
     _lib.call("rt_autotune_backward", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(obj), V, H, W, int(filter),
@@ -470,7 +470,7 @@ def rt_locate(ctx: Context, uv, dirs, obj, filter: int = RT_QUADRILINEAR, stream
     return idx, coord
 
 
-def _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir):
+def _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir, flags=0):
     _check(dL_dout, "dL_dout", torch.float32, 4)
     if dL_dout.numel() != 4 * F:
         raise ValueError("dL_dout must hold F x 4 floats")
@@ -487,14 +487,27 @@ def _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir):
     if dL_dtex:
         n_dtex = max(dL_dtex) + 1
         arr = (ctypes.c_void_p * n_dtex)()
+        dtype = torch.int64 if flags & RT_FIXED_POINT_GRADS else torch.float32
         for o, t in dL_dtex.items():
-            _check(t, f"dL_dtex[{o}]", torch.float32)
+            _check(t, f"dL_dtex[{o}]", dtype)
             info = rt_texture_info(ctx, o)
             buckets = rt_palette_size(ctx, o) or info["w"] * info["h"]
             if t.numel() != buckets * info["n"] ** 2 * 4:
-                raise ValueError(f"dL_dtex[{o}] must hold (w h or K) n^2 x 4 floats")
+                raise ValueError(f"dL_dtex[{o}] must hold (w h or K) n^2 x 4 values")
             arr[o] = t.data_ptr()
     return arr, n_dtex
+
+
+def rt_fixed_to_float(acc: torch.Tensor, dst: torch.Tensor | None = None, flags: int = 0, stream=None) -> torch.Tensor:
+    """FP32 gradients from the int64 fixed-point sums of RT_FIXED_POINT_GRADS (same shape)."""
+    _check(acc, "acc", torch.int64)
+    if dst is None:
+        dst = torch.empty(acc.shape, dtype=torch.float32, device=acc.device)
+    _check(dst, "dst", torch.float32)
+    if dst.numel() != acc.numel():
+        raise ValueError("dst must hold as many values as acc")
+    _lib.call("rt_fixed_to_float", _ptr(acc), _ptr(dst), acc.numel(), int(flags), _stream(stream, acc.device))
+    return dst
 
 
 def rt_shade_backward(ctx: Context, uv, dirs, obj, filter: int, dL_dout: torch.Tensor, dL_dtex=None,
@@ -502,7 +515,7 @@ def rt_shade_backward(ctx: Context, uv, dirs, obj, filter: int, dL_dout: torch.T
                       stream=None) -> None:
     """dL_dtex: dict {object id: FP32 CUDA tensor in the object's storage layout} or None."""
     F = _gbuffer(uv, dirs, obj)
-    arr, n_dtex = _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir)
+    arr, n_dtex = _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir, flags)
     _lib.call("rt_shade_backward", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(obj), F, int(filter), _ptr(dL_dout),
               arr, n_dtex, _ptr(dL_duv), _ptr(dL_ddir), int(flags), _stream(stream, uv.device))
 
@@ -566,7 +579,7 @@ def rt_shade_world_backward(ctx: Context, uv, dirs, nrm, obj, filter: int, dL_do
                             dL_dnrm: torch.Tensor | None = None, flags: int = 0, stream=None) -> None:
     F = _gbuffer(uv, dirs, obj)
     _normals(nrm, F)
-    arr, n_dtex = _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir)
+    arr, n_dtex = _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir, flags)
     if dL_dnrm is not None:
         _normals(dL_dnrm, F)
     _lib.call("rt_shade_world_backward", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(nrm), _ptr(obj), F, int(filter),
@@ -594,7 +607,7 @@ def rt_shade_world_batched_backward(ctx: Context, uv, dirs, nrm, obj, filter: in
     F = _gbuffer(uv, dirs, obj)
     V, H, W = _frames(uv, dirs, obj)
     _normals(nrm, F)
-    arr, n_dtex = _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir)
+    arr, n_dtex = _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir, flags)
     if dL_dnrm is not None:
         _normals(dL_dnrm, F)
     _lib.call("rt_shade_world_batched_backward", ctx.handle, _ptr(uv), _ptr(dirs), _ptr(nrm), _ptr(obj), V, H, W,

@@ -559,16 +559,17 @@ static rt_status shade_backward_impl(rt_ctx* ctx, const float* uv, const float* 
         return RT_ERR_INVALID_ARG;
     }
     const bool accumulate = (flags & RT_ACCUMULATE) != 0;
-    const bool deterministic = (flags & RT_DETERMINISTIC) != 0;
+    const bool fixed_out = (flags & RT_FIXED_POINT_GRADS) != 0;  // the caller's buffers hold the fixed-point sums
+    const bool deterministic = (flags & RT_DETERMINISTIC) != 0 || fixed_out;
     rt::GradTable grads;
     std::memset(&grads, 0, sizeof(grads));
     bool any = false;
     for (int o = 0; o < n_dtex; ++o) {
         if (!dL_dtex[o]) continue;
         if (o >= RT_MAX_OBJECTS || !ctx->table[o].live || !aligned16(dL_dtex[o])) return RT_ERR_INVALID_ARG;
-        if (deterministic && !ctx->det[o]) return RT_ERR_INVALID_ARG;  // rt_prepare_deterministic first
+        if (deterministic && !fixed_out && !ctx->det[o]) return RT_ERR_INVALID_ARG;  // rt_prepare_deterministic first
         if (ctx->table[o].fmt == RT_BIT1) return RT_ERR_UNSUPPORTED;   // bits have no texel gradient
-        grads.p[o] = deterministic ? static_cast<void*>(ctx->det[o]) : static_cast<void*>(dL_dtex[o]);
+        grads.p[o] = (deterministic && !fixed_out) ? static_cast<void*>(ctx->det[o]) : static_cast<void*>(dL_dtex[o]);
         any = true;
     }
     DeviceGuard g(ctx->device);
@@ -579,7 +580,9 @@ static rt_status shade_backward_impl(rt_ctx* ctx, const float* uv, const float* 
         if (!grads.p[o]) continue;
         const TexDesc& d = ctx->table[o];
         const size_t texels = (size_t)d.plane * d.n * d.n;
-        if (deterministic)
+        if (fixed_out) {
+            if (!accumulate) e = cudaMemsetAsync(dL_dtex[o], 0, 32 * texels, s);
+        } else if (deterministic)
             e = cudaMemsetAsync(ctx->det[o], 0, 32 * texels, s);
         else if (!accumulate)
             e = cudaMemsetAsync(dL_dtex[o], 0, 16 * texels, s);
@@ -596,7 +599,7 @@ static rt_status shade_backward_impl(rt_ctx* ctx, const float* uv, const float* 
             e = rt::launch_backward(ctx->d_table, ctx->n_obj, uv, dir, obj, F, filter, T, ctx->spec, dL_dout, grads, any,
                                     dL_duv, dL_ddir, accumulate, deterministic, ctx->d_status, s);
     }
-    if (deterministic)
+    if (deterministic && !fixed_out)
         for (int o = 0; o < n_dtex && e == cudaSuccess; ++o)
             if (grads.p[o]) {
                 const TexDesc& d = ctx->table[o];
@@ -823,6 +826,12 @@ rt_status rt_shade_world_batched_backward(rt_ctx* ctx, const float* uv, const fl
     static const float kNone[4] = {0.f, 0.f, 0.f, 0.f};  // an unused non-null marker for F = 0
     return shade_backward_impl(ctx, uv, dir, obj, F, filter, T, dL_dout, dL_dtex, n_dtex, dL_duv, dL_ddir, flags,
                                stream, nrm ? nrm : kNone, dL_dnrm);
+}
+
+rt_status rt_fixed_to_float(const int64_t* acc, float* dst, int64_t count, int32_t flags, rt_stream_t stream) {
+    if (count < 0 || (count > 0 && (!acc || !dst)) || !aligned16(acc) || !aligned16(dst)) return RT_ERR_INVALID_ARG;
+    return cuda_status(rt::launch_fixed_to_float(reinterpret_cast<const long long*>(acc), dst, count,
+                                                 (flags & RT_ACCUMULATE) != 0, (cudaStream_t)stream));
 }
 
 rt_status rt_zero_texture_grads(rt_ctx* ctx, float* const* dL_dtex, int32_t n_dtex, rt_stream_t stream) {

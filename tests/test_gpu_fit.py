@@ -192,3 +192,68 @@ def test_fit_converges_and_resumes_bitwise(ctx, tmp_path):
         fit3.load(str(tmp_path / "ck.pt"))
     for f in (fit, fit2, fit3):
         api.rt_destroy_texture(ctx, f.oid)
+
+
+def test_fixed_point_gradients_add_up_over_view_shards(ctx):
+    """RT_FIXED_POINT_GRADS: the int64 sums of two view shards (separate calls, as
+    two data-parallel ranks would compute them) add up bit for bit to one call
+    over all views, and accumulating the second shard into the first's buffer
+    gives the same; converted by rt_fixed_to_float they are the deterministic
+    mode's FP32 gradient bit for bit."""
+    g, uv, d, o, t = small_fit_scene(views=4, size=64)
+    fit = TextureFit(ctx, 16, 16, 8, init=0.3)
+    o = for_object(o, fit.oid)
+    fit.tex.uniform_(0, 1)
+    F = lambda: torch.zeros((8, 8, 16, 16, 4), dtype=torch.int64, device=uv.device)  # noqa: E731
+    flags = api.RT_FIXED_POINT_GRADS
+    every, half_a, half_b, acc = F(), F(), F(), F()
+    api.rt_shade_batched_l2_step(ctx, uv, d, o, api.RT_QUADRILINEAR, t, 0.5, None, None, {fit.oid: every},
+                                 flags=flags)
+    api.rt_shade_batched_l2_step(ctx, uv[:2], d[:2], o[:2], api.RT_QUADRILINEAR, t[:2], 0.5, None, None,
+                                 {fit.oid: half_a}, flags=flags)
+    api.rt_shade_batched_l2_step(ctx, uv[2:], d[2:], o[2:], api.RT_QUADRILINEAR, t[2:], 0.5, None, None,
+                                 {fit.oid: half_b}, flags=flags)
+    api.rt_shade_batched_l2_step(ctx, uv[2:], d[2:], o[2:], api.RT_QUADRILINEAR, t[2:], 0.5, None, None,
+                                 {fit.oid: acc}, flags=flags)
+    api.rt_shade_batched_l2_step(ctx, uv[:2], d[:2], o[:2], api.RT_QUADRILINEAR, t[:2], 0.5, None, None,
+                                 {fit.oid: acc}, flags=flags | api.RT_ACCUMULATE)
+    assert int(half_a.abs().sum()) > 0 and int(half_b.abs().sum()) > 0
+    assert torch.equal(half_a + half_b, every)
+    assert torch.equal(acc, every)
+    # the same sums through the separate backward over the same dL/dout
+    out = api.rt_shade_batched(ctx, uv, d, o, api.RT_QUADRILINEAR)
+    dL = torch.empty_like(out)
+    api.rt_l2_loss_grad(out, t, o, 0.5, dL, None)
+    sep = F()
+    api.rt_shade_batched_backward(ctx, uv, d, o, api.RT_QUADRILINEAR, dL, {fit.oid: sep}, None, None, flags)
+    assert int(sep.abs().sum()) > 0
+    # converted: the deterministic mode's FP32 gradient of the separate backward, bit for bit
+    api.rt_prepare_deterministic(ctx)
+    det = torch.empty_like(fit.tex)
+    api.rt_shade_batched_backward(ctx, uv, d, o, api.RT_QUADRILINEAR, dL, {fit.oid: det}, None, None,
+                                  api.RT_DETERMINISTIC)
+    conv = api.rt_fixed_to_float(sep)
+    assert torch.equal(conv, det)
+    twice = conv.clone()
+    api.rt_fixed_to_float(sep, twice, api.RT_ACCUMULATE)
+    assert torch.equal(twice, det + det)
+    api.rt_destroy_texture(ctx, fit.oid)
+
+
+def test_deterministic_fit_steps_match_the_fixed_point_reduction(ctx):
+    """Deterministic fitting steps (fixed-point texel sums, converted once, then
+    Adam) give a bit-identical texture from run to run and move the loss down
+    (the loss itself is an FP64 atomic sum, equal to rounding)."""
+    g, uv, d, o, t = small_fit_scene(views=4, size=64)
+    losses, texs = [], []
+    for _ in range(2):
+        fit = TextureFit(ctx, 16, 16, 8, init=0.3, deterministic=True)
+        oo = for_object(o, fit.oid)
+        count = fit.shaded_count(oo)
+        ls = [float(fit.step(uv, d, oo, t, count)) for _ in range(5)]
+        losses.append(ls)
+        texs.append(fit.tex.clone())
+        api.rt_destroy_texture(ctx, fit.oid)
+    assert torch.equal(texs[0], texs[1])
+    np.testing.assert_allclose(losses[0], losses[1], rtol=1e-12)
+    assert losses[0][-1] < losses[0][0]
