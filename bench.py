@@ -522,21 +522,18 @@ def run_radtex(a):
     # screen tile of the batched kernels, picked by the library's autotuner on this workload
     tile, tile_ms = api.rt_autotune(ctx, uv, dirs, obj, filt, out, reps=3)
     # and of the backward, timed as the step runs it (the gradients it leaves are cleared by every step)
-    for t in dtex.values():
-        t.zero_()
+    api.rt_zero_texture_grads(ctx, dtex)
     btile, btile_ms = api.rt_autotune_backward(ctx, uv, dirs, obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE,
                                                reps=2)
 
     def step():
         if a.fused:
-            for t in dtex.values():
-                t.zero_()
+            api.rt_zero_texture_grads(ctx, dtex)
             api.rt_shade_batched_l2_step(ctx, uv, dirs, obj, filt, target, 1.0, out, sums, dtex, duv, ddir,
                                          api.RT_ACCUMULATE)
             return
         api.rt_shade_batched(ctx, uv, dirs, obj, filt, out)
-        for t in dtex.values():
-            t.zero_()
+        api.rt_zero_texture_grads(ctx, dtex)
         api.rt_shade_batched_backward(ctx, uv, dirs, obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE)
 
     for _ in range(a.warmup):
@@ -561,8 +558,7 @@ def run_radtex(a):
             if not a.fused:
                 api.rt_shade_batched(ctx, uv, dirs, obj, filt, out)
             e[1].record(stream)
-            for t in dtex.values():
-                t.zero_()
+            api.rt_zero_texture_grads(ctx, dtex)
             e[2].record(stream)
             if a.fused:
                 api.rt_shade_batched_l2_step(ctx, uv, dirs, obj, filt, target, 1.0, out, sums, dtex, duv, ddir,
@@ -605,8 +601,7 @@ def run_radtex(a):
 
         def e2e_step():
             comp = torch.cuda.current_stream(dev)
-            for t in dtex.values():
-                t.zero_()
+            api.rt_zero_texture_grads(ctx, dtex)
             for j, (lo, hi) in enumerate(bounds):
                 with torch.cuda.stream(s_in):
                     if consumed[j] is not None:
@@ -677,9 +672,9 @@ def run_radtex(a):
                    "objects": len(oids), "texture_bytes": int(sum(api.rt_texture_info(ctx, o)["bytes"] for o in oids)),
                    "l2": "inputs larger than L2 (G-buffer %.1f GB, textures %.1f GB per rank)" % (
                        24 * F / 1e9, sum(api.rt_texture_info(ctx, o)["bytes"] for o in oids) / 1e9),
-                   "step": ("zero texel grads + rt_shade_batched_l2_step(target 0, scale 1, RT_ACCUMULATE): "
+                   "step": ("rt_zero_texture_grads + rt_shade_batched_l2_step(target 0, scale 1, RT_ACCUMULATE): "
                             "forward, dL/dout = out, backward in one launch" if a.fused else
-                            "rt_shade_batched + zero texel grads + rt_shade_batched_backward(RT_ACCUMULATE, "
+                            "rt_shade_batched + rt_zero_texture_grads + rt_shade_batched_backward(RT_ACCUMULATE, "
                             "dL/dout = out)"),
                    "tile": {"tw": tile[0], "th": tile[1], "bx": tile[2], "by": tile[3], "autotune_ms": tile_ms},
                    "backward_tile": {"tw": btile[0], "th": btile[1], "bx": btile[2], "by": btile[3],
