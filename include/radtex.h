@@ -196,6 +196,16 @@ int64_t rt_kmeans_tc_scratch_bytes(int32_t w, int32_t h, int32_t n, int32_t K);
 rt_status rt_kmeans_assign_tc(rt_ctx* ctx, int32_t obj_id, int32_t K, const float* centroids, uint32_t* index,
                               float* dist, void* scratch, int64_t scratch_bytes, rt_stream_t stream);
 
+/* The number of polls (each followed by a 32 ns sleep) after which a bounded
+ * wait of the library's kernels -- the mbarrier waits of the tensor-core
+ * k-means assignment's pipeline -- gives up: the kernel then raises
+ * RT_ERR_TIMEOUT (read by rt_get_error), lets the copies and MMAs it has
+ * already issued finish (with the default limit), frees its tensor memory and
+ * returns, and the context stays usable.  0 restores the default, 2^22 polls
+ * (a fraction of a second).  A setting of the context; no counterpart in the
+ * paper. */
+rt_status rt_set_wait_limit(rt_ctx* ctx, uint32_t polls);
+
 rt_status rt_kmeans_init(rt_ctx* ctx, int32_t obj_id, int32_t K, const int32_t* buckets, float* centroids,
                          rt_stream_t stream);
 rt_status rt_kmeans_assign(rt_ctx* ctx, int32_t obj_id, int32_t K, const float* centroids, uint32_t* index,

@@ -113,6 +113,11 @@ def rt_palette_size(ctx: Context, obj_id: int) -> int:
     return K.value
 
 
+def rt_set_wait_limit(ctx: Context, polls: int = 0) -> None:
+    """Polls before a bounded device wait gives up with RT_ERR_TIMEOUT (0: the default)."""
+    _lib.call("rt_set_wait_limit", ctx.handle, int(polls))
+
+
 def rt_kmeans_init(ctx: Context, obj_id: int, K: int, buckets: torch.Tensor, centroids: torch.Tensor | None = None,
                    stream=None) -> torch.Tensor:
     """Centroids (n, n, K, 4) FP32 initialised from the buckets numbered `buckets` (CUDA int32, K)."""

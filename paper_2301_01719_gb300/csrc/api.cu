@@ -28,6 +28,7 @@ struct rt_ctx {
     long long* det[RT_MAX_OBJECTS];      // fixed-point gradient sums of the deterministic mode
     uint32_t* index[RT_MAX_OBJECTS];     // palette index maps the library copied
     int spec = -1;                       // the format shared by all objects (dense PLANES, clamp), else -1
+    uint32_t wait_limit = 0;             // polls of a bounded device wait before it gives up (0: the default)
 };
 
 namespace {
@@ -484,8 +485,14 @@ rt_status rt_kmeans_assign_tc(rt_ctx* ctx, int32_t obj_id, int32_t K, const floa
     DeviceGuard g(ctx->device);
     if (!g.ok) return RT_ERR_CUDA;
     cudaError_t e = rt::launch_kmeans_assign_tc(d, K, centroids, index, dist, scratch, ctx->d_status,
-                                                (cudaStream_t)stream);
+                                                ctx->wait_limit, (cudaStream_t)stream);
     return e == cudaErrorNotSupported ? RT_ERR_UNSUPPORTED : cuda_status(e);
+}
+
+rt_status rt_set_wait_limit(rt_ctx* ctx, uint32_t polls) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    ctx->wait_limit = polls;
+    return RT_OK;
 }
 
 rt_status rt_kmeans_update(rt_ctx* ctx, int32_t obj_id, int32_t K, const uint32_t* index, float* centroids,

@@ -65,13 +65,24 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Waits for the phase of `parity` to complete; false after kSpinLimit polls
-// (each followed by a 32 ns sleep: a fraction of a second in all) or once
-// another role of the CTA has given up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+// Waits for the phase of `parity` to complete; false after `limit` polls
+// (each followed by a 32 ns sleep: with the default kSpinLimit a fraction of a
+// second in all) or once another role of the CTA has given up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, uint32_t limit) {
+    for (uint32_t i = 0; i < limit; ++i) {
         if (mbar_test(bar, parity)) return true;
         if ((i & 255) == 255 && *abort_flag) return false;
+        __nanosleep(32);
+    }
+    return false;
+}
+
+// The drain after a timeout: waits (kSpinLimit polls at most) for copies or
+// MMAs this thread has already issued, whatever the other roles did, so that
+// nothing is in flight into the CTA's shared or tensor memory when it exits.
+__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+        if (mbar_test(bar, parity)) return true;
         __nanosleep(32);
     }
     return false;
@@ -138,7 +149,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 __global__ void __launch_bounds__(THREADS, 1)
     assign_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int B, int Dp,
                   int Kp, const float* __restrict__ cn, const float* __restrict__ xn, uint32_t* __restrict__ index,
-                  float* __restrict__ dist, unsigned* status) {
+                  float* __restrict__ dist, unsigned* status, uint32_t spin_limit) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
@@ -189,7 +200,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int kc = 0; kc < kchunks; ++kc, ++it) {
                 const int s = it % STAGES;
                 const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-                if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+                if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, spin_limit)) {
                     timed_out = true;
                     break;
                 }
@@ -203,7 +214,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             // let the copies already issued land before the CTA exits
             for (int k = 1; k <= STAGES && it - k >= 0; ++k) {
                 const int j = it - k;
-                mbar_wait(&full[j % STAGES], (uint32_t)(j / STAGES) & 1u, abort_flag);
+                mbar_drain(&full[j % STAGES], (uint32_t)(j / STAGES) & 1u);
             }
         }
     } else if (warp == 1 && lane == 0) {
@@ -211,7 +222,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         int it = 0;
         for (int job = 0; job < jobs && !timed_out; ++job) {
             const int a = job & 1;
-            if (!mbar_wait(&accempty[a], ((uint32_t)(job >> 1) & 1u) ^ 1u, abort_flag)) {
+            if (!mbar_wait(&accempty[a], ((uint32_t)(job >> 1) & 1u) ^ 1u, abort_flag, spin_limit)) {
                 timed_out = true;
                 break;
             }
@@ -220,7 +231,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int kc = 0; kc < kchunks; ++kc, ++it) {
                 const int s = it % STAGES;
                 const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-                if (!mbar_wait(&full[s], ph, abort_flag)) {
+                if (!mbar_wait(&full[s], ph, abort_flag, spin_limit)) {
                     timed_out = true;
                     break;
                 }
@@ -238,7 +249,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (timed_out && it > 0) {
             // wait for the MMAs in flight before the tensor memory is freed
             const int j = it - 1;
-            mbar_wait(&empty[j % STAGES], (uint32_t)(j / STAGES) & 1u, abort_flag);
+            mbar_drain(&empty[j % STAGES], (uint32_t)(j / STAGES) & 1u);
         }
     } else if (warp >= 2) {
         // epilogue: thread = accumulator row; warp w reads tensor-memory lanes 32 (w % 4) ..
@@ -252,7 +263,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 best = INFINITY;
                 bestk = 0;
             }
-            if (!mbar_wait(&accfull[a], (uint32_t)(job >> 1) & 1u, abort_flag)) {
+            if (!mbar_wait(&accfull[a], (uint32_t)(job >> 1) & 1u, abort_flag, spin_limit)) {
                 timed_out = true;
                 break;
             }
@@ -421,7 +432,7 @@ static cudaError_t convert_x(const TexDesc& d, const Layout& L, __half* X, cudaS
 int64_t kmeans_tc_scratch_bytes(int W, int H, int n, int K) { return (int64_t)tc::layout(W, H, n, K).bytes; }
 
 cudaError_t launch_kmeans_assign_tc(const TexDesc& d, int K, const float* C, uint32_t* index, float* dist,
-                                    void* scratch, unsigned* status, cudaStream_t stream) {
+                                    void* scratch, unsigned* status, uint32_t spin_limit, cudaStream_t stream) {
     using namespace tc;
     const Layout L = layout(d.W, d.H, d.n, K);
     uint8_t* base = static_cast<uint8_t*>(scratch);
@@ -467,7 +478,7 @@ cudaError_t launch_kmeans_assign_tc(const TexDesc& d, int K, const float* C, uin
     const int64_t mtiles = L.Bp / BM;
     const unsigned grid = (unsigned)(mtiles < sms ? mtiles : sms);  // one CTA per SM (its shared memory)
     assign_kernel<<<grid, THREADS, SMEM_BYTES, stream>>>(tmA, tmB, d.W * d.H, (int)L.Dp, (int)L.Kp, cn, xn, index,
-                                                         dist, status);
+                                                         dist, status, spin_limit ? spin_limit : kSpinLimit);
     return cudaGetLastError();
 }
 

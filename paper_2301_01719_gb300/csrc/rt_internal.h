@@ -100,7 +100,7 @@ cudaError_t launch_world_backward(const TexDesc* table, int n_obj, const float* 
                                   unsigned* status, cudaStream_t stream);
 int64_t kmeans_tc_scratch_bytes(int W, int H, int n, int K);
 cudaError_t launch_kmeans_assign_tc(const TexDesc& d, int K, const float* C, uint32_t* index, float* dist,
-                                    void* scratch, unsigned* status, cudaStream_t stream);
+                                    void* scratch, unsigned* status, uint32_t spin_limit, cudaStream_t stream);
 cudaError_t launch_kmeans_init(const TexDesc& d, int K, const int32_t* buckets, float* C, unsigned* status,
                                cudaStream_t stream);
 cudaError_t launch_kmeans_assign(const TexDesc& d, int K, const float* C, uint32_t* index, float* dist,

@@ -258,3 +258,34 @@ def test_kmeans_tensor_core_assign_matches_oracle(ctx, shape):
     assert np.all(np.abs(gd - dall[np.arange(B), gi]) <= tau)
     assert (gi == fi.cpu().numpy().reshape(-1)).mean() > 0.95
     api.rt_destroy_texture(ctx, oid)
+
+
+def test_kmeans_tensor_core_wait_timeout_is_reported_and_recoverable(ctx):
+    """Failure detection without a GPU fault: with the context's wait limit at one
+    poll, the tensor-core assignment's pipeline waits run out (the TMA copies
+    cannot land within one poll), so the kernel raises RT_ERR_TIMEOUT, drains
+    what it issued and returns; the context stays usable -- with the default
+    limit the same assignment passes and matches the FP32 kernel, and shading
+    still works."""
+    W, H, n, K = 160, 161, 4, 300
+    oid, X = dense_texture(ctx, W, H, n, api.RT_F16, 63)
+    pick = np.random.default_rng(10).choice(W * H, K, replace=False).astype(np.int32)
+    C = api.rt_kmeans_init(ctx, oid, K, to_dev(pick))
+    assert api.rt_get_error(ctx) == api.RT_OK
+    api.rt_set_wait_limit(ctx, 1)
+    try:
+        api.rt_kmeans_assign_tc(ctx, oid, K, C)
+        assert api.rt_get_error(ctx) == api.RT_ERR_TIMEOUT
+    finally:
+        api.rt_set_wait_limit(ctx, 0)
+    assert api.rt_get_error(ctx) == api.RT_OK  # the sticky word was read and cleared
+    ti = api.rt_kmeans_assign_tc(ctx, oid, K, C)
+    assert api.rt_get_error(ctx) == api.RT_OK
+    fi = api.rt_kmeans_assign(ctx, oid, K, C)
+    assert (ti.cpu().numpy() == fi.cpu().numpy()).mean() > 0.95
+    uv = torch.full((64, 2), 0.5, device="cuda")
+    d = torch.tensor([[0.0, 0.0, 1.0]] * 64, device="cuda")
+    o = torch.full((64,), oid, dtype=torch.int32, device="cuda")
+    out = api.rt_shade(ctx, uv, d, o, api.RT_QUADRILINEAR)
+    assert api.rt_get_error(ctx) == api.RT_OK and bool(torch.isfinite(out).all())
+    api.rt_destroy_texture(ctx, oid)
