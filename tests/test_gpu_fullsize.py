@@ -114,6 +114,56 @@ def test_fullsize_backward(full):
         assert np.all(np.abs(got_c[far] - ref_c[far]) <= 1e-3 * np.abs(ref_c[far]) + 1e-5 * scale)
 
 
+def test_fullsize_texel_gradients_per_texel(full):
+    """Texel gradients one by one at the benchmark's size and launch: dL/dout is
+    zero except on the sampled fragments (the 200 000 random ones and the four
+    screen tiles, minus those whose floors lie inside the FP32/FP64 band), so
+    every touched texel's gradient is the sum of w_tap dL/dout over exactly
+    those fragments -- the oracle's taps and weights, summed in FP64 -- and
+    every other texel stays zero."""
+    ctx, g, sel = full["ctx"], full["g"], full["sel"]
+    uv, d, o, out = full["uv"], full["d"], full["o"], full["out"]
+    dev = out.device
+    _, oc, _ = oracle.locate(full["textures"], g.uv[sel], g.dir[sel], g.obj[sel], oracle.QUADRILINEAR)
+    near = np.abs(oc - np.round(oc))
+    keep = (g.obj[sel] >= 0) & ~((near < index_taus(BUCKETS, BUCKETS, N)) & (near > 0)).any(axis=1)
+    fs = sel[keep]
+    assert fs.size > 100000
+    rng = np.random.default_rng(8)
+    gsel = rng.uniform(-1.0, 1.0, (fs.size, 4)).astype(np.float32)
+    gout = torch.zeros_like(out).view(-1, 4)
+    gout[torch.from_numpy(fs).to(dev)] = torch.from_numpy(gsel).to(dev)
+    dtex = {k: torch.empty((N, N, BUCKETS, BUCKETS, 4), device=dev) for k in (0, 1)}
+    api.rt_shade_batched_backward(ctx, uv, d, o, api.RT_QUADRILINEAR, gout.view_as(out), dtex)
+    assert api.rt_get_error(ctx) == api.RT_OK
+    index, weight, flags = oracle.taps(full["textures"], g.uv[fs], g.dir[fs], g.obj[fs], oracle.QUADRILINEAR)
+    assert flags == 0
+    W = BUCKETS * N
+    touched_total = 0
+    for k in (0, 1):
+        mine = g.obj[fs] == k
+        tap = index[mine] >= 0  # -1: no tap
+        idx, w = index[mine][tap], weight[mine][tap]
+        gk = np.repeat(gsel[mine], 16, axis=0).reshape(-1, 16, 4)[tap]
+        keys, inv = np.unique(idx, return_inverse=True)
+        ref = np.zeros((keys.size, 4))
+        bound = np.zeros(keys.size)
+        np.add.at(ref, inv, w[:, None] * gk.astype(np.float64))
+        np.add.at(bound, inv, w * np.abs(gk.astype(np.float64)).max(axis=1))
+        Y, X = keys // W, keys % W
+        t, s_, j, i = (torch.from_numpy(a).to(dev) for a in (Y % N, X % N, Y // N, X // N))
+        got = dtex[k][t, s_, j, i].double().cpu().numpy()
+        err = np.abs(got - ref)
+        tol = 1e-4 * bound[:, None] + 2e-5 * np.abs(gsel).max()
+        assert (err <= tol).all(), (f"object {k}: {(err > tol).sum()} texel channels off, worst "
+                                    f"{(err - tol).max():.3e}")
+        # nothing outside the touched texels
+        total = dtex[k].abs().double().sum().item()
+        assert abs(total - np.abs(got).sum()) <= 1e-6 * max(total, 1.0)
+        touched_total += keys.size
+    assert touched_total > 1000000
+
+
 def test_fullsize_fused_l2_step(full):
     """The benchmark's fused step (forward, L2 loss against a zero target and
     backward in one kernel) at full size: its colours are rt_shade_batched's bit
