@@ -194,21 +194,27 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernel sources."""
+def recorded_traffic(kernel: str, algorithmic_bytes: float):
+    """DRAM bytes per launch of `kernel` at this launch's size, scaled from the committed
+    ncu capture of a small case (profiles/traffic.md: DRAM read + write bytes and the
+    algorithmic bytes of that launch) by the ratio of the algorithmic bytes -- if the
+    capture was taken on the current kernel sources; else (None, None)."""
     path = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(path):
-        return None
+        return None, None
     src = kernel_source_hash()
     with open(path) as fh:
         for line in fh:
             parts = [x.strip() for x in line.strip().strip("|").split("|")]
-            if len(parts) >= 4 and parts[0] == kernel and parts[1] == workload and parts[3] == src:
+            if len(parts) >= 5 and parts[0] == kernel and parts[4] == src:
                 try:
-                    return float(parts[2])
+                    dram, alg = float(parts[2]), float(parts[3])
                 except ValueError:
-                    return None
-    return None
+                    return None, None
+                ratio = dram / alg
+                return ratio * algorithmic_bytes, (f"ncu DRAM bytes of {parts[1]} ({ratio:.3f} x its algorithmic "
+                                                   "bytes), scaled to this launch's algorithmic bytes")
+    return None, None
 
 
 # ---------------------------------------------------------------------------
@@ -651,8 +657,9 @@ def run_radtex(a):
     wl = workload_name(a)
 
     def roof(achieved, kernel, nbytes):
+        traffic, traffic_source = recorded_traffic(kernel, nbytes)
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": recorded_traffic(kernel, wl), "peak_source": peak_kind,
+                "traffic": traffic, "traffic_source": traffic_source, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": int(nbytes), "kernel": kernel}
 
     if a.fused:
