@@ -413,10 +413,21 @@ def run_reference(a):
     filt = {"nearest": oracle.NEAREST, "angular_bilinear": oracle.ANGULAR_BILINEAR,
             "quadrilinear": oracle.QUADRILINEAR}[a.filter]
     texs = oracle_textures(a)
-    # about a minute of oracle work over the whole run, between 0.2 and 2 s of forward per step
-    per_step = min(2.0, max(0.2, 60.0 / max(a.steps + a.warmup, 1)))
-    stride, uv, d, o = oracle_sample(a, g, per_step, texs, filt)
     sub = BACKWARD_SUBSAMPLE
+    # about a minute of oracle work over the whole run, between 0.3 and 3 s per step: probe the
+    # forward and backward rates, then size the forward's share of a step so that the forward
+    # over the sample and the backward over every tenth fragment of it fit the step's time
+    per_step = min(3.0, max(0.3, 60.0 / max(a.steps + a.warmup, 1)))
+    k = max(1, g.F // 20000)
+    t0 = time.perf_counter()
+    oracle.shade(texs, g.uv[::k], g.dir[::k], g.obj[::k], filt)
+    t_fwd = (time.perf_counter() - t0) / g.obj[::k].shape[0]
+    kb = max(1, g.F // 2000)
+    t0 = time.perf_counter()
+    oracle.shade_backward(texs, g.uv[::kb], g.dir[::kb], g.obj[::kb], filt, np.ones((g.obj[::kb].shape[0], 4)))
+    t_bwd = (time.perf_counter() - t0) / g.obj[::kb].shape[0]
+    fwd_share = t_fwd / (t_fwd + t_bwd / sub)
+    stride, uv, d, o = oracle_sample(a, g, per_step * fwd_share, texs, filt)
     gout = np.ones((o.shape[0], 4))
     run_ms, norm_ms = [], []
     for k in range(a.warmup + a.steps):

@@ -335,10 +335,14 @@ rt_status rt_shade_backward(rt_ctx* ctx, const float* uv, const float* dir, cons
  * the total.  No rt_prepare_deterministic is needed.  Range |sum| < 2^31. */
 
 /* FP32 values from fixed-point sums (RT_FIXED_POINT_GRADS): dst[k] =
- * (float)(acc[k] * 2^-32) (the product exact in FP64, rounded once), for
- * k < count; with RT_ACCUMULATE in flags added to dst[k] instead.  acc and dst
- * device, 16-byte aligned. */
-rt_status rt_fixed_to_float(const int64_t* acc, float* dst, int64_t count, int32_t flags, rt_stream_t stream);
+ * (float)(acc[k] * 2^-32 * scale) (the product taken in FP64, rounded once),
+ * for k < count; with RT_ACCUMULATE in flags added to dst[k] instead.  A loss
+ * whose dL/dout carries a small constant factor (a mean over many fragments)
+ * keeps its resolution when the sums are taken without it (a fused step with
+ * scale 1) and the factor is applied here.  acc and dst device, 16-byte
+ * aligned; scale finite. */
+rt_status rt_fixed_to_float(const int64_t* acc, float* dst, int64_t count, double scale, int32_t flags,
+                            rt_stream_t stream);
 
 /* Zeroes texel-gradient buffers on `stream` (asynchronous, no allocation): for
  * every non-NULL entry o < n_dtex of dL_dtex (host array of device pointers
@@ -539,6 +543,7 @@ rt_status rt_l2_loss_grad(const float* out, const float* target, const int32_t* 
  * All four arrays device, 16-byte aligned. */
 rt_status rt_adam_step(float* param, const float* grad, float* m, float* v, int64_t count, float lr, float beta1,
                        float beta2, float eps, int32_t step, rt_stream_t stream);
+
 
 /* Converts an FP32 4-channel texture buffer of w x h buckets of n x n texels
  * between layouts (device src and dst, which must not overlap). */

@@ -97,7 +97,7 @@ SIGNATURES = {
     "rt_footprint_noalloc": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, _I32, _P]),
     "rt_zero_texture_grads": (_I32, [_P, _P, _I32, _P]),
     "rt_set_wait_limit": (_I32, [_P, ctypes.c_uint32]),
-    "rt_fixed_to_float": (_I32, [_P, _P, _I64, _I32, _P]),
+    "rt_fixed_to_float": (_I32, [_P, _P, _I64, ctypes.c_double, _I32, _P]),
     "rt_l2_loss_grad": (_I32, [_P, _P, _P, _I64, ctypes.c_float, _P, _P, _P]),
     "rt_adam_step": (_I32, [_P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                             _I32, _P]),

@@ -503,15 +503,17 @@ def _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir, flags=0):
     return arr, n_dtex
 
 
-def rt_fixed_to_float(acc: torch.Tensor, dst: torch.Tensor | None = None, flags: int = 0, stream=None) -> torch.Tensor:
-    """FP32 gradients from the int64 fixed-point sums of RT_FIXED_POINT_GRADS (same shape)."""
+def rt_fixed_to_float(acc: torch.Tensor, dst: torch.Tensor | None = None, flags: int = 0, stream=None,
+                      scale: float = 1.0) -> torch.Tensor:
+    """FP32 gradients (times `scale`) from the int64 fixed-point sums of RT_FIXED_POINT_GRADS (same shape)."""
     _check(acc, "acc", torch.int64)
     if dst is None:
         dst = torch.empty(acc.shape, dtype=torch.float32, device=acc.device)
     _check(dst, "dst", torch.float32)
     if dst.numel() != acc.numel():
         raise ValueError("dst must hold as many values as acc")
-    _lib.call("rt_fixed_to_float", _ptr(acc), _ptr(dst), acc.numel(), int(flags), _stream(stream, acc.device))
+    _lib.call("rt_fixed_to_float", _ptr(acc), _ptr(dst), acc.numel(), float(scale), int(flags),
+              _stream(stream, acc.device))
     return dst
 
 

@@ -835,10 +835,12 @@ rt_status rt_shade_world_batched_backward(rt_ctx* ctx, const float* uv, const fl
                                stream, nrm ? nrm : kNone, dL_dnrm);
 }
 
-rt_status rt_fixed_to_float(const int64_t* acc, float* dst, int64_t count, int32_t flags, rt_stream_t stream) {
-    if (count < 0 || (count > 0 && (!acc || !dst)) || !aligned16(acc) || !aligned16(dst)) return RT_ERR_INVALID_ARG;
+rt_status rt_fixed_to_float(const int64_t* acc, float* dst, int64_t count, double scale, int32_t flags,
+                            rt_stream_t stream) {
+    if (count < 0 || (count > 0 && (!acc || !dst)) || !aligned16(acc) || !aligned16(dst) || !std::isfinite(scale))
+        return RT_ERR_INVALID_ARG;
     return cuda_status(rt::launch_fixed_to_float(reinterpret_cast<const long long*>(acc), dst, count,
-                                                 (flags & RT_ACCUMULATE) != 0, (cudaStream_t)stream));
+                                                 (flags & RT_ACCUMULATE) != 0, (cudaStream_t)stream, scale));
 }
 
 rt_status rt_zero_texture_grads(rt_ctx* ctx, float* const* dL_dtex, int32_t n_dtex, rt_stream_t stream) {

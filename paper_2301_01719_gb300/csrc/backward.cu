@@ -200,20 +200,22 @@ cudaError_t launch_world_backward(const TexDesc* table, int n_obj, const float* 
 #undef RT_WBWD_D
 }
 
-// Fixed-point sums (deterministic mode) -> FP32 gradients, added to or overwriting dst.
+// Fixed-point sums (deterministic mode) -> FP32 gradients, times `scale` (the
+// product taken in FP64, rounded once), added to or overwriting dst.
 __global__ void fixed_to_float_kernel(const long long* __restrict__ acc, float* __restrict__ dst, int64_t count,
-                                      bool accumulate) {
+                                      double scale, bool accumulate) {
+    const double f = scale * (1.0 / 4294967296.0);
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
-        float v = (float)((double)acc[k] * (1.0 / 4294967296.0));
+        float v = (float)((double)acc[k] * f);
         dst[k] = accumulate ? dst[k] + v : v;
     }
 }
 
 cudaError_t launch_fixed_to_float(const long long* acc, float* dst, int64_t count, bool accumulate,
-                                  cudaStream_t stream) {
+                                  cudaStream_t stream, double scale) {
     if (count <= 0) return cudaSuccess;
     int64_t blocks = (count + 255) / 256;
-    fixed_to_float_kernel<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, stream>>>(acc, dst, count,
+    fixed_to_float_kernel<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, stream>>>(acc, dst, count, scale,
                                                                                           accumulate);
     return cudaGetLastError();
 }

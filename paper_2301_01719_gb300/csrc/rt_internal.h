@@ -79,7 +79,7 @@ cudaError_t launch_fused_l2(const TexDesc* table, int n_obj, const float* uv, co
                             float* dL_ddir, bool accumulate, bool deterministic, unsigned* status,
                             cudaStream_t stream);
 cudaError_t launch_fixed_to_float(const long long* acc, float* dst, int64_t count, bool accumulate,
-                                  cudaStream_t stream);
+                                  cudaStream_t stream, double scale = 1.0);
 
 cudaError_t launch_encode(const float* src, int src_layout, void* dst, float* scale, int W, int H, int n, int fmt,
                           cudaStream_t stream);

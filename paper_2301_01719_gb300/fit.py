@@ -108,10 +108,12 @@ class TextureFit:
         self.sums.zero_()
         scale = 1.0 / (4.0 * max(count, 1))
         if self.deterministic:
-            api.rt_shade_batched_l2_step(self.ctx, uv, dirs, obj, self.filt, target, scale, out, self.sums,
+            # the fixed-point sums are taken of w (out - target), unscaled (resolution 2^-32 against
+            # residuals of order one), and the loss's 1 / (4 count) is applied in the conversion
+            api.rt_shade_batched_l2_step(self.ctx, uv, dirs, obj, self.filt, target, 1.0, out, self.sums,
                                          {self.oid: self.grad_fixed}, None, None, api.RT_FIXED_POINT_GRADS)
             all_reduce_gradients(self.grad_fixed, self.sums, self.group)
-            api.rt_fixed_to_float(self.grad_fixed, self.grad)
+            api.rt_fixed_to_float(self.grad_fixed, self.grad, scale=scale)
         else:
             api.rt_shade_batched_l2_step(self.ctx, uv, dirs, obj, self.filt, target, scale, out, self.sums,
                                          {self.oid: self.grad}, None, None, 0)

@@ -257,3 +257,43 @@ def test_deterministic_fit_steps_match_the_fixed_point_reduction(ctx):
     assert torch.equal(texs[0], texs[1])
     np.testing.assert_allclose(losses[0], losses[1], rtol=1e-12)
     assert losses[0][-1] < losses[0][0]
+
+
+def test_deterministic_fit_gradient_matches_the_fast_one(ctx):
+    """The deterministic fit sums w (out - target) in fixed point and applies the
+    loss's 1 / (4 count) in the conversion: its texel gradient equals the fast
+    one to FP32 summation accuracy.  The same at a loss scale of 1e-9, where each
+    scaled contribution w * 1e-9 (out - target) would lie below the fixed point's
+    2^-32 resolution if it were summed with the scale."""
+    g, uv, d, o, t = small_fit_scene(views=4, size=64)
+    grads = []
+    for det in (False, True):
+        fit = TextureFit(ctx, 16, 16, 8, init=0.3, deterministic=det)
+        oo = for_object(o, fit.oid)
+        fit.step(uv, d, oo, t, fit.shaded_count(oo))
+        torch.cuda.synchronize()
+        grads.append(fit.grad.clone())  # the step's gradient (Adam leaves it in place)
+        api.rt_destroy_texture(ctx, fit.oid)
+    fast, det = grads
+    m = float(fast.abs().max())
+    err = float((det - fast).abs().max())
+    print(f"deterministic vs fast fit gradient: max |diff| {err:.3e}, max |g| {m:.3e}")
+    assert m > 0 and err <= 1e-4 * m
+    # a loss scale of 1e-9: the unscaled fixed-point sums, scaled in the conversion
+    fit = TextureFit(ctx, 16, 16, 8, init=0.3)
+    oo = for_object(o, fit.oid)
+    tiny = 1e-9
+    fast = torch.empty_like(fit.tex)
+    api.rt_shade_batched_l2_step(ctx, uv, d, oo, api.RT_QUADRILINEAR, t, tiny, None, None, {fit.oid: fast})
+    acc = torch.zeros(fit.tex.shape, dtype=torch.int64, device=uv.device)
+    api.rt_shade_batched_l2_step(ctx, uv, d, oo, api.RT_QUADRILINEAR, t, 1.0, None, None, {fit.oid: acc},
+                                 flags=api.RT_FIXED_POINT_GRADS)
+    det = api.rt_fixed_to_float(acc, scale=tiny)
+    m = float(fast.abs().max())
+    assert m > 0 and float((det - fast).abs().max()) <= 1e-4 * m
+    # summed with the scale, the contributions round away
+    coarse = torch.zeros_like(acc)
+    api.rt_shade_batched_l2_step(ctx, uv, d, oo, api.RT_QUADRILINEAR, t, tiny, None, None, {fit.oid: coarse},
+                                 flags=api.RT_FIXED_POINT_GRADS)
+    assert float((api.rt_fixed_to_float(coarse) - fast).abs().max()) > 1e-3 * m
+    api.rt_destroy_texture(ctx, fit.oid)
