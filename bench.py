@@ -547,7 +547,7 @@ def run_radtex(a):
         if a.fused:
             api.rt_zero_texture_grads(ctx, dtex)
             api.rt_shade_batched_l2_step(ctx, uv, dirs, obj, filt, target, 1.0, out, sums, dtex, duv, ddir,
-                                         api.RT_ACCUMULATE)
+                                         api.RT_ACCUMULATE_TEXELS)
             return
         api.rt_shade_batched(ctx, uv, dirs, obj, filt, out)
         api.rt_zero_texture_grads(ctx, dtex)
@@ -579,7 +579,7 @@ def run_radtex(a):
             e[2].record(stream)
             if a.fused:
                 api.rt_shade_batched_l2_step(ctx, uv, dirs, obj, filt, target, 1.0, out, sums, dtex, duv, ddir,
-                                             api.RT_ACCUMULATE)
+                                             api.RT_ACCUMULATE_TEXELS)
             else:
                 api.rt_shade_batched_backward(ctx, uv, dirs, obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE)
             e[3].record(stream)
@@ -632,7 +632,7 @@ def run_radtex(a):
                 if a.fused:
                     api.rt_shade_batched_l2_step(ctx, d_uv[lo:hi], d_dir[lo:hi], d_obj[lo:hi], filt, target[lo:hi],
                                                  1.0, out[lo:hi], sums, dtex, duv[lo:hi], ddir[lo:hi],
-                                                 api.RT_ACCUMULATE)
+                                                 api.RT_ACCUMULATE_TEXELS)
                 else:
                     api.rt_shade_batched(ctx, d_uv[lo:hi], d_dir[lo:hi], d_obj[lo:hi], filt, out[lo:hi])
                     api.rt_shade_batched_backward(ctx, d_uv[lo:hi], d_dir[lo:hi], d_obj[lo:hi], filt, out[lo:hi],
@@ -690,7 +690,7 @@ def run_radtex(a):
                    "objects": len(oids), "texture_bytes": int(sum(api.rt_texture_info(ctx, o)["bytes"] for o in oids)),
                    "l2": "inputs larger than L2 (G-buffer %.1f GB, textures %.1f GB per rank)" % (
                        24 * F / 1e9, sum(api.rt_texture_info(ctx, o)["bytes"] for o in oids) / 1e9),
-                   "step": ("rt_zero_texture_grads + rt_shade_batched_l2_step(target 0, scale 1, RT_ACCUMULATE): "
+                   "step": ("rt_zero_texture_grads + rt_shade_batched_l2_step(target 0, scale 1, RT_ACCUMULATE_TEXELS): "
                             "forward, dL/dout = out, backward in one launch" if a.fused else
                             "rt_shade_batched + rt_zero_texture_grads + rt_shade_batched_backward(RT_ACCUMULATE, "
                             "dL/dout = out)"),

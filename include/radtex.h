@@ -86,6 +86,7 @@ typedef enum { RT_LAYOUT_ATLAS = 0, RT_LAYOUT_PLANES = 1 } rt_layout;
 #define RT_ACCUMULATE 1      /* add into dL_dtex / dL_duv / dL_ddir instead of overwriting */
 #define RT_DETERMINISTIC 2   /* bit-reproducible texel gradients (fixed-point sums; see rt_prepare_deterministic) */
 #define RT_FIXED_POINT_GRADS 4 /* dL_dtex entries are int64 buffers that receive the raw fixed-point sums (below) */
+#define RT_ACCUMULATE_TEXELS 8 /* add into dL_dtex (no clear first) but overwrite dL_duv / dL_ddir / dL_dnrm */
 
 #define RT_MAX_OBJECTS 1024
 
@@ -313,7 +314,9 @@ rt_status rt_locate(rt_ctx* ctx, const float* uv, const float* dir, const int32_
  *            the filter weights, the Note's clamp, Eq. 3 and Eq. 1b.
  * Without RT_ACCUMULATE the per-fragment outputs are overwritten and each
  * dL_dtex buffer is zeroed first (a full write of the buffer); with it, all
- * outputs are added to.  With RT_DETERMINISTIC the texel gradients are summed
+ * outputs are added to.  With RT_ACCUMULATE_TEXELS alone the texel gradients
+ * are added to (a caller that clears them itself, rt_zero_texture_grads) and
+ * the per-fragment outputs are overwritten (not read).  With RT_DETERMINISTIC the texel gradients are summed
  * in fixed point (rt_prepare_deterministic, which must have been called after
  * the objects were created) and are bit-identical from run to run; the UV and
  * direction gradients are per fragment and always deterministic.  Subgradients: the floor branch at integer

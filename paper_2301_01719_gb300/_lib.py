@@ -30,6 +30,7 @@ RT_WRAP_V = 4
 RT_ACCUMULATE = 1
 RT_DETERMINISTIC = 2
 RT_FIXED_POINT_GRADS = 4
+RT_ACCUMULATE_TEXELS = 8
 RT_MAX_OBJECTS = 1024
 RT_MAX_AO_DIRECTIONS = 1024
 RT_SURFACE_SPHERE, RT_SURFACE_PLANE = range(2)

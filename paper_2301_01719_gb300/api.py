@@ -12,11 +12,12 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import (RT_ACCUMULATE, RT_ANGULAR_BILINEAR, RT_BF16, RT_BIT1, RT_BORROW, RT_E4M3_BUCKET_SCALE,  # noqa: F401
-                   RT_DETERMINISTIC, RT_ERR_BAD_OBJ_ID, RT_FIXED_POINT_GRADS, RT_ERR_CUDA, RT_ERR_INVALID_ARG, RT_ERR_NONFINITE, RT_ERR_OOM,
-                   RT_ERR_TIMEOUT, RT_ERR_UNSUPPORTED, RT_F16, RT_F32, RT_LAYOUT_ATLAS, RT_LAYOUT_PALETTE,
-                   RT_LAYOUT_PLANES, RT_MAX_AO_DIRECTIONS, RT_MAX_OBJECTS, RT_NEAREST, RT_OK, RT_QUADRILINEAR,
-                   RT_SURFACE_PLANE, RT_SURFACE_SPHERE, RT_WRAP_U, RT_WRAP_V, RadtexError)
+from ._lib import (RT_ACCUMULATE, RT_ACCUMULATE_TEXELS, RT_ANGULAR_BILINEAR, RT_BF16, RT_BIT1,  # noqa: F401
+                   RT_BORROW, RT_DETERMINISTIC, RT_E4M3_BUCKET_SCALE, RT_ERR_BAD_OBJ_ID, RT_ERR_CUDA,
+                   RT_ERR_INVALID_ARG, RT_ERR_NONFINITE, RT_ERR_OOM, RT_ERR_TIMEOUT, RT_ERR_UNSUPPORTED, RT_F16, RT_F32,
+                   RT_FIXED_POINT_GRADS, RT_LAYOUT_ATLAS, RT_LAYOUT_PALETTE, RT_LAYOUT_PLANES, RT_MAX_AO_DIRECTIONS,
+                   RT_MAX_OBJECTS, RT_NEAREST, RT_OK, RT_QUADRILINEAR, RT_SURFACE_PLANE, RT_SURFACE_SPHERE, RT_WRAP_U,
+                   RT_WRAP_V, RadtexError)
 
 FORMAT_BYTES = {RT_F32: 16, RT_F16: 8, RT_BF16: 8, RT_E4M3_BUCKET_SCALE: 4, RT_BIT1: 1 / 8}
 CODE_DTYPE = {RT_F32: torch.float32, RT_F16: torch.int16, RT_BF16: torch.int16, RT_E4M3_BUCKET_SCALE: torch.uint8,

@@ -565,7 +565,8 @@ static rt_status shade_backward_impl(rt_ctx* ctx, const float* uv, const float* 
     } else if (F > 0 && (!dL_dout || !aligned16(dL_dout))) {
         return RT_ERR_INVALID_ARG;
     }
-    const bool accumulate = (flags & RT_ACCUMULATE) != 0;
+    const bool accumulate = (flags & RT_ACCUMULATE) != 0;                       // every output adds
+    const bool accumulate_tex = accumulate || (flags & RT_ACCUMULATE_TEXELS) != 0;  // the texel gradients add
     const bool fixed_out = (flags & RT_FIXED_POINT_GRADS) != 0;  // the caller's buffers hold the fixed-point sums
     const bool deterministic = (flags & RT_DETERMINISTIC) != 0 || fixed_out;
     rt::GradTable grads;
@@ -588,10 +589,10 @@ static rt_status shade_backward_impl(rt_ctx* ctx, const float* uv, const float* 
         const TexDesc& d = ctx->table[o];
         const size_t texels = (size_t)d.plane * d.n * d.n;
         if (fixed_out) {
-            if (!accumulate) e = cudaMemsetAsync(dL_dtex[o], 0, 32 * texels, s);
+            if (!accumulate_tex) e = cudaMemsetAsync(dL_dtex[o], 0, 32 * texels, s);
         } else if (deterministic)
             e = cudaMemsetAsync(ctx->det[o], 0, 32 * texels, s);
-        else if (!accumulate)
+        else if (!accumulate_tex)
             e = cudaMemsetAsync(dL_dtex[o], 0, 16 * texels, s);
     }
     if (e == cudaSuccess && F > 0) {
@@ -610,8 +611,8 @@ static rt_status shade_backward_impl(rt_ctx* ctx, const float* uv, const float* 
         for (int o = 0; o < n_dtex && e == cudaSuccess; ++o)
             if (grads.p[o]) {
                 const TexDesc& d = ctx->table[o];
-                e = rt::launch_fixed_to_float(ctx->det[o], dL_dtex[o], (int64_t)d.plane * d.n * d.n * 4, accumulate,
-                                              s);
+                e = rt::launch_fixed_to_float(ctx->det[o], dL_dtex[o], (int64_t)d.plane * d.n * d.n * 4,
+                                              accumulate_tex, s);
             }
     return cuda_status(e);
 }

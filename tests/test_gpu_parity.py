@@ -502,6 +502,21 @@ def test_zero_texture_grads(ctx):
     torch.cuda.synchronize()
     assert float(own.abs().sum()) > 0
     torch.testing.assert_close(gb, own, rtol=1e-5, atol=1e-6)  # equal up to the order of the atomic sums
+    # RT_ACCUMULATE_TEXELS: texel gradients add to the cleared buffer, per-fragment outputs are overwritten
+    filt = api.RT_QUADRILINEAR
+    duv0, ddir0 = torch.empty_like(uv), torch.empty_like(d)
+    g0 = torch.empty((size,), device="cuda")
+    api.rt_shade_backward(ctx, uv, d, o, filt, gout, {a: g0}, duv0, ddir0)
+    duv1, ddir1 = torch.full_like(uv, float("nan")), torch.full_like(d, float("nan"))
+    g1 = torch.full((size,), 4.0, device="cuda")
+    api.rt_zero_texture_grads(ctx, {a: g1})
+    api.rt_shade_backward(ctx, uv, d, o, filt, gout, {a: g1}, duv1, ddir1, flags=api.RT_ACCUMULATE_TEXELS)
+    torch.cuda.synchronize()
+    assert torch.equal(duv1, duv0) and torch.equal(ddir1, ddir0)
+    torch.testing.assert_close(g1, g0, rtol=1e-5, atol=1e-6)
+    api.rt_shade_backward(ctx, uv, d, o, filt, gout, {a: g1}, duv1, ddir1, flags=api.RT_ACCUMULATE_TEXELS)
+    torch.testing.assert_close(g1, 2 * g0, rtol=1e-5, atol=1e-6)  # no clear: the second call adds
+    assert torch.equal(duv1, duv0) and torch.equal(ddir1, ddir0)  # overwritten, not summed
     api.rt_destroy_texture(ctx, b)
     with pytest.raises(api.RadtexError):
         api.rt_zero_texture_grads(ctx, {b: torch.zeros(size, device="cuda")})
