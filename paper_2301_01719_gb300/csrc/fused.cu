@@ -14,13 +14,14 @@
 
 namespace rt {
 
-// Held to 96 registers (5 blocks, 20 warps per SM): at the backward's 80 the
-// forward's taps and the backward's state do not fit and spill.  A variant
+// Held to 128 registers (4 blocks, 16 warps per SM; it compiles to 102 without
+// spills): at 5 blocks (96 registers) the step took 5.86 ms against 5.65 ms, at
+// 6 blocks (80, spilling) 6.21 ms, on the 60-pose 1080p step.  A variant
 // that gathers the 16 taps once (the colour-derivative vectors formed from the
 // forward's lerps and projected on dL/dout) needs far more registers and
 // measured slower at every occupancy (7.0 ms at best against 6.4 ms).
 template <int FILTER, bool DET, int SPEC>
-__global__ void __launch_bounds__(kBackThreads, (!DET && SPEC >= 0) ? 5 : 1) fused_l2_kernel(
+__global__ void __launch_bounds__(kBackThreads, (!DET && SPEC >= 0) ? 4 : 1) fused_l2_kernel(
     const TexDesc* __restrict__ table, int n_obj, const float* __restrict__ uv, const float* __restrict__ dir,
     const int32_t* __restrict__ obj, int64_t F, Tiling tiling, const float* __restrict__ target, float scale,
     float* __restrict__ out, double* __restrict__ sums, const __grid_constant__ GradTable grads, bool any_grad,
