@@ -57,7 +57,8 @@ typedef enum {
     RT_ERR_BAD_OBJ_ID = 4,   /* device: an object id names no texture */
     RT_ERR_NONFINITE = 5,    /* device: a UV or direction was NaN or infinite */
     RT_ERR_TIMEOUT = 6,      /* device: a bounded wait gave up */
-    RT_ERR_UNSUPPORTED = 7   /* the combination of options is not implemented */
+    RT_ERR_UNSUPPORTED = 7,  /* the combination of options is not implemented */
+    RT_ERR_OUT_OF_BOUNDS = 8 /* device, checked build only: a computed texel address fell outside its object */
 } rt_status;
 
 typedef enum {
@@ -554,9 +555,28 @@ rt_status rt_convert_layout(const float* src, rt_layout src_layout, float* dst, 
                             int32_t h, int32_t n, rt_stream_t stream);
 
 /* Synchronises `stream`, then reads and clears the context's sticky status
- * word: *device_status = RT_OK, or the first of RT_ERR_BAD_OBJ_ID,
- * RT_ERR_NONFINITE, RT_ERR_TIMEOUT raised since the last call. */
+ * word: *device_status = RT_OK, or the first of RT_ERR_OUT_OF_BOUNDS,
+ * RT_ERR_BAD_OBJ_ID, RT_ERR_NONFINITE, RT_ERR_TIMEOUT, RT_ERR_INVALID_ARG raised
+ * since the last call. */
 rt_status rt_get_error(rt_ctx* ctx, rt_stream_t stream, rt_status* device_status);
+
+/* The checked build (libradtex_checked.so, compiled with RADTEX_CHECKED; no
+ * counterpart in the paper).  Every texel index the lookups and the texel-
+ * gradient reductions compute (Section 2's bucket and in-bucket texels), every
+ * bucket of the w x h matrix and every stored bucket a palette's index map
+ * names is checked against its object's extent on the device.  A failed check
+ * sets a sticky bit that rt_get_error reports as RT_ERR_OUT_OF_BOUNDS, and the
+ * access goes to texel 0 (bucket 0) of the same object instead: it stays
+ * inside the object's storage and nothing traps.  The outputs of a call that
+ * raised it are not meaningful.
+ *
+ * rt_checked_limit_extent lowers the extent that those checks allow for object
+ * obj_id to `texels` (0 <= texels <= the object's texel count; larger values,
+ * a bad id or a dead object give RT_ERR_INVALID_ARG) without touching the
+ * storage, so that in-bounds accesses past it raise the error; it exists to
+ * test the checks.  Synchronous.  The normal build returns RT_ERR_UNSUPPORTED
+ * and checks nothing. */
+rt_status rt_checked_limit_extent(rt_ctx* ctx, int32_t obj_id, int64_t texels);
 
 /* A static English description of a status code. */
 const char* rt_status_string(rt_status status);

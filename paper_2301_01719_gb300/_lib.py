@@ -12,12 +12,16 @@ import re
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libradtex.so")
+# RADTEX_CHECKED=1 in the environment loads the bounds-checked build instead
+# (libradtex_checked.so: the same entry points, every computed texel address
+# checked on the device).
+CHECKED = os.environ.get("RADTEX_CHECKED", "0") not in ("", "0")
+LIB_PATH = os.path.join(HERE, "libradtex_checked.so" if CHECKED else "libradtex.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "radtex.h")
 
 # rt_status
 RT_OK, RT_ERR_INVALID_ARG, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_BAD_OBJ_ID, RT_ERR_NONFINITE, RT_ERR_TIMEOUT, \
-    RT_ERR_UNSUPPORTED = range(8)
+    RT_ERR_UNSUPPORTED, RT_ERR_OUT_OF_BOUNDS = range(9)
 # rt_format
 RT_F32, RT_F16, RT_BF16, RT_E4M3_BUCKET_SCALE, RT_BIT1 = range(5)
 # rt_filter
@@ -105,6 +109,7 @@ SIGNATURES = {
     "rt_convert_layout": (_I32, [_P, _I32, _P, _I32, _I32, _I32, _I32, _P]),
     "rt_get_error": (_I32, [_P, _P, ctypes.POINTER(_I32)]),
     "rt_status_string": (ctypes.c_char_p, [_I32]),
+    "rt_checked_limit_extent": (_I32, [_P, _I32, _I64]),
 }
 
 _lock = threading.Lock()

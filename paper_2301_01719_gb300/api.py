@@ -14,7 +14,8 @@ import torch
 from . import _lib
 from ._lib import (RT_ACCUMULATE, RT_ACCUMULATE_TEXELS, RT_ANGULAR_BILINEAR, RT_BF16, RT_BIT1,  # noqa: F401
                    RT_BORROW, RT_DETERMINISTIC, RT_E4M3_BUCKET_SCALE, RT_ERR_BAD_OBJ_ID, RT_ERR_CUDA,
-                   RT_ERR_INVALID_ARG, RT_ERR_NONFINITE, RT_ERR_OOM, RT_ERR_TIMEOUT, RT_ERR_UNSUPPORTED, RT_F16, RT_F32,
+                   RT_ERR_INVALID_ARG, RT_ERR_NONFINITE, RT_ERR_OOM, RT_ERR_OUT_OF_BOUNDS, RT_ERR_TIMEOUT,
+                   RT_ERR_UNSUPPORTED, RT_F16, RT_F32,
                    RT_FIXED_POINT_GRADS, RT_LAYOUT_ATLAS, RT_LAYOUT_PALETTE, RT_LAYOUT_PLANES, RT_MAX_AO_DIRECTIONS,
                    RT_MAX_OBJECTS, RT_NEAREST, RT_OK, RT_QUADRILINEAR, RT_SURFACE_PLANE, RT_SURFACE_SPHERE, RT_WRAP_U,
                    RT_WRAP_V, RadtexError)
@@ -686,6 +687,12 @@ def rt_get_error(ctx: Context, stream=None) -> int:
     dev = torch.device("cuda", ctx.device)
     _lib.call("rt_get_error", ctx.handle, _stream(stream, dev), ctypes.byref(st))
     return st.value
+
+
+def rt_checked_limit_extent(ctx: Context, obj_id: int, texels: int) -> int:
+    """Checked build: lowers the extent the bounds checks allow for one object
+    (returns the status; RT_ERR_UNSUPPORTED from the normal build)."""
+    return _lib.lib().rt_checked_limit_extent(ctx.handle, int(obj_id), int(texels))
 
 
 def rt_status_string(status: int) -> str:

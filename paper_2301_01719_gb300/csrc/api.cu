@@ -144,6 +144,8 @@ const char* rt_status_string(rt_status s) {
             return "a bounded device wait gave up";
         case RT_ERR_UNSUPPORTED:
             return "unsupported combination of options";
+        case RT_ERR_OUT_OF_BOUNDS:
+            return "a computed texel address fell outside its object (checked build)";
     }
     return "unknown status";
 }
@@ -257,6 +259,10 @@ static rt_status create_object(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, int
     d.hi = 1.0f - 1.0f / (float)n;
     d.live = 1;
     d.wrap = (int8_t)(((flags & RT_WRAP_U) ? 1 : 0) | ((flags & RT_WRAP_V) ? 2 : 0));
+#ifdef RADTEX_CHECKED
+    d.extent = texels;
+    d.status = ctx->d_status;
+#endif
     void* storage_ptr = nullptr;
     float* scale_ptr = nullptr;
     uint32_t* index_ptr = nullptr;
@@ -971,6 +977,23 @@ rt_status rt_convert_layout(const float* src, rt_layout src_layout, float* dst, 
     return cuda_status(rt::launch_convert(src, src_layout, dst, dst_layout, w, h, n, (cudaStream_t)stream));
 }
 
+rt_status rt_checked_limit_extent(rt_ctx* ctx, int32_t obj_id, int64_t texels) {
+#ifdef RADTEX_CHECKED
+    if (!ctx || obj_id < 0 || obj_id >= ctx->n_obj || !ctx->table[obj_id].live) return RT_ERR_INVALID_ARG;
+    TexDesc& d = ctx->table[obj_id];
+    if (texels < 0 || texels > d.plane * d.n * d.n) return RT_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RT_ERR_CUDA;
+    d.extent = texels;
+    return upload_table(ctx);
+#else
+    (void)ctx;
+    (void)obj_id;
+    (void)texels;
+    return RT_ERR_UNSUPPORTED;
+#endif
+}
+
 rt_status rt_get_error(rt_ctx* ctx, rt_stream_t stream, rt_status* device_status) {
     if (!ctx || !device_status) return RT_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
@@ -981,7 +1004,8 @@ rt_status rt_get_error(rt_ctx* ctx, rt_stream_t stream, rt_status* device_status
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_status(e);
     unsigned bits = *ctx->h_status;
-    *device_status = (bits & rt::ST_BAD_OBJ)     ? RT_ERR_BAD_OBJ_ID
+    *device_status = (bits & rt::ST_BOUNDS)      ? RT_ERR_OUT_OF_BOUNDS
+                     : (bits & rt::ST_BAD_OBJ)   ? RT_ERR_BAD_OBJ_ID
                      : (bits & rt::ST_NONFINITE) ? RT_ERR_NONFINITE
                      : (bits & rt::ST_TIMEOUT)   ? RT_ERR_TIMEOUT
                      : (bits & rt::ST_BAD_ARG)   ? RT_ERR_INVALID_ARG

@@ -29,7 +29,7 @@ constexpr int kAThreads = 256;
 // Texel p = t n + s of bucket b (i = b mod w, j = b / w) of a dense texture.
 template <int FMT, int LAYOUT>
 __device__ __forceinline__ float4 bucket_texel(const TexDesc& d, int64_t b, int i, int j, int p, float sc) {
-    if (LAYOUT == RT_LAYOUT_PLANES) return load_texel<FMT>(d.base, (int64_t)p * d.plane + b, sc);
+    if (LAYOUT == RT_LAYOUT_PLANES) return load_texel<FMT>(d.base, checked_texel(d, (int64_t)p * d.plane + b), sc);
     return load_texel<FMT>(d.base, texel_index<RT_LAYOUT_ATLAS>(d, i, j, p % d.n, p / d.n), sc);
 }
 

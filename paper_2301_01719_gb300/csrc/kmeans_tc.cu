@@ -321,7 +321,7 @@ __global__ void convert_x_kernel(TexDesc d, int Bp, int Dp, __half* __restrict__
         if (b < B && p < planes) {
             const float sc = FMT == RT_E4M3_BUCKET_SCALE ? __ldg(d.scale + b) : 1.0f;
             if (LAYOUT == RT_LAYOUT_PLANES) {
-                v = load_texel<FMT>(d.base, (int64_t)p * d.plane + b, sc);
+                v = load_texel<FMT>(d.base, checked_texel(d, (int64_t)p * d.plane + b), sc);
             } else {
                 const int j = b / d.W, i = b - j * d.W;
                 v = load_texel<FMT>(d.base, texel_index<RT_LAYOUT_ATLAS>(d, i, j, p % d.n, p / d.n), sc);

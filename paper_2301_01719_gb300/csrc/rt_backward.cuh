@@ -38,8 +38,9 @@ __device__ __forceinline__ void red_add_fixed4(unsigned long long* addr, float4 
 // PLANES layout: planes pl[k] (k = (s0,t0) (s1,t0) (s0,t1) (s1,t1)), spatial
 // offsets o[b] (b = (u0,v0) (u1,v0) (u0,v1) (u1,v1)).
 template <bool DET>
-__device__ __forceinline__ void reduce_quadrilinear_taps(const Lookup<RT_QUADRILINEAR>& L, const int64_t (&pl)[4],
-                                                         const int (&o)[4], float4 g, void* grad) {
+__device__ __forceinline__ void reduce_quadrilinear_taps(const TexDesc& d, const Lookup<RT_QUADRILINEAR>& L,
+                                                         const int64_t (&pl)[4], const int (&o)[4], float4 g,
+                                                         void* grad) {
     const float wu[2] = {1.f - L.u.w, L.u.w}, wv[2] = {1.f - L.v.w, L.v.w};
     const float ws[2] = {1.f - L.s.w, L.s.w}, wt[2] = {1.f - L.t.w, L.t.w};
     if (DET) {
@@ -50,7 +51,7 @@ __device__ __forceinline__ void reduce_quadrilinear_taps(const Lookup<RT_QUADRIL
                 for (int k = 0; k < 4; ++k) {
                     const float w = wu[b & 1] * wv[b >> 1] * ws[k & 1] * wt[k >> 1];
                     if (w == 0.f) continue;
-                    const int64_t idx = pl[k] + o[b];
+                    const int64_t idx = checked_texel(d, pl[k] + o[b]);
                     red_add_fixed4(static_cast<unsigned long long*>(grad) + 4 * idx,
                                    make_float4(w * g.x, w * g.y, w * g.z, w * g.w));
                 }
@@ -71,7 +72,7 @@ __device__ __forceinline__ void reduce_quadrilinear_taps(const Lookup<RT_QUADRIL
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const float w = wu[b & 1] * wv[b >> 1] * ws[k & 1] * wt[k >> 1];
-                const int64_t idx = pl[k] + o[b];
+                const int64_t idx = checked_texel(d, pl[k] + o[b]);
                 float* addr = static_cast<float*>(grad) + 4 * idx;
                 // a lane with nothing to add gets a key no other lane has
                 const unsigned long long key =
@@ -104,7 +105,7 @@ __device__ __forceinline__ CoordGrad backward_quadrilinear_planes(const TexDesc&
     const int o[4] = {bucket_slot<LAYOUT>(d, L.u.k0, L.v.k0), bucket_slot<LAYOUT>(d, L.u.k1, L.v.k0),
                       bucket_slot<LAYOUT>(d, L.u.k0, L.v.k1),
                       bucket_slot<LAYOUT>(d, L.u.k1, L.v.k1)};  // (u0,v0) (u1,v0) (u0,v1) (u1,v1)
-    reduce_quadrilinear_taps<DET>(L, pl, o, g, grad);
+    reduce_quadrilinear_taps<DET>(d, L, pl, o, g, grad);
     CoordGrad cg = {0.f, 0.f, 0.f, 0.f};
     if (!coord_grads) return cg;
     const f32x2 g_rg = pack2(g.x, g.y), g_ba = pack2(g.z, g.w);
@@ -116,7 +117,7 @@ __device__ __forceinline__ CoordGrad backward_quadrilinear_planes(const TexDesc&
         float p[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const P4 T = load_texelP<FMT>(d.base, pl[k] + o[b], sc);
+            const P4 T = load_texelP<FMT>(d.base, checked_texel(d, pl[k] + o[b]), sc);
             f32x2 q;
             asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(q) : "l"(T.rg), "l"(g_rg));
             asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(q) : "l"(T.ba), "l"(g_ba), "l"(q));

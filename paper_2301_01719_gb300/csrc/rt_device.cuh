@@ -19,10 +19,12 @@
 
 namespace rt {
 
-enum : unsigned { ST_BAD_OBJ = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u, ST_BAD_ARG = 8u };
+enum : unsigned { ST_BAD_OBJ = 1u, ST_NONFINITE = 2u, ST_TIMEOUT = 4u, ST_BAD_ARG = 8u, ST_BOUNDS = 16u };
 
-// One object of the texture table (64 bytes).  Built on the host when the
-// texture is created; read by every kernel through the read-only path.
+// One object of the texture table (64 bytes; 80 in the checked build, which
+// adds the object's texel extent and the context's status word).  Built on the
+// host when the texture is created; read by every kernel through the
+// read-only path.
 struct __align__(16) TexDesc {
     const void* base;       // texel storage
     const float* scale;     // per-bucket scale (E4M3 only): h x w, or one per palette bucket
@@ -33,20 +35,59 @@ struct __align__(16) TexDesc {
     float fW, fH;           // w, h as float
     float half_n;           // n / 2
     float hi;               // clamp range of B: [-hi, hi], hi = 1 - 1/n
+#ifdef RADTEX_CHECKED
+    int64_t extent;         // texels a computed index may name: [0, extent)
+    unsigned* status;       // the context's sticky status word
+#endif
 };
+#ifdef RADTEX_CHECKED
+static_assert(sizeof(TexDesc) == 80, "TexDesc is 80 bytes in the checked build");
+#else
 static_assert(sizeof(TexDesc) == 64, "TexDesc is 64 bytes");
+#endif
 
 __device__ __forceinline__ TexDesc load_desc(const TexDesc* __restrict__ table, int o) {
     const int4* p = reinterpret_cast<const int4*>(table + o);
     int4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
+#ifdef RADTEX_CHECKED
+    int4 e = __ldg(p + 4);
+#endif
     TexDesc r;
     int4* q = reinterpret_cast<int4*>(&r);
     q[0] = a;
     q[1] = b;
     q[2] = c;
     q[3] = d;
+#ifdef RADTEX_CHECKED
+    q[4] = e;
+#endif
     return r;
 }
+
+// Bounds checks of the checked build (RADTEX_CHECKED): a texel index outside
+// [0, extent), a bucket outside the w x h matrix or a stored bucket outside
+// [0, plane) sets ST_BOUNDS in the context's status word and is replaced by 0,
+// so the access stays inside the object; nothing traps.  In the normal build
+// each check is the identity.
+__device__ __forceinline__ int64_t checked_texel(const TexDesc& d, int64_t idx) {
+#ifdef RADTEX_CHECKED
+    if (idx < 0 || idx >= d.extent) {
+        atomicOr(d.status, ST_BOUNDS);
+        return 0;
+    }
+#endif
+    return idx;
+}
+
+#ifdef RADTEX_CHECKED
+__device__ __forceinline__ int checked_slot(const TexDesc& d, int64_t slot, int64_t count) {
+    if (slot < 0 || slot >= count) {
+        atomicOr(d.status, ST_BOUNDS);
+        return 0;
+    }
+    return (int)slot;
+}
+#endif
 
 __device__ __forceinline__ bool finite3(float a, float b, float c) {
     return isfinite(a) && isfinite(b) && isfinite(c);
@@ -216,15 +257,21 @@ constexpr int kLayoutPalette = 2;
 // Spatial offset of bucket (i, j) inside a direction plane.
 template <int LAYOUT>
 __device__ __forceinline__ int bucket_slot(const TexDesc& d, int i, int j) {
+#ifdef RADTEX_CHECKED
+    const int b = checked_slot(d, (int64_t)j * d.W + i, (int64_t)d.W * d.H);
+    if (LAYOUT == kLayoutPalette) return checked_slot(d, __ldg(d.index + b), d.plane);
+#else
     const int b = j * d.W + i;
     if (LAYOUT == kLayoutPalette) return (int)__ldg(d.index + b);
+#endif
     return b;
 }
 
 template <int LAYOUT>
 __device__ __forceinline__ int64_t texel_index(const TexDesc& d, int i, int j, int s, int t) {
-    if (LAYOUT == RT_LAYOUT_ATLAS) return ((int64_t)j * d.n + t) * ((int64_t)d.W * d.n) + (int64_t)i * d.n + s;
-    return (int64_t)(t * d.n + s) * d.plane + bucket_slot<LAYOUT>(d, i, j);
+    if (LAYOUT == RT_LAYOUT_ATLAS)
+        return checked_texel(d, ((int64_t)j * d.n + t) * ((int64_t)d.W * d.n) + (int64_t)i * d.n + s);
+    return checked_texel(d, (int64_t)(t * d.n + s) * d.plane + bucket_slot<LAYOUT>(d, i, j));
 }
 
 template <int FMT>

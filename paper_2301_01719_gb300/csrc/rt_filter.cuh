@@ -56,7 +56,7 @@ __device__ __forceinline__ P4 quadrilinear_planes(const TexDesc& d, const Axis& 
 #pragma unroll
     for (int b = 0; b < 4; ++b)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) q[b][k] = load_texelP<FMT>(d.base, pl[k] + o[b], sc[b]);
+        for (int k = 0; k < 4; ++k) q[b][k] = load_texelP<FMT>(d.base, checked_texel(d, pl[k] + o[b]), sc[b]);
     const f32x2 ws = pack2(S.w, S.w), wt = pack2(T.w, T.w), wu = pack2(U.w, U.w), wv = pack2(V.w, V.w);
     P4 c[4];
 #pragma unroll

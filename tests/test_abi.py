@@ -23,6 +23,17 @@ def built_lib():
     return build.build()
 
 
+@pytest.fixture(scope="module")
+def built_checked_lib():
+    from paper_2301_01719_gb300 import build
+
+    try:
+        build.nvcc()
+    except RuntimeError:
+        pytest.skip("no CUDA toolkit")
+    return build.build(checked=True)
+
+
 def test_library_exports_every_header_symbol(built_lib):
     from paper_2301_01719_gb300 import _lib
 
@@ -35,12 +46,24 @@ def test_library_exports_every_header_symbol(built_lib):
     assert sorted(_lib.SIGNATURES) == names
 
 
+def test_checked_library_exports_the_same_symbols(built_checked_lib):
+    from paper_2301_01719_gb300 import _lib
+
+    assert os.path.basename(built_checked_lib) == "libradtex_checked.so"
+    L = ctypes.CDLL(built_checked_lib)
+    missing = [s for s in _lib.header_symbols() if not hasattr(L, s)]
+    assert not missing, missing
+    L.rt_status_string.restype = ctypes.c_char_p
+    L.rt_status_string.argtypes = [ctypes.c_int32]
+    assert L.rt_status_string(8) == b"a computed texel address fell outside its object (checked build)"
+
+
 def test_status_strings(built_lib):
     from paper_2301_01719_gb300 import _lib
 
     L = _lib.lib()
-    for s in range(8):
-        assert L.rt_status_string(s)
+    for s in range(9):
+        assert L.rt_status_string(s) != b"unknown status"
     assert L.rt_status_string(0) == b"ok"
 
 
