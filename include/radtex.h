@@ -524,10 +524,10 @@ rt_status rt_footprint(rt_ctx* ctx, const float* uv, const float* dir, const int
  * per-object offsets are computed on the device from the context's own
  * descriptor table (no host-to-device copy).  The G-buffer rules are
  * rt_footprint's.  The first call on a device (and again after the device's
- * context is reset) looks the arrays' device addresses up, a host-side set-up:
- * make that first call before any stream capture.  All calls share the arrays,
- * and each clears what it uses first, so calls whose work overlaps on the GPU
- * (other streams, other threads) race and must be ordered by the caller. */
+ * context is reset) looks the arrays' device addresses up on the host.  All
+ * calls share the arrays, and each clears what it uses first, so calls whose
+ * work overlaps on the GPU (other streams, other threads) race and must be
+ * ordered by the caller. */
 rt_status rt_footprint_noalloc(rt_ctx* ctx, const float* uv, const float* dir, const int32_t* obj, int64_t F,
                                rt_filter filter, uint64_t* counts_dev, int32_t n_counts, rt_stream_t stream);
 
