@@ -1,11 +1,10 @@
 """The bounds-checked build, libradtex_checked.so (compiled with RADTEX_CHECKED).
 
 A process loads one of the two libraries, chosen by RADTEX_CHECKED when the
-binding first loads it.  So the outer test runs a child pytest with
-RADTEX_CHECKED=1 on this file, the flat and batched parity suites (the fused
-step's among them) and the palette suite (index maps, k-means): there every
-case must pass against the checked build with no bounds error raised
-(conftest.py reads the status of every live context after each test).
+binding first loads it.  So the outer test runs the whole GPU suite again in a
+child pytest with RADTEX_CHECKED=1: there every case must pass against the
+checked build with no bounds error raised (conftest.py reads the status of
+every live context after each test), and the checked-only tests below run.
 
 The failure path is exercised without a bad address.  rt_checked_limit_extent
 lowers the extent the checks allow below the object's real size (here to the
@@ -31,8 +30,6 @@ pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-CHILD_FILES = ["test_gpu_checked.py", "test_gpu_parity.py", "test_gpu_batched.py", "test_gpu_fused.py",
-               "test_gpu_palette.py"]
 
 
 @pytest.fixture(scope="module")
@@ -56,8 +53,7 @@ def test_parity_suites_pass_on_the_checked_build():
 
     build.build(checked=True)
     env = dict(os.environ, RADTEX_CHECKED="1")
-    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-m", "gpu", "-p", "no:cacheprovider"] + \
-        [os.path.join(HERE, f) for f in CHILD_FILES]
+    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-m", "gpu", "-p", "no:cacheprovider", HERE]
     r = subprocess.run(cmd, env=env, cwd=ROOT, capture_output=True, text=True, timeout=1800)
     tail = r.stdout[-6000:] + "\n" + r.stderr[-3000:]
     assert r.returncode == 0, tail
