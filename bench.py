@@ -18,6 +18,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import tempfile
@@ -185,12 +186,21 @@ SHADING_SOURCES = ("backward.cu", "fused.cu", "launch.h", "rt_backward.cuh", "rt
                    "rt_internal.h", "shade.cu")
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without its comments and with whitespace collapsed: edits to
+    comments or layout do not change what the kernels compile to."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2301_01719_gb300", "csrc")
-    for f in SHADING_SOURCES:
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+    paths = [os.path.join(csrc, f) for f in SHADING_SOURCES] + [os.path.join(ROOT, "include", "radtex.h")]
+    for path in paths:
+        with open(path, encoding="utf-8") as fh:
+            h.update(os.path.basename(path).encode() + _code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -33,9 +33,18 @@
  *     RT_LAYOUT_ATLAS : the paper's texture, row-major (h n) x (w n) texels,
  *                       texel (i, j, s, t) at row j n + t, column i n + s.
  *     RT_LAYOUT_PLANES: n x n planes of w x h texels, texel (i, j, s, t) at
- *                       index ((t n + s) h + j) w + i.  Textures the library
- *                       owns are stored this way: fragments that are close on
- *                       screen read texels that are close in memory.
+ *                       index ((t n + s) h + j) w + i: fragments that are close
+ *                       on screen read texels that are close in memory.
+ *     RT_LAYOUT_QUADS : the planes of RT_LAYOUT_PLANES with each plane's
+ *                       buckets in 2 x 2 quads (w and h even): texel
+ *                       (i, j, s, t) at index (t n + s) w h + 4 q + 2 (j mod 2)
+ *                       + (i mod 2), quad q = (j / 2)(w / 2) + i / 2.  The
+ *                       2 x 2 buckets of a quadrilinear lookup at one in-bucket
+ *                       texel then lie in one quad more often, and a warp's taps
+ *                       and texel-gradient reductions in fewer cache lines.
+ *   Textures the library owns are stored in RT_LAYOUT_QUADS when w and h are
+ *   even and the format is not RT_BIT1, and in RT_LAYOUT_PLANES otherwise
+ *   (rt_texture_info reports which).
  */
 #ifndef RADTEX_H
 #define RADTEX_H
@@ -67,7 +76,8 @@ typedef enum {
     RT_BF16 = 2,             /* 8 bytes per texel, round to nearest even */
     RT_E4M3_BUCKET_SCALE = 3, /* 4 bytes per texel: OCP FP8 E4M3 codes of v / s, s = (bucket amax) / 448 */
     RT_BIT1 = 4               /* 1 bit per texel (shadow textures, Section 5): bit k of 32-bit word k >> 5 holds
-                                 texel k of the PLANES numbering; the value (0 or 1) fills every channel.
+                                 texel k of the PLANES numbering (always the storage layout of bit
+                                 textures); the value (0 or 1) fills every channel.
                                  Created from FP32 by channel 0 >= 1/2, or by rt_bake_shadow */
 } rt_format;
 
@@ -77,7 +87,8 @@ typedef enum {
     RT_QUADRILINEAR = 2      /* bilinear over u, v and over s, t: 16 taps */
 } rt_filter;
 
-typedef enum { RT_LAYOUT_ATLAS = 0, RT_LAYOUT_PLANES = 1 } rt_layout;
+typedef enum { RT_LAYOUT_ATLAS = 0, RT_LAYOUT_PLANES = 1, RT_LAYOUT_QUADS = 3 } rt_layout;
+/* (2 is reported by rt_texture_info for a palette texture) */
 
 /* rt_create_texture / rt_create_palette_texture flags */
 #define RT_BORROW 1          /* use the caller's FP32 buffer in place; no copy */
@@ -103,8 +114,10 @@ void rt_context_destroy(rt_ctx* ctx);
  * bucket matrix, stored as w n x h n texels).  1 <= w, h <= 65536, w h <= 2^30, 1 <= n <= 64.
  * src (device, FP32, 4 channels per texel, layout src_layout) gives the texel
  * values; NULL leaves an owned texture zero (fill it with rt_fill_bucket_lobes).
- * Without RT_BORROW the library allocates storage in RT_LAYOUT_PLANES and
- * encodes src into `storage` (E4M3: one FP32 scale per bucket, s = amax / 448,
+ * src_layout may be RT_LAYOUT_QUADS only when w and h are even.  Without
+ * RT_BORROW the library allocates storage (RT_LAYOUT_QUADS or RT_LAYOUT_PLANES,
+ * see the layouts above) and encodes src into `storage` (E4M3: one FP32 scale
+ * per bucket, s = amax / 448,
  * s = 1 for an all-zero bucket; codes = round-to-nearest-even-satfinite(v / s)).
  * With RT_BORROW, `storage` must be RT_F32 and src non-NULL: the library reads
  * src in place, in src_layout, for as long as the texture lives; the caller
@@ -121,15 +134,19 @@ rt_status rt_create_texture(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, rt_for
 rt_status rt_destroy_texture(rt_ctx* ctx, int32_t obj_id);
 
 /* Properties of an object (any output pointer may be NULL).  bytes = texel
- * storage plus scales (plus the index map of a palette texture); layout is
- * 2 for a palette texture (w, h are then its bucket matrix). */
+ * storage plus scales (plus the index map of a palette texture); layout is the
+ * storage layout (an rt_layout; that of the caller's buffer for a borrowed
+ * texture), or 2 for a palette texture (w, h are then its bucket matrix; its
+ * K x 1 palette is stored in RT_LAYOUT_PLANES).  Texel gradients
+ * (rt_shade_backward's dL_dtex) use the same layout. */
 rt_status rt_texture_info(rt_ctx* ctx, int32_t obj_id, int32_t* w, int32_t* h, int32_t* n, int32_t* storage,
                           int32_t* layout, int64_t* bytes);
 
 /* Copies the stored codes of an object into codes_dst (device; w n h n x 4
  * elements of the storage type: float, uint16 (FP16/BF16 bits) or uint8
- * (E4M3 codes)) in dst_layout, and for E4M3 the per-bucket scales into
- * scales_dst (device, h x w floats, may be NULL).  Used to check the encoders. */
+ * (E4M3 codes)) in dst_layout (RT_LAYOUT_QUADS only for even w and h), and for
+ * E4M3 the per-bucket scales into scales_dst (device, h x w floats in row-major
+ * bucket order, may be NULL).  Used to check the encoders. */
 rt_status rt_read_texture(rt_ctx* ctx, int32_t obj_id, rt_layout dst_layout, void* codes_dst, float* scales_dst,
                           rt_stream_t stream);
 
@@ -309,8 +326,10 @@ rt_status rt_locate(rt_ctx* ctx, const float* uv, const float* dir, const int32_
  *   dL_dtex: host array of n_dtex device pointers indexed by object id (the
  *            array itself may be NULL, and so may any entry): FP32 gradient of
  *            the object's decoded texel values, 4 channels per texel, in the
- *            object's storage layout (RT_LAYOUT_PLANES for owned textures, the
- *            borrowed buffer's layout otherwise).  Summed with vector atomics.
+ *            object's storage layout (rt_texture_info: RT_LAYOUT_QUADS for
+ *            owned textures with even w and h, RT_LAYOUT_PLANES for other owned
+ *            ones, the borrowed buffer's layout otherwise; rt_convert_layout
+ *            turns it into another).  Summed with vector atomics.
  *   dL_duv:  device F x 2 or NULL; dL_ddir: device F x 3 or NULL, through
  *            the filter weights, the Note's clamp, Eq. 3 and Eq. 1b.
  * Without RT_ACCUMULATE the per-fragment outputs are overwritten and each
@@ -550,7 +569,9 @@ rt_status rt_adam_step(float* param, const float* grad, float* m, float* v, int6
 
 
 /* Converts an FP32 4-channel texture buffer of w x h buckets of n x n texels
- * between layouts (device src and dst, which must not overlap). */
+ * between layouts (device src and dst, which must not overlap; RT_LAYOUT_QUADS
+ * only for even w and h): for instance a texel-gradient buffer of an owned
+ * texture into the atlas. */
 rt_status rt_convert_layout(const float* src, rt_layout src_layout, float* dst, rt_layout dst_layout, int32_t w,
                             int32_t h, int32_t n, rt_stream_t stream);
 

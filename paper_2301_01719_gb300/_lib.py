@@ -27,7 +27,7 @@ RT_F32, RT_F16, RT_BF16, RT_E4M3_BUCKET_SCALE, RT_BIT1 = range(5)
 # rt_filter
 RT_NEAREST, RT_ANGULAR_BILINEAR, RT_QUADRILINEAR = range(3)
 # rt_layout
-RT_LAYOUT_ATLAS, RT_LAYOUT_PLANES, RT_LAYOUT_PALETTE = range(3)  # PALETTE: reported by rt_texture_info
+RT_LAYOUT_ATLAS, RT_LAYOUT_PLANES, RT_LAYOUT_PALETTE, RT_LAYOUT_QUADS = range(4)  # PALETTE: reported by rt_texture_info
 RT_BORROW = 1
 RT_WRAP_U = 2
 RT_WRAP_V = 4

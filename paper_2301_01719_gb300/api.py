@@ -16,7 +16,8 @@ from ._lib import (RT_ACCUMULATE, RT_ACCUMULATE_TEXELS, RT_ANGULAR_BILINEAR, RT_
                    RT_BORROW, RT_DETERMINISTIC, RT_E4M3_BUCKET_SCALE, RT_ERR_BAD_OBJ_ID, RT_ERR_CUDA,
                    RT_ERR_INVALID_ARG, RT_ERR_NONFINITE, RT_ERR_OOM, RT_ERR_OUT_OF_BOUNDS, RT_ERR_TIMEOUT,
                    RT_ERR_UNSUPPORTED, RT_F16, RT_F32,
-                   RT_FIXED_POINT_GRADS, RT_LAYOUT_ATLAS, RT_LAYOUT_PALETTE, RT_LAYOUT_PLANES, RT_MAX_AO_DIRECTIONS,
+                   RT_FIXED_POINT_GRADS, RT_LAYOUT_ATLAS, RT_LAYOUT_PALETTE, RT_LAYOUT_PLANES, RT_LAYOUT_QUADS,
+                   RT_MAX_AO_DIRECTIONS,
                    RT_MAX_OBJECTS, RT_NEAREST, RT_OK, RT_QUADRILINEAR, RT_SURFACE_PLANE, RT_SURFACE_SPHERE, RT_WRAP_U,
                    RT_WRAP_V, RadtexError)
 
@@ -249,18 +250,29 @@ def rt_texture_info(ctx: Context, obj_id: int) -> dict:
     return {"w": w, "h": h, "n": n, "storage": storage, "layout": layout, "bytes": nbytes.value}
 
 
+def layout_shape(layout: int, w: int, h: int, n: int) -> tuple:
+    """Tensor shape of a 4-channel texture buffer: atlas (h n, w n, 4); planes
+    (n, n, h, w, 4); quads (n, n, h/2, w/2, 2, 2, 4), i.e. (t, s, j/2, i/2, j mod 2,
+    i mod 2, channel)."""
+    if layout == RT_LAYOUT_ATLAS:
+        return (h * n, w * n, 4)
+    if layout == RT_LAYOUT_QUADS:
+        return (n, n, h // 2, w // 2, 2, 2, 4)
+    return (n, n, h, w, 4)
+
+
 def rt_read_texture(ctx: Context, obj_id: int, dst_layout: int = RT_LAYOUT_ATLAS, stream=None):
     """Stored codes (and E4M3 scales) of an owned texture, as new CUDA tensors.
 
-    Atlas layout: codes shape (h n, w n, 4); planes: (n, n, h, w, 4).  Codes are
-    float32 (F32), int16 bit patterns (F16 / BF16) or uint8 (E4M3)."""
+    Codes are shaped by layout_shape(dst_layout, ...) and are float32 (F32),
+    int16 bit patterns (F16 / BF16) or uint8 (E4M3)."""
     info = rt_texture_info(ctx, obj_id)
     w, h, n, fmt = info["w"], info["h"], info["n"], info["storage"]
     K = rt_palette_size(ctx, obj_id)
     if K:  # a palette reads as its K x 1 texture
         w, h = K, 1
     dev = torch.device("cuda", ctx.device)
-    shape = (h * n, w * n, 4) if dst_layout == RT_LAYOUT_ATLAS else (n, n, h, w, 4)
+    shape = layout_shape(dst_layout, w, h, n)
     if fmt == RT_BIT1:  # one byte (0 or 1) per texel, no channels
         shape = shape[:-1]
     codes = torch.empty(shape, dtype=CODE_DTYPE[fmt], device=dev)
@@ -640,8 +652,7 @@ def rt_convert_layout(src: torch.Tensor, src_layout: int, dst_layout: int, w: in
     if src.numel() != w * h * n * n * 4:
         raise ValueError("src must hold w h n^2 x 4 floats")
     if dst is None:
-        shape = (h * n, w * n, 4) if dst_layout == RT_LAYOUT_ATLAS else (n, n, h, w, 4)
-        dst = torch.empty(shape, dtype=torch.float32, device=src.device)
+        dst = torch.empty(layout_shape(dst_layout, w, h, n), dtype=torch.float32, device=src.device)
     _check(dst, "dst", torch.float32)
     if dst.numel() != src.numel():
         raise ValueError("dst must hold as many floats as src")

@@ -98,7 +98,7 @@ int table_spec(const rt_ctx* ctx) {
     for (int o = 0; o < ctx->n_obj; ++o) {
         const TexDesc& d = ctx->table[o];
         if (!d.live) continue;
-        if (d.layout != RT_LAYOUT_PLANES || d.wrap || d.fmt == RT_BIT1) return -1;
+        if (d.layout != RT_LAYOUT_QUADS || d.wrap || d.fmt == RT_BIT1) return -1;
         if (spec == -2)
             spec = d.fmt;
         else if (spec != d.fmt)
@@ -214,6 +214,12 @@ void rt_context_destroy(rt_ctx* ctx) {
     delete ctx;
 }
 
+// Storage layout of an owned dense texture: 2 x 2 bucket quads when both sides
+// are even (bit textures keep the PLANES bit numbering).
+static rt_layout store_layout(int32_t w, int32_t h, rt_format storage) {
+    return (!(w & 1) && !(h & 1) && storage != RT_BIT1) ? RT_LAYOUT_QUADS : RT_LAYOUT_PLANES;
+}
+
 // Creates a dense texture (K = 0) or a palette texture (K palette buckets
 // stored as a K x 1 texture, plus a copy of the w x h index map).
 static rt_status create_object(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, int32_t K, rt_format storage,
@@ -223,9 +229,12 @@ static rt_status create_object(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, int
     if (w < 1 || h < 1 || n < 1 || w > 65536 || h > 65536 || n > 64) return RT_ERR_INVALID_ARG;
     if ((int64_t)w * h > ((int64_t)1 << 30)) return RT_ERR_INVALID_ARG;  // spatial offsets are 32-bit
     if (texel_bytes(storage) == 0) return RT_ERR_INVALID_ARG;
-    if (src_layout != RT_LAYOUT_ATLAS && src_layout != RT_LAYOUT_PLANES) return RT_ERR_INVALID_ARG;
+    if (src_layout != RT_LAYOUT_ATLAS && src_layout != RT_LAYOUT_PLANES && src_layout != RT_LAYOUT_QUADS)
+        return RT_ERR_INVALID_ARG;
     if (src && !aligned16(src)) return RT_ERR_INVALID_ARG;
     const bool palette = K > 0;
+    // a QUADS source is a w x h texture with even sides (a palette's K x 1 source never is)
+    if (src_layout == RT_LAYOUT_QUADS && (palette || (w & 1) || (h & 1))) return RT_ERR_INVALID_ARG;
     if (palette && (K > (1 << 30) || !index || !src)) return RT_ERR_INVALID_ARG;
     const bool borrow = (flags & RT_BORROW) != 0;
     if (borrow && (storage != RT_F32 || !src)) return RT_ERR_INVALID_ARG;
@@ -290,14 +299,15 @@ static rt_status create_object(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, int
         d.layout = (int8_t)(palette ? rt::kLayoutPalette : src_layout);
         ctx->bytes[o] = texels * 16;
     } else {
-        d.layout = (int8_t)(palette ? rt::kLayoutPalette : RT_LAYOUT_PLANES);
+        d.layout = (int8_t)(palette ? rt::kLayoutPalette : store_layout(w, h, storage));
         const int64_t bytes = storage_bytes(storage, texels);
         e = cudaMalloc(&storage_ptr, (size_t)bytes);
         if (e == cudaSuccess && storage == RT_E4M3_BUCKET_SCALE)
             e = cudaMalloc(&scale_ptr, sizeof(float) * (size_t)d.plane);
         if (e == cudaSuccess) {
             if (src) {
-                e = rt::launch_encode(src, src_layout, storage_ptr, scale_ptr, sw, sh, n, storage, 0);
+                e = rt::launch_encode(src, src_layout, storage_ptr, scale_ptr, sw, sh, n, storage,
+                                      palette ? RT_LAYOUT_PLANES : d.layout, 0);
             } else {
                 e = cudaMemset(storage_ptr, 0, (size_t)bytes);
                 if (e == cudaSuccess && scale_ptr) {
@@ -393,18 +403,18 @@ rt_status rt_read_texture(rt_ctx* ctx, int32_t obj_id, rt_layout dst_layout, voi
                           rt_stream_t stream) {
     if (!ctx || obj_id < 0 || obj_id >= RT_MAX_OBJECTS || !ctx->table[obj_id].live || !codes_dst)
         return RT_ERR_INVALID_ARG;
-    if (dst_layout != RT_LAYOUT_ATLAS && dst_layout != RT_LAYOUT_PLANES) return RT_ERR_INVALID_ARG;
+    if (dst_layout != RT_LAYOUT_ATLAS && dst_layout != RT_LAYOUT_PLANES && dst_layout != RT_LAYOUT_QUADS)
+        return RT_ERR_INVALID_ARG;
     const TexDesc& d = ctx->table[obj_id];
     if (d.layout == RT_LAYOUT_ATLAS) return RT_ERR_UNSUPPORTED;
+    const bool pal = d.layout == rt::kLayoutPalette;  // a palette reads as its K x 1 texture (PLANES)
+    const int rw = pal ? (int)d.plane : d.W, rh = pal ? 1 : d.H;
+    if (dst_layout == RT_LAYOUT_QUADS && ((rw & 1) || (rh & 1))) return RT_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return RT_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    const bool pal = d.layout == rt::kLayoutPalette;  // a palette reads as its K x 1 texture
-    cudaError_t e = rt::launch_read(d.base, d.fmt, pal ? (int)d.plane : d.W, pal ? 1 : d.H, d.n, dst_layout,
-                                    codes_dst, s);
-    if (e == cudaSuccess && scales_dst && d.scale)
-        e = cudaMemcpyAsync(scales_dst, d.scale, sizeof(float) * (size_t)d.plane, cudaMemcpyDeviceToDevice, s);
-    return cuda_status(e);
+    return cuda_status(rt::launch_read(d.base, pal ? RT_LAYOUT_PLANES : d.layout, d.scale, d.fmt, rw, rh, d.n,
+                                       dst_layout, codes_dst, scales_dst, s));
 }
 
 rt_status rt_fill_bucket_lobes(rt_ctx* ctx, int32_t obj_id, const float* params, rt_stream_t stream) {
@@ -414,7 +424,8 @@ rt_status rt_fill_bucket_lobes(rt_ctx* ctx, int32_t obj_id, const float* params,
     if (!ctx->owned[obj_id] || d.layout == rt::kLayoutPalette || d.fmt == RT_BIT1) return RT_ERR_UNSUPPORTED;
     DeviceGuard g(ctx->device);
     if (!g.ok) return RT_ERR_CUDA;
-    return cuda_status(rt::launch_fill_lobes(params, ctx->owned[obj_id], ctx->scales[obj_id], d.W, d.H, d.n, d.fmt,
+    return cuda_status(rt::launch_fill_lobes(params, ctx->owned[obj_id], ctx->scales[obj_id], d.layout, d.W, d.H, d.n,
+                                             d.fmt,
                                              (cudaStream_t)stream));
 }
 
@@ -456,7 +467,7 @@ static bool kmeans_source(rt_ctx* ctx, int32_t obj_id, int32_t K) {
     if (!ctx || obj_id < 0 || obj_id >= RT_MAX_OBJECTS || !ctx->table[obj_id].live) return false;
     const TexDesc& d = ctx->table[obj_id];
     return K >= 1 && K <= (1 << 24) && d.fmt != RT_BIT1 &&
-           (d.layout == RT_LAYOUT_PLANES || d.layout == RT_LAYOUT_ATLAS);
+           (d.layout == RT_LAYOUT_PLANES || d.layout == RT_LAYOUT_QUADS || d.layout == RT_LAYOUT_ATLAS);
 }
 
 rt_status rt_kmeans_init(rt_ctx* ctx, int32_t obj_id, int32_t K, const int32_t* buckets, float* centroids,
@@ -971,8 +982,10 @@ rt_status rt_footprint(rt_ctx* ctx, const float* uv, const float* dir, const int
 rt_status rt_convert_layout(const float* src, rt_layout src_layout, float* dst, rt_layout dst_layout, int32_t w,
                             int32_t h, int32_t n, rt_stream_t stream) {
     if (!src || !dst || !aligned16(src) || !aligned16(dst) || w < 1 || h < 1 || n < 1) return RT_ERR_INVALID_ARG;
-    if ((src_layout != RT_LAYOUT_ATLAS && src_layout != RT_LAYOUT_PLANES) ||
-        (dst_layout != RT_LAYOUT_ATLAS && dst_layout != RT_LAYOUT_PLANES))
+    auto ok = [&](rt_layout l) {
+        return l == RT_LAYOUT_ATLAS || l == RT_LAYOUT_PLANES || (l == RT_LAYOUT_QUADS && !(w & 1) && !(h & 1));
+    };
+    if (!ok(src_layout) || !ok(dst_layout))
         return RT_ERR_INVALID_ARG;
     return cuda_status(rt::launch_convert(src, src_layout, dst, dst_layout, w, h, n, (cudaStream_t)stream));
 }

@@ -2,8 +2,8 @@
 // (Section 2.2, Eq. 4a and Eq. 4b).
 //
 // One thread per bucket.  A block covers 128 consecutive buckets (bucket
-// b = j w + i), so at every in-bucket texel (s, t) its stores are 128
-// consecutive texels of one PLANES plane: coalesced.  The grid's y dimension
+// b = j w + i), so at every in-bucket texel (s, t) its stores fall in one
+// direction plane: consecutive texels (PLANES) or pairs of them (QUADS).  The grid's y dimension
 // splits the n^2 planes of a bucket among blocks when there are too few
 // buckets to fill the GPU; FP8 E4M3 keeps a bucket in one thread, which
 // evaluates the bucket twice (its amax sets the bucket's scale, then the
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kBakeThreads) bake_kernel(rt_bake_scene S, int
         float amax = 0.0f;
         for (int p = 0; p < planes; ++p) amax = fmaxf(amax, amax4(bake_texel(S, r, Rtab[p], dirs, K)));
         sc = bucket_scale(amax);
-        scale[b] = sc;
+        scale[slot_in(LAYOUT, W, i, j)] = sc;
     }
     for (int p = p0; p < p1; ++p) {
         const int t = p / n, s = p - t * n;
@@ -296,23 +296,30 @@ static cudaError_t launch_bake_t(const rt_bake_scene& S, int surface, void* dst,
     return cudaGetLastError();
 }
 
+template <int LAYOUT>
+static cudaError_t launch_bake_l(const rt_bake_scene& S, int surface, void* dst, float* scale, int W, int H, int n,
+                                 int fmt, const float* ao_dirs, int K, cudaStream_t stream) {
+    switch (fmt) {
+        case RT_F32:
+            return launch_bake_t<RT_F32, LAYOUT>(S, surface, dst, scale, W, H, n, ao_dirs, K, stream);
+        case RT_F16:
+            return launch_bake_t<RT_F16, LAYOUT>(S, surface, dst, scale, W, H, n, ao_dirs, K, stream);
+        case RT_BF16:
+            return launch_bake_t<RT_BF16, LAYOUT>(S, surface, dst, scale, W, H, n, ao_dirs, K, stream);
+        default:
+            return launch_bake_t<RT_E4M3_BUCKET_SCALE, LAYOUT>(S, surface, dst, scale, W, H, n, ao_dirs, K, stream);
+    }
+}
+
 cudaError_t launch_bake(const rt_bake_scene& S, int surface, void* dst, float* scale, int W, int H, int n, int fmt,
                         int layout, const float* ao_dirs, int K, cudaStream_t stream) {
     if (layout == RT_LAYOUT_ATLAS) {
         if (fmt != RT_F32) return cudaErrorInvalidValue;
         return launch_bake_t<RT_F32, RT_LAYOUT_ATLAS>(S, surface, dst, scale, W, H, n, ao_dirs, K, stream);
     }
-    switch (fmt) {
-        case RT_F32:
-            return launch_bake_t<RT_F32, RT_LAYOUT_PLANES>(S, surface, dst, scale, W, H, n, ao_dirs, K, stream);
-        case RT_F16:
-            return launch_bake_t<RT_F16, RT_LAYOUT_PLANES>(S, surface, dst, scale, W, H, n, ao_dirs, K, stream);
-        case RT_BF16:
-            return launch_bake_t<RT_BF16, RT_LAYOUT_PLANES>(S, surface, dst, scale, W, H, n, ao_dirs, K, stream);
-        default:
-            return launch_bake_t<RT_E4M3_BUCKET_SCALE, RT_LAYOUT_PLANES>(S, surface, dst, scale, W, H, n, ao_dirs, K,
-                                                                         stream);
-    }
+    if (layout == RT_LAYOUT_QUADS) return launch_bake_l<RT_LAYOUT_QUADS>(S, surface, dst, scale, W, H, n, fmt, ao_dirs,
+                                                                         K, stream);
+    return launch_bake_l<RT_LAYOUT_PLANES>(S, surface, dst, scale, W, H, n, fmt, ao_dirs, K, stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -6,20 +6,21 @@
 // direction gradients of the backward for that dL/dout.  The G-buffer and the
 // target are read once, the lookup coordinates are computed once, and the
 // backward's reloads of the taps just gathered for the colour are L1 hits.
-// On the 60-pose 1080p step the fused kernel takes 6.4 ms where the forward
-// and the backward take 1.73 + 5.15 ms.
+// On the 60-pose 1080p step the fused kernel takes 5.15 ms where the forward
+// and the backward take 1.74 + 4.85 ms.
 #include "launch.h"
 #include "rt_backward.cuh"
 #include "rt_internal.h"
 
 namespace rt {
 
-// Held to 128 registers (4 blocks, 16 warps per SM; it compiles to 102 without
-// spills): at 5 blocks (96 registers) the step took 5.86 ms against 5.65 ms, at
-// 6 blocks (80, spilling) 6.21 ms, on the 60-pose 1080p step.  A variant
-// that gathers the 16 taps once (the colour-derivative vectors formed from the
-// forward's lerps and projected on dL/dout) needs far more registers and
-// measured slower at every occupancy (7.0 ms at best against 6.4 ms).
+// Held to 128 registers (4 blocks, 16 warps per SM; it compiles to 104 without
+// spills): at 5 blocks (96 registers) the kernel took 5.86 ms against 5.65 ms,
+// at 6 blocks (80, spilling) 6.21 ms, on the 60-pose 1080p step (textures in
+// row-major planes then).  A variant that gathers the 16 taps once (the
+// colour-derivative vectors formed from the forward's lerps and projected on
+// dL/dout) needs far more registers and measured slower at every occupancy
+// (7.0 ms at best against 6.4 ms then).
 template <int FILTER, bool DET, int SPEC>
 __global__ void __launch_bounds__(kBackThreads, (!DET && SPEC >= 0) ? 4 : 1) fused_l2_kernel(
     const TexDesc* __restrict__ table, int n_obj, const float* __restrict__ uv, const float* __restrict__ dir,

@@ -26,11 +26,18 @@ constexpr int kAN = 64;   // centroids per sweep step
 constexpr int kAP = 4;    // texels per shared-memory stage
 constexpr int kAThreads = 256;
 
-// Texel p = t n + s of bucket b (i = b mod w, j = b / w) of a dense texture.
+// Texel p = t n + s of bucket (i, j) of a dense texture (ATLAS, PLANES or QUADS).
 template <int FMT, int LAYOUT>
-__device__ __forceinline__ float4 bucket_texel(const TexDesc& d, int64_t b, int i, int j, int p, float sc) {
-    if (LAYOUT == RT_LAYOUT_PLANES) return load_texel<FMT>(d.base, checked_texel(d, (int64_t)p * d.plane + b), sc);
-    return load_texel<FMT>(d.base, texel_index<RT_LAYOUT_ATLAS>(d, i, j, p % d.n, p / d.n), sc);
+__device__ __forceinline__ float4 bucket_texel(const TexDesc& d, int i, int j, int p, float sc) {
+    if (LAYOUT == RT_LAYOUT_ATLAS)
+        return load_texel<FMT>(d.base, texel_index<RT_LAYOUT_ATLAS>(d, i, j, p % d.n, p / d.n), sc);
+    return load_texel<FMT>(d.base, checked_texel(d, (int64_t)p * d.plane + bucket_slot<LAYOUT>(d, i, j)), sc);
+}
+
+// The E4M3 scale of bucket (i, j) (1 for the other formats).
+template <int FMT, int LAYOUT>
+__device__ __forceinline__ float bucket_scale_of(const TexDesc& d, int i, int j) {
+    return FMT == RT_E4M3_BUCKET_SCALE ? __ldg(d.scale + bucket_slot<LAYOUT>(d, i, j)) : 1.0f;
 }
 
 __device__ __forceinline__ float dot4f(float4 a, float4 b) {
@@ -58,7 +65,7 @@ __global__ void __launch_bounds__(kAThreads, 2) kmeans_assign_kernel(TexDesc d, 
     if (bvalid) {
         bj = (int)(bb / d.W);
         bi = (int)(bb - (int64_t)bj * d.W);
-        if (FMT == RT_E4M3_BUCKET_SCALE) sc = __ldg(d.scale + bb);
+        sc = bucket_scale_of<FMT, LAYOUT>(d, bi, bj);
     }
     // loader role for C: stage cq, centroid ck of the sweep step
     const int cq = tid >> 6, ck = tid & (kAN - 1);
@@ -83,7 +90,7 @@ __global__ void __launch_bounds__(kAThreads, 2) kmeans_assign_kernel(TexDesc d, 
             for (int q = tid >> 7; q < kAP; q += 2) {
                 const int p = p0 + q;
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (bvalid && p < planes) v = bucket_texel<FMT, LAYOUT>(d, bb, bi, bj, p, sc);
+                if (bvalid && p < planes) v = bucket_texel<FMT, LAYOUT>(d, bi, bj, p, sc);
                 Xs[q][lb] = v;
             }
             {
@@ -166,8 +173,7 @@ __global__ void kmeans_init_kernel(TexDesc d, int K, const int32_t* __restrict__
         b = b < 0 ? 0 : B - 1;
     }
     const int j = (int)(b / d.W), i = (int)(b - (int64_t)j * d.W);
-    const float sc = FMT == RT_E4M3_BUCKET_SCALE ? __ldg(d.scale + b) : 1.0f;
-    C[(int64_t)p * K + k] = bucket_texel<FMT, LAYOUT>(d, b, i, j, p, sc);
+    C[(int64_t)p * K + k] = bucket_texel<FMT, LAYOUT>(d, i, j, p, bucket_scale_of<FMT, LAYOUT>(d, i, j));
 }
 
 __global__ void kmeans_count_kernel(const uint32_t* __restrict__ index, int64_t B, int K, uint32_t* counts,
@@ -231,8 +237,7 @@ __global__ void __launch_bounds__(256) kmeans_mean_kernel(TexDesc d, int K, cons
         for (uint32_t m = m0; m < m1; ++m) {
             const int64_t b = members[m];
             const int j = (int)(b / d.W), i = (int)(b - (int64_t)j * d.W);
-            const float sc = FMT == RT_E4M3_BUCKET_SCALE ? __ldg(d.scale + b) : 1.0f;
-            const float4 v = bucket_texel<FMT, LAYOUT>(d, b, i, j, p, sc);
+            const float4 v = bucket_texel<FMT, LAYOUT>(d, i, j, p, bucket_scale_of<FMT, LAYOUT>(d, i, j));
             sx += v.x;
             sy += v.y;
             sz += v.z;
@@ -244,21 +249,27 @@ __global__ void __launch_bounds__(256) kmeans_mean_kernel(TexDesc d, int K, cons
 
 static unsigned blocks(int64_t items, int threads) { return (unsigned)((items + threads - 1) / threads); }
 
+template <template <int, int> class Launch, int LAYOUT, typename... Args>
+static cudaError_t dispatch_format(const TexDesc& d, Args... args) {
+    switch (d.fmt) {
+        case RT_F16:
+            return Launch<RT_F16, LAYOUT>::run(d, args...);
+        case RT_BF16:
+            return Launch<RT_BF16, LAYOUT>::run(d, args...);
+        case RT_E4M3_BUCKET_SCALE:
+            return Launch<RT_E4M3_BUCKET_SCALE, LAYOUT>::run(d, args...);
+        default:
+            return Launch<RT_F32, LAYOUT>::run(d, args...);
+    }
+}
+
 // Calls Launch<FMT, LAYOUT>::run(args...) for the texture's format and layout (dense textures only).
 template <template <int, int> class Launch, typename... Args>
 static cudaError_t dispatch_dense(const TexDesc& d, Args... args) {
     if (d.layout == RT_LAYOUT_ATLAS) return Launch<RT_F32, RT_LAYOUT_ATLAS>::run(d, args...);
+    if (d.layout == RT_LAYOUT_QUADS) return dispatch_format<Launch, RT_LAYOUT_QUADS>(d, args...);
     if (d.layout != RT_LAYOUT_PLANES) return cudaErrorInvalidValue;
-    switch (d.fmt) {
-        case RT_F16:
-            return Launch<RT_F16, RT_LAYOUT_PLANES>::run(d, args...);
-        case RT_BF16:
-            return Launch<RT_BF16, RT_LAYOUT_PLANES>::run(d, args...);
-        case RT_E4M3_BUCKET_SCALE:
-            return Launch<RT_E4M3_BUCKET_SCALE, RT_LAYOUT_PLANES>::run(d, args...);
-        default:
-            return Launch<RT_F32, RT_LAYOUT_PLANES>::run(d, args...);
-    }
+    return dispatch_format<Launch, RT_LAYOUT_PLANES>(d, args...);
 }
 
 template <int FMT, int LAYOUT>

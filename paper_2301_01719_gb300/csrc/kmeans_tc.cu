@@ -319,12 +319,12 @@ __global__ void convert_x_kernel(TexDesc d, int Bp, int Dp, __half* __restrict__
         const int b = b0 + threadIdx.x, p = p0 + threadIdx.y;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (b < B && p < planes) {
-            const float sc = FMT == RT_E4M3_BUCKET_SCALE ? __ldg(d.scale + b) : 1.0f;
-            if (LAYOUT == RT_LAYOUT_PLANES) {
-                v = load_texel<FMT>(d.base, checked_texel(d, (int64_t)p * d.plane + b), sc);
+            const int j = b / d.W, i = b - j * d.W;
+            if (LAYOUT != RT_LAYOUT_ATLAS) {
+                const float sc = FMT == RT_E4M3_BUCKET_SCALE ? __ldg(d.scale + bucket_slot<LAYOUT>(d, i, j)) : 1.0f;
+                v = load_texel<FMT>(d.base, checked_texel(d, (int64_t)p * d.plane + bucket_slot<LAYOUT>(d, i, j)), sc);
             } else {
-                const int j = b / d.W, i = b - j * d.W;
-                v = load_texel<FMT>(d.base, texel_index<RT_LAYOUT_ATLAS>(d, i, j, p % d.n, p / d.n), sc);
+                v = load_texel<FMT>(d.base, texel_index<RT_LAYOUT_ATLAS>(d, i, j, p % d.n, p / d.n), 1.0f);
             }
         }
         const __half2 lo = __floats2half2_rn(v.x, v.y), hi = __floats2half2_rn(v.z, v.w);
@@ -427,6 +427,20 @@ static cudaError_t convert_x(const TexDesc& d, const Layout& L, __half* X, cudaS
     return cudaGetLastError();
 }
 
+template <int LAYOUT>
+static cudaError_t convert_x_fmt(const TexDesc& d, const Layout& L, __half* X, cudaStream_t stream) {
+    switch (d.fmt) {
+        case RT_F16:
+            return convert_x<RT_F16, LAYOUT>(d, L, X, stream);
+        case RT_BF16:
+            return convert_x<RT_BF16, LAYOUT>(d, L, X, stream);
+        case RT_E4M3_BUCKET_SCALE:
+            return convert_x<RT_E4M3_BUCKET_SCALE, LAYOUT>(d, L, X, stream);
+        default:
+            return convert_x<RT_F32, LAYOUT>(d, L, X, stream);
+    }
+}
+
 }  // namespace tc
 
 int64_t kmeans_tc_scratch_bytes(int W, int H, int n, int K) { return (int64_t)tc::layout(W, H, n, K).bytes; }
@@ -441,23 +455,12 @@ cudaError_t launch_kmeans_assign_tc(const TexDesc& d, int K, const float* C, uin
     float* cn = reinterpret_cast<float*>(base + L.cn_off);
     float* xn = reinterpret_cast<float*>(base + L.xn_off);
     cudaError_t e;
-    if (d.layout == RT_LAYOUT_ATLAS) {
+    if (d.layout == RT_LAYOUT_ATLAS)
         e = convert_x<RT_F32, RT_LAYOUT_ATLAS>(d, L, X, stream);
-    } else {
-        switch (d.fmt) {
-            case RT_F16:
-                e = convert_x<RT_F16, RT_LAYOUT_PLANES>(d, L, X, stream);
-                break;
-            case RT_BF16:
-                e = convert_x<RT_BF16, RT_LAYOUT_PLANES>(d, L, X, stream);
-                break;
-            case RT_E4M3_BUCKET_SCALE:
-                e = convert_x<RT_E4M3_BUCKET_SCALE, RT_LAYOUT_PLANES>(d, L, X, stream);
-                break;
-            default:
-                e = convert_x<RT_F32, RT_LAYOUT_PLANES>(d, L, X, stream);
-        }
-    }
+    else if (d.layout == RT_LAYOUT_QUADS)
+        e = convert_x_fmt<RT_LAYOUT_QUADS>(d, L, X, stream);
+    else
+        e = convert_x_fmt<RT_LAYOUT_PLANES>(d, L, X, stream);
     if (e != cudaSuccess) return e;
     const int64_t ce = L.Kp * (L.Dp / 4);
     convert_c_kernel<<<(unsigned)((ce + 255) / 256), 256, 0, stream>>>(reinterpret_cast<const float4*>(C), K,

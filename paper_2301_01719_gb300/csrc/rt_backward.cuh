@@ -31,11 +31,11 @@ __device__ __forceinline__ void red_add_fixed4(unsigned long long* addr, float4 
     atomicAdd(addr + 3, (unsigned long long)__float2ll_rn(v.w * kFixedScale));
 }
 
-// QUADRILINEAR on the PLANES layout: the four in-bucket texels select four
+// QUADRILINEAR on the PLANES / QUADS layouts: the four in-bucket texels select four
 // planes (64-bit bases), the four buckets four spatial offsets (32-bit), shared
 // by the 16 reductions and the 16 loads.
 // The 16 texel-gradient contributions w_tap g of a quadrilinear lookup on the
-// PLANES layout: planes pl[k] (k = (s0,t0) (s1,t0) (s0,t1) (s1,t1)), spatial
+// PLANES / QUADS layouts: planes pl[k] (k = (s0,t0) (s1,t0) (s0,t1) (s1,t1)), spatial
 // offsets o[b] (b = (u0,v0) (u1,v0) (u0,v1) (u1,v1)).
 template <bool DET>
 __device__ __forceinline__ void reduce_quadrilinear_taps(const TexDesc& d, const Lookup<RT_QUADRILINEAR>& L,
@@ -212,31 +212,34 @@ __device__ __forceinline__ CoordGrad backward_layout(const TexDesc& d, const Loo
         return backward_taps<FILTER, FMT, LAYOUT, DET>(d, L, g, grad, coord_grads);
 }
 
+template <int FILTER, int FMT, bool DET>
+__device__ __forceinline__ CoordGrad backward_dense(const TexDesc& d, const Lookup<FILTER>& L, float4 g, void* grad,
+                                                    bool coord_grads) {
+    if (d.layout == kLayoutPalette) return backward_layout<FILTER, FMT, kLayoutPalette, DET>(d, L, g, grad, coord_grads);
+    if (FMT != RT_BIT1 && d.layout == RT_LAYOUT_QUADS)
+        return backward_layout<FILTER, FMT, RT_LAYOUT_QUADS, DET>(d, L, g, grad, coord_grads);
+    return backward_layout<FILTER, FMT, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
+}
+
 template <int FILTER, bool DET>
 __device__ __forceinline__ CoordGrad backward_any(const TexDesc& d, const Lookup<FILTER>& L, float4 g, void* grad,
                                                   bool coord_grads) {
-    const bool pal = d.layout == kLayoutPalette;
     switch (d.fmt) {
         case RT_F16:
-            return pal ? backward_layout<FILTER, RT_F16, kLayoutPalette, DET>(d, L, g, grad, coord_grads)
-                       : backward_layout<FILTER, RT_F16, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
+            return backward_dense<FILTER, RT_F16, DET>(d, L, g, grad, coord_grads);
         case RT_BF16:
-            return pal ? backward_layout<FILTER, RT_BF16, kLayoutPalette, DET>(d, L, g, grad, coord_grads)
-                       : backward_layout<FILTER, RT_BF16, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
+            return backward_dense<FILTER, RT_BF16, DET>(d, L, g, grad, coord_grads);
         case RT_BIT1:  // no texel gradients (rejected on the host); coordinate gradients only
-            return pal ? backward_layout<FILTER, RT_BIT1, kLayoutPalette, DET>(d, L, g, nullptr, coord_grads)
-                       : backward_layout<FILTER, RT_BIT1, RT_LAYOUT_PLANES, DET>(d, L, g, nullptr, coord_grads);
+            return backward_dense<FILTER, RT_BIT1, DET>(d, L, g, nullptr, coord_grads);
         case RT_E4M3_BUCKET_SCALE:
-            return pal ? backward_layout<FILTER, RT_E4M3_BUCKET_SCALE, kLayoutPalette, DET>(d, L, g, grad, coord_grads)
-                       : backward_layout<FILTER, RT_E4M3_BUCKET_SCALE, RT_LAYOUT_PLANES, DET>(d, L, g, grad,
-                                                                                              coord_grads);
+            return backward_dense<FILTER, RT_E4M3_BUCKET_SCALE, DET>(d, L, g, grad, coord_grads);
         default:
             if (d.layout == RT_LAYOUT_ATLAS)
                 return backward_layout<FILTER, RT_F32, RT_LAYOUT_ATLAS, DET>(d, L, g, grad, coord_grads);
-            return pal ? backward_layout<FILTER, RT_F32, kLayoutPalette, DET>(d, L, g, grad, coord_grads)
-                       : backward_layout<FILTER, RT_F32, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
+            return backward_dense<FILTER, RT_F32, DET>(d, L, g, grad, coord_grads);
     }
 }
+
 
 // dL/dI from dL/dB through Eq. 3 and Eq. 1b.
 //  Eq. 3 (x branch, |A_x| >= |A_y|, q = A_y / A_x = I_y / I_x):
@@ -244,7 +247,9 @@ __device__ __forceinline__ CoordGrad backward_any(const TexDesc& d, const Lookup
 //  and symmetrically on the y branch; the identity at A = 0.
 //  Eq. 1b: dA_r/dI_c = sqrt(2) (delta_rc / D - I_r g_c / D^3), g = (I_x, I_y, I_z + 1), D = |g|.
 //  The same holds for any half-way vector h in place of g (Eq. 1a: h = I + N,
-//  and dA/dI = dA/dN = dA/dh).
+//  and dA/dI = dA/dN = dA/dh).  Every product and sum is an explicit rounded
+//  multiply or fused multiply-add, so that every kernel that inlines this
+//  (the backward, the fused step) rounds it the same way.
 __device__ __forceinline__ float3 half_grad(float Ix, float Iy, float zp, float gBx, float gBy) {
     float ax = fabsf(Ix), ay = fabsf(Iy);
     float gAx, gAy;
@@ -254,21 +259,21 @@ __device__ __forceinline__ float3 half_grad(float Ix, float Iy, float zp, float 
     } else if (ax >= ay) {
         float q = Iy / Ix;
         float r = 1.0f / sqrtf(fmaf(q, q, 1.0f));
-        gAx = (gBx - gBy * q * q * q) * r;
-        gAy = (gBx * q + gBy * fmaf(2.0f * q, q, 1.0f)) * r;
+        gAx = __fmul_rn(fmaf(-gBy, __fmul_rn(__fmul_rn(q, q), q), gBx), r);
+        gAy = __fmul_rn(fmaf(gBx, q, __fmul_rn(gBy, fmaf(2.0f * q, q, 1.0f))), r);
     } else {
         float p = Ix / Iy;
         float r = 1.0f / sqrtf(fmaf(p, p, 1.0f));
-        gAy = (gBy - gBx * p * p * p) * r;
-        gAx = (gBy * p + gBx * fmaf(2.0f * p, p, 1.0f)) * r;
+        gAy = __fmul_rn(fmaf(-gBx, __fmul_rn(__fmul_rn(p, p), p), gBy), r);
+        gAx = __fmul_rn(fmaf(gBy, p, __fmul_rn(gBx, fmaf(2.0f * p, p, 1.0f))), r);
     }
-    float D2 = Ix * Ix + Iy * Iy + zp * zp;
+    float D2 = fmaf(Ix, Ix, fmaf(Iy, Iy, __fmul_rn(zp, zp)));
     if (!(D2 > 1e-30f)) return make_float3(0.f, 0.f, 0.f);
     float invD = 1.0f / sqrtf(D2);
-    float k = 1.41421356237f * invD;
-    float k3 = k * invD * invD;
-    float m = k3 * (gAx * Ix + gAy * Iy);
-    return make_float3(k * gAx - m * Ix, k * gAy - m * Iy, -m * zp);
+    float k = __fmul_rn(1.41421356237f, invD);
+    float k3 = __fmul_rn(__fmul_rn(k, invD), invD);
+    float m = __fmul_rn(k3, fmaf(gAx, Ix, __fmul_rn(gAy, Iy)));
+    return make_float3(fmaf(-m, Ix, __fmul_rn(k, gAx)), fmaf(-m, Iy, __fmul_rn(k, gAy)), __fmul_rn(-m, zp));
 }
 
 __device__ __forceinline__ float3 direction_grad(float Ix, float Iy, float Iz, float gBx, float gBy) {
@@ -291,7 +296,7 @@ __device__ __forceinline__ CoordGrad backward_spec(const TexDesc& d, const Looku
     if constexpr (SPEC < 0)
         return backward_any<FILTER, DET>(d, L, g, grad, coord_grads);
     else
-        return backward_layout<FILTER, SPEC, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
+        return backward_layout<FILTER, SPEC, RT_LAYOUT_QUADS, DET>(d, L, g, grad, coord_grads);
 }
 
 // UV and direction gradients of one fragment from its weight-coordinate

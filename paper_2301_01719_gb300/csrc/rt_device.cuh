@@ -254,13 +254,23 @@ __device__ __forceinline__ Lookup<FILTER> locate_world(const TexDesc& d, float u
 // (plane = K) reached through the index map, bucket (i, j) -> index[j w + i].
 constexpr int kLayoutPalette = 2;
 
+// Offset of bucket (i, j) in its 2 x 2 quad order (RT_LAYOUT_QUADS, w and h even).
+__device__ __forceinline__ int quad_slot(int W, int i, int j) {
+    return (((j >> 1) * (W >> 1) + (i >> 1)) << 2) + ((j & 1) << 1) + (i & 1);
+}
+
 // Spatial offset of bucket (i, j) inside a direction plane.
 template <int LAYOUT>
 __device__ __forceinline__ int bucket_slot(const TexDesc& d, int i, int j) {
 #ifdef RADTEX_CHECKED
     const int b = checked_slot(d, (int64_t)j * d.W + i, (int64_t)d.W * d.H);
     if (LAYOUT == kLayoutPalette) return checked_slot(d, __ldg(d.index + b), d.plane);
+    if (LAYOUT == RT_LAYOUT_QUADS) {
+        const int jb = b / d.W;
+        return quad_slot(d.W, b - jb * d.W, jb);
+    }
 #else
+    if (LAYOUT == RT_LAYOUT_QUADS) return quad_slot(d.W, i, j);
     const int b = j * d.W + i;
     if (LAYOUT == kLayoutPalette) return (int)__ldg(d.index + b);
 #endif

@@ -24,9 +24,9 @@ __device__ __forceinline__ void load_quad(const TexDesc& d, int i, int j, const 
     t11 = load_texel<FMT>(d.base, texel_index<LAYOUT>(d, i, j, s.k1, t.k1), sc);
 }
 
-// Addresses of the taps.  PLANES: the four in-bucket texels (s0|s1, t0|t1)
-// select four planes (64-bit base indices), the (up to) four buckets select
-// spatial offsets j w + i inside a plane (32-bit, w h < 2^31).
+// Addresses of the taps.  PLANES / QUADS: the four in-bucket texels (s0|s1,
+// t0|t1) select four planes (64-bit base indices), the (up to) four buckets
+// select spatial offsets inside a plane (32-bit, w h < 2^31).
 template <int FMT, int LAYOUT>
 __device__ __forceinline__ void load_quadP(const TexDesc& d, int i, int j, const Axis& s, const Axis& t, P4& t00,
                                            P4& t10, P4& t01, P4& t11) {
@@ -101,32 +101,34 @@ __device__ __forceinline__ float4 filter_taps(const TexDesc& d, const Lookup<FIL
 }
 
 // Dispatch on the object's storage format and layout (owned textures are
-// PLANES or palettes; a borrowed FP32 buffer may be any of the three).
+// QUADS, PLANES or palettes; a borrowed FP32 buffer may be ATLAS, PLANES or
+// QUADS).
+template <int FILTER, int FMT>
+__device__ __forceinline__ float4 filter_dense(const TexDesc& d, const Lookup<FILTER>& L) {
+    if (d.layout == kLayoutPalette) return filter_taps<FILTER, FMT, kLayoutPalette>(d, L);
+    if (FMT != RT_BIT1 && d.layout == RT_LAYOUT_QUADS) return filter_taps<FILTER, FMT, RT_LAYOUT_QUADS>(d, L);
+    return filter_taps<FILTER, FMT, RT_LAYOUT_PLANES>(d, L);
+}
+
 template <int FILTER>
 __device__ __forceinline__ float4 filter_any(const TexDesc& d, const Lookup<FILTER>& L) {
-    const bool pal = d.layout == kLayoutPalette;
     switch (d.fmt) {
         case RT_F16:
-            return pal ? filter_taps<FILTER, RT_F16, kLayoutPalette>(d, L)
-                       : filter_taps<FILTER, RT_F16, RT_LAYOUT_PLANES>(d, L);
+            return filter_dense<FILTER, RT_F16>(d, L);
         case RT_BF16:
-            return pal ? filter_taps<FILTER, RT_BF16, kLayoutPalette>(d, L)
-                       : filter_taps<FILTER, RT_BF16, RT_LAYOUT_PLANES>(d, L);
+            return filter_dense<FILTER, RT_BF16>(d, L);
         case RT_E4M3_BUCKET_SCALE:
-            return pal ? filter_taps<FILTER, RT_E4M3_BUCKET_SCALE, kLayoutPalette>(d, L)
-                       : filter_taps<FILTER, RT_E4M3_BUCKET_SCALE, RT_LAYOUT_PLANES>(d, L);
+            return filter_dense<FILTER, RT_E4M3_BUCKET_SCALE>(d, L);
         case RT_BIT1:
-            return pal ? filter_taps<FILTER, RT_BIT1, kLayoutPalette>(d, L)
-                       : filter_taps<FILTER, RT_BIT1, RT_LAYOUT_PLANES>(d, L);
+            return filter_dense<FILTER, RT_BIT1>(d, L);
         default:
             if (d.layout == RT_LAYOUT_ATLAS) return filter_taps<FILTER, RT_F32, RT_LAYOUT_ATLAS>(d, L);
-            return pal ? filter_taps<FILTER, RT_F32, kLayoutPalette>(d, L)
-                       : filter_taps<FILTER, RT_F32, RT_LAYOUT_PLANES>(d, L);
+            return filter_dense<FILTER, RT_F32>(d, L);
     }
 }
 
 // SPEC: -1 = any objects (format, layout, palette and repeat mode dispatched
-// per fragment); a format = every object of the table is a dense PLANES
+// per fragment); a format = every object of the table is a dense QUADS
 // texture of that format in clamp mode, so the fragment code is one path
 // (the host picks the instantiation from the table).
 template <int FILTER, int SPEC>
@@ -134,7 +136,7 @@ __device__ __forceinline__ float4 filter_spec(const TexDesc& d, const Lookup<FIL
     if constexpr (SPEC < 0)
         return filter_any<FILTER>(d, L);
     else
-        return filter_taps<FILTER, SPEC, RT_LAYOUT_PLANES>(d, L);
+        return filter_taps<FILTER, SPEC, RT_LAYOUT_QUADS>(d, L);
 }
 
 // G-buffer staging.  Kernels that walk fragments are persistent: each warp

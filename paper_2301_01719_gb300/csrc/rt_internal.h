@@ -82,8 +82,9 @@ cudaError_t launch_fixed_to_float(const long long* acc, float* dst, int64_t coun
                                   cudaStream_t stream, double scale = 1.0);
 
 cudaError_t launch_encode(const float* src, int src_layout, void* dst, float* scale, int W, int H, int n, int fmt,
-                          cudaStream_t stream);
-cudaError_t launch_read(const void* src, int fmt, int W, int H, int n, int dst_layout, void* dst, cudaStream_t stream);
+                          int dst_layout, cudaStream_t stream);
+cudaError_t launch_read(const void* src, int src_layout, const float* scale, int fmt, int W, int H, int n,
+                        int dst_layout, void* dst, float* scale_dst, cudaStream_t stream);
 cudaError_t launch_bake_shadow(const rt_bake_scene& S, int surface, void* dst, int W, int H, int n,
                                cudaStream_t stream);
 cudaError_t launch_multi_shade(const TexDesc* table, int n_obj, const float* uv, const float* dirs, int S,
@@ -110,7 +111,7 @@ cudaError_t launch_kmeans_update(const TexDesc& d, int K, const uint32_t* index,
 cudaError_t launch_check_index(const uint32_t* index, int64_t count, uint32_t K, unsigned* bad, cudaStream_t stream);
 cudaError_t launch_bake(const rt_bake_scene& S, int surface, void* dst, float* scale, int W, int H, int n, int fmt,
                         int layout, const float* ao_dirs, int K, cudaStream_t stream);
-cudaError_t launch_fill_lobes(const float* params, void* dst, float* scale, int W, int H, int n, int fmt,
+cudaError_t launch_fill_lobes(const float* params, void* dst, float* scale, int layout, int W, int H, int n, int fmt,
                               cudaStream_t stream);
 cudaError_t launch_convert(const float* src, int src_layout, float* dst, int dst_layout, int W, int H, int n,
                            cudaStream_t stream);

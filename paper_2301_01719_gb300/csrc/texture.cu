@@ -12,13 +12,14 @@ constexpr int kThreads = 256;
 
 static inline unsigned blocks_for(int64_t items) { return (unsigned)((items + kThreads - 1) / kThreads); }
 
-// FP32 source (any layout) -> FP32 / FP16 / BF16 storage in PLANES, one thread per texel.
-__global__ void encode_elementwise(const float4* __restrict__ src, int src_layout, void* __restrict__ dst, int W,
-                                   int H, int n, int fmt, int64_t total) {
+// FP32 source (any layout) -> FP32 / FP16 / BF16 storage in dst_layout (PLANES
+// or QUADS), one thread per stored texel.
+__global__ void encode_elementwise(const float4* __restrict__ src, int src_layout, void* __restrict__ dst,
+                                   int dst_layout, int W, int H, int n, int fmt, int64_t total) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
     int i, j, s, t;
-    planes_coords(idx, W, H, n, i, j, s, t);
+    storage_coords(dst_layout, idx, W, H, n, i, j, s, t);
     float4 v = src[index_in(src_layout, W, H, n, i, j, s, t)];
     if (fmt == RT_F32)
         reinterpret_cast<float4*>(dst)[idx] = v;
@@ -28,9 +29,10 @@ __global__ void encode_elementwise(const float4* __restrict__ src, int src_layou
         reinterpret_cast<uint2*>(dst)[idx] = pack_bf16(v);
 }
 
-// FP32 source -> E4M3 + per-bucket scale, one thread per bucket (amax pass, then encode pass).
+// FP32 source -> E4M3 + per-bucket scale (stored at the bucket's slot of
+// dst_layout), one thread per bucket (amax pass, then encode pass).
 __global__ void encode_e4m3_buckets(const float4* __restrict__ src, int src_layout, unsigned* __restrict__ dst,
-                                    float* __restrict__ scale, int W, int H, int n) {
+                                    float* __restrict__ scale, int dst_layout, int W, int H, int n) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)W * H) return;
     int j = (int)(b / W), i = (int)(b - (int64_t)j * W);
@@ -38,11 +40,10 @@ __global__ void encode_e4m3_buckets(const float4* __restrict__ src, int src_layo
     for (int t = 0; t < n; ++t)
         for (int s = 0; s < n; ++s) amax = fmaxf(amax, amax4(src[index_in(src_layout, W, H, n, i, j, s, t)]));
     float sc = bucket_scale(amax);
-    scale[b] = sc;
+    scale[slot_in(dst_layout, W, i, j)] = sc;
     for (int t = 0; t < n; ++t)
         for (int s = 0; s < n; ++s)
-            dst[index_in(RT_LAYOUT_PLANES, W, H, n, i, j, s, t)] =
-                pack_e4m3(src[index_in(src_layout, W, H, n, i, j, s, t)], sc);
+            dst[index_in(dst_layout, W, H, n, i, j, s, t)] = pack_e4m3(src[index_in(src_layout, W, H, n, i, j, s, t)], sc);
 }
 
 // FP32 source -> 1-bit storage: bit = (channel 0 >= 1/2); one thread per 32-bit word.
@@ -62,7 +63,7 @@ __global__ void encode_bits(const float4* __restrict__ src, int src_layout, unsi
 }
 
 cudaError_t launch_encode(const float* src, int src_layout, void* dst, float* scale, int W, int H, int n, int fmt,
-                          cudaStream_t stream) {
+                          int dst_layout, cudaStream_t stream) {
     if (fmt == RT_BIT1) {
         const int64_t total = (int64_t)W * H * n * n;
         encode_bits<<<blocks_for((total + 31) / 32), kThreads, 0, stream>>>(
@@ -70,24 +71,34 @@ cudaError_t launch_encode(const float* src, int src_layout, void* dst, float* sc
     } else if (fmt == RT_E4M3_BUCKET_SCALE) {
         int64_t buckets = (int64_t)W * H;
         encode_e4m3_buckets<<<blocks_for(buckets), kThreads, 0, stream>>>(
-            reinterpret_cast<const float4*>(src), src_layout, reinterpret_cast<unsigned*>(dst), scale, W, H, n);
+            reinterpret_cast<const float4*>(src), src_layout, reinterpret_cast<unsigned*>(dst), scale, dst_layout, W,
+            H, n);
     } else {
         int64_t total = (int64_t)W * H * n * n;
         encode_elementwise<<<blocks_for(total), kThreads, 0, stream>>>(reinterpret_cast<const float4*>(src),
-                                                                       src_layout, dst, W, H, n, fmt, total);
+                                                                       src_layout, dst, dst_layout, W, H, n, fmt,
+                                                                       total);
     }
     return cudaGetLastError();
 }
 
-// Stored codes (PLANES) -> codes in dst_layout; T is the per-texel code type.
+// Stored codes (src_layout: PLANES or QUADS) -> codes in dst_layout; T is the per-texel code type.
 template <typename T>
-__global__ void read_codes(const T* __restrict__ src, T* __restrict__ dst, int W, int H, int n, int dst_layout,
-                           int64_t total) {
+__global__ void read_codes(const T* __restrict__ src, int src_layout, T* __restrict__ dst, int W, int H, int n,
+                           int dst_layout, int64_t total) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
     int i, j, s, t;
-    planes_coords(idx, W, H, n, i, j, s, t);
+    storage_coords(src_layout, idx, W, H, n, i, j, s, t);
     dst[index_in(dst_layout, W, H, n, i, j, s, t)] = src[idx];
+}
+
+// Per-bucket scales stored at their slots of src_layout -> row-major h x w.
+__global__ void read_scales(const float* __restrict__ src, int src_layout, float* __restrict__ dst, int W, int H) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)W * H) return;
+    const int j = (int)(b / W), i = (int)(b - (int64_t)j * W);
+    dst[b] = src[slot_in(src_layout, W, i, j)];
 }
 
 // 1-bit storage -> one byte (0 or 1) per texel in dst_layout.
@@ -101,22 +112,24 @@ __global__ void read_bits(const unsigned* __restrict__ src, uint8_t* __restrict_
     dst[o] = (uint8_t)((src[idx >> 5] >> (unsigned)(idx & 31)) & 1u);
 }
 
-cudaError_t launch_read(const void* src, int fmt, int W, int H, int n, int dst_layout, void* dst,
-                        cudaStream_t stream) {
+cudaError_t launch_read(const void* src, int src_layout, const float* scale, int fmt, int W, int H, int n,
+                        int dst_layout, void* dst, float* scale_dst, cudaStream_t stream) {
     int64_t total = (int64_t)W * H * n * n;
     unsigned g = blocks_for(total);
-    if (fmt == RT_BIT1)
+    if (fmt == RT_BIT1)  // bit textures are always PLANES
         read_bits<<<g, kThreads, 0, stream>>>(reinterpret_cast<const unsigned*>(src), reinterpret_cast<uint8_t*>(dst),
                                               W, H, n, dst_layout, total);
     else if (fmt == RT_F32)
-        read_codes<float4><<<g, kThreads, 0, stream>>>(reinterpret_cast<const float4*>(src),
+        read_codes<float4><<<g, kThreads, 0, stream>>>(reinterpret_cast<const float4*>(src), src_layout,
                                                        reinterpret_cast<float4*>(dst), W, H, n, dst_layout, total);
     else if (fmt == RT_E4M3_BUCKET_SCALE)
-        read_codes<unsigned><<<g, kThreads, 0, stream>>>(reinterpret_cast<const unsigned*>(src),
+        read_codes<unsigned><<<g, kThreads, 0, stream>>>(reinterpret_cast<const unsigned*>(src), src_layout,
                                                          reinterpret_cast<unsigned*>(dst), W, H, n, dst_layout, total);
     else
-        read_codes<uint2><<<g, kThreads, 0, stream>>>(reinterpret_cast<const uint2*>(src),
+        read_codes<uint2><<<g, kThreads, 0, stream>>>(reinterpret_cast<const uint2*>(src), src_layout,
                                                       reinterpret_cast<uint2*>(dst), W, H, n, dst_layout, total);
+    if (scale && scale_dst)
+        read_scales<<<blocks_for((int64_t)W * H), kThreads, 0, stream>>>(scale, src_layout, scale_dst, W, H);
     return cudaGetLastError();
 }
 
@@ -127,7 +140,7 @@ __device__ __forceinline__ float4 lobe_value(const float* P, float3 I) {
 }
 
 __global__ void fill_lobes_kernel(const float* __restrict__ params, void* __restrict__ dst, float* __restrict__ scale,
-                                  int W, int H, int n, int fmt) {
+                                  int layout, int W, int H, int n, int fmt) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (int64_t)W * H) return;
     int j = (int)(b / W), i = (int)(b - (int64_t)j * W);
@@ -142,12 +155,12 @@ __global__ void fill_lobes_kernel(const float* __restrict__ params, void* __rest
         for (int t = 0; t < n; ++t)
             for (int s = 0; s < n; ++s) amax = fmaxf(amax, amax4(lobe_value(P, texel_centre_direction(s, t, n))));
         sc = bucket_scale(amax);
-        scale[b] = sc;
+        scale[slot_in(layout, W, i, j)] = sc;
     }
     for (int t = 0; t < n; ++t)
         for (int s = 0; s < n; ++s) {
             float4 v = lobe_value(P, texel_centre_direction(s, t, n));
-            int64_t idx = index_in(RT_LAYOUT_PLANES, W, H, n, i, j, s, t);
+            int64_t idx = index_in(layout, W, H, n, i, j, s, t);
             if (fmt == RT_F32)
                 reinterpret_cast<float4*>(dst)[idx] = v;
             else if (fmt == RT_F16)
@@ -159,10 +172,10 @@ __global__ void fill_lobes_kernel(const float* __restrict__ params, void* __rest
         }
 }
 
-cudaError_t launch_fill_lobes(const float* params, void* dst, float* scale, int W, int H, int n, int fmt,
+cudaError_t launch_fill_lobes(const float* params, void* dst, float* scale, int layout, int W, int H, int n, int fmt,
                               cudaStream_t stream) {
     int64_t buckets = (int64_t)W * H;
-    fill_lobes_kernel<<<blocks_for(buckets), kThreads, 0, stream>>>(params, dst, scale, W, H, n, fmt);
+    fill_lobes_kernel<<<blocks_for(buckets), kThreads, 0, stream>>>(params, dst, scale, layout, W, H, n, fmt);
     return cudaGetLastError();
 }
 

@@ -5,8 +5,9 @@ fits one to a set of target views instead, which is what the differentiable
 lookup is for.  A step is: forward synthesis of every view, the L2 loss and its
 gradient and the backward pass into the texel gradients, fused into one launch
 (rt_shade_batched_l2_step), then an Adam update (rt_adam_step) -- all in
-libradtex's kernels, on the FP32 texture the context
-borrows (RT_BORROW) in the planes layout.  Checkpoints hold the texture, the
+libradtex's kernels, on the FP32 texture the context borrows (RT_BORROW) in
+the layout the library gives owned textures (2 x 2 bucket quads when both sides
+are even, planes otherwise).  Checkpoints hold the texture, the
 Adam moments, the step count and a hash of the configuration; with
 deterministic=True (fixed-point texel gradients) a run resumed from a
 checkpoint is bit-identical to an uninterrupted one.
@@ -72,8 +73,10 @@ class TextureFit:
         self.w, self.h, self.n = int(w), int(h), int(n)
         self.lr, self.betas, self.eps, self.filt = float(lr), tuple(betas), float(eps), int(filt)
         self.deterministic = bool(deterministic)
-        self.tex = torch.full((n, n, h, w, 4), float(init), dtype=torch.float32, device=dev)
-        self.oid = api.rt_create_texture(ctx, w, h, n, api.RT_F32, api.RT_LAYOUT_PLANES, self.tex, api.RT_BORROW)
+        # the owned textures' layout: 2 x 2 bucket quads when both sides are even
+        self.layout = api.RT_LAYOUT_QUADS if (w % 2 == 0 and h % 2 == 0) else api.RT_LAYOUT_PLANES
+        self.tex = torch.full(api.layout_shape(self.layout, w, h, n), float(init), dtype=torch.float32, device=dev)
+        self.oid = api.rt_create_texture(ctx, w, h, n, api.RT_F32, self.layout, self.tex, api.RT_BORROW)
         self.grad = torch.zeros_like(self.tex)
         self.m = torch.zeros_like(self.tex)
         self.v = torch.zeros_like(self.tex)

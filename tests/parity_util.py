@@ -33,6 +33,50 @@ def atlas_to_planes(a: np.ndarray, W: int, H: int, n: int) -> np.ndarray:
     return a.reshape(H, n, W, n, 4).transpose(1, 3, 0, 2, 4).copy()
 
 
+# RT_LAYOUT_QUADS, written out from its definition: texel (i, j, s, t) at
+# (t n + s) w h + 4 ((j // 2)(w // 2) + i // 2) + 2 (j % 2) + i % 2, i.e. the
+# C-order array (t, s, j // 2, i // 2, j % 2, i % 2, channel).
+
+def quads_to_atlas(t: np.ndarray, W: int, H: int, n: int) -> np.ndarray:
+    """(n, n, h/2, w/2, 2, 2, k) -> (h n, w n, k): row j n + t = (2 jq + jr) n + t, column (2 iq + ir) n + s."""
+    k = t.size // (W * H * n * n)
+    return t.reshape(n, n, H // 2, W // 2, 2, 2, k).transpose(2, 4, 0, 3, 5, 1, 6).reshape(H * n, W * n, k)
+
+
+def atlas_to_quads(a: np.ndarray, W: int, H: int, n: int) -> np.ndarray:
+    k = a.size // (W * H * n * n)
+    return a.reshape(H // 2, 2, n, W // 2, 2, n, k).transpose(2, 5, 0, 3, 1, 4, 6).copy()
+
+
+def storage_to_atlas(t: np.ndarray, layout: int, W: int, H: int, n: int) -> np.ndarray:
+    """A PLANES or QUADS buffer (any shape, 4 channels) as the (h n, w n, 4) atlas."""
+    if layout == api.RT_LAYOUT_QUADS:
+        return quads_to_atlas(t, W, H, n)
+    return planes_to_atlas(t, W, H, n)
+
+
+def atlas_to_storage(a: np.ndarray, layout: int, W: int, H: int, n: int) -> np.ndarray:
+    if layout == api.RT_LAYOUT_QUADS:
+        return atlas_to_quads(a, W, H, n)
+    return atlas_to_planes(a, W, H, n)
+
+
+def storage_index(layout: int, W: int, H: int, n: int, i, j, s, t):
+    """Flat texel index of (i, j, s, t) in a PLANES or QUADS buffer (numpy arrays or ints)."""
+    plane = (np.asarray(t, np.int64) * n + s) * (W * H)
+    if layout == api.RT_LAYOUT_QUADS:
+        i, j = np.asarray(i, np.int64), np.asarray(j, np.int64)
+        return plane + 4 * ((j // 2) * (W // 2) + i // 2) + 2 * (j % 2) + i % 2
+    return plane + np.asarray(j, np.int64) * W + i
+
+
+def grad_to_atlas(ctx, oid: int, t) -> np.ndarray:
+    """The texel-gradient buffer of object oid (its storage layout) as an atlas."""
+    info = api.rt_texture_info(ctx, oid)
+    a = t.detach().cpu().numpy() if isinstance(t, torch.Tensor) else np.asarray(t)
+    return storage_to_atlas(a, info["layout"], info["w"], info["h"], info["n"])
+
+
 def index_taus(W: int, H: int, n: int):
     """Band half-widths (in coordinate units) within which FP32 and FP64 floors may differ:
     8 W 2^-24 for the spatial coordinates and 64 n 2^-24 for the in-bucket ones."""

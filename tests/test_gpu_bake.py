@@ -16,6 +16,7 @@ import torch
 import oracle
 import synth
 from paper_2301_01719_gb300 import api
+from parity_util import storage_to_atlas
 
 pytestmark = pytest.mark.gpu
 
@@ -105,18 +106,18 @@ def test_bake_matches_oracle(ctx, surface, fmt, shape):
     api.rt_destroy_texture(ctx, oid)
 
 
-@pytest.mark.parametrize("layout", [api.RT_LAYOUT_ATLAS, api.RT_LAYOUT_PLANES])
-def test_bake_into_borrowed_fp32(ctx, layout):
-    W, H, n = 19, 11, 6
+@pytest.mark.parametrize("layout,W,H", [(api.RT_LAYOUT_ATLAS, 19, 11), (api.RT_LAYOUT_PLANES, 19, 11),
+                                        (api.RT_LAYOUT_QUADS, 20, 12)])
+def test_bake_into_borrowed_fp32(ctx, layout, W, H):
+    n = 6
     scene = synth.bake_scene(32)
     dev = torch.device("cuda", 0)
-    shape = (H * n, W * n, 4) if layout == api.RT_LAYOUT_ATLAS else (n, n, H, W, 4)
-    buf = torch.full(shape, -7.0, device=dev)
+    buf = torch.full(api.layout_shape(layout, W, H, n), -7.0, device=dev)
     oid = api.rt_create_texture(ctx, W, H, n, api.RT_F32, layout, buf, api.RT_BORROW)
     api.rt_bake(ctx, oid, api.RT_SURFACE_PLANE, scene)
     got = buf.cpu().numpy().astype(np.float64)
-    if layout == api.RT_LAYOUT_PLANES:  # [t, s, j, i, c] -> atlas [j n + t, i n + s, c]
-        got = got.transpose(2, 0, 3, 1, 4).reshape(H * n, W * n, 4)
+    if layout != api.RT_LAYOUT_ATLAS:
+        got = storage_to_atlas(got, layout, W, H, n)
     val, lo, hi = oracle.bake(W, H, n, oracle.SURFACE_PLANE, scene, DELTA)
     check(got, val, lo, hi, api.RT_F32)
     api.rt_destroy_texture(ctx, oid)

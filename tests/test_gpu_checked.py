@@ -24,7 +24,7 @@ import torch
 
 import oracle
 from paper_2301_01719_gb300 import _lib, api
-from parity_util import COLOUR_TOL, atlas_to_planes, planes_to_atlas, quad_workload, to_dev
+from parity_util import COLOUR_TOL, atlas_to_storage, quad_workload, storage_index, storage_to_atlas, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -93,22 +93,22 @@ def test_limit_rejects_bad_arguments(ctx):
     assert api.rt_checked_limit_extent(ctx, oid, 0) == api.RT_ERR_INVALID_ARG  # dead object
 
 
-def _substituted(T, W, H, n, limit):
-    """The oracle texture whose texels at PLANES index >= limit hold texel 0's codes."""
-    P = atlas_to_planes(T.codes, W, H, n).reshape(-1, 4)
+def _substituted(T, layout, W, H, n, limit):
+    """The oracle texture whose texels at storage index >= limit hold texel 0's codes."""
+    P = atlas_to_storage(T.codes, layout, W, H, n).reshape(-1, 4)
     P[limit:] = P[0]
-    return oracle.Texture(W, H, n, T.fmt, planes_to_atlas(P.reshape(n, n, H, W, 4), W, H, n))
+    return oracle.Texture(W, H, n, T.fmt, storage_to_atlas(P, layout, W, H, n))
 
 
-def _median_tap(table, g, obj_np, filt, W, H, n):
-    """The median PLANES index, (t n + s) w h + j w + i, of the taps with a
-    non-zero weight (the oracle's taps are atlas indices (j n + t) w n + i n + s)."""
+def _median_tap(table, g, obj_np, filt, layout, W, H, n):
+    """The median storage index of the taps with a non-zero weight (the
+    oracle's taps are atlas indices (j n + t) w n + i n + s)."""
     idx, weight, _ = oracle.taps(table, g.uv, g.dir, obj_np, filt)
     keep = (idx >= 0) & (weight > 0)
     Y, X = np.divmod(idx[keep], W * n)
     j, t = np.divmod(Y, n)
     i, s = np.divmod(X, n)
-    return int(np.median((t * n + s) * (W * H) + j * W + i))
+    return int(np.median(storage_index(layout, W, H, n, i, j, s, t)))
 
 
 @pytest.mark.parametrize("path", ["flat", "batched", "fused"])
@@ -124,10 +124,12 @@ def test_accesses_past_the_limit_are_redirected_and_reported(ctx, path, filt):
     table = [None] * (oid + 1)
     table[oid] = T
     texels = W * H * n * n
-    limit = _median_tap(table, g, obj_np, filt, W, H, n)  # about half the weighted taps lie past it
+    layout = api.rt_texture_info(ctx, oid)["layout"]
+    assert layout == api.RT_LAYOUT_QUADS
+    limit = _median_tap(table, g, obj_np, filt, layout, W, H, n)  # about half the weighted taps lie past it
     assert 0 < limit < texels
     assert api.rt_checked_limit_extent(ctx, oid, limit) == api.RT_OK
-    T2 = _substituted(T, W, H, n, limit)
+    T2 = _substituted(T, layout, W, H, n, limit)
     table2 = [None] * (oid + 1)
     table2[oid] = T2
 
@@ -165,8 +167,8 @@ def test_accesses_past_the_limit_are_redirected_and_reported(ctx, path, filt):
     gt, _, _, _ = oracle.shade_backward(table, g.uv, g.dir, obj_np, filt, gout, want_uv=False, want_dir=False)
     gabs, _, _, _ = oracle.shade_backward(table, g.uv, g.dir, obj_np, filt, np.abs(gout), want_uv=False,
                                           want_dir=False)
-    G = atlas_to_planes(gt[oid], W, H, n).reshape(-1, 4)
-    A = atlas_to_planes(gabs[oid], W, H, n).reshape(-1, 4)
+    G = atlas_to_storage(gt[oid], layout, W, H, n).reshape(-1, 4)
+    A = atlas_to_storage(gabs[oid], layout, W, H, n).reshape(-1, 4)
     want = G.copy()
     want[0] += G[limit:].sum(axis=0)
     want[limit:] = 0.0

@@ -9,7 +9,7 @@ import oracle
 import synth
 from paper_2301_01719_gb300 import api
 from paper_2301_01719_gb300.fit import TextureFit
-from parity_util import planes_to_atlas, to_dev
+from parity_util import storage_to_atlas, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -149,7 +149,7 @@ def test_texel_gradients_vs_fd_and_oracle(ctx):
     # FP32 colours it changes, about (fragments) * scale * |c - t| * 2^-24 / eps ~ 1e-8 here
     assert np.all(np.abs(fd - ana) <= 2e-3 * np.abs(ana) + 2e-8)
     # against the FP64 oracle on the same texels and dL/dout
-    atlas = planes_to_atlas(fit.tex.cpu().numpy(), W, H, n)
+    atlas = storage_to_atlas(fit.tex.cpu().numpy(), fit.layout, W, H, n)
     T = oracle.Texture(W, H, n, oracle.F64, atlas.astype(np.float64))
     table = [None] * (fit.oid + 1)
     table[fit.oid] = T
@@ -157,7 +157,7 @@ def test_texel_gradients_vs_fd_and_oracle(ctx):
     gt, _, _, _ = oracle.shade_backward(table, g.uv, g.dir, obj_np, oracle.QUADRILINEAR,
                                         dL.reshape(-1, 4).cpu().numpy().astype(np.float64), want_uv=False,
                                         want_dir=False)
-    got = planes_to_atlas(grad_np, W, H, n)
+    got = storage_to_atlas(grad_np, fit.layout, W, H, n)
     assert np.abs(got - gt[fit.oid]).max() <= 1e-4 * np.abs(gt[fit.oid]).max()
     api.rt_destroy_texture(ctx, fit.oid)
 
@@ -204,7 +204,7 @@ def test_fixed_point_gradients_add_up_over_view_shards(ctx):
     fit = TextureFit(ctx, 16, 16, 8, init=0.3)
     o = for_object(o, fit.oid)
     fit.tex.uniform_(0, 1)
-    F = lambda: torch.zeros((8, 8, 16, 16, 4), dtype=torch.int64, device=uv.device)  # noqa: E731
+    F = lambda: torch.zeros(fit.tex.shape, dtype=torch.int64, device=uv.device)  # noqa: E731
     flags = api.RT_FIXED_POINT_GRADS
     every, half_a, half_b, acc = F(), F(), F(), F()
     api.rt_shade_batched_l2_step(ctx, uv, d, o, api.RT_QUADRILINEAR, t, 0.5, None, None, {fit.oid: every},

@@ -16,7 +16,7 @@ import torch
 import oracle
 import synth
 from paper_2301_01719_gb300 import api
-from parity_util import COLOUR_TOL, compare_indices, index_taus
+from parity_util import COLOUR_TOL, compare_indices, index_taus, storage_index
 
 pytestmark = pytest.mark.gpu
 
@@ -151,8 +151,9 @@ def test_fullsize_texel_gradients_per_texel(full):
         np.add.at(ref, inv, w[:, None] * gk.astype(np.float64))
         np.add.at(bound, inv, w * np.abs(gk.astype(np.float64)).max(axis=1))
         Y, X = keys // W, keys % W
-        t, s_, j, i = (torch.from_numpy(a).to(dev) for a in (Y % N, X % N, Y // N, X // N))
-        got = dtex[k][t, s_, j, i].double().cpu().numpy()
+        flat = storage_index(api.rt_texture_info(ctx, k)["layout"], BUCKETS, BUCKETS, N, X // N, Y // N, X % N,
+                             Y % N)
+        got = dtex[k].view(-1, 4)[torch.from_numpy(flat).to(dev)].double().cpu().numpy()
         err = np.abs(got - ref)
         tol = 1e-4 * bound[:, None] + 2e-5 * np.abs(gsel).max()
         assert (err <= tol).all(), (f"object {k}: {(err > tol).sum()} texel channels off, worst "

@@ -25,7 +25,7 @@ import torch
 import oracle
 import synth
 from paper_2301_01719_gb300 import api
-from parity_util import COLOUR_TOL, floor_mismatch
+from parity_util import COLOUR_TOL, floor_mismatch, storage_index
 
 pytestmark = pytest.mark.gpu
 
@@ -146,8 +146,8 @@ def test_max_size_texture(ctx, W, H, n):
     np.add.at(expect, inv, (w[..., None] * g[:, None, :].astype(np.float64))[keep])
     X, Y = touched % (W * n), touched // (W * n)
     i, s, j, t = X // n, X % n, Y // n, Y % n
-    planes = ((t * n + s) * H + j) * W + i
-    got = dtex.view(-1, 4)[torch.from_numpy(planes).to(dev)].double().cpu().numpy()
+    flat = storage_index(api.rt_texture_info(ctx, oid)["layout"], W, H, n, i, j, s, t)
+    got = dtex.view(-1, 4)[torch.from_numpy(flat).to(dev)].double().cpu().numpy()
     # the texel-gradient bar of the other backward parity tests: FP32 weights of FP32 coordinates
     assert np.all(np.abs(got - expect) <= 1e-4 * np.abs(expect) + 2e-5 * np.abs(g).max())
     total = sum(float(dtex[tt].abs().sum(dtype=torch.float64)) for tt in range(n))

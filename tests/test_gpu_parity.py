@@ -12,8 +12,9 @@ import torch
 import oracle
 import synth
 from paper_2301_01719_gb300 import api, autograd
-from parity_util import (COLOUR_TOL, FILTERS, ORACLE_FMT, atlas_to_planes, compare_indices, dev, floor_mismatch,
-                         gbuffer_to_dev, index_taus, planes_to_atlas, quad_workload, to_dev)
+from parity_util import (COLOUR_TOL, FILTERS, ORACLE_FMT, atlas_to_planes, atlas_to_storage, compare_indices, dev,
+                         floor_mismatch, gbuffer_to_dev, grad_to_atlas, index_taus, planes_to_atlas, quad_workload,
+                         quads_to_atlas, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -33,7 +34,7 @@ def ctx():
 
 
 def _new_texture(ctx, atlas, W, H, n, fmt, layout=api.RT_LAYOUT_ATLAS, flags=0):
-    src = to_dev(atlas if layout == api.RT_LAYOUT_ATLAS else atlas_to_planes(atlas, W, H, n))
+    src = to_dev(atlas if layout == api.RT_LAYOUT_ATLAS else atlas_to_storage(atlas, layout, W, H, n))
     oid = api.rt_create_texture(ctx, W, H, n, fmt, layout, src, flags)
     return oid, src
 
@@ -56,10 +57,45 @@ def test_encoders_bit_exact(ctx, fmt):
         np.testing.assert_array_equal(got.view(T.codes.dtype), T.codes)
     if fmt == api.RT_E4M3_BUCKET_SCALE:
         np.testing.assert_array_equal(scales.cpu().numpy().view(np.uint32), T.scales.view(np.uint32))
-    # planes read-back is the same codes, permuted
+    # stored in 2 x 2 bucket quads (even w, h); planes and quads read-backs are the same codes, permuted
+    assert api.rt_texture_info(ctx, oid)["layout"] == api.RT_LAYOUT_QUADS
     pc, _ = api.rt_read_texture(ctx, oid, api.RT_LAYOUT_PLANES)
     np.testing.assert_array_equal(planes_to_atlas(pc.cpu().numpy(), W, H, n), got)
+    qc, _ = api.rt_read_texture(ctx, oid, api.RT_LAYOUT_QUADS)
+    assert tuple(qc.shape) == (n, n, H // 2, W // 2, 2, 2, 4)
+    np.testing.assert_array_equal(quads_to_atlas(qc.cpu().numpy(), W, H, n), got)
     api.rt_destroy_texture(ctx, oid)
+
+
+def test_storage_layout_follows_the_sides(ctx):
+    """Owned textures with even sides are stored in quads, others in planes; a
+    quads source or read-back needs even sides; conversions agree with the
+    definition of each layout."""
+    for (W, H), want in (((6, 4), api.RT_LAYOUT_QUADS), ((5, 4), api.RT_LAYOUT_PLANES),
+                         ((6, 3), api.RT_LAYOUT_PLANES)):
+        oid = api.rt_create_texture(ctx, W, H, 3, api.RT_F16)
+        assert api.rt_texture_info(ctx, oid)["layout"] == want
+        if want == api.RT_LAYOUT_PLANES:
+            with pytest.raises(api.RadtexError):
+                api.rt_read_texture(ctx, oid, api.RT_LAYOUT_QUADS)
+        api.rt_destroy_texture(ctx, oid)
+    bits = api.rt_create_texture(ctx, 8, 8, 2, api.RT_BIT1)  # bit textures keep the planes bit numbering
+    assert api.rt_texture_info(ctx, bits)["layout"] == api.RT_LAYOUT_PLANES
+    api.rt_destroy_texture(ctx, bits)
+    with pytest.raises(api.RadtexError):
+        api.rt_create_texture(ctx, 5, 4, 3, api.RT_F32, api.RT_LAYOUT_QUADS,
+                              to_dev(np.zeros((3, 3, 4, 5, 4), np.float32)))
+    W, H, n = 10, 6, 3
+    a = np.random.default_rng(4).normal(size=(H * n, W * n, 4)).astype(np.float32)
+    for src_l in (api.RT_LAYOUT_ATLAS, api.RT_LAYOUT_PLANES, api.RT_LAYOUT_QUADS):
+        for dst_l in (api.RT_LAYOUT_ATLAS, api.RT_LAYOUT_PLANES, api.RT_LAYOUT_QUADS):
+            src = to_dev(a if src_l == api.RT_LAYOUT_ATLAS else atlas_to_storage(a, src_l, W, H, n))
+            out = api.rt_convert_layout(src, src_l, dst_l, W, H, n).cpu().numpy()
+            want = a if dst_l == api.RT_LAYOUT_ATLAS else atlas_to_storage(a, dst_l, W, H, n)
+            np.testing.assert_array_equal(out.reshape(-1), want.reshape(-1))
+    with pytest.raises(api.RadtexError):  # odd h: the library rejects a quads buffer
+        api.rt_convert_layout(to_dev(np.zeros((5 * 3, 4 * 3, 4), np.float32)), api.RT_LAYOUT_ATLAS,
+                              api.RT_LAYOUT_QUADS, 4, 5, 3, dst=to_dev(np.zeros(4 * 5 * 9 * 4, np.float32)))
 
 
 @pytest.mark.parametrize("filt", FILTERS)
@@ -126,7 +162,7 @@ def test_borrowed_layouts_match_owned(ctx, filt):
     uv, d, o = gbuffer_to_dev(g)
     outs, keep, oids = [], [], []
     for layout, flags in ((api.RT_LAYOUT_ATLAS, 0), (api.RT_LAYOUT_ATLAS, api.RT_BORROW),
-                          (api.RT_LAYOUT_PLANES, api.RT_BORROW)):
+                          (api.RT_LAYOUT_PLANES, api.RT_BORROW), (api.RT_LAYOUT_QUADS, api.RT_BORROW)):
         oid, src = _new_texture(ctx, atlas, W, H, n, api.RT_F32, layout, flags)
         obj = torch.where(o >= 0, torch.full_like(o, oid), o)
         outs.append(api.rt_shade(ctx, uv, d, obj, filt).cpu().numpy())
@@ -134,6 +170,7 @@ def test_borrowed_layouts_match_owned(ctx, filt):
         oids.append(oid)
     np.testing.assert_array_equal(outs[0], outs[1])
     np.testing.assert_array_equal(outs[0], outs[2])
+    np.testing.assert_array_equal(outs[0], outs[3])
     obj_np = np.where(g.obj >= 0, oids[0], -1).astype(np.int32)
     table = [None] * (oids[0] + 1)
     table[oids[0]] = T
@@ -310,8 +347,9 @@ def test_constant_texture_exact(ctx):
 
 
 @pytest.mark.parametrize("fmt", FORMATS)
-def test_fill_bucket_lobes(ctx, fmt):
-    W, H, n = 37, 23, 16
+@pytest.mark.parametrize("W,H", [(37, 23), (38, 24)])  # stored in planes / in quads
+def test_fill_bucket_lobes(ctx, fmt, W, H):
+    n = 16
     params = synth.bucket_lobe_params(9, W, H)
     oid = api.rt_create_texture(ctx, W, H, n, fmt)
     api.rt_fill_bucket_lobes(ctx, oid, to_dev(params))
@@ -368,7 +406,7 @@ def test_backward_matches_oracle(ctx, fmt, filt):
     gt, guv, gdir, flags = oracle.shade_backward(table, g.uv, g.dir, obj_np, filt, gout)
     gabs, _, _, _ = oracle.shade_backward(table, g.uv, g.dir, obj_np, filt, np.abs(gout), want_uv=False,
                                           want_dir=False)
-    got = planes_to_atlas(dtex.cpu().numpy(), W, H, n)
+    got = grad_to_atlas(ctx, oid, dtex)
     # FP32 summation (1e-4 relative to sum w|g|) plus FP32 weights, whose
     # coordinates carry up to ~8 n 2^-24 of rounding per contributing fragment
     tol = 1e-4 * gabs[oid] + 2e-5 * np.abs(gout).max()
@@ -383,7 +421,7 @@ def test_backward_matches_oracle(ctx, fmt, filt):
     duv2 = duv.clone()
     api.rt_shade_backward(ctx, uv, d, o, filt, to_dev(gout), {oid: dtex}, duv2, None, api.RT_ACCUMULATE)
     np.testing.assert_allclose(duv2.cpu().numpy(), 2 * duv.cpu().numpy(), rtol=1e-6, atol=0)
-    got2 = planes_to_atlas(dtex.cpu().numpy(), W, H, n)
+    got2 = grad_to_atlas(ctx, oid, dtex)
     assert np.all(np.abs(got2 - 2 * gt[oid]) <= 2 * tol)
     api.rt_destroy_texture(ctx, oid)
 

@@ -14,8 +14,8 @@ import torch
 import oracle
 import synth
 from paper_2301_01719_gb300 import api
-from parity_util import (COLOUR_TOL, FILTERS, ORACLE_FMT, compare_indices, gbuffer_to_dev, index_taus,
-                         planes_to_atlas, quad_workload, to_dev)
+from parity_util import (COLOUR_TOL, FILTERS, ORACLE_FMT, compare_indices, gbuffer_to_dev, grad_to_atlas, index_taus,
+                         quad_workload, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -100,7 +100,7 @@ def test_world_backward_matches_oracle(ctx):
     assert api.rt_get_error(ctx) == api.RT_OK
     gt, guv, gdir, gnrm, _ = oracle.shade_world_backward(table, g.uv, g.dir, N, obj, api.RT_QUADRILINEAR, gout)
     gabs, _, _, _, _ = oracle.shade_world_backward(table, g.uv, g.dir, N, obj, api.RT_QUADRILINEAR, np.abs(gout))
-    got = planes_to_atlas(dtex.cpu().numpy(), T.W, T.H, T.n)
+    got = grad_to_atlas(ctx, oid, dtex)
     assert np.all(np.abs(got - gt[oid]) <= 1e-4 * gabs[oid] + 2e-5 * np.abs(gout).max())
     np.testing.assert_array_equal(ddir.cpu().numpy(), dnrm.cpu().numpy())
     # away from the kinks: integer coordinates and the clamp bounds of B
