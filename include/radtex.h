@@ -36,15 +36,19 @@
  *                       index ((t n + s) h + j) w + i: fragments that are close
  *                       on screen read texels that are close in memory.
  *     RT_LAYOUT_QUADS : the planes of RT_LAYOUT_PLANES with each plane's
- *                       buckets in 2 x 2 quads (w and h even): texel
- *                       (i, j, s, t) at index (t n + s) w h + 4 q + 2 (j mod 2)
- *                       + (i mod 2), quad q = (j / 2)(w / 2) + i / 2.  The
- *                       2 x 2 buckets of a quadrilinear lookup at one in-bucket
- *                       texel then lie in one quad more often, and a warp's taps
- *                       and texel-gradient reductions in fewer cache lines.
- *   Textures the library owns are stored in RT_LAYOUT_QUADS when w and h are
- *   even and the format is not RT_BIT1, and in RT_LAYOUT_PLANES otherwise
- *   (rt_texture_info reports which).
+ *                       buckets in 2 x 2 quads: a plane holds wq x hq quads,
+ *                       wq = ceil(w / 2), hq = ceil(h / 2) (an odd side is
+ *                       padded; P = 4 wq hq buckets per plane), texel
+ *                       (i, j, s, t) at index (t n + s) P + 4 q + 2 (j mod 2)
+ *                       + (i mod 2), quad q = (j / 2) wq + i / 2.  The 2 x 2
+ *                       buckets of a quadrilinear lookup at one in-bucket texel
+ *                       then lie in one quad more often, and a warp's taps and
+ *                       texel-gradient reductions in fewer cache lines.  A
+ *                       QUADS buffer holds P n^2 texels; the padding is never
+ *                       read by a lookup, is zero in owned textures and is not
+ *                       written by rt_convert_layout or rt_read_texture.
+ *   Textures the library owns are stored in RT_LAYOUT_QUADS, bit textures
+ *   (RT_BIT1) in RT_LAYOUT_PLANES (rt_texture_info reports the layout).
  */
 #ifndef RADTEX_H
 #define RADTEX_H
@@ -112,13 +116,13 @@ void rt_context_destroy(rt_ctx* ctx);
 
 /* Creates a radiance texture of w x h buckets of n x n texels (Section 2: the
  * bucket matrix, stored as w n x h n texels).  1 <= w, h <= 65536, w h <= 2^30, 1 <= n <= 64.
- * src (device, FP32, 4 channels per texel, layout src_layout) gives the texel
- * values; NULL leaves an owned texture zero (fill it with rt_fill_bucket_lobes).
- * src_layout may be RT_LAYOUT_QUADS only when w and h are even.  Without
- * RT_BORROW the library allocates storage (RT_LAYOUT_QUADS or RT_LAYOUT_PLANES,
- * see the layouts above) and encodes src into `storage` (E4M3: one FP32 scale
- * per bucket, s = amax / 448,
- * s = 1 for an all-zero bucket; codes = round-to-nearest-even-satfinite(v / s)).
+ * src (device, FP32, 4 channels per texel, layout src_layout; a QUADS buffer
+ * holds P n^2 texels, see above) gives the texel values; NULL leaves an owned
+ * texture zero (fill it with rt_fill_bucket_lobes).  Without RT_BORROW the
+ * library allocates storage (RT_LAYOUT_QUADS, or RT_LAYOUT_PLANES for RT_BIT1)
+ * and encodes src into `storage` (E4M3: one FP32 scale per bucket,
+ * s = amax / 448, s = 1 for an all-zero bucket; codes =
+ * round-to-nearest-even-satfinite(v / s)).
  * With RT_BORROW, `storage` must be RT_F32 and src non-NULL: the library reads
  * src in place, in src_layout, for as long as the texture lives; the caller
  * keeps it alive and may update its values between calls (texture fitting).
@@ -144,8 +148,8 @@ rt_status rt_texture_info(rt_ctx* ctx, int32_t obj_id, int32_t* w, int32_t* h, i
 
 /* Copies the stored codes of an object into codes_dst (device; w n h n x 4
  * elements of the storage type: float, uint16 (FP16/BF16 bits) or uint8
- * (E4M3 codes)) in dst_layout (RT_LAYOUT_QUADS only for even w and h), and for
- * E4M3 the per-bucket scales into scales_dst (device, h x w floats in row-major
+ * (E4M3 codes)) in dst_layout (a QUADS buffer holds P n^2 texels, its padding
+ * not written), and for E4M3 the per-bucket scales into scales_dst (device, h x w floats in row-major
  * bucket order, may be NULL).  Used to check the encoders. */
 rt_status rt_read_texture(rt_ctx* ctx, int32_t obj_id, rt_layout dst_layout, void* codes_dst, float* scales_dst,
                           rt_stream_t stream);
@@ -327,9 +331,9 @@ rt_status rt_locate(rt_ctx* ctx, const float* uv, const float* dir, const int32_
  *            array itself may be NULL, and so may any entry): FP32 gradient of
  *            the object's decoded texel values, 4 channels per texel, in the
  *            object's storage layout (rt_texture_info: RT_LAYOUT_QUADS for
- *            owned textures with even w and h, RT_LAYOUT_PLANES for other owned
- *            ones, the borrowed buffer's layout otherwise; rt_convert_layout
- *            turns it into another).  Summed with vector atomics.
+ *            owned textures, P n^2 texels with the padding left untouched; the
+ *            borrowed buffer's layout otherwise; rt_convert_layout turns it
+ *            into another).  Summed with vector atomics.
  *   dL_duv:  device F x 2 or NULL; dL_ddir: device F x 3 or NULL, through
  *            the filter weights, the Note's clamp, Eq. 3 and Eq. 1b.
  * Without RT_ACCUMULATE the per-fragment outputs are overwritten and each
@@ -369,8 +373,8 @@ rt_status rt_fixed_to_float(const int64_t* acc, float* dst, int64_t count, doubl
 
 /* Zeroes texel-gradient buffers on `stream` (asynchronous, no allocation): for
  * every non-NULL entry o < n_dtex of dL_dtex (host array of device pointers
- * indexed by object id, as in rt_shade_backward), the object's full extent,
- * (w h or K) x n^2 texels of 4 FP32 values.  The clear that a step which
+ * indexed by object id, as in rt_shade_backward), the object's full extent in
+ * its storage layout, (P, w h or K) x n^2 texels of 4 FP32 values.  The clear that a step which
  * accumulates gradients (RT_ACCUMULATE) runs first; rt_shade_backward without
  * RT_ACCUMULATE does the same itself.  RT_ERR_INVALID_ARG for a dead object, a
  * buffer that is not 16-byte aligned or n_dtex outside [0, RT_MAX_OBJECTS]. */
@@ -569,9 +573,9 @@ rt_status rt_adam_step(float* param, const float* grad, float* m, float* v, int6
 
 
 /* Converts an FP32 4-channel texture buffer of w x h buckets of n x n texels
- * between layouts (device src and dst, which must not overlap; RT_LAYOUT_QUADS
- * only for even w and h): for instance a texel-gradient buffer of an owned
- * texture into the atlas. */
+ * between layouts (device src and dst, which must not overlap; the padding of
+ * a QUADS dst is not written): for instance a texel-gradient buffer of an
+ * owned texture into the atlas. */
 rt_status rt_convert_layout(const float* src, rt_layout src_layout, float* dst, rt_layout dst_layout, int32_t w,
                             int32_t h, int32_t n, rt_stream_t stream);
 

@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 
+import numpy as np
 import torch
 
 from . import _lib
@@ -81,11 +82,12 @@ def rt_context_destroy(ctx: Context) -> None:
 
 def rt_create_texture(ctx: Context, w: int, h: int, n: int, storage: int = RT_F32, src_layout: int = RT_LAYOUT_ATLAS,
                       src: torch.Tensor | None = None, flags: int = 0) -> int:
-    """src: FP32 CUDA tensor with w*h*n*n*4 elements in src_layout (or None).  Returns the object id."""
+    """src: FP32 CUDA tensor shaped by layout_shape(src_layout, w, h, n) (or None).  Returns the object id."""
     if src is not None:
         _check(src, "src", torch.float32)
-        if src.numel() != w * h * n * n * 4:
-            raise ValueError(f"src has {src.numel()} elements, expected {w * h * n * n * 4}")
+        want = layout_numel(src_layout, w, h, n)
+        if src.numel() != want:
+            raise ValueError(f"src has {src.numel()} elements, expected {want}")
     out = ctypes.c_int32(-1)
     _lib.call("rt_create_texture", ctx.handle, int(w), int(h), int(n), int(storage), int(src_layout), _ptr(src),
               int(flags), ctypes.byref(out))
@@ -252,13 +254,27 @@ def rt_texture_info(ctx: Context, obj_id: int) -> dict:
 
 def layout_shape(layout: int, w: int, h: int, n: int) -> tuple:
     """Tensor shape of a 4-channel texture buffer: atlas (h n, w n, 4); planes
-    (n, n, h, w, 4); quads (n, n, h/2, w/2, 2, 2, 4), i.e. (t, s, j/2, i/2, j mod 2,
-    i mod 2, channel)."""
+    (n, n, h, w, 4); quads (n, n, ceil(h/2), ceil(w/2), 2, 2, 4), i.e. (t, s, j // 2,
+    i // 2, j mod 2, i mod 2, channel), an odd side padded."""
     if layout == RT_LAYOUT_ATLAS:
         return (h * n, w * n, 4)
     if layout == RT_LAYOUT_QUADS:
-        return (n, n, h // 2, w // 2, 2, 2, 4)
+        return (n, n, (h + 1) // 2, (w + 1) // 2, 2, 2, 4)
     return (n, n, h, w, 4)
+
+
+def layout_numel(layout: int, w: int, h: int, n: int) -> int:
+    return int(np.prod(layout_shape(layout, w, h, n)))
+
+
+def storage_numel(ctx: Context, obj_id: int) -> int:
+    """Values (4 per texel) of a buffer in the object's storage layout: its texel
+    gradients (rt_shade_backward's dL_dtex) and its stored codes."""
+    info = rt_texture_info(ctx, obj_id)
+    K = rt_palette_size(ctx, obj_id)
+    if K:
+        return K * info["n"] ** 2 * 4
+    return layout_numel(info["layout"], info["w"], info["h"], info["n"])
 
 
 def rt_read_texture(ctx: Context, obj_id: int, dst_layout: int = RT_LAYOUT_ATLAS, stream=None):
@@ -275,7 +291,7 @@ def rt_read_texture(ctx: Context, obj_id: int, dst_layout: int = RT_LAYOUT_ATLAS
     shape = layout_shape(dst_layout, w, h, n)
     if fmt == RT_BIT1:  # one byte (0 or 1) per texel, no channels
         shape = shape[:-1]
-    codes = torch.empty(shape, dtype=CODE_DTYPE[fmt], device=dev)
+    codes = torch.zeros(shape, dtype=CODE_DTYPE[fmt], device=dev)  # the padding of quads stays zero
     scales = torch.empty((h, w), dtype=torch.float32, device=dev) if fmt == RT_E4M3_BUCKET_SCALE else None
     _lib.call("rt_read_texture", ctx.handle, int(obj_id), int(dst_layout), _ptr(codes), _ptr(scales),
               _stream(stream, dev))
@@ -393,10 +409,9 @@ def rt_zero_texture_grads(ctx: Context, dL_dtex: dict, stream=None) -> None:
     dev = None
     for o, t in dL_dtex.items():
         _check(t, f"dL_dtex[{o}]", torch.float32)
-        info = rt_texture_info(ctx, o)
-        buckets = rt_palette_size(ctx, o) or info["w"] * info["h"]
-        if t.numel() != buckets * info["n"] ** 2 * 4:
-            raise ValueError(f"dL_dtex[{o}] must hold (w h or K) n^2 x 4 floats")
+        want = storage_numel(ctx, o)
+        if t.numel() != want:
+            raise ValueError(f"dL_dtex[{o}] must hold {want} floats (the object's storage layout)")
         arr[o] = t.data_ptr()
         dev = t.device
     _lib.call("rt_zero_texture_grads", ctx.handle, arr, n_dtex, _stream(stream, dev))
@@ -509,10 +524,9 @@ def _grad_args(ctx, F, dL_dout, dL_dtex, dL_duv, dL_ddir, flags=0):
         dtype = torch.int64 if flags & RT_FIXED_POINT_GRADS else torch.float32
         for o, t in dL_dtex.items():
             _check(t, f"dL_dtex[{o}]", dtype)
-            info = rt_texture_info(ctx, o)
-            buckets = rt_palette_size(ctx, o) or info["w"] * info["h"]
-            if t.numel() != buckets * info["n"] ** 2 * 4:
-                raise ValueError(f"dL_dtex[{o}] must hold (w h or K) n^2 x 4 values")
+            want = storage_numel(ctx, o)
+            if t.numel() != want:
+                raise ValueError(f"dL_dtex[{o}] must hold {want} values (the object's storage layout)")
             arr[o] = t.data_ptr()
     return arr, n_dtex
 
@@ -649,13 +663,13 @@ def rt_footprint(ctx: Context, uv, dirs, obj, filter: int = RT_QUADRILINEAR, n_c
 def rt_convert_layout(src: torch.Tensor, src_layout: int, dst_layout: int, w: int, h: int, n: int,
                       dst: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     _check(src, "src", torch.float32)
-    if src.numel() != w * h * n * n * 4:
-        raise ValueError("src must hold w h n^2 x 4 floats")
-    if dst is None:
-        dst = torch.empty(layout_shape(dst_layout, w, h, n), dtype=torch.float32, device=src.device)
+    if src.numel() != layout_numel(src_layout, w, h, n):
+        raise ValueError("src must be shaped by layout_shape(src_layout, w, h, n)")
+    if dst is None:  # zeros: the padding of a quads buffer is not written
+        dst = torch.zeros(layout_shape(dst_layout, w, h, n), dtype=torch.float32, device=src.device)
     _check(dst, "dst", torch.float32)
-    if dst.numel() != src.numel():
-        raise ValueError("dst must hold as many floats as src")
+    if dst.numel() != layout_numel(dst_layout, w, h, n):
+        raise ValueError("dst must be shaped by layout_shape(dst_layout, w, h, n)")
     _lib.call("rt_convert_layout", _ptr(src), int(src_layout), _ptr(dst), int(dst_layout), int(w), int(h), int(n),
               _stream(stream, src.device))
     return dst

@@ -10,6 +10,7 @@
 
 #include "radtex.h"
 #include "rt_device.cuh"
+#include "rt_encode.cuh"
 #include "rt_internal.h"
 
 using rt::TexDesc;
@@ -214,10 +215,10 @@ void rt_context_destroy(rt_ctx* ctx) {
     delete ctx;
 }
 
-// Storage layout of an owned dense texture: 2 x 2 bucket quads when both sides
-// are even (bit textures keep the PLANES bit numbering).
-static rt_layout store_layout(int32_t w, int32_t h, rt_format storage) {
-    return (!(w & 1) && !(h & 1) && storage != RT_BIT1) ? RT_LAYOUT_QUADS : RT_LAYOUT_PLANES;
+// Storage layout of an owned dense texture: 2 x 2 bucket quads (an odd side
+// padded); bit textures keep the PLANES bit numbering.
+static rt_layout store_layout(rt_format storage) {
+    return storage != RT_BIT1 ? RT_LAYOUT_QUADS : RT_LAYOUT_PLANES;
 }
 
 // Creates a dense texture (K = 0) or a palette texture (K palette buckets
@@ -233,8 +234,7 @@ static rt_status create_object(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, int
         return RT_ERR_INVALID_ARG;
     if (src && !aligned16(src)) return RT_ERR_INVALID_ARG;
     const bool palette = K > 0;
-    // a QUADS source is a w x h texture with even sides (a palette's K x 1 source never is)
-    if (src_layout == RT_LAYOUT_QUADS && (palette || (w & 1) || (h & 1))) return RT_ERR_INVALID_ARG;
+    if (src_layout == RT_LAYOUT_QUADS && palette) return RT_ERR_INVALID_ARG;  // a palette source is K x 1 planes
     if (palette && (K > (1 << 30) || !index || !src)) return RT_ERR_INVALID_ARG;
     const bool borrow = (flags & RT_BORROW) != 0;
     if (borrow && (storage != RT_F32 || !src)) return RT_ERR_INVALID_ARG;
@@ -252,16 +252,19 @@ static rt_status create_object(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, int
     // src and index may have been written on any stream of the device.
     if (cudaDeviceSynchronize() != cudaSuccess) return RT_ERR_CUDA;
 
-    // the stored buckets: the w x h matrix, or the K x 1 palette
+    // the stored buckets: the w x h matrix (in quads: ceil(w/2) x ceil(h/2) of them), or the K x 1 palette
     const int32_t sw = palette ? K : w, sh = palette ? 1 : h;
-    const int64_t texels = (int64_t)sw * sh * n * n;
+    const int layout = palette ? (int)rt::kLayoutPalette : borrow ? (int)src_layout : (int)store_layout(storage);
+    const int64_t plane = palette ? (int64_t)K : rt::plane_buckets(layout, w, h);
+    const int64_t texels = plane * n * n;
     TexDesc d;
     std::memset(&d, 0, sizeof(d));
     d.W = w;
     d.H = h;
     d.n = n;
     d.fmt = (int8_t)storage;
-    d.plane = (int64_t)sw * sh;
+    d.layout = (int8_t)layout;
+    d.plane = plane;
     d.fW = (float)w;
     d.fH = (float)h;
     d.half_n = 0.5f * (float)n;
@@ -296,26 +299,21 @@ static rt_status create_object(rt_ctx* ctx, int32_t w, int32_t h, int32_t n, int
     }
     if (borrow) {
         d.base = src;
-        d.layout = (int8_t)(palette ? rt::kLayoutPalette : src_layout);
         ctx->bytes[o] = texels * 16;
     } else {
-        d.layout = (int8_t)(palette ? rt::kLayoutPalette : store_layout(w, h, storage));
         const int64_t bytes = storage_bytes(storage, texels);
         e = cudaMalloc(&storage_ptr, (size_t)bytes);
         if (e == cudaSuccess && storage == RT_E4M3_BUCKET_SCALE)
             e = cudaMalloc(&scale_ptr, sizeof(float) * (size_t)d.plane);
-        if (e == cudaSuccess) {
-            if (src) {
-                e = rt::launch_encode(src, src_layout, storage_ptr, scale_ptr, sw, sh, n, storage,
-                                      palette ? RT_LAYOUT_PLANES : d.layout, 0);
-            } else {
-                e = cudaMemset(storage_ptr, 0, (size_t)bytes);
-                if (e == cudaSuccess && scale_ptr) {
-                    std::vector<float> ones((size_t)d.plane, 1.0f);
-                    e = cudaMemcpy(scale_ptr, ones.data(), sizeof(float) * ones.size(), cudaMemcpyHostToDevice);
-                }
-            }
+        // zero codes and unit scales first: the padding of odd sides keeps them (no lookup reads it)
+        if (e == cudaSuccess && (!src || plane != (int64_t)sw * sh)) e = cudaMemset(storage_ptr, 0, (size_t)bytes);
+        if (e == cudaSuccess && scale_ptr) {
+            std::vector<float> ones((size_t)d.plane, 1.0f);
+            e = cudaMemcpy(scale_ptr, ones.data(), sizeof(float) * ones.size(), cudaMemcpyHostToDevice);
         }
+        if (e == cudaSuccess && src)
+            e = rt::launch_encode(src, src_layout, storage_ptr, scale_ptr, sw, sh, n, storage,
+                                  palette ? RT_LAYOUT_PLANES : layout, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) {
             cudaFree(storage_ptr);
@@ -409,7 +407,6 @@ rt_status rt_read_texture(rt_ctx* ctx, int32_t obj_id, rt_layout dst_layout, voi
     if (d.layout == RT_LAYOUT_ATLAS) return RT_ERR_UNSUPPORTED;
     const bool pal = d.layout == rt::kLayoutPalette;  // a palette reads as its K x 1 texture (PLANES)
     const int rw = pal ? (int)d.plane : d.W, rh = pal ? 1 : d.H;
-    if (dst_layout == RT_LAYOUT_QUADS && ((rw & 1) || (rh & 1))) return RT_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return RT_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
@@ -982,9 +979,7 @@ rt_status rt_footprint(rt_ctx* ctx, const float* uv, const float* dir, const int
 rt_status rt_convert_layout(const float* src, rt_layout src_layout, float* dst, rt_layout dst_layout, int32_t w,
                             int32_t h, int32_t n, rt_stream_t stream) {
     if (!src || !dst || !aligned16(src) || !aligned16(dst) || w < 1 || h < 1 || n < 1) return RT_ERR_INVALID_ARG;
-    auto ok = [&](rt_layout l) {
-        return l == RT_LAYOUT_ATLAS || l == RT_LAYOUT_PLANES || (l == RT_LAYOUT_QUADS && !(w & 1) && !(h & 1));
-    };
+    auto ok = [](rt_layout l) { return l == RT_LAYOUT_ATLAS || l == RT_LAYOUT_PLANES || l == RT_LAYOUT_QUADS; };
     if (!ok(src_layout) || !ok(dst_layout))
         return RT_ERR_INVALID_ARG;
     return cuda_status(rt::launch_convert(src, src_layout, dst, dst_layout, w, h, n, (cudaStream_t)stream));

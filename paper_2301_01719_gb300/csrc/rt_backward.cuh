@@ -215,8 +215,10 @@ __device__ __forceinline__ CoordGrad backward_layout(const TexDesc& d, const Loo
 template <int FILTER, int FMT, bool DET>
 __device__ __forceinline__ CoordGrad backward_dense(const TexDesc& d, const Lookup<FILTER>& L, float4 g, void* grad,
                                                     bool coord_grads) {
+    // as filter_dense: owned textures QUADS (bits PLANES), borrowed FP32 buffers QUADS or PLANES
     if (d.layout == kLayoutPalette) return backward_layout<FILTER, FMT, kLayoutPalette, DET>(d, L, g, grad, coord_grads);
-    if (FMT != RT_BIT1 && d.layout == RT_LAYOUT_QUADS)
+    if (FMT == RT_BIT1) return backward_layout<FILTER, FMT, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
+    if (FMT != RT_F32 || d.layout == RT_LAYOUT_QUADS)
         return backward_layout<FILTER, FMT, RT_LAYOUT_QUADS, DET>(d, L, g, grad, coord_grads);
     return backward_layout<FILTER, FMT, RT_LAYOUT_PLANES, DET>(d, L, g, grad, coord_grads);
 }

@@ -254,9 +254,10 @@ __device__ __forceinline__ Lookup<FILTER> locate_world(const TexDesc& d, float u
 // (plane = K) reached through the index map, bucket (i, j) -> index[j w + i].
 constexpr int kLayoutPalette = 2;
 
-// Offset of bucket (i, j) in its 2 x 2 quad order (RT_LAYOUT_QUADS, w and h even).
+// Offset of bucket (i, j) in the 2 x 2 quad order of RT_LAYOUT_QUADS: a plane
+// holds ceil(w/2) x ceil(h/2) quads (an odd side is padded).
 __device__ __forceinline__ int quad_slot(int W, int i, int j) {
-    return (((j >> 1) * (W >> 1) + (i >> 1)) << 2) + ((j & 1) << 1) + (i & 1);
+    return (((j >> 1) * ((W + 1) >> 1) + (i >> 1)) << 2) + ((j & 1) << 1) + (i & 1);
 }
 
 // Spatial offset of bucket (i, j) inside a direction plane.

@@ -20,32 +20,23 @@ __device__ __forceinline__ void planes_coords(int64_t idx, int W, int H, int n, 
     s = (int)(p - (int64_t)t * n);
 }
 
-// (i, j, s, t) of texel `idx` of a PLANES or QUADS buffer.
-__device__ __forceinline__ void storage_coords(int layout, int64_t idx, int W, int H, int n, int& i, int& j, int& s,
-                                               int& t) {
-    if (layout != RT_LAYOUT_QUADS) {
-        planes_coords(idx, W, H, n, i, j, s, t);
-        return;
-    }
-    const int64_t plane = (int64_t)W * H;
-    const int64_t p = idx / plane;
-    const int r = (int)(idx - p * plane), q = r >> 2, wq = W >> 1;
-    const int jq = q / wq;
-    i = 2 * (q - jq * wq) + (r & 1);
-    j = 2 * jq + ((r >> 1) & 1);
-    t = (int)(p / n);
-    s = (int)(p - (int64_t)t * n);
+// Buckets per direction plane of a PLANES buffer (w h) or a QUADS buffer
+// (4 ceil(w/2) ceil(h/2): an odd side is padded to even).
+__host__ __device__ __forceinline__ int64_t plane_buckets(int layout, int W, int H) {
+    if (layout == RT_LAYOUT_QUADS) return 4 * (int64_t)((W + 1) >> 1) * ((H + 1) >> 1);
+    return (int64_t)W * H;
 }
 
 // Offset of bucket (i, j) inside a direction plane of a PLANES or QUADS buffer.
 __host__ __device__ __forceinline__ int64_t slot_in(int layout, int W, int i, int j) {
-    if (layout == RT_LAYOUT_QUADS) return ((int64_t)(j >> 1) * (W >> 1) + (i >> 1)) * 4 + ((j & 1) << 1) + (i & 1);
+    if (layout == RT_LAYOUT_QUADS)
+        return ((int64_t)(j >> 1) * ((W + 1) >> 1) + (i >> 1)) * 4 + ((j & 1) << 1) + (i & 1);
     return (int64_t)j * W + i;
 }
 
 __device__ __forceinline__ int64_t index_in(int layout, int W, int H, int n, int i, int j, int s, int t) {
     if (layout == RT_LAYOUT_PLANES || layout == RT_LAYOUT_QUADS)
-        return ((int64_t)t * n + s) * ((int64_t)W * H) + slot_in(layout, W, i, j);
+        return ((int64_t)t * n + s) * plane_buckets(layout, W, H) + slot_in(layout, W, i, j);
     return ((int64_t)j * n + t) * ((int64_t)W * n) + (int64_t)i * n + s;
 }
 

@@ -100,13 +100,14 @@ __device__ __forceinline__ float4 filter_taps(const TexDesc& d, const Lookup<FIL
     }
 }
 
-// Dispatch on the object's storage format and layout (owned textures are
-// QUADS, PLANES or palettes; a borrowed FP32 buffer may be ATLAS, PLANES or
-// QUADS).
+// Dispatch on the object's storage format and layout: owned textures are
+// QUADS (bit textures PLANES) or palettes; only a borrowed buffer, always
+// FP32, may also be ATLAS or PLANES.
 template <int FILTER, int FMT>
 __device__ __forceinline__ float4 filter_dense(const TexDesc& d, const Lookup<FILTER>& L) {
     if (d.layout == kLayoutPalette) return filter_taps<FILTER, FMT, kLayoutPalette>(d, L);
-    if (FMT != RT_BIT1 && d.layout == RT_LAYOUT_QUADS) return filter_taps<FILTER, FMT, RT_LAYOUT_QUADS>(d, L);
+    if (FMT == RT_BIT1) return filter_taps<FILTER, FMT, RT_LAYOUT_PLANES>(d, L);
+    if (FMT != RT_F32 || d.layout == RT_LAYOUT_QUADS) return filter_taps<FILTER, FMT, RT_LAYOUT_QUADS>(d, L);
     return filter_taps<FILTER, FMT, RT_LAYOUT_PLANES>(d, L);
 }
 

@@ -13,20 +13,21 @@ constexpr int kThreads = 256;
 static inline unsigned blocks_for(int64_t items) { return (unsigned)((items + kThreads - 1) / kThreads); }
 
 // FP32 source (any layout) -> FP32 / FP16 / BF16 storage in dst_layout (PLANES
-// or QUADS), one thread per stored texel.
+// or QUADS), one thread per texel (the padding of a QUADS buffer is not written).
 __global__ void encode_elementwise(const float4* __restrict__ src, int src_layout, void* __restrict__ dst,
                                    int dst_layout, int W, int H, int n, int fmt, int64_t total) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
     int i, j, s, t;
-    storage_coords(dst_layout, idx, W, H, n, i, j, s, t);
-    float4 v = src[index_in(src_layout, W, H, n, i, j, s, t)];
+    planes_coords(idx, W, H, n, i, j, s, t);
+    const float4 v = src[index_in(src_layout, W, H, n, i, j, s, t)];
+    const int64_t o = index_in(dst_layout, W, H, n, i, j, s, t);
     if (fmt == RT_F32)
-        reinterpret_cast<float4*>(dst)[idx] = v;
+        reinterpret_cast<float4*>(dst)[o] = v;
     else if (fmt == RT_F16)
-        reinterpret_cast<uint2*>(dst)[idx] = pack_f16(v);
+        reinterpret_cast<uint2*>(dst)[o] = pack_f16(v);
     else
-        reinterpret_cast<uint2*>(dst)[idx] = pack_bf16(v);
+        reinterpret_cast<uint2*>(dst)[o] = pack_bf16(v);
 }
 
 // FP32 source -> E4M3 + per-bucket scale (stored at the bucket's slot of
@@ -82,15 +83,16 @@ cudaError_t launch_encode(const float* src, int src_layout, void* dst, float* sc
     return cudaGetLastError();
 }
 
-// Stored codes (src_layout: PLANES or QUADS) -> codes in dst_layout; T is the per-texel code type.
+// Stored codes (src_layout: PLANES or QUADS) -> codes in dst_layout; T is the
+// per-texel code type; one thread per texel (padding is not written).
 template <typename T>
 __global__ void read_codes(const T* __restrict__ src, int src_layout, T* __restrict__ dst, int W, int H, int n,
                            int dst_layout, int64_t total) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
     int i, j, s, t;
-    storage_coords(src_layout, idx, W, H, n, i, j, s, t);
-    dst[index_in(dst_layout, W, H, n, i, j, s, t)] = src[idx];
+    planes_coords(idx, W, H, n, i, j, s, t);
+    dst[index_in(dst_layout, W, H, n, i, j, s, t)] = src[index_in(src_layout, W, H, n, i, j, s, t)];
 }
 
 // Per-bucket scales stored at their slots of src_layout -> row-major h x w.

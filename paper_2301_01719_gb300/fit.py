@@ -6,11 +6,10 @@ lookup is for.  A step is: forward synthesis of every view, the L2 loss and its
 gradient and the backward pass into the texel gradients, fused into one launch
 (rt_shade_batched_l2_step), then an Adam update (rt_adam_step) -- all in
 libradtex's kernels, on the FP32 texture the context borrows (RT_BORROW) in
-the layout the library gives owned textures (2 x 2 bucket quads when both sides
-are even, planes otherwise).  Checkpoints hold the texture, the
-Adam moments, the step count and a hash of the configuration; with
-deterministic=True (fixed-point texel gradients) a run resumed from a
-checkpoint is bit-identical to an uninterrupted one.
+the layout the library gives owned textures (2 x 2 bucket quads).  Checkpoints
+hold the texture, the Adam moments, the step count and a hash of the
+configuration; with deterministic=True (fixed-point texel gradients) a run
+resumed from a checkpoint is bit-identical to an uninterrupted one.
 
 Data-parallel fitting: with a torch.distributed process group, every rank
 holds the whole texture (replicated) and a shard of the target views
@@ -73,8 +72,8 @@ class TextureFit:
         self.w, self.h, self.n = int(w), int(h), int(n)
         self.lr, self.betas, self.eps, self.filt = float(lr), tuple(betas), float(eps), int(filt)
         self.deterministic = bool(deterministic)
-        # the owned textures' layout: 2 x 2 bucket quads when both sides are even
-        self.layout = api.RT_LAYOUT_QUADS if (w % 2 == 0 and h % 2 == 0) else api.RT_LAYOUT_PLANES
+        # the owned textures' layout: 2 x 2 bucket quads (an odd side padded)
+        self.layout = api.RT_LAYOUT_QUADS
         self.tex = torch.full(api.layout_shape(self.layout, w, h, n), float(init), dtype=torch.float32, device=dev)
         self.oid = api.rt_create_texture(ctx, w, h, n, api.RT_F32, self.layout, self.tex, api.RT_BORROW)
         self.grad = torch.zeros_like(self.tex)
@@ -83,7 +82,7 @@ class TextureFit:
         self.step_count = 0
         self.sums = torch.zeros(2, dtype=torch.float64, device=dev)
         # deterministic mode: the fixed-point texel sums (4 int64 per texel), reduced over ranks as integers
-        self.grad_fixed = torch.zeros((n, n, h, w, 4), dtype=torch.int64, device=dev) if self.deterministic else None
+        self.grad_fixed = torch.zeros(self.tex.shape, dtype=torch.int64, device=dev) if self.deterministic else None
 
     def config(self) -> dict:
         return {"w": self.w, "h": self.h, "n": self.n, "lr": self.lr, "betas": list(self.betas), "eps": self.eps,

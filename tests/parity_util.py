@@ -33,19 +33,27 @@ def atlas_to_planes(a: np.ndarray, W: int, H: int, n: int) -> np.ndarray:
     return a.reshape(H, n, W, n, 4).transpose(1, 3, 0, 2, 4).copy()
 
 
-# RT_LAYOUT_QUADS, written out from its definition: texel (i, j, s, t) at
-# (t n + s) w h + 4 ((j // 2)(w // 2) + i // 2) + 2 (j % 2) + i % 2, i.e. the
-# C-order array (t, s, j // 2, i // 2, j % 2, i % 2, channel).
+# RT_LAYOUT_QUADS, written out from its definition: a plane holds
+# wq hq quads, wq = ceil(w / 2), hq = ceil(h / 2) (an odd side padded), and
+# texel (i, j, s, t) lies at (t n + s) 4 wq hq + 4 ((j // 2) wq + i // 2) +
+# 2 (j % 2) + i % 2, i.e. the C-order array (t, s, j // 2, i // 2, j % 2, i % 2, channel).
 
 def quads_to_atlas(t: np.ndarray, W: int, H: int, n: int) -> np.ndarray:
-    """(n, n, h/2, w/2, 2, 2, k) -> (h n, w n, k): row j n + t = (2 jq + jr) n + t, column (2 iq + ir) n + s."""
-    k = t.size // (W * H * n * n)
-    return t.reshape(n, n, H // 2, W // 2, 2, 2, k).transpose(2, 4, 0, 3, 5, 1, 6).reshape(H * n, W * n, k)
+    """(n, n, hq, wq, 2, 2, k) -> (h n, w n, k): row j n + t = (2 jq + jr) n + t,
+    column (2 iq + ir) n + s; the padding is dropped."""
+    wq, hq = (W + 1) // 2, (H + 1) // 2
+    k = t.size // (4 * wq * hq * n * n)
+    a = t.reshape(n, n, hq, wq, 2, 2, k).transpose(2, 4, 0, 3, 5, 1, 6).reshape(2 * hq * n, 2 * wq * n, k)
+    return a[: H * n, : W * n]
 
 
 def atlas_to_quads(a: np.ndarray, W: int, H: int, n: int) -> np.ndarray:
+    """(h n, w n, k) -> (n, n, hq, wq, 2, 2, k), the padding zero."""
+    wq, hq = (W + 1) // 2, (H + 1) // 2
     k = a.size // (W * H * n * n)
-    return a.reshape(H // 2, 2, n, W // 2, 2, n, k).transpose(2, 5, 0, 3, 1, 4, 6).copy()
+    p = np.zeros((2 * hq * n, 2 * wq * n, k), a.dtype)
+    p[: H * n, : W * n] = a.reshape(H * n, W * n, k)
+    return p.reshape(hq, 2, n, wq, 2, n, k).transpose(2, 5, 0, 3, 1, 4, 6).copy()
 
 
 def storage_to_atlas(t: np.ndarray, layout: int, W: int, H: int, n: int) -> np.ndarray:
@@ -63,11 +71,11 @@ def atlas_to_storage(a: np.ndarray, layout: int, W: int, H: int, n: int) -> np.n
 
 def storage_index(layout: int, W: int, H: int, n: int, i, j, s, t):
     """Flat texel index of (i, j, s, t) in a PLANES or QUADS buffer (numpy arrays or ints)."""
-    plane = (np.asarray(t, np.int64) * n + s) * (W * H)
     if layout == api.RT_LAYOUT_QUADS:
+        wq, hq = (W + 1) // 2, (H + 1) // 2
         i, j = np.asarray(i, np.int64), np.asarray(j, np.int64)
-        return plane + 4 * ((j // 2) * (W // 2) + i // 2) + 2 * (j % 2) + i % 2
-    return plane + np.asarray(j, np.int64) * W + i
+        return (np.asarray(t, np.int64) * n + s) * (4 * wq * hq) + 4 * ((j // 2) * wq + i // 2) + 2 * (j % 2) + i % 2
+    return (np.asarray(t, np.int64) * n + s) * (W * H) + np.asarray(j, np.int64) * W + i
 
 
 def grad_to_atlas(ctx, oid: int, t) -> np.ndarray:

@@ -114,7 +114,8 @@ def test_max_size_texture(ctx, W, H, n):
     rng = np.random.default_rng(5)
     g = rng.normal(size=(SIDE * SIDE, 4)).astype(np.float32)
     t_g = torch.from_numpy(g).to(dev).view(*shape, 4)
-    dtex = torch.empty((n, n, H, W, 4), dtype=torch.float32, device=dev)
+    dtex = torch.empty(api.layout_shape(api.rt_texture_info(ctx, oid)["layout"], W, H, n), dtype=torch.float32,
+                       device=dev)
     duv = torch.empty_like(t_uv)
     ddir = torch.empty_like(t_d)
     api.rt_shade_batched_backward(ctx, t_uv, t_d, t_o, api.RT_QUADRILINEAR, t_g, {oid: dtex}, duv, ddir)

@@ -57,7 +57,7 @@ def test_encoders_bit_exact(ctx, fmt):
         np.testing.assert_array_equal(got.view(T.codes.dtype), T.codes)
     if fmt == api.RT_E4M3_BUCKET_SCALE:
         np.testing.assert_array_equal(scales.cpu().numpy().view(np.uint32), T.scales.view(np.uint32))
-    # stored in 2 x 2 bucket quads (even w, h); planes and quads read-backs are the same codes, permuted
+    # stored in 2 x 2 bucket quads; planes and quads read-backs are the same codes, permuted
     assert api.rt_texture_info(ctx, oid)["layout"] == api.RT_LAYOUT_QUADS
     pc, _ = api.rt_read_texture(ctx, oid, api.RT_LAYOUT_PLANES)
     np.testing.assert_array_equal(planes_to_atlas(pc.cpu().numpy(), W, H, n), got)
@@ -67,35 +67,42 @@ def test_encoders_bit_exact(ctx, fmt):
     api.rt_destroy_texture(ctx, oid)
 
 
-def test_storage_layout_follows_the_sides(ctx):
-    """Owned textures with even sides are stored in quads, others in planes; a
-    quads source or read-back needs even sides; conversions agree with the
-    definition of each layout."""
-    for (W, H), want in (((6, 4), api.RT_LAYOUT_QUADS), ((5, 4), api.RT_LAYOUT_PLANES),
-                         ((6, 3), api.RT_LAYOUT_PLANES)):
-        oid = api.rt_create_texture(ctx, W, H, 3, api.RT_F16)
-        assert api.rt_texture_info(ctx, oid)["layout"] == want
-        if want == api.RT_LAYOUT_PLANES:
-            with pytest.raises(api.RadtexError):
-                api.rt_read_texture(ctx, oid, api.RT_LAYOUT_QUADS)
-        api.rt_destroy_texture(ctx, oid)
+def test_owned_textures_are_stored_in_quads(ctx):
+    """Owned dense textures are stored in 2 x 2 bucket quads, an odd side padded
+    (zero codes there), bit textures in planes; read-backs and conversions agree
+    with the definition of each layout at even and odd sides; a borrowed quads
+    buffer shades like the owned texture."""
+    W, H, n = 5, 3, 4
+    a = np.random.default_rng(4).normal(size=(H * n, W * n, 4)).astype(np.float32)
+    oid, _ = _new_texture(ctx, a, W, H, n, api.RT_F32)
+    info = api.rt_texture_info(ctx, oid)
+    assert info["layout"] == api.RT_LAYOUT_QUADS
+    assert info["bytes"] == 16 * 4 * 3 * 2 * n * n  # 3 x 2 quads of 4 buckets per plane
+    qc, _ = api.rt_read_texture(ctx, oid, api.RT_LAYOUT_QUADS)
+    want = atlas_to_storage(a, api.RT_LAYOUT_QUADS, W, H, n)  # zero padding
+    np.testing.assert_array_equal(qc.cpu().numpy(), want)
     bits = api.rt_create_texture(ctx, 8, 8, 2, api.RT_BIT1)  # bit textures keep the planes bit numbering
     assert api.rt_texture_info(ctx, bits)["layout"] == api.RT_LAYOUT_PLANES
     api.rt_destroy_texture(ctx, bits)
-    with pytest.raises(api.RadtexError):
-        api.rt_create_texture(ctx, 5, 4, 3, api.RT_F32, api.RT_LAYOUT_QUADS,
-                              to_dev(np.zeros((3, 3, 4, 5, 4), np.float32)))
-    W, H, n = 10, 6, 3
-    a = np.random.default_rng(4).normal(size=(H * n, W * n, 4)).astype(np.float32)
-    for src_l in (api.RT_LAYOUT_ATLAS, api.RT_LAYOUT_PLANES, api.RT_LAYOUT_QUADS):
-        for dst_l in (api.RT_LAYOUT_ATLAS, api.RT_LAYOUT_PLANES, api.RT_LAYOUT_QUADS):
-            src = to_dev(a if src_l == api.RT_LAYOUT_ATLAS else atlas_to_storage(a, src_l, W, H, n))
-            out = api.rt_convert_layout(src, src_l, dst_l, W, H, n).cpu().numpy()
-            want = a if dst_l == api.RT_LAYOUT_ATLAS else atlas_to_storage(a, dst_l, W, H, n)
-            np.testing.assert_array_equal(out.reshape(-1), want.reshape(-1))
-    with pytest.raises(api.RadtexError):  # odd h: the library rejects a quads buffer
-        api.rt_convert_layout(to_dev(np.zeros((5 * 3, 4 * 3, 4), np.float32)), api.RT_LAYOUT_ATLAS,
-                              api.RT_LAYOUT_QUADS, 4, 5, 3, dst=to_dev(np.zeros(4 * 5 * 9 * 4, np.float32)))
+    for W2, H2 in ((10, 6), (5, 3), (1, 1)):
+        b = np.random.default_rng(W2).normal(size=(H2 * n, W2 * n, 4)).astype(np.float32)
+        for src_l in (api.RT_LAYOUT_ATLAS, api.RT_LAYOUT_PLANES, api.RT_LAYOUT_QUADS):
+            for dst_l in (api.RT_LAYOUT_ATLAS, api.RT_LAYOUT_PLANES, api.RT_LAYOUT_QUADS):
+                src = to_dev(b if src_l == api.RT_LAYOUT_ATLAS else atlas_to_storage(b, src_l, W2, H2, n))
+                out = api.rt_convert_layout(src, src_l, dst_l, W2, H2, n).cpu().numpy()
+                want = b if dst_l == api.RT_LAYOUT_ATLAS else atlas_to_storage(b, dst_l, W2, H2, n)
+                np.testing.assert_array_equal(out.reshape(-1), want.reshape(-1))
+    # the same texels borrowed as a padded quads buffer shade bit for bit like the owned texture
+    g = synth.quad_scene(1009, 64, 64)
+    uv, d, o = gbuffer_to_dev(g)
+    bid, keep = _new_texture(ctx, a, W, H, n, api.RT_F32, api.RT_LAYOUT_QUADS, api.RT_BORROW)
+    for filt in FILTERS:
+        own = api.rt_shade(ctx, uv, d, torch.where(o >= 0, torch.full_like(o, oid), o), filt)
+        bor = api.rt_shade(ctx, uv, d, torch.where(o >= 0, torch.full_like(o, bid), o), filt)
+        assert torch.equal(own, bor)
+    assert api.rt_get_error(ctx) == api.RT_OK
+    api.rt_destroy_texture(ctx, bid)
+    api.rt_destroy_texture(ctx, oid)
 
 
 @pytest.mark.parametrize("filt", FILTERS)
@@ -387,8 +394,9 @@ def _kink_mask(table, g, obj, filt, W, H, n, margin=1e-3):
 
 @pytest.mark.parametrize("fmt", [api.RT_F32, api.RT_F16, api.RT_E4M3_BUCKET_SCALE])
 @pytest.mark.parametrize("filt", FILTERS)
-def test_backward_matches_oracle(ctx, fmt, filt):
-    W, H, n = 64, 64, 8
+@pytest.mark.parametrize("W,H", [(64, 64), (37, 23)])  # quads, and quads with padded odd sides
+def test_backward_matches_oracle(ctx, fmt, filt, W, H):
+    n = 8
     atlas, g, T = quad_workload(fmt, W, H, n)
     oid, _ = _new_texture(ctx, atlas, W, H, n, fmt)
     obj_np = np.where(g.obj >= 0, oid, -1).astype(np.int32)
@@ -398,7 +406,8 @@ def test_backward_matches_oracle(ctx, fmt, filt):
     gout = rng.normal(size=(g.F, 4)).astype(np.float32)
     uv, d, _ = gbuffer_to_dev(g)
     o = to_dev(obj_np)
-    dtex = torch.empty((n, n, H, W, 4), dtype=torch.float32, device=dev())
+    dtex = torch.empty(api.layout_shape(api.rt_texture_info(ctx, oid)["layout"], W, H, n), dtype=torch.float32,
+                       device=dev())
     duv = torch.empty_like(uv)
     ddir = torch.empty_like(d)
     api.rt_shade_backward(ctx, uv, d, o, filt, to_dev(gout), {oid: dtex}, duv, ddir)
