@@ -102,9 +102,8 @@ __device__ __forceinline__ CoordGrad backward_quadrilinear_planes(const TexDesc&
     const int64_t p00 = (int64_t)(L.t.k0 * d.n + L.s.k0) * P;
     const int64_t ds = (int64_t)(L.s.k1 - L.s.k0) * P, dt = (int64_t)(L.t.k1 - L.t.k0) * d.n * P;
     const int64_t pl[4] = {p00, p00 + ds, p00 + dt, p00 + dt + ds};  // (s0,t0) (s1,t0) (s0,t1) (s1,t1)
-    const int o[4] = {bucket_slot<LAYOUT>(d, L.u.k0, L.v.k0), bucket_slot<LAYOUT>(d, L.u.k1, L.v.k0),
-                      bucket_slot<LAYOUT>(d, L.u.k0, L.v.k1),
-                      bucket_slot<LAYOUT>(d, L.u.k1, L.v.k1)};  // (u0,v0) (u1,v0) (u0,v1) (u1,v1)
+    int o[4];  // (u0,v0) (u1,v0) (u0,v1) (u1,v1)
+    bucket_slots4<LAYOUT>(d, L.u.k0, L.u.k1, L.v.k0, L.v.k1, o);
     reduce_quadrilinear_taps<DET>(d, L, pl, o, g, grad);
     CoordGrad cg = {0.f, 0.f, 0.f, 0.f};
     if (!coord_grads) return cg;

@@ -278,6 +278,30 @@ __device__ __forceinline__ int bucket_slot(const TexDesc& d, int i, int j) {
     return b;
 }
 
+// The spatial offsets of the 2 x 2 buckets (u0,v0) (u1,v0) (u0,v1) (u1,v1) of a
+// quadrilinear lookup.  The quad order is separable, slot(i, j) = a(j) + b(i)
+// with b(i) = 2 i - (i mod 2) and a(j) = 4 (j / 2) ceil(w / 2) + 2 (j mod 2), so
+// the four offsets cost two terms per axis and four additions.
+template <int LAYOUT>
+__device__ __forceinline__ void bucket_slots4(const TexDesc& d, int u0, int u1, int v0, int v1, int (&o)[4]) {
+#ifndef RADTEX_CHECKED
+    if constexpr (LAYOUT == RT_LAYOUT_QUADS) {
+        const int wq4 = ((d.W + 1) >> 1) << 2;
+        const int b0 = 2 * u0 - (u0 & 1), b1 = 2 * u1 - (u1 & 1);
+        const int a0 = (v0 >> 1) * wq4 + ((v0 & 1) << 1), a1 = (v1 >> 1) * wq4 + ((v1 & 1) << 1);
+        o[0] = a0 + b0;
+        o[1] = a0 + b1;
+        o[2] = a1 + b0;
+        o[3] = a1 + b1;
+        return;
+    }
+#endif
+    o[0] = bucket_slot<LAYOUT>(d, u0, v0);
+    o[1] = bucket_slot<LAYOUT>(d, u1, v0);
+    o[2] = bucket_slot<LAYOUT>(d, u0, v1);
+    o[3] = bucket_slot<LAYOUT>(d, u1, v1);
+}
+
 template <int LAYOUT>
 __device__ __forceinline__ int64_t texel_index(const TexDesc& d, int i, int j, int s, int t) {
     if (LAYOUT == RT_LAYOUT_ATLAS)

@@ -45,8 +45,8 @@ __device__ __forceinline__ P4 quadrilinear_planes(const TexDesc& d, const Axis& 
     const int64_t p00 = (int64_t)(T.k0 * d.n + S.k0) * P;
     const int64_t ds = (int64_t)(S.k1 - S.k0) * P, dt = (int64_t)(T.k1 - T.k0) * d.n * P;
     const int64_t pl[4] = {p00, p00 + ds, p00 + dt, p00 + dt + ds};
-    const int o[4] = {bucket_slot<LAYOUT>(d, U.k0, V.k0), bucket_slot<LAYOUT>(d, U.k1, V.k0),
-                      bucket_slot<LAYOUT>(d, U.k0, V.k1), bucket_slot<LAYOUT>(d, U.k1, V.k1)};
+    int o[4];
+    bucket_slots4<LAYOUT>(d, U.k0, U.k1, V.k0, V.k1, o);
     float sc[4] = {1.f, 1.f, 1.f, 1.f};
     if (FMT == RT_E4M3_BUCKET_SCALE) {
 #pragma unroll
