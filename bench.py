@@ -54,6 +54,8 @@ def parse_args(argv=None):
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fused-line", action="store_true",
+                   help="skip timing the fused step beside the separate kernels")
     p.add_argument("--no-precision", action="store_true",
                    help="skip the storage formats' error against FP32 storage on the step's frames")
     p.add_argument("--samples", type=int, default=4, help="shadow: light samples per fragment")
@@ -610,6 +612,46 @@ def run_radtex(a):
     if st != api.RT_OK:
         raise RuntimeError(f"device status after timing: {api.rt_status_string(st)}")
 
+    # The same step as one fused launch (forward, dL/dout = out - 0, backward), timed
+    # after the separate kernels on the same inputs: reported beside them.
+    fused_step = None
+    if not a.fused and not a.no_fused_line:
+        f_target = torch.zeros_like(out)
+        f_sums = torch.zeros(2, dtype=torch.float64, device=dev)
+
+        def fstep():
+            api.rt_zero_texture_grads(ctx, dtex)
+            api.rt_shade_batched_l2_step(ctx, uv, dirs, obj, filt, f_target, 1.0, out, f_sums, dtex, duv, ddir,
+                                         api.RT_ACCUMULATE_TEXELS)
+
+        for _ in range(a.warmup):
+            fstep()
+        f_steps = min(a.steps, 20)
+        fev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(f_steps)]
+        torch.cuda.synchronize()
+        with ClockSampler(local) as fclk:
+            fclk.mark_start()
+            for e in fev:
+                e[0].record(stream)
+                api.rt_zero_texture_grads(ctx, dtex)
+                e[1].record(stream)
+                api.rt_shade_batched_l2_step(ctx, uv, dirs, obj, filt, f_target, 1.0, out, f_sums, dtex, duv, ddir,
+                                             api.RT_ACCUMULATE_TEXELS)
+                e[2].record(stream)
+            torch.cuda.synchronize()
+            fclk.mark_end()
+        if api.rt_get_error(ctx) != api.RT_OK:
+            raise RuntimeError("device status after the fused step")
+        f_ms = max_over_ranks(float(np.mean([e[0].elapsed_time(e[2]) for e in fev])), dev)
+        f_kernel_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in fev]))
+        fused_step = {"step": "rt_zero_texture_grads + rt_shade_batched_l2_step(target 0, scale 1, "
+                              "RT_ACCUMULATE_TEXELS): the same gradients in one launch",
+                      "value": whole_job_rate(F, world, f_ms), "unit": "Gfrag/s", "ms_per_step": f_ms,
+                      "steps": f_steps, "fused_ms": f_kernel_ms,
+                      "zero_grad_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in fev])),
+                      "clocks": fclk.summary()}
+        del f_target
+
     # End to end through the public API with host buffers: every step copies the
     # G-buffer from pinned host memory and the image back.  The step is pipelined
     # over chunks of views on three streams: the copy of chunk k+1 in, the shading
@@ -694,6 +736,9 @@ def run_radtex(a):
         r_fwd = roof(fwd_gbs, f"shade_kernel<{a.filter}, tiled>", fwd_bytes)
         r_bwd = roof(bwd_gbs, f"backward_kernel<{a.filter}, tiled>", bwd_bytes)
         dominant = r_bwd if bwd_ms >= fwd_ms else r_fwd
+    if fused_step is not None:
+        fused_step["roofline"] = roof(fused_bytes / (fused_step["fused_ms"] * 1e-3) / 1e9,
+                                      f"fused_l2_kernel<{a.filter}, tiled>", fused_bytes)
 
     result = {
         "metric": METRIC, "value": value, "unit": "Gfrag/s", "n_gpus": world, "steps": a.steps,
@@ -722,6 +767,8 @@ def run_radtex(a):
         "clocks": clk.summary(),
         "e2e": e2e,
     }
+    if fused_step is not None:
+        result["fused_step"] = fused_step
     if not a.no_precision and not a.palette:
         result["precision_vs_fp32"] = precision_vs_fp32(a, api, local, uv, dirs, obj, filt, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
