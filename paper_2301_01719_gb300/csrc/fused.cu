@@ -14,13 +14,15 @@
 
 namespace rt {
 
-// Held to 128 registers (4 blocks, 16 warps per SM; it compiles to 104 without
-// spills): at 5 blocks (96 registers) the kernel took 5.86 ms against 5.65 ms,
-// at 6 blocks (80, spilling) 6.21 ms, on the 60-pose 1080p step (textures in
-// row-major planes then).  A variant that gathers the 16 taps once (the
-// colour-derivative vectors formed from the forward's lerps and projected on
-// dL/dout) needs far more registers and measured slower at every occupancy
-// (7.0 ms at best against 6.4 ms then).
+// Held to 128 registers (4 blocks, 16 warps per SM): at 5 blocks (96
+// registers) the kernel took 5.86 ms against 5.65 ms, at 6 blocks (80,
+// spilling) 6.21 ms, on the 60-pose 1080p step (textures in row-major planes
+// then).  With FP16 / BF16 quadrilinear textures the 16 taps' 8-byte codes are
+// gathered once and kept in registers (118, no spills) for the coordinate
+// gradients instead of being reloaded from L1: 5.15 -> 5.03 ms.  A variant that
+// forms colour-derivative vectors from the forward's lerps needs far more
+// registers and measured slower at every occupancy (7.0 ms at best against
+// 6.4 ms then).
 template <int FILTER, bool DET, int SPEC>
 __global__ void __launch_bounds__(kBackThreads, (!DET && SPEC >= 0) ? 4 : 1) fused_l2_kernel(
     const TexDesc* __restrict__ table, int n_obj, const float* __restrict__ uv, const float* __restrict__ dir,
@@ -36,10 +38,29 @@ __global__ void __launch_bounds__(kBackThreads, (!DET && SPEC >= 0) ? 4 : 1) fus
         float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
         TexDesc d;
         Lookup<FILTER> L;
+        // FP16 / BF16 quadrilinear: the 16 taps' codes stay in registers for the backward
+        constexpr bool kKeepTaps = FILTER == RT_QUADRILINEAR && !DET && (SPEC == RT_F16 || SPEC == RT_BF16);
+        constexpr int kSpec8 = kKeepTaps ? SPEC : RT_F16;
+        int64_t pl[4];
+        int o[4];
+        uint2 code[kKeepTaps ? 4 : 1][kKeepTaps ? 4 : 1];  // [bucket][texel]
         const bool valid = fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d);
         if (valid) {
             L = locate<FILTER, (SPEC < 0)>(d, q.u, q.v, q.x, q.y, q.z);
-            c = filter_spec<FILTER, SPEC>(d, L);
+            if constexpr (kKeepTaps) {
+                quad_tap_addresses<RT_LAYOUT_QUADS>(d, L.u, L.v, L.s, L.t, pl, o);
+                P4 tq[4][4];
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        code[b][k] = __ldg(reinterpret_cast<const uint2*>(d.base) + checked_texel(d, pl[k] + o[b]));
+                        tq[b][k] = decode8<kSpec8>(code[b][k]);
+                    }
+                c = toF4(quadrilinear_combine(tq, L.u, L.v, L.s, L.t));
+            } else {
+                c = filter_spec<FILTER, SPEC>(d, L);
+            }
         }
         // the colour and the loss are done with before the backward starts (shorter live ranges)
         if (f >= 0) {
@@ -56,7 +77,14 @@ __global__ void __launch_bounds__(kBackThreads, (!DET && SPEC >= 0) ? 4 : 1) fus
             const float4 g = make_float4(scale * (c.x - t.x), scale * (c.y - t.y), scale * (c.z - t.z),
                                          scale * (c.w - t.w));
             void* grad = any_grad ? grads.p[q.o] : nullptr;
-            CoordGrad cg = backward_spec<FILTER, DET, SPEC>(d, L, g, grad, coord_grads);
+            CoordGrad cg;
+            if constexpr (kKeepTaps) {
+                reduce_quadrilinear_taps<false>(d, L, pl, o, g, grad);
+                cg = CoordGrad{0.f, 0.f, 0.f, 0.f};
+                if (coord_grads) cg = quad_coord_grads(L, g, [&](int b, int k) { return decode8<kSpec8>(code[b][k]); });
+            } else {
+                cg = backward_spec<FILTER, DET, SPEC>(d, L, g, grad, coord_grads);
+            }
             coord_grads_of<FILTER>(d, L, q, cg, dL_ddir != nullptr, guv, gdir);
         }
         if (f < 0) return;

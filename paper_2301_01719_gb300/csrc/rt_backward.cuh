@@ -95,28 +95,21 @@ __device__ __forceinline__ void reduce_quadrilinear_taps(const TexDesc& d, const
     }
 }
 
-template <int FMT, int LAYOUT, bool DET>
-__device__ __forceinline__ CoordGrad backward_quadrilinear_planes(const TexDesc& d, const Lookup<RT_QUADRILINEAR>& L,
-                                                                  float4 g, void* grad, bool coord_grads) {
-    const int64_t P = d.plane;
-    const int64_t p00 = (int64_t)(L.t.k0 * d.n + L.s.k0) * P;
-    const int64_t ds = (int64_t)(L.s.k1 - L.s.k0) * P, dt = (int64_t)(L.t.k1 - L.t.k0) * d.n * P;
-    const int64_t pl[4] = {p00, p00 + ds, p00 + dt, p00 + dt + ds};  // (s0,t0) (s1,t0) (s0,t1) (s1,t1)
-    int o[4];  // (u0,v0) (u1,v0) (u0,v1) (u1,v1)
-    bucket_slots4<LAYOUT>(d, L.u.k0, L.u.k1, L.v.k0, L.v.k1, o);
-    reduce_quadrilinear_taps<DET>(d, L, pl, o, g, grad);
-    CoordGrad cg = {0.f, 0.f, 0.f, 0.f};
-    if (!coord_grads) return cg;
+// UV and in-bucket coordinate gradients of a quadrilinear lookup from its 16
+// taps, texel(b, k) giving tap (bucket b, texel k): each tap is projected on g
+// as it arrives and the lerps run on scalars.
+template <typename Texel>
+__device__ __forceinline__ CoordGrad quad_coord_grads(const Lookup<RT_QUADRILINEAR>& L, float4 g, Texel texel) {
+    CoordGrad cg;
     const f32x2 g_rg = pack2(g.x, g.y), g_ba = pack2(g.z, g.w);
     auto lerpf = [](float a, float b, float w) { return fmaf(w, b - a, a); };
     float c[4], cs[4], ct[4];
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-        const float sc = FMT == RT_E4M3_BUCKET_SCALE ? __ldg(d.scale + o[b]) : 1.0f;
         float p[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const P4 T = load_texelP<FMT>(d.base, checked_texel(d, pl[k] + o[b]), sc);
+            const P4 T = texel(b, k);
             f32x2 q;
             asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(q) : "l"(T.rg), "l"(g_rg));
             asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(q) : "l"(T.ba), "l"(g_ba), "l"(q));
@@ -133,6 +126,20 @@ __device__ __forceinline__ CoordGrad backward_quadrilinear_planes(const TexDesc&
     cg.gs = lerpf(lerpf(cs[0], cs[1], L.u.w), lerpf(cs[2], cs[3], L.u.w), L.v.w);
     cg.gt = lerpf(lerpf(ct[0], ct[1], L.u.w), lerpf(ct[2], ct[3], L.u.w), L.v.w);
     return cg;
+}
+
+template <int FMT, int LAYOUT, bool DET>
+__device__ __forceinline__ CoordGrad backward_quadrilinear_planes(const TexDesc& d, const Lookup<RT_QUADRILINEAR>& L,
+                                                                  float4 g, void* grad, bool coord_grads) {
+    int64_t pl[4];  // (s0,t0) (s1,t0) (s0,t1) (s1,t1)
+    int o[4];       // (u0,v0) (u1,v0) (u0,v1) (u1,v1)
+    quad_tap_addresses<LAYOUT>(d, L.u, L.v, L.s, L.t, pl, o);
+    reduce_quadrilinear_taps<DET>(d, L, pl, o, g, grad);
+    if (!coord_grads) return CoordGrad{0.f, 0.f, 0.f, 0.f};
+    return quad_coord_grads(L, g, [&](int b, int k) {
+        const float sc = FMT == RT_E4M3_BUCKET_SCALE ? __ldg(d.scale + o[b]) : 1.0f;
+        return load_texelP<FMT>(d.base, checked_texel(d, pl[k] + o[b]), sc);
+    });
 }
 
 template <int FILTER, int FMT, int LAYOUT, bool DET>

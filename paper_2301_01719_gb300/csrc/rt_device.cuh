@@ -411,12 +411,27 @@ __device__ __forceinline__ P4 load_texelP<RT_F32>(const void* base, int64_t idx,
     return {pack2(v.x, v.y), pack2(v.z, v.w)};
 }
 
+// The four channels of an 8-byte FP16 / BF16 code, widened to FP32 (exact).
+template <int FMT>
+__device__ __forceinline__ P4 decode8(uint2 r);
+
 template <>
-__device__ __forceinline__ P4 load_texelP<RT_F16>(const void* base, int64_t idx, float) {
-    uint2 r = __ldg(reinterpret_cast<const uint2*>(base) + idx);
+__device__ __forceinline__ P4 decode8<RT_F16>(uint2 r) {
     float2 fa = __half22float2(*reinterpret_cast<__half2*>(&r.x));
     float2 fb = __half22float2(*reinterpret_cast<__half2*>(&r.y));
     return {pack2(fa.x, fa.y), pack2(fb.x, fb.y)};
+}
+
+// BF16 is the upper half of an FP32: widening is a 16-bit shift (exact).
+template <>
+__device__ __forceinline__ P4 decode8<RT_BF16>(uint2 r) {
+    return {pack2(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xFFFF0000u)),
+            pack2(__uint_as_float(r.y << 16), __uint_as_float(r.y & 0xFFFF0000u))};
+}
+
+template <>
+__device__ __forceinline__ P4 load_texelP<RT_F16>(const void* base, int64_t idx, float) {
+    return decode8<RT_F16>(__ldg(reinterpret_cast<const uint2*>(base) + idx));
 }
 
 template <>
@@ -425,12 +440,9 @@ __device__ __forceinline__ P4 load_texelP<RT_BIT1>(const void* base, int64_t idx
     return {pack2(v, v), pack2(v, v)};
 }
 
-// BF16 is the upper half of an FP32: widening is a 16-bit shift (exact).
 template <>
 __device__ __forceinline__ P4 load_texelP<RT_BF16>(const void* base, int64_t idx, float) {
-    uint2 r = __ldg(reinterpret_cast<const uint2*>(base) + idx);
-    return {pack2(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xFFFF0000u)),
-            pack2(__uint_as_float(r.y << 16), __uint_as_float(r.y & 0xFFFF0000u))};
+    return decode8<RT_BF16>(__ldg(reinterpret_cast<const uint2*>(base) + idx));
 }
 
 template <>

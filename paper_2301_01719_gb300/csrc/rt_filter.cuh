@@ -38,15 +38,38 @@ __device__ __forceinline__ void load_quadP(const TexDesc& d, int i, int j, const
     t11 = load_texelP<FMT>(d.base, texel_index<LAYOUT>(d, i, j, s.k1, t.k1), sc);
 }
 
-template <int FMT, int LAYOUT>
-__device__ __forceinline__ P4 quadrilinear_planes(const TexDesc& d, const Axis& U, const Axis& V, const Axis& S,
-                                                  const Axis& T) {
+// The planes (64-bit bases, k = (s0,t0) (s1,t0) (s0,t1) (s1,t1)) and the spatial
+// offsets (b = (u0,v0) (u1,v0) (u0,v1) (u1,v1)) of a quadrilinear lookup's 16 taps
+// on a PLANES / QUADS / palette texture: tap (b, k) is texel pl[k] + o[b].
+template <int LAYOUT>
+__device__ __forceinline__ void quad_tap_addresses(const TexDesc& d, const Axis& U, const Axis& V, const Axis& S,
+                                                   const Axis& T, int64_t (&pl)[4], int (&o)[4]) {
     const int64_t P = d.plane;
     const int64_t p00 = (int64_t)(T.k0 * d.n + S.k0) * P;
     const int64_t ds = (int64_t)(S.k1 - S.k0) * P, dt = (int64_t)(T.k1 - T.k0) * d.n * P;
-    const int64_t pl[4] = {p00, p00 + ds, p00 + dt, p00 + dt + ds};
-    int o[4];
+    pl[0] = p00;
+    pl[1] = p00 + ds;
+    pl[2] = p00 + dt;
+    pl[3] = p00 + dt + ds;
     bucket_slots4<LAYOUT>(d, U.k0, U.k1, V.k0, V.k1, o);
+}
+
+// The colour of 16 taps q[bucket][texel]: lerps in s, t, then u, v.
+__device__ __forceinline__ P4 quadrilinear_combine(const P4 (&q)[4][4], const Axis& U, const Axis& V, const Axis& S,
+                                                   const Axis& T) {
+    const f32x2 ws = pack2(S.w, S.w), wt = pack2(T.w, T.w), wu = pack2(U.w, U.w), wv = pack2(V.w, V.w);
+    P4 c[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) c[b] = lerpP(lerpP(q[b][0], q[b][1], ws), lerpP(q[b][2], q[b][3], ws), wt);
+    return lerpP(lerpP(c[0], c[1], wu), lerpP(c[2], c[3], wu), wv);
+}
+
+template <int FMT, int LAYOUT>
+__device__ __forceinline__ P4 quadrilinear_planes(const TexDesc& d, const Axis& U, const Axis& V, const Axis& S,
+                                                  const Axis& T) {
+    int64_t pl[4];
+    int o[4];
+    quad_tap_addresses<LAYOUT>(d, U, V, S, T, pl, o);
     float sc[4] = {1.f, 1.f, 1.f, 1.f};
     if (FMT == RT_E4M3_BUCKET_SCALE) {
 #pragma unroll
@@ -57,11 +80,7 @@ __device__ __forceinline__ P4 quadrilinear_planes(const TexDesc& d, const Axis& 
     for (int b = 0; b < 4; ++b)
 #pragma unroll
         for (int k = 0; k < 4; ++k) q[b][k] = load_texelP<FMT>(d.base, checked_texel(d, pl[k] + o[b]), sc[b]);
-    const f32x2 ws = pack2(S.w, S.w), wt = pack2(T.w, T.w), wu = pack2(U.w, U.w), wv = pack2(V.w, V.w);
-    P4 c[4];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) c[b] = lerpP(lerpP(q[b][0], q[b][1], ws), lerpP(q[b][2], q[b][3], ws), wt);
-    return lerpP(lerpP(c[0], c[1], wu), lerpP(c[2], c[3], wu), wv);
+    return quadrilinear_combine(q, U, V, S, T);
 }
 
 template <int FILTER, int FMT, int LAYOUT>
