@@ -73,6 +73,8 @@ def parse_args(argv=None):
     p.add_argument("--palette-iters", type=int, default=4, help="Lloyd steps of the palette encoder")
     p.add_argument("--palette-fp32", action="store_true",
                    help="palette encoder: assign on the CUDA cores in FP32 instead of the tensor cores")
+    p.add_argument("--voronoi-backward", action="store_true",
+                   help="voronoi64: time the fused forward + loss + backward launch in the graph (the clear apart)")
     p.add_argument("--mem-fraction", type=float, default=0.7,
                    help="voronoi64: largest share of free device memory the textures may take")
     return p.parse_args(argv)
@@ -1251,7 +1253,11 @@ def run_voronoi(a):
     """Many objects in one launch: --objects textures of seeded uneven sizes, FP16,
     4 views of 3840x2160 whose pixels show the objects in Voronoi regions; the
     forward synthesis of all 33 M fragments is one persistent launch, captured in
-    a CUDA graph and replayed."""
+    a CUDA graph and replayed.  With --voronoi-backward the graph holds the fused
+    forward + L2 loss (zero target) + backward launch instead, adding into FP32
+    gradient buffers for every object (the textures shrink to leave room for
+    them); the clear of those buffers, dense and far larger than the texels one
+    step touches, is timed apart and reported beside it."""
     import torch
     from concurrent.futures import ThreadPoolExecutor
 
@@ -1266,8 +1272,11 @@ def run_voronoi(a):
     build.build()
     views, height, width = 4, 2160, 3840
     filt = api.FILTER_NAMES[a.filter]
+    backward = a.voronoi_backward
     sizes, ns = voronoi_objects(a.objects)
     need = int((sizes ** 2 * ns.astype(np.int64) ** 2 * 8).sum())
+    if backward:  # FP16 codes plus an FP32 gradient per texel
+        need *= 3
     free, total = torch.cuda.mem_get_info(dev)
     budget = a.mem_fraction * free
     scale = min(1.0, float(np.sqrt(budget / need)))
@@ -1299,14 +1308,35 @@ def run_voronoi(a):
         distinct += sum(api.rt_footprint(ctx, uv[v].reshape(-1, 2), dirs[v].reshape(-1, 3), obj[v].reshape(-1),
                                          filt, a.objects))
     fwd_bytes = 40 * F + distinct * 8
+    # the fused step: G-buffer and target in, colour and UV / direction gradients out, each texel
+    # read and its gradient read-modified-written once
+    step_bytes = (24 + 16 + 16 + 8 + 12) * F + distinct * (8 + 32) if backward else fwd_bytes
     tile, tile_ms = api.rt_autotune(ctx, uv, dirs, obj, filt, out, reps=3)
+    btile = None
+    if backward:
+        dtex = {o: torch.empty(api.storage_numel(ctx, o), dtype=torch.float32, device=dev) for o in oids}
+        duv = torch.empty((*shape, 2), dtype=torch.float32, device=dev)
+        ddir = torch.empty((*shape, 3), dtype=torch.float32, device=dev)
+        target = torch.zeros_like(out)
+        sums = torch.zeros(2, dtype=torch.float64, device=dev)
+        api.rt_zero_texture_grads(ctx, dtex)
+        btile, btile_ms = api.rt_autotune_backward(ctx, uv, dirs, obj, filt, out, dtex, duv, ddir,
+                                                   api.RT_ACCUMULATE, reps=2)
+
+    def launch(s):
+        if backward:
+            api.rt_shade_batched_l2_step(ctx, uv, dirs, obj, filt, target, 1.0, out, sums, dtex, duv, ddir,
+                                         api.RT_ACCUMULATE_TEXELS, stream=s)
+        else:
+            api.rt_shade_batched(ctx, uv, dirs, obj, filt, out, stream=s)
+
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
-        api.rt_shade_batched(ctx, uv, dirs, obj, filt, out, stream=stream)  # warm the launch path
+        launch(stream)  # warm the launch path
         stream.synchronize()
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=stream):
-            api.rt_shade_batched(ctx, uv, dirs, obj, filt, out, stream=stream)
+            launch(stream)
     for _ in range(a.warmup):
         graph.replay()
     torch.cuda.synchronize()
@@ -1323,15 +1353,31 @@ def run_voronoi(a):
         torch.cuda.synchronize()
         clk.mark_end()
     ms = e0.elapsed_time(e1) / a.steps
+    if api.rt_get_error(ctx) != api.RT_OK:
+        raise RuntimeError("device status after timing is not RT_OK")
+    clear_ms = None
+    if backward:  # the dense clear of every gradient buffer, as a step that clears would run it
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(cur)
+        for _ in range(3):
+            api.rt_zero_texture_grads(ctx, dtex)
+        c1.record(cur)
+        torch.cuda.synchronize()
+        clear_ms = c0.elapsed_time(c1) / 3
     peak, peak_kind = measured_peak()
-    achieved = fwd_bytes / (ms * 1e-3) / 1e9
+    achieved = step_bytes / (ms * 1e-3) / 1e9
     tex_bytes = int(sum(api.rt_texture_info(ctx, o)["bytes"] for o in oids))
     result = {
-        "metric": "radiance lookups/s (Gfrag/s), forward", "value": F / (ms * 1e-3) / 1e9, "unit": "Gfrag/s",
+        "metric": "radiance lookups/s (Gfrag/s), " + ("forward + backward launch" if backward else "forward"),
+        "value": F / (ms * 1e-3) / 1e9, "unit": "Gfrag/s",
         "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": (f"voronoi {a.objects} objects (buckets log-uniform 128..2048, n in 8..32, FP16), "
-                                f"4 x 3840x2160, {a.filter}, CUDA graph"),
+                                f"4 x 3840x2160, {a.filter}, CUDA graph"
+                                + (": fused forward, L2 loss, backward (texel gradients added)" if backward else "")),
+                   **({"backward_tile": {"tw": btile[0], "th": btile[1], "bx": btile[2], "by": btile[3]},
+                       "gradient_bytes": int(sum(t.numel() * 4 for t in dtex.values())),
+                       "gradient_clear_ms": clear_ms, "step_with_clear_ms": ms + clear_ms} if backward else {}),
                    "fragments_per_step": F, "objects": a.objects, "texture_bytes": tex_bytes,
                    "texture_bytes_uncapped": need, "bucket_scale_cap": scale,
                    "buckets_min_max": [int(sizes.min()), int(sizes.max())],
@@ -1340,8 +1386,9 @@ def run_voronoi(a):
                    "distinct_texels_per_step": int(distinct), "scene_gen_s": round(scene_s, 2),
                    "fill_s": round(fill_s, 2), "free_bytes_before": int(free)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_source": peak_kind, "algorithmic_bytes_per_launch": int(fwd_bytes),
-                     "kernel": f"shade_kernel<{a.filter}, tiled>"},
+                     "traffic": None, "peak_source": peak_kind, "algorithmic_bytes_per_launch": int(step_bytes),
+                     "kernel": (f"fused_l2_kernel<{a.filter}, tiled>" if backward
+                                else f"shade_kernel<{a.filter}, tiled>")},
         "gpu_launches": a.steps, "clocks": clk.summary(), "e2e": None,
     }
     print(json.dumps(result), flush=True)
