@@ -1222,7 +1222,7 @@ def run_variant(a):
                    "filter": a.filter, "fragments_per_step": F * world,
                    "l2": "inputs larger than L2 (G-buffer %.1f GB per rank)" % (nbytes / 1e9)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
+                     "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
                      "traffic": None, "peak_source": peak_kind, "algorithmic_bytes_per_step": int(nbytes),
                      "kernel": kernel},
         "gpu_launches": (1 if shadow else 2) * a.steps,
@@ -1389,7 +1389,7 @@ def run_voronoi(a):
                    "distinct_texels_per_step": int(distinct), "scene_gen_s": round(scene_s, 2),
                    "fill_s": round(fill_s, 2), "free_bytes_before": int(free)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
+                     "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
                      "traffic": None, "peak_source": peak_kind, "algorithmic_bytes_per_launch": int(step_bytes),
                      "kernel": (f"fused_l2_kernel<{a.filter}, tiled>" if backward
                                 else f"shade_kernel<{a.filter}, tiled>")},
