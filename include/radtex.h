@@ -596,11 +596,11 @@ rt_status rt_get_error(rt_ctx* ctx, rt_stream_t stream, rt_status* device_status
  * raised it are not meaningful.
  *
  * rt_checked_limit_extent lowers the extent that those checks allow for object
- * obj_id to `texels` (0 <= texels <= the object's texel count; larger values,
- * a bad id or a dead object give RT_ERR_INVALID_ARG) without touching the
- * storage, so that in-bounds accesses past it raise the error; it exists to
- * test the checks.  Synchronous.  The normal build returns RT_ERR_UNSUPPORTED
- * and checks nothing. */
+ * obj_id to `texels` (0 <= texels <= the object's stored texel count, P n^2 in
+ * quads; larger values, a bad id or a dead object give RT_ERR_INVALID_ARG)
+ * without touching the storage, so that in-bounds accesses past it raise the
+ * error; it exists to test the checks.  Synchronous.  The normal build returns
+ * RT_ERR_UNSUPPORTED and checks nothing. */
 rt_status rt_checked_limit_extent(rt_ctx* ctx, int32_t obj_id, int64_t texels);
 
 /* A static English description of a status code. */
