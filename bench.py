@@ -702,7 +702,8 @@ def run_radtex(a):
             comp.wait_stream(s_out)
             comp.wait_stream(s_in)
 
-        e2e_step()
+        for _ in range(2):  # the first steps also page in the pinned buffers' mappings
+            e2e_step()
         torch.cuda.synchronize()
         # each step between its own events: the host link is shared with the machine's other
         # jobs, so the median step is reported (every step's time beside it)
