@@ -116,10 +116,12 @@ def test_world_backward_matches_oracle(ctx):
 
 
 @pytest.mark.parametrize("wrap", [1, 2, 3])
-def test_wrap_forward_and_backward(ctx, wrap):
+@pytest.mark.parametrize("W,H", [(48, 40), (37, 23)])  # quads, and quads with padded odd sides
+def test_wrap_forward_and_backward(ctx, wrap, W, H):
     """Repeat mode on a UV range that crosses the texture's edges: forward
-    colours of the flat and the batched entry points, and UV gradients."""
-    oid, g, obj, table = world_case(ctx, api.RT_F16, wrap=wrap)
+    colours of the flat and the batched entry points, UV gradients, and the texel
+    gradients of taps that wrap from the last bucket to the first."""
+    oid, g, obj, table = world_case(ctx, api.RT_F16, wrap=wrap, W=W, H=H)
     rng = np.random.default_rng(6)
     g.uv[:] = (g.uv * 2.0 - 0.5 + rng.uniform(-0.01, 0.01, g.uv.shape)).astype(np.float32)
     uv, d, _ = gbuffer_to_dev(g)
@@ -135,9 +137,13 @@ def test_wrap_forward_and_backward(ctx, wrap):
         assert np.abs(out - ref)[~mism].max() <= COLOUR_TOL
     gout = rng.normal(size=(g.F, 4)).astype(np.float32)
     duv = torch.empty_like(uv)
-    api.rt_shade_backward(ctx, uv, d, o, api.RT_QUADRILINEAR, to_dev(gout), None, duv, None)
-    _, guv, _, _ = oracle.shade_backward(table, g.uv, g.dir, obj, api.RT_QUADRILINEAR, gout, want_tex=False,
-                                         want_dir=False)
+    dtex = torch.empty(api.storage_numel(ctx, oid), device=uv.device)
+    api.rt_shade_backward(ctx, uv, d, o, api.RT_QUADRILINEAR, to_dev(gout), {oid: dtex}, duv, None)
+    gt, guv, _, _ = oracle.shade_backward(table, g.uv, g.dir, obj, api.RT_QUADRILINEAR, gout, want_dir=False)
+    gabs, _, _, _ = oracle.shade_backward(table, g.uv, g.dir, obj, api.RT_QUADRILINEAR, np.abs(gout),
+                                          want_uv=False, want_dir=False)
+    got_t = grad_to_atlas(ctx, oid, dtex)
+    assert np.all(np.abs(got_t - gt[oid]) <= 1e-4 * gabs[oid] + 2e-5 * np.abs(gout).max())
     _, oc, _ = oracle.locate(table, g.uv, g.dir, obj, api.RT_QUADRILINEAR)
     far = (np.abs(oc - np.round(oc)) > 1e-3).all(axis=1) & (obj >= 0)
     got = duv.cpu().numpy()
