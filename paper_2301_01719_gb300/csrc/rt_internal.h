@@ -62,7 +62,7 @@ struct GradTable {
     void* p[RT_MAX_OBJECTS];  // float* (FP32 sums) or long long* (fixed-point sums, deterministic mode)
 };
 
-// spec: the storage format shared by every object of the table (dense PLANES,
+// spec: the storage format shared by every object of the table (dense QUADS,
 // clamp mode), or -1; selects a single-format instantiation of the tiled kernels.
 cudaError_t launch_shade(const TexDesc* table, int n_obj, const float* uv, const float* dir, const int32_t* obj,
                          int64_t F, int filter, const Tiling& T, int spec, float* out, unsigned* status,
