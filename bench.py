@@ -55,13 +55,15 @@ def parse_args(argv=None):
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--no-fused-line", action="store_true",
-                   help="skip timing the fused step beside the separate kernels")
+    p.add_argument("--no-other-step", "--no-fused-line", dest="no_other_step", action="store_true",
+                   help="skip timing the other form of the step (fused or separate) beside the timed one")
     p.add_argument("--no-precision", action="store_true",
                    help="skip the storage formats' error against FP32 storage on the step's frames")
     p.add_argument("--samples", type=int, default=4, help="shadow: light samples per fragment")
-    p.add_argument("--fused", action="store_true",
-                   help="the step as one fused forward + L2 loss (zero target) + backward launch")
+    p.add_argument("--separate", action="store_true",
+                   help="time the step as three launches (forward, gradient clear, backward) instead of the "
+                        "default: the clear and one fused forward + L2 loss (zero target) + backward launch")
+    p.add_argument("--fused", action="store_true", help="the fused step (the default)")
     p.add_argument("--deferred", type=int, default=0,
                    help="bake: the deferred payload (albedo + ambient occlusion) over this many AO directions")
     p.add_argument("--workload", choices=["sphere-plane", "voronoi64", "bake", "world", "shadow"],
@@ -78,7 +80,11 @@ def parse_args(argv=None):
                    help="voronoi64: time the fused forward + loss + backward launch in the graph (the clear apart)")
     p.add_argument("--mem-fraction", type=float, default=0.7,
                    help="voronoi64: largest share of free device memory the textures may take")
-    return p.parse_args(argv)
+    a = p.parse_args(argv)
+    if a.fused and a.separate:
+        p.error("--fused and --separate exclude each other")
+    a.fused = not a.separate
+    return a
 
 
 def dist_info():
@@ -548,112 +554,87 @@ def run_radtex(a):
     # the fused step: G-buffer and target in, colour and UV / direction gradients out, each texel read and its
     # gradient read-modified-written once
     fused_bytes = (24 + 16 + 16 + 8 + 12) * F + distinct * (tb + 32) + scale_bytes + index_bytes
-    target = torch.zeros_like(out) if a.fused else None
+    target = torch.zeros_like(out)  # the fused step's L2 target: dL/dout = out - 0 = out, as the separate step
     sums = torch.zeros(2, dtype=torch.float64, device=dev)
 
     stream = torch.cuda.current_stream(dev)
     # screen tile of the batched kernels, picked by the library's autotuner on this workload
     tile, tile_ms = api.rt_autotune(ctx, uv, dirs, obj, filt, out, reps=3)
-    # and of the backward, timed as the step runs it (the gradients it leaves are cleared by every step)
+    # and of the backward (the fused step uses it too), timed as the step runs it (the gradients it
+    # leaves are cleared by every step)
     api.rt_zero_texture_grads(ctx, dtex)
     btile, btile_ms = api.rt_autotune_backward(ctx, uv, dirs, obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE,
                                                reps=2)
 
-    def step():
-        if a.fused:
-            api.rt_zero_texture_grads(ctx, dtex)
-            api.rt_shade_batched_l2_step(ctx, uv, dirs, obj, filt, target, 1.0, out, sums, dtex, duv, ddir,
-                                         api.RT_ACCUMULATE_TEXELS)
-            return
-        api.rt_shade_batched(ctx, uv, dirs, obj, filt, out)
-        api.rt_zero_texture_grads(ctx, dtex)
-        api.rt_shade_batched_backward(ctx, uv, dirs, obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE)
+    # The two forms of the step, as lists of (part name, launch).  Fused: the clear and one
+    # launch doing the forward, dL/dout = out - 0 and the backward.  Separate: the forward, the
+    # clear and the backward with dL/dout = out.  Both leave the same colours and gradients.
+    fused_parts = [("zero", lambda: api.rt_zero_texture_grads(ctx, dtex)),
+                   ("fused", lambda: api.rt_shade_batched_l2_step(ctx, uv, dirs, obj, filt, target, 1.0, out, sums,
+                                                                  dtex, duv, ddir, api.RT_ACCUMULATE_TEXELS))]
+    separate_parts = [("fwd", lambda: api.rt_shade_batched(ctx, uv, dirs, obj, filt, out)),
+                      ("zero", lambda: api.rt_zero_texture_grads(ctx, dtex)),
+                      ("bwd", lambda: api.rt_shade_batched_backward(ctx, uv, dirs, obj, filt, out, dtex, duv, ddir,
+                                                                    api.RT_ACCUMULATE))]
+    main_parts, other_parts = (fused_parts, separate_parts) if a.fused else (separate_parts, fused_parts)
 
-    for _ in range(a.warmup):
-        step()
-    torch.cuda.synchronize()
-    st = api.rt_get_error(ctx)
-    if st != api.RT_OK:
-        raise RuntimeError(f"device status after warm-up: {api.rt_status_string(st)}")
-
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(a.steps)]
-    start = torch.cuda.Event(enable_timing=True)
-    end = torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        clk.mark_start()
-        start.record(stream)
-        for k in range(a.steps):
-            e = ev[k]
-            e[0].record(stream)
-            if not a.fused:
-                api.rt_shade_batched(ctx, uv, dirs, obj, filt, out)
-            e[1].record(stream)
-            api.rt_zero_texture_grads(ctx, dtex)
-            e[2].record(stream)
-            if a.fused:
-                api.rt_shade_batched_l2_step(ctx, uv, dirs, obj, filt, target, 1.0, out, sums, dtex, duv, ddir,
-                                             api.RT_ACCUMULATE_TEXELS)
-            else:
-                api.rt_shade_batched_backward(ctx, uv, dirs, obj, filt, out, dtex, duv, ddir, api.RT_ACCUMULATE)
-            e[3].record(stream)
-        end.record(stream)
+    def run_steps(parts, n, warmup, barrier):
+        """warmup untimed steps, then n steps between CUDA events on the launching stream
+        (one event before each part and one after the step) with the SM clocks sampled.
+        Returns the total ms, the mean ms of each part and the clock summary."""
+        for _ in range(warmup):
+            for _, fn in parts:
+                fn()
         torch.cuda.synchronize()
-        clk.mark_end()
-    if world > 1:
-        torch.distributed.barrier()
-    total_ms = start.elapsed_time(end)
-    fwd_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
-    zero_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
-    bwd_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in ev]))
+        st = api.rt_get_error(ctx)
+        if st != api.RT_OK:
+            raise RuntimeError(f"device status after warm-up: {api.rt_status_string(st)}")
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)] for _ in range(n)]
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        if barrier and world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            clk.mark_start()
+            start.record(stream)
+            for k in range(n):
+                for i, (_, fn) in enumerate(parts):
+                    ev[k][i].record(stream)
+                    fn()
+                ev[k][-1].record(stream)
+            end.record(stream)
+            torch.cuda.synchronize()
+            clk.mark_end()
+        if barrier and world > 1:
+            torch.distributed.barrier()
+        st = api.rt_get_error(ctx)
+        if st != api.RT_OK:
+            raise RuntimeError(f"device status after timing: {api.rt_status_string(st)}")
+        part_ms = {name: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in ev])) for i, (name, _) in
+                   enumerate(parts)}
+        return start.elapsed_time(end), part_ms, clk.summary()
+
+    total_ms, part_ms, clocks = run_steps(main_parts, a.steps, a.warmup, barrier=True)
     total_ms = max_over_ranks(total_ms, dev)
     ms_per_step = total_ms / a.steps
     value = whole_job_rate(F, world, ms_per_step)
-    st = api.rt_get_error(ctx)
-    if st != api.RT_OK:
-        raise RuntimeError(f"device status after timing: {api.rt_status_string(st)}")
 
-    # The same step as one fused launch (forward, dL/dout = out - 0, backward), timed
-    # after the separate kernels on the same inputs: reported beside them.
-    fused_step = None
-    if not a.fused and not a.no_fused_line:
-        f_target = torch.zeros_like(out)
-        f_sums = torch.zeros(2, dtype=torch.float64, device=dev)
-
-        def fstep():
-            api.rt_zero_texture_grads(ctx, dtex)
-            api.rt_shade_batched_l2_step(ctx, uv, dirs, obj, filt, f_target, 1.0, out, f_sums, dtex, duv, ddir,
-                                         api.RT_ACCUMULATE_TEXELS)
-
-        for _ in range(a.warmup):
-            fstep()
-        f_steps = min(a.steps, 20)
-        fev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(f_steps)]
-        torch.cuda.synchronize()
-        with ClockSampler(local) as fclk:
-            fclk.mark_start()
-            for e in fev:
-                e[0].record(stream)
-                api.rt_zero_texture_grads(ctx, dtex)
-                e[1].record(stream)
-                api.rt_shade_batched_l2_step(ctx, uv, dirs, obj, filt, f_target, 1.0, out, f_sums, dtex, duv, ddir,
-                                             api.RT_ACCUMULATE_TEXELS)
-                e[2].record(stream)
-            torch.cuda.synchronize()
-            fclk.mark_end()
-        if api.rt_get_error(ctx) != api.RT_OK:
-            raise RuntimeError("device status after the fused step")
-        f_ms = max_over_ranks(float(np.mean([e[0].elapsed_time(e[2]) for e in fev])), dev)
-        f_kernel_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in fev]))
-        fused_step = {"step": "rt_zero_texture_grads + rt_shade_batched_l2_step(target 0, scale 1, "
-                              "RT_ACCUMULATE_TEXELS): the same gradients in one launch",
-                      "value": whole_job_rate(F, world, f_ms), "unit": "Gfrag/s", "ms_per_step": f_ms,
-                      "steps": f_steps, "fused_ms": f_kernel_ms,
-                      "zero_grad_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in fev])),
-                      "clocks": fclk.summary()}
-        del f_target
+    # The other form of the step, timed after the main one on the same inputs: reported beside it
+    # (and it gives the forward and backward kernels' own times, or the fused kernel's).
+    other = None
+    if not a.no_other_step:
+        o_steps = min(a.steps, 20)
+        o_total, o_parts, o_clocks = run_steps(other_parts, o_steps, a.warmup, barrier=False)
+        o_ms = max_over_ranks(o_total / o_steps, dev)
+        other = {"value": whole_job_rate(F, world, o_ms), "unit": "Gfrag/s", "ms_per_step": o_ms,
+                 "steps": o_steps, "part_ms": o_parts, "clocks": o_clocks}
+    times = dict(part_ms)
+    if other is not None:
+        for k, v in other["part_ms"].items():
+            times.setdefault(k, v)
+    zero_ms = part_ms["zero"]
+    fwd_ms, bwd_ms, fused_ms = times.get("fwd"), times.get("bwd"), times.get("fused")
 
     # End to end through the public API with host buffers: every step copies the
     # G-buffer from pinned host memory and the image back.  The step is pipelined
@@ -723,27 +704,32 @@ def run_radtex(a):
         del h_out
 
     peak, peak_kind = measured_peak()
-    fwd_gbs = fwd_bytes / (fwd_ms * 1e-3) / 1e9 if not a.fused else None
-    bwd_gbs = bwd_bytes / (bwd_ms * 1e-3) / 1e9
     wl = workload_name(a)
 
-    def roof(achieved, kernel, nbytes):
+    def roof(ms, kernel, nbytes):
+        if ms is None:
+            return None
+        achieved = nbytes / (ms * 1e-3) / 1e9
         traffic, traffic_source = recorded_traffic(kernel, nbytes)
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
                 "traffic": traffic, "traffic_source": traffic_source, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": int(nbytes), "kernel": kernel}
 
-    if a.fused:
-        r_fwd = r_bwd = None
-        dominant = roof(fused_bytes / (bwd_ms * 1e-3) / 1e9, f"fused_l2_kernel<{a.filter}, tiled>", fused_bytes)
-    else:
-        r_fwd = roof(fwd_gbs, f"shade_kernel<{a.filter}, tiled>", fwd_bytes)
-        r_bwd = roof(bwd_gbs, f"backward_kernel<{a.filter}, tiled>", bwd_bytes)
-        dominant = r_bwd if bwd_ms >= fwd_ms else r_fwd
-    if fused_step is not None:
-        fused_step["roofline"] = roof(fused_bytes / (fused_step["fused_ms"] * 1e-3) / 1e9,
-                                      f"fused_l2_kernel<{a.filter}, tiled>", fused_bytes)
+    r_fwd = roof(fwd_ms, f"shade_kernel<{a.filter}, tiled>", fwd_bytes)
+    r_bwd = roof(bwd_ms, f"backward_kernel<{a.filter}, tiled>", bwd_bytes)
+    r_fused = roof(fused_ms, f"fused_l2_kernel<{a.filter}, tiled>", fused_bytes)
+    # the dominant kernel of the timed step
+    dominant = r_fused if a.fused else (r_bwd if bwd_ms >= fwd_ms else r_fwd)
+    fused_desc = ("rt_zero_texture_grads + rt_shade_batched_l2_step(target 0, scale 1, RT_ACCUMULATE_TEXELS): "
+                  "forward, dL/dout = out, backward in one launch")
+    separate_desc = ("rt_shade_batched + rt_zero_texture_grads + rt_shade_batched_backward(RT_ACCUMULATE, "
+                     "dL/dout = out)")
+    if other is not None:
+        other["step"] = separate_desc if a.fused else fused_desc
+
+    def rate(ms):
+        return None if ms is None else F / (ms * 1e-3) / 1e9
 
     result = {
         "metric": METRIC, "value": value, "unit": "Gfrag/s", "n_gpus": world, "steps": a.steps,
@@ -754,26 +740,25 @@ def run_radtex(a):
                    "objects": len(oids), "texture_bytes": int(sum(api.rt_texture_info(ctx, o)["bytes"] for o in oids)),
                    "l2": "inputs larger than L2 (G-buffer %.1f GB, textures %.1f GB per rank)" % (
                        24 * F / 1e9, sum(api.rt_texture_info(ctx, o)["bytes"] for o in oids) / 1e9),
-                   "step": ("rt_zero_texture_grads + rt_shade_batched_l2_step(target 0, scale 1, RT_ACCUMULATE_TEXELS): "
-                            "forward, dL/dout = out, backward in one launch" if a.fused else
-                            "rt_shade_batched + rt_zero_texture_grads + rt_shade_batched_backward(RT_ACCUMULATE, "
-                            "dL/dout = out)"),
+                   "step": fused_desc if a.fused else separate_desc,
                    "tile": {"tw": tile[0], "th": tile[1], "bx": tile[2], "by": tile[3], "autotune_ms": tile_ms},
                    "backward_tile": {"tw": btile[0], "th": btile[1], "bx": btile[2], "by": btile[3],
                                      "autotune_ms": btile_ms},
                    "distinct_texels_per_step": int(distinct), "scene_gen_s": round(scene_s, 2),
                    "palette": palette},
-        **({"fused_ms": bwd_ms, "fused_gfrag_s": F / (bwd_ms * 1e-3) / 1e9} if a.fused else
-           {"fwd_gfrag_s": F / (fwd_ms * 1e-3) / 1e9, "bwd_gfrag_s": F / (bwd_ms * 1e-3) / 1e9,
-            "fwd_ms": fwd_ms, "bwd_ms": bwd_ms}),
+        "fused_ms": fused_ms, "fused_gfrag_s": rate(fused_ms),
+        "fwd_ms": fwd_ms, "fwd_gfrag_s": rate(fwd_ms), "bwd_ms": bwd_ms, "bwd_gfrag_s": rate(bwd_ms),
         "zero_grad_ms": zero_ms,
-        "roofline": dominant, "roofline_fwd": r_fwd, "roofline_bwd": r_bwd,
+        "part_times": ("kernel times from per-step CUDA events: those of the timed step, the others from "
+                       "the other form of the step timed after it (%s)" % ("separate_step" if a.fused else
+                                                                        "fused_step")),
+        "roofline": dominant, "roofline_fwd": r_fwd, "roofline_bwd": r_bwd, "roofline_fused": r_fused,
         "gpu_launches": (1 if a.fused else 2) * a.steps,
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "e2e": e2e,
     }
-    if fused_step is not None:
-        result["fused_step"] = fused_step
+    if other is not None:
+        result["separate_step" if a.fused else "fused_step"] = other
     if not a.no_precision and not a.palette:
         result["precision_vs_fp32"] = precision_vs_fp32(a, api, local, uv, dirs, obj, filt, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
