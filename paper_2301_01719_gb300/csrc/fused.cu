@@ -6,9 +6,11 @@
 // direction gradients of the backward for that dL/dout.  The G-buffer and the
 // target are read once, the lookup coordinates are computed once, and the
 // taps gathered for the colour serve the backward too (kept in registers for
-// FP16 / BF16, reloaded from L1 otherwise).  On the 60-pose 1080p step the
-// fused kernel takes 5.04 ms where the forward and the backward take
-// 1.74 + 4.85 ms.
+// FP16 / BF16 / E4M3, reloaded from L1 otherwise).  On the 60-pose 1080p step
+// the fused kernel takes 5.01 ms where the forward and the backward take
+// 1.74 + 4.83 ms.
+#include <type_traits>
+
 #include "launch.h"
 #include "rt_backward.cuh"
 #include "rt_internal.h"
@@ -20,7 +22,8 @@ namespace rt {
 // spilling) 6.21 ms, on the 60-pose 1080p step (textures in row-major planes
 // then).  With FP16 / BF16 quadrilinear textures the 16 taps' 8-byte codes are
 // gathered once and kept in registers (118, no spills) for the coordinate
-// gradients instead of being reloaded from L1: 5.15 -> 5.03 ms.  A variant that
+// gradients instead of being reloaded from L1: 5.15 -> 5.03 ms (E4M3: the
+// 4-byte codes and the buckets' scales, 127 registers, 5.28 -> 5.09 ms).  A variant that
 // forms colour-derivative vectors from the forward's lerps needs far more
 // registers and measured slower at every occupancy (7.0 ms at best against
 // 6.4 ms then).
@@ -39,24 +42,38 @@ __global__ void __launch_bounds__(kBackThreads, (!DET && SPEC >= 0) ? 4 : 1) fus
         float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
         TexDesc d;
         Lookup<FILTER> L;
-        // FP16 / BF16 quadrilinear: the 16 taps' codes stay in registers for the backward
-        constexpr bool kKeepTaps = FILTER == RT_QUADRILINEAR && !DET && (SPEC == RT_F16 || SPEC == RT_BF16);
-        constexpr int kSpec8 = kKeepTaps ? SPEC : RT_F16;
+        // FP16 / BF16 / E4M3 quadrilinear: the 16 taps' codes (and E4M3's four bucket scales)
+        // stay in registers for the backward
+        constexpr bool kE4 = SPEC == RT_E4M3_BUCKET_SCALE;
+        constexpr bool kKeepTaps = FILTER == RT_QUADRILINEAR && !DET && (SPEC == RT_F16 || SPEC == RT_BF16 || kE4);
+        constexpr int kSpec8 = kKeepTaps && !kE4 ? SPEC : RT_F16;
+        using Code = std::conditional_t<kE4, unsigned, uint2>;
         int64_t pl[4];
         int o[4];
-        uint2 code[kKeepTaps ? 4 : 1][kKeepTaps ? 4 : 1];  // [bucket][texel]
+        Code code[kKeepTaps ? 4 : 1][kKeepTaps ? 4 : 1];  // [bucket][texel]
+        float sc[kE4 ? 4 : 1];                             // E4M3: the scale of each bucket
+        auto decode = [&](int b, int k) -> P4 {
+            if constexpr (kE4)
+                return decode4_e4m3(code[b][k], sc[b]);
+            else
+                return decode8<kSpec8>(code[b][k]);
+        };
         const bool valid = fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d);
         if (valid) {
             L = locate<FILTER, (SPEC < 0)>(d, q.u, q.v, q.x, q.y, q.z);
             if constexpr (kKeepTaps) {
                 quad_tap_addresses<RT_LAYOUT_QUADS>(d, L.u, L.v, L.s, L.t, pl, o);
+                if constexpr (kE4) {
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) sc[b] = __ldg(d.scale + o[b]);
+                }
                 P4 tq[4][4];
 #pragma unroll
                 for (int b = 0; b < 4; ++b)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        code[b][k] = __ldg(reinterpret_cast<const uint2*>(d.base) + checked_texel(d, pl[k] + o[b]));
-                        tq[b][k] = decode8<kSpec8>(code[b][k]);
+                        code[b][k] = __ldg(reinterpret_cast<const Code*>(d.base) + checked_texel(d, pl[k] + o[b]));
+                        tq[b][k] = decode(b, k);
                     }
                 c = toF4(quadrilinear_combine(tq, L.u, L.v, L.s, L.t));
             } else {
@@ -82,7 +99,7 @@ __global__ void __launch_bounds__(kBackThreads, (!DET && SPEC >= 0) ? 4 : 1) fus
             if constexpr (kKeepTaps) {
                 reduce_quadrilinear_taps<false>(d, L, pl, o, g, grad);
                 cg = CoordGrad{0.f, 0.f, 0.f, 0.f};
-                if (coord_grads) cg = quad_coord_grads(L, g, [&](int b, int k) { return decode8<kSpec8>(code[b][k]); });
+                if (coord_grads) cg = quad_coord_grads(L, g, decode);
             } else {
                 cg = backward_spec<FILTER, DET, SPEC>(d, L, g, grad, coord_grads);
             }

@@ -445,12 +445,16 @@ __device__ __forceinline__ P4 load_texelP<RT_BF16>(const void* base, int64_t idx
     return decode8<RT_BF16>(__ldg(reinterpret_cast<const uint2*>(base) + idx));
 }
 
-template <>
-__device__ __forceinline__ P4 load_texelP<RT_E4M3_BUCKET_SCALE>(const void* base, int64_t idx, float scale) {
-    unsigned r = __ldg(reinterpret_cast<const unsigned*>(base) + idx);
+// The four channels of a 4-byte E4M3 code times its bucket's scale, in FP32.
+__device__ __forceinline__ P4 decode4_e4m3(unsigned r, float scale) {
     float2 a = e4m3x2_to_float2((unsigned short)(r & 0xFFFFu));
     float2 b = e4m3x2_to_float2((unsigned short)(r >> 16));
     return {pack2(a.x * scale, a.y * scale), pack2(b.x * scale, b.y * scale)};
+}
+
+template <>
+__device__ __forceinline__ P4 load_texelP<RT_E4M3_BUCKET_SCALE>(const void* base, int64_t idx, float scale) {
+    return decode4_e4m3(__ldg(reinterpret_cast<const unsigned*>(base) + idx), scale);
 }
 
 // Vector reduction of four floats into global memory (one 16-byte atomic).
