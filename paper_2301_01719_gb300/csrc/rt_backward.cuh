@@ -37,6 +37,16 @@ __device__ __forceinline__ void red_add_fixed4(unsigned long long* addr, float4 
 // The 16 texel-gradient contributions w_tap g of a quadrilinear lookup on the
 // PLANES / QUADS layouts: planes pl[k] (k = (s0,t0) (s1,t0) (s0,t1) (s1,t1)), spatial
 // offsets o[b] (b = (u0,v0) (u1,v0) (u0,v1) (u1,v1)).
+// The weights a lane whose axis has taps pk0, pk0 + 1 and weight pw (of pk0 + 1)
+// puts on coordinates k0 and k0 + 1: 1 - pw on pk0, pw on pk0 + 1, 0 elsewhere --
+// the values that lane uses for its own taps, bit for bit.
+__device__ __forceinline__ void partner_axis_weights(int k0, int pk0, float pw, float (&out)[2]) {
+    const int dk = k0 - pk0;
+    const float w0 = 1.f - pw;
+    out[0] = dk == 0 ? w0 : (dk == 1 ? pw : 0.f);
+    out[1] = dk == -1 ? w0 : (dk == 0 ? pw : 0.f);
+}
+
 template <bool DET>
 __device__ __forceinline__ void reduce_quadrilinear_taps(const TexDesc& d, const Lookup<RT_QUADRILINEAR>& L,
                                                          const int64_t (&pl)[4], const int (&o)[4], float4 g,
@@ -57,40 +67,61 @@ __device__ __forceinline__ void reduce_quadrilinear_taps(const TexDesc& d, const
                 }
         }
     } else {
-        // Neighbouring fragments often update the same texel through the same
-        // tap: lanes 2m and 2m + 1 (horizontal neighbours on screen) compare
-        // their tap addresses, and on a match the odd lane hands its
-        // contribution to the even lane, which issues one reduction for both.
-        // A lane without a gradient buffer leaves before the exchange (its
-        // partner sees it inactive and reduces alone).
+        // Neighbouring fragments often update the same texels: lanes 2m and
+        // 2m + 1 (horizontal neighbours on screen) exchange, once per fragment,
+        // their texture's addressing (gradient buffer, plane size, width, n,
+        // layout), their four axes' floors k0 and weights, and dL/dout.  Each
+        // lane then knows the other's weight on each of its own taps -- the same
+        // tap or one a bucket or texel over -- as the same product of the same
+        // axis weights the other lane forms, so both decide alike: for a texel
+        // both reduce into, the even lane adds the odd lane's contribution to its
+        // own and issues one reduction, and the odd lane issues none.  Only pairs
+        // whose four axes each have the two taps k0, k0 + 1 merge (not at a
+        // clamped edge or a wrapped seam).  A lane without a gradient buffer
+        // leaves before the exchange (its partner sees it inactive).
         if (!grad) return;
         const unsigned active = __activemask();
         const int lane = threadIdx.x & 31;
         const bool partner = (active >> (lane ^ 1)) & 1u;
+        const bool plain = L.u.k1 == L.u.k0 + 1 && L.v.k1 == L.v.k0 + 1 && L.s.k1 == L.s.k0 + 1 &&
+                           L.t.k1 == L.t.k0 + 1 && d.plane < ((int64_t)1 << 32) && d.W < (1 << 17) && d.n < 256;
+        // the texel index of given coordinates depends on (plane, W, n, layout) only
+        const uint64_t gp = (uint64_t)grad;
+        const unsigned geo = plain ? ((unsigned)d.W | ((unsigned)d.n << 17) | ((unsigned)(d.layout & 3) << 25))
+                                   : (0x80000000u | (unsigned)lane);  // matches no other lane
+        const unsigned id[4] = {(unsigned)gp, (unsigned)(gp >> 32), (unsigned)d.plane, geo};
+        bool merge = partner;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) merge &= __shfl_xor_sync(active, id[m], 1) == id[m];
+        const int pk[4] = {__shfl_xor_sync(active, L.u.k0, 1), __shfl_xor_sync(active, L.v.k0, 1),
+                           __shfl_xor_sync(active, L.s.k0, 1), __shfl_xor_sync(active, L.t.k0, 1)};
+        const float pwk[4] = {__shfl_xor_sync(active, L.u.w, 1), __shfl_xor_sync(active, L.v.w, 1),
+                              __shfl_xor_sync(active, L.s.w, 1), __shfl_xor_sync(active, L.t.w, 1)};
+        const float4 pg = make_float4(__shfl_xor_sync(active, g.x, 1), __shfl_xor_sync(active, g.y, 1),
+                                      __shfl_xor_sync(active, g.z, 1), __shfl_xor_sync(active, g.w, 1));
+        // the partner's weight on this lane's coordinates k0 and k0 + 1 of each axis
+        float pu[2], pv[2], ps[2], pt[2];
+        partner_axis_weights(L.u.k0, pk[0], pwk[0], pu);
+        partner_axis_weights(L.v.k0, pk[1], pwk[1], pv);
+        partner_axis_weights(L.s.k0, pk[2], pwk[2], ps);
+        partner_axis_weights(L.t.k0, pk[3], pwk[3], pt);
 #pragma unroll
         for (int b = 0; b < 4; ++b)
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const float w = wu[b & 1] * wv[b >> 1] * ws[k & 1] * wt[k >> 1];
-                const int64_t idx = checked_texel(d, pl[k] + o[b]);
-                float* addr = static_cast<float*>(grad) + 4 * idx;
-                // a lane with nothing to add gets a key no other lane has
-                const unsigned long long key =
-                    w != 0.f ? (unsigned long long)addr : (~0ull - (unsigned long long)lane);
+                if (w == 0.f) continue;
+                const float pw = pu[b & 1] * pv[b >> 1] * ps[k & 1] * pt[k >> 1];
+                const bool shared = merge && pw != 0.f;
+                if (shared && (lane & 1)) continue;  // the even lane reduces it for both
                 float4 c = make_float4(w * g.x, w * g.y, w * g.z, w * g.w);
-                const unsigned klo = (unsigned)key, khi = (unsigned)(key >> 32);
-                const unsigned plo = __shfl_xor_sync(active, klo, 1), phi = __shfl_xor_sync(active, khi, 1);
-                const float px = __shfl_xor_sync(active, c.x, 1), py = __shfl_xor_sync(active, c.y, 1);
-                const float pz = __shfl_xor_sync(active, c.z, 1), pw = __shfl_xor_sync(active, c.w, 1);
-                const bool same = partner && plo == klo && phi == khi;
-                if (same && (lane & 1)) continue;  // handed to the even lane
-                if (same) {
-                    c.x += px;
-                    c.y += py;
-                    c.z += pz;
-                    c.w += pw;
+                if (shared) {
+                    c.x += pw * pg.x;
+                    c.y += pw * pg.y;
+                    c.z += pw * pg.z;
+                    c.w += pw * pg.w;
                 }
-                if (w != 0.f) red_add_v4(addr, c);
+                red_add_v4(static_cast<float*>(grad) + 4 * checked_texel(d, pl[k] + o[b]), c);
             }
     }
 }
