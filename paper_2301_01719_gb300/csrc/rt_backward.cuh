@@ -31,12 +31,6 @@ __device__ __forceinline__ void red_add_fixed4(unsigned long long* addr, float4 
     atomicAdd(addr + 3, (unsigned long long)__float2ll_rn(v.w * kFixedScale));
 }
 
-// QUADRILINEAR on the PLANES / QUADS layouts: the four in-bucket texels select four
-// planes (64-bit bases), the four buckets four spatial offsets (32-bit), shared
-// by the 16 reductions and the 16 loads.
-// The 16 texel-gradient contributions w_tap g of a quadrilinear lookup on the
-// PLANES / QUADS layouts: planes pl[k] (k = (s0,t0) (s1,t0) (s0,t1) (s1,t1)), spatial
-// offsets o[b] (b = (u0,v0) (u1,v0) (u0,v1) (u1,v1)).
 // The weights a lane whose axis has taps pk0, pk0 + 1 and weight pw (of pk0 + 1)
 // puts on coordinates k0 and k0 + 1: 1 - pw on pk0, pw on pk0 + 1, 0 elsewhere --
 // the values that lane uses for its own taps, bit for bit.
@@ -47,6 +41,12 @@ __device__ __forceinline__ void partner_axis_weights(int k0, int pk0, float pw, 
     out[1] = dk == -1 ? w0 : (dk == 0 ? pw : 0.f);
 }
 
+// QUADRILINEAR on the PLANES / QUADS / palette layouts: the four in-bucket
+// texels select four planes (64-bit bases), the four buckets four spatial
+// offsets (32-bit), shared by the 16 reductions and the 16 loads.  The 16
+// texel-gradient contributions w_tap g of a lookup: planes pl[k] (k = (s0,t0)
+// (s1,t0) (s0,t1) (s1,t1)), spatial offsets o[b] (b = (u0,v0) (u1,v0) (u0,v1)
+// (u1,v1)).
 template <bool DET>
 __device__ __forceinline__ void reduce_quadrilinear_taps(const TexDesc& d, const Lookup<RT_QUADRILINEAR>& L,
                                                          const int64_t (&pl)[4], const int (&o)[4], float4 g,
@@ -86,6 +86,7 @@ __device__ __forceinline__ void reduce_quadrilinear_taps(const TexDesc& d, const
         const bool plain = L.u.k1 == L.u.k0 + 1 && L.v.k1 == L.v.k0 + 1 && L.s.k1 == L.s.k0 + 1 &&
                            L.t.k1 == L.t.k0 + 1 && d.plane < ((int64_t)1 << 32) && d.W < (1 << 17) && d.n < 256;
         // the texel index of given coordinates depends on (plane, W, n, layout) only
+        // (the layouts are 0 to 3)
         const uint64_t gp = (uint64_t)grad;
         const unsigned geo = plain ? ((unsigned)d.W | ((unsigned)d.n << 17) | ((unsigned)(d.layout & 3) << 25))
                                    : (0x80000000u | (unsigned)lane);  // matches no other lane
