@@ -9,13 +9,30 @@
 // FP16 / BF16 / E4M3, reloaded from L1 otherwise).  On the 60-pose 1080p step
 // the fused kernel takes 5.01 ms where the forward and the backward take
 // 1.74 + 4.83 ms.
-#include <type_traits>
-
 #include "launch.h"
 #include "rt_backward.cuh"
 #include "rt_internal.h"
 
 namespace rt {
+
+// The stored code of one texel as the fused step keeps it in registers: 8 bytes
+// for FP16 / BF16, 4 for E4M3 (whose bucket scale is kept beside it).
+template <int FMT>
+struct KeptCode {
+    using type = uint2;
+};
+template <>
+struct KeptCode<RT_E4M3_BUCKET_SCALE> {
+    using type = unsigned;
+};
+
+template <int FMT>
+__device__ __forceinline__ P4 decode_kept(typename KeptCode<FMT>::type c, float scale) {
+    if constexpr (FMT == RT_E4M3_BUCKET_SCALE)
+        return decode4_e4m3(c, scale);
+    else
+        return decode8<FMT>(c);
+}
 
 // Held to 128 registers (4 blocks, 16 warps per SM): at 5 blocks (96
 // registers) the kernel took 5.86 ms against 5.65 ms, at 6 blocks (80,
@@ -46,18 +63,12 @@ __global__ void __launch_bounds__(kBackThreads, (!DET && SPEC >= 0) ? 4 : 1) fus
         // stay in registers for the backward
         constexpr bool kE4 = SPEC == RT_E4M3_BUCKET_SCALE;
         constexpr bool kKeepTaps = FILTER == RT_QUADRILINEAR && !DET && (SPEC == RT_F16 || SPEC == RT_BF16 || kE4);
-        constexpr int kSpec8 = kKeepTaps && !kE4 ? SPEC : RT_F16;
-        using Code = std::conditional_t<kE4, unsigned, uint2>;
+        constexpr int kKept = kKeepTaps ? SPEC : RT_F16;
+        using Code = typename KeptCode<kKept>::type;
         int64_t pl[4];
         int o[4];
         Code code[kKeepTaps ? 4 : 1][kKeepTaps ? 4 : 1];  // [bucket][texel]
         float sc[kE4 ? 4 : 1];                             // E4M3: the scale of each bucket
-        auto decode = [&](int b, int k) -> P4 {
-            if constexpr (kE4)
-                return decode4_e4m3(code[b][k], sc[b]);
-            else
-                return decode8<kSpec8>(code[b][k]);
-        };
         const bool valid = fragment_valid(table, n_obj, q.o, q.u, q.v, q.x, q.y, q.z, status, d);
         if (valid) {
             L = locate<FILTER, (SPEC < 0)>(d, q.u, q.v, q.x, q.y, q.z);
@@ -73,7 +84,7 @@ __global__ void __launch_bounds__(kBackThreads, (!DET && SPEC >= 0) ? 4 : 1) fus
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         code[b][k] = __ldg(reinterpret_cast<const Code*>(d.base) + checked_texel(d, pl[k] + o[b]));
-                        tq[b][k] = decode(b, k);
+                        tq[b][k] = decode_kept<kKept>(code[b][k], sc[kE4 ? b : 0]);
                     }
                 c = toF4(quadrilinear_combine(tq, L.u, L.v, L.s, L.t));
             } else {
@@ -99,7 +110,8 @@ __global__ void __launch_bounds__(kBackThreads, (!DET && SPEC >= 0) ? 4 : 1) fus
             if constexpr (kKeepTaps) {
                 reduce_quadrilinear_taps<false>(d, L, pl, o, g, grad);
                 cg = CoordGrad{0.f, 0.f, 0.f, 0.f};
-                if (coord_grads) cg = quad_coord_grads(L, g, decode);
+                if (coord_grads)
+                    cg = quad_coord_grads(L, g, [&](int b, int k) { return decode_kept<kKept>(code[b][k], sc[kE4 ? b : 0]); });
             } else {
                 cg = backward_spec<FILTER, DET, SPEC>(d, L, g, grad, coord_grads);
             }
