@@ -61,3 +61,20 @@ def test_gpu_arm_fails_loudly_without_cuda():
     r = bench("--steps", "1", "--warmup", "1", *SMALL)
     assert r.returncode != 0
     assert "CUDA" in (r.stderr + r.stdout)
+
+
+def test_step_form_flags():
+    """The timed step is the fused launch unless --separate asks for the three launches;
+    --fused names the default, the two exclude each other, and --no-fused-line is the
+    older name of --no-other-step."""
+    sys.path.insert(0, ROOT)
+    import bench as b
+
+    assert b.parse_args([]).fused is True
+    assert b.parse_args(["--fused"]).fused is True
+    assert b.parse_args(["--separate"]).fused is False
+    with pytest.raises(SystemExit):
+        b.parse_args(["--fused", "--separate"])
+    assert b.parse_args(["--no-fused-line"]).no_other_step is True
+    assert b.parse_args(["--no-other-step"]).no_other_step is True
+    assert b.parse_args([]).no_other_step is False
