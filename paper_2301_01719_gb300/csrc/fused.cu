@@ -7,8 +7,8 @@
 // target are read once, the lookup coordinates are computed once, and the
 // taps gathered for the colour serve the backward too (kept in registers for
 // FP16 / BF16 / E4M3, reloaded from L1 otherwise).  On the 60-pose 1080p step
-// the fused kernel takes 5.01 ms where the forward and the backward take
-// 1.74 + 4.83 ms.
+// the fused kernel takes 4.83 ms where the forward and the backward take
+// 1.74 + 4.62 ms.
 #include "launch.h"
 #include "rt_backward.cuh"
 #include "rt_internal.h"
@@ -38,9 +38,10 @@ __device__ __forceinline__ P4 decode_kept(typename KeptCode<FMT>::type c, float 
 // registers) the kernel took 5.86 ms against 5.65 ms, at 6 blocks (80,
 // spilling) 6.21 ms, on the 60-pose 1080p step (textures in row-major planes
 // then).  With FP16 / BF16 quadrilinear textures the 16 taps' 8-byte codes are
-// gathered once and kept in registers (118, no spills) for the coordinate
-// gradients instead of being reloaded from L1: 5.15 -> 5.03 ms (E4M3: the
-// 4-byte codes and the buckets' scales, 127 registers, 5.28 -> 5.09 ms).  A variant that
+// gathered once and kept in registers (118 then, no spills; 126 with the
+// reductions' once-per-fragment pair exchange) for the coordinate gradients
+// instead of being reloaded from L1: 5.15 -> 5.03 ms (E4M3: the 4-byte codes and
+// the buckets' scales, 5.28 -> 5.09 ms).  A variant that
 // forms colour-derivative vectors from the forward's lerps needs far more
 // registers and measured slower at every occupancy (7.0 ms at best against
 // 6.4 ms then).
